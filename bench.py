@@ -1,0 +1,367 @@
+"""Benchmark of the fractional FEM hot path on one GB300 (or N independent replicas).
+
+One step = the whole hot path on the 16^3 jittered cube (24,576 tets, 98,304 Gauss
+points, 3,375 dofs, alpha = (1.3, 1.6, 1.8), K = (1, 2, 0.5)): mesh records and
+transverse bins/template (mesh_upload), FP64 path walk + closed-form derivative
+tables + contraction (assemble), load vector + factorisation + refined solve (solve).
+Inputs (vertices, tets, nodal f) are resident in HBM when the timed region starts.
+
+metric: Gauss-point paths per second - one path = one Gauss point and one axis, both
+directions walked and tabulated - through the whole step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--precision tf32x3|fp32|fp64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cube16_jitter"
+METRIC = "gauss_point_paths_per_s"
+UNIT = "paths/s"
+L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------------
+def oracle_step(mesh, w, f):
+    import oracle
+    o = oracle.Oracle.from_mesh(mesh)
+    A = o.assemble(w["alpha"], w["K"])
+    u = oracle.solve(A, o.load(f))
+    return 3 * o.n_gp, u
+
+
+def cpu_baseline(mesh, w, f):
+    t0 = time.perf_counter()
+    n_paths, _ = oracle_step(mesh, w, f)
+    dt = time.perf_counter() - t0
+    return {"value": n_paths / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full step of {WORKLOAD} (mesh records, {n_paths} paths walked and "
+                      f"tabulated, sparse-row contraction, Cholesky solve) in {dt:.1f} s, "
+                      f"single-threaded C"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    from paper_1811_03339_gb300 import inputs
+    w = inputs.WORKLOADS[WORKLOAD]
+    mesh = inputs.workload_mesh(WORKLOAD)
+    f = inputs.nodal_source(mesh, w["alpha"], w["K"])
+    times = []
+    budget = 150.0
+    t_start = time.perf_counter()
+    steps_run = 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        n_paths, _ = oracle_step(mesh, w, f)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            steps_run += 1
+        if time.perf_counter() - t_start > budget and steps_run >= 1:
+            break
+    value = n_paths * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": len(times), "steps_requested": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tets": int(mesh.n_tets), "gauss_points": 4 * int(mesh.n_tets),
+                   "alpha": list(w["alpha"]), "K": list(w["K"])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "full steps of the workload (oracle, single-threaded C); "
+                                   "stopped early after 150 s of work"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_1811_03339_gb300 import fem3, inputs
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = inputs.WORKLOADS[WORKLOAD]
+    mesh = inputs.workload_mesh(WORKLOAD)
+    alpha, K = w["alpha"], w["K"]
+    f_host = inputs.nodal_source(mesh, alpha, K)
+    verts_d = torch.from_numpy(mesh.verts).to(dev)
+    tets_d = torch.from_numpy(mesh.tets).to(dev)
+    f_d = torch.from_numpy(f_host).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    n_paths = 3 * 4 * mesh.n_tets
+    stream = torch.cuda.current_stream()
+
+    def step(precision, profile=False, keep=False):
+        m = fem3.Mesh(verts_d, tets_d, profile=profile)
+        m.assemble(alpha, K, precision)
+        u = m.solve(f_d, tol=1e-12)
+        if keep:
+            return m, u
+        m.free()
+        return None, u
+
+    def timed(precision, k, warm):
+        for _ in range(warm):
+            step(precision)
+        times = []
+        for _ in range(k):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(precision)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # --- main timed region: mixed-precision form ---------------------------------
+    barrier()
+    with ClockSampler(local) as clk:
+        times = timed(args.precision, args.steps, args.warmup)
+    barrier()
+    t_mix = sum(times)
+    if world > 1:
+        t = torch.tensor([t_mix], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_mix = float(t.item())
+    ms_step = t_mix / args.steps
+    value = world * n_paths * args.steps / (t_mix / 1e3)
+
+    # --- FP64 form (comparison) ----------------------------------------------------
+    k64 = max(2, min(args.steps, 5))
+    t64 = timed("fp64", k64, 1)
+    ms_fp64 = sum(t64) / k64
+
+    # --- stage breakdown and counters (profiled, untimed) ----------------------------
+    m, u_mix = step(args.precision, profile=True, keep=True)
+    stages = m.stage_ms()
+    m.sync()
+    cnt = m.counters()
+    m.free()
+    m64, u64 = step("fp64", profile=True, keep=True)
+    stages64 = m64.stage_ms()
+    m64.free()
+    rel_mix_fp64 = float(torch.linalg.norm(u_mix - u64) / torch.linalg.norm(u64))
+
+    # walk+tables kernel: 3 launches per step (one per axis), timed live by the library's
+    # events on the launch stream
+    walk_ms = stages[2] / 3.0
+    segs_per_launch = cnt["segments"] / 3.0
+    fp64_flops_per_seg = 46.0
+    walk_flops = fp64_flops_per_seg * segs_per_launch
+    fp64_peak_gflops = 1250.0
+    roofline = {
+        "kernel": "k_walk_tables",
+        "bound": "alu", "unit": "GFLOP/s (FP64)",
+        "achieved": walk_flops / (walk_ms * 1e-3) / 1e9,
+        "peak": fp64_peak_gflops,
+        "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
+        "frac": walk_flops / (walk_ms * 1e-3) / 1e9 / fp64_peak_gflops,
+        "traffic": None,
+        "launch_ms": walk_ms,
+        "algorithmic_unit": f"{fp64_flops_per_seg:.0f} FP64 flops per walked segment "
+                            "(pow excluded)",
+    }
+
+    # --- end to end through the C ABI with host buffers -----------------------------
+    verts_h = torch.from_numpy(mesh.verts).pin_memory()
+    tets_h = torch.from_numpy(mesh.tets).pin_memory()
+    f_h = torch.from_numpy(f_host).pin_memory()
+    e2e_t = []
+    n_dof = None
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mh = fem3.Mesh(verts_h.numpy(), tets_h.numpy())
+        mh.assemble(alpha, K, args.precision)
+        u = mh.solve(f_h.numpy(), tol=1e-12)
+        u_host = u.cpu()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        n_dof = mh.n_dof
+        mh.free()
+        if it >= args.warmup:
+            e2e_t.append(e0.elapsed_time(e1))
+    e2e_value = world * n_paths * len(e2e_t) / (sum(e2e_t) / 1e3)
+    h2d = mesh.verts.nbytes + mesh.tets.nbytes + f_host.nbytes
+    d2h = 8 * n_dof
+
+    # --- kernel launches per step (CUPTI via torch.profiler, outside the timed region)
+    launches = None
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            step(args.precision)
+            torch.cuda.synchronize()
+        launches = sum(1 for e in prof.events()
+                       if e.device_type.name == "CUDA" and not e.name.lower().startswith("memcpy")
+                       and not e.name.lower().startswith("memset")) * args.steps
+    except Exception:
+        launches = None
+
+    line = None
+    if rank == 0:
+        peaks, src = _peaks()
+        base = cpu_baseline(mesh, w, f_host) if (world == 1 and not args.no_cpu_baseline) else None
+        ctr_flops = cnt["contract_flops"]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"tf32x3": "f64 walk/tables, tf32x3 contraction, f32 factor, f64 refinement",
+                      "fp32": "f64 walk/tables, f32 contraction and factor, f64 refinement",
+                      "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tets": int(mesh.n_tets),
+                       "gauss_points": 4 * int(mesh.n_tets), "dofs": int(n_dof),
+                       "paths_per_step": n_paths, "alpha": list(alpha), "K": list(K),
+                       "precision": args.precision, "parallelism": f"replicas{world}",
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": base,
+            "clocks": clk.summary(),
+            "fp64_form_ms_per_step": ms_fp64,
+            "mixed_vs_fp64_speedup": ms_fp64 / ms_step,
+            "u_rel_diff_mixed_vs_fp64": rel_mix_fp64,
+            "stages_ms": dict(zip(["mesh", "bins", "walk_tables", "contract", "load", "factor",
+                                   "solve_refine"], [round(x, 4) for x in stages])),
+            "stages_ms_fp64": dict(zip(["mesh", "bins", "walk_tables", "contract", "load",
+                                        "factor", "solve_refine"],
+                                       [round(x, 4) for x in stages64])),
+            "segments_per_step": cnt["segments"],
+            "contraction": {"bin_dense_gflop": ctr_flops / 1e9,
+                            "gflops": ctr_flops / (stages[3] * 1e-3) / 1e9 if stages[3] > 0 else None},
+            "peaks_source": src,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["tf32x3", "fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * fem3.h - C ABI of the GB300 (sm_103a) library for the fractional finite element
+ * assembly of Yang, Nie, Yuan and Wang, "Finite Element Methods for Fractional PDEs in
+ * Three Dimensions" (arXiv 1811.03339).
+ *
+ * Problem: the Riesz-type operator -sum_i K_i d^{alpha_i} u / d|x_i|^{alpha_i} = f on a
+ * convex polyhedron meshed by linear tetrahedra, u = 0 outside the domain.  The
+ * Galerkin matrix (Section 2.1, the uniform form (c D^a_i u, D^b_i v) with a = b =
+ * alpha_i / 2 and the Riesz constant s_i = 1/(2 cos(pi alpha_i/2))) is
+ *
+ *     A = sum_i s_i K_i (L_i^T W R_i + R_i^T W L_i),
+ *
+ * where L_i[g, j] / R_i[g, j] is the left / right Riemann-Liouville derivative of
+ * order alpha_i/2 of the P1 basis function of interior vertex j at Gauss point g along
+ * axis i, and W = diag(Gauss weights).  The derivatives are summed over the path from
+ * the Gauss point to the domain boundary (Section 2.2 path search).
+ *
+ * Conventions for every call:
+ *   - Every call returns an int status: FEM3_OK (0) or a negative FEM3_E_* code.  The
+ *     text of the last error of the calling thread is available from fem3_last_error.
+ *     No exception crosses this interface.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Work is enqueued on it; results are ready when the stream reaches them.  Errors
+ *     found by kernels (walk cap, template miss, non-SPD pivot) are reported by the
+ *     next call that synchronises: fem3_sync, fem3_solve (which reads residual norms)
+ *     and fem3_mesh_upload.
+ *   - Pointers documented as "host or device" are inspected with
+ *     cudaPointerGetAttributes; host memory is copied to the device inside the call
+ *     (pinned host memory makes the copy asynchronous).  Pointers documented as
+ *     "device" must be device (or managed) memory on the current device.
+ *   - Dense matrices are row-major; multi-vector arguments are column-major
+ *     [rows][nrhs] (column r starts at r * rows).
+ *   - The library owns the memory behind a fem3_mesh handle until fem3_mesh_free.
+ *     It never frees caller memory.
+ */
+#ifndef FEM3_H
+#define FEM3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FEM3_OK 0
+#define FEM3_E_ARG (-1)          /* invalid argument (null, size, range) */
+#define FEM3_E_MESH (-2)         /* degenerate tet, non-manifold or non-conforming mesh */
+#define FEM3_E_WALK (-3)         /* a path walk exceeded its step cap (no hang) */
+#define FEM3_E_NOT_SPD (-4)      /* Cholesky met a non-positive pivot */
+#define FEM3_E_NO_CONVERGE (-5)  /* iterative refinement did not reach the tolerance */
+#define FEM3_E_CUDA (-6)         /* a CUDA runtime call failed */
+#define FEM3_E_OOM (-7)          /* device allocation failed */
+#define FEM3_E_STATE (-8)        /* call order violated (e.g. solve before assemble) */
+#define FEM3_E_TEMPLATE (-9)     /* a path touched a dof outside its bin's template set */
+
+/* arithmetic of the contraction and of the factorisation */
+#define FEM3_FP64 0     /* FP64 tables, FP64 contraction (CUDA cores), FP64 Cholesky */
+#define FEM3_TF32X3 1   /* FP64 tables split into TF32 hi/lo, 3 tensor-core products
+                           (tcgen05 kind::tf32, FP32 accumulate); FP32 Cholesky;
+                           FP64 iterative refinement against the FP64 tables */
+#define FEM3_FP32 2     /* FP64 tables rounded to FP32, FP32 contraction (CUDA cores);
+                           FP32 Cholesky; FP64 iterative refinement */
+
+typedef struct fem3_mesh_s *fem3_mesh;
+
+typedef struct fem3_options {
+    double bin_scale;  /* transverse bin width in units of the mean cell size h
+                          (h = (6 * mean tet volume)^(1/3)); <= 0 selects 1.0 */
+    int32_t max_steps; /* cap on tets crossed by one walk; <= 0 selects
+                          8 * n_tets^(1/3) + 64 */
+    int32_t profile;   /* nonzero: record CUDA events around each stage (fem3_stage_ms) */
+} fem3_options;
+
+/*
+ * fem3_mesh_upload - build the device records of a tetrahedral mesh.
+ *
+ * Section 2.2 ("Assume we have known the adjacent information of the triangulation"):
+ * per tet the 4x4 barycentric (volume-coordinate) map, its volume and the four face
+ * neighbours (hash matching of sorted face keys); per vertex the list of tets holding
+ * it (the m-face star searched on edge and vertex exits); the boundary vertices (on a
+ * face without neighbour) and the dof numbering (interior vertices in ascending node
+ * order, u = 0 outside the domain, Section 3); the 4-point degree-2 Gauss rule per tet
+ * (Section 2.1 quadrature); and, per axis, the transverse bins with their template dof
+ * sets (Section 2.3 template matrix, read per axis as overlap of element-patch
+ * bounding boxes in the coordinates other than the axis) that lay out the tables.
+ *
+ *   verts    host or device, float64 [n_nodes][3]; copied.
+ *   tets     host or device, int32 [n_tets][4] node ids, any orientation; copied.
+ *   opt      host, may be NULL (defaults).
+ *   out      host; receives the handle.
+ * Requires 4 <= n_nodes < 2^21 and 1 <= n_tets < 2^29.  Synchronises `stream`.
+ * Errors: FEM3_E_ARG, FEM3_E_MESH (zero-volume tet, a face shared by > 2 tets),
+ * FEM3_E_OOM, FEM3_E_CUDA.
+ */
+int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets,
+                     int64_t n_tets, const fem3_options *opt, void *stream, fem3_mesh *out);
+
+/* Sizes of the mesh.  dof_of_node: host int32 [n_nodes] (dof index or -1), may be NULL.
+ * Any output pointer may be NULL. */
+int fem3_mesh_info(fem3_mesh m, int64_t *n_dof, int64_t *n_gp, int32_t *dof_of_node);
+
+/*
+ * fem3_assemble - path walk, derivative tables and contraction (Sections 2.1-2.3).
+ *
+ * For every Gauss point g and axis i the left and right paths are walked in FP64
+ * across tets (Section 2.2: interval b~ + r d~ >= 0 per tet, exit m-face from the
+ * zero pattern of the go-out volume coordinate).  On each segment the left/right
+ * Riemann-Liouville derivative of order gamma = alpha_i/2 of every local P1 basis
+ * function is added in closed form (integration by parts of eq. "def" on a segment
+ * where the basis function is linear):
+ *     L_i[g,j] += dphi_j/dx_i * (r_far^(1-gamma) - r_near^(1-gamma)) / Gamma(2-gamma)
+ *     R_i[g,j] -= (same with the right path)
+ * Then A = sum_i s_i K_i (L_i^T W R_i + R_i^T W L_i), s_i = 1/(2 cos(pi alpha_i/2)).
+ *
+ *   alpha    host float64[3], each in (1, 2] (alpha = 2 gives the P1 Laplacian).
+ *   K        host float64[3], each > 0.
+ *   precision  FEM3_FP64, FEM3_TF32X3 or FEM3_FP32 (see above).
+ *   A_out    device float64 [n_dof][n_dof] or NULL; when given, the assembled matrix
+ *            (converted to FP64 for the mixed precisions) is written there.
+ * The matrix and its precision stay in the handle for fem3_solve / fem3_adjoint.
+ * Errors (FEM3_E_WALK, FEM3_E_TEMPLATE) are reported at the next synchronising call.
+ */
+int fem3_assemble(fem3_mesh m, const double alpha[3], const double K[3], int precision,
+                  double *A_out, void *stream);
+
+/* Load vector b = M f, M the P1 mass matrix (rows: dofs, columns: all nodes), the
+ * weak right-hand side (f, v) of Section 3.
+ *   f    host or device float64 column-major [n_nodes][nrhs] (nodal values).
+ *   b    device float64 column-major [n_dof][nrhs]. */
+int fem3_load(fem3_mesh m, const double *f, int nrhs, double *b, void *stream);
+
+/*
+ * fem3_solve - u = A^{-1} M f for the last assembled A.
+ *   FP64: FP64 Cholesky and triangular solves.
+ *   TF32X3 / FP32: FP32 Cholesky of the mixed-precision A, then iterative refinement
+ *   with residuals r = M f - A u where A u is applied in FP64 from the FP64 tables,
+ *   until ||r||_2 <= tol ||M f||_2 for every column or max_iter corrections.
+ *   f         host or device float64 column-major [n_nodes][nrhs].
+ *   u         device float64 column-major [n_dof][nrhs].
+ *   iters_out host int or NULL: refinement steps taken (0 for FP64).
+ *   resid_out host float64 or NULL: largest final relative residual.
+ * Synchronises `stream`.  Errors: FEM3_E_STATE (no matrix), FEM3_E_NOT_SPD,
+ * FEM3_E_NO_CONVERGE (u then holds the last iterate), FEM3_E_WALK, FEM3_E_TEMPLATE.
+ */
+int fem3_solve(fem3_mesh m, const double *f, int nrhs, double tol, int max_iter, double *u,
+               int *iters_out, double *resid_out, void *stream);
+
+/*
+ * fem3_adjoint - gradient of J = 0.5 ||u - u_obs||^2 with u = A(K)^{-1} M f.
+ *   lambda = A^{-1} (u - u_obs)  (same factorisation and refinement as fem3_solve),
+ *   dJ/dK_i = -s_i sum_g w_g ((L_i lambda)_g (R_i u)_g + (R_i lambda)_g (L_i u)_g),
+ *   dJ/df   = M^T lambda (nodal).
+ *   u, u_obs  device float64 [n_dof] (one right-hand side).
+ *   dJ_dK     host float64[3].
+ *   dJ_df     device float64 [n_nodes] or NULL.
+ * Synchronises `stream`.  Not in the paper: the gradient of the discrete solve.
+ */
+int fem3_adjoint(fem3_mesh m, const double *u, const double *u_obs, double tol, int max_iter,
+                 double *dJ_dK, double *dJ_df, void *stream);
+
+/*
+ * fem3_paths - export walks for parity checks (Section 2.2).
+ *   For each Gauss point gps[l] (device int64 [n_lines]) along `axis` in direction
+ *   dir (-1 left, +1 right): tet ids (device int32 [n_lines][cap]), segment ends
+ *   r_in / r_out (device float64 [n_lines][cap]) and the segment count (device int32
+ *   [n_lines]; -1 if the walk exceeded cap or its step limit).
+ */
+int fem3_paths(fem3_mesh m, int axis, int dir, const int64_t *gps, int64_t n_lines, int cap,
+               int32_t *tet_out, double *r_in_out, double *r_out_out, int32_t *nseg_out,
+               void *stream);
+
+/*
+ * fem3_table_rows - export rows of the FP64 derivative tables of the last assemble.
+ *   rows: device float64 [n][n_dof]; row l = L_axis[gps[l], :] (dir = -1) or
+ *   R_axis[gps[l], :] (dir = +1) scattered from the binned storage.
+ */
+int fem3_table_rows(fem3_mesh m, int axis, int dir, const int64_t *gps, int64_t n,
+                    double *rows, void *stream);
+
+/* Synchronise `stream` and report errors recorded by kernels since the last check. */
+int fem3_sync(fem3_mesh m, void *stream);
+
+/* Stage timings in milliseconds from the last profiled calls (opt.profile != 0).
+ * Stages: 0 mesh geometry, 1 bins/template, 2 walk+tables, 3 contraction,
+ * 4 load vector, 5 factorisation, 6 triangular solves + refinement. */
+int fem3_stage_ms(fem3_mesh m, int stage, float *ms);
+
+/* Counters of the last assemble: total segments walked (all axes, both sides) and
+ * algorithmic contraction flops (sum over bins of 2 * D_b^2 * G_b per product). */
+int fem3_counters(fem3_mesh m, int64_t *segments, double *contract_flops,
+                  int64_t *table_bytes);
+
+/* Text of the last error of the calling thread. */
+int fem3_last_error(char *buf, size_t len);
+
+void fem3_mesh_free(fem3_mesh m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEM3_H */

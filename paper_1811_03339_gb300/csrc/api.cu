@@ -1,0 +1,401 @@
+// C ABI entry points of libfem3 (declared in include/fem3.h).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+
+#include "fem3_impl.cuh"
+
+namespace fem3 {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *where) {
+    int code = (e == cudaErrorMemoryAllocation) ? FEM3_E_OOM : FEM3_E_CUDA;
+    return set_error(code, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int dev_alloc(Mesh *m, void **p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMallocAsync(p, bytes, m->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_error(e, "cudaMallocAsync");
+    }
+    m->allocs.push_back(*p);
+    return FEM3_OK;
+}
+
+void dev_free_all(Mesh *m) {
+    for (void *p : m->allocs) cudaFreeAsync(p, m->stream);
+    m->allocs.clear();
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void stage_begin(Mesh *m, int stage) {
+    if (m->profile) cudaEventRecord(m->ev[2 * stage], m->stream);
+}
+void stage_end(Mesh *m, int stage) {
+    if (m->profile) cudaEventRecord(m->ev[2 * stage + 1], m->stream);
+}
+void stage_collect(Mesh *m) {
+    if (!m->profile) return;
+    cudaStreamSynchronize(m->stream);
+    for (int k = 0; k < 7; k++) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, m->ev[2 * k], m->ev[2 * k + 1]) == cudaSuccess)
+            m->stage_ms[k] = ms;
+        else
+            cudaGetLastError();
+    }
+}
+
+int read_errors(Mesh *m, int32_t *h_err) {
+    FEM3_CUDA(cudaMemcpyAsync(h_err, m->err, sizeof(int32_t) * ERR_COUNT, cudaMemcpyDeviceToHost,
+                              m->stream));
+    FEM3_CUDA(cudaStreamSynchronize(m->stream));
+    return FEM3_OK;
+}
+
+static int check_errors(Mesh *m) {
+    int32_t e[ERR_COUNT];
+    FEM3_TRY(read_errors(m, e));
+    if (e[ERR_WALK])
+        return set_error(FEM3_E_WALK, std::to_string(e[ERR_WALK]) +
+                                          " path walks exceeded the step cap or found no exit");
+    if (e[ERR_TEMPLATE])
+        return set_error(FEM3_E_TEMPLATE, std::to_string(e[ERR_TEMPLATE]) +
+                                              " table updates fell outside the bin template");
+    if (e[ERR_NOT_SPD]) {
+        int col = e[ERR_NOT_SPD] - 1;
+        cudaMemsetAsync(m->err + ERR_NOT_SPD, 0, sizeof(int32_t), m->stream);
+        return set_error(FEM3_E_NOT_SPD,
+                         "non-positive pivot in Cholesky at column " + std::to_string(col));
+    }
+    if (e[ERR_MESH] || e[ERR_FACE]) return set_error(FEM3_E_MESH, "mesh error");
+    return FEM3_OK;
+}
+
+// Copy a host or device array into a device buffer owned by the mesh (or return the
+// device pointer itself).
+static int to_device(Mesh *m, const void *src, size_t bytes, const void **dst, void **owned) {
+    *owned = nullptr;
+    if (is_device_ptr(src)) {
+        *dst = src;
+        return FEM3_OK;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, m->stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync");
+    e = cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, m->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(p, m->stream);
+        return cuda_error(e, "cudaMemcpyAsync");
+    }
+    *dst = p;
+    *owned = p;
+    return FEM3_OK;
+}
+
+}  // namespace fem3
+
+using namespace fem3;
+
+extern "C" {
+
+int fem3_last_error(char *buf, size_t len) {
+    if (!buf || len == 0) return FEM3_E_ARG;
+    snprintf(buf, len, "%s", g_last_error.c_str());
+    return FEM3_OK;
+}
+
+void fem3_mesh_free(fem3_mesh h) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m) return;
+    dev_free_all(m);
+    cudaStreamSynchronize(m->stream);
+    if (m->h_norms) cudaFreeHost(m->h_norms);
+    if (m->ev_made)
+        for (int k = 0; k < 16; k++) cudaEventDestroy(m->ev[k]);
+    delete m;
+}
+
+int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                     const fem3_options *opt, void *stream, fem3_mesh *out) {
+    if (!verts || !tets || !out) return set_error(FEM3_E_ARG, "null argument");
+    *out = nullptr;
+    if (n_nodes < 4 || n_nodes >= (1ll << 21) || n_tets < 1 || n_tets >= (1ll << 29))
+        return set_error(FEM3_E_ARG, "mesh size out of range (4 <= n_nodes < 2^21, "
+                                     "1 <= n_tets < 2^29)");
+    Mesh *m = new Mesh();
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaGetDevice(&m->device);
+    m->n_nodes = n_nodes;
+    m->n_tets = n_tets;
+    m->n_gp = 4 * n_tets;
+    m->bin_scale = (opt && opt->bin_scale > 0) ? opt->bin_scale : 1.0;
+    m->max_steps = (opt && opt->max_steps > 0) ? opt->max_steps
+                                               : (int)(8.0 * cbrt((double)n_tets)) + 64;
+    m->profile = opt && opt->profile;
+    auto fail = [&](int code) {
+        fem3_mesh_free(reinterpret_cast<fem3_mesh>(m));
+        return code;
+    };
+    if (m->profile) {
+        for (int k = 0; k < 16; k++) cudaEventCreate(&m->ev[k]);
+        m->ev_made = true;
+    }
+    // keep freed pool memory cached so that repeated uploads do not hit the driver
+    {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, m->device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+    }
+    int st;
+    stage_begin(m, 0);
+    if ((st = dev_alloc_t(m, &m->err, ERR_COUNT)) != FEM3_OK) return fail(st);
+    if ((st = dev_alloc_t(m, &m->norms, 64)) != FEM3_OK) return fail(st);
+    if (cudaMallocHost(&m->h_norms, 64 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(set_error(FEM3_E_OOM, "cudaMallocHost"));
+    }
+    if (cudaMemsetAsync(m->err, 0, sizeof(int32_t) * ERR_COUNT, m->stream) != cudaSuccess)
+        return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
+    if ((st = dev_alloc_t(m, &m->verts, 3 * n_nodes)) != FEM3_OK) return fail(st);
+    if ((st = dev_alloc_t(m, &m->tets, 4 * n_tets)) != FEM3_OK) return fail(st);
+    cudaMemcpyKind kv = is_device_ptr(verts) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaMemcpyKind kt = is_device_ptr(tets) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(m->verts, verts, sizeof(double) * 3 * n_nodes, kv, m->stream) != cudaSuccess ||
+        cudaMemcpyAsync(m->tets, tets, sizeof(int32_t) * 4 * n_tets, kt, m->stream) != cudaSuccess)
+        return fail(cuda_error(cudaGetLastError(), "cudaMemcpyAsync"));
+    if ((st = mesh_build(m, m->verts, m->tets)) != FEM3_OK) return fail(st);
+    stage_end(m, 0);
+    stage_begin(m, 1);
+    if ((st = bins_build(m)) != FEM3_OK) return fail(st);
+    stage_end(m, 1);
+    const int64_t n = std::max<int64_t>(1, m->n_dof);
+    for (int k = 0; k < 6; k++)
+        if ((st = dev_alloc_t(m, &m->vec64[k], std::max<int64_t>(n, m->n_nodes))) != FEM3_OK)
+            return fail(st);
+    for (int k = 0; k < 2; k++)
+        if ((st = dev_alloc_t(m, &m->vec32[k], n)) != FEM3_OK) return fail(st);
+    if ((st = check_errors(m)) != FEM3_OK) return fail(st);
+    *out = reinterpret_cast<fem3_mesh>(m);
+    return FEM3_OK;
+}
+
+int fem3_mesh_info(fem3_mesh h, int64_t *n_dof, int64_t *n_gp, int32_t *dof_of_node) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m) return set_error(FEM3_E_ARG, "null mesh");
+    if (n_dof) *n_dof = m->n_dof;
+    if (n_gp) *n_gp = m->n_gp;
+    if (dof_of_node) {
+        FEM3_CUDA(cudaMemcpyAsync(dof_of_node, m->dof, sizeof(int32_t) * m->n_nodes,
+                                  cudaMemcpyDeviceToHost, m->stream));
+        FEM3_CUDA(cudaStreamSynchronize(m->stream));
+    }
+    return FEM3_OK;
+}
+
+int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int precision,
+                  double *A_out, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !alpha || !K) return set_error(FEM3_E_ARG, "null argument");
+    if (precision != FEM3_FP64 && precision != FEM3_TF32X3 && precision != FEM3_FP32)
+        return set_error(FEM3_E_ARG, "unknown precision");
+    for (int a = 0; a < 3; a++) {
+        if (!(alpha[a] > 1.0 && alpha[a] <= 2.0))
+            return set_error(FEM3_E_ARG, "alpha must lie in (1, 2]");
+        if (!(K[a] > 0.0)) return set_error(FEM3_E_ARG, "K must be positive");
+    }
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = m->n_dof;
+    if (precision == FEM3_FP64 && !m->A64) FEM3_TRY(dev_alloc_t(m, &m->A64, n * n));
+    if (precision != FEM3_FP64 && !m->A32) FEM3_TRY(dev_alloc_t(m, &m->A32, n * n));
+    for (int a = 0; a < 3; a++) {
+        m->alpha[a] = alpha[a];
+        m->K[a] = K[a];
+        m->s[a] = 1.0 / (2.0 * cos(M_PI * alpha[a] / 2.0));
+        m->sK[a] = m->s[a] * K[a];
+    }
+    m->precision = precision;
+    m->factored = false;
+    FEM3_TRY(walk_tables(m, alpha));
+    stage_begin(m, 3);
+    FEM3_TRY(contract(m, precision == FEM3_FP64 ? FEM3_FP64 : FEM3_FP32));
+    stage_end(m, 3);
+    if (A_out) {
+        if (precision == FEM3_FP64) {
+            FEM3_CUDA(cudaMemcpyAsync(A_out, m->A64, sizeof(double) * n * n,
+                                      cudaMemcpyDeviceToDevice, m->stream));
+        } else {
+            FEM3_TRY(f32_to_f64(m->A32, A_out, n * n, m->stream));
+        }
+    }
+    return FEM3_OK;
+}
+
+int fem3_load(fem3_mesh h, const double *f, int nrhs, double *b, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !f || !b || nrhs < 1) return set_error(FEM3_E_ARG, "bad argument");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    const void *fd;
+    void *owned;
+    FEM3_TRY(to_device(m, f, sizeof(double) * m->n_nodes * nrhs, &fd, &owned));
+    int st = load_vector(m, (const double *)fd, nrhs, b);
+    if (owned) cudaFreeAsync(owned, m->stream);
+    return st;
+}
+
+int fem3_solve(fem3_mesh h, const double *f, int nrhs, double tol, int max_iter, double *u,
+               int *iters_out, double *resid_out, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !f || !u || nrhs < 1) return set_error(FEM3_E_ARG, "bad argument");
+    if (m->precision < 0) return set_error(FEM3_E_STATE, "solve before assemble");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = m->n_dof;
+    if (n == 0) {
+        if (iters_out) *iters_out = 0;
+        if (resid_out) *resid_out = 0;
+        return check_errors(m);
+    }
+    const void *fd;
+    void *owned;
+    FEM3_TRY(to_device(m, f, sizeof(double) * m->n_nodes * nrhs, &fd, &owned));
+    double *b = nullptr;
+    int st = FEM3_OK;
+    cudaError_t e = cudaMallocAsync((void **)&b, sizeof(double) * std::max<int64_t>(1, n * nrhs), m->stream);
+    if (e != cudaSuccess) st = cuda_error(e, "cudaMallocAsync");
+    stage_begin(m, 4);
+    if (st == FEM3_OK) st = load_vector(m, (const double *)fd, nrhs, b);
+    stage_end(m, 4);
+    if (st == FEM3_OK && !m->factored) {
+        stage_begin(m, 5);
+        st = factor(m);
+        stage_end(m, 5);
+        if (st == FEM3_OK) st = check_errors(m);
+        if (st == FEM3_OK) m->factored = true;
+    }
+    stage_begin(m, 6);
+    if (st == FEM3_OK) {
+        if (m->precision == FEM3_FP64) {
+            st = solve_direct(m, b, nrhs, u);
+            if (st == FEM3_OK && resid_out) {
+                double worst = 0;
+                for (int r = 0; r < nrhs && st == FEM3_OK; r++) {
+                    st = apply_A64(m, u + r * n, m->vec64[0]);
+                    double rel = 0;
+                    if (st == FEM3_OK) st = residual_norm(m, b + r * n, m->vec64[0], &rel);
+                    worst = std::max(worst, rel);
+                }
+                *resid_out = worst;
+            }
+            if (iters_out) *iters_out = 0;
+        } else {
+            st = solve_refined(m, b, nrhs, tol, max_iter > 0 ? max_iter : 50, u, iters_out, resid_out);
+        }
+    }
+    stage_end(m, 6);
+    if (b) cudaFreeAsync(b, m->stream);
+    if (owned) cudaFreeAsync(owned, m->stream);
+    int st2 = check_errors(m);
+    stage_collect(m);
+    return st != FEM3_OK ? st : st2;
+}
+
+int fem3_adjoint(fem3_mesh h, const double *u, const double *u_obs, double tol, int max_iter,
+                 double *dJ_dK, double *dJ_df, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !u || !u_obs || !dJ_dK) return set_error(FEM3_E_ARG, "bad argument");
+    if (m->precision < 0 || !m->factored) return set_error(FEM3_E_STATE, "adjoint before solve");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = m->n_dof;
+    double *res = m->vec64[2], *lam = m->vec64[3];
+    FEM3_TRY(sub_vec(u, u_obs, res, n, m->stream));
+    if (m->precision == FEM3_FP64) {
+        FEM3_TRY(solve_direct(m, res, 1, lam));
+    } else {
+        FEM3_TRY(solve_refined(m, res, 1, tol, max_iter > 0 ? max_iter : 50, lam, nullptr, nullptr));
+    }
+    double forms[3];
+    FEM3_TRY(axis_forms(m, u, lam, forms));
+    for (int a = 0; a < 3; a++) dJ_dK[a] = -forms[a];
+    if (dJ_df) FEM3_TRY(load_vector_T(m, lam, dJ_df));
+    return check_errors(m);
+}
+
+int fem3_paths(fem3_mesh h, int axis, int dir, const int64_t *gps, int64_t n_lines, int cap,
+               int32_t *tet_out, double *r_in_out, double *r_out_out, int32_t *nseg_out,
+               void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !gps || !tet_out || !r_in_out || !r_out_out || !nseg_out || cap < 1 ||
+        axis < 0 || axis > 2 || (dir != 1 && dir != -1) || n_lines < 0)
+        return set_error(FEM3_E_ARG, "bad argument");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (n_lines == 0) return FEM3_OK;
+    return walk_paths(m, axis, dir, gps, n_lines, cap, tet_out, r_in_out, r_out_out, nseg_out);
+}
+
+int fem3_table_rows(fem3_mesh h, int axis, int dir, const int64_t *gps, int64_t n,
+                    double *rows, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !gps || !rows || axis < 0 || axis > 2 || (dir != 1 && dir != -1) || n < 0)
+        return set_error(FEM3_E_ARG, "bad argument");
+    if (m->precision < 0) return set_error(FEM3_E_STATE, "tables before assemble");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    return table_rows(m, axis, dir, gps, n, rows);
+}
+
+int fem3_sync(fem3_mesh h, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m) return set_error(FEM3_E_ARG, "null mesh");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    int st = check_errors(m);
+    stage_collect(m);
+    if (st == FEM3_OK) {
+        unsigned long long segs = 0;
+        FEM3_CUDA(cudaMemcpy(&segs, m->norms + 8, sizeof(segs), cudaMemcpyDeviceToHost));
+        m->segments = (int64_t)segs;
+    }
+    return st;
+}
+
+int fem3_stage_ms(fem3_mesh h, int stage, float *ms) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !ms || stage < 0 || stage > 6) return set_error(FEM3_E_ARG, "bad argument");
+    *ms = m->stage_ms[stage];
+    return FEM3_OK;
+}
+
+int fem3_counters(fem3_mesh h, int64_t *segments, double *contract_flops, int64_t *table_bytes) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m) return set_error(FEM3_E_ARG, "null mesh");
+    if (segments) *segments = m->segments;
+    if (contract_flops) *contract_flops = m->contract_flops;
+    if (table_bytes) {
+        int64_t t = 0;
+        for (int a = 0; a < 3; a++) t += 2 * m->bins[a].tab_elems * (int64_t)sizeof(double);
+        *table_bytes = t;
+    }
+    return FEM3_OK;
+}
+
+}  // extern "C"

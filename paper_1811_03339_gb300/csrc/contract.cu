@@ -1,0 +1,130 @@
+// Contraction A = sum_i s_i K_i (L_i^T W R_i + R_i^T W L_i) on CUDA cores, bin by bin
+// (Section 2.1 element sum, Section 2.3 template: only dofs of a bin's template set can
+// meet the bin's Gauss points, so each bin contributes a dense D_b x D_b block).
+//
+// Work item (bin, t1, t2), t1 <= t2, covers the 64 x 64 output tile of local dofs
+// [64 t1, 64 t1 + 64) x [64 t2, 64 t2 + 64):
+//   out(c1, c2) = sum_r w_r (L[c1][r] R[c2][r] + R[c1][r] L[c2][r])   (symmetric)
+// and adds s K out(c1, c2) to A[dof c1][dof c2] (and to the mirror element when t1 < t2).
+// TA is the arithmetic type (double for the FP64 form, float for the FP32 form).
+#include "fem3_impl.cuh"
+
+namespace fem3 {
+
+namespace {
+
+constexpr int kTile = 64, kKC = 16;
+
+template <class TA>
+__global__ void __launch_bounds__(256) k_contract_simt(
+    const double *__restrict__ tabL, const double *__restrict__ tabR,
+    const int4 *__restrict__ work, const int32_t *__restrict__ gp_off,
+    const int32_t *__restrict__ gp_idx, const int32_t *__restrict__ dof_off,
+    const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
+    const int32_t *__restrict__ tab_ld, const double *__restrict__ gw, double sK, TA *A,
+    int64_t n_dof) {
+    __shared__ TA sLa[kKC][kTile], sRa[kKC][kTile], sLb[kKC][kTile], sRb[kKC][kTile];
+    __shared__ TA sw[kKC];
+    const int4 wk = work[blockIdx.x];
+    const int bin = wk.x, t1 = wk.y, t2 = wk.z;
+    const int D = dof_off[bin + 1] - dof_off[bin];
+    const int G = gp_off[bin + 1] - gp_off[bin];
+    const int ld = tab_ld[bin];
+    const double *L = tabL + tab_off[bin], *R = tabR + tab_off[bin];
+    const int32_t *slots = gp_idx + gp_off[bin];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int a0 = t1 * kTile, b0 = t2 * kTile;
+
+    TA acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = TA(0);
+
+    for (int r0 = 0; r0 < G; r0 += kKC) {
+        if (threadIdx.x < kKC) {
+            int r = r0 + threadIdx.x;
+            sw[threadIdx.x] = r < G ? TA(gw[slots[r]]) : TA(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int e = threadIdx.x + 256 * q;  // 0..1023 over 64 rows x 16 columns
+            int c = e >> 4, k = e & 15, r = r0 + k;
+            bool okr = r < G;
+            int ca = a0 + c, cb = b0 + c;
+            sLa[k][c] = (okr && ca < D) ? TA(L[(int64_t)ca * ld + r]) : TA(0);
+            sRa[k][c] = (okr && ca < D) ? TA(R[(int64_t)ca * ld + r]) : TA(0);
+            sLb[k][c] = (okr && cb < D) ? TA(L[(int64_t)cb * ld + r]) : TA(0);
+            sRb[k][c] = (okr && cb < D) ? TA(R[(int64_t)cb * ld + r]) : TA(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kKC; k++) {
+            TA la[4], ra[4], lb[4], rb[4];
+            TA w = sw[k];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                la[i] = sLa[k][ty * 4 + i];
+                ra[i] = sRa[k][ty * 4 + i];
+                lb[i] = sLb[k][tx * 4 + i] * w;
+                rb[i] = sRb[k][tx * 4 + i] * w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(la[i], rb[j], fma(ra[i], lb[j], acc[i][j]));
+        }
+        __syncthreads();
+    }
+    const int32_t *dofs = dof_idx + dof_off[bin];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int c1 = a0 + ty * 4 + i;
+        if (c1 >= D) continue;
+        int64_t j1 = dofs[c1];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int c2 = b0 + tx * 4 + j;
+            if (c2 >= D) continue;
+            int64_t j2 = dofs[c2];
+            TA v = TA(sK) * acc[i][j];
+            atomicAdd(&A[j1 * n_dof + j2], v);
+            if (t1 != t2) atomicAdd(&A[j2 * n_dof + j1], v);
+        }
+    }
+}
+
+}  // namespace
+
+int contract(Mesh *m, int precision) {
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n_dof;
+    double flops = 0;
+    if (precision == FEM3_FP64) {
+        FEM3_CUDA(cudaMemsetAsync(m->A64, 0, sizeof(double) * n * n, s));
+    } else {
+        FEM3_CUDA(cudaMemsetAsync(m->A32, 0, sizeof(float) * n * n, s));
+    }
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        for (int b = 0; b < B.n_bins; b++) {
+            double D = B.h_dof_off[b + 1] - B.h_dof_off[b];
+            double G = B.h_gp_off[b + 1] - B.h_gp_off[b];
+            flops += 2.0 * D * D * G;
+        }
+        if (!B.n_work) continue;
+        if (precision == FEM3_FP64)
+            k_contract_simt<double><<<B.n_work, 256, 0, s>>>(
+                m->tabL[axis], m->tabR[axis], B.work, B.gp_off, B.gp_idx, B.dof_off, B.dof_idx,
+                B.tab_off, B.tab_ld, m->gw, m->sK[axis], m->A64, n);
+        else
+            k_contract_simt<float><<<B.n_work, 256, 0, s>>>(
+                m->tabL[axis], m->tabR[axis], B.work, B.gp_off, B.gp_idx, B.dof_off, B.dof_idx,
+                B.tab_off, B.tab_ld, m->gw, m->sK[axis], m->A32, n);
+    }
+    m->contract_flops = flops;
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+}  // namespace fem3

@@ -1,0 +1,171 @@
+// Internal declarations shared by the translation units of libfem3 (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fem3.h"
+
+namespace fem3 {
+
+// ---------------------------------------------------------------------------------
+// error reporting (thread-local text, status codes from fem3.h)
+// ---------------------------------------------------------------------------------
+int set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *where);
+
+#define FEM3_CUDA(call)                                                        \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return ::fem3::cuda_error(e_, #call);           \
+    } while (0)
+
+#define FEM3_TRY(call)                                                         \
+    do {                                                                       \
+        int s_ = (call);                                                       \
+        if (s_ != FEM3_OK) return s_;                                          \
+    } while (0)
+
+// Error words written by kernels (device int32 array in the handle).
+enum ErrWord {
+    ERR_WALK = 0,      // number of walks that exceeded the step cap or found no exit
+    ERR_TEMPLATE = 1,  // number of table updates whose dof was not in the bin's template
+    ERR_NOT_SPD = 2,   // 1 + first column with a non-positive pivot (0: none)
+    ERR_MESH = 3,      // number of degenerate tets
+    ERR_FACE = 4,      // non-manifold faces or hash overflow
+    ERR_COUNT = 8
+};
+
+// Walk tolerances (the paper's exact zero tests, made relative).  The CPU oracle uses
+// the same constants; nothing is shared between the two code bases but the numbers.
+constexpr double kEpsLambda = 1e-12;  // zero test of a volume coordinate
+constexpr double kEpsRRel = 1e-12;    // segment-length / tie tolerance, times the mesh span
+constexpr double kEpsDRel = 1e-12;    // |gradient| below this fraction of the largest: parallel
+
+constexpr int kMaxBinItems = 4096;    // max dofs or Gauss points in one transverse bin
+
+// Transverse bins of one axis: the plane of the two other coordinates is cut into an
+// nb0 x nb1 grid; a Gauss point belongs to the bin of its transverse position, a dof
+// to every bin its element patch's transverse bounding box meets (template set).
+struct AxisBins {
+    int c0 = 0, c1 = 0;          // transverse coordinates (c0 < c1)
+    int nb0 = 0, nb1 = 0, n_bins = 0;
+    double org0 = 0, org1 = 0, width = 0;
+    int32_t *gp_off = nullptr;   // [n_bins+1]   bin -> slots
+    int32_t *gp_idx = nullptr;   // [n_gp]       slot -> Gauss point (sorted along the axis)
+    int32_t *slot_bin = nullptr; // [n_gp]       slot -> bin
+    int32_t *slot_of_gp = nullptr; // [n_gp]     Gauss point -> slot
+    int32_t *dof_off = nullptr;  // [n_bins+1]
+    int32_t *dof_idx = nullptr;  // [n_tmpl]     sorted dof ids per bin
+    int64_t *tab_off = nullptr;  // [n_bins]     element offset of the bin's table block
+    int32_t *tab_ld = nullptr;   // [n_bins]     leading dimension (padded Gauss-point count)
+    int64_t n_tmpl = 0, tab_elems = 0;
+    int max_dof = 0, max_gp = 0;
+    int4 *work = nullptr;        // contraction work items (bin, t1, t2, 0)
+    int n_work = 0;
+    std::vector<int32_t> h_gp_off, h_dof_off;
+    std::vector<int64_t> h_tab_off;
+    std::vector<int32_t> h_tab_ld;
+};
+
+struct Mesh {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n_nodes = 0, n_tets = 0, n_gp = 0, n_dof = 0;
+    double span = 0, h_est = 0, bin_scale = 1.0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int max_steps = 0;
+    bool profile = false;
+
+    // geometry (device)
+    double *verts = nullptr;   // [n_nodes][3]
+    int32_t *tets = nullptr;   // [n_tets][4]
+    double *M = nullptr;       // [n_tets][16] rows (c_k, dlam_k/dx, dlam_k/dy, dlam_k/dz)
+    double *inv = nullptr;     // [n_tets][3][4] 1/dlam_k/dx_axis, 0 if parallel
+    double *vol = nullptr;     // [n_tets]
+    int32_t *nbr = nullptr;    // [n_tets][4]
+    int32_t *dof = nullptr;    // [n_nodes]
+    int32_t *dof_node = nullptr;  // [n_dof]
+    int32_t *vt_off = nullptr;    // [n_nodes+1]
+    int32_t *vt_tet = nullptr;    // [4 n_tets]
+    double *gp = nullptr;      // [n_gp][3]
+    double *gw = nullptr;      // [n_gp]
+    double *node_box = nullptr;   // [n_nodes][6] patch bounding box (lo xyz, hi xyz)
+    int32_t *err = nullptr;    // [ERR_COUNT]
+
+    AxisBins bins[3];
+    double *tabL[3] = {nullptr, nullptr, nullptr};
+    double *tabR[3] = {nullptr, nullptr, nullptr};
+
+    // assembled operator
+    int precision = -1;        // of the last assemble, -1: none
+    double alpha[3] = {0, 0, 0}, K[3] = {0, 0, 0};
+    double s[3] = {0, 0, 0};   // Riesz constants s_i = 1/(2 cos(pi alpha_i/2))
+    double sK[3] = {0, 0, 0};  // s_i K_i
+    double *A64 = nullptr;     // [n_dof][n_dof]
+    float *A32 = nullptr;      // [n_dof][n_dof]
+    bool factored = false;
+
+    // workspaces
+    double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    float *vec32[2] = {nullptr, nullptr};
+    double *norms = nullptr;   // device scratch for reductions
+    double *h_norms = nullptr; // pinned host mirror
+
+    // counters
+    int64_t segments = 0;
+    double contract_flops = 0;
+
+    // profiling
+    cudaEvent_t ev[16];
+    bool ev_made = false;
+    float stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+    std::vector<void *> allocs;
+};
+
+// device memory owned by a mesh (stream-ordered pool allocations)
+int dev_alloc(Mesh *m, void **p, size_t bytes);
+template <class T>
+int dev_alloc_t(Mesh *m, T **p, size_t n) {
+    return dev_alloc(m, reinterpret_cast<void **>(p), n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+}
+void dev_free_all(Mesh *m);
+
+// true if p is device or managed memory
+bool is_device_ptr(const void *p);
+
+// profiling helpers
+void stage_begin(Mesh *m, int stage);
+void stage_end(Mesh *m, int stage);
+void stage_collect(Mesh *m);
+
+// exclusive scan of int32 counts into offsets [n+1]; returns total via device offsets[n]
+int scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, Mesh *m);
+
+// translation-unit entry points
+int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d);
+int bins_build(Mesh *m);
+int walk_tables(Mesh *m, const double alpha[3]);
+int walk_paths(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, int cap,
+               int32_t *tet_out, double *r0, double *r1, int32_t *nseg);
+int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double *rows);
+int contract(Mesh *m, int precision);
+int load_vector(Mesh *m, const double *f_d, int nrhs, double *b_d);
+int load_vector_T(Mesh *m, const double *lam_d, double *out_d);
+int factor(Mesh *m);
+int solve_direct(Mesh *m, const double *b_d, int nrhs, double *u_d);
+int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter, double *u_d,
+                  int *iters, double *resid);
+int apply_A64(Mesh *m, const double *u_d, double *Au_d);
+int axis_forms(Mesh *m, const double *u_d, const double *lam_d, double out[3]);
+int read_errors(Mesh *m, int32_t *h_err);
+int f32_to_f64(const float *a, double *b, int64_t n, cudaStream_t s);
+int sub_vec(const double *a, const double *b, double *c, int64_t n, cudaStream_t s);
+// rel = ||b - Au|| / ||b|| (synchronises)
+int residual_norm(Mesh *m, const double *b, const double *Au, double *rel);
+
+}  // namespace fem3

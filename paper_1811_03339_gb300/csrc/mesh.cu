@@ -1,0 +1,646 @@
+// Mesh records on the device (Section 2.2 volume coordinates and adjacency, Section 2.1
+// Gauss rule, Section 2.3 template sets per transverse bin).
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "fem3_impl.cuh"
+
+namespace fem3 {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+inline unsigned grid_for(int64_t n, int threads = kThreads) {
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)(g > 0 ? g : 1);   // kernels check their bounds; never a 0-size grid
+}
+
+// order-preserving map of a double to an unsigned 64-bit integer (for atomic min/max)
+__device__ __forceinline__ unsigned long long ord_of(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double double_of_ord(unsigned long long o) {
+    unsigned long long b = (o & 0x8000000000000000ull) ? (o & 0x7fffffffffffffffull) : ~o;
+    return __longlong_as_double((long long)b);
+}
+
+// ---------------------------------------------------------------------------------
+// per tet: barycentric map, gradient reciprocals, volume, Gauss points, bounding box
+// ---------------------------------------------------------------------------------
+__global__ void k_tet_geom(const double *__restrict__ verts, const int32_t *__restrict__ tets,
+                           int64_t n_tets, int64_t n_nodes, double qa, double qb,
+                           double *__restrict__ M, double *__restrict__ inv,
+                           double *__restrict__ vol, double *__restrict__ gp,
+                           double *__restrict__ gw, unsigned long long *__restrict__ node_box,
+                           int32_t *__restrict__ err) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_tets) return;
+    double v[4][3];
+    for (int k = 0; k < 4; k++) {
+        int32_t id = tets[4 * t + k];
+        if (id < 0 || id >= n_nodes) {
+            atomicAdd(&err[ERR_MESH], 1);
+            return;
+        }
+        for (int d = 0; d < 3; d++) v[k][d] = verts[3 * id + d];
+    }
+    // edge vectors e_c = v_{c+1} - v_0 and det (no contraction: same rounding as a plain
+    // evaluation of the triple product, so the weights match any IEEE evaluation)
+    double e[3][3];
+    for (int c = 0; c < 3; c++)
+        for (int d = 0; d < 3; d++) e[c][d] = __dsub_rn(v[c + 1][d], v[0][d]);
+    double m0 = __dsub_rn(__dmul_rn(e[1][1], e[2][2]), __dmul_rn(e[1][2], e[2][1]));
+    double m1 = __dsub_rn(__dmul_rn(e[1][0], e[2][2]), __dmul_rn(e[1][2], e[2][0]));
+    double m2 = __dsub_rn(__dmul_rn(e[1][0], e[2][1]), __dmul_rn(e[1][1], e[2][0]));
+    double det = __dadd_rn(__dsub_rn(__dmul_rn(e[0][0], m0), __dmul_rn(e[0][1], m1)),
+                           __dmul_rn(e[0][2], m2));
+    double emax = 0;
+    for (int c = 0; c < 3; c++)
+        for (int d = 0; d < 3; d++) emax = fmax(emax, fabs(e[c][d]));
+    if (!(fabs(det) > 1e-14 * emax * emax * emax)) {
+        atomicAdd(&err[ERR_MESH], 1);
+        return;
+    }
+    double V = __ddiv_rn(fabs(det), 6.0);
+    vol[t] = V;
+    // gradients of lambda_1..3 are the rows of J^{-1}, J = [e_0 e_1 e_2] (columns):
+    // grad lambda_1 = (e_1 x e_2)/det, grad lambda_2 = (e_2 x e_0)/det,
+    // grad lambda_3 = (e_0 x e_1)/det
+    double g[4][3];
+    const int pa[3] = {1, 2, 0}, pb[3] = {2, 0, 1};
+    double rdet = 1.0 / det;
+    for (int r = 0; r < 3; r++) {
+        const double *a = e[pa[r]], *b = e[pb[r]];
+        g[r + 1][0] = (a[1] * b[2] - a[2] * b[1]) * rdet;
+        g[r + 1][1] = (a[2] * b[0] - a[0] * b[2]) * rdet;
+        g[r + 1][2] = (a[0] * b[1] - a[1] * b[0]) * rdet;
+    }
+    for (int d = 0; d < 3; d++) g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
+    double c[4];
+    c[1] = -(g[1][0] * v[0][0] + g[1][1] * v[0][1] + g[1][2] * v[0][2]);
+    c[2] = -(g[2][0] * v[0][0] + g[2][1] * v[0][1] + g[2][2] * v[0][2]);
+    c[3] = -(g[3][0] * v[0][0] + g[3][1] * v[0][1] + g[3][2] * v[0][2]);
+    c[0] = 1.0 - (c[1] + c[2] + c[3]);
+    double *Mt = M + 16 * t;
+    for (int k = 0; k < 4; k++) {
+        Mt[4 * k + 0] = c[k];
+        Mt[4 * k + 1] = g[k][0];
+        Mt[4 * k + 2] = g[k][1];
+        Mt[4 * k + 3] = g[k][2];
+    }
+    for (int a = 0; a < 3; a++) {
+        double ds = 0;
+        for (int k = 0; k < 4; k++) ds = fmax(ds, fabs(g[k][a]));
+        for (int k = 0; k < 4; k++)
+            inv[12 * t + 4 * a + k] = fabs(g[k][a]) > kEpsDRel * ds ? 1.0 / g[k][a] : 0.0;
+    }
+    // Gauss points: point q has barycentric qa at vertex q, qb elsewhere; summed in
+    // vertex order without contraction (bit-identical to a plain IEEE evaluation)
+    for (int q = 0; q < 4; q++) {
+        for (int d = 0; d < 3; d++) {
+            double x = 0.0;
+            for (int k = 0; k < 4; k++) x = __dadd_rn(x, __dmul_rn(k == q ? qa : qb, v[k][d]));
+            gp[3 * (4 * t + q) + d] = x;
+        }
+        gw[4 * t + q] = __ddiv_rn(V, 4.0);
+    }
+    // element-patch bounding boxes of the four vertices
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; d++) {
+        lo[d] = fmin(fmin(v[0][d], v[1][d]), fmin(v[2][d], v[3][d]));
+        hi[d] = fmax(fmax(v[0][d], v[1][d]), fmax(v[2][d], v[3][d]));
+    }
+    for (int k = 0; k < 4; k++) {
+        int32_t id = tets[4 * t + k];
+        for (int d = 0; d < 3; d++) {
+            atomicMin(&node_box[6 * (int64_t)id + d], ord_of(lo[d]));
+            atomicMax(&node_box[6 * (int64_t)id + 3 + d], ord_of(hi[d]));
+        }
+    }
+}
+
+// bounding box of the vertices (ordered-integer atomics) and total volume
+__global__ void k_extent(const double *__restrict__ verts, int64_t n_nodes,
+                         const double *__restrict__ vol, int64_t n_tets,
+                         unsigned long long *ext, double *vsum) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n_nodes)
+        for (int d = 0; d < 3; d++) {
+            atomicMin(&ext[d], ord_of(verts[3 * i + d]));
+            atomicMax(&ext[3 + d], ord_of(verts[3 * i + d]));
+        }
+    if (i < n_tets) atomicAdd(vsum, vol[i]);
+}
+
+__global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+__global__ void k_box_init(unsigned long long *box, int64_t n_nodes) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 6 * n_nodes) return;
+    box[i] = (i % 6) < 3 ? ~0ull : 0ull;
+}
+
+__global__ void k_box_decode(unsigned long long *box, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = double_of_ord(box[i]);
+    reinterpret_cast<double *>(box)[i] = v;
+}
+
+// ---------------------------------------------------------------------------------
+// face neighbours by hashing sorted vertex triples
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long face_key(const int32_t *tv, int k) {
+    int32_t f[3];
+    int n = 0;
+    for (int q = 0; q < 4; q++)
+        if (q != k) f[n++] = tv[q];
+    if (f[1] < f[0]) { int32_t s = f[0]; f[0] = f[1]; f[1] = s; }
+    if (f[2] < f[1]) { int32_t s = f[1]; f[1] = f[2]; f[2] = s; }
+    if (f[1] < f[0]) { int32_t s = f[0]; f[0] = f[1]; f[1] = s; }
+    return ((unsigned long long)f[0] << 42) | ((unsigned long long)f[1] << 21) |
+           (unsigned long long)f[2];
+}
+
+__device__ __forceinline__ unsigned long long hash_slot(unsigned long long key, int bits) {
+    return (key * 0x9E3779B97F4A7C15ull) >> (64 - bits);
+}
+
+__global__ void k_face_insert(const int32_t *__restrict__ tets, int64_t n_tets,
+                              unsigned long long *keys, int32_t *vals, int bits,
+                              int32_t *err) {
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= 4 * n_tets) return;
+    int64_t t = f >> 2;
+    int k = (int)(f & 3);
+    unsigned long long key = face_key(tets + 4 * t, k);
+    unsigned long long mask = (1ull << bits) - 1;
+    unsigned long long h = hash_slot(key, bits);
+    for (int probe = 0; probe < 4096; probe++) {
+        unsigned long long prev = atomicCAS(&keys[h], kEmptyKey, key);
+        if (prev == kEmptyKey || prev == key) {
+            if (atomicCAS(&vals[2 * h], -1, (int32_t)f) != -1 &&
+                atomicCAS(&vals[2 * h + 1], -1, (int32_t)f) != -1)
+                atomicAdd(&err[ERR_FACE], 1);  // face shared by more than two tets
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    atomicAdd(&err[ERR_FACE], 1);
+}
+
+__global__ void k_face_match(const int32_t *__restrict__ tets, int64_t n_tets,
+                             const unsigned long long *__restrict__ keys,
+                             const int32_t *__restrict__ vals, int bits,
+                             int32_t *__restrict__ nbr, int32_t *err) {
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= 4 * n_tets) return;
+    int64_t t = f >> 2;
+    int k = (int)(f & 3);
+    unsigned long long key = face_key(tets + 4 * t, k);
+    unsigned long long mask = (1ull << bits) - 1;
+    unsigned long long h = hash_slot(key, bits);
+    for (int probe = 0; probe < 4096; probe++) {
+        if (keys[h] == key) {
+            int32_t a = vals[2 * h], b = vals[2 * h + 1];
+            int32_t other = (a == (int32_t)f) ? b : a;
+            nbr[f] = other >= 0 ? (other >> 2) : -1;
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    nbr[f] = -1;
+    atomicAdd(&err[ERR_FACE], 1);
+}
+
+__global__ void k_mark_nodes(const int32_t *__restrict__ tets, const int32_t *__restrict__ nbr,
+                             int64_t n_tets, int64_t n_nodes, int32_t *used, int32_t *bnd,
+                             int32_t *vt_count) {
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= 4 * n_tets) return;
+    int64_t t = f >> 2;
+    int k = (int)(f & 3);
+    for (int q = 0; q < 4; q++) {
+        int32_t id = tets[4 * t + q];
+        if (id < 0 || id >= n_nodes) return;   // reported by k_tet_geom
+    }
+    int32_t node = tets[f];
+    used[node] = 1;
+    atomicAdd(&vt_count[node], 1);
+    if (nbr[f] < 0)
+        for (int q = 0; q < 4; q++)
+            if (q != k) bnd[tets[4 * t + q]] = 1;
+}
+
+__global__ void k_interior_flag(const int32_t *used, const int32_t *bnd, int64_t n,
+                                int32_t *flag) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = (used[i] && !bnd[i]) ? 1 : 0;
+}
+
+__global__ void k_dof_number(const int32_t *flag, const int32_t *off, int64_t n,
+                             int32_t *dof, int32_t *dof_node) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flag[i]) {
+        dof[i] = off[i];
+        dof_node[off[i]] = (int32_t)i;
+    } else {
+        dof[i] = -1;
+    }
+}
+
+__global__ void k_vt_fill(const int32_t *__restrict__ tets, int64_t n_tets, int64_t n_nodes,
+                          const int32_t *__restrict__ off, int32_t *cursor, int32_t *vt_tet) {
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= 4 * n_tets) return;
+    int32_t node = tets[f];
+    if (node < 0 || node >= n_nodes) return;
+    int32_t pos = atomicAdd(&cursor[node], 1);
+    vt_tet[off[node] + pos] = (int32_t)(f >> 2);
+}
+
+// ---------------------------------------------------------------------------------
+// scan (three-phase: per-block sums, scan of block sums, add back)
+// ---------------------------------------------------------------------------------
+constexpr int kScanBlock = 1024;
+
+__device__ int32_t block_excl_scan(int32_t v, int32_t *sh, int32_t *total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int32_t s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    int32_t base = w > 0 ? sh[w - 1] : 0;
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__global__ void k_scan_blocks(const int32_t *in, int32_t *out, int64_t n, int32_t *bsum) {
+    __shared__ int32_t sh[32];
+    int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    int32_t v = i < n ? in[i] : 0, tot;
+    int32_t e = block_excl_scan(v, sh, &tot);
+    if (i < n) out[i] = e;
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int32_t *bsum, int64_t nb, int32_t *total_out) {
+    __shared__ int32_t sh[32];
+    int32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += kScanBlock) {
+        int64_t i = base + threadIdx.x;
+        int32_t v = i < nb ? bsum[i] : 0, tot;
+        int32_t e = block_excl_scan(v, sh, &tot);
+        if (i < nb) bsum[i] = e + carry;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *bsum) {
+    int64_t i = blockIdx.x * (int64_t)kScanBlock + threadIdx.x;
+    if (i < n) out[i] += bsum[blockIdx.x];
+}
+
+// ---------------------------------------------------------------------------------
+// transverse bins of one axis
+// ---------------------------------------------------------------------------------
+struct BinGeom {
+    int c0, c1, nb0, nb1;
+    double org0, org1, width;
+};
+
+__device__ __forceinline__ int bin_coord(double p, double org, double w, int nb) {
+    double q = floor((p - org) / w);
+    int i = q < 0 ? 0 : (q > nb - 1 ? nb - 1 : (int)q);
+    return i;
+}
+
+__global__ void k_gp_bin_count(const double *__restrict__ gp, int64_t n_gp, BinGeom G,
+                               int32_t *count, int32_t *gbin) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n_gp) return;
+    int i0 = bin_coord(gp[3 * g + G.c0], G.org0, G.width, G.nb0);
+    int i1 = bin_coord(gp[3 * g + G.c1], G.org1, G.width, G.nb1);
+    int b = i0 + G.nb0 * i1;
+    gbin[g] = b;
+    atomicAdd(&count[b], 1);
+}
+
+__global__ void k_dof_bin_count(const double *__restrict__ box, const int32_t *__restrict__ dof_node,
+                                int64_t n_dof, BinGeom G, int32_t *count) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n_dof) return;
+    const double *bx = box + 6 * (int64_t)dof_node[j];
+    int a0 = bin_coord(bx[G.c0], G.org0, G.width, G.nb0);
+    int a1 = bin_coord(bx[3 + G.c0], G.org0, G.width, G.nb0);
+    int b0 = bin_coord(bx[G.c1], G.org1, G.width, G.nb1);
+    int b1 = bin_coord(bx[3 + G.c1], G.org1, G.width, G.nb1);
+    for (int i1 = b0; i1 <= b1; i1++)
+        for (int i0 = a0; i0 <= a1; i0++) atomicAdd(&count[i0 + G.nb0 * i1], 1);
+}
+
+__global__ void k_gp_bin_fill(const double *__restrict__ gp, int64_t n_gp, int axis, double lo,
+                              double span, const int32_t *__restrict__ gbin,
+                              const int32_t *__restrict__ off, int32_t *cursor,
+                              unsigned long long *keys) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n_gp) return;
+    int b = gbin[g];
+    int32_t pos = atomicAdd(&cursor[b], 1);
+    // sort key: position along the axis (30-bit quantised), then the Gauss point id
+    double u = (gp[3 * g + axis] - lo) / span;
+    u = u < 0 ? 0 : (u > 1 ? 1 : u);
+    unsigned long long q = (unsigned long long)(u * 1073741823.0);
+    keys[off[b] + pos] = (q << 32) | (unsigned long long)g;
+}
+
+__global__ void k_dof_bin_fill(const double *__restrict__ box, const int32_t *__restrict__ dof_node,
+                               int64_t n_dof, BinGeom G, const int32_t *__restrict__ off,
+                               int32_t *cursor, unsigned long long *keys) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n_dof) return;
+    const double *bx = box + 6 * (int64_t)dof_node[j];
+    int a0 = bin_coord(bx[G.c0], G.org0, G.width, G.nb0);
+    int a1 = bin_coord(bx[3 + G.c0], G.org0, G.width, G.nb0);
+    int b0 = bin_coord(bx[G.c1], G.org1, G.width, G.nb1);
+    int b1 = bin_coord(bx[3 + G.c1], G.org1, G.width, G.nb1);
+    for (int i1 = b0; i1 <= b1; i1++)
+        for (int i0 = a0; i0 <= a1; i0++) {
+            int b = i0 + G.nb0 * i1;
+            int32_t pos = atomicAdd(&cursor[b], 1);
+            keys[off[b] + pos] = (unsigned long long)j;
+        }
+}
+
+// One CTA per bin: bitonic sort of the bin's keys in shared memory, then write the
+// low 32 bits as the sorted ids (and the slot -> bin map for Gauss points).
+__global__ void k_bin_sort(const int32_t *__restrict__ off, unsigned long long *keys,
+                           int32_t *ids, int32_t *slot_bin) {
+    __shared__ unsigned long long sh[kMaxBinItems];
+    int b = blockIdx.x;
+    int lo = off[b], n = off[b + 1] - lo;
+    int p2 = 1;
+    while (p2 < n) p2 <<= 1;
+    for (int i = threadIdx.x; i < p2; i += blockDim.x) sh[i] = i < n ? keys[lo + i] : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+                int l = i ^ j;
+                if (l > i) {
+                    bool up = (i & k) == 0;
+                    unsigned long long a = sh[i], c = sh[l];
+                    if ((a > c) == up) { sh[i] = c; sh[l] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        ids[lo + i] = (int32_t)(sh[i] & 0xffffffffull);
+        if (slot_bin) slot_bin[lo + i] = b;
+    }
+}
+
+__global__ void k_invert_slots(const int32_t *__restrict__ gp_idx, int64_t n_gp,
+                               int32_t *slot_of_gp) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s < n_gp) slot_of_gp[gp_idx[s]] = (int32_t)s;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+int scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, Mesh *m) {
+    int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    if (nb < 1) nb = 1;
+    int32_t *bsum = nullptr;
+    FEM3_TRY(dev_alloc_t(m, &bsum, nb));
+    k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(in, out, n, bsum);
+    k_scan_sums<<<1, kScanBlock, 0, s>>>(bsum, nb, out + n);
+    k_scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(out, n, bsum);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
+    cudaStream_t s = m->stream;
+    const int64_t T = m->n_tets, N = m->n_nodes;
+    FEM3_TRY(dev_alloc_t(m, &m->M, 16 * T));
+    FEM3_TRY(dev_alloc_t(m, &m->inv, 12 * T));
+    FEM3_TRY(dev_alloc_t(m, &m->vol, T));
+    FEM3_TRY(dev_alloc_t(m, &m->nbr, 4 * T));
+    FEM3_TRY(dev_alloc_t(m, &m->dof, N));
+    FEM3_TRY(dev_alloc_t(m, &m->vt_off, N + 1));
+    FEM3_TRY(dev_alloc_t(m, &m->vt_tet, 4 * T));
+    FEM3_TRY(dev_alloc_t(m, &m->gp, 3 * m->n_gp));
+    FEM3_TRY(dev_alloc_t(m, &m->gw, m->n_gp));
+    FEM3_TRY(dev_alloc_t(m, &m->node_box, 6 * N));
+
+    // Gauss rule constants, evaluated like any IEEE host evaluation of the same formula
+    const double qa = (5.0 + 3.0 * sqrt(5.0)) / 20.0;
+    const double qb = (5.0 - sqrt(5.0)) / 20.0;
+
+    unsigned long long *box = reinterpret_cast<unsigned long long *>(m->node_box);
+    k_box_init<<<grid_for(6 * N), kThreads, 0, s>>>(box, N);
+    k_tet_geom<<<grid_for(T), kThreads, 0, s>>>(verts_d, tets_d, T, N, qa, qb, m->M, m->inv,
+                                                 m->vol, m->gp, m->gw, box, m->err);
+    k_box_decode<<<grid_for(6 * N), kThreads, 0, s>>>(box, 6 * N);
+
+    // face hash: load factor <= 1/4 of 4T face slots
+    int bits = 4;
+    while ((1ll << bits) < 16 * T) bits++;
+    int64_t H = 1ll << bits;
+    unsigned long long *keys = nullptr;
+    int32_t *vals = nullptr;
+    FEM3_TRY(dev_alloc_t(m, &keys, H));
+    FEM3_TRY(dev_alloc_t(m, &vals, 2 * H));
+    k_fill_u64<<<grid_for(H), kThreads, 0, s>>>(keys, H, kEmptyKey);
+    FEM3_CUDA(cudaMemsetAsync(vals, 0xff, sizeof(int32_t) * 2 * H, s));
+    k_face_insert<<<grid_for(4 * T), kThreads, 0, s>>>(tets_d, T, keys, vals, bits, m->err);
+    k_face_match<<<grid_for(4 * T), kThreads, 0, s>>>(tets_d, T, keys, vals, bits, m->nbr,
+                                                       m->err);
+
+    // boundary vertices, dof numbering, vertex -> tets
+    int32_t *used, *bnd, *flag, *off, *vcount, *cursor;
+    FEM3_TRY(dev_alloc_t(m, &used, N));
+    FEM3_TRY(dev_alloc_t(m, &bnd, N));
+    FEM3_TRY(dev_alloc_t(m, &flag, N));
+    FEM3_TRY(dev_alloc_t(m, &off, N + 1));
+    FEM3_TRY(dev_alloc_t(m, &vcount, N));
+    FEM3_TRY(dev_alloc_t(m, &cursor, N));
+    FEM3_CUDA(cudaMemsetAsync(used, 0, sizeof(int32_t) * N, s));
+    FEM3_CUDA(cudaMemsetAsync(bnd, 0, sizeof(int32_t) * N, s));
+    FEM3_CUDA(cudaMemsetAsync(vcount, 0, sizeof(int32_t) * N, s));
+    FEM3_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * N, s));
+    k_mark_nodes<<<grid_for(4 * T), kThreads, 0, s>>>(tets_d, m->nbr, T, N, used, bnd, vcount);
+    k_interior_flag<<<grid_for(N), kThreads, 0, s>>>(used, bnd, N, flag);
+    FEM3_TRY(scan_i32(flag, off, N, s, m));
+    FEM3_TRY(scan_i32(vcount, m->vt_off, N, s, m));
+    k_vt_fill<<<grid_for(4 * T), kThreads, 0, s>>>(tets_d, T, N, m->vt_off, cursor, m->vt_tet);
+
+    unsigned long long *ext = nullptr;
+    double *vsum = nullptr;
+    FEM3_TRY(dev_alloc_t(m, &ext, 6));
+    FEM3_TRY(dev_alloc_t(m, &vsum, 1));
+    k_box_init<<<1, 32, 0, s>>>(ext, 1);
+    FEM3_CUDA(cudaMemsetAsync(vsum, 0, sizeof(double), s));
+    k_extent<<<grid_for(std::max(N, T)), kThreads, 0, s>>>(verts_d, N, m->vol, T, ext, vsum);
+
+    int32_t n_dof = 0;
+    unsigned long long h_ext[6];
+    double h_vsum = 0;
+    FEM3_CUDA(cudaMemcpyAsync(&n_dof, off + N, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FEM3_CUDA(cudaMemcpyAsync(h_ext, ext, sizeof(h_ext), cudaMemcpyDeviceToHost, s));
+    FEM3_CUDA(cudaMemcpyAsync(&h_vsum, vsum, sizeof(double), cudaMemcpyDeviceToHost, s));
+    int32_t h_err[ERR_COUNT];
+    FEM3_CUDA(cudaMemcpyAsync(h_err, m->err, sizeof(h_err), cudaMemcpyDeviceToHost, s));
+    FEM3_CUDA(cudaStreamSynchronize(s));
+    if (h_err[ERR_MESH]) return set_error(FEM3_E_MESH, "degenerate tetrahedron or node id out of range");
+    if (h_err[ERR_FACE]) return set_error(FEM3_E_MESH, "a face is shared by more than two tetrahedra");
+    for (int d = 0; d < 6; d++) {
+        unsigned long long o = h_ext[d];
+        unsigned long long b = (o & 0x8000000000000000ull) ? (o & 0x7fffffffffffffffull) : ~o;
+        double v;
+        std::memcpy(&v, &b, sizeof(v));
+        (d < 3 ? m->lo[d] : m->hi[d - 3]) = v;
+    }
+    m->span = 0;
+    for (int d = 0; d < 3; d++) m->span = std::max(m->span, m->hi[d] - m->lo[d]);
+    m->h_est = cbrt(6.0 * h_vsum / (double)T);
+    m->n_dof = n_dof;
+    FEM3_TRY(dev_alloc_t(m, &m->dof_node, n_dof > 0 ? n_dof : 1));
+    k_dof_number<<<grid_for(N), kThreads, 0, s>>>(flag, off, N, m->dof, m->dof_node);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int bins_build(Mesh *m) {
+    cudaStream_t s = m->stream;
+    const int64_t n_gp = m->n_gp, n_dof = m->n_dof;
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        B.c0 = axis == 0 ? 1 : 0;
+        B.c1 = axis == 2 ? 1 : 2;
+        B.width = m->bin_scale * m->h_est;
+        B.org0 = m->lo[B.c0];
+        B.org1 = m->lo[B.c1];
+        B.nb0 = std::max(1, (int)ceil((m->hi[B.c0] - m->lo[B.c0]) / B.width));
+        B.nb1 = std::max(1, (int)ceil((m->hi[B.c1] - m->lo[B.c1]) / B.width));
+        B.n_bins = B.nb0 * B.nb1;
+        BinGeom G{B.c0, B.c1, B.nb0, B.nb1, B.org0, B.org1, B.width};
+        const int nb = B.n_bins;
+
+        int32_t *gcount, *dcount, *gcur, *dcur, *gbin;
+        FEM3_TRY(dev_alloc_t(m, &gcount, nb));
+        FEM3_TRY(dev_alloc_t(m, &dcount, nb));
+        FEM3_TRY(dev_alloc_t(m, &gcur, nb));
+        FEM3_TRY(dev_alloc_t(m, &dcur, nb));
+        FEM3_TRY(dev_alloc_t(m, &gbin, n_gp));
+        FEM3_TRY(dev_alloc_t(m, &B.gp_off, nb + 1));
+        FEM3_TRY(dev_alloc_t(m, &B.dof_off, nb + 1));
+        FEM3_CUDA(cudaMemsetAsync(gcount, 0, sizeof(int32_t) * nb, s));
+        FEM3_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int32_t) * nb, s));
+        FEM3_CUDA(cudaMemsetAsync(gcur, 0, sizeof(int32_t) * nb, s));
+        FEM3_CUDA(cudaMemsetAsync(dcur, 0, sizeof(int32_t) * nb, s));
+        k_gp_bin_count<<<grid_for(n_gp), kThreads, 0, s>>>(m->gp, n_gp, G, gcount, gbin);
+        k_dof_bin_count<<<grid_for(n_dof), kThreads, 0, s>>>(m->node_box, m->dof_node, n_dof, G,
+                                                             dcount);
+        FEM3_TRY(scan_i32(gcount, B.gp_off, nb, s, m));
+        FEM3_TRY(scan_i32(dcount, B.dof_off, nb, s, m));
+        B.h_gp_off.resize(nb + 1);
+        B.h_dof_off.resize(nb + 1);
+        FEM3_CUDA(cudaMemcpyAsync(B.h_gp_off.data(), B.gp_off, sizeof(int32_t) * (nb + 1),
+                                  cudaMemcpyDeviceToHost, s));
+        FEM3_CUDA(cudaMemcpyAsync(B.h_dof_off.data(), B.dof_off, sizeof(int32_t) * (nb + 1),
+                                  cudaMemcpyDeviceToHost, s));
+        FEM3_CUDA(cudaStreamSynchronize(s));
+        B.n_tmpl = B.h_dof_off[nb];
+        B.max_dof = 0;
+        B.max_gp = 0;
+        for (int b = 0; b < nb; b++) {
+            B.max_dof = std::max(B.max_dof, B.h_dof_off[b + 1] - B.h_dof_off[b]);
+            B.max_gp = std::max(B.max_gp, B.h_gp_off[b + 1] - B.h_gp_off[b]);
+        }
+        if (B.max_dof > kMaxBinItems || B.max_gp > kMaxBinItems)
+            return set_error(FEM3_E_ARG, "a transverse bin holds more than 4096 dofs or Gauss "
+                                         "points; lower fem3_options.bin_scale");
+
+        unsigned long long *gkeys, *dkeys;
+        FEM3_TRY(dev_alloc_t(m, &gkeys, n_gp));
+        FEM3_TRY(dev_alloc_t(m, &dkeys, B.n_tmpl));
+        FEM3_TRY(dev_alloc_t(m, &B.gp_idx, n_gp));
+        FEM3_TRY(dev_alloc_t(m, &B.slot_bin, n_gp));
+        FEM3_TRY(dev_alloc_t(m, &B.dof_idx, B.n_tmpl));
+        double lo = m->lo[axis], span = std::max(m->hi[axis] - m->lo[axis], 1e-300);
+        k_gp_bin_fill<<<grid_for(n_gp), kThreads, 0, s>>>(m->gp, n_gp, axis, lo, span, gbin,
+                                                          B.gp_off, gcur, gkeys);
+        k_dof_bin_fill<<<grid_for(n_dof), kThreads, 0, s>>>(m->node_box, m->dof_node, n_dof, G,
+                                                            B.dof_off, dcur, dkeys);
+        k_bin_sort<<<nb, 1024, 0, s>>>(B.gp_off, gkeys, B.gp_idx, B.slot_bin);
+        k_bin_sort<<<nb, 1024, 0, s>>>(B.dof_off, dkeys, B.dof_idx, nullptr);
+        FEM3_TRY(dev_alloc_t(m, &B.slot_of_gp, n_gp));
+        k_invert_slots<<<grid_for(n_gp), kThreads, 0, s>>>(B.gp_idx, n_gp, B.slot_of_gp);
+
+        // table layout: block of bin b is [D_b][ld_b], ld_b = Gauss points rounded up to 8
+        B.h_tab_off.resize(nb);
+        B.h_tab_ld.resize(nb);
+        int64_t acc = 0;
+        std::vector<int4> work;
+        for (int b = 0; b < nb; b++) {
+            int D = B.h_dof_off[b + 1] - B.h_dof_off[b];
+            int Gc = B.h_gp_off[b + 1] - B.h_gp_off[b];
+            int ld = (Gc + 7) & ~7;
+            B.h_tab_off[b] = acc;
+            B.h_tab_ld[b] = ld;
+            acc += (int64_t)D * ld;
+            if (D == 0 || Gc == 0) continue;
+            int nt = (D + 63) / 64;
+            for (int t1 = 0; t1 < nt; t1++)
+                for (int t2 = t1; t2 < nt; t2++) work.push_back(make_int4(b, t1, t2, 0));
+        }
+        B.tab_elems = acc;
+        B.n_work = (int)work.size();
+        FEM3_TRY(dev_alloc_t(m, &B.tab_off, nb));
+        FEM3_TRY(dev_alloc_t(m, &B.tab_ld, nb));
+        FEM3_TRY(dev_alloc_t(m, &B.work, std::max(1, B.n_work)));
+        FEM3_CUDA(cudaMemcpyAsync(B.tab_off, B.h_tab_off.data(), sizeof(int64_t) * nb,
+                                  cudaMemcpyHostToDevice, s));
+        FEM3_CUDA(cudaMemcpyAsync(B.tab_ld, B.h_tab_ld.data(), sizeof(int32_t) * nb,
+                                  cudaMemcpyHostToDevice, s));
+        if (B.n_work)
+            FEM3_CUDA(cudaMemcpyAsync(B.work, work.data(), sizeof(int4) * B.n_work,
+                                      cudaMemcpyHostToDevice, s));
+        FEM3_TRY(dev_alloc_t(m, &m->tabL[axis], std::max<int64_t>(1, acc)));
+        FEM3_TRY(dev_alloc_t(m, &m->tabR[axis], std::max<int64_t>(1, acc)));
+        // host vectors passed to async copies must outlive them
+        FEM3_CUDA(cudaStreamSynchronize(s));
+    }
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+}  // namespace fem3

@@ -1,0 +1,521 @@
+// Load vector, dense SPD solve and iterative refinement.
+//
+//  - b = M f with the P1 mass matrix (|T|/20 (1 + delta_ab) per tet), the weak
+//    right-hand side (f, v) of Section 3.
+//  - Right-looking blocked Cholesky A = L L^T (block 64): diagonal block in shared
+//    memory, panel triangular solve, trailing symmetric update; row-major storage,
+//    lower triangle.  TF is double (FP64 form) or float (mixed forms).
+//  - Blocked forward / backward substitution.
+//  - Refinement for the mixed forms: r = b - A u with A u applied in FP64 from the FP64
+//    derivative tables (A u = sum_i s_i K_i (L_i^T W (R_i u) + R_i^T W (L_i u))), the
+//    correction solved with the FP32 factor.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fem3_impl.cuh"
+
+namespace fem3 {
+
+namespace {
+
+constexpr int NB = 64;
+
+__global__ void k_load(const int32_t *__restrict__ tets, const double *__restrict__ vol,
+                       const int32_t *__restrict__ dof, int64_t n_tets, int64_t n_nodes,
+                       int64_t n_dof, const double *__restrict__ f, int nrhs, double *b) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_tets) return;
+    int32_t v[4];
+    for (int k = 0; k < 4; k++) v[k] = tets[4 * t + k];
+    double c = vol[t] / 20.0;
+    for (int r = 0; r < nrhs; r++) {
+        const double *fr = f + (int64_t)r * n_nodes;
+        double fv[4], fs = 0;
+        for (int k = 0; k < 4; k++) { fv[k] = fr[v[k]]; fs += fv[k]; }
+        for (int k = 0; k < 4; k++) {
+            int32_t j = dof[v[k]];
+            if (j >= 0) atomicAdd(&b[(int64_t)r * n_dof + j], c * (fs + fv[k]));
+        }
+    }
+}
+
+__global__ void k_load_T(const int32_t *__restrict__ tets, const double *__restrict__ vol,
+                         const int32_t *__restrict__ dof, int64_t n_tets,
+                         const double *__restrict__ lam, double *out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_tets) return;
+    int32_t v[4];
+    double lv[4], ls = 0;
+    for (int k = 0; k < 4; k++) {
+        v[k] = tets[4 * t + k];
+        int32_t j = dof[v[k]];
+        lv[k] = j >= 0 ? lam[j] : 0.0;
+        ls += lv[k];
+    }
+    double c = vol[t] / 20.0;
+    for (int k = 0; k < 4; k++) atomicAdd(&out[v[k]], c * (ls + lv[k]));
+}
+
+// ---------------------------------------------------------------------------------
+// Cholesky
+// ---------------------------------------------------------------------------------
+template <class TF>
+__global__ void __launch_bounds__(256) k_potrf_diag(TF *A, int64_t n, int k0, int32_t *err) {
+    __shared__ TF a[NB][NB + 1];
+    const int nb = (int)min((int64_t)NB, n - k0);
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        a[i][j] = (i < nb && j < nb) ? A[(int64_t)(k0 + i) * n + k0 + j] : TF(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; j++) {
+        if (threadIdx.x == 0) {
+            TF d = a[j][j];
+            if (!(d > TF(0))) {
+                atomicCAS(&err[ERR_NOT_SPD], 0, k0 + j + 1);
+                d = TF(1);
+            }
+            a[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        TF djj = a[j][j];
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] /= djj;
+        __syncthreads();
+        // rank-1 update of the remaining lower part
+        for (int e = threadIdx.x; e < (nb - j - 1) * (nb - j - 1); e += blockDim.x) {
+            int i = j + 1 + e / (nb - j - 1), c = j + 1 + e % (nb - j - 1);
+            if (c <= i) a[i][c] -= a[i][j] * a[c][j];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        int i = e / nb, j = e % nb;
+        A[(int64_t)(k0 + i) * n + k0 + j] = j <= i ? a[i][j] : TF(0);
+    }
+}
+
+// rows [k0+NB, n) of the panel: X L_kk^T = B  (one thread per row, NB columns)
+template <class TF>
+__global__ void __launch_bounds__(NB) k_trsm_panel(TF *A, int64_t n, int k0) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TF(*l)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
+    TF(*x)[NB + 1] = l + NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        l[i][j] = A[(int64_t)(k0 + i) * n + k0 + j];
+    }
+    const int64_t row0 = k0 + NB + (int64_t)blockIdx.x * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        x[i][j] = (row0 + i < n) ? A[(row0 + i) * n + k0 + j] : TF(0);
+    }
+    __syncthreads();
+    const int i = threadIdx.x;
+    for (int j = 0; j < NB; j++) {
+        TF s = x[i][j];
+        for (int c = 0; c < j; c++) s -= x[i][c] * l[j][c];
+        x[i][j] = s / l[j][j];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        int r = e / NB, j = e % NB;
+        if (row0 + r < n) A[(row0 + r) * n + k0 + j] = x[r][j];
+    }
+}
+
+// trailing update of lower tiles: A[i][j] -= sum_c P[i][c] P[j][c], P = panel columns
+template <class TF>
+__global__ void __launch_bounds__(256) k_syrk(TF *A, int64_t n, int k0, int ntile) {
+    // blockIdx.x enumerates lower tiles (ti >= tj) of the trailing matrix
+    int idx = blockIdx.x, ti = 0;
+    while (idx > ti) { idx -= ti + 1; ti++; }
+    int tj = idx;
+    const int64_t base = k0 + NB;
+    const int64_t i0 = base + (int64_t)ti * NB, j0 = base + (int64_t)tj * NB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TF(*pi)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
+    TF(*pj)[NB + 1] = pi + NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        int r = e / NB, c = e % NB;
+        pi[r][c] = (i0 + r < n) ? A[(i0 + r) * n + k0 + c] : TF(0);
+        pj[r][c] = (j0 + r < n) ? A[(j0 + r) * n + k0 + c] : TF(0);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    TF acc[4][4];
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++) acc[a][b] = TF(0);
+    for (int c = 0; c < NB; c++) {
+        TF u[4], v[4];
+        for (int a = 0; a < 4; a++) { u[a] = pi[ty * 4 + a][c]; v[a] = pj[tx * 4 + a][c]; }
+        for (int a = 0; a < 4; a++)
+            for (int b = 0; b < 4; b++) acc[a][b] = fma(u[a], v[b], acc[a][b]);
+    }
+    for (int a = 0; a < 4; a++) {
+        int64_t r = i0 + ty * 4 + a;
+        if (r >= n) continue;
+        for (int b = 0; b < 4; b++) {
+            int64_t c = j0 + tx * 4 + b;
+            if (c >= n || c > r) continue;
+            A[r * n + c] -= acc[a][b];
+        }
+    }
+    (void)ntile;
+}
+
+// ---------------------------------------------------------------------------------
+// triangular solves (single right-hand side, in place in y)
+// ---------------------------------------------------------------------------------
+// forward: y_k <- L_kk^{-1} y_k (one warp), then y_i -= L_ik y_k for rows below
+template <class TF>
+__global__ void k_trsv_fwd_diag(const TF *L, int64_t n, int k0, TF *y) {
+    __shared__ TF ys[NB];
+    const int nb = (int)min((int64_t)NB, n - k0);
+    const int lane = threadIdx.x;
+    for (int i = lane; i < nb; i += 32) ys[i] = y[k0 + i];
+    __syncwarp();
+    for (int j = 0; j < nb; j++) {
+        TF s = TF(0);
+        for (int c = lane; c < j; c += 32) s += L[(int64_t)(k0 + j) * n + k0 + c] * ys[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) ys[j] = (ys[j] - s) / L[(int64_t)(k0 + j) * n + k0 + j];
+        __syncwarp();
+    }
+    for (int i = lane; i < nb; i += 32) y[k0 + i] = ys[i];
+}
+
+template <class TF>
+__global__ void k_trsv_fwd_update(const TF *L, int64_t n, int k0, TF *y) {
+    // one warp per row below the block
+    int64_t row = k0 + NB + (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    TF s = L[row * n + k0 + lane] * y[k0 + lane] + L[row * n + k0 + 32 + lane] * y[k0 + 32 + lane];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] -= s;
+}
+
+// backward with L^T: block k solved with L_kk^T, then y_i -= sum_c L[k0+c][i] y[k0+c]
+template <class TF>
+__global__ void k_trsv_bwd_diag(const TF *L, int64_t n, int k0, TF *y) {
+    __shared__ TF ys[NB];
+    const int nb = (int)min((int64_t)NB, n - k0);
+    const int lane = threadIdx.x;
+    for (int i = lane; i < nb; i += 32) ys[i] = y[k0 + i];
+    __syncwarp();
+    for (int j = nb - 1; j >= 0; j--) {
+        TF s = TF(0);
+        for (int c = j + 1 + lane; c < nb; c += 32) s += L[(int64_t)(k0 + c) * n + k0 + j] * ys[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) ys[j] = (ys[j] - s) / L[(int64_t)(k0 + j) * n + k0 + j];
+        __syncwarp();
+    }
+    for (int i = lane; i < nb; i += 32) y[k0 + i] = ys[i];
+}
+
+template <class TF>
+__global__ void k_trsv_bwd_update(const TF *L, int64_t n, int k0, int nb, TF *y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k0) return;
+    TF s = TF(0);
+    for (int c = 0; c < nb; c++) s += L[(int64_t)(k0 + c) * n + i] * y[k0 + c];
+    y[i] -= s;
+}
+
+template <class TF>
+int cholesky_t(TF *A, int64_t n, cudaStream_t s, int32_t *err) {
+    const size_t sh = 2 * NB * (NB + 1) * sizeof(TF);
+    FEM3_CUDA(cudaFuncSetAttribute(k_trsm_panel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    FEM3_CUDA(cudaFuncSetAttribute(k_syrk<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    for (int64_t k0 = 0; k0 < n; k0 += NB) {
+        k_potrf_diag<TF><<<1, 256, 0, s>>>(A, n, (int)k0, err);
+        int64_t rest = n - k0 - NB;
+        if (rest > 0) {
+            int nblk = (int)((rest + NB - 1) / NB);
+            k_trsm_panel<TF><<<nblk, NB, sh, s>>>(A, n, (int)k0);
+            int ntiles = nblk * (nblk + 1) / 2;
+            k_syrk<TF><<<ntiles, 256, sh, s>>>(A, n, (int)k0, nblk);
+        }
+    }
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+template <class TF>
+int trsv_t(const TF *L, int64_t n, TF *y, cudaStream_t s) {
+    for (int64_t k0 = 0; k0 < n; k0 += NB) {
+        k_trsv_fwd_diag<TF><<<1, 32, 0, s>>>(L, n, (int)k0, y);
+        int64_t rest = n - k0 - NB;
+        if (rest > 0) k_trsv_fwd_update<TF><<<(unsigned)((rest + 7) / 8), 256, 0, s>>>(L, n, (int)k0, y);
+    }
+    int64_t last = ((n - 1) / NB) * NB;
+    for (int64_t k0 = last; k0 >= 0; k0 -= NB) {
+        k_trsv_bwd_diag<TF><<<1, 32, 0, s>>>(L, n, (int)k0, y);
+        if (k0 > 0) {
+            int nb = (int)std::min<int64_t>(NB, n - k0);
+            k_trsv_bwd_update<TF><<<(unsigned)((k0 + 255) / 256), 256, 0, s>>>(L, n, (int)k0, nb, y);
+        }
+    }
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// matrix-free FP64 operator from the tables; one CTA per (bin) of one axis
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_apply_tables(
+    const double *__restrict__ tabL, const double *__restrict__ tabR,
+    const int32_t *__restrict__ gp_off, const int32_t *__restrict__ gp_idx,
+    const int32_t *__restrict__ dof_off, const int32_t *__restrict__ dof_idx,
+    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
+    const double *__restrict__ gw, const double *__restrict__ u, double sK, double *Au) {
+    extern __shared__ double sm[];
+    const int bin = blockIdx.x;
+    const int D = dof_off[bin + 1] - dof_off[bin];
+    const int G = gp_off[bin + 1] - gp_off[bin];
+    if (D == 0 || G == 0) return;
+    const int ld = tab_ld[bin];
+    const double *L = tabL + tab_off[bin], *R = tabR + tab_off[bin];
+    const int32_t *dofs = dof_idx + dof_off[bin];
+    const int32_t *slots = gp_idx + gp_off[bin];
+    double *ub = sm, *yL = sm + D, *yR = yL + G;
+    for (int c = threadIdx.x; c < D; c += blockDim.x) ub[c] = u[dofs[c]];
+    __syncthreads();
+    for (int r = threadIdx.x; r < G; r += blockDim.x) {
+        double sl = 0, sr = 0;
+        for (int c = 0; c < D; c++) {
+            sl = fma(L[(int64_t)c * ld + r], ub[c], sl);
+            sr = fma(R[(int64_t)c * ld + r], ub[c], sr);
+        }
+        double w = gw[slots[r]];
+        yL[r] = w * sl;
+        yR[r] = w * sr;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = warp; c < D; c += nw) {
+        double z = 0;
+        for (int r = lane; r < G; r += 32)
+            z = fma(L[(int64_t)c * ld + r], yR[r], fma(R[(int64_t)c * ld + r], yL[r], z));
+        for (int o = 16; o > 0; o >>= 1) z += __shfl_down_sync(0xffffffffu, z, o);
+        if (lane == 0) atomicAdd(&Au[dofs[c]], sK * z);
+    }
+}
+
+// per-axis forms sum_g w_g ((L lam)(R u) + (R lam)(L u)) (adjoint), one CTA per bin
+__global__ void __launch_bounds__(256) k_axis_form(
+    const double *__restrict__ tabL, const double *__restrict__ tabR,
+    const int32_t *__restrict__ gp_off, const int32_t *__restrict__ gp_idx,
+    const int32_t *__restrict__ dof_off, const int32_t *__restrict__ dof_idx,
+    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
+    const double *__restrict__ gw, const double *__restrict__ u, const double *__restrict__ lam,
+    double *out) {
+    extern __shared__ double sm[];
+    const int bin = blockIdx.x;
+    const int D = dof_off[bin + 1] - dof_off[bin];
+    const int G = gp_off[bin + 1] - gp_off[bin];
+    if (D == 0 || G == 0) return;
+    const int ld = tab_ld[bin];
+    const double *L = tabL + tab_off[bin], *R = tabR + tab_off[bin];
+    const int32_t *dofs = dof_idx + dof_off[bin];
+    const int32_t *slots = gp_idx + gp_off[bin];
+    double *ub = sm, *lb = sm + D;
+    __shared__ double red[8];
+    for (int c = threadIdx.x; c < D; c += blockDim.x) { ub[c] = u[dofs[c]]; lb[c] = lam[dofs[c]]; }
+    __syncthreads();
+    double acc = 0;
+    for (int r = threadIdx.x; r < G; r += blockDim.x) {
+        double Lu = 0, Ru = 0, Ll = 0, Rl = 0;
+        for (int c = 0; c < D; c++) {
+            double lv = L[(int64_t)c * ld + r], rv = R[(int64_t)c * ld + r];
+            Lu = fma(lv, ub[c], Lu); Ru = fma(rv, ub[c], Ru);
+            Ll = fma(lv, lb[c], Ll); Rl = fma(rv, lb[c], Rl);
+        }
+        acc += gw[slots[r]] * (Ll * Ru + Rl * Lu);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+        atomicAdd(out, s);
+    }
+}
+
+// r = b - Au; norms[0] += |r|^2, norms[1] += |b|^2
+__global__ void k_residual(const double *__restrict__ b, const double *__restrict__ Au, int64_t n,
+                           double *r, double *norms) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double rr = 0, bb = 0;
+    if (i < n) {
+        double v = b[i] - Au[i];
+        r[i] = v;
+        rr = v * v;
+        bb = b[i] * b[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_down_sync(0xffffffffu, rr, o);
+        bb += __shfl_down_sync(0xffffffffu, bb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&norms[0], rr);
+        atomicAdd(&norms[1], bb);
+    }
+}
+
+__global__ void k_to_f32(const double *__restrict__ a, float *b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_axpy_f32(const float *__restrict__ d, double *u, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) u[i] += (double)d[i];
+}
+__global__ void k_f32_to_f64(const float *__restrict__ a, double *b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+__global__ void k_sub(const double *__restrict__ a, const double *__restrict__ b, double *c,
+                      int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) c[i] = a[i] - b[i];
+}
+
+inline unsigned g256(int64_t n) { return (unsigned)(n > 0 ? (n + 255) / 256 : 1); }
+
+}  // namespace
+
+int f32_to_f64(const float *a, double *b, int64_t n, cudaStream_t s) {
+    k_f32_to_f64<<<g256(n), 256, 0, s>>>(a, b, n);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int sub_vec(const double *a, const double *b, double *c, int64_t n, cudaStream_t s) {
+    k_sub<<<g256(n), 256, 0, s>>>(a, b, c, n);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int residual_norm(Mesh *m, const double *b, const double *Au, double *rel) {
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n_dof;
+    FEM3_CUDA(cudaMemsetAsync(m->norms, 0, sizeof(double) * 2, s));
+    k_residual<<<g256(n), 256, 0, s>>>(b, Au, n, m->vec64[1], m->norms);
+    FEM3_CUDA(cudaMemcpyAsync(m->h_norms, m->norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    FEM3_CUDA(cudaStreamSynchronize(s));
+    *rel = m->h_norms[1] > 0 ? sqrt(m->h_norms[0] / m->h_norms[1]) : 0.0;
+    return FEM3_OK;
+}
+
+int load_vector(Mesh *m, const double *f_d, int nrhs, double *b_d) {
+    cudaStream_t s = m->stream;
+    FEM3_CUDA(cudaMemsetAsync(b_d, 0, sizeof(double) * m->n_dof * nrhs, s));
+    k_load<<<g256(m->n_tets), 256, 0, s>>>(m->tets, m->vol, m->dof, m->n_tets, m->n_nodes, m->n_dof,
+                                            f_d, nrhs, b_d);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int load_vector_T(Mesh *m, const double *lam_d, double *out_d) {
+    cudaStream_t s = m->stream;
+    FEM3_CUDA(cudaMemsetAsync(out_d, 0, sizeof(double) * m->n_nodes, s));
+    k_load_T<<<g256(m->n_tets), 256, 0, s>>>(m->tets, m->vol, m->dof, m->n_tets, lam_d, out_d);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int factor(Mesh *m) {
+    if (m->precision == FEM3_FP64) return cholesky_t<double>(m->A64, m->n_dof, m->stream, m->err);
+    return cholesky_t<float>(m->A32, m->n_dof, m->stream, m->err);
+}
+
+int apply_A64(Mesh *m, const double *u_d, double *Au_d) {
+    cudaStream_t s = m->stream;
+    FEM3_CUDA(cudaFuncSetAttribute(k_apply_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(double) * 3 * kMaxBinItems)));
+    FEM3_CUDA(cudaMemsetAsync(Au_d, 0, sizeof(double) * m->n_dof, s));
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        size_t sh = sizeof(double) * (B.max_dof + 2 * B.max_gp);
+        k_apply_tables<<<B.n_bins, 256, sh, s>>>(m->tabL[axis], m->tabR[axis], B.gp_off, B.gp_idx,
+                                                  B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, m->gw,
+                                                  u_d, m->sK[axis], Au_d);
+    }
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int axis_forms(Mesh *m, const double *u_d, const double *lam_d, double out[3]) {
+    cudaStream_t s = m->stream;
+    FEM3_CUDA(cudaFuncSetAttribute(k_axis_form, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(double) * 2 * kMaxBinItems)));
+    FEM3_CUDA(cudaMemsetAsync(m->norms, 0, sizeof(double) * 3, s));
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        size_t sh = sizeof(double) * 2 * B.max_dof;
+        k_axis_form<<<B.n_bins, 256, sh, s>>>(m->tabL[axis], m->tabR[axis], B.gp_off, B.gp_idx,
+                                               B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, m->gw, u_d,
+                                               lam_d, m->norms + axis);
+    }
+    FEM3_CUDA(cudaMemcpyAsync(m->h_norms, m->norms, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    FEM3_CUDA(cudaStreamSynchronize(s));
+    for (int a = 0; a < 3; a++) out[a] = m->s[a] * m->h_norms[a];
+    return FEM3_OK;
+}
+
+int solve_direct(Mesh *m, const double *b_d, int nrhs, double *u_d) {
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n_dof;
+    FEM3_CUDA(cudaMemcpyAsync(u_d, b_d, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
+    for (int r = 0; r < nrhs; r++) FEM3_TRY(trsv_t<double>(m->A64, n, u_d + r * n, s));
+    return FEM3_OK;
+}
+
+int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter, double *u_d,
+                  int *iters, double *resid) {
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n_dof;
+    double *Au = m->vec64[0], *r = m->vec64[1];
+    float *r32 = m->vec32[0];
+    int it_max = 0;
+    double worst = 0;
+    for (int col = 0; col < nrhs; col++) {
+        const double *b = b_d + col * n;
+        double *u = u_d + col * n;
+        FEM3_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
+        FEM3_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        int it = 0;
+        double rel = 1.0;
+        for (;;) {
+            k_to_f32<<<g256(n), 256, 0, s>>>(r, r32, n);
+            FEM3_TRY(trsv_t<float>(m->A32, n, r32, s));
+            k_axpy_f32<<<g256(n), 256, 0, s>>>(r32, u, n);
+            FEM3_TRY(apply_A64(m, u, Au));
+            FEM3_CUDA(cudaMemsetAsync(m->norms, 0, sizeof(double) * 2, s));
+            k_residual<<<g256(n), 256, 0, s>>>(b, Au, n, r, m->norms);
+            FEM3_CUDA(cudaMemcpyAsync(m->h_norms, m->norms, sizeof(double) * 2,
+                                      cudaMemcpyDeviceToHost, s));
+            FEM3_CUDA(cudaStreamSynchronize(s));
+            rel = m->h_norms[1] > 0 ? sqrt(m->h_norms[0] / m->h_norms[1]) : 0.0;
+            it++;
+            if (rel <= tol || it >= max_iter || !(rel == rel)) break;
+        }
+        it_max = std::max(it_max, it);
+        worst = std::max(worst, rel);
+        if (!(rel <= tol)) {
+            if (iters) *iters = it_max;
+            if (resid) *resid = worst;
+            return set_error(FEM3_E_NO_CONVERGE, "iterative refinement did not reach the tolerance");
+        }
+    }
+    if (iters) *iters = it_max;
+    if (resid) *resid = worst;
+    return FEM3_OK;
+}
+
+}  // namespace fem3

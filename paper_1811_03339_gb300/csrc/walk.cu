@@ -1,0 +1,315 @@
+// Path walk (Section 2.2) fused with the closed-form derivative tables (Section 2.1).
+//
+// One thread walks one (Gauss point, axis, side) ray x_g + r * dir * e_axis, r >= 0.
+// In the current tet the ray's volume coordinates are b~ + r d~ with b~ = lambda_T(x_g)
+// and d~ = dir * dlambda/dx_axis (eq. "cond"); the go-out parameter is
+// r_max = min over d~_k < 0 of -b~_k / d~_k, and the zero pattern of b~ + r_max d~
+// names the exit m-face (Fig. "fig:vc"): one zero -> the face neighbour, two -> an edge,
+// three -> a vertex, in which case every tet holding the m-face is searched and the one
+// the ray runs furthest into is taken (ties within eps_r: smallest id).
+//
+// On each segment [r_near, r_far] of tet T the left / right Riemann-Liouville
+// derivative of order gamma of every local P1 basis function is added in closed form:
+//   D_L:  + dphi/dx_axis |_T * (r_far^(1-gamma) - r_near^(1-gamma)) / Gamma(2-gamma)
+//   D_R:  - (same)
+// (integration by parts of eq. "def" on a segment where phi is linear; the end-point
+// term phi(a) (x-a)^(-gamma)/Gamma(1-gamma) vanishes for interior basis functions).
+// The sum telescopes over the path, so only one power r^(1-gamma) per segment end is
+// evaluated.  Rows are accumulated in place in the thread's own column of its bin's
+// table block [D_b][ld_b] (no two threads share an element).
+#include <math.h>
+
+#include "fem3_impl.cuh"
+
+namespace fem3 {
+
+namespace {
+
+struct WalkGeom {
+    const double *__restrict__ M;     // [T][16]
+    const double *__restrict__ inv;   // [T][3][4]
+    const int32_t *__restrict__ tets; // [T][4]
+    const int32_t *__restrict__ nbr;  // [T][4]
+    const int32_t *__restrict__ dof;  // [N]
+    const int32_t *__restrict__ vt_off;
+    const int32_t *__restrict__ vt_tet;
+    const double *__restrict__ gp;    // [G][3]
+    double eps_r;
+    int max_steps;
+};
+
+// go-out parameter of the ray in tet t: min over exit candidates of b~_k * nd_k
+__device__ __forceinline__ double tet_rmax(const WalkGeom &W, int32_t t, int axis, int dir,
+                                           double x0, double x1, double x2, double b[4]) {
+    const double2 *Mt = reinterpret_cast<const double2 *>(W.M + 16 * (int64_t)t);
+    const double *iv = W.inv + 12 * (int64_t)t + 4 * axis;
+    double rmax = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        double2 a = Mt[2 * k], c = Mt[2 * k + 1];
+        b[k] = fma(c.y, x2, fma(c.x, x1, fma(a.y, x0, a.x)));
+        double nd = dir > 0 ? -iv[k] : iv[k];  // -dir / (dlambda_k/dx_axis)
+        if (nd > 0.0) rmax = fmin(rmax, b[k] * nd);
+    }
+    return rmax;
+}
+
+// next tet after leaving t at parameter rmax; -1 at the boundary, -2 on a bad pattern
+__device__ int32_t next_tet(const WalkGeom &W, int32_t t, int axis, int dir, double x0,
+                            double x1, double x2, const double b[4], double rmax) {
+    const double *Mt = W.M + 16 * (int64_t)t;
+    int zmask = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        double lam = fma(rmax, dir * Mt[4 * k + 1 + axis], b[k]);
+        if (lam <= kEpsLambda) zmask |= 1 << k;
+    }
+    int nz = __popc(zmask);
+    if (nz == 1) return W.nbr[4 * (int64_t)t + (__ffs(zmask) - 1)];
+    if (nz < 2 || nz > 3) return -2;
+    // edge or vertex exit: search the star of the m-face
+    int32_t fv[4];
+    int nf = 0;
+    for (int k = 0; k < 4; k++)
+        if (!(zmask & (1 << k))) fv[nf++] = W.tets[4 * (int64_t)t + k];
+    int32_t v0 = fv[0];
+    double best = -INFINITY;
+    int32_t next = -1;
+    for (int pass = 0; pass < 2; pass++) {
+        for (int32_t c = W.vt_off[v0]; c < W.vt_off[v0 + 1]; c++) {
+            int32_t u = W.vt_tet[c];
+            if (u == t) continue;
+            bool has_all = true;
+            for (int f = 1; f < nf; f++) {
+                bool found = false;
+                for (int q = 0; q < 4; q++) found |= W.tets[4 * (int64_t)u + q] == fv[f];
+                has_all &= found;
+            }
+            if (!has_all) continue;
+            double bu[4];
+            double ru = tet_rmax(W, u, axis, dir, x0, x1, x2, bu);
+            if (!(ru > rmax + W.eps_r)) continue;
+            if (pass == 0) {
+                best = fmax(best, ru);
+            } else if (ru >= best - W.eps_r && (next < 0 || u < next)) {
+                next = u;
+            }
+        }
+    }
+    return next;
+}
+
+__device__ __forceinline__ int bsearch_dof(const int32_t *__restrict__ d, int n, int32_t j) {
+    int lo = 0, hi = n - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int32_t v = __ldg(d + mid);
+        if (v == j) return mid;
+        if (v < j) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+struct TableArgs {
+    const int32_t *__restrict__ gp_idx;   // [n_gp] slot -> Gauss point
+    const int32_t *__restrict__ slot_bin; // [n_gp]
+    const int32_t *__restrict__ gp_off;   // [n_bins+1]
+    const int32_t *__restrict__ dof_off;  // [n_bins+1]
+    const int32_t *__restrict__ dof_idx;
+    const int64_t *__restrict__ tab_off;
+    const int32_t *__restrict__ tab_ld;
+    double *tab;                          // L (side 0) or R (side 1) of this axis
+    double p_exp;                         // 1 - gamma
+    double coef;                          // +1/Gamma(2-gamma) (left) or -1/Gamma(2-gamma)
+};
+
+// grid: x over slots of one axis, y = side (0 left, 1 right); one launch per axis
+__global__ void __launch_bounds__(128) k_walk_tables(WalkGeom W, TableArgs A0, TableArgs A1,
+                                                     int axis, int64_t n_gp, int32_t *err,
+                                                     unsigned long long *seg_count) {
+    int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int side = blockIdx.y;
+    const TableArgs &A = side ? A1 : A0;
+    const int dir = side ? 1 : -1;
+    int nseg = 0;
+    if (slot < n_gp) {
+        const int32_t g = A.gp_idx[slot];
+        const int32_t bin = A.slot_bin[slot];
+        const int32_t row = (int32_t)(slot - A.gp_off[bin]);
+        const int32_t *dofs = A.dof_idx + A.dof_off[bin];
+        const int nd = A.dof_off[bin + 1] - A.dof_off[bin];
+        const int32_t ld = A.tab_ld[bin];
+        double *tab = A.tab + A.tab_off[bin] + row;
+
+        const double x0 = W.gp[3 * (int64_t)g], x1 = W.gp[3 * (int64_t)g + 1],
+                     x2 = W.gp[3 * (int64_t)g + 2];
+        int32_t t = g >> 2;
+        double r_prev = 0.0, P_prev = 0.0;
+        int32_t cj[4] = {-1, -1, -1, -1}, cc[4] = {-1, -1, -1, -1};
+        int miss = 0;
+        bool ok = false;
+        for (int step = 0; step < W.max_steps; step++) {
+            double b[4];
+            double rmax = tet_rmax(W, t, axis, dir, x0, x1, x2, b);
+            if (!(rmax < INFINITY)) break;
+            if (rmax - r_prev > W.eps_r) {
+                double P = pow(rmax, A.p_exp);
+                double c = A.coef * (P - P_prev);
+                const double *Mt = W.M + 16 * (int64_t)t;
+                int32_t nj[4], nc[4];
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    int32_t j = W.dof[W.tets[4 * (int64_t)t + v]];
+                    int32_t col = -1;
+                    if (j >= 0) {
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            if (cj[q] == j) col = cc[q];
+                        if (col < 0) col = bsearch_dof(dofs, nd, j);
+                        if (col >= 0)
+                            tab[(int64_t)col * ld] += c * Mt[4 * v + 1 + axis];
+                        else
+                            miss++;
+                    }
+                    nj[v] = j;
+                    nc[v] = col;
+                }
+#pragma unroll
+                for (int v = 0; v < 4; v++) { cj[v] = nj[v]; cc[v] = nc[v]; }
+                P_prev = P;
+                r_prev = rmax;
+                nseg++;
+            }
+            int32_t nx = next_tet(W, t, axis, dir, x0, x1, x2, b, rmax);
+            if (nx == -1) { ok = true; break; }
+            if (nx < 0) break;
+            t = nx;
+        }
+        if (!ok) atomicAdd(&err[ERR_WALK], 1);
+        if (miss) atomicAdd(&err[ERR_TEMPLATE], miss);
+    }
+    // segment counter (one atomic per warp; every lane takes part)
+    unsigned long long ns = (unsigned long long)nseg;
+    for (int o = 16; o > 0; o >>= 1) ns += __shfl_down_sync(0xffffffffu, ns, o);
+    if ((threadIdx.x & 31) == 0 && ns) atomicAdd(seg_count, ns);
+}
+
+// Path export: same walk, segments written out for requested lines.
+__global__ void k_walk_paths(WalkGeom W, int axis, int dir, const int64_t *__restrict__ gps,
+                             int64_t n_lines, int64_t n_gp, int cap, int32_t *tet_out, double *r0_out,
+                             double *r1_out, int32_t *nseg_out) {
+    int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (l >= n_lines) return;
+    int64_t g = gps[l];
+    if (g < 0 || g >= n_gp) {
+        nseg_out[l] = -1;
+        return;
+    }
+    const double x0 = W.gp[3 * g], x1 = W.gp[3 * g + 1], x2 = W.gp[3 * g + 2];
+    int32_t t = (int32_t)(g >> 2);
+    double r_prev = 0.0;
+    int nseg = 0;
+    bool ok = false;
+    for (int step = 0; step < W.max_steps; step++) {
+        double b[4];
+        double rmax = tet_rmax(W, t, axis, dir, x0, x1, x2, b);
+        if (!(rmax < INFINITY)) break;
+        if (rmax - r_prev > W.eps_r) {
+            if (nseg >= cap) break;
+            tet_out[l * cap + nseg] = t;
+            r0_out[l * cap + nseg] = r_prev;
+            r1_out[l * cap + nseg] = rmax;
+            nseg++;
+            r_prev = rmax;
+        }
+        int32_t nx = next_tet(W, t, axis, dir, x0, x1, x2, b, rmax);
+        if (nx == -1) { ok = true; break; }
+        if (nx < 0) break;
+        t = nx;
+    }
+    nseg_out[l] = ok ? nseg : -1;
+}
+
+// Gather rows of a binned table into dense rows [n][n_dof] (zero elsewhere).
+__global__ void k_table_rows(const double *__restrict__ tab, const int32_t *__restrict__ gbin_slot,
+                             const int64_t *__restrict__ gps, int64_t n,
+                             const int32_t *__restrict__ slot_of_gp,
+                             const int32_t *__restrict__ gp_off, const int32_t *__restrict__ dof_off,
+                             const int32_t *__restrict__ dof_idx,
+                             const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
+                             int64_t n_dof, int64_t n_gp, double *rows) {
+    int64_t l = blockIdx.x;
+    if (l >= n) return;
+    int64_t g = gps[l];
+    if (g < 0 || g >= n_gp) return;
+    int32_t slot = slot_of_gp[g];
+    int32_t bin = gbin_slot[slot];
+    int32_t row = slot - gp_off[bin];
+    int d0 = dof_off[bin], nd = dof_off[bin + 1] - d0;
+    for (int c = threadIdx.x; c < nd; c += blockDim.x)
+        rows[l * n_dof + dof_idx[d0 + c]] = tab[tab_off[bin] + (int64_t)c * tab_ld[bin] + row];
+}
+
+WalkGeom make_geom(Mesh *m) {
+    WalkGeom W;
+    W.M = m->M; W.inv = m->inv; W.tets = m->tets; W.nbr = m->nbr; W.dof = m->dof;
+    W.vt_off = m->vt_off; W.vt_tet = m->vt_tet; W.gp = m->gp;
+    W.eps_r = kEpsRRel * m->span;
+    W.max_steps = m->max_steps;
+    return W;
+}
+
+}  // namespace
+
+int walk_tables(Mesh *m, const double alpha[3]) {
+    cudaStream_t s = m->stream;
+    WalkGeom W = make_geom(m);
+    unsigned long long *segc = reinterpret_cast<unsigned long long *>(m->norms + 8);
+    FEM3_CUDA(cudaMemsetAsync(segc, 0, sizeof(unsigned long long), s));
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        FEM3_CUDA(cudaMemsetAsync(m->tabL[axis], 0, sizeof(double) * B.tab_elems, s));
+        FEM3_CUDA(cudaMemsetAsync(m->tabR[axis], 0, sizeof(double) * B.tab_elems, s));
+    }
+    stage_begin(m, 2);
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        double gamma = alpha[axis] / 2.0;
+        double ig = 1.0 / tgamma(2.0 - gamma);
+        TableArgs A0{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
+                     B.tab_ld, m->tabL[axis], 1.0 - gamma, ig};
+        TableArgs A1 = A0;
+        A1.tab = m->tabR[axis];
+        A1.coef = -ig;
+        dim3 grid((unsigned)((m->n_gp + 127) / 128), 2);
+        k_walk_tables<<<grid, 128, 0, s>>>(W, A0, A1, axis, m->n_gp, m->err, segc);
+    }
+    stage_end(m, 2);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int walk_paths(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, int cap,
+               int32_t *tet_out, double *r0, double *r1, int32_t *nseg) {
+    WalkGeom W = make_geom(m);
+    k_walk_paths<<<(unsigned)((n + 127) / 128), 128, 0, m->stream>>>(W, axis, dir, gps, n, m->n_gp,
+                                                                      cap, tet_out, r0, r1, nseg);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double *rows) {
+    cudaStream_t s = m->stream;
+    AxisBins &B = m->bins[axis];
+    const int32_t *slot_of_gp = B.slot_of_gp;
+    FEM3_CUDA(cudaMemsetAsync(rows, 0, sizeof(double) * n * m->n_dof, s));
+    const double *tab = dir < 0 ? m->tabL[axis] : m->tabR[axis];
+    if (n > 0)
+        k_table_rows<<<(unsigned)n, 128, 0, s>>>(tab, B.slot_bin, gps, n, slot_of_gp, B.gp_off,
+                                                  B.dof_off, B.dof_idx, B.tab_off, B.tab_ld,
+                                                  m->n_dof, m->n_gp, rows);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+}  // namespace fem3

@@ -1,0 +1,276 @@
+"""Thin Python binding of libfem3 (argument marshalling only).
+
+Every step of the method runs in the CUDA library; this module converts torch tensors
+or numpy arrays into pointers, passes the current torch stream, and turns status codes
+into exceptions.  There is no CPU fallback: if the library is missing the calls raise.
+
+The functions mirror the C ABI of ``include/fem3.h`` (``fem3_mesh_upload`` ->
+``mesh_upload`` ...); ``Mesh`` wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build_lib
+
+FEM3_OK = 0
+FEM3_E_ARG, FEM3_E_MESH, FEM3_E_WALK, FEM3_E_NOT_SPD = -1, -2, -3, -4
+FEM3_E_NO_CONVERGE, FEM3_E_CUDA, FEM3_E_OOM, FEM3_E_STATE, FEM3_E_TEMPLATE = -5, -6, -7, -8, -9
+
+PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2}
+
+# every entry point declared in include/fem3.h
+SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_load", "fem3_solve",
+           "fem3_adjoint", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
+           "fem3_counters", "fem3_last_error", "fem3_mesh_free")
+
+_lib = None
+
+
+class Fem3Error(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fem3 status {code}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("bin_scale", C.c_double), ("max_steps", C.c_int32), ("profile", C.c_int32)]
+
+
+def lib_path() -> str:
+    return _build_lib.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libfem3.so (compiling it first if it is missing or stale and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build_lib.up_to_date():
+        _build_lib.build()
+    if not os.path.exists(_build_lib.LIB):
+        raise RuntimeError("libfem3.so is not built; call __graft_entry__.build()")
+    lib = C.CDLL(_build_lib.LIB)
+    p, i64, i32, dbl, ci = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_int
+    sig = {
+        "fem3_mesh_upload": [p, i64, p, i64, C.POINTER(Options), p, C.POINTER(p)],
+        "fem3_mesh_info": [p, C.POINTER(i64), C.POINTER(i64), p],
+        "fem3_assemble": [p, p, p, ci, p, p],
+        "fem3_load": [p, p, ci, p, p],
+        "fem3_solve": [p, p, ci, dbl, ci, p, C.POINTER(ci), C.POINTER(dbl), p],
+        "fem3_adjoint": [p, p, p, dbl, ci, p, p, p],
+        "fem3_paths": [p, ci, ci, p, i64, ci, p, p, p, p, p],
+        "fem3_table_rows": [p, ci, ci, p, i64, p, p],
+        "fem3_sync": [p, p],
+        "fem3_stage_ms": [p, ci, C.POINTER(C.c_float)],
+        "fem3_counters": [p, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)],
+        "fem3_last_error": [C.c_char_p, C.c_size_t],
+        "fem3_mesh_free": [p],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = None if name == "fem3_mesh_free" else ci
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != FEM3_OK:
+        buf = C.create_string_buffer(512)
+        _lib.fem3_last_error(buf, 512)
+        raise Fem3Error(code, buf.value.decode(errors="replace"))
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(x):
+    """Pointer of a torch tensor (any device) or a numpy array (host)."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"] or x.flags["F_CONTIGUOUS"]
+        return C.c_void_p(x.ctypes.data)
+    assert x.is_contiguous(), "tensor must be contiguous"
+    return C.c_void_p(x.data_ptr())
+
+
+# ---------------------------------------------------------------------------------
+# functions with the C ABI's names
+# ---------------------------------------------------------------------------------
+def mesh_upload(verts, tets, bin_scale: float = 1.0, max_steps: int = 0, profile: bool = False,
+                stream=None):
+    lib = load_library()
+    opt = Options(bin_scale, max_steps, 1 if profile else 0)
+    h = C.c_void_p()
+    _check(lib.fem3_mesh_upload(_ptr(verts), int(verts.shape[0]), _ptr(tets), int(tets.shape[0]),
+                                C.byref(opt), _stream(stream), C.byref(h)))
+    return h
+
+
+def mesh_info(h, n_nodes: int | None = None):
+    n_dof, n_gp = C.c_int64(), C.c_int64()
+    dof = np.empty(n_nodes, dtype=np.int32) if n_nodes else None
+    _check(_lib.fem3_mesh_info(h, C.byref(n_dof), C.byref(n_gp),
+                               _ptr(dof) if dof is not None else None))
+    return n_dof.value, n_gp.value, dof
+
+
+def assemble(h, alpha, K, precision="fp64", A_out=None, stream=None):
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    k = np.ascontiguousarray(K, dtype=np.float64)
+    _check(_lib.fem3_assemble(h, _ptr(a), _ptr(k), PRECISIONS[precision],
+                              _ptr(A_out) if A_out is not None else None, _stream(stream)))
+
+
+def load(h, f, nrhs, b, stream=None):
+    _check(_lib.fem3_load(h, _ptr(f), int(nrhs), _ptr(b), _stream(stream)))
+
+
+def solve(h, f, nrhs, u, tol=1e-12, max_iter=50, stream=None):
+    it, res = C.c_int(0), C.c_double(0)
+    _check(_lib.fem3_solve(h, _ptr(f), int(nrhs), float(tol), int(max_iter), _ptr(u),
+                           C.byref(it), C.byref(res), _stream(stream)))
+    return it.value, res.value
+
+
+def adjoint(h, u, u_obs, dJ_df=None, tol=1e-12, max_iter=50, stream=None):
+    dK = np.zeros(3)
+    _check(_lib.fem3_adjoint(h, _ptr(u), _ptr(u_obs), float(tol), int(max_iter), _ptr(dK),
+                             _ptr(dJ_df) if dJ_df is not None else None, _stream(stream)))
+    return dK
+
+
+def paths(h, axis, direction, gps, cap, tet_out, r_in, r_out, nseg, stream=None):
+    _check(_lib.fem3_paths(h, int(axis), int(direction), _ptr(gps), int(gps.shape[0]), int(cap),
+                           _ptr(tet_out), _ptr(r_in), _ptr(r_out), _ptr(nseg), _stream(stream)))
+
+
+def table_rows(h, axis, direction, gps, rows, stream=None):
+    _check(_lib.fem3_table_rows(h, int(axis), int(direction), _ptr(gps), int(gps.shape[0]),
+                                _ptr(rows), _stream(stream)))
+
+
+def sync(h, stream=None):
+    _check(_lib.fem3_sync(h, _stream(stream)))
+
+
+def stage_ms(h):
+    out = []
+    for k in range(7):
+        v = C.c_float(0)
+        _check(_lib.fem3_stage_ms(h, k, C.byref(v)))
+        out.append(v.value)
+    return out
+
+
+def counters(h):
+    s, f, b = C.c_int64(), C.c_double(), C.c_int64()
+    _check(_lib.fem3_counters(h, C.byref(s), C.byref(f), C.byref(b)))
+    return dict(segments=s.value, contract_flops=f.value, table_bytes=b.value)
+
+
+def mesh_free(h):
+    if h and _lib is not None:
+        _lib.fem3_mesh_free(h)
+
+
+# ---------------------------------------------------------------------------------
+class Mesh:
+    """A mesh uploaded to the current CUDA device (torch's current stream by default)."""
+
+    def __init__(self, verts, tets, bin_scale: float = 1.0, max_steps: int = 0,
+                 profile: bool = False, stream=None):
+        import torch
+        self._torch = torch
+        self.stream = stream
+        if isinstance(verts, np.ndarray):
+            verts = np.ascontiguousarray(verts, dtype=np.float64)
+            tets = np.ascontiguousarray(tets, dtype=np.int32)
+        self.n_nodes = int(verts.shape[0])
+        self.n_tets = int(tets.shape[0])
+        self.h = mesh_upload(verts, tets, bin_scale, max_steps, profile, stream)
+        self.n_dof, self.n_gp, self.dof_of_node = mesh_info(self.h, self.n_nodes)
+        self.precision = None
+
+    def _dev(self, shape, dtype=None):
+        t = self._torch
+        return t.empty(shape, dtype=dtype or t.float64, device="cuda")
+
+    def assemble(self, alpha, K, precision="fp64", return_matrix=False):
+        A = self._dev((self.n_dof, self.n_dof)) if return_matrix else None
+        assemble(self.h, alpha, K, precision, A, self.stream)
+        self.precision = precision
+        return A
+
+    def load(self, f):
+        f = self._as_nodal(f)
+        nrhs = 1 if f.dim() == 1 else f.shape[1]
+        b = self._dev((nrhs, self.n_dof))
+        load(self.h, f, nrhs, b, self.stream)
+        return b[0] if nrhs == 1 else b.T
+
+    def _as_nodal(self, f):
+        t = self._torch
+        if isinstance(f, np.ndarray):
+            f = t.from_numpy(np.ascontiguousarray(f, dtype=np.float64))
+        if f.dim() == 2:
+            f = f.T.contiguous()   # column-major [n_nodes][nrhs] = row-major [nrhs][n_nodes]
+        return f.contiguous()
+
+    def solve(self, f, tol=1e-12, max_iter=50):
+        """u = A^{-1} M f; f nodal [n_nodes] or [n_nodes, nrhs] (host or device)."""
+        f = self._as_nodal(f)
+        nrhs = 1 if f.dim() == 1 else f.shape[0]
+        u = self._dev((nrhs, self.n_dof))
+        self.iters, self.resid = solve(self.h, f, nrhs, u, tol, max_iter, self.stream)
+        return u[0] if nrhs == 1 else u.T
+
+    def adjoint(self, u, u_obs, tol=1e-12, max_iter=50):
+        dJdf = self._dev((self.n_nodes,))
+        dK = adjoint(self.h, u.contiguous(), u_obs.contiguous(), dJdf, tol, max_iter, self.stream)
+        return dK, dJdf
+
+    def paths(self, axis, direction, gps, cap=None):
+        t = self._torch
+        gps = t.as_tensor(gps, dtype=t.int64, device="cuda").contiguous()
+        cap = cap or int(8 * round(self.n_tets ** (1 / 3))) + 64
+        n = gps.shape[0]
+        tet = t.full((n, cap), -1, dtype=t.int32, device="cuda")
+        r0 = t.zeros((n, cap), dtype=t.float64, device="cuda")
+        r1 = t.zeros((n, cap), dtype=t.float64, device="cuda")
+        ns = t.zeros((n,), dtype=t.int32, device="cuda")
+        paths(self.h, axis, direction, gps, cap, tet, r0, r1, ns, self.stream)
+        return tet, r0, r1, ns
+
+    def table_rows(self, axis, direction, gps):
+        t = self._torch
+        gps = t.as_tensor(gps, dtype=t.int64, device="cuda").contiguous()
+        rows = self._dev((gps.shape[0], self.n_dof))
+        table_rows(self.h, axis, direction, gps, rows, self.stream)
+        return rows
+
+    def sync(self):
+        sync(self.h, self.stream)
+
+    def stage_ms(self):
+        return stage_ms(self.h)
+
+    def counters(self):
+        return counters(self.h)
+
+    def free(self):
+        if getattr(self, "h", None):
+            mesh_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

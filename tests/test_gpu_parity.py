@@ -1,0 +1,234 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: path tet ids bit-exact; path ends and FP64 tables within 1e-10 relative; FP64
+matrix and solution within 1e-10; mixed (FP32 contraction and factor + FP64 refinement)
+matrix within 1e-4 and solution within 1e-8 of the oracle's FP64 solution.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_03339_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1811_03339_gb300 import fem3  # noqa: E402
+
+AFF = ((1.0, 0.3, 0.0), (0.0, 1.0, 0.2), (0.0, 0.0, 0.7))
+_CACHE = {}
+
+
+def _case(name):
+    """(mesh, oracle, alpha, K) for a named small case."""
+    if name in _CACHE:
+        return _CACHE[name]
+    specs = {
+        "cube4": (4, 0.0, 0, None, (1.5, 1.5, 1.5), (1.0, 1.0, 1.0)),
+        "cube3_jitter": (3, 0.2, 5, None, (1.3, 1.6, 1.8), (1.0, 2.0, 0.5)),
+        "cube7_jitter": (7, 0.2, 1, None, (1.3, 1.6, 1.8), (1.0, 2.0, 0.5)),
+        "ppd5": (5, 0.15, 2, AFF, (1.2, 1.5, 1.9), (1.0, 1.0, 1.0)),
+        "cube16_jitter": (16, 0.2, 1, None, (1.3, 1.6, 1.8), (1.0, 2.0, 0.5)),
+    }
+    n, jit, seed, aff, alpha, K = specs[name]
+    mesh = inputs.cube_mesh(n, jit, seed, aff)
+    _CACHE[name] = (mesh, oracle.Oracle.from_mesh(mesh), alpha, K)
+    return _CACHE[name]
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("name", ["cube4", "cube3_jitter", "ppd5"])
+def test_mesh_records(name):
+    mesh, o, _, _ = _case(name)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    assert m.n_dof == o.n_dof and m.n_gp == o.n_gp
+    assert np.array_equal(m.dof_of_node, o.dof)
+    m.free()
+
+
+@pytest.mark.parametrize("name", ["cube4", "cube3_jitter", "ppd5", "cube7_jitter"])
+def test_paths_bit_exact(name):
+    mesh, o, _, _ = _case(name)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    rng = np.random.default_rng(0)
+    gps = np.arange(o.n_gp) if o.n_gp <= 1536 else np.sort(rng.choice(o.n_gp, 1500, replace=False))
+    for axis in range(3):
+        for d in (-1, 1):
+            tet, r0, r1, ns = m.paths(axis, d, gps)
+            tet, r0, r1, ns = tet.cpu().numpy(), r0.cpu().numpy(), r1.cpu().numpy(), ns.cpu().numpy()
+            for l, g in enumerate(gps):
+                st, a, b, _, _ = o.walk(int(g), axis, d)
+                assert ns[l] == len(st), (g, axis, d)
+                assert np.array_equal(tet[l, :ns[l]], st), (g, axis, d)
+                assert np.abs(r0[l, :ns[l]] - a).max(initial=0) <= 1e-12 * o.span
+                assert np.abs(r1[l, :ns[l]] - b).max(initial=0) <= 1e-12 * o.span
+    m.free()
+
+
+@pytest.mark.parametrize("name", ["cube4", "cube3_jitter", "ppd5", "cube7_jitter"])
+def test_tables_fp64(name):
+    mesh, o, alpha, K = _case(name)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    m.assemble(alpha, K, "fp64")
+    m.sync()
+    rng = np.random.default_rng(1)
+    gps = np.sort(rng.choice(o.n_gp, min(o.n_gp, 300), replace=False))
+    for axis in range(3):
+        gamma = alpha[axis] / 2
+        L, R = o.tables(axis, gamma, gps)
+        gl = m.table_rows(axis, -1, gps).cpu().numpy()
+        gr = m.table_rows(axis, +1, gps).cpu().numpy()
+        assert _rel(gl, L) <= 1e-10
+        assert _rel(gr, R) <= 1e-10
+        # structural: the same nonzero support (exact zeros outside the path's dofs)
+        assert np.array_equal(gl != 0, L != 0)
+    m.free()
+
+
+@pytest.mark.parametrize("name", ["cube4", "cube3_jitter", "ppd5", "cube7_jitter"])
+def test_assemble_and_solve_fp64(name):
+    mesh, o, alpha, K = _case(name)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    A = m.assemble(alpha, K, "fp64", return_matrix=True).cpu().numpy()
+    A_ref = o.assemble(alpha, K)
+    assert _rel(A, A_ref) <= 1e-10
+    f = inputs.nodal_source(mesh, alpha, K) if mesh.affine is None else np.ones(mesh.n_nodes)
+    u = m.solve(f).cpu().numpy()
+    u_ref = oracle.solve(A_ref, o.load(f))
+    assert np.linalg.norm(u - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
+    assert m.resid <= 1e-12
+    m.free()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("name", ["cube4", "cube7_jitter", "ppd5"])
+def test_mixed_with_refinement(name, precision):
+    mesh, o, alpha, K = _case(name)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    A = m.assemble(alpha, K, precision, return_matrix=True).cpu().numpy()
+    A_ref = o.assemble(alpha, K)
+    assert _rel(A, A_ref) <= 1e-4
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((mesh.n_nodes, 3))
+    u = m.solve(f, tol=1e-13).cpu().numpy()
+    u_ref = oracle.solve(A_ref, o.load(f))
+    assert np.linalg.norm(u - u_ref) <= 1e-8 * np.linalg.norm(u_ref)
+    assert m.iters >= 1 and m.resid <= 1e-13
+    m.free()
+
+
+def test_load_vector():
+    mesh, o, alpha, K = _case("cube3_jitter")
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    f = np.random.default_rng(4).standard_normal((mesh.n_nodes, 2))
+    b = m.load(f).cpu().numpy()
+    assert _rel(b, o.load(f)) <= 1e-13
+    m.free()
+
+
+def test_full_size_cube16_fp64_matrix():
+    """16^3 jittered cube (24,576 tets, 3,375 dofs): whole matrix and solution."""
+    mesh, o, alpha, K = _case("cube16_jitter")
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    A = m.assemble(alpha, K, "fp64", return_matrix=True).cpu().numpy()
+    A_ref = o.assemble(alpha, K)
+    assert _rel(A, A_ref) <= 1e-10
+    f = inputs.nodal_source(mesh, alpha, K)
+    u = m.solve(f).cpu().numpy()
+    u_ref = oracle.solve(A_ref, o.load(f))
+    assert np.linalg.norm(u - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
+    # mixed form reaches the FP64 solution to 1e-8
+    m.assemble(alpha, K, "tf32x3")
+    u2 = m.solve(f, tol=1e-13).cpu().numpy()
+    assert np.linalg.norm(u2 - u_ref) <= 1e-8 * np.linalg.norm(u_ref)
+    m.free()
+
+
+def test_full_size_parallelepiped24_sampled():
+    """24^3 parallelepiped (82,944 tets, 12,167 dofs): sampled paths and table rows
+    against the oracle, chord ends in closed form, symmetry and residual at full size."""
+    w = inputs.PARALLELEPIPED24
+    mesh = inputs.workload_mesh("parallelepiped24")
+    o = oracle.Oracle.from_mesh(mesh)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    alpha, K = w["alpha"], w["K"]
+    A = m.assemble(alpha, K, "tf32x3", return_matrix=True)
+    m.sync()
+    rng = np.random.default_rng(7)
+    gps = np.sort(rng.choice(o.n_gp, 200, replace=False))
+    for axis in range(3):
+        tet, _, r1, ns = m.paths(axis, -1, gps)
+        tet, ns = tet.cpu().numpy(), ns.cpu().numpy()
+        for l, g in enumerate(gps[:60]):
+            st, _, _, _, _ = o.walk(int(g), axis, -1)
+            assert np.array_equal(tet[l, :ns[l]], st)
+        L, R = o.tables(axis, alpha[axis] / 2, gps[:50])
+        assert _rel(m.table_rows(axis, -1, gps[:50]).cpu().numpy(), L) <= 1e-10
+        assert _rel(m.table_rows(axis, +1, gps[:50]).cpu().numpy(), R) <= 1e-10
+    idx = rng.integers(0, o.n_dof, size=(2000, 2))
+    a = A[idx[:, 0], idx[:, 1]].cpu().numpy()
+    at = A[idx[:, 1], idx[:, 0]].cpu().numpy()
+    assert np.abs(a - at).max() <= 1e-5 * float(A.abs().max())
+    u = m.solve(np.ones(mesh.n_nodes), tol=1e-12)
+    assert m.resid <= 1e-12
+    m.free()
+
+
+def test_status_codes():
+    mesh, o, alpha, K = _case("cube4")
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    with pytest.raises(fem3.Fem3Error) as e:
+        m.solve(np.ones(mesh.n_nodes))
+    assert e.value.code == fem3.FEM3_E_STATE
+    with pytest.raises(fem3.Fem3Error) as e:
+        m.assemble((0.9, 1.5, 1.5), K)
+    assert e.value.code == fem3.FEM3_E_ARG
+    with pytest.raises(fem3.Fem3Error) as e:
+        m.assemble(alpha, (1.0, -1.0, 1.0))
+    assert e.value.code == fem3.FEM3_E_ARG
+    m.free()
+    # a walk cap of 2 tets cannot reach the boundary: error status, no hang
+    m = fem3.Mesh(mesh.verts, mesh.tets, max_steps=2)
+    m.assemble(alpha, K)
+    with pytest.raises(fem3.Fem3Error) as e:
+        m.sync()
+    assert e.value.code == fem3.FEM3_E_WALK
+    m.free()
+    # zero-volume tet
+    bad = mesh.tets.copy()
+    bad[0, 3] = bad[0, 2]
+    with pytest.raises(fem3.Fem3Error) as e:
+        fem3.Mesh(mesh.verts, bad)
+    assert e.value.code == fem3.FEM3_E_MESH
+    # a face shared by three tets
+    dup = np.vstack([mesh.tets, mesh.tets[:1]])
+    with pytest.raises(fem3.Fem3Error) as e:
+        fem3.Mesh(mesh.verts, dup)
+    assert e.value.code == fem3.FEM3_E_MESH
+
+
+def test_no_interior_dofs():
+    """One cell: every vertex is on the boundary, n_dof = 0."""
+    mesh = inputs.cube_mesh(1)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    assert m.n_dof == 0
+    m.assemble((1.5, 1.5, 1.5), (1.0, 1.0, 1.0), "fp64")
+    m.sync()
+    m.free()
+
+
+def test_device_inputs_match_host_inputs():
+    mesh, o, alpha, K = _case("cube3_jitter")
+    mh = fem3.Mesh(mesh.verts, mesh.tets)
+    md = fem3.Mesh(torch.from_numpy(mesh.verts).cuda(), torch.from_numpy(mesh.tets).cuda())
+    Ah = mh.assemble(alpha, K, "fp64", return_matrix=True)
+    Ad = md.assemble(alpha, K, "fp64", return_matrix=True)
+    assert _rel(Ad.cpu().numpy(), Ah.cpu().numpy()) <= 1e-14
+    mh.free()
+    md.free()
