@@ -240,6 +240,7 @@ def run_ours(args):
     stages = m.stage_ms()
     m.sync()
     cnt = m.counters()
+    ir_iters, ir_resid = m.iters, m.resid
     m.free()
     m64, u64 = step("fp64", profile=True, keep=True)
     stages64 = m64.stage_ms()
@@ -291,18 +292,9 @@ def run_ours(args):
     h2d = mesh.verts.nbytes + mesh.tets.nbytes + f_host.nbytes
     d2h = 8 * n_dof
 
-    # --- kernel launches per step (CUPTI via torch.profiler, outside the timed region)
-    launches = None
-    try:
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            step(args.precision)
-            torch.cuda.synchronize()
-        launches = sum(1 for e in prof.events()
-                       if e.device_type.name == "CUDA" and not e.name.lower().startswith("memcpy")
-                       and not e.name.lower().startswith("memset")) * args.steps
-    except Exception:
-        launches = None
+    # --- kernel launches per step: counted by the library at every launch ------------
+    launches = cnt["launches"] * args.steps
+    launch_note = f"{cnt['launches']} libfem3 kernel launches per step (library counter)"
 
     line = None
     if rank == 0:
@@ -325,6 +317,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches,
+            "gpu_launches_note": launch_note,
             "roofline": roofline,
             "cpu_baseline": base,
             "clocks": clk.summary(),
@@ -337,6 +330,8 @@ def run_ours(args):
                                         "factor", "solve_refine"],
                                        [round(x, 4) for x in stages64])),
             "segments_per_step": cnt["segments"],
+            "refinement": {"iterations": ir_iters, "final_rel_residual": ir_resid},
+            "table_bytes": cnt["table_bytes"],
             "contraction": {"bin_dense_gflop": ctr_flops / 1e9,
                             "gflops": ctr_flops / (stages[3] * 1e-3) / 1e9 if stages[3] > 0 else None},
             "peaks_source": src,

@@ -187,10 +187,12 @@ int fem3_sync(fem3_mesh m, void *stream);
  * 4 load vector, 5 factorisation, 6 triangular solves + refinement. */
 int fem3_stage_ms(fem3_mesh m, int stage, float *ms);
 
-/* Counters of the last assemble: total segments walked (all axes, both sides) and
- * algorithmic contraction flops (sum over bins of 2 * D_b^2 * G_b per product). */
+/* Counters: segments walked by the last assemble (all axes, both sides; read by
+ * fem3_sync), flops of its contraction counted on the dense bin blocks (sum over bins of
+ * 2 * D_b^2 * G_b), bytes of the FP64 tables, and the number of kernels this handle has
+ * launched since upload.  Any output pointer may be NULL. */
 int fem3_counters(fem3_mesh m, int64_t *segments, double *contract_flops,
-                  int64_t *table_bytes);
+                  int64_t *table_bytes, int64_t *launches);
 
 /* Text of the last error of the calling thread. */
 int fem3_last_error(char *buf, size_t len);

@@ -88,6 +88,10 @@ static int check_errors(Mesh *m) {
                          "non-positive pivot in Cholesky at column " + std::to_string(col));
     }
     if (e[ERR_MESH] || e[ERR_FACE]) return set_error(FEM3_E_MESH, "mesh error");
+    if (e[ERR_SOLVE])
+        return set_error(FEM3_E_CUDA, "a triangular-solve wait gave up (bounded wait expired)");
+    if (e[ERR_TC])
+        return set_error(FEM3_E_CUDA, "a tensor-core contraction wait gave up (bounded wait expired)");
     return FEM3_OK;
 }
 
@@ -192,8 +196,12 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
     if ((st = bins_build(m)) != FEM3_OK) return fail(st);
     stage_end(m, 1);
     const int64_t n = std::max<int64_t>(1, m->n_dof);
-    for (int k = 0; k < 6; k++)
-        if ((st = dev_alloc_t(m, &m->vec64[k], std::max<int64_t>(n, m->n_nodes))) != FEM3_OK)
+    if ((st = dev_alloc_t(m, &m->flags, (n + 63) / 64 + 1)) != FEM3_OK) return fail(st);
+    if (cudaMemsetAsync(m->flags, 0, sizeof(int32_t) * ((n + 63) / 64 + 1), m->stream) != cudaSuccess)
+        return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
+    for (int k = 0; k < 6; k++)   // vec64[5] doubles as the 64x64 Cholesky scratch
+        if ((st = dev_alloc_t(m, &m->vec64[k], std::max<int64_t>(std::max<int64_t>(n, m->n_nodes),
+                                                                 64 * 64))) != FEM3_OK)
             return fail(st);
     for (int k = 0; k < 2; k++)
         if ((st = dev_alloc_t(m, &m->vec32[k], n)) != FEM3_OK) return fail(st);
@@ -240,7 +248,10 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
     m->factored = false;
     FEM3_TRY(walk_tables(m, alpha));
     stage_begin(m, 3);
-    FEM3_TRY(contract(m, precision == FEM3_FP64 ? FEM3_FP64 : FEM3_FP32));
+    if (precision == FEM3_TF32X3)
+        FEM3_TRY(contract_tc(m));
+    else
+        FEM3_TRY(contract(m, precision));
     stage_end(m, 3);
     if (A_out) {
         if (precision == FEM3_FP64) {
@@ -248,6 +259,7 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
                                       cudaMemcpyDeviceToDevice, m->stream));
         } else {
             FEM3_TRY(f32_to_f64(m->A32, A_out, n * n, m->stream));
+            note_launch(m);
         }
     }
     return FEM3_OK;
@@ -330,6 +342,7 @@ int fem3_adjoint(fem3_mesh h, const double *u, const double *u_obs, double tol, 
     const int64_t n = m->n_dof;
     double *res = m->vec64[2], *lam = m->vec64[3];
     FEM3_TRY(sub_vec(u, u_obs, res, n, m->stream));
+    note_launch(m);
     if (m->precision == FEM3_FP64) {
         FEM3_TRY(solve_direct(m, res, 1, lam));
     } else {
@@ -385,9 +398,11 @@ int fem3_stage_ms(fem3_mesh h, int stage, float *ms) {
     return FEM3_OK;
 }
 
-int fem3_counters(fem3_mesh h, int64_t *segments, double *contract_flops, int64_t *table_bytes) {
+int fem3_counters(fem3_mesh h, int64_t *segments, double *contract_flops, int64_t *table_bytes,
+                  int64_t *launches) {
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m) return set_error(FEM3_E_ARG, "null mesh");
+    if (launches) *launches = m->launches;
     if (segments) *segments = m->segments;
     if (contract_flops) *contract_flops = m->contract_flops;
     if (table_bytes) {

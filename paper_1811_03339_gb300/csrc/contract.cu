@@ -121,6 +121,7 @@ int contract(Mesh *m, int precision) {
             k_contract_simt<float><<<B.n_work, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.work, B.gp_off, B.gp_idx, B.dof_off, B.dof_idx,
                 B.tab_off, B.tab_ld, m->gw, m->sK[axis], m->A32, n);
+        note_launch(m);
     }
     m->contract_flops = flops;
     FEM3_CUDA(cudaGetLastError());

@@ -1,0 +1,376 @@
+// Tensor-core contraction X_b = L_b^T W R_b (TF32 x 3 split products, FP32 accumulate)
+// on sm_103a: TMA loads with 128-byte swizzle, tcgen05.mma issued by one thread, the
+// accumulator in tensor memory, tcgen05.ld epilogue adding s K (X + X^T) into the FP32
+// matrix.  Section 2.1 element sum restricted, bin by bin, to the Section 2.3 template.
+//
+// Operands.  The FP64 tables of one axis are split into TF32 pairs v = hi + lo (each
+// rounded to TF32, cvt.rna) with the Gauss weights folded into R; they are stored as
+// four row-major FP32 arrays [n_tmpl rows][Kp] where row dof_off[b] + c is local dof c
+// of bin b and column k its k-th Gauss point (zero for k >= G_b).  The product
+//   X = Lhi Rhi^T + Lhi Rlo^T + Llo Rhi^T
+// drops only lo*lo (relative 2^-22).
+//
+// Tiles.  One CTA computes the 128 x N block (N <= 256) of X for rows
+// [128 mt, 128 mt + 128) and columns [256 nt, 256 nt + N) of one bin.  K steps of
+// 32 Gauss points (128 bytes: one swizzle row) go through a 2-stage TMA pipeline.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fem3_impl.cuh"
+
+namespace fem3 {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 256, kBK = 32, kStages = 2;
+constexpr uint32_t kTileA = kBM * kBK * 4;     // 16 KB
+constexpr uint32_t kTileB = kBN * kBK * 4;     // 32 KB
+constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;   // 96 KB
+constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kWaitLimit = 1 << 22;
+
+// ------------------------------- PTX helpers -------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false after kWaitLimit polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int i = 0; i < kWaitLimit; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// K-major operand, 128-byte swizzle: rows 128 B apart, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                            // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset
+    d |= (uint64_t)1 << 46;                            // descriptor version (sm_100 family)
+    d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+    return d;
+}
+// kind::tf32 instruction descriptor: FP32 accumulate, TF32 A/B, both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// ------------------------------- split kernel ------------------------------------
+__global__ void k_split_tf32(const double *__restrict__ tabL, const double *__restrict__ tabR,
+                             const int32_t *__restrict__ row_bin,
+                             const int32_t *__restrict__ dof_off, const int32_t *__restrict__ gp_off,
+                             const int32_t *__restrict__ gp_idx, const int64_t *__restrict__ tab_off,
+                             const int32_t *__restrict__ tab_ld, const double *__restrict__ gw,
+                             int64_t n_rows, int Kp, float *Lhi, float *Llo, float *Rhi, float *Rlo) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n_rows * Kp) return;
+    int64_t row = e / Kp;
+    int k = (int)(e % Kp);
+    int b = row_bin[row];
+    int c = (int)(row - dof_off[b]);
+    int G = gp_off[b + 1] - gp_off[b];
+    float lh = 0.f, ll = 0.f, rh = 0.f, rl = 0.f;
+    if (k < G) {
+        int64_t idx = tab_off[b] + (int64_t)c * tab_ld[b] + k;
+        double l = tabL[idx];
+        double r = tabR[idx] * gw[gp_idx[gp_off[b] + k]];
+        lh = tf32_rna((float)l);
+        ll = tf32_rna((float)(l - (double)lh));
+        rh = tf32_rna((float)r);
+        rl = tf32_rna((float)(r - (double)rh));
+    }
+    Lhi[e] = lh; Llo[e] = ll; Rhi[e] = rh; Rlo[e] = rl;
+}
+
+__global__ void k_row_bin(const int32_t *__restrict__ dof_off, int n_bins, int32_t *row_bin) {
+    int b = blockIdx.x;
+    if (b >= n_bins) return;
+    for (int r = dof_off[b] + threadIdx.x; r < dof_off[b + 1]; r += blockDim.x) row_bin[r] = b;
+}
+
+// ------------------------------- GEMM kernel --------------------------------------
+struct TcWork {
+    int bin, mt, nt, pad;
+};
+
+__global__ void __launch_bounds__(128, 1) k_contract_tc(
+    const __grid_constant__ CUtensorMap mLhi, const __grid_constant__ CUtensorMap mLlo,
+    const __grid_constant__ CUtensorMap mRhi, const __grid_constant__ CUtensorMap mRlo,
+    const int4 *__restrict__ work, const int32_t *__restrict__ dof_off,
+    const int32_t *__restrict__ dof_idx, const int32_t *__restrict__ gp_off, float sK, float *A,
+    int64_t n_dof, int32_t *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned tile area (swizzle atoms), barriers after it
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + kStages * kStageBytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 1);
+    __shared__ int s_fail;
+
+    const int4 wk = work[blockIdx.x];
+    const int bin = wk.x, mt = wk.y, nt = wk.z;
+    const int row0 = dof_off[bin];
+    const int D = dof_off[bin + 1] - row0;
+    const int G = gp_off[bin + 1] - gp_off[bin];
+    const int nvalid = min(kBN, D - nt * kBN);          // columns of this tile
+    const int N = (nvalid + 15) & ~15;                  // MMA N: multiple of 16, <= 256
+    const int nk = (G + kBK - 1) / kBK;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const uint32_t full0 = smem_u32(&bars[0]);          // full[s]  = bars[s]
+    const uint32_t empty0 = smem_u32(&bars[kStages]);   // empty[s] = bars[kStages + s]
+    const uint32_t done = smem_u32(&bars[2 * kStages]);
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0 && nk > 0) {
+        // producer: TMA loads into the stage ring
+        for (int k = 0; k < nk; k++) {
+            const int s = k % kStages;
+            if (k >= kStages) {
+                if (!mbar_wait(empty0 + 8 * s, ((k / kStages) - 1) & 1)) { s_fail = 1; break; }
+            }
+            uint8_t *st = base + s * kStageBytes;
+            const uint32_t bar = full0 + 8 * s;
+            const int nbox = N > kBN / 2 ? 2 : 1;          // 128-row boxes of each B operand
+            mbar_expect_tx(bar, 2 * kTileA + 2 * nbox * (kTileB / 2));
+            const int x = k * kBK;
+            const int ya = row0 + mt * kBM, yb = row0 + nt * kBN;
+            tma_load_2d(smem_u32(st), &mLhi, x, ya, bar);
+            tma_load_2d(smem_u32(st + kTileA), &mLlo, x, ya, bar);
+            for (int h = 0; h < nbox; h++) {
+                tma_load_2d(smem_u32(st + 2 * kTileA + h * (kTileB / 2)), &mRhi, x, yb + h * (kBN / 2), bar);
+                tma_load_2d(smem_u32(st + 2 * kTileA + kTileB + h * (kTileB / 2)), &mRlo, x,
+                            yb + h * (kBN / 2), bar);
+            }
+        }
+    } else if (warp == 1 && lane == 0 && nk > 0) {
+        // MMA issuer
+        const uint32_t idesc = idesc_tf32(kBM, N);
+        for (int k = 0; k < nk; k++) {
+            const int s = k % kStages;
+            if (!mbar_wait(full0 + 8 * s, (k / kStages) & 1)) { s_fail = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t st = smem_u32(base + s * kStageBytes);
+            const uint32_t aH = st, aL = st + kTileA, bH = st + 2 * kTileA, bL = st + 2 * kTileA + kTileB;
+#pragma unroll
+            for (int ks = 0; ks < kBK / 8; ks++) {      // 8 TF32 = 32 bytes per MMA K step
+                const uint32_t off = ks * 32;
+                const uint32_t acc = (k > 0 || ks > 0) ? 1u : 0u;
+                umma_tf32(tmem, umma_desc_sw128(aH + off), umma_desc_sw128(bH + off), idesc, acc);
+                umma_tf32(tmem, umma_desc_sw128(aH + off), umma_desc_sw128(bL + off), idesc, 1u);
+                umma_tf32(tmem, umma_desc_sw128(aL + off), umma_desc_sw128(bH + off), idesc, 1u);
+            }
+            umma_commit(empty0 + 8 * s);   // frees the stage when these MMAs finish
+        }
+        umma_commit(done);
+    }
+    __syncthreads();
+    // epilogue: every warp waits for the accumulator
+    bool ok = (nk > 0) && mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok || s_fail) {
+        if (threadIdx.x == 0 && nk > 0) atomicAdd(&err[ERR_TC], 1);
+    } else {
+        const int c1 = mt * kBM + warp * 32 + lane;     // local row (dof) of this thread
+        const bool row_ok = c1 < D;
+        const int64_t j1 = row_ok ? dof_idx[row0 + c1] : 0;
+        for (int cb = 0; cb < N; cb += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, v);
+            if (!row_ok) continue;
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                const int c2 = nt * kBN + cb + q;
+                if (cb + q >= nvalid) break;
+                const int64_t j2 = dof_idx[row0 + c2];
+                const float x = sK * v[q];
+                atomicAdd(&A[j1 * n_dof + j2], x);
+                atomicAdd(&A[j2 * n_dof + j1], x);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+}
+
+// ------------------------------- host side ----------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+int make_map(CUtensorMap *map, float *base, int64_t rows, int Kp) {
+    auto enc = get_encode();
+    if (!enc) return set_error(FEM3_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FEM3_E_CUDA, "cuTensorMapEncodeTiled failed");
+    return FEM3_OK;
+}
+
+}  // namespace
+
+// Build the per-axis operand buffers and work lists once per mesh.
+static int tc_prepare(Mesh *m) {
+    if (m->tc_ready) return FEM3_OK;
+    cudaStream_t s = m->stream;
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        int maxG = 0;
+        for (int b = 0; b < B.n_bins; b++) maxG = std::max(maxG, B.h_gp_off[b + 1] - B.h_gp_off[b]);
+        B.tc_Kp = std::max(kBK, (maxG + kBK - 1) / kBK * kBK);
+        const int64_t rows = std::max<int64_t>(1, B.n_tmpl);
+        for (int q = 0; q < 4; q++)
+            FEM3_TRY(dev_alloc_t(m, &B.tc_op[q], rows * B.tc_Kp));
+        FEM3_TRY(dev_alloc_t(m, &B.row_bin, rows));
+        if (B.n_tmpl > 0) {
+            k_row_bin<<<B.n_bins, 256, 0, s>>>(B.dof_off, B.n_bins, B.row_bin);
+            note_launch(m);
+        }
+        std::vector<int4> work;
+        for (int b = 0; b < B.n_bins; b++) {
+            int D = B.h_dof_off[b + 1] - B.h_dof_off[b];
+            int G = B.h_gp_off[b + 1] - B.h_gp_off[b];
+            if (D == 0 || G == 0) continue;
+            for (int mt = 0; mt * kBM < D; mt++)
+                for (int nt = 0; nt * kBN < D; nt++) work.push_back(make_int4(b, mt, nt, 0));
+        }
+        B.tc_n_work = (int)work.size();
+        FEM3_TRY(dev_alloc_t(m, &B.tc_work, std::max(1, B.tc_n_work)));
+        if (B.tc_n_work)
+            FEM3_CUDA(cudaMemcpyAsync(B.tc_work, work.data(), sizeof(int4) * work.size(),
+                                      cudaMemcpyHostToDevice, s));
+        FEM3_CUDA(cudaStreamSynchronize(s));   // `work` is a host temporary
+    }
+    FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kSmemBytes));
+    m->tc_ready = true;
+    return FEM3_OK;
+}
+
+int contract_tc(Mesh *m) {
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n_dof;
+    FEM3_TRY(tc_prepare(m));
+    FEM3_CUDA(cudaMemsetAsync(m->A32, 0, sizeof(float) * n * n, s));
+    double flops = 0;
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        for (int b = 0; b < B.n_bins; b++) {
+            double D = B.h_dof_off[b + 1] - B.h_dof_off[b];
+            double G = B.h_gp_off[b + 1] - B.h_gp_off[b];
+            flops += 2.0 * D * D * G;
+        }
+        if (!B.tc_n_work) continue;
+        const int64_t elems = B.n_tmpl * (int64_t)B.tc_Kp;
+        k_split_tf32<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(
+            m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.gp_idx, B.tab_off,
+            B.tab_ld, m->gw, B.n_tmpl, B.tc_Kp, B.tc_op[0], B.tc_op[1], B.tc_op[2], B.tc_op[3]);
+        note_launch(m);
+        CUtensorMap maps[4];
+        for (int q = 0; q < 4; q++) FEM3_TRY(make_map(&maps[q], B.tc_op[q], B.n_tmpl, B.tc_Kp));
+        k_contract_tc<<<B.tc_n_work, 128, kSmemBytes, s>>>(
+            maps[0], maps[1], maps[2], maps[3], B.tc_work, B.dof_off, B.dof_idx, B.gp_off,
+            (float)m->sK[axis], m->A32, n, m->err);
+        note_launch(m);
+    }
+    m->contract_flops = flops;
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+}  // namespace fem3

@@ -36,6 +36,8 @@ enum ErrWord {
     ERR_NOT_SPD = 2,   // 1 + first column with a non-positive pivot (0: none)
     ERR_MESH = 3,      // number of degenerate tets
     ERR_FACE = 4,      // non-manifold faces or hash overflow
+    ERR_SOLVE = 5,     // a triangular-solve wait gave up (bounded spin)
+    ERR_TC = 6,        // a tensor-core contraction pipeline wait gave up
     ERR_COUNT = 8
 };
 
@@ -66,6 +68,12 @@ struct AxisBins {
     int max_dof = 0, max_gp = 0;
     int4 *work = nullptr;        // contraction work items (bin, t1, t2, 0)
     int n_work = 0;
+    // tensor-core contraction operands: TF32 hi/lo of L and of W R, [n_tmpl][tc_Kp]
+    float *tc_op[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t *row_bin = nullptr;  // [n_tmpl] template row -> bin
+    int tc_Kp = 0;
+    int4 *tc_work = nullptr;     // (bin, m-tile, n-tile, 0)
+    int tc_n_work = 0;
     std::vector<int32_t> h_gp_off, h_dof_off;
     std::vector<int64_t> h_tab_off;
     std::vector<int32_t> h_tab_ld;
@@ -108,14 +116,18 @@ struct Mesh {
     double *A64 = nullptr;     // [n_dof][n_dof]
     float *A32 = nullptr;      // [n_dof][n_dof]
     bool factored = false;
+    bool tc_ready = false;
 
     // workspaces
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     float *vec32[2] = {nullptr, nullptr};
+    int32_t *flags = nullptr;  // wavefront triangular-solve flags (one per 64-row block)
+    int flag_epoch = 0;        // value that marks "ready" in the current solve
     double *norms = nullptr;   // device scratch for reductions
     double *h_norms = nullptr; // pinned host mirror
 
     // counters
+    int64_t launches = 0;      // kernels this handle has launched
     int64_t segments = 0;
     double contract_flops = 0;
 
@@ -126,6 +138,8 @@ struct Mesh {
 
     std::vector<void *> allocs;
 };
+
+inline void note_launch(Mesh *m) { m->launches++; }
 
 // device memory owned by a mesh (stream-ordered pool allocations)
 int dev_alloc(Mesh *m, void **p, size_t bytes);
@@ -154,6 +168,7 @@ int walk_paths(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, int ca
                int32_t *tet_out, double *r0, double *r1, int32_t *nseg);
 int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double *rows);
 int contract(Mesh *m, int precision);
+int contract_tc(Mesh *m);
 int load_vector(Mesh *m, const double *f_d, int nrhs, double *b_d);
 int load_vector_T(Mesh *m, const double *lam_d, double *out_d);
 int factor(Mesh *m);

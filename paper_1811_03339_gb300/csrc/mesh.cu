@@ -440,8 +440,11 @@ int scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, Mesh *m
     int32_t *bsum = nullptr;
     FEM3_TRY(dev_alloc_t(m, &bsum, nb));
     k_scan_blocks<<<(unsigned)nb, kScanBlock, 0, s>>>(in, out, n, bsum);
+    note_launch(m);
     k_scan_sums<<<1, kScanBlock, 0, s>>>(bsum, nb, out + n);
+    note_launch(m);
     k_scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(out, n, bsum);
+    note_launch(m);
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
@@ -466,9 +469,12 @@ int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
 
     unsigned long long *box = reinterpret_cast<unsigned long long *>(m->node_box);
     k_box_init<<<grid_for(6 * N), kThreads, 0, s>>>(box, N);
+    note_launch(m);
     k_tet_geom<<<grid_for(T), kThreads, 0, s>>>(verts_d, tets_d, T, N, qa, qb, m->M, m->inv,
                                                  m->vol, m->gp, m->gw, box, m->err);
+    note_launch(m);
     k_box_decode<<<grid_for(6 * N), kThreads, 0, s>>>(box, 6 * N);
+    note_launch(m);
 
     // face hash: load factor <= 1/4 of 4T face slots
     int bits = 4;
@@ -479,10 +485,13 @@ int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
     FEM3_TRY(dev_alloc_t(m, &keys, H));
     FEM3_TRY(dev_alloc_t(m, &vals, 2 * H));
     k_fill_u64<<<grid_for(H), kThreads, 0, s>>>(keys, H, kEmptyKey);
+    note_launch(m);
     FEM3_CUDA(cudaMemsetAsync(vals, 0xff, sizeof(int32_t) * 2 * H, s));
     k_face_insert<<<grid_for(4 * T), kThreads, 0, s>>>(tets_d, T, keys, vals, bits, m->err);
+    note_launch(m);
     k_face_match<<<grid_for(4 * T), kThreads, 0, s>>>(tets_d, T, keys, vals, bits, m->nbr,
                                                        m->err);
+    note_launch(m);
 
     // boundary vertices, dof numbering, vertex -> tets
     int32_t *used, *bnd, *flag, *off, *vcount, *cursor;
@@ -497,18 +506,23 @@ int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
     FEM3_CUDA(cudaMemsetAsync(vcount, 0, sizeof(int32_t) * N, s));
     FEM3_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * N, s));
     k_mark_nodes<<<grid_for(4 * T), kThreads, 0, s>>>(tets_d, m->nbr, T, N, used, bnd, vcount);
+    note_launch(m);
     k_interior_flag<<<grid_for(N), kThreads, 0, s>>>(used, bnd, N, flag);
+    note_launch(m);
     FEM3_TRY(scan_i32(flag, off, N, s, m));
     FEM3_TRY(scan_i32(vcount, m->vt_off, N, s, m));
     k_vt_fill<<<grid_for(4 * T), kThreads, 0, s>>>(tets_d, T, N, m->vt_off, cursor, m->vt_tet);
+    note_launch(m);
 
     unsigned long long *ext = nullptr;
     double *vsum = nullptr;
     FEM3_TRY(dev_alloc_t(m, &ext, 6));
     FEM3_TRY(dev_alloc_t(m, &vsum, 1));
     k_box_init<<<1, 32, 0, s>>>(ext, 1);
+    note_launch(m);
     FEM3_CUDA(cudaMemsetAsync(vsum, 0, sizeof(double), s));
     k_extent<<<grid_for(std::max(N, T)), kThreads, 0, s>>>(verts_d, N, m->vol, T, ext, vsum);
+    note_launch(m);
 
     int32_t n_dof = 0;
     unsigned long long h_ext[6];
@@ -534,6 +548,7 @@ int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
     m->n_dof = n_dof;
     FEM3_TRY(dev_alloc_t(m, &m->dof_node, n_dof > 0 ? n_dof : 1));
     k_dof_number<<<grid_for(N), kThreads, 0, s>>>(flag, off, N, m->dof, m->dof_node);
+    note_launch(m);
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
@@ -567,8 +582,10 @@ int bins_build(Mesh *m) {
         FEM3_CUDA(cudaMemsetAsync(gcur, 0, sizeof(int32_t) * nb, s));
         FEM3_CUDA(cudaMemsetAsync(dcur, 0, sizeof(int32_t) * nb, s));
         k_gp_bin_count<<<grid_for(n_gp), kThreads, 0, s>>>(m->gp, n_gp, G, gcount, gbin);
+        note_launch(m);
         k_dof_bin_count<<<grid_for(n_dof), kThreads, 0, s>>>(m->node_box, m->dof_node, n_dof, G,
                                                              dcount);
+        note_launch(m);
         FEM3_TRY(scan_i32(gcount, B.gp_off, nb, s, m));
         FEM3_TRY(scan_i32(dcount, B.dof_off, nb, s, m));
         B.h_gp_off.resize(nb + 1);
@@ -598,12 +615,17 @@ int bins_build(Mesh *m) {
         double lo = m->lo[axis], span = std::max(m->hi[axis] - m->lo[axis], 1e-300);
         k_gp_bin_fill<<<grid_for(n_gp), kThreads, 0, s>>>(m->gp, n_gp, axis, lo, span, gbin,
                                                           B.gp_off, gcur, gkeys);
+        note_launch(m);
         k_dof_bin_fill<<<grid_for(n_dof), kThreads, 0, s>>>(m->node_box, m->dof_node, n_dof, G,
                                                             B.dof_off, dcur, dkeys);
+        note_launch(m);
         k_bin_sort<<<nb, 1024, 0, s>>>(B.gp_off, gkeys, B.gp_idx, B.slot_bin);
+        note_launch(m);
         k_bin_sort<<<nb, 1024, 0, s>>>(B.dof_off, dkeys, B.dof_idx, nullptr);
+        note_launch(m);
         FEM3_TRY(dev_alloc_t(m, &B.slot_of_gp, n_gp));
         k_invert_slots<<<grid_for(n_gp), kThreads, 0, s>>>(B.gp_idx, n_gp, B.slot_of_gp);
+        note_launch(m);
 
         // table layout: block of bin b is [D_b][ld_b], ld_b = Gauss points rounded up to 8
         B.h_tab_off.resize(nb);

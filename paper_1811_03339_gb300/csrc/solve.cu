@@ -61,13 +61,20 @@ __global__ void k_load_T(const int32_t *__restrict__ tets, const double *__restr
 // ---------------------------------------------------------------------------------
 // Cholesky
 // ---------------------------------------------------------------------------------
+// Diagonal block: factor A_kk = L_kk L_kk^T in shared memory (right-looking, one column
+// at a time), write L_kk back, and form L_kk^{-1} (thread c solves column c) so that the
+// panel solve becomes a product.  A non-positive pivot records 1 + its column.
 template <class TF>
-__global__ void __launch_bounds__(256) k_potrf_diag(TF *A, int64_t n, int k0, int32_t *err) {
-    __shared__ TF a[NB][NB + 1];
+__global__ void __launch_bounds__(256) k_potrf_inv(TF *A, int64_t n, int k0, TF *Linv,
+                                                   int32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TF(*a)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
+    TF(*li)[NB + 1] = a + NB;
     const int nb = (int)min((int64_t)NB, n - k0);
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         int i = e / NB, j = e % NB;
-        a[i][j] = (i < nb && j < nb) ? A[(int64_t)(k0 + i) * n + k0 + j] : TF(0);
+        a[i][j] = (i < nb && j < nb) ? A[(int64_t)(k0 + i) * n + k0 + j]
+                                     : (i == j ? TF(1) : TF(0));
     }
     __syncthreads();
     for (int j = 0; j < nb; j++) {
@@ -83,9 +90,9 @@ __global__ void __launch_bounds__(256) k_potrf_diag(TF *A, int64_t n, int k0, in
         TF djj = a[j][j];
         for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] /= djj;
         __syncthreads();
-        // rank-1 update of the remaining lower part
-        for (int e = threadIdx.x; e < (nb - j - 1) * (nb - j - 1); e += blockDim.x) {
-            int i = j + 1 + e / (nb - j - 1), c = j + 1 + e % (nb - j - 1);
+        const int m = nb - j - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            int i = j + 1 + e / m, c = j + 1 + e % m;
             if (c <= i) a[i][c] -= a[i][j] * a[c][j];
         }
         __syncthreads();
@@ -94,34 +101,47 @@ __global__ void __launch_bounds__(256) k_potrf_diag(TF *A, int64_t n, int k0, in
         int i = e / nb, j = e % nb;
         A[(int64_t)(k0 + i) * n + k0 + j] = j <= i ? a[i][j] : TF(0);
     }
+    if (threadIdx.x < NB) {
+        const int c = threadIdx.x;
+        for (int r = 0; r < NB; r++) li[r][c] = TF(0);
+        li[c][c] = TF(1) / a[c][c];
+        for (int r = c + 1; r < NB; r++) {
+            TF sacc = TF(0);
+            for (int k = c; k < r; k++) sacc += a[r][k] * li[k][c];
+            li[r][c] = -sacc / a[r][r];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Linv[e] = li[e / NB][e % NB];
 }
 
-// rows [k0+NB, n) of the panel: X L_kk^T = B  (one thread per row, NB columns)
+// Panel rows [k0+NB, n): X = B L_kk^{-T}, i.e. X[r][c] = sum_k B[r][k] Linv[c][k].
 template <class TF>
-__global__ void __launch_bounds__(NB) k_trsm_panel(TF *A, int64_t n, int k0) {
+__global__ void __launch_bounds__(256) k_trsm_gemm(TF *A, int64_t n, int k0, const TF *Linv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TF(*l)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
-    TF(*x)[NB + 1] = l + NB;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        int i = e / NB, j = e % NB;
-        l[i][j] = A[(int64_t)(k0 + i) * n + k0 + j];
-    }
+    TF(*bt)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
+    TF(*li)[NB + 1] = bt + NB;
     const int64_t row0 = k0 + NB + (int64_t)blockIdx.x * NB;
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         int i = e / NB, j = e % NB;
-        x[i][j] = (row0 + i < n) ? A[(row0 + i) * n + k0 + j] : TF(0);
+        bt[i][j] = (row0 + i < n) ? A[(row0 + i) * n + k0 + j] : TF(0);
+        li[i][j] = Linv[e];
     }
     __syncthreads();
-    const int i = threadIdx.x;
-    for (int j = 0; j < NB; j++) {
-        TF s = x[i][j];
-        for (int c = 0; c < j; c++) s -= x[i][c] * l[j][c];
-        x[i][j] = s / l[j][j];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    TF acc[4][4];
+    for (int p = 0; p < 4; p++)
+        for (int q = 0; q < 4; q++) acc[p][q] = TF(0);
+    for (int k = 0; k < NB; k++) {
+        TF u[4], v[4];
+        for (int p = 0; p < 4; p++) { u[p] = bt[ty * 4 + p][k]; v[p] = li[tx * 4 + p][k]; }
+        for (int p = 0; p < 4; p++)
+            for (int q = 0; q < 4; q++) acc[p][q] = fma(u[p], v[q], acc[p][q]);
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        int r = e / NB, j = e % NB;
-        if (row0 + r < n) A[(row0 + r) * n + k0 + j] = x[r][j];
+    for (int p = 0; p < 4; p++) {
+        int64_t r = row0 + ty * 4 + p;
+        if (r >= n) continue;
+        for (int q = 0; q < 4; q++) A[r * n + k0 + tx * 4 + q] = acc[p][q];
     }
 }
 
@@ -224,38 +244,210 @@ __global__ void k_trsv_bwd_update(const TF *L, int64_t n, int k0, int nb, TF *y)
     y[i] -= s;
 }
 
+// ---------------------------------------------------------------------------------
+// Wavefront triangular solve: one CTA per 64-row block, all CTAs co-resident
+// (cooperative launch).  CTA for block i accumulates the products with the blocks it
+// depends on as their flags are published, solves its diagonal block and publishes
+// its own flag.  Every wait is bounded; a timeout sets ERR_SOLVE and the CTA returns.
+// ---------------------------------------------------------------------------------
+constexpr int kSpinLimit = 1 << 22;   // x >= 64 ns sleep: > 0.25 s before giving up
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// backward = 0: solve L y = b in place; backward = 1: solve L^T x = y in place.
 template <class TF>
-int cholesky_t(TF *A, int64_t n, cudaStream_t s, int32_t *err) {
+__global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L, int64_t n, TF *y,
+                                                   int *flags, int epoch, int32_t *err,
+                                                   int backward) {
+    __shared__ TF Ld[NB][NB + 1];
+    __shared__ TF xs[NB];
+    __shared__ TF red[8][NB];
+    __shared__ TF t[NB];
+    __shared__ int abort_flag;
+    const int nblk = gridDim.x;
+    const int i = backward ? nblk - 1 - (int)blockIdx.x : (int)blockIdx.x;
+    const int64_t r0 = (int64_t)i * NB;
+    const int nb = (int)min((int64_t)NB, n - r0);
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        int rr = e / NB, cc = e % NB;
+        Ld[rr][cc] = (rr < nb && cc < nb) ? L[(r0 + rr) * n + r0 + cc] : TF(0);
+    }
+    if (tid == 0) abort_flag = 0;
+    // per-thread partial sums: forward rows w*8..w*8+7 over columns {lane, lane+32};
+    // backward columns {lane, lane+32} over rows w*8..w*8+7
+    TF acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) acc[q] = TF(0);
+    __syncthreads();
+    const int ndep = backward ? (nblk - 1 - i) : i;
+    for (int d = 0; d < ndep; d++) {
+        const int j = backward ? (nblk - 1 - d) : d;
+        if (tid == 0) {
+            int spins = 0;
+            while (ld_acquire_gpu(&flags[j]) != epoch) {
+                if (++spins > kSpinLimit) {
+                    atomicAdd(&err[ERR_SOLVE], 1);
+                    abort_flag = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __syncthreads();
+        if (abort_flag) return;
+        const int64_t c0 = (int64_t)j * NB;
+        const int njb = (int)min((int64_t)NB, n - c0);
+        if (tid < NB) xs[tid] = tid < njb ? __ldcg(&y[c0 + tid]) : TF(0);
+        __syncthreads();
+        if (!backward) {
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                int rr = w * 8 + q;
+                if (rr < nb) {
+                    const TF *row = L + (r0 + rr) * n + c0;
+                    TF v = lane < njb ? row[lane] * xs[lane] : TF(0);
+                    if (lane + 32 < njb) v += row[lane + 32] * xs[lane + 32];
+                    acc[q] += v;
+                }
+            }
+        } else {
+            TF a0 = TF(0), a1 = TF(0);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                int rr = w * 8 + q;
+                if (rr < njb) {
+                    const TF *row = L + (c0 + rr) * n + r0;
+                    if (lane < nb) a0 += row[lane] * xs[rr];
+                    if (lane + 32 < nb) a1 += row[lane + 32] * xs[rr];
+                }
+            }
+            acc[0] += a0;
+            acc[1] += a1;
+        }
+        __syncthreads();   // xs is rewritten by the next dependency
+    }
+    // reduce the partial sums into t = b - (sum over dependencies)
+    if (!backward) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            TF v = acc[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[0][w * 8 + q] = v;
+        }
+        __syncthreads();
+        if (tid < NB) t[tid] = tid < nb ? y[r0 + tid] - red[0][tid] : TF(0);
+    } else {
+        red[w][lane] = acc[0];
+        red[w][lane + 32] = acc[1];
+        __syncthreads();
+        if (tid < NB) {
+            TF v = TF(0);
+            for (int q = 0; q < 8; q++) v += red[q][tid];
+            t[tid] = tid < nb ? y[r0 + tid] - v : TF(0);
+        }
+    }
+    __syncthreads();
+    // diagonal block, one warp, column-oriented updates (lane owns rows lane, lane+32)
+    if (w == 0) {
+        TF t0 = t[lane], t1 = t[lane + 32];
+        if (!backward) {
+            for (int c = 0; c < nb; c++) {
+                TF tc = c < 32 ? __shfl_sync(0xffffffffu, t0, c) : __shfl_sync(0xffffffffu, t1, c - 32);
+                TF yc = tc / Ld[c][c];
+                if (lane == (c & 31)) { if (c < 32) t0 = yc; else t1 = yc; }
+                if (lane > c) t0 -= Ld[lane][c] * yc;
+                if (lane + 32 > c) t1 -= Ld[lane + 32][c] * yc;
+            }
+        } else {
+            for (int c = nb - 1; c >= 0; c--) {
+                TF tc = c < 32 ? __shfl_sync(0xffffffffu, t0, c) : __shfl_sync(0xffffffffu, t1, c - 32);
+                TF xc = tc / Ld[c][c];
+                if (lane == (c & 31)) { if (c < 32) t0 = xc; else t1 = xc; }
+                if (lane < c) t0 -= Ld[c][lane] * xc;
+                if (lane + 32 < c) t1 -= Ld[c][lane + 32] * xc;
+            }
+        }
+        if (lane < nb) y[r0 + lane] = t0;
+        if (lane + 32 < nb) y[r0 + lane + 32] = t1;
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_gpu(&flags[i], epoch);
+    }
+}
+
+template <class TF>
+int cholesky_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
     const size_t sh = 2 * NB * (NB + 1) * sizeof(TF);
-    FEM3_CUDA(cudaFuncSetAttribute(k_trsm_panel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    FEM3_CUDA(cudaFuncSetAttribute(k_potrf_inv<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    FEM3_CUDA(cudaFuncSetAttribute(k_trsm_gemm<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
     FEM3_CUDA(cudaFuncSetAttribute(k_syrk<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    TF *Linv = reinterpret_cast<TF *>(m->vec64[5]);   // NB x NB scratch
     for (int64_t k0 = 0; k0 < n; k0 += NB) {
-        k_potrf_diag<TF><<<1, 256, 0, s>>>(A, n, (int)k0, err);
+        k_potrf_inv<TF><<<1, 256, sh, s>>>(A, n, (int)k0, Linv, m->err);
+        note_launch(m);
         int64_t rest = n - k0 - NB;
         if (rest > 0) {
             int nblk = (int)((rest + NB - 1) / NB);
-            k_trsm_panel<TF><<<nblk, NB, sh, s>>>(A, n, (int)k0);
+            k_trsm_gemm<TF><<<nblk, 256, sh, s>>>(A, n, (int)k0, Linv);
+            note_launch(m);
             int ntiles = nblk * (nblk + 1) / 2;
             k_syrk<TF><<<ntiles, 256, sh, s>>>(A, n, (int)k0, nblk);
+            note_launch(m);
         }
     }
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
 
+// L y = b then L^T x = y, in place; cooperative wavefront kernel when all block CTAs
+// fit on the device at once, otherwise blocked substitution with one launch per block.
 template <class TF>
-int trsv_t(const TF *L, int64_t n, TF *y, cudaStream_t s) {
+int trsv_t(const TF *L, int64_t n, TF *y, cudaStream_t s, Mesh *m) {
+    if (n <= 0) return FEM3_OK;
+    int nblk = (int)((n + NB - 1) / NB);
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_wave<TF>, 256, 0);
+    if (m && m->flags && coop && (int64_t)per_sm * sms >= nblk) {
+        for (int backward = 0; backward < 2; backward++) {
+            int epoch = ++m->flag_epoch;
+            int32_t *err = m->err;
+            int *flags = m->flags;
+            void *args[] = {(void *)&L, (void *)&n, (void *)&y, (void *)&flags, (void *)&epoch,
+                            (void *)&err, (void *)&backward};
+            FEM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_trsv_wave<TF>, dim3(nblk),
+                                                  dim3(256), args, 0, s));
+            note_launch(m);
+        }
+        return FEM3_OK;
+    }
     for (int64_t k0 = 0; k0 < n; k0 += NB) {
         k_trsv_fwd_diag<TF><<<1, 32, 0, s>>>(L, n, (int)k0, y);
+        note_launch(m);
         int64_t rest = n - k0 - NB;
-        if (rest > 0) k_trsv_fwd_update<TF><<<(unsigned)((rest + 7) / 8), 256, 0, s>>>(L, n, (int)k0, y);
+        if (rest > 0) {
+            k_trsv_fwd_update<TF><<<(unsigned)((rest + 7) / 8), 256, 0, s>>>(L, n, (int)k0, y);
+            note_launch(m);
+        }
     }
     int64_t last = ((n - 1) / NB) * NB;
     for (int64_t k0 = last; k0 >= 0; k0 -= NB) {
         k_trsv_bwd_diag<TF><<<1, 32, 0, s>>>(L, n, (int)k0, y);
+        note_launch(m);
         if (k0 > 0) {
             int nb = (int)std::min<int64_t>(NB, n - k0);
             k_trsv_bwd_update<TF><<<(unsigned)((k0 + 255) / 256), 256, 0, s>>>(L, n, (int)k0, nb, y);
+            note_launch(m);
         }
     }
     FEM3_CUDA(cudaGetLastError());
@@ -406,6 +598,7 @@ int residual_norm(Mesh *m, const double *b, const double *Au, double *rel) {
     const int64_t n = m->n_dof;
     FEM3_CUDA(cudaMemsetAsync(m->norms, 0, sizeof(double) * 2, s));
     k_residual<<<g256(n), 256, 0, s>>>(b, Au, n, m->vec64[1], m->norms);
+    note_launch(m);
     FEM3_CUDA(cudaMemcpyAsync(m->h_norms, m->norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
     FEM3_CUDA(cudaStreamSynchronize(s));
     *rel = m->h_norms[1] > 0 ? sqrt(m->h_norms[0] / m->h_norms[1]) : 0.0;
@@ -417,6 +610,7 @@ int load_vector(Mesh *m, const double *f_d, int nrhs, double *b_d) {
     FEM3_CUDA(cudaMemsetAsync(b_d, 0, sizeof(double) * m->n_dof * nrhs, s));
     k_load<<<g256(m->n_tets), 256, 0, s>>>(m->tets, m->vol, m->dof, m->n_tets, m->n_nodes, m->n_dof,
                                             f_d, nrhs, b_d);
+    note_launch(m);
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
@@ -425,13 +619,14 @@ int load_vector_T(Mesh *m, const double *lam_d, double *out_d) {
     cudaStream_t s = m->stream;
     FEM3_CUDA(cudaMemsetAsync(out_d, 0, sizeof(double) * m->n_nodes, s));
     k_load_T<<<g256(m->n_tets), 256, 0, s>>>(m->tets, m->vol, m->dof, m->n_tets, lam_d, out_d);
+    note_launch(m);
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
 
 int factor(Mesh *m) {
-    if (m->precision == FEM3_FP64) return cholesky_t<double>(m->A64, m->n_dof, m->stream, m->err);
-    return cholesky_t<float>(m->A32, m->n_dof, m->stream, m->err);
+    if (m->precision == FEM3_FP64) return cholesky_t<double>(m->A64, m->n_dof, m->stream, m);
+    return cholesky_t<float>(m->A32, m->n_dof, m->stream, m);
 }
 
 int apply_A64(Mesh *m, const double *u_d, double *Au_d) {
@@ -445,6 +640,7 @@ int apply_A64(Mesh *m, const double *u_d, double *Au_d) {
         k_apply_tables<<<B.n_bins, 256, sh, s>>>(m->tabL[axis], m->tabR[axis], B.gp_off, B.gp_idx,
                                                   B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, m->gw,
                                                   u_d, m->sK[axis], Au_d);
+        note_launch(m);
     }
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
@@ -461,6 +657,7 @@ int axis_forms(Mesh *m, const double *u_d, const double *lam_d, double out[3]) {
         k_axis_form<<<B.n_bins, 256, sh, s>>>(m->tabL[axis], m->tabR[axis], B.gp_off, B.gp_idx,
                                                B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, m->gw, u_d,
                                                lam_d, m->norms + axis);
+        note_launch(m);
     }
     FEM3_CUDA(cudaMemcpyAsync(m->h_norms, m->norms, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
     FEM3_CUDA(cudaStreamSynchronize(s));
@@ -472,7 +669,7 @@ int solve_direct(Mesh *m, const double *b_d, int nrhs, double *u_d) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
     FEM3_CUDA(cudaMemcpyAsync(u_d, b_d, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
-    for (int r = 0; r < nrhs; r++) FEM3_TRY(trsv_t<double>(m->A64, n, u_d + r * n, s));
+    for (int r = 0; r < nrhs; r++) FEM3_TRY(trsv_t<double>(m->A64, n, u_d + r * n, s, m));
     return FEM3_OK;
 }
 
@@ -493,11 +690,14 @@ int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter
         double rel = 1.0;
         for (;;) {
             k_to_f32<<<g256(n), 256, 0, s>>>(r, r32, n);
-            FEM3_TRY(trsv_t<float>(m->A32, n, r32, s));
+            note_launch(m);
+            FEM3_TRY(trsv_t<float>(m->A32, n, r32, s, m));
             k_axpy_f32<<<g256(n), 256, 0, s>>>(r32, u, n);
+            note_launch(m);
             FEM3_TRY(apply_A64(m, u, Au));
             FEM3_CUDA(cudaMemsetAsync(m->norms, 0, sizeof(double) * 2, s));
             k_residual<<<g256(n), 256, 0, s>>>(b, Au, n, r, m->norms);
+            note_launch(m);
             FEM3_CUDA(cudaMemcpyAsync(m->h_norms, m->norms, sizeof(double) * 2,
                                       cudaMemcpyDeviceToHost, s));
             FEM3_CUDA(cudaStreamSynchronize(s));

@@ -283,6 +283,7 @@ int walk_tables(Mesh *m, const double alpha[3]) {
         A1.coef = -ig;
         dim3 grid((unsigned)((m->n_gp + 127) / 128), 2);
         k_walk_tables<<<grid, 128, 0, s>>>(W, A0, A1, axis, m->n_gp, m->err, segc);
+        note_launch(m);
     }
     stage_end(m, 2);
     FEM3_CUDA(cudaGetLastError());
@@ -294,6 +295,7 @@ int walk_paths(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, int ca
     WalkGeom W = make_geom(m);
     k_walk_paths<<<(unsigned)((n + 127) / 128), 128, 0, m->stream>>>(W, axis, dir, gps, n, m->n_gp,
                                                                       cap, tet_out, r0, r1, nseg);
+    note_launch(m);
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
@@ -304,10 +306,12 @@ int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double
     const int32_t *slot_of_gp = B.slot_of_gp;
     FEM3_CUDA(cudaMemsetAsync(rows, 0, sizeof(double) * n * m->n_dof, s));
     const double *tab = dir < 0 ? m->tabL[axis] : m->tabR[axis];
-    if (n > 0)
+    if (n > 0) {
         k_table_rows<<<(unsigned)n, 128, 0, s>>>(tab, B.slot_bin, gps, n, slot_of_gp, B.gp_off,
                                                   B.dof_off, B.dof_idx, B.tab_off, B.tab_ld,
                                                   m->n_dof, m->n_gp, rows);
+        note_launch(m);
+    }
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }

@@ -66,7 +66,7 @@ def load_library(build_if_missing: bool = True):
         "fem3_table_rows": [p, ci, ci, p, i64, p, p],
         "fem3_sync": [p, p],
         "fem3_stage_ms": [p, ci, C.POINTER(C.c_float)],
-        "fem3_counters": [p, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)],
+        "fem3_counters": [p, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)],
         "fem3_last_error": [C.c_char_p, C.c_size_t],
         "fem3_mesh_free": [p],
     }
@@ -170,9 +170,9 @@ def stage_ms(h):
 
 
 def counters(h):
-    s, f, b = C.c_int64(), C.c_double(), C.c_int64()
-    _check(_lib.fem3_counters(h, C.byref(s), C.byref(f), C.byref(b)))
-    return dict(segments=s.value, contract_flops=f.value, table_bytes=b.value)
+    s, f, b, n = C.c_int64(), C.c_double(), C.c_int64(), C.c_int64()
+    _check(_lib.fem3_counters(h, C.byref(s), C.byref(f), C.byref(b), C.byref(n)))
+    return dict(segments=s.value, contract_flops=f.value, table_bytes=b.value, launches=n.value)
 
 
 def mesh_free(h):
@@ -210,7 +210,7 @@ class Mesh:
 
     def load(self, f):
         f = self._as_nodal(f)
-        nrhs = 1 if f.dim() == 1 else f.shape[1]
+        nrhs = 1 if f.dim() == 1 else f.shape[0]
         b = self._dev((nrhs, self.n_dof))
         load(self.h, f, nrhs, b, self.stream)
         return b[0] if nrhs == 1 else b.T

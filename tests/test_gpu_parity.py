@@ -123,6 +123,21 @@ def test_mixed_with_refinement(name, precision):
     m.free()
 
 
+@pytest.mark.parametrize("name", ["cube7_jitter", "ppd5"])
+def test_tensor_core_split_products_reach_fp32_accuracy(name):
+    """TF32 x 3 (hi*hi + hi*lo + lo*hi) keeps about 22 significant bits: the matrix is
+    within 2e-6 of the FP64 oracle (a single TF32 product would be ~1e-3 off)."""
+    mesh, o, alpha, K = _case(name)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    A = m.assemble(alpha, K, "tf32x3", return_matrix=True).cpu().numpy()
+    m.sync()
+    A_ref = o.assemble(alpha, K)
+    assert _rel(A, A_ref) <= 2e-6
+    # symmetric up to FP32 summation order
+    assert np.abs(A - A.T).max() <= 1e-6 * np.abs(A).max()
+    m.free()
+
+
 def test_load_vector():
     mesh, o, alpha, K = _case("cube3_jitter")
     m = fem3.Mesh(mesh.verts, mesh.tets)
