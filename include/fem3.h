@@ -194,6 +194,30 @@ int fem3_stage_ms(fem3_mesh m, int stage, float *ms);
 int fem3_counters(fem3_mesh m, int64_t *segments, double *contract_flops,
                   int64_t *table_bytes, int64_t *launches);
 
+/*
+ * fem3_spd_solve_static - solve A x = b for a dense symmetric positive definite matrix
+ * without allocating any device memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc where they need a solve (code
+ * running while a stream is captured into a CUDA graph, latency-critical loops that
+ * must not enter the allocator, host applications that own every device allocation).
+ *
+ *   A       device float64 row-major [n][n], SPD; read only (the lower triangle is used).
+ *   b       device float64 [n]; read only.
+ *   x       device float64 [n]; receives the solution.
+ *   n       1 <= n <= 512; larger systems are rejected with FEM3_E_ARG.
+ * Working memory is one static device array of about 2.1 MB (a 512 x 512 FP64 factor,
+ * one 64 x 64 block inverse and an error word) that every GPU which loads the library
+ * holds until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the last call's
+ * contents: each call clears the error word and rewrites the factor, so calls that
+ * overlap on the GPU (other streams, other host threads) race and must be serialised
+ * by the caller.  Synchronises `stream`.  Errors: FEM3_E_ARG, FEM3_E_NOT_SPD,
+ * FEM3_E_CUDA.
+ */
+int fem3_spd_solve_static(const double *A, int64_t n, const double *b, double *x,
+                          void *stream);
+
 /* Text of the last error of the calling thread. */
 int fem3_last_error(char *buf, size_t len);
 

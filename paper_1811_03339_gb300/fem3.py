@@ -25,7 +25,7 @@ PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2}
 # every entry point declared in include/fem3.h
 SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_load", "fem3_solve",
            "fem3_adjoint", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
-           "fem3_counters", "fem3_last_error", "fem3_mesh_free")
+           "fem3_counters", "fem3_last_error", "fem3_mesh_free", "fem3_spd_solve_static")
 
 _lib = None
 
@@ -69,6 +69,7 @@ def load_library(build_if_missing: bool = True):
         "fem3_counters": [p, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)],
         "fem3_last_error": [C.c_char_p, C.c_size_t],
         "fem3_mesh_free": [p],
+        "fem3_spd_solve_static": [p, i64, p, p, p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -173,6 +174,12 @@ def counters(h):
     s, f, b, n = C.c_int64(), C.c_double(), C.c_int64(), C.c_int64()
     _check(_lib.fem3_counters(h, C.byref(s), C.byref(f), C.byref(b), C.byref(n)))
     return dict(segments=s.value, contract_flops=f.value, table_bytes=b.value, launches=n.value)
+
+
+def spd_solve_static(A, b, x, stream=None):
+    """Dense SPD solve with no device allocation (n <= 512); see include/fem3.h."""
+    lib = load_library()
+    _check(lib.fem3_spd_solve_static(_ptr(A), int(A.shape[0]), _ptr(b), _ptr(x), _stream(stream)))
 
 
 def mesh_free(h):
