@@ -189,7 +189,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(precision, profile=False, keep=False):
-        m = fem3.Mesh(verts_d, tets_d, profile=profile)
+        m = fem3.Mesh(verts_d, tets_d, bin_scale=args.bin_scale, profile=profile)
         m.assemble(alpha, K, precision)
         u = m.solve(f_d, tol=1e-12)
         if keep:
@@ -278,7 +278,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        mh = fem3.Mesh(verts_h.numpy(), tets_h.numpy())
+        mh = fem3.Mesh(verts_h.numpy(), tets_h.numpy(), bin_scale=args.bin_scale)
         mh.assemble(alpha, K, args.precision)
         u = mh.solve(f_h.numpy(), tol=1e-12)
         u_host = u.cpu()
@@ -313,6 +313,7 @@ def run_ours(args):
                        "gauss_points": 4 * int(mesh.n_tets), "dofs": int(n_dof),
                        "paths_per_step": n_paths, "alpha": list(alpha), "K": list(K),
                        "precision": args.precision, "parallelism": f"replicas{world}",
+                       "bin_scale": args.bin_scale,
                        "l2": "flushed (256 MB write) between timed steps"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
@@ -350,6 +351,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["tf32x3", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bin-scale", type=float, default=0.5,
+                    help="transverse bin width in mean cell sizes (template granularity)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

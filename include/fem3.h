@@ -67,7 +67,7 @@ typedef struct fem3_mesh_s *fem3_mesh;
 
 typedef struct fem3_options {
     double bin_scale;  /* transverse bin width in units of the mean cell size h
-                          (h = (6 * mean tet volume)^(1/3)); <= 0 selects 1.0 */
+                          (h = (6 * mean tet volume)^(1/3)); <= 0 selects 0.5 */
     int32_t max_steps; /* cap on tets crossed by one walk; <= 0 selects
                           8 * n_tets^(1/3) + 64 */
     int32_t profile;   /* nonzero: record CUDA events around each stage (fem3_stage_ms) */

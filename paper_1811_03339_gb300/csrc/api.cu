@@ -134,6 +134,8 @@ void fem3_mesh_free(fem3_mesh h) {
     dev_free_all(m);
     cudaStreamSynchronize(m->stream);
     if (m->h_norms) cudaFreeHost(m->h_norms);
+    for (int k = 0; k < 2; k++)
+        if (m->chol_exec[k]) cudaGraphExecDestroy(m->chol_exec[k]);
     if (m->ev_made)
         for (int k = 0; k < 16; k++) cudaEventDestroy(m->ev[k]);
     delete m;
@@ -152,7 +154,7 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
     m->n_nodes = n_nodes;
     m->n_tets = n_tets;
     m->n_gp = 4 * n_tets;
-    m->bin_scale = (opt && opt->bin_scale > 0) ? opt->bin_scale : 1.0;
+    m->bin_scale = (opt && opt->bin_scale > 0) ? opt->bin_scale : 0.5;
     m->max_steps = (opt && opt->max_steps > 0) ? opt->max_steps
                                                : (int)(8.0 * cbrt((double)n_tets)) + 64;
     m->profile = opt && opt->profile;
@@ -197,9 +199,12 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
     stage_end(m, 1);
     const int64_t n = std::max<int64_t>(1, m->n_dof);
     if ((st = dev_alloc_t(m, &m->flags, (n + 63) / 64 + 1)) != FEM3_OK) return fail(st);
+    if ((st = dev_alloc(m, &m->dinv, sizeof(double) * 64 * 64 * ((n + 63) / 64))) != FEM3_OK)
+        return fail(st);
+    if ((st = dev_alloc_t(m, &m->ybuf, 2 * m->n_gp)) != FEM3_OK) return fail(st);
     if (cudaMemsetAsync(m->flags, 0, sizeof(int32_t) * ((n + 63) / 64 + 1), m->stream) != cudaSuccess)
         return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
-    for (int k = 0; k < 6; k++)   // vec64[5] doubles as the 64x64 Cholesky scratch
+    for (int k = 0; k < 6; k++)
         if ((st = dev_alloc_t(m, &m->vec64[k], std::max<int64_t>(std::max<int64_t>(n, m->n_nodes),
                                                                  64 * 64))) != FEM3_OK)
             return fail(st);

@@ -115,36 +115,38 @@ __device__ __forceinline__ float tf32_rna(float x) {
 }
 
 // ------------------------------- split kernel ------------------------------------
-__global__ void k_split_tf32(const double *__restrict__ tabL, const double *__restrict__ tabR,
-                             const int32_t *__restrict__ row_bin,
-                             const int32_t *__restrict__ dof_off, const int32_t *__restrict__ gp_off,
-                             const int32_t *__restrict__ gp_idx, const int64_t *__restrict__ tab_off,
-                             const int32_t *__restrict__ tab_ld, const double *__restrict__ gw,
-                             int64_t n_rows, int Kp, float *Lhi, float *Llo, float *Rhi, float *Rlo) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n_rows * Kp) return;
-    int64_t row = e / Kp;
-    int k = (int)(e % Kp);
-    int b = row_bin[row];
-    int c = (int)(row - dof_off[b]);
-    int G = gp_off[b + 1] - gp_off[b];
-    float lh = 0.f, ll = 0.f, rh = 0.f, rl = 0.f;
-    if (k < G) {
-        int64_t idx = tab_off[b] + (int64_t)c * tab_ld[b] + k;
-        double l = tabL[idx];
-        double r = tabR[idx] * gw[gp_idx[gp_off[b] + k]];
-        lh = tf32_rna((float)l);
-        ll = tf32_rna((float)(l - (double)lh));
-        rh = tf32_rna((float)r);
-        rl = tf32_rna((float)(r - (double)rh));
+// One warp per template row (bin b, local dof c): coalesced reads of the FP64 table row
+// and writes of the four TF32 halves; zero past the bin's Gauss points.
+__global__ void __launch_bounds__(256) k_split_tf32(
+    const double *__restrict__ tabL, const double *__restrict__ tabR,
+    const int32_t *__restrict__ row_bin, const int32_t *__restrict__ dof_off,
+    const int32_t *__restrict__ gp_off, const int32_t *__restrict__ gp_idx,
+    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
+    const double *__restrict__ gw, int64_t n_rows, int Kp, float *Lhi, float *Llo, float *Rhi,
+    float *Rlo) {
+    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n_rows) return;
+    const int b = row_bin[row];
+    const int c = (int)(row - dof_off[b]);
+    const int g0 = gp_off[b], G = gp_off[b + 1] - g0;
+    const int64_t src = tab_off[b] + (int64_t)c * tab_ld[b];
+    const int64_t dst = row * (int64_t)Kp;
+    for (int k = lane; k < Kp; k += 32) {
+        float lh = 0.f, ll = 0.f, rh = 0.f, rl = 0.f;
+        if (k < G) {
+            const double l = tabL[src + k];
+            const double r = tabR[src + k] * __ldg(gw + gp_idx[g0 + k]);
+            lh = tf32_rna((float)l);
+            ll = tf32_rna((float)(l - (double)lh));
+            rh = tf32_rna((float)r);
+            rl = tf32_rna((float)(r - (double)rh));
+        }
+        Lhi[dst + k] = lh;
+        Llo[dst + k] = ll;
+        Rhi[dst + k] = rh;
+        Rlo[dst + k] = rl;
     }
-    Lhi[e] = lh; Llo[e] = ll; Rhi[e] = rh; Rlo[e] = rl;
-}
-
-__global__ void k_row_bin(const int32_t *__restrict__ dof_off, int n_bins, int32_t *row_bin) {
-    int b = blockIdx.x;
-    if (b >= n_bins) return;
-    for (int r = dof_off[b] + threadIdx.x; r < dof_off[b + 1]; r += blockDim.x) row_bin[r] = b;
 }
 
 // ------------------------------- GEMM kernel --------------------------------------
@@ -316,11 +318,6 @@ static int tc_prepare(Mesh *m) {
         const int64_t rows = std::max<int64_t>(1, B.n_tmpl);
         for (int q = 0; q < 4; q++)
             FEM3_TRY(dev_alloc_t(m, &B.tc_op[q], rows * B.tc_Kp));
-        FEM3_TRY(dev_alloc_t(m, &B.row_bin, rows));
-        if (B.n_tmpl > 0) {
-            k_row_bin<<<B.n_bins, 256, 0, s>>>(B.dof_off, B.n_bins, B.row_bin);
-            note_launch(m);
-        }
         std::vector<int4> work;
         for (int b = 0; b < B.n_bins; b++) {
             int D = B.h_dof_off[b + 1] - B.h_dof_off[b];
@@ -356,8 +353,7 @@ int contract_tc(Mesh *m) {
             flops += 2.0 * D * D * G;
         }
         if (!B.tc_n_work) continue;
-        const int64_t elems = B.n_tmpl * (int64_t)B.tc_Kp;
-        k_split_tf32<<<(unsigned)((elems + 255) / 256), 256, 0, s>>>(
+        k_split_tf32<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
             m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.gp_idx, B.tab_off,
             B.tab_ld, m->gw, B.n_tmpl, B.tc_Kp, B.tc_op[0], B.tc_op[1], B.tc_op[2], B.tc_op[3]);
         note_launch(m);

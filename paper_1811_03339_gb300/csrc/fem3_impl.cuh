@@ -107,6 +107,8 @@ struct Mesh {
     AxisBins bins[3];
     double *tabL[3] = {nullptr, nullptr, nullptr};
     double *tabR[3] = {nullptr, nullptr, nullptr};
+    double *pow_cell = nullptr;   // [3][256][8] tables of the table-driven power
+    double *pow_exp = nullptr;    // [3][128]
 
     // assembled operator
     int precision = -1;        // of the last assemble, -1: none
@@ -116,12 +118,17 @@ struct Mesh {
     double *A64 = nullptr;     // [n_dof][n_dof]
     float *A32 = nullptr;      // [n_dof][n_dof]
     bool factored = false;
+    cudaGraphExec_t chol_exec[2] = {nullptr, nullptr};   // factorisation graphs (FP64, FP32)
+    int64_t chol_launches[2] = {0, 0};
+    int factor_count[2] = {0, 0};
     bool tc_ready = false;
 
     // workspaces
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     float *vec32[2] = {nullptr, nullptr};
     int32_t *flags = nullptr;  // wavefront triangular-solve flags (one per 64-row block)
+    void *dinv = nullptr;      // inverses of the 64 x 64 diagonal blocks of the factor
+    double *ybuf = nullptr;    // [2][n_gp] weighted table-times-vector rows (operator apply)
     int flag_epoch = 0;        // value that marks "ready" in the current solve
     double *norms = nullptr;   // device scratch for reductions
     double *h_norms = nullptr; // pinned host mirror

@@ -425,6 +425,12 @@ __global__ void k_bin_sort(const int32_t *__restrict__ off, unsigned long long *
     }
 }
 
+__global__ void k_row_bin(const int32_t *__restrict__ dof_off, int n_bins, int32_t *row_bin) {
+    int b = blockIdx.x;
+    if (b >= n_bins) return;
+    for (int r = dof_off[b] + threadIdx.x; r < dof_off[b + 1]; r += blockDim.x) row_bin[r] = b;
+}
+
 __global__ void k_invert_slots(const int32_t *__restrict__ gp_idx, int64_t n_gp,
                                int32_t *slot_of_gp) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -623,6 +629,11 @@ int bins_build(Mesh *m) {
         note_launch(m);
         k_bin_sort<<<nb, 1024, 0, s>>>(B.dof_off, dkeys, B.dof_idx, nullptr);
         note_launch(m);
+        FEM3_TRY(dev_alloc_t(m, &B.row_bin, std::max<int64_t>(1, B.n_tmpl)));
+        if (B.n_tmpl > 0) {
+            k_row_bin<<<nb, 256, 0, s>>>(B.dof_off, nb, B.row_bin);
+            note_launch(m);
+        }
         FEM3_TRY(dev_alloc_t(m, &B.slot_of_gp, n_gp));
         k_invert_slots<<<grid_for(n_gp), kThreads, 0, s>>>(B.gp_idx, n_gp, B.slot_of_gp);
         note_launch(m);

@@ -61,9 +61,13 @@ __global__ void k_load_T(const int32_t *__restrict__ tets, const double *__restr
 // ---------------------------------------------------------------------------------
 // Cholesky
 // ---------------------------------------------------------------------------------
-// Diagonal block: factor A_kk = L_kk L_kk^T in shared memory (right-looking, one column
-// at a time), write L_kk back, and form L_kk^{-1} (thread c solves column c) so that the
-// panel solve becomes a product.  A non-positive pivot records 1 + its column.
+// Diagonal block: factor A_kk = L_kk L_kk^T in shared memory and form L_kk^{-1}.
+// Factor: right-looking elimination on the unscaled columns (a[i][c] -= a[i][j] a[c][j] /
+// a[j][j]), one barrier per column; the columns are scaled by 1/sqrt(pivot) at the end.
+// Thread t owns row t/4 and every fourth column of it.  Inverse: four lanes of a warp
+// solve L x = e_c for one column c (split inner products, shuffle reduction), no block
+// barrier.  Linv receives the inverse (row-major 64 x 64); a non-positive pivot records
+// 1 + its column.
 template <class TF>
 __global__ void __launch_bounds__(256) k_potrf_inv(TF *A, int64_t n, int k0, TF *Linv,
                                                    int32_t *err) {
@@ -77,38 +81,51 @@ __global__ void __launch_bounds__(256) k_potrf_inv(TF *A, int64_t n, int k0, TF 
                                      : (i == j ? TF(1) : TF(0));
     }
     __syncthreads();
-    for (int j = 0; j < nb; j++) {
-        if (threadIdx.x == 0) {
-            TF d = a[j][j];
-            if (!(d > TF(0))) {
-                atomicCAS(&err[ERR_NOT_SPD], 0, k0 + j + 1);
-                d = TF(1);
-            }
-            a[j][j] = sqrt(d);
-        }
-        __syncthreads();
-        TF djj = a[j][j];
-        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] /= djj;
-        __syncthreads();
-        const int m = nb - j - 1;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            int i = j + 1 + e / m, c = j + 1 + e % m;
-            if (c <= i) a[i][c] -= a[i][j] * a[c][j];
+    const int row = threadIdx.x >> 2, q = threadIdx.x & 3;
+    for (int j = 0; j < NB - 1; j++) {
+        const TF piv = a[j][j];
+        if (row > j) {
+            const TF f = a[row][j] / (piv > TF(0) ? piv : TF(1));
+            for (int c = j + 1 + q; c <= row; c += 4) a[row][c] -= f * a[c][j];
         }
         __syncthreads();
     }
+    // pivots, scaling, pivot check
+    if (threadIdx.x < NB) {
+        const int j = threadIdx.x;
+        if (j < nb && !(a[j][j] > TF(0))) atomicCAS(&err[ERR_NOT_SPD], 0, k0 + j + 1);
+    }
+    __syncthreads();
+    {
+        // L[i][j] = a[i][j] / sqrt(a[j][j]) (i > j), L[j][j] = sqrt(a[j][j])
+        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+            int i = e / NB, j = e % NB;
+            TF d = a[j][j] > TF(0) ? a[j][j] : TF(1);
+            TF v = i == j ? sqrt(d) : (i > j ? a[i][j] / sqrt(d) : TF(0));
+            li[i][j] = v;   // li holds L for now
+        }
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
         int i = e / nb, j = e % nb;
-        A[(int64_t)(k0 + i) * n + k0 + j] = j <= i ? a[i][j] : TF(0);
+        A[(int64_t)(k0 + i) * n + k0 + j] = li[i][j];
     }
-    if (threadIdx.x < NB) {
-        const int c = threadIdx.x;
-        for (int r = 0; r < NB; r++) li[r][c] = TF(0);
-        li[c][c] = TF(1) / a[c][c];
-        for (int r = c + 1; r < NB; r++) {
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) a[e / NB][e % NB] = li[e / NB][e % NB];
+    __syncthreads();
+    // inverse: column c by lanes 4*(c%8) .. of warp c/8; X stored in li
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const int c = w * 8 + (lane >> 2), part = lane & 3;
+        for (int r = 0; r < NB; r++) {
             TF sacc = TF(0);
-            for (int k = c; k < r; k++) sacc += a[r][k] * li[k][c];
-            li[r][c] = -sacc / a[r][r];
+            if (r > c)
+                for (int k = c + part; k < r; k += 4) sacc += a[r][k] * li[k][c];
+            sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+            sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+            TF x = r < c ? TF(0) : ((r == c ? TF(1) : TF(0)) - sacc) / a[r][r];
+            __syncwarp();
+            if (part == 0) li[r][c] = x;
+            __syncwarp();
         }
     }
     __syncthreads();
@@ -262,11 +279,14 @@ __device__ __forceinline__ void st_release_gpu(int *p, int v) {
 }
 
 // backward = 0: solve L y = b in place; backward = 1: solve L^T x = y in place.
+// Dinv holds the inverses of the 64 x 64 diagonal blocks (written by the factorisation),
+// so the diagonal step is a product.  Each CTA loads its share of a dependency's factor
+// tile before waiting for that dependency's flag.
 template <class TF>
-__global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L, int64_t n, TF *y,
+__global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L,
+                                                   const TF *__restrict__ Dinv, int64_t n, TF *y,
                                                    int *flags, int epoch, int32_t *err,
                                                    int backward) {
-    __shared__ TF Ld[NB][NB + 1];
     __shared__ TF xs[NB];
     __shared__ TF red[8][NB];
     __shared__ TF t[NB];
@@ -276,20 +296,32 @@ __global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L, int
     const int64_t r0 = (int64_t)i * NB;
     const int nb = (int)min((int64_t)NB, n - r0);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        int rr = e / NB, cc = e % NB;
-        Ld[rr][cc] = (rr < nb && cc < nb) ? L[(r0 + rr) * n + r0 + cc] : TF(0);
-    }
     if (tid == 0) abort_flag = 0;
-    // per-thread partial sums: forward rows w*8..w*8+7 over columns {lane, lane+32};
-    // backward columns {lane, lane+32} over rows w*8..w*8+7
-    TF acc[8];
+    TF acc0 = TF(0), acc1 = TF(0);   // backward: columns lane, lane + 32
+    TF accr[8];                      // forward: rows w*8 + q
 #pragma unroll
-    for (int q = 0; q < 8; q++) acc[q] = TF(0);
+    for (int q = 0; q < 8; q++) accr[q] = TF(0);
     __syncthreads();
     const int ndep = backward ? (nblk - 1 - i) : i;
     for (int d = 0; d < ndep; d++) {
         const int j = backward ? (nblk - 1 - d) : d;
+        const int64_t c0 = (int64_t)j * NB;
+        const int njb = (int)min((int64_t)NB, n - c0);
+        // this thread's factor values for dependency j (independent of x_j)
+        TF l0[8], l1[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int rr = w * 8 + q;
+            if (!backward) {
+                const TF *row = L + (r0 + rr) * n + c0;
+                l0[q] = (rr < nb && lane < njb) ? row[lane] : TF(0);
+                l1[q] = (rr < nb && lane + 32 < njb) ? row[lane + 32] : TF(0);
+            } else {
+                const TF *row = L + (c0 + rr) * n + r0;
+                l0[q] = (rr < njb && lane < nb) ? row[lane] : TF(0);
+                l1[q] = (rr < njb && lane + 32 < nb) ? row[lane + 32] : TF(0);
+            }
+        }
         if (tid == 0) {
             int spins = 0;
             while (ld_acquire_gpu(&flags[j]) != epoch) {
@@ -298,55 +330,39 @@ __global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L, int
                     abort_flag = 1;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __syncthreads();
         if (abort_flag) return;
-        const int64_t c0 = (int64_t)j * NB;
-        const int njb = (int)min((int64_t)NB, n - c0);
         if (tid < NB) xs[tid] = tid < njb ? __ldcg(&y[c0 + tid]) : TF(0);
         __syncthreads();
         if (!backward) {
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                int rr = w * 8 + q;
-                if (rr < nb) {
-                    const TF *row = L + (r0 + rr) * n + c0;
-                    TF v = lane < njb ? row[lane] * xs[lane] : TF(0);
-                    if (lane + 32 < njb) v += row[lane + 32] * xs[lane + 32];
-                    acc[q] += v;
-                }
-            }
+            for (int q = 0; q < 8; q++) accr[q] += l0[q] * xs[lane] + l1[q] * xs[lane + 32];
         } else {
-            TF a0 = TF(0), a1 = TF(0);
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-                int rr = w * 8 + q;
-                if (rr < njb) {
-                    const TF *row = L + (c0 + rr) * n + r0;
-                    if (lane < nb) a0 += row[lane] * xs[rr];
-                    if (lane + 32 < nb) a1 += row[lane + 32] * xs[rr];
-                }
+                const TF xv = xs[w * 8 + q];
+                acc0 += l0[q] * xv;
+                acc1 += l1[q] * xv;
             }
-            acc[0] += a0;
-            acc[1] += a1;
         }
         __syncthreads();   // xs is rewritten by the next dependency
     }
-    // reduce the partial sums into t = b - (sum over dependencies)
+    // t = b - (sum over dependencies)
     if (!backward) {
 #pragma unroll
         for (int q = 0; q < 8; q++) {
-            TF v = acc[q];
+            TF v = accr[q];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if (lane == 0) red[0][w * 8 + q] = v;
         }
         __syncthreads();
         if (tid < NB) t[tid] = tid < nb ? y[r0 + tid] - red[0][tid] : TF(0);
     } else {
-        red[w][lane] = acc[0];
-        red[w][lane + 32] = acc[1];
+        red[w][lane] = acc0;
+        red[w][lane + 32] = acc1;
         __syncthreads();
         if (tid < NB) {
             TF v = TF(0);
@@ -355,42 +371,46 @@ __global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L, int
         }
     }
     __syncthreads();
-    // diagonal block, one warp, column-oriented updates (lane owns rows lane, lane+32)
-    if (w == 0) {
-        TF t0 = t[lane], t1 = t[lane + 32];
-        if (!backward) {
-            for (int c = 0; c < nb; c++) {
-                TF tc = c < 32 ? __shfl_sync(0xffffffffu, t0, c) : __shfl_sync(0xffffffffu, t1, c - 32);
-                TF yc = tc / Ld[c][c];
-                if (lane == (c & 31)) { if (c < 32) t0 = yc; else t1 = yc; }
-                if (lane > c) t0 -= Ld[lane][c] * yc;
-                if (lane + 32 > c) t1 -= Ld[lane + 32][c] * yc;
-            }
-        } else {
-            for (int c = nb - 1; c >= 0; c--) {
-                TF tc = c < 32 ? __shfl_sync(0xffffffffu, t0, c) : __shfl_sync(0xffffffffu, t1, c - 32);
-                TF xc = tc / Ld[c][c];
-                if (lane == (c & 31)) { if (c < 32) t0 = xc; else t1 = xc; }
-                if (lane < c) t0 -= Ld[c][lane] * xc;
-                if (lane + 32 < c) t1 -= Ld[c][lane + 32] * xc;
+    // diagonal block: y_i = Dinv_i t (forward) or Dinv_i^T t (backward)
+    const TF *Di = Dinv + (int64_t)i * NB * NB;
+    if (!backward) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int rr = w * 8 + q;
+            TF v = Di[rr * NB + lane] * t[lane] + Di[rr * NB + lane + 32] * t[lane + 32];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0 && rr < nb) {
+                y[r0 + rr] = v;
+                __threadfence();
             }
         }
-        if (lane < nb) y[r0 + lane] = t0;
-        if (lane + 32 < nb) y[r0 + lane + 32] = t1;
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) st_release_gpu(&flags[i], epoch);
+    } else {
+        TF v0 = TF(0), v1 = TF(0);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int rr = w * 8 + q;
+            v0 += Di[rr * NB + lane] * t[rr];
+            v1 += Di[rr * NB + lane + 32] * t[rr];
+        }
+        red[w][lane] = v0;
+        red[w][lane + 32] = v1;
+        __syncthreads();
+        if (tid < nb) {
+            TF v = TF(0);
+            for (int q = 0; q < 8; q++) v += red[q][tid];
+            y[r0 + tid] = v;
+            __threadfence();
+        }
     }
+    __syncthreads();
+    if (tid == 0) st_release_gpu(&flags[i], epoch);
 }
 
 template <class TF>
 int cholesky_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
     const size_t sh = 2 * NB * (NB + 1) * sizeof(TF);
-    FEM3_CUDA(cudaFuncSetAttribute(k_potrf_inv<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    FEM3_CUDA(cudaFuncSetAttribute(k_trsm_gemm<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    FEM3_CUDA(cudaFuncSetAttribute(k_syrk<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    TF *Linv = reinterpret_cast<TF *>(m->vec64[5]);   // NB x NB scratch
     for (int64_t k0 = 0; k0 < n; k0 += NB) {
+        TF *Linv = reinterpret_cast<TF *>(m->dinv) + (k0 / NB) * NB * NB;   // kept for the solves
         k_potrf_inv<TF><<<1, 256, sh, s>>>(A, n, (int)k0, Linv, m->err);
         note_launch(m);
         int64_t rest = n - k0 - NB;
@@ -423,8 +443,9 @@ int trsv_t(const TF *L, int64_t n, TF *y, cudaStream_t s, Mesh *m) {
             int epoch = ++m->flag_epoch;
             int32_t *err = m->err;
             int *flags = m->flags;
-            void *args[] = {(void *)&L, (void *)&n, (void *)&y, (void *)&flags, (void *)&epoch,
-                            (void *)&err, (void *)&backward};
+            const TF *Dinv = reinterpret_cast<const TF *>(m->dinv);
+            void *args[] = {(void *)&L, (void *)&Dinv, (void *)&n, (void *)&y, (void *)&flags,
+                            (void *)&epoch, (void *)&err, (void *)&backward};
             FEM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_trsv_wave<TF>, dim3(nblk),
                                                   dim3(256), args, 0, s));
             note_launch(m);
@@ -455,45 +476,60 @@ int trsv_t(const TF *L, int64_t n, TF *y, cudaStream_t s, Mesh *m) {
 }
 
 // ---------------------------------------------------------------------------------
-// matrix-free FP64 operator from the tables; one CTA per (bin) of one axis
+// matrix-free FP64 operator from the tables:
+//   A u = sum_i s_i K_i (L_i^T W (R_i u) + R_i^T W (L_i u))
+// pass 1: one thread per Gauss point (slot) of an axis, yL = w (L u), yR = w (R u);
+// pass 2: one warp per template row (bin, local dof), z = L yR + R yL, added into Au.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_apply_tables(
+__global__ void __launch_bounds__(256) k_apply_rows(
     const double *__restrict__ tabL, const double *__restrict__ tabR,
-    const int32_t *__restrict__ gp_off, const int32_t *__restrict__ gp_idx,
+    const int32_t *__restrict__ slot_bin, const int32_t *__restrict__ gp_off,
+    const int32_t *__restrict__ gp_idx, const int32_t *__restrict__ dof_off,
+    const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
+    const int32_t *__restrict__ tab_ld, const double *__restrict__ gw, int64_t n_gp,
+    const double *__restrict__ u, double *yL, double *yR) {
+    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (slot >= n_gp) return;
+    const int b = slot_bin[slot];
+    const int r = (int)(slot - gp_off[b]);
+    const int d0 = dof_off[b], D = dof_off[b + 1] - d0, ld = tab_ld[b];
+    const double *Lc = tabL + tab_off[b] + r, *Rc = tabR + tab_off[b] + r;
+    double sl0 = 0, sl1 = 0, sr0 = 0, sr1 = 0;
+    int c = 0;
+    for (; c + 1 < D; c += 2) {
+        const double u0 = __ldg(u + dof_idx[d0 + c]), u1 = __ldg(u + dof_idx[d0 + c + 1]);
+        sl0 = fma(Lc[(int64_t)c * ld], u0, sl0);
+        sr0 = fma(Rc[(int64_t)c * ld], u0, sr0);
+        sl1 = fma(Lc[(int64_t)(c + 1) * ld], u1, sl1);
+        sr1 = fma(Rc[(int64_t)(c + 1) * ld], u1, sr1);
+    }
+    if (c < D) {
+        const double u0 = __ldg(u + dof_idx[d0 + c]);
+        sl0 = fma(Lc[(int64_t)c * ld], u0, sl0);
+        sr0 = fma(Rc[(int64_t)c * ld], u0, sr0);
+    }
+    const double wv = gw[gp_idx[slot]];
+    yL[slot] = wv * (sl0 + sl1);
+    yR[slot] = wv * (sr0 + sr1);
+}
+
+__global__ void __launch_bounds__(256) k_apply_cols(
+    const double *__restrict__ tabL, const double *__restrict__ tabR,
+    const int32_t *__restrict__ row_bin, const int32_t *__restrict__ gp_off,
     const int32_t *__restrict__ dof_off, const int32_t *__restrict__ dof_idx,
-    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
-    const double *__restrict__ gw, const double *__restrict__ u, double sK, double *Au) {
-    extern __shared__ double sm[];
-    const int bin = blockIdx.x;
-    const int D = dof_off[bin + 1] - dof_off[bin];
-    const int G = gp_off[bin + 1] - gp_off[bin];
-    if (D == 0 || G == 0) return;
-    const int ld = tab_ld[bin];
-    const double *L = tabL + tab_off[bin], *R = tabR + tab_off[bin];
-    const int32_t *dofs = dof_idx + dof_off[bin];
-    const int32_t *slots = gp_idx + gp_off[bin];
-    double *ub = sm, *yL = sm + D, *yR = yL + G;
-    for (int c = threadIdx.x; c < D; c += blockDim.x) ub[c] = u[dofs[c]];
-    __syncthreads();
-    for (int r = threadIdx.x; r < G; r += blockDim.x) {
-        double sl = 0, sr = 0;
-        for (int c = 0; c < D; c++) {
-            sl = fma(L[(int64_t)c * ld + r], ub[c], sl);
-            sr = fma(R[(int64_t)c * ld + r], ub[c], sr);
-        }
-        double w = gw[slots[r]];
-        yL[r] = w * sl;
-        yR[r] = w * sr;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = warp; c < D; c += nw) {
-        double z = 0;
-        for (int r = lane; r < G; r += 32)
-            z = fma(L[(int64_t)c * ld + r], yR[r], fma(R[(int64_t)c * ld + r], yL[r], z));
-        for (int o = 16; o > 0; o >>= 1) z += __shfl_down_sync(0xffffffffu, z, o);
-        if (lane == 0) atomicAdd(&Au[dofs[c]], sK * z);
-    }
+    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld, int64_t n_rows,
+    const double *__restrict__ yL, const double *__restrict__ yR, double sK, double *Au) {
+    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n_rows) return;
+    const int b = row_bin[row];
+    const int c = (int)(row - dof_off[b]);
+    const int g0 = gp_off[b], G = gp_off[b + 1] - g0, ld = tab_ld[b];
+    const double *Lr = tabL + tab_off[b] + (int64_t)c * ld, *Rr = tabR + tab_off[b] + (int64_t)c * ld;
+    double z = 0;
+    for (int r = lane; r < G; r += 32) z = fma(Lr[r], yR[g0 + r], fma(Rr[r], yL[g0 + r], z));
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_down_sync(0xffffffffu, z, o);
+    if (lane == 0) atomicAdd(&Au[dof_idx[row]], sK * z);
 }
 
 // per-axis forms sum_g w_g ((L lam)(R u) + (R lam)(L u)) (adjoint), one CTA per bin
@@ -624,22 +660,69 @@ int load_vector_T(Mesh *m, const double *lam_d, double *out_d) {
     return FEM3_OK;
 }
 
+// The factorisation is a fixed sequence of ~3 n/64 launches for a given handle and
+// precision.  The first factorisation of a handle launches it directly; a second one
+// (a new assemble with other alpha or K on the same mesh) captures the sequence into a
+// CUDA graph on a private stream, and later ones replay the graph on the caller's stream.
+static int chol_attributes() {
+    const size_t sh64 = 2 * NB * (NB + 1) * sizeof(double), sh32 = 2 * NB * (NB + 1) * sizeof(float);
+    FEM3_CUDA(cudaFuncSetAttribute(k_potrf_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh64));
+    FEM3_CUDA(cudaFuncSetAttribute(k_trsm_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh64));
+    FEM3_CUDA(cudaFuncSetAttribute(k_syrk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh64));
+    FEM3_CUDA(cudaFuncSetAttribute(k_potrf_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32));
+    FEM3_CUDA(cudaFuncSetAttribute(k_trsm_gemm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32));
+    FEM3_CUDA(cudaFuncSetAttribute(k_syrk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32));
+    return FEM3_OK;
+}
+
 int factor(Mesh *m) {
-    if (m->precision == FEM3_FP64) return cholesky_t<double>(m->A64, m->n_dof, m->stream, m);
-    return cholesky_t<float>(m->A32, m->n_dof, m->stream, m);
+    const int slot = m->precision == FEM3_FP64 ? 0 : 1;
+    FEM3_TRY(chol_attributes());
+    if (m->factor_count[slot]++ == 0) {
+        if (slot == 0) return cholesky_t<double>(m->A64, m->n_dof, m->stream, m);
+        return cholesky_t<float>(m->A32, m->n_dof, m->stream, m);
+    }
+    if (!m->chol_exec[slot]) {
+        cudaStream_t cs;
+        FEM3_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        int st = FEM3_OK;
+        if (e == cudaSuccess) {
+            const int64_t launches0 = m->launches;
+            st = slot == 0 ? cholesky_t<double>(m->A64, m->n_dof, cs, m)
+                           : cholesky_t<float>(m->A32, m->n_dof, cs, m);
+            m->chol_launches[slot] = m->launches - launches0;
+            m->launches = launches0;
+            e = cudaStreamEndCapture(cs, &g);
+        }
+        if (e == cudaSuccess && st == FEM3_OK)
+            e = cudaGraphInstantiate(&m->chol_exec[slot], g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        if (st != FEM3_OK) return st;
+        if (e != cudaSuccess) return cuda_error(e, "factorisation graph capture");
+    }
+    FEM3_CUDA(cudaGraphLaunch(m->chol_exec[slot], m->stream));
+    m->launches += m->chol_launches[slot];
+    return FEM3_OK;
 }
 
 int apply_A64(Mesh *m, const double *u_d, double *Au_d) {
     cudaStream_t s = m->stream;
-    FEM3_CUDA(cudaFuncSetAttribute(k_apply_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(double) * 3 * kMaxBinItems)));
     FEM3_CUDA(cudaMemsetAsync(Au_d, 0, sizeof(double) * m->n_dof, s));
+    double *yL = m->ybuf, *yR = m->ybuf + m->n_gp;
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
-        size_t sh = sizeof(double) * (B.max_dof + 2 * B.max_gp);
-        k_apply_tables<<<B.n_bins, 256, sh, s>>>(m->tabL[axis], m->tabR[axis], B.gp_off, B.gp_idx,
-                                                  B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, m->gw,
-                                                  u_d, m->sK[axis], Au_d);
+        if (B.n_tmpl == 0) continue;
+        k_apply_rows<<<g256(m->n_gp), 256, 0, s>>>(m->tabL[axis], m->tabR[axis], B.slot_bin,
+                                                    B.gp_off, B.gp_idx, B.dof_off, B.dof_idx,
+                                                    B.tab_off, B.tab_ld, m->gw, m->n_gp, u_d, yL,
+                                                    yR);
+        note_launch(m);
+        k_apply_cols<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
+            m->tabL[axis], m->tabR[axis], B.row_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
+            B.tab_ld, B.n_tmpl, yL, yR, m->sK[axis], Au_d);
         note_launch(m);
     }
     FEM3_CUDA(cudaGetLastError());

@@ -38,31 +38,55 @@ struct WalkGeom {
     int max_steps;
 };
 
-// go-out parameter of the ray in tet t: min over exit candidates of b~_k * nd_k
+// Monotone map of a double to a signed 64-bit key (same order as the doubles), so that
+// comparisons and minima run on the integer pipes; the FP64 pipe is the scarce unit.
+__device__ __forceinline__ long long ord_key(double v) {
+    long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double key_double(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+// lambda <= eps for every non-NaN lambda, on the integer pipe: IEEE bit patterns of
+// non-negative doubles are ordered like the values, negative ones are negative integers
+__device__ __forceinline__ bool le_eps(double lam) {
+    return __double_as_longlong(lam) <= __double_as_longlong(kEpsLambda);
+}
+
+// go-out parameter of the ray in tet t: min over exit candidates k (dir * dlambda_k/dx
+// < 0, i.e. inv_k of the sign of -dir) of -b~_k / d~_k = -dir * b~_k * inv_k
 __device__ __forceinline__ double tet_rmax(const WalkGeom &W, int32_t t, int axis, int dir,
                                            double x0, double x1, double x2, double b[4]) {
     const double2 *Mt = reinterpret_cast<const double2 *>(W.M + 16 * (int64_t)t);
-    const double *iv = W.inv + 12 * (int64_t)t + 4 * axis;
-    double rmax = INFINITY;
+    const double2 *ivp = reinterpret_cast<const double2 *>(W.inv + 12 * (int64_t)t + 4 * axis);
+    const double2 iv0 = ivp[0], iv1 = ivp[1];
+    const double ivk[4] = {iv0.x, iv0.y, iv1.x, iv1.y};
+    long long kmin = ord_key(INFINITY);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         double2 a = Mt[2 * k], c = Mt[2 * k + 1];
         b[k] = fma(c.y, x2, fma(c.x, x1, fma(a.y, x0, a.x)));
-        double nd = dir > 0 ? -iv[k] : iv[k];  // -dir / (dlambda_k/dx_axis)
-        if (nd > 0.0) rmax = fmin(rmax, b[k] * nd);
+        const long long ib = __double_as_longlong(ivk[k]);
+        const bool cand = dir > 0 ? (ib < 0) : (ib > 0);
+        if (cand) {
+            double r = dir > 0 ? -(b[k] * ivk[k]) : b[k] * ivk[k];
+            long long kr = ord_key(r);
+            kmin = kr < kmin ? kr : kmin;
+        }
     }
-    return rmax;
+    return key_double(kmin);
 }
 
 // next tet after leaving t at parameter rmax; -1 at the boundary, -2 on a bad pattern
 __device__ int32_t next_tet(const WalkGeom &W, int32_t t, int axis, int dir, double x0,
                             double x1, double x2, const double b[4], double rmax) {
     const double *Mt = W.M + 16 * (int64_t)t;
+    const double rs = dir > 0 ? rmax : -rmax;
     int zmask = 0;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        double lam = fma(rmax, dir * Mt[4 * k + 1 + axis], b[k]);
-        if (lam <= kEpsLambda) zmask |= 1 << k;
+        double lam = fma(rs, Mt[4 * k + 1 + axis], b[k]);
+        if (le_eps(lam)) zmask |= 1 << k;
     }
     int nz = __popc(zmask);
     if (nz == 1) return W.nbr[4 * (int64_t)t + (__ffs(zmask) - 1)];
@@ -121,7 +145,46 @@ struct TableArgs {
     double *tab;                          // L (side 0) or R (side 1) of this axis
     double p_exp;                         // 1 - gamma
     double coef;                          // +1/Gamma(2-gamma) (left) or -1/Gamma(2-gamma)
+    const double *__restrict__ pow_cell;  // [256][8] local Taylor coefficients of m^p, m_c
+    const double *__restrict__ pow_exp;   // [128] 2^(e p) for e = -64 .. 63
 };
+
+// r^p for r > 0 by table-driven range reduction (after Tang's table-driven elementary
+// functions): r = 2^e m with m in [1, 2); the top 8 fraction bits pick a cell of width
+// 1/256 with centre m_c; m^p = sum_k C(p,k) m_c^(p-k) (m - m_c)^k, k <= 4, whose
+// truncation error is below 1e-15 relative for p in [0, 1); 2^(e p) from a table.
+// Six FP64 operations; exponents outside [-64, 63] fall back to pow.
+__device__ __forceinline__ double pow_table(double r, double p, const double *__restrict__ cell,
+                                            const double *__restrict__ pexp) {
+    const long long bits = __double_as_longlong(r);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    if (e < -64 || e > 63) return pow(r, p);
+    const int j = (int)((bits >> 44) & 0xff);
+    const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+    const double *c = cell + 8 * j;
+    const double d = m - __ldg(c + 5);
+    const double q = fma(fma(fma(fma(__ldg(c + 4), d, __ldg(c + 3)), d, __ldg(c + 2)), d,
+                             __ldg(c + 1)), d, __ldg(c));
+    return __ldg(pexp + e + 64) * q;
+}
+
+// coefficients of pow_table for p = 1 - gamma_axis: cell j of axis a at
+// cell[a][j][0..4] (Taylor terms), cell[a][j][5] = m_c; pexp[a][e + 64] = 2^(e p)
+__global__ void k_pow_tables(double p0, double p1, double p2, double *cell, double *pexp) {
+    const int a = blockIdx.x, j = threadIdx.x;   // 3 blocks x 256 threads
+    const double p = a == 0 ? p0 : (a == 1 ? p1 : p2);
+    const double mc = 1.0 + (2.0 * j + 1.0) / 512.0;
+    double binom = 1.0;
+    double *c = cell + (size_t)a * 256 * 8 + 8 * j;
+    for (int k = 0; k <= 4; k++) {
+        c[k] = binom * pow(mc, p - k);
+        binom = binom * (p - k) / (k + 1);
+    }
+    c[5] = mc;
+    c[6] = 0.0;
+    c[7] = 0.0;
+    if (j < 128) pexp[a * 128 + j] = exp2((double)(j - 64) * p);
+}
 
 // grid: x over slots of one axis, y = side (0 left, 1 right); one launch per axis
 __global__ void __launch_bounds__(128) k_walk_tables(WalkGeom W, TableArgs A0, TableArgs A1,
@@ -153,7 +216,7 @@ __global__ void __launch_bounds__(128) k_walk_tables(WalkGeom W, TableArgs A0, T
             double rmax = tet_rmax(W, t, axis, dir, x0, x1, x2, b);
             if (!(rmax < INFINITY)) break;
             if (rmax - r_prev > W.eps_r) {
-                double P = pow(rmax, A.p_exp);
+                double P = pow_table(rmax, A.p_exp, A.pow_cell, A.pow_exp);
                 double c = A.coef * (P - P_prev);
                 const double *Mt = W.M + 16 * (int64_t)t;
                 int32_t nj[4], nc[4];
@@ -266,6 +329,13 @@ int walk_tables(Mesh *m, const double alpha[3]) {
     WalkGeom W = make_geom(m);
     unsigned long long *segc = reinterpret_cast<unsigned long long *>(m->norms + 8);
     FEM3_CUDA(cudaMemsetAsync(segc, 0, sizeof(unsigned long long), s));
+    if (!m->pow_cell) {
+        FEM3_TRY(dev_alloc_t(m, &m->pow_cell, 3 * 256 * 8));
+        FEM3_TRY(dev_alloc_t(m, &m->pow_exp, 3 * 128));
+    }
+    k_pow_tables<<<3, 256, 0, s>>>(1.0 - alpha[0] / 2.0, 1.0 - alpha[1] / 2.0, 1.0 - alpha[2] / 2.0,
+                                   m->pow_cell, m->pow_exp);
+    note_launch(m);
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
         FEM3_CUDA(cudaMemsetAsync(m->tabL[axis], 0, sizeof(double) * B.tab_elems, s));
@@ -277,7 +347,8 @@ int walk_tables(Mesh *m, const double alpha[3]) {
         double gamma = alpha[axis] / 2.0;
         double ig = 1.0 / tgamma(2.0 - gamma);
         TableArgs A0{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
-                     B.tab_ld, m->tabL[axis], 1.0 - gamma, ig};
+                     B.tab_ld, m->tabL[axis], 1.0 - gamma, ig,
+                     m->pow_cell + (size_t)axis * 256 * 8, m->pow_exp + axis * 128};
         TableArgs A1 = A0;
         A1.tab = m->tabR[axis];
         A1.coef = -ig;

@@ -104,7 +104,7 @@ def _ptr(x):
 # ---------------------------------------------------------------------------------
 # functions with the C ABI's names
 # ---------------------------------------------------------------------------------
-def mesh_upload(verts, tets, bin_scale: float = 1.0, max_steps: int = 0, profile: bool = False,
+def mesh_upload(verts, tets, bin_scale: float = 0.5, max_steps: int = 0, profile: bool = False,
                 stream=None):
     lib = load_library()
     opt = Options(bin_scale, max_steps, 1 if profile else 0)
@@ -191,7 +191,7 @@ def mesh_free(h):
 class Mesh:
     """A mesh uploaded to the current CUDA device (torch's current stream by default)."""
 
-    def __init__(self, verts, tets, bin_scale: float = 1.0, max_steps: int = 0,
+    def __init__(self, verts, tets, bin_scale: float = 0.5, max_steps: int = 0,
                  profile: bool = False, stream=None):
         import torch
         self._torch = torch

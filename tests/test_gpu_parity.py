@@ -138,6 +138,39 @@ def test_tensor_core_split_products_reach_fp32_accuracy(name):
     m.free()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_adjoint_matches_oracle(precision):
+    """dJ/dK and dJ/df of J = 0.5 ||u(K, f) - u_obs||^2 against the oracle's adjoint (which is
+    itself pinned to central differences)."""
+    mesh, o, alpha, K = _case("cube7_jitter")
+    f = inputs.nodal_source(mesh, alpha, K) + 0.1
+    u_true = oracle.solve(o.assemble(alpha, K), o.load(f))
+    u_obs = inputs.noisy_observation(u_true, 0.01, 3)
+    J, dK_ref, df_ref, _ = o.adjoint(alpha, K, f, u_obs)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    m.assemble(alpha, K, precision)
+    u = m.solve(f, tol=1e-13)
+    dK, dJdf = m.adjoint(u, torch.from_numpy(u_obs).cuda(), tol=1e-13)
+    assert np.abs(dK - dK_ref).max() <= 1e-8 * np.abs(dK_ref).max()
+    assert _rel(dJdf.cpu().numpy(), df_ref) <= 1e-8
+    m.free()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_reassemble_same_mesh(precision):
+    """Three assembles with different K on one handle: the second and third factorisations
+    run from the captured factorisation graph and must match the oracle like the first."""
+    mesh, o, alpha, _ = _case("cube7_jitter")
+    f = inputs.nodal_source(mesh, alpha, (1.0, 1.0, 1.0))
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    for K in ((1.0, 2.0, 0.5), (0.7, 1.0, 1.3), (2.0, 0.5, 1.0)):
+        m.assemble(alpha, K, precision)
+        u = m.solve(f, tol=1e-13).cpu().numpy()
+        u_ref = oracle.solve(o.assemble(alpha, K), o.load(f))
+        assert np.linalg.norm(u - u_ref) <= 1e-8 * np.linalg.norm(u_ref), K
+    m.free()
+
+
 def test_load_vector():
     mesh, o, alpha, K = _case("cube3_jitter")
     m = fem3.Mesh(mesh.verts, mesh.tets)
