@@ -42,6 +42,24 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# DRAM bytes (read + write) of one k_walk_tables launch from the ncu capture summarised in
+# profiles/k_walk_tables_cube16_jitter.md, valid only for the kernel source it was taken
+# on (sha256 of csrc/walk.cu); otherwise the traffic is reported as unknown.
+WALK_TRAFFIC = {"walk_cu_sha256": None, "bytes_per_launch": None, "segments_per_launch": None}
+
+
+def _walk_traffic(segs_per_launch):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1811_03339_gb300", "csrc", "walk.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if WALK_TRAFFIC["walk_cu_sha256"] != sha or not WALK_TRAFFIC["bytes_per_launch"]:
+        return None
+    return WALK_TRAFFIC["bytes_per_launch"]
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -191,7 +209,7 @@ def run_ours(args):
     def step(precision, profile=False, keep=False):
         m = fem3.Mesh(verts_d, tets_d, bin_scale=args.bin_scale, profile=profile)
         m.assemble(alpha, K, precision)
-        u = m.solve(f_d, tol=1e-12)
+        u = m.solve(f_d, tol=args.tol)
         if keep:
             return m, u
         m.free()
@@ -248,23 +266,29 @@ def run_ours(args):
     rel_mix_fp64 = float(torch.linalg.norm(u_mix - u64) / torch.linalg.norm(u64))
 
     # walk+tables kernel: 3 launches per step (one per axis), timed live by the library's
-    # events on the launch stream
+    # events on the launch stream.  Algorithmic FP64 flops per walked segment:
+    # 24 (b~ = lambda_T(x_g), 12 FMA) + 2 (go-out ratios of ~2 exit candidates)
+    # + 8 (exit zero pattern, 4 FMA) + 1 (length test) + 10 (power r^(1-gamma):
+    # 1 sub, 4 FMA, 1 mul) + 2 (coefficient) + 8 (table update, 4 FMA) = 55.
     walk_ms = stages[2] / 3.0
     segs_per_launch = cnt["segments"] / 3.0
-    fp64_flops_per_seg = 46.0
+    fp64_flops_per_seg = 55.0
     walk_flops = fp64_flops_per_seg * segs_per_launch
     fp64_peak_gflops = 1250.0
+    traffic = _walk_traffic(segs_per_launch)
     roofline = {
         "kernel": "k_walk_tables",
         "bound": "alu", "unit": "GFLOP/s (FP64)",
         "achieved": walk_flops / (walk_ms * 1e-3) / 1e9,
         "peak": fp64_peak_gflops,
-        "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
+        "peak_source": "GB300 FP64 rate derived from unit counts and clocks: 152 SMs x 2 "
+                       "DFMA/clk x 2 flops x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25; a DFMA "
+                       "loop measured 1,249.6 GFLOP/s on this pool)",
         "frac": walk_flops / (walk_ms * 1e-3) / 1e9 / fp64_peak_gflops,
-        "traffic": None,
+        "traffic": traffic,
         "launch_ms": walk_ms,
-        "algorithmic_unit": f"{fp64_flops_per_seg:.0f} FP64 flops per walked segment "
-                            "(pow excluded)",
+        "algorithmic_unit": f"{fp64_flops_per_seg:.0f} FP64 flops per walked segment, "
+                            f"{segs_per_launch:.0f} segments per launch (one axis)",
     }
 
     # --- end to end through the C ABI with host buffers -----------------------------
@@ -280,7 +304,7 @@ def run_ours(args):
         e0.record(stream)
         mh = fem3.Mesh(verts_h.numpy(), tets_h.numpy(), bin_scale=args.bin_scale)
         mh.assemble(alpha, K, args.precision)
-        u = mh.solve(f_h.numpy(), tol=1e-12)
+        u = mh.solve(f_h.numpy(), tol=args.tol)
         u_host = u.cpu()
         e1.record(stream)
         torch.cuda.synchronize()
@@ -295,6 +319,11 @@ def run_ours(args):
     # --- kernel launches per step: counted by the library at every launch ------------
     launches = cnt["launches"] * args.steps
     launch_note = f"{cnt['launches']} libfem3 kernel launches per step (library counter)"
+
+    # --- batched workload: 64 uneven cube meshes, 16 right-hand sides each -----------
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, torch, fem3, inputs, stream)
 
     line = None
     if rank == 0:
@@ -331,16 +360,60 @@ def run_ours(args):
                                         "factor", "solve_refine"],
                                        [round(x, 4) for x in stages64])),
             "segments_per_step": cnt["segments"],
-            "refinement": {"iterations": ir_iters, "final_rel_residual": ir_resid},
+            "refinement": {"iterations": ir_iters, "final_rel_residual": ir_resid, "tol": args.tol},
             "table_bytes": cnt["table_bytes"],
             "contraction": {"bin_dense_gflop": ctr_flops / 1e9,
                             "gflops": ctr_flops / (stages[3] * 1e-3) / 1e9 if stages[3] > 0 else None},
             "peaks_source": src,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_batch(args, torch, fem3, inputs, stream):
+    """64 cube meshes with n ~ U{6..20} cells per side (6 tets per cell), alpha_i ~
+    U(1.1, 1.9) per mesh and axis, K = 1, 16 N(0,1) nodal right-hand sides per mesh;
+    mesh records uploaded once; one step = fem3_batch_run (walk, tables, contraction,
+    load, factorisation and refinement of every mesh)."""
+    specs = inputs.batch_specs(64, seed=3, nmin=6, nmax=20)
+    meshes = [inputs.cube_mesh(sp["n"]) for sp in specs]
+    alpha = np.array([sp["alpha"] for sp in specs])
+    K = np.ones((len(specs), 3))
+    fs = [torch.from_numpy(inputs.random_rhs(m.n_nodes, 16, seed=100 + i)).cuda()
+          for i, m in enumerate(meshes)]
+    paths = sum(3 * 4 * m.n_tets for m in meshes)
+    b = fem3.Batch([(m.verts, m.tets) for m in meshes])
+
+    def timed(precision, k, warm):
+        for _ in range(warm):
+            b.run(alpha, K, fs, precision, tol=args.tol)
+        ts = []
+        for _ in range(k):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            us = b.run(alpha, K, fs, precision, tol=args.tol)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sum(ts) / len(ts), us
+
+    ms_mix, u_mix = timed(args.precision, 3, 1)
+    iters = list(b.iters)
+    ms_64, u_64 = timed("fp64", 1, 1)
+    err = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(u_mix, u_64))
+    out = {"workload": "64 Kuhn cubes, n ~ U{6..20} cells per side, 16 right-hand sides each",
+           "tets": int(sum(m.n_tets for m in meshes)),
+           "dofs": int(sum(b.n_dof)), "paths_per_step": paths,
+           "ms_per_step": ms_mix, "paths_per_s": paths / (ms_mix / 1e3),
+           "fp64_ms_per_step": ms_64, "mixed_vs_fp64_speedup": ms_64 / ms_mix,
+           "u_rel_err_mixed_vs_fp64_max": err, "refinement_sweeps_max": max(iters),
+           "precision": args.precision}
+    b.free()
+    return out
 
 
 def main():
@@ -349,8 +422,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["tf32x3", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched workload")
+    ap.add_argument("--tol", type=float, default=1e-10,
+                    help="relative residual at which refinement stops (the mixed form targets "
+                         "1e-8 relative solution error; the FP64 form is direct)")
     ap.add_argument("--bin-scale", type=float, default=0.5,
                     help="transverse bin width in mean cell sizes (template granularity)")
     args = ap.parse_args()

@@ -195,6 +195,38 @@ int fem3_counters(fem3_mesh m, int64_t *segments, double *contract_flops,
                   int64_t *table_bytes, int64_t *launches);
 
 /*
+ * Batches of meshes (not in the paper, which assembles one mesh at a time).
+ *
+ * fem3_batch_create - upload n_meshes meshes; arrays as in fem3_mesh_upload, one
+ *   pointer and size per mesh (host arrays of pointers to host or device data).
+ *   Synchronises `stream`.
+ * fem3_batch_mesh - the handle of mesh i (owned by the batch: do not free it); use it
+ *   for fem3_mesh_info, fem3_paths or fem3_table_rows.
+ * fem3_batch_run - assemble and solve every mesh of the batch.
+ *   One launch walks every Gauss-point line of every mesh (Section 2.2, 2.1 tables);
+ *   contraction, load vector and factorisation of each mesh run on internal streams;
+ *   each refinement sweep solves all meshes in one batched triangular solve.
+ *   alpha, K  host float64 [n_meshes][3].
+ *   f         host array of n_meshes device pointers, each column-major [n_nodes_i][nrhs].
+ *   u         host array of n_meshes device pointers, each column-major [n_dof_i][nrhs].
+ *   nrhs      1..16.  iters, resid: host [n_meshes] or NULL (refinement sweeps and the
+ *             largest final relative residual of each mesh; FP64 solves directly).
+ *   Synchronises `stream`; work is ordered after earlier work on `stream`.
+ *   Errors: as fem3_assemble / fem3_solve, the text names the mesh.
+ * fem3_batch_free - release the batch and its meshes.
+ */
+typedef struct fem3_batch_s *fem3_batch;
+
+int fem3_batch_create(int n_meshes, const double *const *verts, const int64_t *n_nodes,
+                      const int32_t *const *tets, const int64_t *n_tets, const fem3_options *opt,
+                      void *stream, fem3_batch *out);
+int fem3_batch_mesh(fem3_batch b, int i, fem3_mesh *out);
+int fem3_batch_run(fem3_batch b, const double *alpha, const double *K, int precision,
+                   const double *const *f, int nrhs, double tol, int max_iter, double *const *u,
+                   int *iters, double *resid, void *stream);
+void fem3_batch_free(fem3_batch b);
+
+/*
  * fem3_spd_solve_static - solve A x = b for a dense symmetric positive definite matrix
  * without allocating any device memory.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc where they need a solve (code

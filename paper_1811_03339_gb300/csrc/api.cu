@@ -178,8 +178,8 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
     int st;
     stage_begin(m, 0);
     if ((st = dev_alloc_t(m, &m->err, ERR_COUNT)) != FEM3_OK) return fail(st);
-    if ((st = dev_alloc_t(m, &m->norms, 64)) != FEM3_OK) return fail(st);
-    if (cudaMallocHost(&m->h_norms, 64 * sizeof(double)) != cudaSuccess) {
+    if ((st = dev_alloc_t(m, &m->norms, 128)) != FEM3_OK) return fail(st);
+    if (cudaMallocHost(&m->h_norms, 128 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return fail(set_error(FEM3_E_OOM, "cudaMallocHost"));
     }
@@ -265,6 +265,10 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
         } else {
             FEM3_TRY(f32_to_f64(m->A32, A_out, n * n, m->stream));
             note_launch(m);
+            if (precision == FEM3_TF32X3) {   // the tensor-core path fills the lower triangle
+                FEM3_TRY(sym_from_lower(A_out, n, m->stream));
+                note_launch(m);
+            }
         }
     }
     return FEM3_OK;
@@ -390,7 +394,7 @@ int fem3_sync(fem3_mesh h, void *stream) {
     stage_collect(m);
     if (st == FEM3_OK) {
         unsigned long long segs = 0;
-        FEM3_CUDA(cudaMemcpy(&segs, m->norms + 8, sizeof(segs), cudaMemcpyDeviceToHost));
+        FEM3_CUDA(cudaMemcpy(&segs, m->norms + kSegCounterSlot, sizeof(segs), cudaMemcpyDeviceToHost));
         m->segments = (int64_t)segs;
     }
     return st;

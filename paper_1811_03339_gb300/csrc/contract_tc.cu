@@ -1,7 +1,7 @@
 // Tensor-core contraction X_b = L_b^T W R_b (TF32 x 3 split products, FP32 accumulate)
 // on sm_103a: TMA loads with 128-byte swizzle, tcgen05.mma issued by one thread, the
-// accumulator in tensor memory, tcgen05.ld epilogue adding s K (X + X^T) into the FP32
-// matrix.  Section 2.1 element sum restricted, bin by bin, to the Section 2.3 template.
+// accumulator in tensor memory, tcgen05.ld epilogue adding s K (X + X^T) into the lower
+// triangle of the FP32 matrix.  Section 2.1 element sum restricted, bin by bin, to the Section 2.3 template.
 //
 // Operands.  The FP64 tables of one axis are split into TF32 pairs v = hi + lo (each
 // rounded to TF32, cvt.rna) with the Gauss weights folded into R; they are stored as
@@ -120,10 +120,9 @@ __device__ __forceinline__ float tf32_rna(float x) {
 __global__ void __launch_bounds__(256) k_split_tf32(
     const double *__restrict__ tabL, const double *__restrict__ tabR,
     const int32_t *__restrict__ row_bin, const int32_t *__restrict__ dof_off,
-    const int32_t *__restrict__ gp_off, const int32_t *__restrict__ gp_idx,
+    const int32_t *__restrict__ gp_off, const double *__restrict__ w_slot,
     const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
-    const double *__restrict__ gw, int64_t n_rows, int Kp, float *Lhi, float *Llo, float *Rhi,
-    float *Rlo) {
+    int64_t n_rows, int Kp, float *Lhi, float *Llo, float *Rhi, float *Rlo) {
     const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n_rows) return;
@@ -136,7 +135,7 @@ __global__ void __launch_bounds__(256) k_split_tf32(
         float lh = 0.f, ll = 0.f, rh = 0.f, rl = 0.f;
         if (k < G) {
             const double l = tabL[src + k];
-            const double r = tabR[src + k] * __ldg(gw + gp_idx[g0 + k]);
+            const double r = tabR[src + k] * w_slot[g0 + k];
             lh = tf32_rna((float)l);
             ll = tf32_rna((float)(l - (double)lh));
             rh = tf32_rna((float)r);
@@ -262,9 +261,11 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(
                 const int c2 = nt * kBN + cb + q;
                 if (cb + q >= nvalid) break;
                 const int64_t j2 = dof_idx[row0 + c2];
-                const float x = sK * v[q];
-                atomicAdd(&A[j1 * n_dof + j2], x);
-                atomicAdd(&A[j2 * n_dof + j1], x);
+                // A = sK (X + X^T): X[c1][c2] and X[c2][c1] both land on the lower-triangle
+                // element (the factorisation reads only the lower triangle); the diagonal
+                // gets 2 X[c][c]
+                const float x = (j1 == j2 ? 2.f : 1.f) * sK * v[q];
+                atomicAdd(&A[(j1 > j2 ? j1 : j2) * n_dof + (j1 > j2 ? j2 : j1)], x);
             }
         }
     }
@@ -354,8 +355,8 @@ int contract_tc(Mesh *m) {
         }
         if (!B.tc_n_work) continue;
         k_split_tf32<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
-            m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.gp_idx, B.tab_off,
-            B.tab_ld, m->gw, B.n_tmpl, B.tc_Kp, B.tc_op[0], B.tc_op[1], B.tc_op[2], B.tc_op[3]);
+            m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot, B.tab_off,
+            B.tab_ld, B.n_tmpl, B.tc_Kp, B.tc_op[0], B.tc_op[1], B.tc_op[2], B.tc_op[3]);
         note_launch(m);
         CUtensorMap maps[4];
         for (int q = 0; q < 4; q++) FEM3_TRY(make_map(&maps[q], B.tc_op[q], B.n_tmpl, B.tc_Kp));

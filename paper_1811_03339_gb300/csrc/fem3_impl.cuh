@@ -48,6 +48,7 @@ constexpr double kEpsRRel = 1e-12;    // segment-length / tie tolerance, times t
 constexpr double kEpsDRel = 1e-12;    // |gradient| below this fraction of the largest: parallel
 
 constexpr int kMaxBinItems = 4096;    // max dofs or Gauss points in one transverse bin
+constexpr int kSegCounterSlot = 120;  // norms[120]: segment counter (norms[0..63] reductions)
 
 // Transverse bins of one axis: the plane of the two other coordinates is cut into an
 // nb0 x nb1 grid; a Gauss point belongs to the bin of its transverse position, a dof
@@ -60,6 +61,7 @@ struct AxisBins {
     int32_t *gp_idx = nullptr;   // [n_gp]       slot -> Gauss point (sorted along the axis)
     int32_t *slot_bin = nullptr; // [n_gp]       slot -> bin
     int32_t *slot_of_gp = nullptr; // [n_gp]     Gauss point -> slot
+    double *w_slot = nullptr;    // [n_gp]       Gauss weight of each slot
     int32_t *dof_off = nullptr;  // [n_bins+1]
     int32_t *dof_idx = nullptr;  // [n_tmpl]     sorted dof ids per bin
     int64_t *tab_off = nullptr;  // [n_bins]     element offset of the bin's table block
@@ -167,10 +169,28 @@ void stage_collect(Mesh *m);
 // exclusive scan of int32 counts into offsets [n+1]; returns total via device offsets[n]
 int scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, Mesh *m);
 
+// scratch of the batched walk (descriptor arrays; freed by the batch)
+struct BatchWalkScratch {
+    void *d_desc = nullptr, *h_desc = nullptr;
+    void *d_zptr = nullptr, *d_zlen = nullptr, *h_zptr = nullptr, *h_zlen = nullptr;
+};
+
+// one mesh of a batched triangular solve (device-resident descriptor)
+struct BatchTrsmDesc {
+    const void *L;      // factor, row-major n x n (float or double)
+    const void *dinv;   // inverses of the 64 x 64 diagonal blocks
+    void *y;            // right-hand sides / solutions, column-major [n][nrhs]
+    int64_t n;
+    int nblk;
+    int active;         // 0: skip this mesh
+};
+
 // translation-unit entry points
 int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d);
 int bins_build(Mesh *m);
 int walk_tables(Mesh *m, const double alpha[3]);
+int walk_tables_batch(Mesh *const *ms, int n, const double *alpha, cudaStream_t s,
+                      BatchWalkScratch *bs);
 int walk_paths(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, int cap,
                int32_t *tet_out, double *r0, double *r1, int32_t *nseg);
 int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double *rows);
@@ -185,7 +205,11 @@ int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter
 int apply_A64(Mesh *m, const double *u_d, double *Au_d);
 int axis_forms(Mesh *m, const double *u_d, const double *lam_d, double out[3]);
 int read_errors(Mesh *m, int32_t *h_err);
+int trsm_batch(const BatchTrsmDesc *d_desc, int n_mesh, int max_nblk, int nrhs, bool fp64,
+               cudaStream_t s);
+int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d);
 int f32_to_f64(const float *a, double *b, int64_t n, cudaStream_t s);
+int sym_from_lower(double *A, int64_t n, cudaStream_t s);
 int sub_vec(const double *a, const double *b, double *c, int64_t n, cudaStream_t s);
 // rel = ||b - Au|| / ||b|| (synchronises)
 int residual_norm(Mesh *m, const double *b, const double *Au, double *rel);

@@ -431,6 +431,12 @@ __global__ void k_row_bin(const int32_t *__restrict__ dof_off, int n_bins, int32
     for (int r = dof_off[b] + threadIdx.x; r < dof_off[b + 1]; r += blockDim.x) row_bin[r] = b;
 }
 
+__global__ void k_slot_weights(const int32_t *__restrict__ gp_idx, const double *__restrict__ gw,
+                               int64_t n_gp, double *w_slot) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s < n_gp) w_slot[s] = gw[gp_idx[s]];
+}
+
 __global__ void k_invert_slots(const int32_t *__restrict__ gp_idx, int64_t n_gp,
                                int32_t *slot_of_gp) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -634,6 +640,9 @@ int bins_build(Mesh *m) {
             k_row_bin<<<nb, 256, 0, s>>>(B.dof_off, nb, B.row_bin);
             note_launch(m);
         }
+        FEM3_TRY(dev_alloc_t(m, &B.w_slot, n_gp));
+        k_slot_weights<<<grid_for(n_gp), kThreads, 0, s>>>(B.gp_idx, m->gw, n_gp, B.w_slot);
+        note_launch(m);
         FEM3_TRY(dev_alloc_t(m, &B.slot_of_gp, n_gp));
         k_invert_slots<<<grid_for(n_gp), kThreads, 0, s>>>(B.gp_idx, n_gp, B.slot_of_gp);
         note_launch(m);

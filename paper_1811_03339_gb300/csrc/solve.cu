@@ -61,19 +61,20 @@ __global__ void k_load_T(const int32_t *__restrict__ tets, const double *__restr
 // ---------------------------------------------------------------------------------
 // Cholesky
 // ---------------------------------------------------------------------------------
-// Diagonal block: factor A_kk = L_kk L_kk^T in shared memory and form L_kk^{-1}.
-// Factor: right-looking elimination on the unscaled columns (a[i][c] -= a[i][j] a[c][j] /
-// a[j][j]), one barrier per column; the columns are scaled by 1/sqrt(pivot) at the end.
-// Thread t owns row t/4 and every fourth column of it.  Inverse: four lanes of a warp
-// solve L x = e_c for one column c (split inner products, shuffle reduction), no block
-// barrier.  Linv receives the inverse (row-major 64 x 64); a non-positive pivot records
-// 1 + its column.
+// Diagonal block: factor A_kk = L_kk L_kk^T in shared memory and form L_kk^{-1}
+// (512 threads).  Factor: right-looking elimination on the unscaled columns
+// (a[i][c] -= a[i][j] a[c][j] / a[j][j]), one barrier per column, eight threads per row;
+// the thread that finishes a pivot also stores its reciprocal, so each column costs one
+// division.  The columns are scaled by 1/sqrt(pivot) at the end.  Inverse: eight lanes
+// of a warp solve L x = e_c for one column c (split inner products, shuffle reduction)
+// with precomputed 1/L_rr, no block barrier.  Linv receives the inverse (row-major
+// 64 x 64); a non-positive pivot records 1 + its column.
 template <class TF>
-__global__ void __launch_bounds__(256) k_potrf_inv(TF *A, int64_t n, int k0, TF *Linv,
-                                                   int32_t *err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void potrf_inv_block(TF *A, int64_t n, int k0, TF *Linv, int32_t *err,
+                                unsigned char *smem_raw) {
     TF(*a)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
     TF(*li)[NB + 1] = a + NB;
+    __shared__ TF rinv[NB], rsq[NB], sq[NB];
     const int nb = (int)min((int64_t)NB, n - k0);
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
         int i = e / NB, j = e % NB;
@@ -81,48 +82,64 @@ __global__ void __launch_bounds__(256) k_potrf_inv(TF *A, int64_t n, int k0, TF 
                                      : (i == j ? TF(1) : TF(0));
     }
     __syncthreads();
-    const int row = threadIdx.x >> 2, q = threadIdx.x & 3;
+    if (threadIdx.x == 0) rinv[0] = a[0][0] > TF(0) ? TF(1) / a[0][0] : TF(1);
+    __syncthreads();
+    const int row = threadIdx.x >> 3, q = threadIdx.x & 7;
     for (int j = 0; j < NB - 1; j++) {
-        const TF piv = a[j][j];
         if (row > j) {
-            const TF f = a[row][j] / (piv > TF(0) ? piv : TF(1));
-            for (int c = j + 1 + q; c <= row; c += 4) a[row][c] -= f * a[c][j];
+            const TF f = a[row][j] * rinv[j];
+            TF cv[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int c = j + 1 + q + 8 * u;
+                cv[u] = c <= row ? a[c][j] : TF(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int c = j + 1 + q + 8 * u;
+                if (c <= row) a[row][c] -= f * cv[u];
+            }
+            // the owner of the next pivot publishes its reciprocal
+            if (row == j + 1 && q == 0) {
+                const TF d = a[j + 1][j + 1];
+                rinv[j + 1] = d > TF(0) ? TF(1) / d : TF(1);
+            }
         }
         __syncthreads();
     }
-    // pivots, scaling, pivot check
     if (threadIdx.x < NB) {
         const int j = threadIdx.x;
-        if (j < nb && !(a[j][j] > TF(0))) atomicCAS(&err[ERR_NOT_SPD], 0, k0 + j + 1);
+        const TF d = a[j][j];
+        if (j < nb && !(d > TF(0))) atomicCAS(&err[ERR_NOT_SPD], 0, k0 + j + 1);
+        const TF r = sqrt(d > TF(0) ? d : TF(1));
+        sq[j] = r;
+        rsq[j] = TF(1) / r;
     }
     __syncthreads();
-    {
-        // L[i][j] = a[i][j] / sqrt(a[j][j]) (i > j), L[j][j] = sqrt(a[j][j])
-        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-            int i = e / NB, j = e % NB;
-            TF d = a[j][j] > TF(0) ? a[j][j] : TF(1);
-            TF v = i == j ? sqrt(d) : (i > j ? a[i][j] / sqrt(d) : TF(0));
-            li[i][j] = v;   // li holds L for now
-        }
+    // L[i][j] = a[i][j] / sqrt(d_j) (i > j), L[j][j] = sqrt(d_j); li holds L
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, j = e % NB;
+        li[i][j] = i == j ? sq[j] : (i > j ? a[i][j] * rsq[j] : TF(0));
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        int i = e / nb, j = e % nb;
+        const int i = e / nb, j = e % nb;
         A[(int64_t)(k0 + i) * n + k0 + j] = li[i][j];
     }
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) a[e / NB][e % NB] = li[e / NB][e % NB];
+    if (threadIdx.x < NB) rinv[threadIdx.x] = rsq[threadIdx.x];   // 1 / L_rr
     __syncthreads();
-    // inverse: column c by lanes 4*(c%8) .. of warp c/8; X stored in li
     {
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        const int c = w * 8 + (lane >> 2), part = lane & 3;
+        const int c = w * 4 + (lane >> 3), part = lane & 7;
         for (int r = 0; r < NB; r++) {
             TF sacc = TF(0);
             if (r > c)
-                for (int k = c + part; k < r; k += 4) sacc += a[r][k] * li[k][c];
+                for (int k = c + part; k < r; k += 8) sacc += a[r][k] * li[k][c];
             sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
             sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
-            TF x = r < c ? TF(0) : ((r == c ? TF(1) : TF(0)) - sacc) / a[r][r];
+            sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
+            const TF x = r < c ? TF(0) : ((r == c ? TF(1) : TF(0)) - sacc) * rinv[r];
             __syncwarp();
             if (part == 0) li[r][c] = x;
             __syncwarp();
@@ -130,6 +147,13 @@ __global__ void __launch_bounds__(256) k_potrf_inv(TF *A, int64_t n, int k0, TF 
     }
     __syncthreads();
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Linv[e] = li[e / NB][e % NB];
+}
+
+template <class TF>
+__global__ void __launch_bounds__(512) k_potrf_inv(TF *A, int64_t n, int k0, TF *Linv,
+                                                   int32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    potrf_inv_block<TF>(A, n, k0, Linv, err, smem_raw);
 }
 
 // Panel rows [k0+NB, n): X = B L_kk^{-T}, i.e. X[r][c] = sum_k B[r][k] Linv[c][k].
@@ -163,43 +187,61 @@ __global__ void __launch_bounds__(256) k_trsm_gemm(TF *A, int64_t n, int k0, con
 }
 
 // trailing update of lower tiles: A[i][j] -= sum_c P[i][c] P[j][c], P = panel columns
+// (512 threads, 2 x 4 outputs each).  The CTA of tile (0, 0) updates the next diagonal
+// block and, when Linv_next is given, factors it right away (look-ahead), so that the
+// next panel solve can start as soon as this launch ends.
 template <class TF>
-__global__ void __launch_bounds__(256) k_syrk(TF *A, int64_t n, int k0, int ntile) {
+__global__ void __launch_bounds__(512) k_syrk(TF *A, int64_t n, int k0, TF *Linv_next,
+                                              int32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     // blockIdx.x enumerates lower tiles (ti >= tj) of the trailing matrix
     int idx = blockIdx.x, ti = 0;
     while (idx > ti) { idx -= ti + 1; ti++; }
     int tj = idx;
     const int64_t base = k0 + NB;
     const int64_t i0 = base + (int64_t)ti * NB, j0 = base + (int64_t)tj * NB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TF(*pi)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
-    TF(*pj)[NB + 1] = pi + NB;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        int r = e / NB, c = e % NB;
-        pi[r][c] = (i0 + r < n) ? A[(i0 + r) * n + k0 + c] : TF(0);
-        pj[r][c] = (j0 + r < n) ? A[(j0 + r) * n + k0 + c] : TF(0);
-    }
-    __syncthreads();
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    TF acc[4][4];
-    for (int a = 0; a < 4; a++)
-        for (int b = 0; b < 4; b++) acc[a][b] = TF(0);
-    for (int c = 0; c < NB; c++) {
-        TF u[4], v[4];
-        for (int a = 0; a < 4; a++) { u[a] = pi[ty * 4 + a][c]; v[a] = pj[tx * 4 + a][c]; }
-        for (int a = 0; a < 4; a++)
-            for (int b = 0; b < 4; b++) acc[a][b] = fma(u[a], v[b], acc[a][b]);
-    }
-    for (int a = 0; a < 4; a++) {
-        int64_t r = i0 + ty * 4 + a;
-        if (r >= n) continue;
-        for (int b = 0; b < 4; b++) {
-            int64_t c = j0 + tx * 4 + b;
-            if (c >= n || c > r) continue;
-            A[r * n + c] -= acc[a][b];
+    {
+        TF(*pi)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
+        TF(*pj)[NB + 1] = pi + NB;
+        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+            int r = e / NB, c = e % NB;
+            pi[r][c] = (i0 + r < n) ? A[(i0 + r) * n + k0 + c] : TF(0);
+            pj[r][c] = (j0 + r < n) ? A[(j0 + r) * n + k0 + c] : TF(0);
+        }
+        __syncthreads();
+        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // ty: 0..31
+        TF acc[2][4];
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) acc[a][b] = TF(0);
+        for (int c = 0; c < NB; c++) {
+            TF u[2], v[4];
+#pragma unroll
+            for (int a = 0; a < 2; a++) u[a] = pi[ty * 2 + a][c];
+#pragma unroll
+            for (int b = 0; b < 4; b++) v[b] = pj[tx * 4 + b][c];
+#pragma unroll
+            for (int a = 0; a < 2; a++)
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc[a][b] = fma(u[a], v[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            int64_t r = i0 + ty * 2 + a;
+            if (r >= n) continue;
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                int64_t c = j0 + tx * 4 + b;
+                if (c >= n || c > r) continue;
+                A[r * n + c] -= acc[a][b];
+            }
         }
     }
-    (void)ntile;
+    if (Linv_next != nullptr && blockIdx.x == 0) {
+        __syncthreads();   // this CTA's writes of the diagonal tile are visible to it
+        potrf_inv_block<TF>(A, n, (int)base, Linv_next, err, smem_raw);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -290,6 +332,7 @@ __global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L,
     __shared__ TF xs[NB];
     __shared__ TF red[8][NB];
     __shared__ TF t[NB];
+    __shared__ TF dsh[NB * NB];          // this block's diagonal inverse, loaded up front
     __shared__ int abort_flag;
     const int nblk = gridDim.x;
     const int i = backward ? nblk - 1 - (int)blockIdx.x : (int)blockIdx.x;
@@ -297,6 +340,10 @@ __global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L,
     const int nb = (int)min((int64_t)NB, n - r0);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     if (tid == 0) abort_flag = 0;
+    {
+        const TF *Dsrc = Dinv + (int64_t)i * NB * NB;
+        for (int e = tid; e < NB * NB; e += blockDim.x) dsh[e] = Dsrc[e];
+    }
     TF acc0 = TF(0), acc1 = TF(0);   // backward: columns lane, lane + 32
     TF accr[8];                      // forward: rows w*8 + q
 #pragma unroll
@@ -330,7 +377,7 @@ __global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L,
                     abort_flag = 1;
                     break;
                 }
-                __nanosleep(32);
+                if (spins > 64) __nanosleep(32);
             }
         }
         __syncthreads();
@@ -372,7 +419,7 @@ __global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L,
     }
     __syncthreads();
     // diagonal block: y_i = Dinv_i t (forward) or Dinv_i^T t (backward)
-    const TF *Di = Dinv + (int64_t)i * NB * NB;
+    const TF *Di = dsh;
     if (!backward) {
 #pragma unroll
         for (int q = 0; q < 8; q++) {
@@ -406,22 +453,199 @@ __global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L,
     if (tid == 0) st_release_gpu(&flags[i], epoch);
 }
 
+// Multi-column wavefront solve (nrhs <= 16 columns, column-major with leading dimension
+// n).  Same block protocol as k_trsv_wave; the dependency products are small GEMMs on
+// a shared-memory copy of the factor tile, which is loaded before the dependency's
+// flag is awaited.
+constexpr int kMaxRhs = 16;
+
+template <class TF>
+__global__ void __launch_bounds__(256) k_trsm_wave(const TF *__restrict__ L,
+                                                   const TF *__restrict__ Dinv, int64_t n, TF *Y,
+                                                   int nrhs, int *flags, int epoch, int32_t *err,
+                                                   int backward) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TF(*lt)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);    // factor tile
+    TF(*dv)[NB + 1] = lt + NB;                                      // diagonal inverse
+    TF(*xs)[kMaxRhs + 1] = reinterpret_cast<TF(*)[kMaxRhs + 1]>(dv + NB);   // X_j
+    TF(*tt)[kMaxRhs + 1] = xs + NB;                                 // right-hand side block
+    __shared__ int abort_flag;
+    const int nblk = gridDim.x;
+    const int i = backward ? nblk - 1 - (int)blockIdx.x : (int)blockIdx.x;
+    const int64_t r0 = (int64_t)i * NB;
+    const int nb = (int)min((int64_t)NB, n - r0);
+    const int tid = threadIdx.x;
+    const int nout = NB * nrhs;
+    if (tid == 0) abort_flag = 0;
+    for (int e = tid; e < NB * NB; e += blockDim.x)
+        dv[e >> 6][e & 63] = Dinv[(int64_t)i * NB * NB + e];
+    TF acc[4] = {TF(0), TF(0), TF(0), TF(0)};   // outputs e = tid + 256 q: row e % 64, col e / 64
+    const int ndep = backward ? (nblk - 1 - i) : i;
+    for (int d = 0; d < ndep; d++) {
+        const int j = backward ? (nblk - 1 - d) : d;
+        const int64_t c0 = (int64_t)j * NB;
+        const int njb = (int)min((int64_t)NB, n - c0);
+        __syncthreads();   // previous tile and X_j no longer in use
+        for (int e = tid; e < NB * NB; e += blockDim.x) {
+            const int rr = e >> 6, cc = e & 63;
+            // forward: lt[r][k] = L[r0 + r][c0 + k]; backward: lt[r][k] = L[c0 + k][r0 + r]
+            TF v = TF(0);
+            if (!backward) {
+                if (rr < nb && cc < njb) v = L[(r0 + rr) * n + c0 + cc];
+                lt[rr][cc] = v;
+            } else {
+                if (rr < njb && cc < nb) v = L[(c0 + rr) * n + r0 + cc];
+                lt[cc][rr] = v;
+            }
+        }
+        if (tid == 0) {
+            int spins = 0;
+            while (ld_acquire_gpu(&flags[j]) != epoch) {
+                if (++spins > kSpinLimit) {
+                    atomicAdd(&err[ERR_SOLVE], 1);
+                    abort_flag = 1;
+                    break;
+                }
+                if (spins > 64) __nanosleep(32);
+            }
+        }
+        __syncthreads();
+        if (abort_flag) return;
+        for (int e = tid; e < NB * nrhs; e += blockDim.x) {
+            const int k = e & 63, c = e >> 6;
+            xs[k][c] = k < njb ? __ldcg(&Y[(int64_t)c * n + c0 + k]) : TF(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int e = tid + 256 * q;
+            if (e < nout) {
+                const int r = e & 63, c = e >> 6;
+                TF sacc = TF(0);
+#pragma unroll 8
+                for (int k = 0; k < NB; k++) sacc += lt[r][k] * xs[k][c];
+                acc[q] += sacc;
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int e = tid + 256 * q;
+        if (e < nout) {
+            const int r = e & 63, c = e >> 6;
+            tt[r][c] = r < nb ? Y[(int64_t)c * n + r0 + r] - acc[q] : TF(0);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int e = tid + 256 * q;
+        if (e < nout) {
+            const int r = e & 63, c = e >> 6;
+            TF sacc = TF(0);
+            if (!backward)
+                for (int k = 0; k <= r; k++) sacc += dv[r][k] * tt[k][c];
+            else
+                for (int k = r; k < NB; k++) sacc += dv[k][r] * tt[k][c];
+            if (r < nb) {
+                Y[(int64_t)c * n + r0 + r] = sacc;
+                __threadfence();
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) st_release_gpu(&flags[i], epoch);
+}
+
+// ---------------------------------------------------------------------------------
+// Batched block-step triangular solves across meshes (no waiting between CTAs, so the
+// meshes of a batch share launches).  Step s: mesh m solves its block k = s (forward)
+// or nblk_m - 1 - s (backward) with the diagonal inverse, then updates the blocks that
+// depend on it.  All right-hand sides of a mesh (<= 16, column-major, ld = n) together.
+// ---------------------------------------------------------------------------------
+template <class TF>
+__global__ void __launch_bounds__(256) k_btrsm_diag(const BatchTrsmDesc *__restrict__ d, int s,
+                                                    int nrhs, int backward) {
+    __shared__ TF dv[NB][NB + 1];
+    __shared__ TF tt[NB][kMaxRhs + 1];
+    const BatchTrsmDesc &D = d[blockIdx.x];
+    if (!D.active || s >= D.nblk) return;
+    const int k = backward ? D.nblk - 1 - s : s;
+    const int64_t n = D.n, r0 = (int64_t)k * NB;
+    const int nb = (int)min((int64_t)NB, n - r0);
+    const TF *Dinv = reinterpret_cast<const TF *>(D.dinv) + (int64_t)k * NB * NB;
+    TF *Y = reinterpret_cast<TF *>(D.y);
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) dv[e >> 6][e & 63] = Dinv[e];
+    for (int e = threadIdx.x; e < NB * nrhs; e += blockDim.x) {
+        const int r = e & 63, c = e >> 6;
+        tt[r][c] = r < nb ? Y[(int64_t)c * n + r0 + r] : TF(0);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * nrhs; e += blockDim.x) {
+        const int r = e & 63, c = e >> 6;
+        TF acc = TF(0);
+        if (!backward)
+            for (int q = 0; q <= r; q++) acc += dv[r][q] * tt[q][c];
+        else
+            for (int q = r; q < NB; q++) acc += dv[q][r] * tt[q][c];
+        if (r < nb) Y[(int64_t)c * n + r0 + r] = acc;
+    }
+}
+
+template <class TF>
+__global__ void __launch_bounds__(256) k_btrsm_update(const BatchTrsmDesc *__restrict__ d, int s,
+                                                      int nrhs, int backward) {
+    __shared__ TF lt[NB][NB + 1];
+    __shared__ TF xs[NB][kMaxRhs + 1];
+    const BatchTrsmDesc &D = d[blockIdx.y];
+    if (!D.active || s >= D.nblk) return;
+    const int k = backward ? D.nblk - 1 - s : s;
+    const int i = backward ? k - 1 - (int)blockIdx.x : k + 1 + (int)blockIdx.x;
+    if (i < 0 || i >= D.nblk) return;
+    const int64_t n = D.n, r0 = (int64_t)i * NB, c0 = (int64_t)k * NB;
+    const int nb = (int)min((int64_t)NB, n - r0), nk = (int)min((int64_t)NB, n - c0);
+    const TF *L = reinterpret_cast<const TF *>(D.L);
+    TF *Y = reinterpret_cast<TF *>(D.y);
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int a = e >> 6, b = e & 63;
+        if (!backward) {   // lt[r][q] = L[r0 + r][c0 + q]
+            lt[a][b] = (a < nb && b < nk) ? L[(r0 + a) * n + c0 + b] : TF(0);
+        } else {           // lt[r][q] = L[c0 + q][r0 + r]
+            lt[b][a] = (a < nk && b < nb) ? L[(c0 + a) * n + r0 + b] : TF(0);
+        }
+    }
+    for (int e = threadIdx.x; e < NB * nrhs; e += blockDim.x) {
+        const int q = e & 63, c = e >> 6;
+        xs[q][c] = q < nk ? Y[(int64_t)c * n + c0 + q] : TF(0);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * nrhs; e += blockDim.x) {
+        const int r = e & 63, c = e >> 6;
+        TF acc = TF(0);
+#pragma unroll 8
+        for (int q = 0; q < NB; q++) acc += lt[r][q] * xs[q][c];
+        if (r < nb) Y[(int64_t)c * n + r0 + r] -= acc;
+    }
+}
+
 template <class TF>
 int cholesky_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
     const size_t sh = 2 * NB * (NB + 1) * sizeof(TF);
+    TF *dinv = reinterpret_cast<TF *>(m->dinv);   // inverses of the diagonal blocks, kept
+    if (n <= 0) return FEM3_OK;
+    k_potrf_inv<TF><<<1, 512, sh, s>>>(A, n, 0, dinv, m->err);
+    note_launch(m);
     for (int64_t k0 = 0; k0 < n; k0 += NB) {
-        TF *Linv = reinterpret_cast<TF *>(m->dinv) + (k0 / NB) * NB * NB;   // kept for the solves
-        k_potrf_inv<TF><<<1, 256, sh, s>>>(A, n, (int)k0, Linv, m->err);
-        note_launch(m);
         int64_t rest = n - k0 - NB;
-        if (rest > 0) {
-            int nblk = (int)((rest + NB - 1) / NB);
-            k_trsm_gemm<TF><<<nblk, 256, sh, s>>>(A, n, (int)k0, Linv);
-            note_launch(m);
-            int ntiles = nblk * (nblk + 1) / 2;
-            k_syrk<TF><<<ntiles, 256, sh, s>>>(A, n, (int)k0, nblk);
-            note_launch(m);
-        }
+        if (rest <= 0) break;
+        TF *Linv = dinv + (k0 / NB) * NB * NB;
+        int nblk = (int)((rest + NB - 1) / NB);
+        k_trsm_gemm<TF><<<nblk, 256, sh, s>>>(A, n, (int)k0, Linv);
+        note_launch(m);
+        int ntiles = nblk * (nblk + 1) / 2;
+        k_syrk<TF><<<ntiles, 512, sh, s>>>(A, n, (int)k0, Linv + NB * NB, m->err);
+        note_launch(m);
     }
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
@@ -481,44 +705,53 @@ int trsv_t(const TF *L, int64_t n, TF *y, cudaStream_t s, Mesh *m) {
 // pass 1: one thread per Gauss point (slot) of an axis, yL = w (L u), yR = w (R u);
 // pass 2: one warp per template row (bin, local dof), z = L yR + R yL, added into Au.
 // ---------------------------------------------------------------------------------
+template <int NR>
 __global__ void __launch_bounds__(256) k_apply_rows(
     const double *__restrict__ tabL, const double *__restrict__ tabR,
     const int32_t *__restrict__ slot_bin, const int32_t *__restrict__ gp_off,
-    const int32_t *__restrict__ gp_idx, const int32_t *__restrict__ dof_off,
+    const double *__restrict__ w_slot, const int32_t *__restrict__ dof_off,
     const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
-    const int32_t *__restrict__ tab_ld, const double *__restrict__ gw, int64_t n_gp,
-    const double *__restrict__ u, double *yL, double *yR) {
+    const int32_t *__restrict__ tab_ld, int64_t n_gp, const double *__restrict__ u,
+    int64_t ldu, int nv, double *yL, double *yR) {
     const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (slot >= n_gp) return;
     const int b = slot_bin[slot];
     const int r = (int)(slot - gp_off[b]);
     const int d0 = dof_off[b], D = dof_off[b + 1] - d0, ld = tab_ld[b];
     const double *Lc = tabL + tab_off[b] + r, *Rc = tabR + tab_off[b] + r;
-    double sl0 = 0, sl1 = 0, sr0 = 0, sr1 = 0;
-    int c = 0;
-    for (; c + 1 < D; c += 2) {
-        const double u0 = __ldg(u + dof_idx[d0 + c]), u1 = __ldg(u + dof_idx[d0 + c + 1]);
-        sl0 = fma(Lc[(int64_t)c * ld], u0, sl0);
-        sr0 = fma(Rc[(int64_t)c * ld], u0, sr0);
-        sl1 = fma(Lc[(int64_t)(c + 1) * ld], u1, sl1);
-        sr1 = fma(Rc[(int64_t)(c + 1) * ld], u1, sr1);
+    double sl[NR], sr[NR];
+#pragma unroll
+    for (int v = 0; v < NR; v++) { sl[v] = 0; sr[v] = 0; }
+    for (int c = 0; c < D; c++) {
+        const int64_t o = (int64_t)c * ld;
+        const double lv = Lc[o], rv = Rc[o];
+        const int32_t dof = dof_idx[d0 + c];
+#pragma unroll
+        for (int v = 0; v < NR; v++) {
+            if (v < nv) {
+                const double uv = __ldg(u + (int64_t)v * ldu + dof);
+                sl[v] = fma(lv, uv, sl[v]);
+                sr[v] = fma(rv, uv, sr[v]);
+            }
+        }
     }
-    if (c < D) {
-        const double u0 = __ldg(u + dof_idx[d0 + c]);
-        sl0 = fma(Lc[(int64_t)c * ld], u0, sl0);
-        sr0 = fma(Rc[(int64_t)c * ld], u0, sr0);
-    }
-    const double wv = gw[gp_idx[slot]];
-    yL[slot] = wv * (sl0 + sl1);
-    yR[slot] = wv * (sr0 + sr1);
+    const double wv = w_slot[slot];
+#pragma unroll
+    for (int v = 0; v < NR; v++)
+        if (v < nv) {
+            yL[(int64_t)v * n_gp + slot] = wv * sl[v];
+            yR[(int64_t)v * n_gp + slot] = wv * sr[v];
+        }
 }
 
+template <int NR>
 __global__ void __launch_bounds__(256) k_apply_cols(
     const double *__restrict__ tabL, const double *__restrict__ tabR,
     const int32_t *__restrict__ row_bin, const int32_t *__restrict__ gp_off,
     const int32_t *__restrict__ dof_off, const int32_t *__restrict__ dof_idx,
     const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld, int64_t n_rows,
-    const double *__restrict__ yL, const double *__restrict__ yR, double sK, double *Au) {
+    int64_t n_gp, const double *__restrict__ yL, const double *__restrict__ yR, double sK,
+    int nv, double *Au, int64_t ldA) {
     const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n_rows) return;
@@ -526,10 +759,25 @@ __global__ void __launch_bounds__(256) k_apply_cols(
     const int c = (int)(row - dof_off[b]);
     const int g0 = gp_off[b], G = gp_off[b + 1] - g0, ld = tab_ld[b];
     const double *Lr = tabL + tab_off[b] + (int64_t)c * ld, *Rr = tabR + tab_off[b] + (int64_t)c * ld;
-    double z = 0;
-    for (int r = lane; r < G; r += 32) z = fma(Lr[r], yR[g0 + r], fma(Rr[r], yL[g0 + r], z));
-    for (int o = 16; o > 0; o >>= 1) z += __shfl_down_sync(0xffffffffu, z, o);
-    if (lane == 0) atomicAdd(&Au[dof_idx[row]], sK * z);
+    double z[NR];
+#pragma unroll
+    for (int v = 0; v < NR; v++) z[v] = 0;
+    for (int r = lane; r < G; r += 32) {
+        const double lv = Lr[r], rv = Rr[r];
+#pragma unroll
+        for (int v = 0; v < NR; v++)
+            if (v < nv)
+                z[v] = fma(lv, yR[(int64_t)v * n_gp + g0 + r], fma(rv, yL[(int64_t)v * n_gp + g0 + r], z[v]));
+    }
+    const int32_t dof = dof_idx[row];
+#pragma unroll
+    for (int v = 0; v < NR; v++) {
+        if (v < nv) {
+            double zz = z[v];
+            for (int o = 16; o > 0; o >>= 1) zz += __shfl_down_sync(0xffffffffu, zz, o);
+            if (lane == 0) atomicAdd(&Au[(int64_t)v * ldA + dof], sK * zz);
+        }
+    }
 }
 
 // per-axis forms sum_g w_g ((L lam)(R u) + (R lam)(L u)) (adjoint), one CTA per bin
@@ -594,6 +842,29 @@ __global__ void k_residual(const double *__restrict__ b, const double *__restric
     }
 }
 
+// r = b - Au for column blockIdx.y; norms[2c] += |r_c|^2, norms[2c+1] += |b_c|^2
+__global__ void k_residual_cols(const double *__restrict__ b, const double *__restrict__ Au,
+                                int64_t n, double *r, double *norms) {
+    const int c = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double rr = 0, bb = 0;
+    if (i < n) {
+        const int64_t k = (int64_t)c * n + i;
+        const double v = b[k] - Au[k];
+        r[k] = v;
+        rr = v * v;
+        bb = b[k] * b[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_down_sync(0xffffffffu, rr, o);
+        bb += __shfl_down_sync(0xffffffffu, bb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&norms[2 * c], rr);
+        atomicAdd(&norms[2 * c + 1], bb);
+    }
+}
+
 __global__ void k_to_f32(const double *__restrict__ a, float *b, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
@@ -617,6 +888,20 @@ inline unsigned g256(int64_t n) { return (unsigned)(n > 0 ? (n + 255) / 256 : 1)
 
 }  // namespace
 
+// upper triangle := transpose of the lower triangle (n x n row-major)
+__global__ void k_sym_from_lower(double *A, int64_t n) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    int64_t i = e / n, j = e % n;
+    if (j > i) A[e] = A[j * n + i];
+}
+
+int sym_from_lower(double *A, int64_t n, cudaStream_t s) {
+    k_sym_from_lower<<<g256(n * n), 256, 0, s>>>(A, n);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
 int f32_to_f64(const float *a, double *b, int64_t n, cudaStream_t s) {
     k_f32_to_f64<<<g256(n), 256, 0, s>>>(a, b, n);
     FEM3_CUDA(cudaGetLastError());
@@ -639,6 +924,58 @@ int residual_norm(Mesh *m, const double *b, const double *Au, double *rel) {
     FEM3_CUDA(cudaStreamSynchronize(s));
     *rel = m->h_norms[1] > 0 ? sqrt(m->h_norms[0] / m->h_norms[1]) : 0.0;
     return FEM3_OK;
+}
+
+// L Y = B then L^T X = Y for nrhs <= 16 columns (column-major, leading dimension n)
+template <class TF>
+int trsm_t(const TF *L, int64_t n, TF *Y, int nrhs, cudaStream_t s, Mesh *m) {
+    if (n <= 0) return FEM3_OK;
+    if (nrhs == 1) return trsv_t<TF>(L, n, Y, s, m);
+    const int nblk = (int)((n + NB - 1) / NB);
+    const size_t sh = (2 * NB * (NB + 1) + 2 * NB * (kMaxRhs + 1)) * sizeof(TF);
+    FEM3_CUDA(cudaFuncSetAttribute(k_trsm_wave<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsm_wave<TF>, 256, sh);
+    if (!(coop && (int64_t)per_sm * sms >= nblk)) {
+        for (int c = 0; c < nrhs; c++) FEM3_TRY(trsv_t<TF>(L, n, Y + (int64_t)c * n, s, m));
+        return FEM3_OK;
+    }
+    for (int backward = 0; backward < 2; backward++) {
+        int epoch = ++m->flag_epoch;
+        int32_t *err = m->err;
+        int *flags = m->flags;
+        const TF *Dinv = reinterpret_cast<const TF *>(m->dinv);
+        void *args[] = {(void *)&L, (void *)&Dinv, (void *)&n, (void *)&Y, (void *)&nrhs,
+                        (void *)&flags, (void *)&epoch, (void *)&err, (void *)&backward};
+        FEM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_trsm_wave<TF>, dim3(nblk), dim3(256),
+                                              args, sh, s));
+        note_launch(m);
+    }
+    return FEM3_OK;
+}
+
+// Forward then backward block-step sweeps over all meshes of a batch (descriptors in
+// device memory, nrhs <= 16, max_nblk = largest block count).
+template <class TF>
+int trsm_batch_t(const BatchTrsmDesc *d_desc, int n_mesh, int max_nblk, int nrhs, cudaStream_t s) {
+    for (int backward = 0; backward < 2; backward++)
+        for (int st = 0; st < max_nblk; st++) {
+            k_btrsm_diag<TF><<<n_mesh, 256, 0, s>>>(d_desc, st, nrhs, backward);
+            if (st + 1 < max_nblk)
+                k_btrsm_update<TF><<<dim3(max_nblk - 1 - st, n_mesh), 256, 0, s>>>(d_desc, st, nrhs,
+                                                                                   backward);
+        }
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int trsm_batch(const BatchTrsmDesc *d_desc, int n_mesh, int max_nblk, int nrhs, bool fp64,
+               cudaStream_t s) {
+    return fp64 ? trsm_batch_t<double>(d_desc, n_mesh, max_nblk, nrhs, s)
+                : trsm_batch_t<float>(d_desc, n_mesh, max_nblk, nrhs, s);
 }
 
 int load_vector(Mesh *m, const double *f_d, int nrhs, double *b_d) {
@@ -708,26 +1045,54 @@ int factor(Mesh *m) {
     return FEM3_OK;
 }
 
-int apply_A64(Mesh *m, const double *u_d, double *Au_d) {
+// Au = A u for nv vectors (column-major, leading dimension n_dof), applied in FP64 from
+// the tables; vectors go through the tables in groups of up to eight per pass.
+int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
     cudaStream_t s = m->stream;
-    FEM3_CUDA(cudaMemsetAsync(Au_d, 0, sizeof(double) * m->n_dof, s));
-    double *yL = m->ybuf, *yR = m->ybuf + m->n_gp;
-    for (int axis = 0; axis < 3; axis++) {
-        AxisBins &B = m->bins[axis];
-        if (B.n_tmpl == 0) continue;
-        k_apply_rows<<<g256(m->n_gp), 256, 0, s>>>(m->tabL[axis], m->tabR[axis], B.slot_bin,
-                                                    B.gp_off, B.gp_idx, B.dof_off, B.dof_idx,
-                                                    B.tab_off, B.tab_ld, m->gw, m->n_gp, u_d, yL,
-                                                    yR);
-        note_launch(m);
-        k_apply_cols<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
-            m->tabL[axis], m->tabR[axis], B.row_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
-            B.tab_ld, B.n_tmpl, yL, yR, m->sK[axis], Au_d);
-        note_launch(m);
+    const int64_t n = m->n_dof;
+    FEM3_CUDA(cudaMemsetAsync(Au_d, 0, sizeof(double) * n * nv, s));
+    double *yL = nullptr;
+    const int group = nv > 1 ? 8 : 1;
+    if (group > 1) {
+        FEM3_CUDA(cudaMallocAsync((void **)&yL, sizeof(double) * 2 * group * m->n_gp, s));
+    } else {
+        yL = m->ybuf;
     }
+    double *yR = yL + (int64_t)group * m->n_gp;
+    for (int v0 = 0; v0 < nv; v0 += group) {
+        const int cnt = std::min(group, nv - v0);
+        for (int axis = 0; axis < 3; axis++) {
+            AxisBins &B = m->bins[axis];
+            if (B.n_tmpl == 0) continue;
+            if (group == 1) {
+                k_apply_rows<1><<<g256(m->n_gp), 256, 0, s>>>(
+                    m->tabL[axis], m->tabR[axis], B.slot_bin, B.gp_off, B.w_slot, B.dof_off,
+                    B.dof_idx, B.tab_off, B.tab_ld, m->n_gp, u_d + v0 * n, n, cnt, yL, yR);
+                note_launch(m);
+                k_apply_cols<1><<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
+                    m->tabL[axis], m->tabR[axis], B.row_bin, B.gp_off, B.dof_off, B.dof_idx,
+                    B.tab_off, B.tab_ld, B.n_tmpl, m->n_gp, yL, yR, m->sK[axis], cnt,
+                    Au_d + v0 * n, n);
+                note_launch(m);
+            } else {
+                k_apply_rows<8><<<g256(m->n_gp), 256, 0, s>>>(
+                    m->tabL[axis], m->tabR[axis], B.slot_bin, B.gp_off, B.w_slot, B.dof_off,
+                    B.dof_idx, B.tab_off, B.tab_ld, m->n_gp, u_d + v0 * n, n, cnt, yL, yR);
+                note_launch(m);
+                k_apply_cols<8><<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
+                    m->tabL[axis], m->tabR[axis], B.row_bin, B.gp_off, B.dof_off, B.dof_idx,
+                    B.tab_off, B.tab_ld, B.n_tmpl, m->n_gp, yL, yR, m->sK[axis], cnt,
+                    Au_d + v0 * n, n);
+                note_launch(m);
+            }
+        }
+    }
+    if (group > 1) FEM3_CUDA(cudaFreeAsync(yL, s));
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
+
+int apply_A64(Mesh *m, const double *u_d, double *Au_d) { return apply_multi(m, u_d, 1, Au_d); }
 
 int axis_forms(Mesh *m, const double *u_d, const double *lam_d, double out[3]) {
     cudaStream_t s = m->stream;
@@ -752,52 +1117,62 @@ int solve_direct(Mesh *m, const double *b_d, int nrhs, double *u_d) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
     FEM3_CUDA(cudaMemcpyAsync(u_d, b_d, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
-    for (int r = 0; r < nrhs; r++) FEM3_TRY(trsv_t<double>(m->A64, n, u_d + r * n, s, m));
+    for (int c0 = 0; c0 < nrhs; c0 += kMaxRhs)
+        FEM3_TRY(trsm_t<double>(m->A64, n, u_d + (int64_t)c0 * n, std::min(kMaxRhs, nrhs - c0), s, m));
     return FEM3_OK;
 }
 
+// Refinement for all right-hand sides together: u = 0, r = b; repeat
+//   d = A32^{-1} r (FP32 factor, all columns in one wavefront sweep pair), u += d,
+//   r = b - A u (FP64 operator from the tables), until every column has
+//   ||r|| <= tol ||b|| or max_iter sweeps.
 int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter, double *u_d,
                   int *iters, double *resid) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
-    double *Au = m->vec64[0], *r = m->vec64[1];
-    float *r32 = m->vec32[0];
-    int it_max = 0;
-    double worst = 0;
-    for (int col = 0; col < nrhs; col++) {
-        const double *b = b_d + col * n;
-        double *u = u_d + col * n;
-        FEM3_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
-        FEM3_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        int it = 0;
-        double rel = 1.0;
-        for (;;) {
-            k_to_f32<<<g256(n), 256, 0, s>>>(r, r32, n);
-            note_launch(m);
-            FEM3_TRY(trsv_t<float>(m->A32, n, r32, s, m));
-            k_axpy_f32<<<g256(n), 256, 0, s>>>(r32, u, n);
-            note_launch(m);
-            FEM3_TRY(apply_A64(m, u, Au));
-            FEM3_CUDA(cudaMemsetAsync(m->norms, 0, sizeof(double) * 2, s));
-            k_residual<<<g256(n), 256, 0, s>>>(b, Au, n, r, m->norms);
-            note_launch(m);
-            FEM3_CUDA(cudaMemcpyAsync(m->h_norms, m->norms, sizeof(double) * 2,
-                                      cudaMemcpyDeviceToHost, s));
-            FEM3_CUDA(cudaStreamSynchronize(s));
-            rel = m->h_norms[1] > 0 ? sqrt(m->h_norms[0] / m->h_norms[1]) : 0.0;
-            it++;
-            if (rel <= tol || it >= max_iter || !(rel == rel)) break;
+    const int64_t nn = n * nrhs;
+    if (nrhs > 32) return set_error(FEM3_E_ARG, "at most 32 right-hand sides per solve");
+    double *Au = nullptr, *r = nullptr;
+    float *r32 = nullptr;
+    FEM3_CUDA(cudaMallocAsync((void **)&Au, sizeof(double) * nn, s));
+    FEM3_CUDA(cudaMallocAsync((void **)&r, sizeof(double) * nn, s));
+    FEM3_CUDA(cudaMallocAsync((void **)&r32, sizeof(float) * nn, s));
+    FEM3_CUDA(cudaMemsetAsync(u_d, 0, sizeof(double) * nn, s));
+    FEM3_CUDA(cudaMemcpyAsync(r, b_d, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+    int it = 0;
+    double worst = 1.0;
+    int st = FEM3_OK;
+    for (;;) {
+        k_to_f32<<<g256(nn), 256, 0, s>>>(r, r32, nn);
+        note_launch(m);
+        for (int c0 = 0; c0 < nrhs && st == FEM3_OK; c0 += kMaxRhs)
+            st = trsm_t<float>(m->A32, n, r32 + c0 * n, std::min(kMaxRhs, nrhs - c0), s, m);
+        if (st != FEM3_OK) break;
+        k_axpy_f32<<<g256(nn), 256, 0, s>>>(r32, u_d, nn);
+        note_launch(m);
+        if ((st = apply_multi(m, u_d, nrhs, Au)) != FEM3_OK) break;
+        FEM3_CUDA(cudaMemsetAsync(m->norms, 0, sizeof(double) * 2 * nrhs, s));
+        k_residual_cols<<<dim3(g256(n), nrhs), 256, 0, s>>>(b_d, Au, n, r, m->norms);
+        note_launch(m);
+        FEM3_CUDA(cudaMemcpyAsync(m->h_norms, m->norms, sizeof(double) * 2 * nrhs,
+                                  cudaMemcpyDeviceToHost, s));
+        FEM3_CUDA(cudaStreamSynchronize(s));
+        worst = 0;
+        for (int c = 0; c < nrhs; c++) {
+            const double rel = m->h_norms[2 * c + 1] > 0 ? sqrt(m->h_norms[2 * c] / m->h_norms[2 * c + 1]) : 0.0;
+            worst = (rel == rel) ? std::max(worst, rel) : INFINITY;
         }
-        it_max = std::max(it_max, it);
-        worst = std::max(worst, rel);
-        if (!(rel <= tol)) {
-            if (iters) *iters = it_max;
-            if (resid) *resid = worst;
-            return set_error(FEM3_E_NO_CONVERGE, "iterative refinement did not reach the tolerance");
-        }
+        it++;
+        if (worst <= tol || it >= max_iter || !(worst < INFINITY)) break;
     }
-    if (iters) *iters = it_max;
+    cudaFreeAsync(Au, s);
+    cudaFreeAsync(r, s);
+    cudaFreeAsync(r32, s);
+    if (iters) *iters = it;
     if (resid) *resid = worst;
+    if (st != FEM3_OK) return st;
+    if (!(worst <= tol))
+        return set_error(FEM3_E_NO_CONVERGE, "iterative refinement did not reach the tolerance");
     return FEM3_OK;
 }
 

@@ -186,38 +186,40 @@ __global__ void k_pow_tables(double p0, double p1, double p2, double *cell, doub
     if (j < 128) pexp[a * 128 + j] = exp2((double)(j - 64) * p);
 }
 
-// grid: x over slots of one axis, y = side (0 left, 1 right); one launch per axis
-__global__ void __launch_bounds__(128) k_walk_tables(WalkGeom W, TableArgs A0, TableArgs A1,
-                                                     int axis, int64_t n_gp, int32_t *err,
-                                                     unsigned long long *seg_count) {
-    int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int side = blockIdx.y;
-    const TableArgs &A = side ? A1 : A0;
-    const int dir = side ? 1 : -1;
+// One line (Gauss point in slot `slot` of an axis): both directions in one loop.  When
+// the left walk reaches the boundary the same iteration switches to the right walk, so a
+// lane's trip count is one whole chord (nearly equal for neighbouring Gauss points) and
+// the lanes of a warp stay converged.  Returns the number of segments; counts template
+// misses and failed walks.
+__device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
+                                         const TableArgs &A1, int axis, int64_t slot,
+                                         int &miss, int &bad) {
     int nseg = 0;
-    if (slot < n_gp) {
-        const int32_t g = A.gp_idx[slot];
-        const int32_t bin = A.slot_bin[slot];
-        const int32_t row = (int32_t)(slot - A.gp_off[bin]);
-        const int32_t *dofs = A.dof_idx + A.dof_off[bin];
-        const int nd = A.dof_off[bin + 1] - A.dof_off[bin];
-        const int32_t ld = A.tab_ld[bin];
-        double *tab = A.tab + A.tab_off[bin] + row;
-
-        const double x0 = W.gp[3 * (int64_t)g], x1 = W.gp[3 * (int64_t)g + 1],
-                     x2 = W.gp[3 * (int64_t)g + 2];
-        int32_t t = g >> 2;
-        double r_prev = 0.0, P_prev = 0.0;
-        int32_t cj[4] = {-1, -1, -1, -1}, cc[4] = {-1, -1, -1, -1};
-        int miss = 0;
-        bool ok = false;
-        for (int step = 0; step < W.max_steps; step++) {
-            double b[4];
-            double rmax = tet_rmax(W, t, axis, dir, x0, x1, x2, b);
-            if (!(rmax < INFINITY)) break;
+    const int32_t g = A0.gp_idx[slot];
+    const int32_t bin = A0.slot_bin[slot];
+    const int32_t row = (int32_t)(slot - A0.gp_off[bin]);
+    const int32_t *dofs = A0.dof_idx + A0.dof_off[bin];
+    const int nd = A0.dof_off[bin + 1] - A0.dof_off[bin];
+    const int32_t ld = A0.tab_ld[bin];
+    const int64_t toff = A0.tab_off[bin] + row;
+    const double x0 = W.gp[3 * (int64_t)g], x1 = W.gp[3 * (int64_t)g + 1],
+                 x2 = W.gp[3 * (int64_t)g + 2];
+    const double p_exp = A0.p_exp;   // same order on both sides of the line
+    int side = 0, dir = -1;
+    double *tab = A0.tab + toff;
+    double coef = A0.coef;
+    int32_t t = g >> 2;
+    double r_prev = 0.0, P_prev = 0.0;
+    int32_t cj[4] = {-1, -1, -1, -1}, cc[4] = {-1, -1, -1, -1};
+    int steps = 0;
+    for (int it = 0; it < 2 * W.max_steps; it++) {
+        double b[4];
+        const double rmax = tet_rmax(W, t, axis, dir, x0, x1, x2, b);
+        int32_t nx = -2;
+        if (rmax < INFINITY) {
             if (rmax - r_prev > W.eps_r) {
-                double P = pow_table(rmax, A.p_exp, A.pow_cell, A.pow_exp);
-                double c = A.coef * (P - P_prev);
+                const double P = pow_table(rmax, p_exp, A0.pow_cell, A0.pow_exp);
+                const double c = coef * (P - P_prev);
                 const double *Mt = W.M + 16 * (int64_t)t;
                 int32_t nj[4], nc[4];
 #pragma unroll
@@ -243,18 +245,113 @@ __global__ void __launch_bounds__(128) k_walk_tables(WalkGeom W, TableArgs A0, T
                 r_prev = rmax;
                 nseg++;
             }
-            int32_t nx = next_tet(W, t, axis, dir, x0, x1, x2, b, rmax);
-            if (nx == -1) { ok = true; break; }
-            if (nx < 0) break;
-            t = nx;
+            nx = next_tet(W, t, axis, dir, x0, x1, x2, b, rmax);
         }
-        if (!ok) atomicAdd(&err[ERR_WALK], 1);
-        if (miss) atomicAdd(&err[ERR_TEMPLATE], miss);
+        steps++;
+        if (nx >= 0 && steps < W.max_steps) {
+            t = nx;
+            continue;
+        }
+        bad += (nx != -1);   // no exit found, bad pattern or step cap
+        if (side == 1) break;
+        // switch to the right walk of the same line
+        side = 1;
+        dir = 1;
+        tab = A1.tab + toff;
+        coef = A1.coef;
+        t = g >> 2;
+        r_prev = 0.0;
+        P_prev = 0.0;
+        steps = 0;
+#pragma unroll
+        for (int v = 0; v < 4; v++) { cj[v] = -1; cc[v] = -1; }
     }
-    // segment counter (one atomic per warp; every lane takes part)
+    return nseg;
+}
+
+__device__ __forceinline__ void count_segments(int nseg, unsigned long long *seg_count) {
     unsigned long long ns = (unsigned long long)nseg;
     for (int o = 16; o > 0; o >>= 1) ns += __shfl_down_sync(0xffffffffu, ns, o);
     if ((threadIdx.x & 31) == 0 && ns) atomicAdd(seg_count, ns);
+}
+
+// grid: x over slots of one axis; one launch per axis
+__global__ void __launch_bounds__(128) k_walk_tables(WalkGeom W, TableArgs A0, TableArgs A1,
+                                                     int axis, int64_t n_gp, int32_t *err,
+                                                     unsigned long long *seg_count) {
+    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int nseg = 0, miss = 0, bad = 0;
+    if (slot < n_gp) nseg = walk_line(W, A0, A1, axis, slot, miss, bad);
+    if (bad) atomicAdd(&err[ERR_WALK], bad);
+    if (miss) atomicAdd(&err[ERR_TEMPLATE], miss);
+    count_segments(nseg, seg_count);   // every lane takes part
+}
+
+// ---------------------------------------------------------------------------------
+// Batched walk: one launch walks every line of every axis of every mesh in a batch.
+// Descriptor d covers the n_gp slots of one (mesh, axis); item i belongs to the last
+// descriptor with slot0 <= i.
+// ---------------------------------------------------------------------------------
+struct WalkDesc {
+    WalkGeom W;
+    TableArgs A0, A1;
+    int axis;
+    int64_t slot0, n_gp;
+    int32_t *err;
+    unsigned long long *seg;
+};
+
+__global__ void __launch_bounds__(128) k_walk_batch(const WalkDesc *__restrict__ descs, int n_desc,
+                                                    int64_t n_items) {
+    const int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int nseg = 0, miss = 0, bad = 0, d = 0;
+    if (item < n_items) {
+        int lo = 0, hi = n_desc - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (descs[mid].slot0 <= item) lo = mid; else hi = mid - 1;
+        }
+        d = lo;
+        const WalkDesc &D = descs[d];
+        nseg = walk_line(D.W, D.A0, D.A1, D.axis, item - D.slot0, miss, bad);
+        if (bad) atomicAdd(&D.err[ERR_WALK], bad);
+        if (miss) atomicAdd(&D.err[ERR_TEMPLATE], miss);
+    }
+    // segment counts per mesh: lanes of a warp that share a descriptor add once
+    const unsigned group = __match_any_sync(0xffffffffu, d);
+    const unsigned sum = __reduce_add_sync(group, (unsigned)nseg);
+    if ((threadIdx.x & 31) == __ffs(group) - 1 && sum && item - (threadIdx.x & 31) < n_items)
+        atomicAdd(descs[d].seg, (unsigned long long)sum);
+}
+
+// tables of the table-driven power for each descriptor (block d, 256 threads)
+__global__ void k_pow_tables_batch(const WalkDesc *__restrict__ descs) {
+    const WalkDesc &D = descs[blockIdx.x];
+    const int j = threadIdx.x;
+    const double p = D.A0.p_exp;
+    const double mc = 1.0 + (2.0 * j + 1.0) / 512.0;
+    double *c = const_cast<double *>(D.A0.pow_cell) + 8 * j;
+    double binom = 1.0;
+    for (int k = 0; k <= 4; k++) {
+        c[k] = binom * pow(mc, p - k);
+        binom = binom * (p - k) / (k + 1);
+    }
+    c[5] = mc;
+    c[6] = 0.0;
+    c[7] = 0.0;
+    if (j < 128) const_cast<double *>(D.A0.pow_exp)[j] = exp2((double)(j - 64) * p);
+}
+
+// zero n_buf device buffers given as (pointer, element count) pairs
+__global__ void k_zero_batch(double *const *__restrict__ ptr, const int64_t *__restrict__ len,
+                             int n_buf) {
+    for (int b = blockIdx.y; b < n_buf; b += gridDim.y) {
+        double *p = ptr[b];
+        const int64_t n = len[b];
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x)
+            p[i] = 0.0;
+    }
 }
 
 // Path export: same walk, segments written out for requested lines.
@@ -327,7 +424,7 @@ WalkGeom make_geom(Mesh *m) {
 int walk_tables(Mesh *m, const double alpha[3]) {
     cudaStream_t s = m->stream;
     WalkGeom W = make_geom(m);
-    unsigned long long *segc = reinterpret_cast<unsigned long long *>(m->norms + 8);
+    unsigned long long *segc = reinterpret_cast<unsigned long long *>(m->norms + kSegCounterSlot);
     FEM3_CUDA(cudaMemsetAsync(segc, 0, sizeof(unsigned long long), s));
     if (!m->pow_cell) {
         FEM3_TRY(dev_alloc_t(m, &m->pow_cell, 3 * 256 * 8));
@@ -352,8 +449,8 @@ int walk_tables(Mesh *m, const double alpha[3]) {
         TableArgs A1 = A0;
         A1.tab = m->tabR[axis];
         A1.coef = -ig;
-        dim3 grid((unsigned)((m->n_gp + 127) / 128), 2);
-        k_walk_tables<<<grid, 128, 0, s>>>(W, A0, A1, axis, m->n_gp, m->err, segc);
+        k_walk_tables<<<(unsigned)((m->n_gp + 127) / 128), 128, 0, s>>>(W, A0, A1, axis, m->n_gp,
+                                                                          m->err, segc);
         note_launch(m);
     }
     stage_end(m, 2);
@@ -383,6 +480,73 @@ int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double
                                                   m->n_dof, m->n_gp, rows);
         note_launch(m);
     }
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+// Walk + tables for every mesh of a batch in three launches (zero, power tables, walk).
+// Scratch: device and pinned host arrays owned by the caller, sized for the batch.
+int walk_tables_batch(Mesh *const *ms, int n, const double *alpha, cudaStream_t s,
+                      BatchWalkScratch *bs) {
+    const int n_desc = 3 * n;
+    if (!bs->d_desc) {
+        FEM3_CUDA(cudaMalloc(&bs->d_desc, sizeof(WalkDesc) * n_desc));
+        FEM3_CUDA(cudaMallocHost(&bs->h_desc, sizeof(WalkDesc) * n_desc));
+        FEM3_CUDA(cudaMalloc(&bs->d_zptr, sizeof(double *) * 2 * n_desc));
+        FEM3_CUDA(cudaMalloc(&bs->d_zlen, sizeof(int64_t) * 2 * n_desc));
+        FEM3_CUDA(cudaMallocHost(&bs->h_zptr, sizeof(double *) * 2 * n_desc));
+        FEM3_CUDA(cudaMallocHost(&bs->h_zlen, sizeof(int64_t) * 2 * n_desc));
+    }
+    WalkDesc *hd = reinterpret_cast<WalkDesc *>(bs->h_desc);
+    double **zp = reinterpret_cast<double **>(bs->h_zptr);
+    int64_t *zl = reinterpret_cast<int64_t *>(bs->h_zlen);
+    int64_t items = 0;
+    int64_t max_tab = 0;
+    for (int i = 0; i < n; i++) {
+        Mesh *m = ms[i];
+        if (!m->pow_cell) {
+            FEM3_TRY(dev_alloc_t(m, &m->pow_cell, 3 * 256 * 8));
+            FEM3_TRY(dev_alloc_t(m, &m->pow_exp, 3 * 128));
+        }
+        WalkGeom W = make_geom(m);
+        for (int axis = 0; axis < 3; axis++) {
+            AxisBins &B = m->bins[axis];
+            const double gamma = alpha[3 * i + axis] / 2.0;
+            const double ig = 1.0 / tgamma(2.0 - gamma);
+            WalkDesc &D = hd[3 * i + axis];
+            D.W = W;
+            D.A0 = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
+                             B.tab_ld, m->tabL[axis], 1.0 - gamma, ig,
+                             m->pow_cell + (size_t)axis * 256 * 8, m->pow_exp + axis * 128};
+            D.A1 = D.A0;
+            D.A1.tab = m->tabR[axis];
+            D.A1.coef = -ig;
+            D.axis = axis;
+            D.slot0 = items;
+            D.n_gp = m->n_gp;
+            D.err = m->err;
+            D.seg = reinterpret_cast<unsigned long long *>(m->norms + kSegCounterSlot);
+            items += m->n_gp;
+            zp[2 * (3 * i + axis)] = m->tabL[axis];
+            zl[2 * (3 * i + axis)] = B.tab_elems;
+            zp[2 * (3 * i + axis) + 1] = m->tabR[axis];
+            zl[2 * (3 * i + axis) + 1] = B.tab_elems;
+            max_tab = std::max<int64_t>(max_tab, B.tab_elems);
+        }
+        FEM3_CUDA(cudaMemsetAsync(m->norms + kSegCounterSlot, 0, sizeof(double), s));
+    }
+    FEM3_CUDA(cudaMemcpyAsync(bs->d_desc, hd, sizeof(WalkDesc) * n_desc, cudaMemcpyHostToDevice, s));
+    FEM3_CUDA(cudaMemcpyAsync(bs->d_zptr, zp, sizeof(double *) * 2 * n_desc, cudaMemcpyHostToDevice, s));
+    FEM3_CUDA(cudaMemcpyAsync(bs->d_zlen, zl, sizeof(int64_t) * 2 * n_desc, cudaMemcpyHostToDevice, s));
+    const unsigned gx = (unsigned)std::min<int64_t>(4096, std::max<int64_t>(1, (max_tab + 255) / 256));
+    k_zero_batch<<<dim3(gx, std::min(2 * n_desc, 65535)), 256, 0, s>>>(
+        reinterpret_cast<double *const *>(bs->d_zptr), reinterpret_cast<const int64_t *>(bs->d_zlen),
+        2 * n_desc);
+    k_pow_tables_batch<<<n_desc, 256, 0, s>>>(reinterpret_cast<const WalkDesc *>(bs->d_desc));
+    if (items > 0)
+        k_walk_batch<<<(unsigned)((items + 127) / 128), 128, 0, s>>>(
+            reinterpret_cast<const WalkDesc *>(bs->d_desc), n_desc, items);
+    for (int i = 0; i < n; i++) ms[i]->launches += 3;   // the batch's launches, counted per mesh
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }

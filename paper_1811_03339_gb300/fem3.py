@@ -25,7 +25,8 @@ PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2}
 # every entry point declared in include/fem3.h
 SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_load", "fem3_solve",
            "fem3_adjoint", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
-           "fem3_counters", "fem3_last_error", "fem3_mesh_free", "fem3_spd_solve_static")
+           "fem3_counters", "fem3_last_error", "fem3_mesh_free", "fem3_spd_solve_static",
+           "fem3_batch_create", "fem3_batch_mesh", "fem3_batch_run", "fem3_batch_free")
 
 _lib = None
 
@@ -70,11 +71,15 @@ def load_library(build_if_missing: bool = True):
         "fem3_last_error": [C.c_char_p, C.c_size_t],
         "fem3_mesh_free": [p],
         "fem3_spd_solve_static": [p, i64, p, p, p],
+        "fem3_batch_create": [ci, p, p, p, p, C.POINTER(Options), p, C.POINTER(p)],
+        "fem3_batch_mesh": [p, ci, C.POINTER(p)],
+        "fem3_batch_run": [p, p, p, ci, p, ci, dbl, ci, p, p, p, p],
+        "fem3_batch_free": [p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = None if name == "fem3_mesh_free" else ci
+        f.restype = None if name in ("fem3_mesh_free", "fem3_batch_free") else ci
     _lib = lib
     return lib
 
@@ -274,6 +279,72 @@ class Mesh:
     def free(self):
         if getattr(self, "h", None):
             mesh_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many meshes assembled and solved together (fem3_batch_*).
+
+    meshes: list of (verts, tets) host arrays.  run() takes per-mesh alpha and K
+    ([n][3]) and per-mesh nodal right-hand sides ([n_nodes_i, nrhs] host or device) and
+    returns per-mesh solutions ([n_dof_i, nrhs] device tensors)."""
+
+    def __init__(self, meshes, bin_scale: float = 0.5, max_steps: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        lib = load_library()
+        self.stream = stream
+        self._keep = [(np.ascontiguousarray(v, dtype=np.float64), np.ascontiguousarray(t, dtype=np.int32))
+                      for v, t in meshes]
+        n = len(self._keep)
+        vp = (C.c_void_p * n)(*[v.ctypes.data for v, _ in self._keep])
+        tp = (C.c_void_p * n)(*[t.ctypes.data for _, t in self._keep])
+        nn = (C.c_int64 * n)(*[v.shape[0] for v, _ in self._keep])
+        nt = (C.c_int64 * n)(*[t.shape[0] for _, t in self._keep])
+        opt = Options(bin_scale, max_steps, 0)
+        h = C.c_void_p()
+        _check(lib.fem3_batch_create(n, vp, nn, tp, nt, C.byref(opt), _stream(stream), C.byref(h)))
+        self.h = h
+        self.n = n
+        self.n_dof, self.n_nodes = [], []
+        for i in range(n):
+            mh = C.c_void_p()
+            _check(lib.fem3_batch_mesh(self.h, i, C.byref(mh)))
+            nd, _, _ = mesh_info(mh)
+            self.n_dof.append(nd)
+            self.n_nodes.append(self._keep[i][0].shape[0])
+
+    def run(self, alpha, K, fs, precision="tf32x3", tol=1e-12, max_iter=50):
+        t = self._torch
+        a = np.ascontiguousarray(alpha, dtype=np.float64).reshape(self.n, 3)
+        k = np.ascontiguousarray(K, dtype=np.float64).reshape(self.n, 3)
+        f_dev = []
+        nrhs = None
+        for i, f in enumerate(fs):
+            ft = t.as_tensor(f, dtype=t.float64)
+            if ft.dim() == 1:
+                ft = ft[:, None]
+            nrhs = ft.shape[1]
+            f_dev.append(ft.T.contiguous().cuda())       # column-major [n_nodes][nrhs]
+        u_dev = [t.empty((nrhs, self.n_dof[i]), dtype=t.float64, device="cuda") for i in range(self.n)]
+        fp = (C.c_void_p * self.n)(*[x.data_ptr() for x in f_dev])
+        up = (C.c_void_p * self.n)(*[x.data_ptr() for x in u_dev])
+        it = (C.c_int * self.n)()
+        rs = (C.c_double * self.n)()
+        _check(_lib.fem3_batch_run(self.h, _ptr(a), _ptr(k), PRECISIONS[precision], fp, int(nrhs),
+                                   float(tol), int(max_iter), up, it, rs, _stream(self.stream)))
+        self.iters, self.resid = list(it), list(rs)
+        return [x.T for x in u_dev]
+
+    def free(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.fem3_batch_free(self.h)
             self.h = None
 
     def __del__(self):

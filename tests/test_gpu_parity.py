@@ -171,6 +171,22 @@ def test_reassemble_same_mesh(precision):
     m.free()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("nrhs", [16, 21])
+def test_many_right_hand_sides(precision, nrhs):
+    """Columns go through the wavefront solve 16 at a time and through the table operator
+    8 at a time; every column must match the oracle."""
+    mesh, o, alpha, K = _case("cube7_jitter")
+    f = np.random.default_rng(nrhs).standard_normal((mesh.n_nodes, nrhs))
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    m.assemble(alpha, K, precision)
+    u = m.solve(f, tol=1e-13).cpu().numpy()
+    u_ref = oracle.solve(o.assemble(alpha, K), o.load(f))
+    err = np.linalg.norm(u - u_ref, axis=0) / np.linalg.norm(u_ref, axis=0)
+    assert err.max() <= (1e-10 if precision == "fp64" else 1e-8), err
+    m.free()
+
+
 def test_load_vector():
     mesh, o, alpha, K = _case("cube3_jitter")
     m = fem3.Mesh(mesh.verts, mesh.tets)
