@@ -45,7 +45,8 @@ def _peaks():
 # DRAM bytes (read + write) of one k_walk_tables launch from the ncu capture summarised in
 # profiles/k_walk_tables_cube16_jitter.md, valid only for the kernel source it was taken
 # on (sha256 of csrc/walk.cu); otherwise the traffic is reported as unknown.
-WALK_TRAFFIC = {"walk_cu_sha256": None, "bytes_per_launch": None, "segments_per_launch": None}
+WALK_TRAFFIC = {"walk_cu_sha256": "33917058bdbc94d83a117185f385933d6342e6bdde1612aa71b9f5f8d0ad408b",
+                "bytes_per_launch": 72459008 + 10040576, "segments_per_launch": 5366660}
 
 
 def _walk_traffic(segs_per_launch):
