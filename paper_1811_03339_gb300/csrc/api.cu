@@ -92,6 +92,8 @@ static int check_errors(Mesh *m) {
         return set_error(FEM3_E_CUDA, "a triangular-solve wait gave up (bounded wait expired)");
     if (e[ERR_TC])
         return set_error(FEM3_E_CUDA, "a tensor-core contraction wait gave up (bounded wait expired)");
+    if (e[ERR_CHOL])
+        return set_error(FEM3_E_CUDA, "a factorisation wait gave up (bounded wait expired)");
     return FEM3_OK;
 }
 
@@ -201,6 +203,11 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
     if ((st = dev_alloc_t(m, &m->flags, (n + 63) / 64 + 1)) != FEM3_OK) return fail(st);
     if ((st = dev_alloc(m, &m->dinv, sizeof(double) * 64 * 64 * ((n + 63) / 64))) != FEM3_OK)
         return fail(st);
+    {
+        const int64_t nblk = (n + 63) / 64;
+        if ((st = dev_alloc_t(m, &m->chol_flags, nblk * (nblk + 1) / 2 + 2)) != FEM3_OK)
+            return fail(st);
+    }
     if ((st = dev_alloc_t(m, &m->ybuf, 2 * m->n_gp)) != FEM3_OK) return fail(st);
     if (cudaMemsetAsync(m->flags, 0, sizeof(int32_t) * ((n + 63) / 64 + 1), m->stream) != cudaSuccess)
         return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));

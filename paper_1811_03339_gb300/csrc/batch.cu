@@ -99,7 +99,7 @@ static int check_mesh(Mesh *m, int i) {
         return set_error(FEM3_E_NOT_SPD, who + "non-positive pivot at column " +
                                              std::to_string(e[ERR_NOT_SPD] - 1));
     }
-    if (e[ERR_TC] || e[ERR_SOLVE]) return set_error(FEM3_E_CUDA, who + "a bounded wait expired");
+    if (e[ERR_TC] || e[ERR_SOLVE] || e[ERR_CHOL]) return set_error(FEM3_E_CUDA, who + "a bounded wait expired");
     return FEM3_OK;
 }
 

@@ -38,6 +38,7 @@ enum ErrWord {
     ERR_FACE = 4,      // non-manifold faces or hash overflow
     ERR_SOLVE = 5,     // a triangular-solve wait gave up (bounded spin)
     ERR_TC = 6,        // a tensor-core contraction pipeline wait gave up
+    ERR_CHOL = 7,      // a tile-factorisation wait gave up (bounded spin)
     ERR_COUNT = 8
 };
 
@@ -129,6 +130,7 @@ struct Mesh {
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     float *vec32[2] = {nullptr, nullptr};
     int32_t *flags = nullptr;  // wavefront triangular-solve flags (one per 64-row block)
+    int32_t *chol_flags = nullptr;  // tile-factorisation flags, then ticket and abort words
     void *dinv = nullptr;      // inverses of the 64 x 64 diagonal blocks of the factor
     double *ybuf = nullptr;    // [2][n_gp] weighted table-times-vector rows (operator apply)
     int flag_epoch = 0;        // value that marks "ready" in the current solve

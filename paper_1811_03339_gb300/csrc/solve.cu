@@ -61,92 +61,238 @@ __global__ void k_load_T(const int32_t *__restrict__ tets, const double *__restr
 // ---------------------------------------------------------------------------------
 // Cholesky
 // ---------------------------------------------------------------------------------
-// Diagonal block: factor A_kk = L_kk L_kk^T in shared memory and form L_kk^{-1}
-// (512 threads).  Factor: right-looking elimination on the unscaled columns
-// (a[i][c] -= a[i][j] a[c][j] / a[j][j]), one barrier per column, eight threads per row;
-// the thread that finishes a pivot also stores its reciprocal, so each column costs one
-// division.  The columns are scaled by 1/sqrt(pivot) at the end.  Inverse: eight lanes
-// of a warp solve L x = e_c for one column c (split inner products, shuffle reduction)
-// with precomputed 1/L_rr, no block barrier.  Linv receives the inverse (row-major
-// 64 x 64); a non-positive pivot records 1 + its column.
+constexpr int kSpinLimit = 1 << 22;   // x >= 64 ns sleep: > 0.25 s before giving up
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Diagonal block: factor A_kk = L_kk L_kk^T and form L_kk^{-1} (512 threads), blocked
+// by 16.  For each 16-column panel p (P = 16 p):
+//   S1  warp 0 factors the 16 x 16 diagonal block L_pp in registers (row per lane; the
+//       pivot column goes through a double-buffered shared vector) and inverts it by
+//       forward substitution (column of L_pp^{-1} per lane); meanwhile the other warps
+//       form T_pJ = sum_K L_pK (L^{-1})_KJ for the blocks J < p of the inverse's block
+//       row p.
+//   S2  panel L_ip = A_ip L_pp^{-T} (rows below) and (L^{-1})_pJ = -L_pp^{-1} T_pJ.
+//   S3  trailing update A_ij -= L_ip L_jp^T (lower part, rows/columns past the panel).
+// a_s holds the block (rows and columns >= nb padded with the identity) and receives L;
+// x_s receives L^{-1}.  L goes to A (rows/columns k0 .. k0 + nb), L^{-1} to Linv
+// (row-major 64 x 64); a non-positive pivot records 1 + its global column.
+template <class TF> __device__ __forceinline__ TF rsqrt_t(TF x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+template <class TF>
+__device__ __forceinline__ void lds4(const TF *p, TF v[4]) {   // 16-byte aligned (float) / 32 (double)
+    if constexpr (sizeof(TF) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 q0 = *reinterpret_cast<const double2 *>(p);
+        const double2 q1 = *reinterpret_cast<const double2 *>(p + 2);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+}
+template <class TF>
+__device__ __forceinline__ void lds2(const TF *p, TF v[2]) {
+    if constexpr (sizeof(TF) == 4) {
+        const float2 q = *reinterpret_cast<const float2 *>(p);
+        v[0] = q.x; v[1] = q.y;
+    } else {
+        const double2 q = *reinterpret_cast<const double2 *>(p);
+        v[0] = q.x; v[1] = q.y;
+    }
+}
+
+constexpr int PB = 16;   // panel width inside the diagonal block
+
+template <class TF>
+__device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, TF *A, int64_t n,
+                               int64_t k0, TF *Linv, int32_t *err) {
+    __shared__ __align__(16) TF lt[PB][PB + 4];        // lt[k][c] = (L_pp^{-1})[c][k]
+    __shared__ __align__(16) TF pant[PB][NB + 4];      // pant[k][r] = L[r][P + k], r >= P + 16
+    __shared__ __align__(16) TF tq[PB][NB - PB + 4];   // T_pJ, columns c < P
+    __shared__ __align__(16) TF colb16[2][PB];         // pivot column (16 x 16 factor)
+    __shared__ __align__(16) TF lcol[PB][PB + 4];      // lcol[k][i] = L_pp[i][k]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int p = 0; p < NB / PB; p++) {
+        const int P = p * PB;
+        // ---------------- S1 ----------------
+        if (warp == 0) {
+            const int r = lane & (PB - 1);
+            TF v[PB], rdv[PB];
+#pragma unroll
+            for (int c = 0; c < PB; c++) v[c] = c <= r ? a_s[P + r][P + c] : TF(0);
+            int bad = -1;
+#pragma unroll
+            for (int j = 0; j < PB; j++) {
+                // column j (unscaled) through a double-buffered shared vector
+                TF *cb = colb16[j & 1];
+                if (lane < PB && r >= j) cb[r] = v[j];
+                __syncwarp();
+                TF col[PB];
+#pragma unroll
+                for (int k = 0; k < PB; k += 4) lds4<TF>(cb + k, col + k);
+                const TF d = col[j];
+                if (!(d > TF(0)) && bad < 0) bad = j;
+                const TF rs = d > TF(0) ? rsqrt_t<TF>(d) : TF(1);
+                rdv[j] = rs;
+                const TF f = v[j] * rs * rs;   // a[r][j] / d
+#pragma unroll
+                for (int k = 1; k < PB; k++)
+                    if (k > j && r >= k) v[k] -= f * col[k];
+                v[j] = r == j ? d * rs : v[j] * rs;
+            }
+            if (bad >= 0 && lane == 0 && P + bad < nb)
+                atomicCAS(&err[ERR_NOT_SPD], 0, (int32_t)(k0 + P + bad + 1));
+            if (lane < PB) {
+#pragma unroll
+                for (int c = 0; c < PB; c++) {
+                    if (c <= r) a_s[P + r][P + c] = v[c];
+                    lcol[c][r] = v[c];   // zero above the diagonal
+                }
+            }
+            __syncwarp();
+            // column cc of L_pp^{-1}: t_k = (delta_kc - sum_{i<k} L_ki t_i) / L_kk
+            const int cc = lane & (PB - 1);
+            TF t[PB];
+#pragma unroll
+            for (int i = 0; i < PB; i++) t[i] = i == cc ? TF(1) : TF(0);
+#pragma unroll
+            for (int k = 0; k < PB; k++) {
+                t[k] *= rdv[k];
+                TF lc[PB];
+#pragma unroll
+                for (int i = 0; i < PB; i += 4) lds4<TF>(&lcol[k][i], lc + i);
+#pragma unroll
+                for (int i = 1; i < PB; i++)
+                    if (i > k) t[i] -= lc[i] * t[k];
+            }
+            if (lane < PB) {
+#pragma unroll
+                for (int i = 0; i < PB; i++) {
+                    x_s[P + i][P + cc] = i >= cc ? t[i] : TF(0);
+                    lt[cc][i] = t[i];
+                }
+            }
+        } else if (p > 0) {
+            // T_pJ[i][c] = sum_{k = c}^{P-1} L[P + i][k] (L^{-1})[k][c], by 16-wide k blocks
+            for (int e = tid - 32; e < PB * P; e += blockDim.x - 32) {
+                const int i = e / P, c = e - i * P;
+                TF acc = TF(0);
+                for (int kb = c & ~(PB - 1); kb < P; kb += PB) {
+#pragma unroll
+                    for (int k = 0; k < PB; k++)
+                        if (kb + k >= c) acc += a_s[P + i][kb + k] * x_s[kb + k][c];
+                }
+                tq[i][c] = acc;
+            }
+        }
+        __syncthreads();
+        // ---------------- S2 (into registers) ----------------
+        const int m = NB - P - PB;   // panel rows below the diagonal block
+        TF pv[4] = {TF(0), TF(0), TF(0), TF(0)};
+        const int pr = P + PB + (tid >> 2), pc = (tid & 3) * 4;
+        const bool panel = tid < 4 * m;
+        if (panel) {
+#pragma unroll
+            for (int k = 0; k < PB; k++) {
+                const TF av = a_s[pr][P + k];
+                TF lv[4];
+                lds4<TF>(&lt[k][pc], lv);
+#pragma unroll
+                for (int q = 0; q < 4; q++) pv[q] += av * lv[q];
+            }
+        }
+        TF iv[3] = {TF(0), TF(0), TF(0)};
+        if (tid >= 256 && p > 0) {
+#pragma unroll
+            for (int s2 = 0; s2 < 3; s2++) {
+                const int e = (tid - 256) + 256 * s2;
+                if (s2 < p) {
+                    const int i = e / P, c = e - i * P;
+                    TF acc = TF(0);
+#pragma unroll
+                    for (int k = 0; k < PB; k++)
+                        if (k <= i) acc += x_s[P + i][P + k] * tq[k][c];
+                    iv[s2] = -acc;
+                }
+            }
+        }
+        __syncthreads();
+        if (panel) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                a_s[pr][P + pc + q] = pv[q];
+                pant[pc + q][pr] = pv[q];
+            }
+        }
+        if (tid >= 256 && p > 0) {
+#pragma unroll
+            for (int s2 = 0; s2 < 3; s2++) {
+                const int e = (tid - 256) + 256 * s2;
+                if (s2 < p) {
+                    const int i = e / P, c = e - i * P;
+                    x_s[P + i][c] = iv[s2];
+                }
+            }
+        }
+        __syncthreads();
+        // ---------------- S3: trailing update ----------------
+        const int T0 = P + PB;
+        if (T0 < NB) {
+            const int tx = tid & 15, ty = tid >> 4;
+            const int i0 = ty * 2, j0 = tx * 4;
+            if (i0 >= T0 && j0 >= T0 && j0 <= i0 + 1) {
+                TF acc[2][4];
+#pragma unroll
+                for (int a2 = 0; a2 < 2; a2++)
+#pragma unroll
+                    for (int b2 = 0; b2 < 4; b2++) acc[a2][b2] = TF(0);
+#pragma unroll
+                for (int k = 0; k < PB; k++) {
+                    TF u[2], w[4];
+                    lds2<TF>(&pant[k][i0], u);
+                    lds4<TF>(&pant[k][j0], w);
+#pragma unroll
+                    for (int a2 = 0; a2 < 2; a2++)
+#pragma unroll
+                        for (int b2 = 0; b2 < 4; b2++) acc[a2][b2] += u[a2] * w[b2];
+                }
+#pragma unroll
+                for (int a2 = 0; a2 < 2; a2++)
+#pragma unroll
+                    for (int b2 = 0; b2 < 4; b2++)
+                        if (j0 + b2 <= i0 + a2) a_s[i0 + a2][j0 + b2] -= acc[a2][b2];
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int i = e >> 6, c = e & 63;
+        if (i < nb && c < nb) A[(k0 + i) * n + k0 + c] = c <= i ? a_s[i][c] : TF(0);
+        Linv[e] = c <= i ? x_s[i][c] : TF(0);
+    }
+}
+
 template <class TF>
 __device__ void potrf_inv_block(TF *A, int64_t n, int k0, TF *Linv, int32_t *err,
                                 unsigned char *smem_raw) {
     TF(*a)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
-    TF(*li)[NB + 1] = a + NB;
-    __shared__ TF rinv[NB], rsq[NB], sq[NB];
     const int nb = (int)min((int64_t)NB, n - k0);
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        int i = e / NB, j = e % NB;
+        const int i = e / NB, j = e % NB;
         a[i][j] = (i < nb && j < nb) ? A[(int64_t)(k0 + i) * n + k0 + j]
                                      : (i == j ? TF(1) : TF(0));
     }
     __syncthreads();
-    if (threadIdx.x == 0) rinv[0] = a[0][0] > TF(0) ? TF(1) / a[0][0] : TF(1);
-    __syncthreads();
-    const int row = threadIdx.x >> 3, q = threadIdx.x & 7;
-    for (int j = 0; j < NB - 1; j++) {
-        if (row > j) {
-            const TF f = a[row][j] * rinv[j];
-            TF cv[8];
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int c = j + 1 + q + 8 * u;
-                cv[u] = c <= row ? a[c][j] : TF(0);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int c = j + 1 + q + 8 * u;
-                if (c <= row) a[row][c] -= f * cv[u];
-            }
-            // the owner of the next pivot publishes its reciprocal
-            if (row == j + 1 && q == 0) {
-                const TF d = a[j + 1][j + 1];
-                rinv[j + 1] = d > TF(0) ? TF(1) / d : TF(1);
-            }
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x < NB) {
-        const int j = threadIdx.x;
-        const TF d = a[j][j];
-        if (j < nb && !(d > TF(0))) atomicCAS(&err[ERR_NOT_SPD], 0, k0 + j + 1);
-        const TF r = sqrt(d > TF(0) ? d : TF(1));
-        sq[j] = r;
-        rsq[j] = TF(1) / r;
-    }
-    __syncthreads();
-    // L[i][j] = a[i][j] / sqrt(d_j) (i > j), L[j][j] = sqrt(d_j); li holds L
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        const int i = e / NB, j = e % NB;
-        li[i][j] = i == j ? sq[j] : (i > j ? a[i][j] * rsq[j] : TF(0));
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        const int i = e / nb, j = e % nb;
-        A[(int64_t)(k0 + i) * n + k0 + j] = li[i][j];
-    }
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) a[e / NB][e % NB] = li[e / NB][e % NB];
-    if (threadIdx.x < NB) rinv[threadIdx.x] = rsq[threadIdx.x];   // 1 / L_rr
-    __syncthreads();
-    {
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        const int c = w * 4 + (lane >> 3), part = lane & 7;
-        for (int r = 0; r < NB; r++) {
-            TF sacc = TF(0);
-            if (r > c)
-                for (int k = c + part; k < r; k += 8) sacc += a[r][k] * li[k][c];
-            sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
-            sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
-            sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
-            const TF x = r < c ? TF(0) : ((r == c ? TF(1) : TF(0)) - sacc) * rinv[r];
-            __syncwarp();
-            if (part == 0) li[r][c] = x;
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Linv[e] = li[e / NB][e % NB];
+    potrf_inv_smem<TF>(a, a + NB, nb, A, n, k0, Linv, err);
 }
 
 template <class TF>
@@ -191,7 +337,7 @@ __global__ void __launch_bounds__(256) k_trsm_gemm(TF *A, int64_t n, int k0, con
 // block and, when Linv_next is given, factors it right away (look-ahead), so that the
 // next panel solve can start as soon as this launch ends.
 template <class TF>
-__global__ void __launch_bounds__(512) k_syrk(TF *A, int64_t n, int k0, TF *Linv_next,
+__global__ void __launch_bounds__(512, sizeof(TF) == 4 ? 2 : 1) k_syrk(TF *A, int64_t n, int k0, TF *Linv_next,
                                               int32_t *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // blockIdx.x enumerates lower tiles (ti >= tj) of the trailing matrix
@@ -241,6 +387,160 @@ __global__ void __launch_bounds__(512) k_syrk(TF *A, int64_t n, int k0, TF *Linv
     if (Linv_next != nullptr && blockIdx.x == 0) {
         __syncthreads();   // this CTA's writes of the diagonal tile are visible to it
         potrf_inv_block<TF>(A, n, (int)base, Linv_next, err, smem_raw);
+    }
+}
+
+
+// ---------------------------------------------------------------------------------
+// Tile-task Cholesky in one launch.  Tasks T(i, j) over the lower 64 x 64 tiles are
+// numbered column by column (j, then i >= j) and handed out by an atomic ticket.  T(i, j)
+// subtracts L_ik L_jk^T for k < j, each as soon as tiles (i, k) and (j, k) are final, then
+// either factors the diagonal tile (i == j: L_jj and L_jj^{-1}) or solves
+// L_ij = A_ij L_jj^{-T}, stores the tile and publishes its flag.  Every dependency of a
+// task has a smaller ticket, so the earliest unfinished claimed task always has what it
+// needs: the launch needs no co-residency.  Waits are bounded; a wait that expires sets
+// the abort word, which every other wait also watches, and records ERR_CHOL.
+// flags: [ntask] tile flags (1 = final), [ntask] ticket, [ntask + 1] abort word; all zero
+// at launch.
+// ---------------------------------------------------------------------------------
+constexpr int kTileLd = NB + 4;
+
+__device__ __forceinline__ int tile_id(int i, int j) { return i * (i + 1) / 2 + j; }
+
+__device__ __forceinline__ bool wait_tile(const int *f, int *abort_w, int32_t *err) {
+    int spins = 0;
+    while (ld_acquire_gpu(f) == 0) {
+        if (ld_acquire_gpu(abort_w) != 0) return false;
+        if (++spins > kSpinLimit) {
+            atomicAdd(&err[ERR_CHOL], 1);
+            atomicExch(abort_w, 1);
+            return false;
+        }
+        if (spins > 64) __nanosleep(32);
+    }
+    return true;
+}
+
+// dst[c][r] = src[r * ld + c] (r < rows, else 0), c < 64; 512 threads, 8 columns each.
+// L2 loads: the tile was written by another CTA of the same launch.
+template <class TF>
+__device__ __forceinline__ void load_tile_T(const TF *src, int64_t ld, int64_t rows,
+                                            TF (*dst)[kTileLd]) {
+    const int r = threadIdx.x & 63, c0 = (threadIdx.x >> 6) * 8;
+    TF v[8];
+    if (r < rows) {
+        const TF *p = src + (int64_t)r * ld + c0;
+#pragma unroll
+        for (int e = 0; e < 8; e++) v[e] = __ldcg(p + e);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; e++) v[e] = TF(0);
+    }
+#pragma unroll
+    for (int e = 0; e < 8; e++) dst[c0 + e][r] = v[e];
+}
+
+template <class TF>
+__global__ void __launch_bounds__(512, sizeof(TF) == 4 ? 2 : 1) k_chol_tiles(TF *A, int64_t n, int nblk, TF *dinv,
+                                                    int *flags, int32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TF(*b0)[kTileLd] = reinterpret_cast<TF(*)[kTileLd]>(smem_raw);
+    TF(*b1)[kTileLd] = b0 + NB;
+    TF(*a)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);   // overlays b0 only
+    __shared__ int s_task, s_ok;
+    const int ntask = nblk * (nblk + 1) / 2;
+    int *ticket = flags + ntask, *abort_w = flags + ntask + 1;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;   // rows ty*2+{0,1}, cols tx*4+{0..3}
+    for (;;) {
+        if (tid == 0) s_task = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int t = s_task;
+        if (t >= ntask) return;
+        int j = 0, rem = t;
+        while (rem >= nblk - j) { rem -= nblk - j; j++; }
+        const int i = j + rem;
+        const int64_t r0 = (int64_t)i * NB, c0 = (int64_t)j * NB;
+        const int64_t rows_i = n - r0;
+        TF acc[2][4];
+#pragma unroll
+        for (int p = 0; p < 2; p++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int r = ty * 2 + p, c = tx * 4 + q;
+                acc[p][q] = (r < rows_i && c0 + c < n) ? A[(r0 + r) * n + c0 + c]
+                                                       : ((i == j && r == c) ? TF(1) : TF(0));
+            }
+        for (int k = 0; k < j; k++) {
+            if (tid == 0)
+                s_ok = wait_tile(&flags[tile_id(i, k)], abort_w, err) &&
+                       wait_tile(&flags[tile_id(j, k)], abort_w, err);
+            __syncthreads();
+            if (!s_ok) return;
+            load_tile_T<TF>(A + r0 * n + (int64_t)k * NB, n, rows_i, b0);
+            if (i != j) load_tile_T<TF>(A + c0 * n + (int64_t)k * NB, n, n - c0, b1);
+            __syncthreads();
+            TF(*bj)[kTileLd] = i == j ? b0 : b1;
+#pragma unroll 8
+            for (int c = 0; c < NB; c++) {
+                TF u[2], v[4];
+#pragma unroll
+                for (int p = 0; p < 2; p++) u[p] = b0[c][ty * 2 + p];
+#pragma unroll
+                for (int q = 0; q < 4; q++) v[q] = bj[c][tx * 4 + q];
+#pragma unroll
+                for (int p = 0; p < 2; p++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) acc[p][q] = fma(-u[p], v[q], acc[p][q]);
+            }
+            __syncthreads();
+        }
+        if (i == j) {
+#pragma unroll
+            for (int p = 0; p < 2; p++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) a[ty * 2 + p][tx * 4 + q] = acc[p][q];
+            __syncthreads();
+            potrf_inv_smem<TF>(a, reinterpret_cast<TF(*)[NB + 1]>(&b1[0][0]),
+                               (int)min((int64_t)NB, rows_i), A, n, c0,
+                               dinv + (int64_t)j * NB * NB, err);
+        } else {
+#pragma unroll
+            for (int p = 0; p < 2; p++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) a[ty * 2 + p][tx * 4 + q] = acc[p][q];
+            if (tid == 0) s_ok = wait_tile(&flags[tile_id(j, j)], abort_w, err);
+            __syncthreads();
+            if (!s_ok) return;
+            load_tile_T<TF>(dinv + (int64_t)j * NB * NB, NB, NB, b1);   // b1[q][c] = Linv[c][q]
+            __syncthreads();
+            TF o[2][4];
+#pragma unroll
+            for (int p = 0; p < 2; p++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) o[p][q] = TF(0);
+#pragma unroll 8
+            for (int c = 0; c < NB; c++) {
+                TF u[2], v[4];
+#pragma unroll
+                for (int p = 0; p < 2; p++) u[p] = a[ty * 2 + p][c];
+#pragma unroll
+                for (int q = 0; q < 4; q++) v[q] = b1[c][tx * 4 + q];
+#pragma unroll
+                for (int p = 0; p < 2; p++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) o[p][q] = fma(u[p], v[q], o[p][q]);
+            }
+#pragma unroll
+            for (int p = 0; p < 2; p++) {
+                const int r = ty * 2 + p;
+                if (r >= rows_i) continue;
+#pragma unroll
+                for (int q = 0; q < 4; q++) A[(r0 + r) * n + c0 + tx * 4 + q] = o[p][q];
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) st_release_gpu(&flags[tile_id(i, j)], 1);
     }
 }
 
@@ -309,16 +609,6 @@ __global__ void k_trsv_bwd_update(const TF *L, int64_t n, int k0, int nb, TF *y)
 // depends on as their flags are published, solves its diagonal block and publishes
 // its own flag.  Every wait is bounded; a timeout sets ERR_SOLVE and the CTA returns.
 // ---------------------------------------------------------------------------------
-constexpr int kSpinLimit = 1 << 22;   // x >= 64 ns sleep: > 0.25 s before giving up
-
-__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_gpu(int *p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // backward = 0: solve L y = b in place; backward = 1: solve L^T x = y in place.
 // Dinv holds the inverses of the 64 x 64 diagonal blocks (written by the factorisation),
@@ -651,6 +941,29 @@ int cholesky_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
     return FEM3_OK;
 }
 
+template <class TF>
+int chol_tiles_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
+    if (n <= 0) return FEM3_OK;
+    const int nblk = (int)((n + NB - 1) / NB);
+    const int ntask = nblk * (nblk + 1) / 2;
+    const size_t sh = 2 * NB * kTileLd * sizeof(TF);
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+        int dev = 0;
+        FEM3_CUDA(cudaGetDevice(&dev));
+        FEM3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        FEM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_tiles<TF>, 512, sh));
+        if (per_sm < 1) per_sm = 1;
+    }
+    FEM3_CUDA(cudaMemsetAsync(m->chol_flags, 0, sizeof(int32_t) * (ntask + 2), s));
+    const int grid = std::min(ntask, per_sm * sms);
+    k_chol_tiles<TF><<<grid, 512, sh, s>>>(A, n, nblk, reinterpret_cast<TF *>(m->dinv),
+                                           m->chol_flags, m->err);
+    note_launch(m);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
 // L y = b then L^T x = y, in place; cooperative wavefront kernel when all block CTAs
 // fit on the device at once, otherwise blocked substitution with one launch per block.
 template <class TF>
@@ -780,6 +1093,87 @@ __global__ void __launch_bounds__(256) k_apply_cols(
     }
 }
 
+// Eight vectors at a time with interleaved storage: u8[dof][8], y8[slot][8], so that the
+// eight values a thread needs per table element are one contiguous 64-byte read.
+__global__ void __launch_bounds__(256) k_apply_rows8(
+    const double *__restrict__ tabL, const double *__restrict__ tabR,
+    const int32_t *__restrict__ slot_bin, const int32_t *__restrict__ gp_off,
+    const double *__restrict__ w_slot, const int32_t *__restrict__ dof_off,
+    const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
+    const int32_t *__restrict__ tab_ld, int64_t n_gp, const double *__restrict__ u8,
+    double *yL8, double *yR8) {
+    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (slot >= n_gp) return;
+    const int b = slot_bin[slot];
+    const int r = (int)(slot - gp_off[b]);
+    const int d0 = dof_off[b], D = dof_off[b + 1] - d0, ld = tab_ld[b];
+    const double *Lc = tabL + tab_off[b] + r, *Rc = tabR + tab_off[b] + r;
+    double sl[8], sr[8];
+#pragma unroll
+    for (int v = 0; v < 8; v++) { sl[v] = 0; sr[v] = 0; }
+    for (int c = 0; c < D; c++) {
+        const int64_t o = (int64_t)c * ld;
+        const double lv = Lc[o], rv = Rc[o];
+        const double2 *up = reinterpret_cast<const double2 *>(u8 + 8 * (int64_t)dof_idx[d0 + c]);
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const double2 uv = __ldg(up + h);
+            sl[2 * h] = fma(lv, uv.x, sl[2 * h]);
+            sl[2 * h + 1] = fma(lv, uv.y, sl[2 * h + 1]);
+            sr[2 * h] = fma(rv, uv.x, sr[2 * h]);
+            sr[2 * h + 1] = fma(rv, uv.y, sr[2 * h + 1]);
+        }
+    }
+    const double wv = w_slot[slot];
+    double2 *yl = reinterpret_cast<double2 *>(yL8 + 8 * slot);
+    double2 *yr = reinterpret_cast<double2 *>(yR8 + 8 * slot);
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+        yl[h] = make_double2(wv * sl[2 * h], wv * sl[2 * h + 1]);
+        yr[h] = make_double2(wv * sr[2 * h], wv * sr[2 * h + 1]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_apply_cols8(
+    const double *__restrict__ tabL, const double *__restrict__ tabR,
+    const int32_t *__restrict__ row_bin, const int32_t *__restrict__ gp_off,
+    const int32_t *__restrict__ dof_off, const int32_t *__restrict__ dof_idx,
+    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld, int64_t n_rows,
+    const double *__restrict__ yL8, const double *__restrict__ yR8, double sK, int nv,
+    double *Au, int64_t ldA) {
+    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n_rows) return;
+    const int b = row_bin[row];
+    const int c = (int)(row - dof_off[b]);
+    const int g0 = gp_off[b], G = gp_off[b + 1] - g0, ld = tab_ld[b];
+    const double *Lr = tabL + tab_off[b] + (int64_t)c * ld, *Rr = tabR + tab_off[b] + (int64_t)c * ld;
+    double z[8];
+#pragma unroll
+    for (int v = 0; v < 8; v++) z[v] = 0;
+    for (int r = lane; r < G; r += 32) {
+        const double lv = Lr[r], rv = Rr[r];
+        const double2 *yr = reinterpret_cast<const double2 *>(yR8 + 8 * (int64_t)(g0 + r));
+        const double2 *yl = reinterpret_cast<const double2 *>(yL8 + 8 * (int64_t)(g0 + r));
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const double2 a = yr[h], q = yl[h];
+            z[2 * h] = fma(lv, a.x, fma(rv, q.x, z[2 * h]));
+            z[2 * h + 1] = fma(lv, a.y, fma(rv, q.y, z[2 * h + 1]));
+        }
+    }
+    // butterfly: every lane ends with all eight totals; lane v stores total v
+#pragma unroll
+    for (int v = 0; v < 8; v++)
+        for (int o = 16; o > 0; o >>= 1) z[v] += __shfl_xor_sync(0xffffffffu, z[v], o);
+    if (lane < 8 && lane < nv) {
+        double zz = z[0];
+#pragma unroll
+        for (int v = 1; v < 8; v++) if (lane == v) zz = z[v];
+        atomicAdd(&Au[(int64_t)lane * ldA + dof_idx[row]], sK * zz);
+    }
+}
+
 // per-axis forms sum_g w_g ((L lam)(R u) + (R lam)(L u)) (adjoint), one CTA per bin
 __global__ void __launch_bounds__(256) k_axis_form(
     const double *__restrict__ tabL, const double *__restrict__ tabR,
@@ -863,6 +1257,15 @@ __global__ void k_residual_cols(const double *__restrict__ b, const double *__re
         atomicAdd(&norms[2 * c], rr);
         atomicAdd(&norms[2 * c + 1], bb);
     }
+}
+
+// u8[i][v] = u[v * n + i] for v < nv, zero for nv <= v < 8
+__global__ void k_interleave8(const double *__restrict__ u, int64_t n, int nv, double *u8) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 8 * n) return;
+    const int64_t i = e >> 3;
+    const int v = (int)(e & 7);
+    u8[e] = v < nv ? u[(int64_t)v * n + i] : 0.0;
 }
 
 __global__ void k_to_f32(const double *__restrict__ a, float *b, int64_t n) {
@@ -1009,6 +1412,10 @@ static int chol_attributes() {
     FEM3_CUDA(cudaFuncSetAttribute(k_potrf_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32));
     FEM3_CUDA(cudaFuncSetAttribute(k_trsm_gemm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32));
     FEM3_CUDA(cudaFuncSetAttribute(k_syrk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32));
+    FEM3_CUDA(cudaFuncSetAttribute(k_chol_tiles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(2 * NB * kTileLd * sizeof(double))));
+    FEM3_CUDA(cudaFuncSetAttribute(k_chol_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(2 * NB * kTileLd * sizeof(float))));
     return FEM3_OK;
 }
 
@@ -1059,8 +1466,14 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
         yL = m->ybuf;
     }
     double *yR = yL + (int64_t)group * m->n_gp;
+    double *u8 = nullptr;
+    if (group > 1) FEM3_CUDA(cudaMallocAsync((void **)&u8, sizeof(double) * 8 * std::max<int64_t>(1, n), s));
     for (int v0 = 0; v0 < nv; v0 += group) {
         const int cnt = std::min(group, nv - v0);
+        if (group > 1) {
+            k_interleave8<<<g256(8 * n), 256, 0, s>>>(u_d + v0 * n, n, cnt, u8);
+            note_launch(m);
+        }
         for (int axis = 0; axis < 3; axis++) {
             AxisBins &B = m->bins[axis];
             if (B.n_tmpl == 0) continue;
@@ -1075,19 +1488,21 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
                     Au_d + v0 * n, n);
                 note_launch(m);
             } else {
-                k_apply_rows<8><<<g256(m->n_gp), 256, 0, s>>>(
+                k_apply_rows8<<<g256(m->n_gp), 256, 0, s>>>(
                     m->tabL[axis], m->tabR[axis], B.slot_bin, B.gp_off, B.w_slot, B.dof_off,
-                    B.dof_idx, B.tab_off, B.tab_ld, m->n_gp, u_d + v0 * n, n, cnt, yL, yR);
+                    B.dof_idx, B.tab_off, B.tab_ld, m->n_gp, u8, yL, yR);
                 note_launch(m);
-                k_apply_cols<8><<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
+                k_apply_cols8<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
                     m->tabL[axis], m->tabR[axis], B.row_bin, B.gp_off, B.dof_off, B.dof_idx,
-                    B.tab_off, B.tab_ld, B.n_tmpl, m->n_gp, yL, yR, m->sK[axis], cnt,
-                    Au_d + v0 * n, n);
+                    B.tab_off, B.tab_ld, B.n_tmpl, yL, yR, m->sK[axis], cnt, Au_d + v0 * n, n);
                 note_launch(m);
             }
         }
     }
-    if (group > 1) FEM3_CUDA(cudaFreeAsync(yL, s));
+    if (group > 1) {
+        FEM3_CUDA(cudaFreeAsync(yL, s));
+        FEM3_CUDA(cudaFreeAsync(u8, s));
+    }
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
