@@ -136,8 +136,6 @@ void fem3_mesh_free(fem3_mesh h) {
     dev_free_all(m);
     cudaStreamSynchronize(m->stream);
     if (m->h_norms) cudaFreeHost(m->h_norms);
-    for (int k = 0; k < 2; k++)
-        if (m->chol_exec[k]) cudaGraphExecDestroy(m->chol_exec[k]);
     if (m->ev_made)
         for (int k = 0; k < 16; k++) cudaEventDestroy(m->ev[k]);
     delete m;
@@ -205,7 +203,7 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
         return fail(st);
     {
         const int64_t nblk = (n + 63) / 64;
-        if ((st = dev_alloc_t(m, &m->chol_flags, nblk * (nblk + 1) / 2 + 2)) != FEM3_OK)
+        if ((st = dev_alloc_t(m, &m->chol_flags, nblk * (nblk + 1) + 2)) != FEM3_OK)
             return fail(st);
     }
     if ((st = dev_alloc_t(m, &m->ybuf, 2 * m->n_gp)) != FEM3_OK) return fail(st);

@@ -121,9 +121,6 @@ struct Mesh {
     double *A64 = nullptr;     // [n_dof][n_dof]
     float *A32 = nullptr;      // [n_dof][n_dof]
     bool factored = false;
-    cudaGraphExec_t chol_exec[2] = {nullptr, nullptr};   // factorisation graphs (FP64, FP32)
-    int64_t chol_launches[2] = {0, 0};
-    int factor_count[2] = {0, 0};
     bool tc_ready = false;
 
     // workspaces

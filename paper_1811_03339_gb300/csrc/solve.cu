@@ -85,7 +85,14 @@ __device__ __forceinline__ void st_release_gpu(int *p, int v) {
 // x_s receives L^{-1}.  L goes to A (rows/columns k0 .. k0 + nb), L^{-1} to Linv
 // (row-major 64 x 64); a non-positive pivot records 1 + its global column.
 template <class TF> __device__ __forceinline__ TF rsqrt_t(TF x);
-template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+// FP32: hardware estimate plus one Newton step y <- y + y (1 - x y^2) / 2, so that the
+// factor is as accurate as one built from a correctly rounded square root (refinement
+// then converges in as many sweeps).
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) {
+    const float y = rsqrtf(x);
+    const float r = fmaf(-x * y, y, 1.0f);
+    return fmaf(0.5f * y, r, y);
+}
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
 
 template <class TF>
@@ -278,132 +285,30 @@ __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, TF 
         const int i = e >> 6, c = e & 63;
         if (i < nb && c < nb) A[(k0 + i) * n + k0 + c] = c <= i ? a_s[i][c] : TF(0);
         Linv[e] = c <= i ? x_s[i][c] : TF(0);
+        if (c > i) x_s[i][c] = TF(0);   // x_s = L^{-1} in full for callers that keep it
     }
 }
-
-template <class TF>
-__device__ void potrf_inv_block(TF *A, int64_t n, int k0, TF *Linv, int32_t *err,
-                                unsigned char *smem_raw) {
-    TF(*a)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
-    const int nb = (int)min((int64_t)NB, n - k0);
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        const int i = e / NB, j = e % NB;
-        a[i][j] = (i < nb && j < nb) ? A[(int64_t)(k0 + i) * n + k0 + j]
-                                     : (i == j ? TF(1) : TF(0));
-    }
-    __syncthreads();
-    potrf_inv_smem<TF>(a, a + NB, nb, A, n, k0, Linv, err);
-}
-
-template <class TF>
-__global__ void __launch_bounds__(512) k_potrf_inv(TF *A, int64_t n, int k0, TF *Linv,
-                                                   int32_t *err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    potrf_inv_block<TF>(A, n, k0, Linv, err, smem_raw);
-}
-
-// Panel rows [k0+NB, n): X = B L_kk^{-T}, i.e. X[r][c] = sum_k B[r][k] Linv[c][k].
-template <class TF>
-__global__ void __launch_bounds__(256) k_trsm_gemm(TF *A, int64_t n, int k0, const TF *Linv) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TF(*bt)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
-    TF(*li)[NB + 1] = bt + NB;
-    const int64_t row0 = k0 + NB + (int64_t)blockIdx.x * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        int i = e / NB, j = e % NB;
-        bt[i][j] = (row0 + i < n) ? A[(row0 + i) * n + k0 + j] : TF(0);
-        li[i][j] = Linv[e];
-    }
-    __syncthreads();
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    TF acc[4][4];
-    for (int p = 0; p < 4; p++)
-        for (int q = 0; q < 4; q++) acc[p][q] = TF(0);
-    for (int k = 0; k < NB; k++) {
-        TF u[4], v[4];
-        for (int p = 0; p < 4; p++) { u[p] = bt[ty * 4 + p][k]; v[p] = li[tx * 4 + p][k]; }
-        for (int p = 0; p < 4; p++)
-            for (int q = 0; q < 4; q++) acc[p][q] = fma(u[p], v[q], acc[p][q]);
-    }
-    for (int p = 0; p < 4; p++) {
-        int64_t r = row0 + ty * 4 + p;
-        if (r >= n) continue;
-        for (int q = 0; q < 4; q++) A[r * n + k0 + tx * 4 + q] = acc[p][q];
-    }
-}
-
-// trailing update of lower tiles: A[i][j] -= sum_c P[i][c] P[j][c], P = panel columns
-// (512 threads, 2 x 4 outputs each).  The CTA of tile (0, 0) updates the next diagonal
-// block and, when Linv_next is given, factors it right away (look-ahead), so that the
-// next panel solve can start as soon as this launch ends.
-template <class TF>
-__global__ void __launch_bounds__(512, sizeof(TF) == 4 ? 2 : 1) k_syrk(TF *A, int64_t n, int k0, TF *Linv_next,
-                                              int32_t *err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // blockIdx.x enumerates lower tiles (ti >= tj) of the trailing matrix
-    int idx = blockIdx.x, ti = 0;
-    while (idx > ti) { idx -= ti + 1; ti++; }
-    int tj = idx;
-    const int64_t base = k0 + NB;
-    const int64_t i0 = base + (int64_t)ti * NB, j0 = base + (int64_t)tj * NB;
-    {
-        TF(*pi)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);
-        TF(*pj)[NB + 1] = pi + NB;
-        for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-            int r = e / NB, c = e % NB;
-            pi[r][c] = (i0 + r < n) ? A[(i0 + r) * n + k0 + c] : TF(0);
-            pj[r][c] = (j0 + r < n) ? A[(j0 + r) * n + k0 + c] : TF(0);
-        }
-        __syncthreads();
-        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // ty: 0..31
-        TF acc[2][4];
-#pragma unroll
-        for (int a = 0; a < 2; a++)
-#pragma unroll
-            for (int b = 0; b < 4; b++) acc[a][b] = TF(0);
-        for (int c = 0; c < NB; c++) {
-            TF u[2], v[4];
-#pragma unroll
-            for (int a = 0; a < 2; a++) u[a] = pi[ty * 2 + a][c];
-#pragma unroll
-            for (int b = 0; b < 4; b++) v[b] = pj[tx * 4 + b][c];
-#pragma unroll
-            for (int a = 0; a < 2; a++)
-#pragma unroll
-                for (int b = 0; b < 4; b++) acc[a][b] = fma(u[a], v[b], acc[a][b]);
-        }
-#pragma unroll
-        for (int a = 0; a < 2; a++) {
-            int64_t r = i0 + ty * 2 + a;
-            if (r >= n) continue;
-#pragma unroll
-            for (int b = 0; b < 4; b++) {
-                int64_t c = j0 + tx * 4 + b;
-                if (c >= n || c > r) continue;
-                A[r * n + c] -= acc[a][b];
-            }
-        }
-    }
-    if (Linv_next != nullptr && blockIdx.x == 0) {
-        __syncthreads();   // this CTA's writes of the diagonal tile are visible to it
-        potrf_inv_block<TF>(A, n, (int)base, Linv_next, err, smem_raw);
-    }
-}
-
 
 // ---------------------------------------------------------------------------------
-// Tile-task Cholesky in one launch.  Tasks T(i, j) over the lower 64 x 64 tiles are
-// numbered column by column (j, then i >= j) and handed out by an atomic ticket.  T(i, j)
-// subtracts L_ik L_jk^T for k < j, each as soon as tiles (i, k) and (j, k) are final, then
-// either factors the diagonal tile (i == j: L_jj and L_jj^{-1}) or solves
-// L_ij = A_ij L_jj^{-T}, stores the tile and publishes its flag.  Every dependency of a
-// task has a smaller ticket, so the earliest unfinished claimed task always has what it
-// needs: the launch needs no co-residency.  Waits are bounded; a wait that expires sets
-// the abort word, which every other wait also watches, and records ERR_CHOL.
-// flags: [ntask] tile flags (1 = final), [ntask] ticket, [ntask + 1] abort word; all zero
-// at launch.
+// Tile-task Cholesky in one launch.  CTA 0 runs the diagonal chain: for each block
+// column j it applies the last update (k = j - 1) to the diagonal tile, factors it
+// (L_jj and L_jj^{-1}), solves the tile below it, L_{j+1,j} = A_{j+1,j} L_jj^{-T}, and
+// keeps that tile in shared memory for the next diagonal update, so the critical path
+// never leaves one SM.  The other CTAs take tasks W(i, j) over the lower 64 x 64 tiles
+// from an atomic ticket, column by column: W(i, j) subtracts L_ik L_jk^T for k < j (for a
+// diagonal tile k < j - 1), each as soon as tiles (i, k) and (j, k) are final; the
+// diagonal and sub-diagonal tiles are then stored for the chain ("updated" flag U),
+// every other tile is solved with L_jj^{-1} once the chain has published it and stored
+// as final (flag F).  Every task depends only on tiles of earlier columns (or, for the
+// solve, on the chain's step j), and tickets are taken in column order, so the earliest
+// unfinished claimed task always proceeds and the launch needs no co-residency.  Waits
+// are bounded; a wait that expires sets the abort word, which every other wait also
+// watches, and records ERR_CHOL.
+// flags: F [0, ntask), U [ntask, 2 ntask), ticket [2 ntask], abort word [2 ntask + 1];
+// all zero at launch.
 // ---------------------------------------------------------------------------------
 constexpr int kTileLd = NB + 4;
+constexpr int kCholTilesSmem = 3 * NB * kTileLd;   // elements of dynamic shared memory
 
 __device__ __forceinline__ int tile_id(int i, int j) { return i * (i + 1) / 2 + j; }
 
@@ -440,16 +345,154 @@ __device__ __forceinline__ void load_tile_T(const TF *src, int64_t ld, int64_t r
     for (int e = 0; e < 8; e++) dst[c0 + e][r] = v[e];
 }
 
+// acc[p][q] += sgn * sum_c bi[c][ty*2+p] bj[c][tx*4+q] (operands in transposed layout).
+// The 64-term product is summed from zero and added to acc once: summing into acc
+// directly would round every term at the magnitude of the (much larger) tile entry,
+// which made the FP32 factor several times less accurate.
+template <class TF, bool SUB>
+__device__ __forceinline__ void tile_gemm_T(TF acc[2][4], const TF (*bi)[kTileLd],
+                                            const TF (*bj)[kTileLd], int tx, int ty) {
+    TF t[2][4];
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) t[p][q] = TF(0);
+#pragma unroll 8
+    for (int c = 0; c < NB; c++) {
+        TF u[2], v[4];
+        lds2<TF>(&bi[c][ty * 2], u);
+        lds4<TF>(&bj[c][tx * 4], v);
+#pragma unroll
+        for (int p = 0; p < 2; p++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) t[p][q] = fma(u[p], v[q], t[p][q]);
+    }
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[p][q] = SUB ? acc[p][q] - t[p][q] : acc[p][q] + t[p][q];
+}
+
+// load tile (r0, c0) of A into acc (rows/columns beyond n: identity on the diagonal tile)
 template <class TF>
-__global__ void __launch_bounds__(512, sizeof(TF) == 4 ? 2 : 1) k_chol_tiles(TF *A, int64_t n, int nblk, TF *dinv,
-                                                    int *flags, int32_t *err) {
+__device__ __forceinline__ void load_acc(const TF *A, int64_t n, int64_t r0, int64_t c0,
+                                         bool diag, TF acc[2][4], int tx, int ty) {
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int r = ty * 2 + p, c = tx * 4 + q;
+            acc[p][q] = (r0 + r < n && c0 + c < n) ? __ldcg(&A[(r0 + r) * n + c0 + c])
+                                                   : ((diag && r == c) ? TF(1) : TF(0));
+        }
+}
+
+template <class TF>
+__device__ __forceinline__ void store_acc(TF *A, int64_t n, int64_t r0, int64_t c0,
+                                          const TF acc[2][4], int tx, int ty) {
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        const int r = ty * 2 + p;
+        if (r0 + r >= n) continue;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (c0 + tx * 4 + q < n) A[(r0 + r) * n + c0 + tx * 4 + q] = acc[p][q];
+    }
+}
+
+// all threads' global stores of a tile are visible before its flag
+__device__ __forceinline__ void publish(int *f) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release_gpu(f, 1);
+}
+
+template <class TF>
+__device__ void chol_chain(TF *A, int64_t n, int nblk, TF *dinv, int *F, int *U, int *abort_w,
+                           int32_t *err, unsigned char *smem_raw) {
+    TF(*b0)[kTileLd] = reinterpret_cast<TF(*)[kTileLd]>(smem_raw);
+    TF(*b1)[kTileLd] = b0 + NB;
+    TF(*xt)[kTileLd] = b1 + NB;   // L_{j,j-1}^T of the previous step
+    TF(*a_s)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(&b0[0][0]);
+    TF(*x_s)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(&b1[0][0]);
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    for (int j = 0; j < nblk; j++) {
+        const int64_t c0 = (int64_t)j * NB;
+        if (tid == 0) s_ok = wait_tile(&U[tile_id(j, j)], abort_w, err);
+        __syncthreads();
+        if (!s_ok) return;
+        TF acc[2][4];
+        load_acc<TF>(A, n, c0, c0, true, acc, tx, ty);
+        if (j > 0) tile_gemm_T<TF, true>(acc, xt, xt, tx, ty);
+#pragma unroll
+        for (int p = 0; p < 2; p++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) a_s[ty * 2 + p][tx * 4 + q] = acc[p][q];
+        __syncthreads();
+        potrf_inv_smem<TF>(a_s, x_s, (int)min((int64_t)NB, n - c0), A, n, c0,
+                           dinv + (int64_t)j * NB * NB, err);
+        publish(&F[tile_id(j, j)]);
+        if (j + 1 >= nblk) break;
+        // L_{j+1,j} = A_{j+1,j} L_jj^{-T}, computed transposed: X^T = L_jj^{-1} A_{j+1,j}^T
+        const int64_t r0 = c0 + NB;
+        if (tid == 0) s_ok = wait_tile(&U[tile_id(j + 1, j)], abort_w, err);
+        __syncthreads();
+        if (!s_ok) return;
+        load_tile_T<TF>(A + r0 * n + c0, n, n - r0, b0);   // b0[k][r] = A_{j+1,j}[r][k]
+        __syncthreads();
+        TF o[2][4];
+#pragma unroll
+        for (int p = 0; p < 2; p++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) o[p][q] = TF(0);
+#pragma unroll 8
+        for (int k = 0; k < NB; k++) {
+            TF v[4];
+            lds4<TF>(&b0[k][tx * 4], v);
+            const TF u0 = x_s[ty * 2][k], u1 = x_s[ty * 2 + 1][k];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                o[0][q] = fma(u0, v[q], o[0][q]);
+                o[1][q] = fma(u1, v[q], o[1][q]);
+            }
+        }
+        // o[p][q] = L_{j+1,j}[tx*4+q][ty*2+p]
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+            TF *dst = &xt[ty * 2 + p][tx * 4];
+            if constexpr (sizeof(TF) == 4) {
+                *reinterpret_cast<float4 *>(dst) = make_float4(o[p][0], o[p][1], o[p][2], o[p][3]);
+            } else {
+                *reinterpret_cast<double2 *>(dst) = make_double2(o[p][0], o[p][1]);
+                *reinterpret_cast<double2 *>(dst + 2) = make_double2(o[p][2], o[p][3]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int64_t r = r0 + tx * 4 + q;
+            if (r < n) {
+                A[r * n + c0 + ty * 2] = o[0][q];
+                A[r * n + c0 + ty * 2 + 1] = o[1][q];
+            }
+        }
+        publish(&F[tile_id(j + 1, j)]);
+    }
+}
+
+template <class TF>
+__global__ void __launch_bounds__(512, 1) k_chol_tiles(TF *A, int64_t n, int nblk, TF *dinv,
+                                                       int *flags, int32_t *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TF(*b0)[kTileLd] = reinterpret_cast<TF(*)[kTileLd]>(smem_raw);
     TF(*b1)[kTileLd] = b0 + NB;
-    TF(*a)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);   // overlays b0 only
     __shared__ int s_task, s_ok;
     const int ntask = nblk * (nblk + 1) / 2;
-    int *ticket = flags + ntask, *abort_w = flags + ntask + 1;
+    int *F = flags, *U = flags + ntask, *ticket = flags + 2 * ntask, *abort_w = ticket + 1;
+    if (blockIdx.x == 0) {
+        chol_chain<TF>(A, n, nblk, dinv, F, U, abort_w, err, smem_raw);
+        return;
+    }
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;   // rows ty*2+{0,1}, cols tx*4+{0..3}
     for (;;) {
         if (tid == 0) s_task = atomicAdd(ticket, 1);
@@ -461,86 +504,56 @@ __global__ void __launch_bounds__(512, sizeof(TF) == 4 ? 2 : 1) k_chol_tiles(TF 
         const int i = j + rem;
         const int64_t r0 = (int64_t)i * NB, c0 = (int64_t)j * NB;
         const int64_t rows_i = n - r0;
+        const int kmax = i == j ? max(j - 1, 0) : j;   // the chain applies k = j - 1 to (j, j)
         TF acc[2][4];
-#pragma unroll
-        for (int p = 0; p < 2; p++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int r = ty * 2 + p, c = tx * 4 + q;
-                acc[p][q] = (r < rows_i && c0 + c < n) ? A[(r0 + r) * n + c0 + c]
-                                                       : ((i == j && r == c) ? TF(1) : TF(0));
-            }
-        for (int k = 0; k < j; k++) {
+        load_acc<TF>(A, n, r0, c0, false, acc, tx, ty);
+        for (int k = 0; k < kmax; k++) {
             if (tid == 0)
-                s_ok = wait_tile(&flags[tile_id(i, k)], abort_w, err) &&
-                       wait_tile(&flags[tile_id(j, k)], abort_w, err);
+                s_ok = wait_tile(&F[tile_id(i, k)], abort_w, err) &&
+                       wait_tile(&F[tile_id(j, k)], abort_w, err);
             __syncthreads();
             if (!s_ok) return;
             load_tile_T<TF>(A + r0 * n + (int64_t)k * NB, n, rows_i, b0);
             if (i != j) load_tile_T<TF>(A + c0 * n + (int64_t)k * NB, n, n - c0, b1);
             __syncthreads();
-            TF(*bj)[kTileLd] = i == j ? b0 : b1;
-#pragma unroll 8
-            for (int c = 0; c < NB; c++) {
-                TF u[2], v[4];
-#pragma unroll
-                for (int p = 0; p < 2; p++) u[p] = b0[c][ty * 2 + p];
-#pragma unroll
-                for (int q = 0; q < 4; q++) v[q] = bj[c][tx * 4 + q];
-#pragma unroll
-                for (int p = 0; p < 2; p++)
-#pragma unroll
-                    for (int q = 0; q < 4; q++) acc[p][q] = fma(-u[p], v[q], acc[p][q]);
-            }
+            tile_gemm_T<TF, true>(acc, b0, i == j ? b0 : b1, tx, ty);
             __syncthreads();
         }
-        if (i == j) {
-#pragma unroll
-            for (int p = 0; p < 2; p++)
-#pragma unroll
-                for (int q = 0; q < 4; q++) a[ty * 2 + p][tx * 4 + q] = acc[p][q];
-            __syncthreads();
-            potrf_inv_smem<TF>(a, reinterpret_cast<TF(*)[NB + 1]>(&b1[0][0]),
-                               (int)min((int64_t)NB, rows_i), A, n, c0,
-                               dinv + (int64_t)j * NB * NB, err);
-        } else {
-#pragma unroll
-            for (int p = 0; p < 2; p++)
-#pragma unroll
-                for (int q = 0; q < 4; q++) a[ty * 2 + p][tx * 4 + q] = acc[p][q];
-            if (tid == 0) s_ok = wait_tile(&flags[tile_id(j, j)], abort_w, err);
-            __syncthreads();
-            if (!s_ok) return;
-            load_tile_T<TF>(dinv + (int64_t)j * NB * NB, NB, NB, b1);   // b1[q][c] = Linv[c][q]
-            __syncthreads();
-            TF o[2][4];
-#pragma unroll
-            for (int p = 0; p < 2; p++)
-#pragma unroll
-                for (int q = 0; q < 4; q++) o[p][q] = TF(0);
-#pragma unroll 8
-            for (int c = 0; c < NB; c++) {
-                TF u[2], v[4];
-#pragma unroll
-                for (int p = 0; p < 2; p++) u[p] = a[ty * 2 + p][c];
-#pragma unroll
-                for (int q = 0; q < 4; q++) v[q] = b1[c][tx * 4 + q];
-#pragma unroll
-                for (int p = 0; p < 2; p++)
-#pragma unroll
-                    for (int q = 0; q < 4; q++) o[p][q] = fma(u[p], v[q], o[p][q]);
-            }
-#pragma unroll
-            for (int p = 0; p < 2; p++) {
-                const int r = ty * 2 + p;
-                if (r >= rows_i) continue;
-#pragma unroll
-                for (int q = 0; q < 4; q++) A[(r0 + r) * n + c0 + tx * 4 + q] = o[p][q];
-            }
+        if (i <= j + 1) {
+            // diagonal or sub-diagonal tile: the chain finishes it
+            store_acc<TF>(A, n, r0, c0, acc, tx, ty);
+            publish(&U[tile_id(i, j)]);
+            continue;
         }
-        __threadfence();
+        // L_ij = A_ij L_jj^{-T}: o[p][q] = sum_c acc[ty*2+p][c] Linv[tx*4+q][c]
+        TF(*a)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);   // overlays b0 only
+#pragma unroll
+        for (int p = 0; p < 2; p++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) a[ty * 2 + p][tx * 4 + q] = acc[p][q];
+        if (tid == 0) s_ok = wait_tile(&F[tile_id(j, j)], abort_w, err);
         __syncthreads();
-        if (tid == 0) st_release_gpu(&flags[tile_id(i, j)], 1);
+        if (!s_ok) return;
+        load_tile_T<TF>(dinv + (int64_t)j * NB * NB, NB, NB, b1);   // b1[c][q] = Linv[q][c]
+        __syncthreads();
+        TF o[2][4];
+#pragma unroll
+        for (int p = 0; p < 2; p++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) o[p][q] = TF(0);
+#pragma unroll 8
+        for (int c = 0; c < NB; c++) {
+            TF v[4];
+            lds4<TF>(&b1[c][tx * 4], v);
+            const TF u0 = a[ty * 2][c], u1 = a[ty * 2 + 1][c];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                o[0][q] = fma(u0, v[q], o[0][q]);
+                o[1][q] = fma(u1, v[q], o[1][q]);
+            }
+        }
+        store_acc<TF>(A, n, r0, c0, o, tx, ty);
+        publish(&F[tile_id(i, j)]);
     }
 }
 
@@ -920,45 +933,21 @@ __global__ void __launch_bounds__(256) k_btrsm_update(const BatchTrsmDesc *__res
 }
 
 template <class TF>
-int cholesky_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
-    const size_t sh = 2 * NB * (NB + 1) * sizeof(TF);
-    TF *dinv = reinterpret_cast<TF *>(m->dinv);   // inverses of the diagonal blocks, kept
-    if (n <= 0) return FEM3_OK;
-    k_potrf_inv<TF><<<1, 512, sh, s>>>(A, n, 0, dinv, m->err);
-    note_launch(m);
-    for (int64_t k0 = 0; k0 < n; k0 += NB) {
-        int64_t rest = n - k0 - NB;
-        if (rest <= 0) break;
-        TF *Linv = dinv + (k0 / NB) * NB * NB;
-        int nblk = (int)((rest + NB - 1) / NB);
-        k_trsm_gemm<TF><<<nblk, 256, sh, s>>>(A, n, (int)k0, Linv);
-        note_launch(m);
-        int ntiles = nblk * (nblk + 1) / 2;
-        k_syrk<TF><<<ntiles, 512, sh, s>>>(A, n, (int)k0, Linv + NB * NB, m->err);
-        note_launch(m);
-    }
-    FEM3_CUDA(cudaGetLastError());
-    return FEM3_OK;
-}
-
-template <class TF>
 int chol_tiles_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
     if (n <= 0) return FEM3_OK;
     const int nblk = (int)((n + NB - 1) / NB);
     const int ntask = nblk * (nblk + 1) / 2;
-    const size_t sh = 2 * NB * kTileLd * sizeof(TF);
-    static int per_sm = 0, sms = 0;
-    if (per_sm == 0) {
+    static int sms = 0;
+    if (sms == 0) {
         int dev = 0;
         FEM3_CUDA(cudaGetDevice(&dev));
         FEM3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        FEM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_tiles<TF>, 512, sh));
-        if (per_sm < 1) per_sm = 1;
     }
-    FEM3_CUDA(cudaMemsetAsync(m->chol_flags, 0, sizeof(int32_t) * (ntask + 2), s));
-    const int grid = std::min(ntask, per_sm * sms);
-    k_chol_tiles<TF><<<grid, 512, sh, s>>>(A, n, nblk, reinterpret_cast<TF *>(m->dinv),
-                                           m->chol_flags, m->err);
+    FEM3_CUDA(cudaMemsetAsync(m->chol_flags, 0, sizeof(int32_t) * (2 * ntask + 2), s));
+    // one CTA per SM: the chain CTA gets an SM of its own
+    const int grid = std::min(ntask + 1, std::max(sms, 2));
+    k_chol_tiles<TF><<<grid, 512, kCholTilesSmem * sizeof(TF), s>>>(
+        A, n, nblk, reinterpret_cast<TF *>(m->dinv), m->chol_flags, m->err);
     note_launch(m);
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
@@ -1405,51 +1394,20 @@ int load_vector_T(Mesh *m, const double *lam_d, double *out_d) {
 // (a new assemble with other alpha or K on the same mesh) captures the sequence into a
 // CUDA graph on a private stream, and later ones replay the graph on the caller's stream.
 static int chol_attributes() {
-    const size_t sh64 = 2 * NB * (NB + 1) * sizeof(double), sh32 = 2 * NB * (NB + 1) * sizeof(float);
-    FEM3_CUDA(cudaFuncSetAttribute(k_potrf_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh64));
-    FEM3_CUDA(cudaFuncSetAttribute(k_trsm_gemm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh64));
-    FEM3_CUDA(cudaFuncSetAttribute(k_syrk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh64));
-    FEM3_CUDA(cudaFuncSetAttribute(k_potrf_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32));
-    FEM3_CUDA(cudaFuncSetAttribute(k_trsm_gemm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32));
-    FEM3_CUDA(cudaFuncSetAttribute(k_syrk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh32));
+    static bool done = false;
+    if (done) return FEM3_OK;
     FEM3_CUDA(cudaFuncSetAttribute(k_chol_tiles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(2 * NB * kTileLd * sizeof(double))));
+                                   (int)(kCholTilesSmem * sizeof(double))));
     FEM3_CUDA(cudaFuncSetAttribute(k_chol_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(2 * NB * kTileLd * sizeof(float))));
+                                   (int)(kCholTilesSmem * sizeof(float))));
+    done = true;
     return FEM3_OK;
 }
 
 int factor(Mesh *m) {
-    const int slot = m->precision == FEM3_FP64 ? 0 : 1;
     FEM3_TRY(chol_attributes());
-    if (m->factor_count[slot]++ == 0) {
-        if (slot == 0) return cholesky_t<double>(m->A64, m->n_dof, m->stream, m);
-        return cholesky_t<float>(m->A32, m->n_dof, m->stream, m);
-    }
-    if (!m->chol_exec[slot]) {
-        cudaStream_t cs;
-        FEM3_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        int st = FEM3_OK;
-        if (e == cudaSuccess) {
-            const int64_t launches0 = m->launches;
-            st = slot == 0 ? cholesky_t<double>(m->A64, m->n_dof, cs, m)
-                           : cholesky_t<float>(m->A32, m->n_dof, cs, m);
-            m->chol_launches[slot] = m->launches - launches0;
-            m->launches = launches0;
-            e = cudaStreamEndCapture(cs, &g);
-        }
-        if (e == cudaSuccess && st == FEM3_OK)
-            e = cudaGraphInstantiate(&m->chol_exec[slot], g, 0);
-        if (g) cudaGraphDestroy(g);
-        cudaStreamDestroy(cs);
-        if (st != FEM3_OK) return st;
-        if (e != cudaSuccess) return cuda_error(e, "factorisation graph capture");
-    }
-    FEM3_CUDA(cudaGraphLaunch(m->chol_exec[slot], m->stream));
-    m->launches += m->chol_launches[slot];
-    return FEM3_OK;
+    if (m->precision == FEM3_FP64) return chol_tiles_t<double>(m->A64, m->n_dof, m->stream, m);
+    return chol_tiles_t<float>(m->A32, m->n_dof, m->stream, m);
 }
 
 // Au = A u for nv vectors (column-major, leading dimension n_dof), applied in FP64 from
