@@ -198,7 +198,11 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
     if ((st = bins_build(m)) != FEM3_OK) return fail(st);
     stage_end(m, 1);
     const int64_t n = std::max<int64_t>(1, m->n_dof);
-    if ((st = dev_alloc_t(m, &m->flags, (n + 63) / 64 + 1)) != FEM3_OK) return fail(st);
+    if ((st = dev_alloc_t(m, &m->flags, 2 * ((n + 63) / 64) + 2)) != FEM3_OK) return fail(st);
+    if ((st = dev_alloc(m, &m->solve_ws, sizeof(double) * 64 * 16 * ((n + 63) / 64))) != FEM3_OK)
+        return fail(st);
+    if ((st = dev_alloc(m, &m->solve_G, sizeof(double) * 2 * 3 * 64 * 64 * ((n + 63) / 64))) != FEM3_OK)
+        return fail(st);
     if ((st = dev_alloc(m, &m->dinv, sizeof(double) * 64 * 64 * ((n + 63) / 64))) != FEM3_OK)
         return fail(st);
     {
@@ -207,7 +211,7 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
             return fail(st);
     }
     if ((st = dev_alloc_t(m, &m->ybuf, 2 * m->n_gp)) != FEM3_OK) return fail(st);
-    if (cudaMemsetAsync(m->flags, 0, sizeof(int32_t) * ((n + 63) / 64 + 1), m->stream) != cudaSuccess)
+    if (cudaMemsetAsync(m->flags, 0, sizeof(int32_t) * (2 * ((n + 63) / 64) + 2), m->stream) != cudaSuccess)
         return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
     for (int k = 0; k < 6; k++)
         if ((st = dev_alloc_t(m, &m->vec64[k], std::max<int64_t>(std::max<int64_t>(n, m->n_nodes),

@@ -126,7 +126,9 @@ struct Mesh {
     // workspaces
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     float *vec32[2] = {nullptr, nullptr};
-    int32_t *flags = nullptr;  // wavefront triangular-solve flags (one per 64-row block)
+    int32_t *flags = nullptr;  // triangular-solve flags: [2 nblk + 2]
+    void *solve_ws = nullptr;  // triangular-solve z blocks: nblk x 64 x 16 doubles
+    void *solve_G = nullptr;   // triangular-solve chain operators: nblk x 2 x 3 x 64 x 64 doubles
     int32_t *chol_flags = nullptr;  // tile-factorisation flags, then ticket and abort words
     void *dinv = nullptr;      // inverses of the 64 x 64 diagonal blocks of the factor
     double *ybuf = nullptr;    // [2][n_gp] weighted table-times-vector rows (operator apply)

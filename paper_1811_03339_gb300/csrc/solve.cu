@@ -400,9 +400,9 @@ __device__ __forceinline__ void store_acc(TF *A, int64_t n, int64_t r0, int64_t 
     }
 }
 
-// all threads' global stores of a tile are visible before its flag
+// all threads' global stores of a tile are visible before its flag: the barrier orders
+// them before thread 0's release, which is cumulative
 __device__ __forceinline__ void publish(int *f) {
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) st_release_gpu(f, 1);
 }
@@ -557,309 +557,8 @@ __global__ void __launch_bounds__(512, 1) k_chol_tiles(TF *A, int64_t n, int nbl
     }
 }
 
-// ---------------------------------------------------------------------------------
-// triangular solves (single right-hand side, in place in y)
-// ---------------------------------------------------------------------------------
-// forward: y_k <- L_kk^{-1} y_k (one warp), then y_i -= L_ik y_k for rows below
-template <class TF>
-__global__ void k_trsv_fwd_diag(const TF *L, int64_t n, int k0, TF *y) {
-    __shared__ TF ys[NB];
-    const int nb = (int)min((int64_t)NB, n - k0);
-    const int lane = threadIdx.x;
-    for (int i = lane; i < nb; i += 32) ys[i] = y[k0 + i];
-    __syncwarp();
-    for (int j = 0; j < nb; j++) {
-        TF s = TF(0);
-        for (int c = lane; c < j; c += 32) s += L[(int64_t)(k0 + j) * n + k0 + c] * ys[c];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) ys[j] = (ys[j] - s) / L[(int64_t)(k0 + j) * n + k0 + j];
-        __syncwarp();
-    }
-    for (int i = lane; i < nb; i += 32) y[k0 + i] = ys[i];
-}
-
-template <class TF>
-__global__ void k_trsv_fwd_update(const TF *L, int64_t n, int k0, TF *y) {
-    // one warp per row below the block
-    int64_t row = k0 + NB + (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (row >= n) return;
-    TF s = L[row * n + k0 + lane] * y[k0 + lane] + L[row * n + k0 + 32 + lane] * y[k0 + 32 + lane];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) y[row] -= s;
-}
-
-// backward with L^T: block k solved with L_kk^T, then y_i -= sum_c L[k0+c][i] y[k0+c]
-template <class TF>
-__global__ void k_trsv_bwd_diag(const TF *L, int64_t n, int k0, TF *y) {
-    __shared__ TF ys[NB];
-    const int nb = (int)min((int64_t)NB, n - k0);
-    const int lane = threadIdx.x;
-    for (int i = lane; i < nb; i += 32) ys[i] = y[k0 + i];
-    __syncwarp();
-    for (int j = nb - 1; j >= 0; j--) {
-        TF s = TF(0);
-        for (int c = j + 1 + lane; c < nb; c += 32) s += L[(int64_t)(k0 + c) * n + k0 + j] * ys[c];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) ys[j] = (ys[j] - s) / L[(int64_t)(k0 + j) * n + k0 + j];
-        __syncwarp();
-    }
-    for (int i = lane; i < nb; i += 32) y[k0 + i] = ys[i];
-}
-
-template <class TF>
-__global__ void k_trsv_bwd_update(const TF *L, int64_t n, int k0, int nb, TF *y) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k0) return;
-    TF s = TF(0);
-    for (int c = 0; c < nb; c++) s += L[(int64_t)(k0 + c) * n + i] * y[k0 + c];
-    y[i] -= s;
-}
-
-// ---------------------------------------------------------------------------------
-// Wavefront triangular solve: one CTA per 64-row block, all CTAs co-resident
-// (cooperative launch).  CTA for block i accumulates the products with the blocks it
-// depends on as their flags are published, solves its diagonal block and publishes
-// its own flag.  Every wait is bounded; a timeout sets ERR_SOLVE and the CTA returns.
-// ---------------------------------------------------------------------------------
-
-// backward = 0: solve L y = b in place; backward = 1: solve L^T x = y in place.
-// Dinv holds the inverses of the 64 x 64 diagonal blocks (written by the factorisation),
-// so the diagonal step is a product.  Each CTA loads its share of a dependency's factor
-// tile before waiting for that dependency's flag.
-template <class TF>
-__global__ void __launch_bounds__(256) k_trsv_wave(const TF *__restrict__ L,
-                                                   const TF *__restrict__ Dinv, int64_t n, TF *y,
-                                                   int *flags, int epoch, int32_t *err,
-                                                   int backward) {
-    __shared__ TF xs[NB];
-    __shared__ TF red[8][NB];
-    __shared__ TF t[NB];
-    __shared__ TF dsh[NB * NB];          // this block's diagonal inverse, loaded up front
-    __shared__ int abort_flag;
-    const int nblk = gridDim.x;
-    const int i = backward ? nblk - 1 - (int)blockIdx.x : (int)blockIdx.x;
-    const int64_t r0 = (int64_t)i * NB;
-    const int nb = (int)min((int64_t)NB, n - r0);
-    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    if (tid == 0) abort_flag = 0;
-    {
-        const TF *Dsrc = Dinv + (int64_t)i * NB * NB;
-        for (int e = tid; e < NB * NB; e += blockDim.x) dsh[e] = Dsrc[e];
-    }
-    TF acc0 = TF(0), acc1 = TF(0);   // backward: columns lane, lane + 32
-    TF accr[8];                      // forward: rows w*8 + q
-#pragma unroll
-    for (int q = 0; q < 8; q++) accr[q] = TF(0);
-    __syncthreads();
-    const int ndep = backward ? (nblk - 1 - i) : i;
-    for (int d = 0; d < ndep; d++) {
-        const int j = backward ? (nblk - 1 - d) : d;
-        const int64_t c0 = (int64_t)j * NB;
-        const int njb = (int)min((int64_t)NB, n - c0);
-        // this thread's factor values for dependency j (independent of x_j)
-        TF l0[8], l1[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int rr = w * 8 + q;
-            if (!backward) {
-                const TF *row = L + (r0 + rr) * n + c0;
-                l0[q] = (rr < nb && lane < njb) ? row[lane] : TF(0);
-                l1[q] = (rr < nb && lane + 32 < njb) ? row[lane + 32] : TF(0);
-            } else {
-                const TF *row = L + (c0 + rr) * n + r0;
-                l0[q] = (rr < njb && lane < nb) ? row[lane] : TF(0);
-                l1[q] = (rr < njb && lane + 32 < nb) ? row[lane + 32] : TF(0);
-            }
-        }
-        if (tid == 0) {
-            int spins = 0;
-            while (ld_acquire_gpu(&flags[j]) != epoch) {
-                if (++spins > kSpinLimit) {
-                    atomicAdd(&err[ERR_SOLVE], 1);
-                    abort_flag = 1;
-                    break;
-                }
-                if (spins > 64) __nanosleep(32);
-            }
-        }
-        __syncthreads();
-        if (abort_flag) return;
-        if (tid < NB) xs[tid] = tid < njb ? __ldcg(&y[c0 + tid]) : TF(0);
-        __syncthreads();
-        if (!backward) {
-#pragma unroll
-            for (int q = 0; q < 8; q++) accr[q] += l0[q] * xs[lane] + l1[q] * xs[lane + 32];
-        } else {
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const TF xv = xs[w * 8 + q];
-                acc0 += l0[q] * xv;
-                acc1 += l1[q] * xv;
-            }
-        }
-        __syncthreads();   // xs is rewritten by the next dependency
-    }
-    // t = b - (sum over dependencies)
-    if (!backward) {
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            TF v = accr[q];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) red[0][w * 8 + q] = v;
-        }
-        __syncthreads();
-        if (tid < NB) t[tid] = tid < nb ? y[r0 + tid] - red[0][tid] : TF(0);
-    } else {
-        red[w][lane] = acc0;
-        red[w][lane + 32] = acc1;
-        __syncthreads();
-        if (tid < NB) {
-            TF v = TF(0);
-            for (int q = 0; q < 8; q++) v += red[q][tid];
-            t[tid] = tid < nb ? y[r0 + tid] - v : TF(0);
-        }
-    }
-    __syncthreads();
-    // diagonal block: y_i = Dinv_i t (forward) or Dinv_i^T t (backward)
-    const TF *Di = dsh;
-    if (!backward) {
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int rr = w * 8 + q;
-            TF v = Di[rr * NB + lane] * t[lane] + Di[rr * NB + lane + 32] * t[lane + 32];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0 && rr < nb) {
-                y[r0 + rr] = v;
-                __threadfence();
-            }
-        }
-    } else {
-        TF v0 = TF(0), v1 = TF(0);
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int rr = w * 8 + q;
-            v0 += Di[rr * NB + lane] * t[rr];
-            v1 += Di[rr * NB + lane + 32] * t[rr];
-        }
-        red[w][lane] = v0;
-        red[w][lane + 32] = v1;
-        __syncthreads();
-        if (tid < nb) {
-            TF v = TF(0);
-            for (int q = 0; q < 8; q++) v += red[q][tid];
-            y[r0 + tid] = v;
-            __threadfence();
-        }
-    }
-    __syncthreads();
-    if (tid == 0) st_release_gpu(&flags[i], epoch);
-}
-
-// Multi-column wavefront solve (nrhs <= 16 columns, column-major with leading dimension
-// n).  Same block protocol as k_trsv_wave; the dependency products are small GEMMs on
-// a shared-memory copy of the factor tile, which is loaded before the dependency's
-// flag is awaited.
+// at most this many right-hand sides per triangular-solve launch
 constexpr int kMaxRhs = 16;
-
-template <class TF>
-__global__ void __launch_bounds__(256) k_trsm_wave(const TF *__restrict__ L,
-                                                   const TF *__restrict__ Dinv, int64_t n, TF *Y,
-                                                   int nrhs, int *flags, int epoch, int32_t *err,
-                                                   int backward) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TF(*lt)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);    // factor tile
-    TF(*dv)[NB + 1] = lt + NB;                                      // diagonal inverse
-    TF(*xs)[kMaxRhs + 1] = reinterpret_cast<TF(*)[kMaxRhs + 1]>(dv + NB);   // X_j
-    TF(*tt)[kMaxRhs + 1] = xs + NB;                                 // right-hand side block
-    __shared__ int abort_flag;
-    const int nblk = gridDim.x;
-    const int i = backward ? nblk - 1 - (int)blockIdx.x : (int)blockIdx.x;
-    const int64_t r0 = (int64_t)i * NB;
-    const int nb = (int)min((int64_t)NB, n - r0);
-    const int tid = threadIdx.x;
-    const int nout = NB * nrhs;
-    if (tid == 0) abort_flag = 0;
-    for (int e = tid; e < NB * NB; e += blockDim.x)
-        dv[e >> 6][e & 63] = Dinv[(int64_t)i * NB * NB + e];
-    TF acc[4] = {TF(0), TF(0), TF(0), TF(0)};   // outputs e = tid + 256 q: row e % 64, col e / 64
-    const int ndep = backward ? (nblk - 1 - i) : i;
-    for (int d = 0; d < ndep; d++) {
-        const int j = backward ? (nblk - 1 - d) : d;
-        const int64_t c0 = (int64_t)j * NB;
-        const int njb = (int)min((int64_t)NB, n - c0);
-        __syncthreads();   // previous tile and X_j no longer in use
-        for (int e = tid; e < NB * NB; e += blockDim.x) {
-            const int rr = e >> 6, cc = e & 63;
-            // forward: lt[r][k] = L[r0 + r][c0 + k]; backward: lt[r][k] = L[c0 + k][r0 + r]
-            TF v = TF(0);
-            if (!backward) {
-                if (rr < nb && cc < njb) v = L[(r0 + rr) * n + c0 + cc];
-                lt[rr][cc] = v;
-            } else {
-                if (rr < njb && cc < nb) v = L[(c0 + rr) * n + r0 + cc];
-                lt[cc][rr] = v;
-            }
-        }
-        if (tid == 0) {
-            int spins = 0;
-            while (ld_acquire_gpu(&flags[j]) != epoch) {
-                if (++spins > kSpinLimit) {
-                    atomicAdd(&err[ERR_SOLVE], 1);
-                    abort_flag = 1;
-                    break;
-                }
-                if (spins > 64) __nanosleep(32);
-            }
-        }
-        __syncthreads();
-        if (abort_flag) return;
-        for (int e = tid; e < NB * nrhs; e += blockDim.x) {
-            const int k = e & 63, c = e >> 6;
-            xs[k][c] = k < njb ? __ldcg(&Y[(int64_t)c * n + c0 + k]) : TF(0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int e = tid + 256 * q;
-            if (e < nout) {
-                const int r = e & 63, c = e >> 6;
-                TF sacc = TF(0);
-#pragma unroll 8
-                for (int k = 0; k < NB; k++) sacc += lt[r][k] * xs[k][c];
-                acc[q] += sacc;
-            }
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const int e = tid + 256 * q;
-        if (e < nout) {
-            const int r = e & 63, c = e >> 6;
-            tt[r][c] = r < nb ? Y[(int64_t)c * n + r0 + r] - acc[q] : TF(0);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const int e = tid + 256 * q;
-        if (e < nout) {
-            const int r = e & 63, c = e >> 6;
-            TF sacc = TF(0);
-            if (!backward)
-                for (int k = 0; k <= r; k++) sacc += dv[r][k] * tt[k][c];
-            else
-                for (int k = r; k < NB; k++) sacc += dv[k][r] * tt[k][c];
-            if (r < nb) {
-                Y[(int64_t)c * n + r0 + r] = sacc;
-                __threadfence();
-            }
-        }
-    }
-    __syncthreads();
-    if (tid == 0) st_release_gpu(&flags[i], epoch);
-}
 
 // ---------------------------------------------------------------------------------
 // Batched block-step triangular solves across meshes (no waiting between CTAs, so the
@@ -953,52 +652,387 @@ int chol_tiles_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
     return FEM3_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Chain triangular solves (one launch per direction, 1..16 right-hand sides).
+// Forward: y_j = Dinv_j (b_j - sum_{k<j} L_jk y_k); backward: x_j = Dinv_j^T (y_j -
+// sum_{k>j} L_kj^T x_k).  Step s solves block j(s) (j = s forward, nblk-1-s backward);
+// M(s, s') is the coefficient tile between the blocks of steps s and s' < s.
+// CTA 0 runs the chain: at step s it waits for the workers' partial sum S_s (all
+// dependencies s' < s - D), applies the D nearest tiles M(s, s-1 .. s-D) itself from
+// registers loaded one step ahead, multiplies by the diagonal inverse and publishes the
+// block (flag Yf).  Worker CTAs take steps s > D from an atomic ticket in increasing order,
+// accumulate S_s as the blocks s' <= s - D - 1 appear and publish it (flag Pf).  The
+// chain only waits for tickets that precede the ones any worker can be blocked on, so the
+// launch needs no co-residency; waits are bounded (ERR_SOLVE, abort word).
+// Y is column-major (n x nrhs, leading dimension n), solved in place.  flags: Yf [nblk],
+// Pf [nblk], ticket, abort word, all zero at launch; S: nblk x 64 x 16 workspace.
+// ---------------------------------------------------------------------------------
+constexpr int kSolveThreads = 512;            // thread (r, g): row r = t & 63, column chunk g = t >> 6
+
+template <class TF> struct SolveCfg {
+    static constexpr int D = sizeof(TF) == 4 ? 3 : 2;   // dependency tiles the chain applies itself
+};
+
+// shared memory: ring of D + 1 solved blocks [64][NR] (chain) or one dependency block and
+// one right-hand-side block (worker), and 8 partial buffers [64][NR + 1]
+template <class TF, int NR>
+constexpr size_t solve_chain_smem() {
+    return ((size_t)(SolveCfg<TF>::D + 1) * NB * NR + (size_t)8 * NB * (NR + 1)) * sizeof(TF);
+}
+
+// Precomputed chain operators.  Step s of a direction solves block j; its dependency d
+// (d < D) is the block solved at step s - 1 - d.  G(s, d) = Dm_j M(s, s-1-d), with Dm_j
+// the diagonal inverse as applied (transposed when backward) and M the coefficient tile,
+// so that the chain step is y_s = z_s - sum_d G(s, d) y_{s-1-d}, z_s = Dm_j (b_s - S_s).
+// Layout per (direction, s, d): element (r, c = 8g + e) at (g * 64 + r) * 8 + e, i.e. the
+// eight values thread (r, g) needs are 32 contiguous bytes.
+__device__ __forceinline__ int64_t gop_index(int dir, int s, int d, int nblk, int D) {
+    return (((int64_t)dir * nblk + s) * D + d) * (NB * NB);
+}
+
+__device__ __forceinline__ int solve_blk(int s, int nblk, bool backward) {
+    return backward ? nblk - 1 - s : s;
+}
+
+// NR consecutive values of a shared row (16-byte aligned when NR > 1)
+template <class TF, int NR>
+__device__ __forceinline__ void ld_row(const TF *p, TF out[NR]) {
+    if constexpr (NR == 1) {
+        out[0] = p[0];
+    } else if constexpr (sizeof(TF) == 4) {
+#pragma unroll
+        for (int k = 0; k < NR / 4; k++) {
+            const float4 q = reinterpret_cast<const float4 *>(p)[k];
+            out[4 * k] = q.x; out[4 * k + 1] = q.y; out[4 * k + 2] = q.z; out[4 * k + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NR / 2; k++) {
+            const double2 q = reinterpret_cast<const double2 *>(p)[k];
+            out[2 * k] = q.x; out[2 * k + 1] = q.y;
+        }
+    }
+}
+
+// this thread's eight entries M[r][8g .. 8g+7] of the tile between blocks j (solved) and jd
+template <class TF>
+__device__ __forceinline__ void load_coef(const TF *__restrict__ L, int64_t n, int j, int jd,
+                                          bool backward, int r, int g, TF out[8]) {
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        const int c = g * 8 + e;
+        const int64_t row = backward ? (int64_t)jd * NB + c : (int64_t)j * NB + r;
+        const int64_t col = backward ? (int64_t)j * NB + r : (int64_t)jd * NB + c;
+        out[e] = row < n ? __ldg(&L[row * n + col]) : TF(0);
+    }
+}
+
+// diagonal inverse of block j as applied at this step (transposed when backward)
+template <class TF>
+__device__ __forceinline__ void load_dinv(const TF *__restrict__ Dinv, int j, bool backward, int r,
+                                          int g, TF out[8]) {
+    const TF *Dj = Dinv + (int64_t)j * NB * NB;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        const int c = g * 8 + e;
+        out[e] = __ldg(&Dj[backward ? c * NB + r : r * NB + c]);
+    }
+}
+
+__device__ __forceinline__ bool wait_flag(const int *f, int *abort_w, int32_t *err) {
+    int spins = 0;
+    while (ld_acquire_gpu(f) == 0) {
+        if (ld_acquire_gpu(abort_w) != 0) return false;
+        if (++spins > kSpinLimit) {
+            atomicAdd(&err[ERR_SOLVE], 1);
+            atomicExch(abort_w, 1);
+            return false;
+        }
+        if (spins > 64) __nanosleep(32);
+    }
+    return true;
+}
+
+// part[v] += sum_e m[e] rows[8g + e][v], v < NR
+template <class TF, int NR>
+__device__ __forceinline__ void chunk_gemv(const TF m[8], const TF *rows, int g, TF part[NR]) {
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        TF yv[NR];
+        ld_row<TF, NR>(rows + (g * 8 + e) * NR, yv);
+#pragma unroll
+        for (int v = 0; v < NR; v++) part[v] = fma(m[e], yv[v], part[v]);
+    }
+}
+
+// red[g][r][v] = part[v]; after a barrier, the owner of (r, v) adds the eight partials
+template <class TF, int NR>
+__device__ __forceinline__ void store_partial(TF *red, int r, int g, const TF part[NR]) {
+#pragma unroll
+    for (int v = 0; v < NR; v++) red[(g * NB + r) * (NR + 1) + v] = part[v];
+}
+template <class TF, int NR>
+__device__ __forceinline__ TF sum_partials(const TF *red, int r, int v) {
+    TF t = TF(0);
+#pragma unroll
+    for (int q = 0; q < 8; q++) t += red[(q * NB + r) * (NR + 1) + v];
+    return t;
+}
+
+// G(s, d) for one direction, step and dependency (grid: nblk x D x 2 directions)
+template <class TF>
+__global__ void __launch_bounds__(256) k_solve_prep(const TF *__restrict__ L,
+                                                    const TF *__restrict__ Dinv, int64_t n,
+                                                    int nblk, TF *Gop) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int D = SolveCfg<TF>::D;
+    TF(*dm)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(smem_raw);   // Dm[r][k]
+    TF(*mm)[NB + 1] = dm + NB;                                     // M[k][c]
+    const int s = blockIdx.x, d = blockIdx.y, dir = blockIdx.z;
+    if (s - 1 - d < 0) return;
+    const bool bw = dir != 0;
+    const int j = solve_blk(s, nblk, bw), jd = solve_blk(s - 1 - d, nblk, bw);
+    const TF *Dj = Dinv + (int64_t)j * NB * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int hi = e >> 6, lo = e & 63;
+        // Dm[r][k] = Dinv_j[r][k] (forward) or Dinv_j[k][r] (backward); read row-major
+        if (!bw) dm[hi][lo] = Dj[e];
+        else dm[lo][hi] = Dj[e];
+        // M[k][c] = L[j*64 + k][jd*64 + c] (forward) or L[jd*64 + c][j*64 + k] (backward)
+        const int64_t grow = (bw ? (int64_t)jd : (int64_t)j) * NB + hi;
+        const int64_t gcol = (bw ? (int64_t)j : (int64_t)jd) * NB + lo;
+        const TF v = grow < n ? L[grow * n + gcol] : TF(0);
+        if (!bw) mm[hi][lo] = v;
+        else mm[lo][hi] = v;
+    }
+    __syncthreads();
+    TF *G = Gop + gop_index(dir, s, d, nblk, D);
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int r = e & 63, c = e >> 6;
+        TF acc = TF(0);
+#pragma unroll 8
+        for (int k = 0; k < NB; k++) acc = fma(dm[r][k], mm[k][c], acc);
+        G[((c >> 3) * NB + r) * 8 + (c & 7)] = acc;
+    }
+}
+
+template <class TF>
+__device__ __forceinline__ void load_g(const TF *G, int r, int g, TF out[8]) {
+    const TF *p = G + (g * NB + r) * 8;
+    if constexpr (sizeof(TF) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+        out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const double2 a = __ldg(reinterpret_cast<const double2 *>(p) + k);
+            out[2 * k] = a.x; out[2 * k + 1] = a.y;
+        }
+    }
+}
+
+template <class TF, int NR>
+__device__ void solve_chain(int64_t n, int nblk, TF *Y, int nrhs, bool backward, const TF *Gop,
+                            const TF *Z, int *Yf, const int *Pf, int *abort_w, int32_t *err,
+                            unsigned char *smem_raw) {
+    constexpr int D = SolveCfg<TF>::D;
+    TF *yr = reinterpret_cast<TF *>(smem_raw);        // [D + 1][64][NR] ring of solved blocks
+    TF *red = yr + (D + 1) * NB * NR;                 // [8][64][NR + 1]
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
+    const int dir = backward ? 1 : 0;
+    TF gc[D][8], gn[D][8];
+#pragma unroll
+    for (int d = 0; d < D; d++)
+#pragma unroll
+        for (int e = 0; e < 8; e++) { gc[d][e] = TF(0); gn[d][e] = TF(0); }
+    for (int s = 0; s < nblk; s++) {
+        const int j = solve_blk(s, nblk, backward);
+        const int64_t row = (int64_t)j * NB + r;
+        // warp 1 waits for z_s while thread 0 may still be publishing the last block
+        if (tid == 32) s_ok = wait_flag(&Pf[s], abort_w, err);
+        if (s + 1 < nblk) {
+#pragma unroll
+            for (int d = 0; d < D; d++)
+                if (s - d >= 0) load_g<TF>(Gop + gop_index(dir, s + 1, d, nblk, D), r, g, gn[d]);
+        }
+        TF part[NR];
+#pragma unroll
+        for (int v = 0; v < NR; v++) part[v] = TF(0);
+#pragma unroll
+        for (int d = 0; d < D; d++)
+            if (s - 1 - d >= 0)
+                chunk_gemv<TF, NR>(gc[d], yr + ((s - 1 - d) % (D + 1)) * NB * NR, g, part);
+        store_partial<TF, NR>(red, r, g, part);
+        __syncthreads();
+        if (!s_ok) return;
+        TF *ys = yr + (s % (D + 1)) * NB * NR;
+#pragma unroll
+        for (int h = 0; h < (NR + 7) / 8; h++) {
+            const int v = g + 8 * h;
+            if (v < NR) {
+                const TF y = __ldcg(&Z[((int64_t)s * NB + r) * kMaxRhs + v]) -
+                             sum_partials<TF, NR>(red, r, v);
+                ys[r * NR + v] = y;
+                if (row < n && v < nrhs) Y[row + (int64_t)v * n] = y;
+            }
+        }
+        __syncthreads();
+        // the barrier orders every thread's stores of the block before thread 0's release,
+        // which carries them to the consumers that acquire the flag (release is cumulative)
+        if (tid == 0) st_release_gpu(&Yf[s], 1);
+#pragma unroll
+        for (int d = 0; d < D; d++)
+#pragma unroll
+            for (int e = 0; e < 8; e++) gc[d][e] = gn[d][e];
+    }
+}
+
+template <class TF, int NR>
+__global__ void __launch_bounds__(kSolveThreads, 1) k_solve_chain(
+    const TF *__restrict__ L, const TF *__restrict__ Dinv, int64_t n, int nblk, TF *Y, int nrhs,
+    int backward, const TF *__restrict__ Gop, TF *Z, int *flags, int32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int D = SolveCfg<TF>::D;
+    int *Yf = flags, *Pf = flags + nblk, *ticket = flags + 2 * nblk, *abort_w = ticket + 1;
+    if (blockIdx.x == 0) {
+        solve_chain<TF, NR>(n, nblk, Y, nrhs, backward != 0, Gop, Z, Yf, Pf, abort_w, err, smem_raw);
+        return;
+    }
+    TF *yb = reinterpret_cast<TF *>(smem_raw);   // [64][NR] dependency block, then b - S
+    TF *red = yb + NB * NR;                      // [8][64][NR + 1]
+    __shared__ int s_task, s_ok;
+    const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
+    const bool bw = backward != 0;
+    for (;;) {
+        if (tid == 0) s_task = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int s = s_task;
+        if (s >= nblk) return;
+        const int j = solve_blk(s, nblk, bw);
+        TF part[NR];
+#pragma unroll
+        for (int v = 0; v < NR; v++) part[v] = TF(0);
+        TF tc[8];
+        if (s - D - 1 >= 0) load_coef<TF>(L, n, j, solve_blk(0, nblk, bw), bw, r, g, tc);
+        for (int sd = 0; sd <= s - D - 1; sd++) {
+            if (tid == 0) s_ok = wait_flag(&Yf[sd], abort_w, err);
+            __syncthreads();
+            if (!s_ok) return;
+            const int jd = solve_blk(sd, nblk, bw);
+            for (int e = tid; e < NB * NR; e += kSolveThreads) {
+                const int c = e / NR, v = e % NR;
+                const int64_t rr = (int64_t)jd * NB + c;
+                yb[e] = (rr < n && v < nrhs) ? __ldcg(&Y[rr + (int64_t)v * n]) : TF(0);
+            }
+            __syncthreads();
+            TF tn[8];
+            if (sd + 1 <= s - D - 1) load_coef<TF>(L, n, j, solve_blk(sd + 1, nblk, bw), bw, r, g, tn);
+            chunk_gemv<TF, NR>(tc, yb, g, part);
+#pragma unroll
+            for (int e = 0; e < 8; e++) tc[e] = tn[e];
+            __syncthreads();   // yb is refilled by the next dependency
+        }
+        // t = b_s - S_s into yb, then z_s = Dm_j t
+        store_partial<TF, NR>(red, r, g, part);
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < (NR + 7) / 8; h++) {
+            const int v = g + 8 * h;
+            if (v < NR) {
+                const int64_t row = (int64_t)j * NB + r;
+                const TF b = (row < n && v < nrhs) ? __ldcg(&Y[row + (int64_t)v * n]) : TF(0);
+                yb[r * NR + v] = b - sum_partials<TF, NR>(red, r, v);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < NR; v++) part[v] = TF(0);
+        {
+            TF dm[8];
+            load_dinv<TF>(Dinv, j, bw, r, g, dm);
+            chunk_gemv<TF, NR>(dm, yb, g, part);
+        }
+        store_partial<TF, NR>(red, r, g, part);
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < (NR + 7) / 8; h++) {
+            const int v = g + 8 * h;
+            if (v < NR) Z[((int64_t)s * NB + r) * kMaxRhs + v] = sum_partials<TF, NR>(red, r, v);
+        }
+        __syncthreads();
+        if (tid == 0) st_release_gpu(&Pf[s], 1);
+    }
+}
+
+template <class TF, int NR>
+static int launch_solve_chain(const TF *L, const TF *Dinv, int64_t n, int nblk, TF *Y, int nrhs,
+                              const TF *Gop, TF *Z, int workers, cudaStream_t s, Mesh *m) {
+    static bool attr = false;
+    if (!attr) {
+        FEM3_CUDA(cudaFuncSetAttribute(k_solve_chain<TF, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)solve_chain_smem<TF, NR>()));
+        attr = true;
+    }
+    for (int backward = 0; backward < 2; backward++) {
+        FEM3_CUDA(cudaMemsetAsync(m->flags, 0, sizeof(int32_t) * (2 * nblk + 2), s));
+        k_solve_chain<TF, NR><<<1 + workers, kSolveThreads, solve_chain_smem<TF, NR>(), s>>>(
+            L, Dinv, n, nblk, Y, nrhs, backward, Gop, Z, m->flags, m->err);
+        note_launch(m);
+    }
+    return FEM3_OK;
+}
+
+// Chain operators of the current factor (run once per factorisation).
+template <class TF>
+int solve_prep_t(const TF *L, int64_t n, cudaStream_t s, Mesh *m) {
+    if (n <= 0) return FEM3_OK;
+    const int nblk = (int)((n + NB - 1) / NB);
+    const size_t sh = 2 * NB * (NB + 1) * sizeof(TF);
+    static bool attr = false;
+    if (!attr) {
+        FEM3_CUDA(cudaFuncSetAttribute(k_solve_prep<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+        attr = true;
+    }
+    k_solve_prep<TF><<<dim3(nblk, SolveCfg<TF>::D, 2), 256, sh, s>>>(
+        L, reinterpret_cast<const TF *>(m->dinv), n, nblk, reinterpret_cast<TF *>(m->solve_G));
+    note_launch(m);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+// L y = b (forward) then L^T x = y (backward), in place in Y (n x nrhs, nrhs <= 16);
+// uses the operators of solve_prep_t for the same factor.
+template <class TF>
+int solve_chain_t(const TF *L, int64_t n, TF *Y, int nrhs, cudaStream_t s, Mesh *m) {
+    if (n <= 0) return FEM3_OK;
+    if (nrhs < 1 || nrhs > kMaxRhs) return set_error(FEM3_E_ARG, "1..16 right-hand sides per block solve");
+    const int nblk = (int)((n + NB - 1) / NB);
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        FEM3_CUDA(cudaGetDevice(&dev));
+        FEM3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int workers = std::max(1, std::min(nblk, sms - 1));
+    const TF *Dinv = reinterpret_cast<const TF *>(m->dinv);
+    const TF *Gop = reinterpret_cast<const TF *>(m->solve_G);
+    TF *Z = reinterpret_cast<TF *>(m->solve_ws);
+    if (nrhs == 1) FEM3_TRY((launch_solve_chain<TF, 1>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
+    else if (nrhs <= 4) FEM3_TRY((launch_solve_chain<TF, 4>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
+    else if (nrhs <= 8) FEM3_TRY((launch_solve_chain<TF, 8>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
+    else FEM3_TRY((launch_solve_chain<TF, 16>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
 // L y = b then L^T x = y, in place; cooperative wavefront kernel when all block CTAs
 // fit on the device at once, otherwise blocked substitution with one launch per block.
 template <class TF>
 int trsv_t(const TF *L, int64_t n, TF *y, cudaStream_t s, Mesh *m) {
-    if (n <= 0) return FEM3_OK;
-    int nblk = (int)((n + NB - 1) / NB);
-    int dev = 0, sms = 0, per_sm = 0, coop = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_wave<TF>, 256, 0);
-    if (m && m->flags && coop && (int64_t)per_sm * sms >= nblk) {
-        for (int backward = 0; backward < 2; backward++) {
-            int epoch = ++m->flag_epoch;
-            int32_t *err = m->err;
-            int *flags = m->flags;
-            const TF *Dinv = reinterpret_cast<const TF *>(m->dinv);
-            void *args[] = {(void *)&L, (void *)&Dinv, (void *)&n, (void *)&y, (void *)&flags,
-                            (void *)&epoch, (void *)&err, (void *)&backward};
-            FEM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_trsv_wave<TF>, dim3(nblk),
-                                                  dim3(256), args, 0, s));
-            note_launch(m);
-        }
-        return FEM3_OK;
-    }
-    for (int64_t k0 = 0; k0 < n; k0 += NB) {
-        k_trsv_fwd_diag<TF><<<1, 32, 0, s>>>(L, n, (int)k0, y);
-        note_launch(m);
-        int64_t rest = n - k0 - NB;
-        if (rest > 0) {
-            k_trsv_fwd_update<TF><<<(unsigned)((rest + 7) / 8), 256, 0, s>>>(L, n, (int)k0, y);
-            note_launch(m);
-        }
-    }
-    int64_t last = ((n - 1) / NB) * NB;
-    for (int64_t k0 = last; k0 >= 0; k0 -= NB) {
-        k_trsv_bwd_diag<TF><<<1, 32, 0, s>>>(L, n, (int)k0, y);
-        note_launch(m);
-        if (k0 > 0) {
-            int nb = (int)std::min<int64_t>(NB, n - k0);
-            k_trsv_bwd_update<TF><<<(unsigned)((k0 + 255) / 256), 256, 0, s>>>(L, n, (int)k0, nb, y);
-            note_launch(m);
-        }
-    }
-    FEM3_CUDA(cudaGetLastError());
-    return FEM3_OK;
+    return solve_chain_t<TF>(L, n, y, 1, s, m);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1321,32 +1355,7 @@ int residual_norm(Mesh *m, const double *b, const double *Au, double *rel) {
 // L Y = B then L^T X = Y for nrhs <= 16 columns (column-major, leading dimension n)
 template <class TF>
 int trsm_t(const TF *L, int64_t n, TF *Y, int nrhs, cudaStream_t s, Mesh *m) {
-    if (n <= 0) return FEM3_OK;
-    if (nrhs == 1) return trsv_t<TF>(L, n, Y, s, m);
-    const int nblk = (int)((n + NB - 1) / NB);
-    const size_t sh = (2 * NB * (NB + 1) + 2 * NB * (kMaxRhs + 1)) * sizeof(TF);
-    FEM3_CUDA(cudaFuncSetAttribute(k_trsm_wave<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    int dev = 0, sms = 0, per_sm = 0, coop = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsm_wave<TF>, 256, sh);
-    if (!(coop && (int64_t)per_sm * sms >= nblk)) {
-        for (int c = 0; c < nrhs; c++) FEM3_TRY(trsv_t<TF>(L, n, Y + (int64_t)c * n, s, m));
-        return FEM3_OK;
-    }
-    for (int backward = 0; backward < 2; backward++) {
-        int epoch = ++m->flag_epoch;
-        int32_t *err = m->err;
-        int *flags = m->flags;
-        const TF *Dinv = reinterpret_cast<const TF *>(m->dinv);
-        void *args[] = {(void *)&L, (void *)&Dinv, (void *)&n, (void *)&Y, (void *)&nrhs,
-                        (void *)&flags, (void *)&epoch, (void *)&err, (void *)&backward};
-        FEM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_trsm_wave<TF>, dim3(nblk), dim3(256),
-                                              args, sh, s));
-        note_launch(m);
-    }
-    return FEM3_OK;
+    return solve_chain_t<TF>(L, n, Y, nrhs, s, m);
 }
 
 // Forward then backward block-step sweeps over all meshes of a batch (descriptors in
@@ -1406,8 +1415,12 @@ static int chol_attributes() {
 
 int factor(Mesh *m) {
     FEM3_TRY(chol_attributes());
-    if (m->precision == FEM3_FP64) return chol_tiles_t<double>(m->A64, m->n_dof, m->stream, m);
-    return chol_tiles_t<float>(m->A32, m->n_dof, m->stream, m);
+    if (m->precision == FEM3_FP64) {
+        FEM3_TRY(chol_tiles_t<double>(m->A64, m->n_dof, m->stream, m));
+        return solve_prep_t<double>(m->A64, m->n_dof, m->stream, m);
+    }
+    FEM3_TRY(chol_tiles_t<float>(m->A32, m->n_dof, m->stream, m));
+    return solve_prep_t<float>(m->A32, m->n_dof, m->stream, m);
 }
 
 // Au = A u for nv vectors (column-major, leading dimension n_dof), applied in FP64 from
