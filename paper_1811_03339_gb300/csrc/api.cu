@@ -210,7 +210,6 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
         if ((st = dev_alloc_t(m, &m->chol_flags, nblk * (nblk + 1) + 2)) != FEM3_OK)
             return fail(st);
     }
-    if ((st = dev_alloc_t(m, &m->ybuf, 2 * m->n_gp)) != FEM3_OK) return fail(st);
     if (cudaMemsetAsync(m->flags, 0, sizeof(int32_t) * (2 * ((n + 63) / 64) + 2), m->stream) != cudaSuccess)
         return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
     for (int k = 0; k < 6; k++)
@@ -260,6 +259,7 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
     }
     m->precision = precision;
     m->factored = false;
+    m->ap_ready = false;
     FEM3_TRY(walk_tables(m, alpha));
     stage_begin(m, 3);
     if (precision == FEM3_TF32X3)

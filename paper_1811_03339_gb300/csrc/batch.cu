@@ -190,6 +190,7 @@ int fem3_batch_run(fem3_batch hb, const double *alpha, const double *K, int prec
         m->precision = precision;
         m->factored = false;
     }
+    for (int i = 0; i < n; i++) b->ms[i]->ap_ready = false;
     FEM3_TRY(walk_tables_batch(b->ms.data(), n, alpha, cs, &b->ws));
     FEM3_TRY(fork_to(b, cs));
 

@@ -115,14 +115,18 @@ __device__ __forceinline__ float tf32_rna(float x) {
 }
 
 // ------------------------------- split kernel ------------------------------------
-// One warp per template row (bin b, local dof c): coalesced reads of the FP64 table row
-// and writes of the four TF32 halves; zero past the bin's Gauss points.
-__global__ void __launch_bounds__(256) k_split_tf32(
+// One warp per template row (bin b, local dof c), lanes over the row's Gauss points:
+// coalesced reads of the FP64 table row.  Writes the operator-apply operands L and W R as
+// hi + lo FP32 pairs in the table layout and, when Lhi is given, the tensor-core operands
+// (the TF32 pairs of the same values, zero past the bin's Gauss points).  No FP64
+// arithmetic: the split and W R run in integer and FP32 operations.
+__global__ void __launch_bounds__(256) k_split_ops(
     const double *__restrict__ tabL, const double *__restrict__ tabR,
     const int32_t *__restrict__ row_bin, const int32_t *__restrict__ dof_off,
     const int32_t *__restrict__ gp_off, const double *__restrict__ w_slot,
     const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
-    int64_t n_rows, int Kp, float *Lhi, float *Llo, float *Rhi, float *Rlo) {
+    int64_t n_rows, int Kp, float *Lhi, float *Llo, float *Rhi, float *Rlo, float2 *apL,
+    float2 *apR) {
     const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n_rows) return;
@@ -131,20 +135,32 @@ __global__ void __launch_bounds__(256) k_split_tf32(
     const int g0 = gp_off[b], G = gp_off[b + 1] - g0;
     const int64_t src = tab_off[b] + (int64_t)c * tab_ld[b];
     const int64_t dst = row * (int64_t)Kp;
-    for (int k = lane; k < Kp; k += 32) {
+    const int kend = Lhi ? Kp : G;
+    for (int k = lane; k < kend; k += 32) {
         float lh = 0.f, ll = 0.f, rh = 0.f, rl = 0.f;
         if (k < G) {
-            const double l = tabL[src + k];
-            const double r = tabR[src + k] * w_slot[g0 + k];
-            lh = tf32_rna((float)l);
-            ll = tf32_rna((float)(l - (double)lh));
-            rh = tf32_rna((float)r);
-            rl = tf32_rna((float)(r - (double)rh));
+            float a, a2, r1, r2, wh, wl;
+            f64_split(tabL[src + k], a, a2);
+            f64_split(tabR[src + k], r1, r2);
+            f64_split(w_slot[g0 + k], wh, wl);
+            float sh = 0.f, sl = 0.f;
+            df_fma(r1, r2, wh, wl, sh, sl);
+            const float wr = sh + sl, wr2 = sl - (wr - sh);
+            apL[src + k] = make_float2(a, a2);
+            apR[src + k] = make_float2(wr, wr2);
+            if (Lhi) {
+                lh = tf32_rna(a);
+                ll = tf32_rna((a - lh) + a2);
+                rh = tf32_rna(wr);
+                rl = tf32_rna((wr - rh) + wr2);
+            }
         }
-        Lhi[dst + k] = lh;
-        Llo[dst + k] = ll;
-        Rhi[dst + k] = rh;
-        Rlo[dst + k] = rl;
+        if (Lhi) {
+            Lhi[dst + k] = lh;
+            Llo[dst + k] = ll;
+            Rhi[dst + k] = rh;
+            Rlo[dst + k] = rl;
+        }
     }
 }
 
@@ -354,9 +370,11 @@ int contract_tc(Mesh *m) {
             flops += 2.0 * D * D * G;
         }
         if (!B.tc_n_work) continue;
-        k_split_tf32<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
+        FEM3_TRY(ap_alloc(m, axis));
+        k_split_ops<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
             m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot, B.tab_off,
-            B.tab_ld, B.n_tmpl, B.tc_Kp, B.tc_op[0], B.tc_op[1], B.tc_op[2], B.tc_op[3]);
+            B.tab_ld, B.n_tmpl, B.tc_Kp, B.tc_op[0], B.tc_op[1], B.tc_op[2], B.tc_op[3], B.ap_L,
+            B.ap_R);
         note_launch(m);
         CUtensorMap maps[4];
         for (int q = 0; q < 4; q++) FEM3_TRY(make_map(&maps[q], B.tc_op[q], B.n_tmpl, B.tc_Kp));
@@ -366,6 +384,34 @@ int contract_tc(Mesh *m) {
         note_launch(m);
     }
     m->contract_flops = flops;
+    m->ap_ready = true;
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+int ap_alloc(Mesh *m, int axis) {
+    AxisBins &B = m->bins[axis];
+    if (B.ap_L) return FEM3_OK;
+    const int64_t e = std::max<int64_t>(1, B.tab_elems);
+    FEM3_TRY(dev_alloc(m, (void **)&B.ap_L, sizeof(float2) * e));
+    FEM3_TRY(dev_alloc(m, (void **)&B.ap_R, sizeof(float2) * e));
+    return FEM3_OK;
+}
+
+// Operator-apply operands of the current tables, without the tensor-core operands.
+int ap_prepare(Mesh *m) {
+    if (m->ap_ready) return FEM3_OK;
+    cudaStream_t s = m->stream;
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        if (B.n_tmpl == 0) continue;
+        FEM3_TRY(ap_alloc(m, axis));
+        k_split_ops<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
+            m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot, B.tab_off,
+            B.tab_ld, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_L, B.ap_R);
+        note_launch(m);
+    }
+    m->ap_ready = true;
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }

@@ -76,6 +76,8 @@ struct AxisBins {
     int32_t *row_bin = nullptr;  // [n_tmpl] template row -> bin
     int tc_Kp = 0;
     int4 *tc_work = nullptr;     // (bin, m-tile, n-tile, 0)
+    // operator-apply operands in the table layout: L and W R as hi + lo FP32 pairs
+    float2 *ap_L = nullptr, *ap_R = nullptr;
     int tc_n_work = 0;
     std::vector<int32_t> h_gp_off, h_dof_off;
     std::vector<int64_t> h_tab_off;
@@ -122,6 +124,7 @@ struct Mesh {
     float *A32 = nullptr;      // [n_dof][n_dof]
     bool factored = false;
     bool tc_ready = false;
+    bool ap_ready = false;     // ap_L / ap_R hold the current tables
 
     // workspaces
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -131,7 +134,6 @@ struct Mesh {
     void *solve_G = nullptr;   // triangular-solve chain operators: nblk x 2 x 3 x 64 x 64 doubles
     int32_t *chol_flags = nullptr;  // tile-factorisation flags, then ticket and abort words
     void *dinv = nullptr;      // inverses of the 64 x 64 diagonal blocks of the factor
-    double *ybuf = nullptr;    // [2][n_gp] weighted table-times-vector rows (operator apply)
     int flag_epoch = 0;        // value that marks "ready" in the current solve
     double *norms = nullptr;   // device scratch for reductions
     double *h_norms = nullptr; // pinned host mirror
@@ -214,5 +216,62 @@ int sym_from_lower(double *A, int64_t n, cudaStream_t s);
 int sub_vec(const double *a, const double *b, double *c, int64_t n, cudaStream_t s);
 // rel = ||b - Au|| / ||b|| (synchronises)
 int residual_norm(Mesh *m, const double *b, const double *Au, double *rel);
+
+int ap_alloc(Mesh *m, int axis);   // operator-apply operand buffers of one axis
+int ap_prepare(Mesh *m);           // split the current tables into the apply operands
+
+// ---------------------------------------------------------------------------------
+// FP64 values in FP32 arithmetic.  GB300 runs FP64 arithmetic and f64 <-> f32
+// conversions at 1/64 of the FP32 rate, so the operator apply keeps FP64 only as the
+// storage format: values are split into unevaluated sums hi + lo of two FP32 numbers by
+// integer operations and products are accumulated in that form.
+// ---------------------------------------------------------------------------------
+// hi: leading 24 bits of the significand (truncated); lo: the next 29 bits rounded to 24.
+// |x - hi - lo| <= 2^-48 |x| for 2^-74 <= |x| < 2^128; below 2^-74 lo = 0, below 2^-126
+// both are (signed) zero.
+__device__ __forceinline__ void f64_split(double x, float &hi, float &lo) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const uint32_t sign = static_cast<uint32_t>(b >> 32) & 0x80000000u;
+    const uint32_t ef = static_cast<uint32_t>(b >> 52) & 0x7FFu;
+    const float zero = __uint_as_float(sign);
+    if (ef < 897u) {
+        hi = zero;
+        lo = zero;
+        return;
+    }
+    hi = __uint_as_float(sign | ((ef - 896u) << 23) | (static_cast<uint32_t>(b >> 29) & 0x7FFFFFu));
+    const uint32_t rest = static_cast<uint32_t>(b) & 0x1FFFFFFFu;
+    if (ef < 949u || rest == 0) {
+        lo = zero;
+        return;
+    }
+    // rest = rh 2^23 + rl with both parts exact in FP32 (2^23 + m has the bits of m)
+    const float rh = __uint_as_float(0x4B000000u | (rest >> 23)) - 8388608.0f;
+    const float rl = __uint_as_float(0x4B000000u | (rest & 0x7FFFFFu)) - 8388608.0f;
+    const float mag = fmaf(rh, 8388608.0f, rl) * __uint_as_float((ef - 948u) << 23);
+    lo = __uint_as_float(__float_as_uint(mag) | sign);
+}
+
+// (sh, sl) += (ah + al)(bh + bl): ah bh exactly as p + e (FMA), the cross terms in FP32
+// (their rounding is 2^-24 of a 2^-24-sized term), al bl dropped, p added by TwoSum.
+__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float &sh, float &sl) {
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p);
+    const float x = fmaf(ah, bl, al * bh);
+    const float t = sh + p;
+    const float z = t - sh;
+    const float err = (sh - (t - z)) + (p - z);
+    sh = t;
+    sl += err + (e + x);
+}
+
+// (sh, sl) += (bh, bl)
+__device__ __forceinline__ void df_add(float bh, float bl, float &sh, float &sl) {
+    const float t = sh + bh;
+    const float z = t - sh;
+    const float err = (sh - (t - z)) + (bh - z);
+    sh = t;
+    sl += err + bl;
+}
 
 }  // namespace fem3

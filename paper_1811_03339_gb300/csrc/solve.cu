@@ -1035,168 +1035,6 @@ int trsv_t(const TF *L, int64_t n, TF *y, cudaStream_t s, Mesh *m) {
     return solve_chain_t<TF>(L, n, y, 1, s, m);
 }
 
-// ---------------------------------------------------------------------------------
-// matrix-free FP64 operator from the tables:
-//   A u = sum_i s_i K_i (L_i^T W (R_i u) + R_i^T W (L_i u))
-// pass 1: one thread per Gauss point (slot) of an axis, yL = w (L u), yR = w (R u);
-// pass 2: one warp per template row (bin, local dof), z = L yR + R yL, added into Au.
-// ---------------------------------------------------------------------------------
-template <int NR>
-__global__ void __launch_bounds__(256) k_apply_rows(
-    const double *__restrict__ tabL, const double *__restrict__ tabR,
-    const int32_t *__restrict__ slot_bin, const int32_t *__restrict__ gp_off,
-    const double *__restrict__ w_slot, const int32_t *__restrict__ dof_off,
-    const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
-    const int32_t *__restrict__ tab_ld, int64_t n_gp, const double *__restrict__ u,
-    int64_t ldu, int nv, double *yL, double *yR) {
-    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (slot >= n_gp) return;
-    const int b = slot_bin[slot];
-    const int r = (int)(slot - gp_off[b]);
-    const int d0 = dof_off[b], D = dof_off[b + 1] - d0, ld = tab_ld[b];
-    const double *Lc = tabL + tab_off[b] + r, *Rc = tabR + tab_off[b] + r;
-    double sl[NR], sr[NR];
-#pragma unroll
-    for (int v = 0; v < NR; v++) { sl[v] = 0; sr[v] = 0; }
-    for (int c = 0; c < D; c++) {
-        const int64_t o = (int64_t)c * ld;
-        const double lv = Lc[o], rv = Rc[o];
-        const int32_t dof = dof_idx[d0 + c];
-#pragma unroll
-        for (int v = 0; v < NR; v++) {
-            if (v < nv) {
-                const double uv = __ldg(u + (int64_t)v * ldu + dof);
-                sl[v] = fma(lv, uv, sl[v]);
-                sr[v] = fma(rv, uv, sr[v]);
-            }
-        }
-    }
-    const double wv = w_slot[slot];
-#pragma unroll
-    for (int v = 0; v < NR; v++)
-        if (v < nv) {
-            yL[(int64_t)v * n_gp + slot] = wv * sl[v];
-            yR[(int64_t)v * n_gp + slot] = wv * sr[v];
-        }
-}
-
-template <int NR>
-__global__ void __launch_bounds__(256) k_apply_cols(
-    const double *__restrict__ tabL, const double *__restrict__ tabR,
-    const int32_t *__restrict__ row_bin, const int32_t *__restrict__ gp_off,
-    const int32_t *__restrict__ dof_off, const int32_t *__restrict__ dof_idx,
-    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld, int64_t n_rows,
-    int64_t n_gp, const double *__restrict__ yL, const double *__restrict__ yR, double sK,
-    int nv, double *Au, int64_t ldA) {
-    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row >= n_rows) return;
-    const int b = row_bin[row];
-    const int c = (int)(row - dof_off[b]);
-    const int g0 = gp_off[b], G = gp_off[b + 1] - g0, ld = tab_ld[b];
-    const double *Lr = tabL + tab_off[b] + (int64_t)c * ld, *Rr = tabR + tab_off[b] + (int64_t)c * ld;
-    double z[NR];
-#pragma unroll
-    for (int v = 0; v < NR; v++) z[v] = 0;
-    for (int r = lane; r < G; r += 32) {
-        const double lv = Lr[r], rv = Rr[r];
-#pragma unroll
-        for (int v = 0; v < NR; v++)
-            if (v < nv)
-                z[v] = fma(lv, yR[(int64_t)v * n_gp + g0 + r], fma(rv, yL[(int64_t)v * n_gp + g0 + r], z[v]));
-    }
-    const int32_t dof = dof_idx[row];
-#pragma unroll
-    for (int v = 0; v < NR; v++) {
-        if (v < nv) {
-            double zz = z[v];
-            for (int o = 16; o > 0; o >>= 1) zz += __shfl_down_sync(0xffffffffu, zz, o);
-            if (lane == 0) atomicAdd(&Au[(int64_t)v * ldA + dof], sK * zz);
-        }
-    }
-}
-
-// Eight vectors at a time with interleaved storage: u8[dof][8], y8[slot][8], so that the
-// eight values a thread needs per table element are one contiguous 64-byte read.
-__global__ void __launch_bounds__(256) k_apply_rows8(
-    const double *__restrict__ tabL, const double *__restrict__ tabR,
-    const int32_t *__restrict__ slot_bin, const int32_t *__restrict__ gp_off,
-    const double *__restrict__ w_slot, const int32_t *__restrict__ dof_off,
-    const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
-    const int32_t *__restrict__ tab_ld, int64_t n_gp, const double *__restrict__ u8,
-    double *yL8, double *yR8) {
-    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (slot >= n_gp) return;
-    const int b = slot_bin[slot];
-    const int r = (int)(slot - gp_off[b]);
-    const int d0 = dof_off[b], D = dof_off[b + 1] - d0, ld = tab_ld[b];
-    const double *Lc = tabL + tab_off[b] + r, *Rc = tabR + tab_off[b] + r;
-    double sl[8], sr[8];
-#pragma unroll
-    for (int v = 0; v < 8; v++) { sl[v] = 0; sr[v] = 0; }
-    for (int c = 0; c < D; c++) {
-        const int64_t o = (int64_t)c * ld;
-        const double lv = Lc[o], rv = Rc[o];
-        const double2 *up = reinterpret_cast<const double2 *>(u8 + 8 * (int64_t)dof_idx[d0 + c]);
-#pragma unroll
-        for (int h = 0; h < 4; h++) {
-            const double2 uv = __ldg(up + h);
-            sl[2 * h] = fma(lv, uv.x, sl[2 * h]);
-            sl[2 * h + 1] = fma(lv, uv.y, sl[2 * h + 1]);
-            sr[2 * h] = fma(rv, uv.x, sr[2 * h]);
-            sr[2 * h + 1] = fma(rv, uv.y, sr[2 * h + 1]);
-        }
-    }
-    const double wv = w_slot[slot];
-    double2 *yl = reinterpret_cast<double2 *>(yL8 + 8 * slot);
-    double2 *yr = reinterpret_cast<double2 *>(yR8 + 8 * slot);
-#pragma unroll
-    for (int h = 0; h < 4; h++) {
-        yl[h] = make_double2(wv * sl[2 * h], wv * sl[2 * h + 1]);
-        yr[h] = make_double2(wv * sr[2 * h], wv * sr[2 * h + 1]);
-    }
-}
-
-__global__ void __launch_bounds__(256) k_apply_cols8(
-    const double *__restrict__ tabL, const double *__restrict__ tabR,
-    const int32_t *__restrict__ row_bin, const int32_t *__restrict__ gp_off,
-    const int32_t *__restrict__ dof_off, const int32_t *__restrict__ dof_idx,
-    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld, int64_t n_rows,
-    const double *__restrict__ yL8, const double *__restrict__ yR8, double sK, int nv,
-    double *Au, int64_t ldA) {
-    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row >= n_rows) return;
-    const int b = row_bin[row];
-    const int c = (int)(row - dof_off[b]);
-    const int g0 = gp_off[b], G = gp_off[b + 1] - g0, ld = tab_ld[b];
-    const double *Lr = tabL + tab_off[b] + (int64_t)c * ld, *Rr = tabR + tab_off[b] + (int64_t)c * ld;
-    double z[8];
-#pragma unroll
-    for (int v = 0; v < 8; v++) z[v] = 0;
-    for (int r = lane; r < G; r += 32) {
-        const double lv = Lr[r], rv = Rr[r];
-        const double2 *yr = reinterpret_cast<const double2 *>(yR8 + 8 * (int64_t)(g0 + r));
-        const double2 *yl = reinterpret_cast<const double2 *>(yL8 + 8 * (int64_t)(g0 + r));
-#pragma unroll
-        for (int h = 0; h < 4; h++) {
-            const double2 a = yr[h], q = yl[h];
-            z[2 * h] = fma(lv, a.x, fma(rv, q.x, z[2 * h]));
-            z[2 * h + 1] = fma(lv, a.y, fma(rv, q.y, z[2 * h + 1]));
-        }
-    }
-    // butterfly: every lane ends with all eight totals; lane v stores total v
-#pragma unroll
-    for (int v = 0; v < 8; v++)
-        for (int o = 16; o > 0; o >>= 1) z[v] += __shfl_xor_sync(0xffffffffu, z[v], o);
-    if (lane < 8 && lane < nv) {
-        double zz = z[0];
-#pragma unroll
-        for (int v = 1; v < 8; v++) if (lane == v) zz = z[v];
-        atomicAdd(&Au[(int64_t)lane * ldA + dof_idx[row]], sK * zz);
-    }
-}
-
 // per-axis forms sum_g w_g ((L lam)(R u) + (R lam)(L u)) (adjoint), one CTA per bin
 __global__ void __launch_bounds__(256) k_axis_form(
     const double *__restrict__ tabL, const double *__restrict__ tabR,
@@ -1423,57 +1261,179 @@ int factor(Mesh *m) {
     return solve_prep_t<float>(m->A32, m->n_dof, m->stream, m);
 }
 
-// Au = A u for nv vectors (column-major, leading dimension n_dof), applied in FP64 from
+// Fused operator apply, one CTA per transverse bin, in double-float arithmetic on the FP32
+// pipes.  With R~ = W R (split once per assembly, see k_split_ops), A u restricted to
+// the bin is L^T (R~ u) + R~^T (L u).  For each chunk of up to 128 Gauss points, phase 1
+// forms yR = R~ u_b and yL = L u_b (two threads per Gauss point: one vector split over the
+// template rows, or eight vectors split 4 + 4; u_b staged in shared memory as hi + lo
+// pairs), phase 2 adds s K (L^T yR + R~^T yL) to Au (warp per template row, lanes over the
+// chunk's Gauss points, then a butterfly over the lanes).  Phase 2 reads the chunk's
+// operands right after phase 1 did, so they come from cache.  Every product is exact up
+// to 2^-48 relative and sums carry their rounding errors (df_fma), so Au matches an FP64
+// evaluation to a few units in 2^-48.  NR = 1: u plain; NR = 8: u interleaved [dof][8].
+constexpr int kApplyThreads = 256;
+constexpr int kApplyGC = 128;   // Gauss points per chunk (two threads each)
+constexpr int kApplyUC = 512;   // template rows of u staged per pass
+
+template <int NR>
+constexpr size_t apply_bin_smem() {
+    return (size_t)(kApplyUC * NR + 2 * kApplyGC * NR + 2 * kApplyGC) * sizeof(float2);
+}
+
+template <int NR>
+__global__ void __launch_bounds__(kApplyThreads) k_apply_bin(
+    const float2 *__restrict__ apL, const float2 *__restrict__ apR,
+    const int32_t *__restrict__ gp_off, const int32_t *__restrict__ dof_off,
+    const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
+    const int32_t *__restrict__ tab_ld, const double *__restrict__ u, int nv, double sK,
+    double *Au, int64_t ldA) {
+    constexpr int NH = NR == 1 ? 1 : NR / 2;   // vectors per thread in phase 1
+    extern __shared__ __align__(16) float2 sm_apply[];
+    float2 *us = sm_apply;                  // [UC][NR]
+    float2 *yls = us + kApplyUC * NR;       // [GC][NR]  L u
+    float2 *yrs = yls + kApplyGC * NR;      // [GC][NR]  R~ u
+    float2 *half = yrs + kApplyGC * NR;     // [2][GC]: second half's partial sums (NR = 1)
+    const int b = blockIdx.x;
+    const int d0 = dof_off[b], D = dof_off[b + 1] - d0;
+    const int g0 = gp_off[b], G = gp_off[b + 1] - g0, ld = tab_ld[b];
+    if (D == 0 || G == 0) return;
+    const float2 *TL = apL + tab_off[b], *TR = apR + tab_off[b];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gi = tid & (kApplyGC - 1), h = tid >> 7;
+    for (int gc0 = 0; gc0 < G; gc0 += kApplyGC) {
+        const int gn = min(kApplyGC, G - gc0);
+        float lh[NH], ll[NH], rh[NH], rl[NH];
+#pragma unroll
+        for (int v = 0; v < NH; v++) { lh[v] = 0.f; ll[v] = 0.f; rh[v] = 0.f; rl[v] = 0.f; }
+        for (int cc0 = 0; cc0 < D; cc0 += kApplyUC) {
+            const int cn = min(kApplyUC, D - cc0);
+            __syncthreads();   // earlier readers of us and of the y buffers are done
+            for (int e = tid; e < cn * NR; e += kApplyThreads) {
+                const int c = e / NR, v = e - c * NR;
+                const int64_t dof = dof_idx[d0 + cc0 + c];
+                float a, a2;
+                f64_split(NR == 1 ? u[dof] : u[dof * 8 + v], a, a2);
+                us[e] = make_float2(a, a2);
+            }
+            __syncthreads();
+            if (gi < gn) {
+                const float2 *Lc = TL + (int64_t)cc0 * ld + gc0 + gi;
+                const float2 *Rc = TR + (int64_t)cc0 * ld + gc0 + gi;
+                if constexpr (NR == 1) {
+#pragma unroll 4
+                    for (int c = h; c < cn; c += 2) {
+                        const float2 lv = Lc[(int64_t)c * ld], rv = Rc[(int64_t)c * ld];
+                        const float2 uv = us[c];
+                        df_fma(lv.x, lv.y, uv.x, uv.y, lh[0], ll[0]);
+                        df_fma(rv.x, rv.y, uv.x, uv.y, rh[0], rl[0]);
+                    }
+                } else {
+#pragma unroll 2
+                    for (int c = 0; c < cn; c++) {
+                        const float2 lv = Lc[(int64_t)c * ld], rv = Rc[(int64_t)c * ld];
+#pragma unroll
+                        for (int k = 0; k < NH; k++) {
+                            const float2 uv = us[c * NR + h * NH + k];
+                            df_fma(lv.x, lv.y, uv.x, uv.y, lh[k], ll[k]);
+                            df_fma(rv.x, rv.y, uv.x, uv.y, rh[k], rl[k]);
+                        }
+                    }
+                }
+            }
+        }
+        if constexpr (NR == 1) {
+            if (h == 1 && gi < gn) {
+                half[gi] = make_float2(lh[0], ll[0]);
+                half[kApplyGC + gi] = make_float2(rh[0], rl[0]);
+            }
+            __syncthreads();
+            if (h == 0 && gi < gn) {
+                const float2 ol = half[gi], orr = half[kApplyGC + gi];
+                df_add(ol.x, ol.y, lh[0], ll[0]);
+                df_add(orr.x, orr.y, rh[0], rl[0]);
+                yls[gi] = make_float2(lh[0], ll[0]);
+                yrs[gi] = make_float2(rh[0], rl[0]);
+            }
+        } else {
+            if (gi < gn) {
+#pragma unroll
+                for (int k = 0; k < NH; k++) {
+                    yls[gi * NR + h * NH + k] = make_float2(lh[k], ll[k]);
+                    yrs[gi * NR + h * NH + k] = make_float2(rh[k], rl[k]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = warp; c < D; c += kApplyThreads / 32) {
+            const float2 *Lr = TL + (int64_t)c * ld + gc0, *Rr = TR + (int64_t)c * ld + gc0;
+            float zh[NR], zl[NR];
+#pragma unroll
+            for (int v = 0; v < NR; v++) { zh[v] = 0.f; zl[v] = 0.f; }
+            for (int r = lane; r < gn; r += 32) {
+                const float2 lv = Lr[r], rv = Rr[r];
+#pragma unroll
+                for (int v = 0; v < NR; v++) {
+                    const float2 a = yrs[r * NR + v], q = yls[r * NR + v];
+                    df_fma(lv.x, lv.y, a.x, a.y, zh[v], zl[v]);
+                    df_fma(rv.x, rv.y, q.x, q.y, zh[v], zl[v]);
+                }
+            }
+            // butterfly: every lane ends with all totals; lane v stores total v
+#pragma unroll
+            for (int v = 0; v < NR; v++)
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, zh[v], o);
+                    const float ol = __shfl_xor_sync(0xffffffffu, zl[v], o);
+                    df_add(oh, ol, zh[v], zl[v]);
+                }
+            if (lane < NR && lane < nv) {
+                float th = zh[0], tl = zl[0];
+#pragma unroll
+                for (int v = 1; v < NR; v++)
+                    if (lane == v) { th = zh[v]; tl = zl[v]; }
+                atomicAdd(&Au[(int64_t)lane * ldA + dof_idx[d0 + c]], sK * ((double)th + (double)tl));
+            }
+        }
+    }
+}
+
+// Au = A u for nv vectors (column-major, leading dimension n_dof), applied from
 // the tables; vectors go through the tables in groups of up to eight per pass.
 int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
     FEM3_CUDA(cudaMemsetAsync(Au_d, 0, sizeof(double) * n * nv, s));
-    double *yL = nullptr;
-    const int group = nv > 1 ? 8 : 1;
-    if (group > 1) {
-        FEM3_CUDA(cudaMallocAsync((void **)&yL, sizeof(double) * 2 * group * m->n_gp, s));
-    } else {
-        yL = m->ybuf;
+    static bool attr = false;
+    if (!attr) {
+        FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)apply_bin_smem<8>()));
+        attr = true;
     }
-    double *yR = yL + (int64_t)group * m->n_gp;
+    FEM3_TRY(ap_prepare(m));
     double *u8 = nullptr;
-    if (group > 1) FEM3_CUDA(cudaMallocAsync((void **)&u8, sizeof(double) * 8 * std::max<int64_t>(1, n), s));
-    for (int v0 = 0; v0 < nv; v0 += group) {
-        const int cnt = std::min(group, nv - v0);
-        if (group > 1) {
+    if (nv > 1) FEM3_CUDA(cudaMallocAsync((void **)&u8, sizeof(double) * 8 * std::max<int64_t>(1, n), s));
+    for (int v0 = 0; v0 < nv; v0 += 8) {
+        const int cnt = nv > 1 ? std::min(8, nv - v0) : 1;
+        if (nv > 1) {
             k_interleave8<<<g256(8 * n), 256, 0, s>>>(u_d + v0 * n, n, cnt, u8);
             note_launch(m);
         }
         for (int axis = 0; axis < 3; axis++) {
             AxisBins &B = m->bins[axis];
-            if (B.n_tmpl == 0) continue;
-            if (group == 1) {
-                k_apply_rows<1><<<g256(m->n_gp), 256, 0, s>>>(
-                    m->tabL[axis], m->tabR[axis], B.slot_bin, B.gp_off, B.w_slot, B.dof_off,
-                    B.dof_idx, B.tab_off, B.tab_ld, m->n_gp, u_d + v0 * n, n, cnt, yL, yR);
-                note_launch(m);
-                k_apply_cols<1><<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
-                    m->tabL[axis], m->tabR[axis], B.row_bin, B.gp_off, B.dof_off, B.dof_idx,
-                    B.tab_off, B.tab_ld, B.n_tmpl, m->n_gp, yL, yR, m->sK[axis], cnt,
-                    Au_d + v0 * n, n);
-                note_launch(m);
+            if (B.n_tmpl == 0 || B.n_bins == 0) continue;
+            if (nv == 1) {
+                k_apply_bin<1><<<B.n_bins, kApplyThreads, apply_bin_smem<1>(), s>>>(
+                    B.ap_L, B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, u_d, 1,
+                    m->sK[axis], Au_d, n);
             } else {
-                k_apply_rows8<<<g256(m->n_gp), 256, 0, s>>>(
-                    m->tabL[axis], m->tabR[axis], B.slot_bin, B.gp_off, B.w_slot, B.dof_off,
-                    B.dof_idx, B.tab_off, B.tab_ld, m->n_gp, u8, yL, yR);
-                note_launch(m);
-                k_apply_cols8<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
-                    m->tabL[axis], m->tabR[axis], B.row_bin, B.gp_off, B.dof_off, B.dof_idx,
-                    B.tab_off, B.tab_ld, B.n_tmpl, yL, yR, m->sK[axis], cnt, Au_d + v0 * n, n);
-                note_launch(m);
+                k_apply_bin<8><<<B.n_bins, kApplyThreads, apply_bin_smem<8>(), s>>>(
+                    B.ap_L, B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, u8, cnt,
+                    m->sK[axis], Au_d + v0 * n, n);
             }
+            note_launch(m);
         }
     }
-    if (group > 1) {
-        FEM3_CUDA(cudaFreeAsync(yL, s));
-        FEM3_CUDA(cudaFreeAsync(u8, s));
-    }
+    if (u8) FEM3_CUDA(cudaFreeAsync(u8, s));
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
