@@ -15,9 +15,17 @@ namespace {
 
 constexpr int kTile = 64, kKC = 16;
 
+// table entry (hi + lo pair) in the arithmetic type of the contraction
+template <class TA>
+__device__ __forceinline__ TA tab_value(const float2 *p) {
+    const float2 v = *p;
+    if constexpr (sizeof(TA) == 8) return (double)v.x + (double)v.y;
+    else return v.x + v.y;
+}
+
 template <class TA>
 __global__ void __launch_bounds__(256) k_contract_simt(
-    const double *__restrict__ tabL, const double *__restrict__ tabR,
+    const float2 *__restrict__ tabL, const float2 *__restrict__ tabR,
     const int4 *__restrict__ work, const int32_t *__restrict__ gp_off,
     const int32_t *__restrict__ gp_idx, const int32_t *__restrict__ dof_off,
     const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
@@ -30,7 +38,7 @@ __global__ void __launch_bounds__(256) k_contract_simt(
     const int D = dof_off[bin + 1] - dof_off[bin];
     const int G = gp_off[bin + 1] - gp_off[bin];
     const int ld = tab_ld[bin];
-    const double *L = tabL + tab_off[bin], *R = tabR + tab_off[bin];
+    const float2 *L = tabL + tab_off[bin], *R = tabR + tab_off[bin];
     const int32_t *slots = gp_idx + gp_off[bin];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int a0 = t1 * kTile, b0 = t2 * kTile;
@@ -52,10 +60,10 @@ __global__ void __launch_bounds__(256) k_contract_simt(
             int c = e >> 4, k = e & 15, r = r0 + k;
             bool okr = r < G;
             int ca = a0 + c, cb = b0 + c;
-            sLa[k][c] = (okr && ca < D) ? TA(L[(int64_t)ca * ld + r]) : TA(0);
-            sRa[k][c] = (okr && ca < D) ? TA(R[(int64_t)ca * ld + r]) : TA(0);
-            sLb[k][c] = (okr && cb < D) ? TA(L[(int64_t)cb * ld + r]) : TA(0);
-            sRb[k][c] = (okr && cb < D) ? TA(R[(int64_t)cb * ld + r]) : TA(0);
+            sLa[k][c] = (okr && ca < D) ? tab_value<TA>(L + (int64_t)ca * ld + r) : TA(0);
+            sRa[k][c] = (okr && ca < D) ? tab_value<TA>(R + (int64_t)ca * ld + r) : TA(0);
+            sLb[k][c] = (okr && cb < D) ? tab_value<TA>(L + (int64_t)cb * ld + r) : TA(0);
+            sRb[k][c] = (okr && cb < D) ? tab_value<TA>(R + (int64_t)cb * ld + r) : TA(0);
         }
         __syncthreads();
 #pragma unroll

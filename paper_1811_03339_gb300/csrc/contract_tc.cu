@@ -116,12 +116,12 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 // ------------------------------- split kernel ------------------------------------
 // One warp per template row (bin b, local dof c), lanes over the row's Gauss points:
-// coalesced reads of the FP64 table row.  Writes the operator-apply operands L and W R as
-// hi + lo FP32 pairs in the table layout and, when Lhi is given, the tensor-core operands
-// (the TF32 pairs of the same values, zero past the bin's Gauss points).  No FP64
-// arithmetic: the split and W R run in integer and FP32 operations.
+// coalesced reads of the table row (hi + lo pairs).  Writes the operator-apply operands L
+// and W R as hi + lo FP32 pairs in the table layout and, when Lhi is given, the
+// tensor-core operands (the TF32 pairs of the same values, zero past the bin's Gauss
+// points).  No FP64 arithmetic: W R is formed in double-float FP32 operations.
 __global__ void __launch_bounds__(256) k_split_ops(
-    const double *__restrict__ tabL, const double *__restrict__ tabR,
+    const float2 *__restrict__ tabL, const float2 *__restrict__ tabR,
     const int32_t *__restrict__ row_bin, const int32_t *__restrict__ dof_off,
     const int32_t *__restrict__ gp_off, const double *__restrict__ w_slot,
     const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(256) k_split_ops(
     for (int k = lane; k < kend; k += 32) {
         float lh = 0.f, ll = 0.f, rh = 0.f, rl = 0.f;
         if (k < G) {
-            float a, a2, r1, r2, wh, wl;
-            f64_split(tabL[src + k], a, a2);
-            f64_split(tabR[src + k], r1, r2);
+            const float2 lp = tabL[src + k], rp = tabR[src + k];
+            const float a = lp.x, a2 = lp.y, r1 = rp.x, r2 = rp.y;
+            float wh, wl;
             f64_split(w_slot[g0 + k], wh, wl);
             float sh = 0.f, sl = 0.f;
             df_fma(r1, r2, wh, wl, sh, sl);

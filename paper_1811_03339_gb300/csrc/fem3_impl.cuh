@@ -110,10 +110,11 @@ struct Mesh {
     int32_t *err = nullptr;    // [ERR_COUNT]
 
     AxisBins bins[3];
-    double *tabL[3] = {nullptr, nullptr, nullptr};
-    double *tabR[3] = {nullptr, nullptr, nullptr};
-    double *pow_cell = nullptr;   // [3][256][8] tables of the table-driven power
-    double *pow_exp = nullptr;    // [3][128]
+    // derivative tables L, R as unevaluated hi + lo FP32 pairs (value = x + y)
+    float2 *tabL[3] = {nullptr, nullptr, nullptr};
+    float2 *tabR[3] = {nullptr, nullptr, nullptr};
+    float2 *pow_cell = nullptr;   // [3][256][8] tables of the table-driven power (hi + lo pairs)
+    float2 *pow_exp = nullptr;    // [3][128]
 
     // assembled operator
     int precision = -1;        // of the last assemble, -1: none
@@ -272,6 +273,30 @@ __device__ __forceinline__ void df_add(float bh, float bl, float &sh, float &sl)
     const float err = (sh - (t - z)) + (bh - z);
     sh = t;
     sl += err + bl;
+}
+
+// (rh, rl) = (ah + al)(bh + bl), normalised (|rl| <= ulp(rh) / 2)
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &rh, float &rl) {
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p);
+    const float x = fmaf(ah, bl, al * bh) + e;
+    rh = p + x;
+    rl = x - (rh - p);
+}
+
+// (rh, rl) = (ah + al) + (bh + bl), normalised
+__device__ __forceinline__ void df_add2(float ah, float al, float bh, float bl, float &rh, float &rl) {
+    const float t = ah + bh;
+    const float z = t - ah;
+    const float x = ((ah - (t - z)) + (bh - z)) + (al + bl);
+    rh = t + x;
+    rl = x - (rh - t);
+}
+
+// exact FP32 value of an integer |v| <= 2^22 without a conversion instruction:
+// 1.5 * 2^23 + v has the bits of the magic constant plus v
+__device__ __forceinline__ float small_int_f32(int v) {
+    return __int_as_float(0x4B400000 + v) - 12582912.0f;
 }
 
 }  // namespace fem3

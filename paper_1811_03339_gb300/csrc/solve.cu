@@ -1037,7 +1037,7 @@ int trsv_t(const TF *L, int64_t n, TF *y, cudaStream_t s, Mesh *m) {
 
 // per-axis forms sum_g w_g ((L lam)(R u) + (R lam)(L u)) (adjoint), one CTA per bin
 __global__ void __launch_bounds__(256) k_axis_form(
-    const double *__restrict__ tabL, const double *__restrict__ tabR,
+    const float2 *__restrict__ tabL, const float2 *__restrict__ tabR,
     const int32_t *__restrict__ gp_off, const int32_t *__restrict__ gp_idx,
     const int32_t *__restrict__ dof_off, const int32_t *__restrict__ dof_idx,
     const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
@@ -1049,7 +1049,7 @@ __global__ void __launch_bounds__(256) k_axis_form(
     const int G = gp_off[bin + 1] - gp_off[bin];
     if (D == 0 || G == 0) return;
     const int ld = tab_ld[bin];
-    const double *L = tabL + tab_off[bin], *R = tabR + tab_off[bin];
+    const float2 *L = tabL + tab_off[bin], *R = tabR + tab_off[bin];
     const int32_t *dofs = dof_idx + dof_off[bin];
     const int32_t *slots = gp_idx + gp_off[bin];
     double *ub = sm, *lb = sm + D;
@@ -1060,7 +1060,8 @@ __global__ void __launch_bounds__(256) k_axis_form(
     for (int r = threadIdx.x; r < G; r += blockDim.x) {
         double Lu = 0, Ru = 0, Ll = 0, Rl = 0;
         for (int c = 0; c < D; c++) {
-            double lv = L[(int64_t)c * ld + r], rv = R[(int64_t)c * ld + r];
+            const float2 lp = L[(int64_t)c * ld + r], rp = R[(int64_t)c * ld + r];
+            const double lv = (double)lp.x + (double)lp.y, rv = (double)rp.x + (double)rp.y;
             Lu = fma(lv, ub[c], Lu); Ru = fma(rv, ub[c], Ru);
             Ll = fma(lv, lb[c], Ll); Rl = fma(rv, lb[c], Rl);
         }

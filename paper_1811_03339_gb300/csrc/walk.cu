@@ -142,48 +142,71 @@ struct TableArgs {
     const int32_t *__restrict__ dof_idx;
     const int64_t *__restrict__ tab_off;
     const int32_t *__restrict__ tab_ld;
-    double *tab;                          // L (side 0) or R (side 1) of this axis
+    float2 *tab;                          // L (side 0) or R (side 1) of this axis, hi + lo pairs
     double p_exp;                         // 1 - gamma
-    double coef;                          // +1/Gamma(2-gamma) (left) or -1/Gamma(2-gamma)
-    const double *__restrict__ pow_cell;  // [256][8] local Taylor coefficients of m^p, m_c
-    const double *__restrict__ pow_exp;   // [128] 2^(e p) for e = -64 .. 63
+    float coef_h, coef_l;                 // +1/Gamma(2-gamma) (left) or -1/Gamma(2-gamma), hi + lo
+    const float2 *__restrict__ pow_cell;  // [256][8] local Taylor coefficients of m^p (hi + lo)
+    const float2 *__restrict__ pow_exp;   // [128] 2^(e p) for e = -64 .. 63 (hi + lo)
 };
 
 // r^p for r > 0 by table-driven range reduction (after Tang's table-driven elementary
 // functions): r = 2^e m with m in [1, 2); the top 8 fraction bits pick a cell of width
 // 1/256 with centre m_c; m^p = sum_k C(p,k) m_c^(p-k) (m - m_c)^k, k <= 4, whose
 // truncation error is below 1e-15 relative for p in [0, 1); 2^(e p) from a table.
-// Six FP64 operations; exponents outside [-64, 63] fall back to pow.
-__device__ __forceinline__ double pow_table(double r, double p, const double *__restrict__ cell,
-                                            const double *__restrict__ pexp) {
+// Evaluated in double-float FP32 arithmetic (hi + lo pairs, about 1e-14 relative): the
+// range reduction is integer work and m - m_c is exact from the fraction bits, so the only
+// FP64 operation is the rare fallback for exponents outside [-64, 63].
+__device__ __forceinline__ void pow_df(double r, double p, const float2 *__restrict__ cell,
+                                       const float2 *__restrict__ pexp, float &ph, float &pl) {
     const long long bits = __double_as_longlong(r);
     const int e = (int)((bits >> 52) & 0x7ff) - 1023;
-    if (e < -64 || e > 63) return pow(r, p);
+    if (e < -64 || e > 63) {
+        f64_split(pow(r, p), ph, pl);
+        return;
+    }
     const int j = (int)((bits >> 44) & 0xff);
-    const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
-    const double *c = cell + 8 * j;
-    const double d = m - __ldg(c + 5);
-    const double q = fma(fma(fma(fma(__ldg(c + 4), d, __ldg(c + 3)), d, __ldg(c + 2)), d,
-                             __ldg(c + 1)), d, __ldg(c));
-    return __ldg(pexp + e + 64) * q;
+    // m - m_c in units of 2^-52: the low 44 fraction bits minus the cell centre's 2^43
+    const long long D = (bits & 0xFFFFFFFFFFFLL) - (1LL << 43);
+    const float dh = small_int_f32((int)(D >> 21)) * 4.656612873077393e-10f;         // 2^-31
+    const float dl = small_int_f32((int)(D & 0x1FFFFF)) * 2.220446049250313e-16f;    // 2^-52
+    const float2 *c = cell + 8 * j;
+    float2 ck = __ldg(c + 4);
+    float qh = ck.x, ql = ck.y;
+#pragma unroll
+    for (int k = 3; k >= 0; k--) {
+        df_mul(qh, ql, dh, dl, qh, ql);
+        ck = __ldg(c + k);
+        df_add2(qh, ql, ck.x, ck.y, qh, ql);
+    }
+    const float2 s = __ldg(pexp + e + 64);
+    df_mul(qh, ql, s.x, s.y, ph, pl);
 }
 
-// coefficients of pow_table for p = 1 - gamma_axis: cell j of axis a at
-// cell[a][j][0..4] (Taylor terms), cell[a][j][5] = m_c; pexp[a][e + 64] = 2^(e p)
-__global__ void k_pow_tables(double p0, double p1, double p2, double *cell, double *pexp) {
-    const int a = blockIdx.x, j = threadIdx.x;   // 3 blocks x 256 threads
-    const double p = a == 0 ? p0 : (a == 1 ? p1 : p2);
+// cell j of the power for exponent p: Taylor terms C(p,k) m_c^(p-k) (k <= 4) and, for
+// j < 128, 2^((j - 64) p); FP64 values stored as hi + lo pairs
+__device__ __forceinline__ void fill_pow_cell(double p, int j, float2 *cell, float2 *pexp) {
     const double mc = 1.0 + (2.0 * j + 1.0) / 512.0;
     double binom = 1.0;
-    double *c = cell + (size_t)a * 256 * 8 + 8 * j;
+    float2 *c = cell + 8 * j;
+    for (int k = 0; k < 8; k++) c[k] = make_float2(0.f, 0.f);
     for (int k = 0; k <= 4; k++) {
-        c[k] = binom * pow(mc, p - k);
+        float h, l;
+        f64_split(binom * pow(mc, p - k), h, l);
+        c[k] = make_float2(h, l);
         binom = binom * (p - k) / (k + 1);
     }
-    c[5] = mc;
-    c[6] = 0.0;
-    c[7] = 0.0;
-    if (j < 128) pexp[a * 128 + j] = exp2((double)(j - 64) * p);
+    if (j < 128) {
+        float h, l;
+        f64_split(exp2((double)(j - 64) * p), h, l);
+        pexp[j] = make_float2(h, l);
+    }
+}
+
+// tables of the power for p = 1 - gamma_axis: cell[a][j][0..4], pexp[a][e + 64]
+__global__ void k_pow_tables(double p0, double p1, double p2, float2 *cell, float2 *pexp) {
+    const int a = blockIdx.x, j = threadIdx.x;   // 3 blocks x 256 threads
+    const double p = a == 0 ? p0 : (a == 1 ? p1 : p2);
+    fill_pow_cell(p, j, cell + (size_t)a * 256 * 8, pexp + a * 128);
 }
 
 // One line (Gauss point in slot `slot` of an axis): both directions in one loop.  When
@@ -206,10 +229,11 @@ __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
                  x2 = W.gp[3 * (int64_t)g + 2];
     const double p_exp = A0.p_exp;   // same order on both sides of the line
     int side = 0, dir = -1;
-    double *tab = A0.tab + toff;
-    double coef = A0.coef;
+    float2 *tab = A0.tab + toff;
+    float coef_h = A0.coef_h, coef_l = A0.coef_l;
     int32_t t = g >> 2;
-    double r_prev = 0.0, P_prev = 0.0;
+    double r_prev = 0.0;
+    float pp_h = 0.f, pp_l = 0.f;   // r_prev^p
     int32_t cj[4] = {-1, -1, -1, -1}, cc[4] = {-1, -1, -1, -1};
     int steps = 0;
     for (int it = 0; it < 2 * W.max_steps; it++) {
@@ -218,8 +242,11 @@ __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
         int32_t nx = -2;
         if (rmax < INFINITY) {
             if (rmax - r_prev > W.eps_r) {
-                const double P = pow_table(rmax, p_exp, A0.pow_cell, A0.pow_exp);
-                const double c = coef * (P - P_prev);
+                // table part in double-float FP32: c = coef (rmax^p - r_prev^p)
+                float ph, pl, ch, cl;
+                pow_df(rmax, p_exp, A0.pow_cell, A0.pow_exp, ph, pl);
+                df_add2(ph, pl, -pp_h, -pp_l, ch, cl);
+                df_mul(ch, cl, coef_h, coef_l, ch, cl);
                 const double *Mt = W.M + 16 * (int64_t)t;
                 int32_t nj[4], nc[4];
 #pragma unroll
@@ -231,17 +258,24 @@ __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
                         for (int q = 0; q < 4; q++)
                             if (cj[q] == j) col = cc[q];
                         if (col < 0) col = bsearch_dof(dofs, nd, j);
-                        if (col >= 0)
-                            tab[(int64_t)col * ld] += c * Mt[4 * v + 1 + axis];
-                        else
+                        if (col >= 0) {
+                            float gh, gl;
+                            f64_split(Mt[4 * v + 1 + axis], gh, gl);
+                            float2 *te = tab + (int64_t)col * ld;
+                            float2 tv = *te;
+                            df_fma(ch, cl, gh, gl, tv.x, tv.y);
+                            *te = tv;
+                        } else {
                             miss++;
+                        }
                     }
                     nj[v] = j;
                     nc[v] = col;
                 }
 #pragma unroll
                 for (int v = 0; v < 4; v++) { cj[v] = nj[v]; cc[v] = nc[v]; }
-                P_prev = P;
+                pp_h = ph;
+                pp_l = pl;
                 r_prev = rmax;
                 nseg++;
             }
@@ -258,10 +292,12 @@ __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
         side = 1;
         dir = 1;
         tab = A1.tab + toff;
-        coef = A1.coef;
+        coef_h = A1.coef_h;
+        coef_l = A1.coef_l;
         t = g >> 2;
         r_prev = 0.0;
-        P_prev = 0.0;
+        pp_h = 0.f;
+        pp_l = 0.f;
         steps = 0;
 #pragma unroll
         for (int v = 0; v < 4; v++) { cj[v] = -1; cc[v] = -1; }
@@ -327,19 +363,8 @@ __global__ void __launch_bounds__(128) k_walk_batch(const WalkDesc *__restrict__
 // tables of the table-driven power for each descriptor (block d, 256 threads)
 __global__ void k_pow_tables_batch(const WalkDesc *__restrict__ descs) {
     const WalkDesc &D = descs[blockIdx.x];
-    const int j = threadIdx.x;
-    const double p = D.A0.p_exp;
-    const double mc = 1.0 + (2.0 * j + 1.0) / 512.0;
-    double *c = const_cast<double *>(D.A0.pow_cell) + 8 * j;
-    double binom = 1.0;
-    for (int k = 0; k <= 4; k++) {
-        c[k] = binom * pow(mc, p - k);
-        binom = binom * (p - k) / (k + 1);
-    }
-    c[5] = mc;
-    c[6] = 0.0;
-    c[7] = 0.0;
-    if (j < 128) const_cast<double *>(D.A0.pow_exp)[j] = exp2((double)(j - 64) * p);
+    fill_pow_cell(D.A0.p_exp, threadIdx.x, const_cast<float2 *>(D.A0.pow_cell),
+                  const_cast<float2 *>(D.A0.pow_exp));
 }
 
 // zero n_buf device buffers given as (pointer, element count) pairs
@@ -391,7 +416,7 @@ __global__ void k_walk_paths(WalkGeom W, int axis, int dir, const int64_t *__res
 }
 
 // Gather rows of a binned table into dense rows [n][n_dof] (zero elsewhere).
-__global__ void k_table_rows(const double *__restrict__ tab, const int32_t *__restrict__ gbin_slot,
+__global__ void k_table_rows(const float2 *__restrict__ tab, const int32_t *__restrict__ gbin_slot,
                              const int64_t *__restrict__ gps, int64_t n,
                              const int32_t *__restrict__ slot_of_gp,
                              const int32_t *__restrict__ gp_off, const int32_t *__restrict__ dof_off,
@@ -406,8 +431,10 @@ __global__ void k_table_rows(const double *__restrict__ tab, const int32_t *__re
     int32_t bin = gbin_slot[slot];
     int32_t row = slot - gp_off[bin];
     int d0 = dof_off[bin], nd = dof_off[bin + 1] - d0;
-    for (int c = threadIdx.x; c < nd; c += blockDim.x)
-        rows[l * n_dof + dof_idx[d0 + c]] = tab[tab_off[bin] + (int64_t)c * tab_ld[bin] + row];
+    for (int c = threadIdx.x; c < nd; c += blockDim.x) {
+        const float2 v = tab[tab_off[bin] + (int64_t)c * tab_ld[bin] + row];
+        rows[l * n_dof + dof_idx[d0 + c]] = (double)v.x + (double)v.y;
+    }
 }
 
 WalkGeom make_geom(Mesh *m) {
@@ -435,20 +462,22 @@ int walk_tables(Mesh *m, const double alpha[3]) {
     note_launch(m);
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
-        FEM3_CUDA(cudaMemsetAsync(m->tabL[axis], 0, sizeof(double) * B.tab_elems, s));
-        FEM3_CUDA(cudaMemsetAsync(m->tabR[axis], 0, sizeof(double) * B.tab_elems, s));
+        FEM3_CUDA(cudaMemsetAsync(m->tabL[axis], 0, sizeof(float2) * B.tab_elems, s));
+        FEM3_CUDA(cudaMemsetAsync(m->tabR[axis], 0, sizeof(float2) * B.tab_elems, s));
     }
     stage_begin(m, 2);
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
         double gamma = alpha[axis] / 2.0;
         double ig = 1.0 / tgamma(2.0 - gamma);
+        const float igh = (float)ig, igl = (float)(ig - (double)igh);
         TableArgs A0{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
-                     B.tab_ld, m->tabL[axis], 1.0 - gamma, ig,
+                     B.tab_ld, m->tabL[axis], 1.0 - gamma, igh, igl,
                      m->pow_cell + (size_t)axis * 256 * 8, m->pow_exp + axis * 128};
         TableArgs A1 = A0;
         A1.tab = m->tabR[axis];
-        A1.coef = -ig;
+        A1.coef_h = -igh;
+        A1.coef_l = -igl;
         k_walk_tables<<<(unsigned)((m->n_gp + 127) / 128), 128, 0, s>>>(W, A0, A1, axis, m->n_gp,
                                                                           m->err, segc);
         note_launch(m);
@@ -473,7 +502,7 @@ int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double
     AxisBins &B = m->bins[axis];
     const int32_t *slot_of_gp = B.slot_of_gp;
     FEM3_CUDA(cudaMemsetAsync(rows, 0, sizeof(double) * n * m->n_dof, s));
-    const double *tab = dir < 0 ? m->tabL[axis] : m->tabR[axis];
+    const float2 *tab = dir < 0 ? m->tabL[axis] : m->tabR[axis];
     if (n > 0) {
         k_table_rows<<<(unsigned)n, 128, 0, s>>>(tab, B.slot_bin, gps, n, slot_of_gp, B.gp_off,
                                                   B.dof_off, B.dof_idx, B.tab_off, B.tab_ld,
@@ -513,23 +542,25 @@ int walk_tables_batch(Mesh *const *ms, int n, const double *alpha, cudaStream_t 
             AxisBins &B = m->bins[axis];
             const double gamma = alpha[3 * i + axis] / 2.0;
             const double ig = 1.0 / tgamma(2.0 - gamma);
+            const float igh = (float)ig, igl = (float)(ig - (double)igh);
             WalkDesc &D = hd[3 * i + axis];
             D.W = W;
             D.A0 = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
-                             B.tab_ld, m->tabL[axis], 1.0 - gamma, ig,
+                             B.tab_ld, m->tabL[axis], 1.0 - gamma, igh, igl,
                              m->pow_cell + (size_t)axis * 256 * 8, m->pow_exp + axis * 128};
             D.A1 = D.A0;
             D.A1.tab = m->tabR[axis];
-            D.A1.coef = -ig;
+            D.A1.coef_h = -igh;
+            D.A1.coef_l = -igl;
             D.axis = axis;
             D.slot0 = items;
             D.n_gp = m->n_gp;
             D.err = m->err;
             D.seg = reinterpret_cast<unsigned long long *>(m->norms + kSegCounterSlot);
             items += m->n_gp;
-            zp[2 * (3 * i + axis)] = m->tabL[axis];
+            zp[2 * (3 * i + axis)] = reinterpret_cast<double *>(m->tabL[axis]);
             zl[2 * (3 * i + axis)] = B.tab_elems;
-            zp[2 * (3 * i + axis) + 1] = m->tabR[axis];
+            zp[2 * (3 * i + axis) + 1] = reinterpret_cast<double *>(m->tabR[axis]);
             zl[2 * (3 * i + axis) + 1] = B.tab_elems;
             max_tab = std::max<int64_t>(max_tab, B.tab_elems);
         }
