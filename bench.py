@@ -45,8 +45,8 @@ def _peaks():
 # DRAM bytes (read + write) of one k_walk_tables launch from the ncu capture summarised in
 # profiles/k_walk_tables_cube16_jitter.md, valid only for the kernel source it was taken
 # on (sha256 of csrc/walk.cu); otherwise the traffic is reported as unknown.
-WALK_TRAFFIC = {"walk_cu_sha256": "33917058bdbc94d83a117185f385933d6342e6bdde1612aa71b9f5f8d0ad408b",
-                "bytes_per_launch": 72459008 + 10040576, "segments_per_launch": 5366660}
+WALK_TRAFFIC = {"walk_cu_sha256": "ddd5359012ad9668a52ce237a89efbe597d289c5957557e6f4484ee46e526ff8",
+                "bytes_per_launch": 201950720 + 107748096, "segments_per_launch": 16099980}
 
 
 def _walk_traffic(segs_per_launch):
@@ -266,14 +266,14 @@ def run_ours(args):
     m64.free()
     rel_mix_fp64 = float(torch.linalg.norm(u_mix - u64) / torch.linalg.norm(u64))
 
-    # walk+tables kernel: 3 launches per step (one per axis), timed live by the library's
-    # events on the launch stream.  Algorithmic FP64 flops per walked segment:
+    # walk+tables kernel: one launch per step covering the three axes, timed live by the
+    # library's events on the launch stream.  Algorithmic FP64 flops per walked segment
+    # (the quantities that decide the path; the table part runs in double-float FP32):
     # 24 (b~ = lambda_T(x_g), 12 FMA) + 2 (go-out ratios of ~2 exit candidates)
-    # + 8 (exit zero pattern, 4 FMA) + 1 (length test) + 10 (power r^(1-gamma):
-    # 1 sub, 4 FMA, 1 mul) + 2 (coefficient) + 8 (table update, 4 FMA) = 55.
-    walk_ms = stages[2] / 3.0
-    segs_per_launch = cnt["segments"] / 3.0
-    fp64_flops_per_seg = 55.0
+    # + 8 (exit zero pattern, 4 FMA) + 1 (length test) = 35.
+    walk_ms = stages[2]
+    segs_per_launch = cnt["segments"]
+    fp64_flops_per_seg = 35.0
     walk_flops = fp64_flops_per_seg * segs_per_launch
     fp64_peak_gflops = 1250.0
     traffic = _walk_traffic(segs_per_launch)
@@ -289,7 +289,7 @@ def run_ours(args):
         "traffic": traffic,
         "launch_ms": walk_ms,
         "algorithmic_unit": f"{fp64_flops_per_seg:.0f} FP64 flops per walked segment, "
-                            f"{segs_per_launch:.0f} segments per launch (one axis)",
+                            f"{segs_per_launch:.0f} segments per launch (three axes)",
     }
 
     # --- end to end through the C ABI with host buffers -----------------------------

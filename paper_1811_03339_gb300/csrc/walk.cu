@@ -311,13 +311,20 @@ __device__ __forceinline__ void count_segments(int nseg, unsigned long long *seg
     if ((threadIdx.x & 31) == 0 && ns) atomicAdd(seg_count, ns);
 }
 
-// grid: x over slots of one axis; one launch per axis
-__global__ void __launch_bounds__(128) k_walk_tables(WalkGeom W, TableArgs A0, TableArgs A1,
-                                                     int axis, int64_t n_gp, int32_t *err,
-                                                     unsigned long long *seg_count) {
+// the three axes' table arguments (kernel parameters)
+struct AxisTables {
+    TableArgs A0[3], A1[3];
+};
+
+// grid: x over the slots of an axis, y = axis; the three axes in one launch keep every SM
+// filled (one axis alone is about five CTAs per SM)
+__global__ void __launch_bounds__(128, 7) k_walk_tables(WalkGeom W, AxisTables T, int64_t n_gp,
+                                                        int32_t *err,
+                                                        unsigned long long *seg_count) {
+    const int axis = blockIdx.y;
     const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int nseg = 0, miss = 0, bad = 0;
-    if (slot < n_gp) nseg = walk_line(W, A0, A1, axis, slot, miss, bad);
+    if (slot < n_gp) nseg = walk_line(W, T.A0[axis], T.A1[axis], axis, slot, miss, bad);
     if (bad) atomicAdd(&err[ERR_WALK], bad);
     if (miss) atomicAdd(&err[ERR_TEMPLATE], miss);
     count_segments(nseg, seg_count);   // every lane takes part
@@ -337,7 +344,7 @@ struct WalkDesc {
     unsigned long long *seg;
 };
 
-__global__ void __launch_bounds__(128) k_walk_batch(const WalkDesc *__restrict__ descs, int n_desc,
+__global__ void __launch_bounds__(128, 7) k_walk_batch(const WalkDesc *__restrict__ descs, int n_desc,
                                                     int64_t n_items) {
     const int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int nseg = 0, miss = 0, bad = 0, d = 0;
@@ -466,22 +473,23 @@ int walk_tables(Mesh *m, const double alpha[3]) {
         FEM3_CUDA(cudaMemsetAsync(m->tabR[axis], 0, sizeof(float2) * B.tab_elems, s));
     }
     stage_begin(m, 2);
+    AxisTables T;
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
         double gamma = alpha[axis] / 2.0;
         double ig = 1.0 / tgamma(2.0 - gamma);
         const float igh = (float)ig, igl = (float)(ig - (double)igh);
-        TableArgs A0{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
-                     B.tab_ld, m->tabL[axis], 1.0 - gamma, igh, igl,
-                     m->pow_cell + (size_t)axis * 256 * 8, m->pow_exp + axis * 128};
-        TableArgs A1 = A0;
-        A1.tab = m->tabR[axis];
-        A1.coef_h = -igh;
-        A1.coef_l = -igl;
-        k_walk_tables<<<(unsigned)((m->n_gp + 127) / 128), 128, 0, s>>>(W, A0, A1, axis, m->n_gp,
-                                                                          m->err, segc);
-        note_launch(m);
+        T.A0[axis] = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
+                               B.tab_ld, m->tabL[axis], 1.0 - gamma, igh, igl,
+                               m->pow_cell + (size_t)axis * 256 * 8, m->pow_exp + axis * 128};
+        T.A1[axis] = T.A0[axis];
+        T.A1[axis].tab = m->tabR[axis];
+        T.A1[axis].coef_h = -igh;
+        T.A1[axis].coef_l = -igl;
     }
+    k_walk_tables<<<dim3((unsigned)((m->n_gp + 127) / 128), 3), 128, 0, s>>>(W, T, m->n_gp, m->err,
+                                                                            segc);
+    note_launch(m);
     stage_end(m, 2);
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
