@@ -72,18 +72,6 @@ __device__ __forceinline__ void st_release_gpu(int *p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Diagonal block: factor A_kk = L_kk L_kk^T and form L_kk^{-1} (512 threads), blocked
-// by 16.  For each 16-column panel p (P = 16 p):
-//   S1  warp 0 factors the 16 x 16 diagonal block L_pp in registers (row per lane; the
-//       pivot column goes through a double-buffered shared vector) and inverts it by
-//       forward substitution (column of L_pp^{-1} per lane); meanwhile the other warps
-//       form T_pJ = sum_K L_pK (L^{-1})_KJ for the blocks J < p of the inverse's block
-//       row p.
-//   S2  panel L_ip = A_ip L_pp^{-T} (rows below) and (L^{-1})_pJ = -L_pp^{-1} T_pJ.
-//   S3  trailing update A_ij -= L_ip L_jp^T (lower part, rows/columns past the panel).
-// a_s holds the block (rows and columns >= nb padded with the identity) and receives L;
-// x_s receives L^{-1}.  L goes to A (rows/columns k0 .. k0 + nb), L^{-1} to Linv
-// (row-major 64 x 64); a non-positive pivot records 1 + its global column.
 template <class TF> __device__ __forceinline__ TF rsqrt_t(TF x);
 // FP32: hardware estimate plus one Newton step y <- y + y (1 - x y^2) / 2, so that the
 // factor is as accurate as one built from a correctly rounded square root (refinement
@@ -119,168 +107,215 @@ __device__ __forceinline__ void lds2(const TF *p, TF v[2]) {
 
 constexpr int PB = 16;   // panel width inside the diagonal block
 
+// named barriers of the diagonal factor (0 is __syncthreads)
+constexpr int kBarPanelReady = 1;   // warp 0 -> update warps: block p factored and inverted
+constexpr int kBarNextReady = 2;    // update warps -> warp 0: block p + 1 fully updated
+constexpr int kBarUpdate = 3;       // among the 15 update warps
+__device__ __forceinline__ void bar_sync_n(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_n(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// warp 0: 16 x 16 Cholesky of block p of a_s (row per lane, pivot column through a
+// double-buffered shared vector) and the inverse by forward substitution (column per
+// lane); writes L_pp into a_s, L_pp^{-1} into x_s and lt[k][c] = L_pp^{-1}[c][k]
+template <class TF>
+__device__ __forceinline__ void chol_inv16(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], TF (*lt)[PB + 4],
+                                           TF (*colb16)[PB], TF (*lcol)[PB + 4], int P, int nb,
+                                           int64_t k0, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    const int r = lane & (PB - 1);
+    TF v[PB], rdv[PB];
+#pragma unroll
+    for (int c = 0; c < PB; c++) v[c] = c <= r ? a_s[P + r][P + c] : TF(0);
+    int bad = -1;
+#pragma unroll
+    for (int j = 0; j < PB; j++) {
+        TF *cb = colb16[j & 1];
+        if (lane < PB && r >= j) cb[r] = v[j];
+        __syncwarp();
+        TF col[PB];
+#pragma unroll
+        for (int k = 0; k < PB; k += 4) lds4<TF>(cb + k, col + k);
+        const TF d = col[j];
+        if (!(d > TF(0)) && bad < 0) bad = j;
+        const TF rs = d > TF(0) ? rsqrt_t<TF>(d) : TF(1);
+        rdv[j] = rs;
+        const TF f = v[j] * rs * rs;   // a[r][j] / d
+#pragma unroll
+        for (int k = 1; k < PB; k++)
+            if (k > j && r >= k) v[k] -= f * col[k];
+        v[j] = r == j ? d * rs : v[j] * rs;
+    }
+    if (bad >= 0 && lane == 0 && P + bad < nb)
+        atomicCAS(&err[ERR_NOT_SPD], 0, (int32_t)(k0 + P + bad + 1));
+    if (lane < PB) {
+#pragma unroll
+        for (int c = 0; c < PB; c++) {
+            if (c <= r) a_s[P + r][P + c] = v[c];
+            lcol[c][r] = v[c];   // zero above the diagonal
+        }
+    }
+    __syncwarp();
+    // column cc of L_pp^{-1}: t_k = (delta_kc - sum_{i<k} L_ki t_i) / L_kk
+    const int cc = lane & (PB - 1);
+    TF t[PB];
+#pragma unroll
+    for (int i = 0; i < PB; i++) t[i] = i == cc ? TF(1) : TF(0);
+#pragma unroll
+    for (int k = 0; k < PB; k++) {
+        t[k] *= rdv[k];
+        TF lc[PB];
+#pragma unroll
+        for (int i = 0; i < PB; i += 4) lds4<TF>(&lcol[k][i], lc + i);
+#pragma unroll
+        for (int i = 1; i < PB; i++)
+            if (i > k) t[i] -= lc[i] * t[k];
+    }
+    if (lane < PB) {
+#pragma unroll
+        for (int i = 0; i < PB; i++) {
+            x_s[P + i][P + cc] = i >= cc ? t[i] : TF(0);
+            lt[cc][i] = t[i];
+        }
+    }
+}
+
+// Diagonal block: factor A_kk = L_kk L_kk^T and form L_kk^{-1} (512 threads), blocked by
+// 16 with look-ahead.  Warp 0 factors and inverts the 16 x 16 diagonal block p; the other
+// 15 warps then (a) solve the 16 rows of block p + 1 in panel p (L_{p+1,p} = A L_pp^{-T})
+// and update diagonal block p + 1, which releases warp 0 for block p + 1 at once, and
+// (b) meanwhile solve the rest of panel p, form the inverse's block row p
+// ((L^{-1})_pJ = -L_pp^{-1} sum_K L_pK (L^{-1})_KJ) and apply the rest of the trailing update.
+// a_s holds the block (rows and columns >= nb padded with the identity) and receives L;
+// x_s receives L^{-1} (zero above the diagonal on return).  L goes to A (rows/columns
+// k0 .. k0 + nb), L^{-1} to Linv (row-major 64 x 64); a non-positive pivot records 1 +
+// its global column.  Needs exactly 512 threads, all of the CTA.
 template <class TF>
 __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, TF *A, int64_t n,
                                int64_t k0, TF *Linv, int32_t *err) {
-    __shared__ __align__(16) TF lt[PB][PB + 4];        // lt[k][c] = (L_pp^{-1})[c][k]
+    constexpr int NT = 512, NU = NT - 32, NP = NB / PB;
+    __shared__ __align__(16) TF lt[2][PB][PB + 4];     // lt[p & 1][k][c] = L_pp^{-1}[c][k]
     __shared__ __align__(16) TF pant[PB][NB + 4];      // pant[k][r] = L[r][P + k], r >= P + 16
     __shared__ __align__(16) TF tq[PB][NB - PB + 4];   // T_pJ, columns c < P
     __shared__ __align__(16) TF colb16[2][PB];         // pivot column (16 x 16 factor)
     __shared__ __align__(16) TF lcol[PB][PB + 4];      // lcol[k][i] = L_pp[i][k]
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int p = 0; p < NB / PB; p++) {
-        const int P = p * PB;
-        // ---------------- S1 ----------------
-        if (warp == 0) {
-            const int r = lane & (PB - 1);
-            TF v[PB], rdv[PB];
-#pragma unroll
-            for (int c = 0; c < PB; c++) v[c] = c <= r ? a_s[P + r][P + c] : TF(0);
-            int bad = -1;
-#pragma unroll
-            for (int j = 0; j < PB; j++) {
-                // column j (unscaled) through a double-buffered shared vector
-                TF *cb = colb16[j & 1];
-                if (lane < PB && r >= j) cb[r] = v[j];
-                __syncwarp();
-                TF col[PB];
-#pragma unroll
-                for (int k = 0; k < PB; k += 4) lds4<TF>(cb + k, col + k);
-                const TF d = col[j];
-                if (!(d > TF(0)) && bad < 0) bad = j;
-                const TF rs = d > TF(0) ? rsqrt_t<TF>(d) : TF(1);
-                rdv[j] = rs;
-                const TF f = v[j] * rs * rs;   // a[r][j] / d
-#pragma unroll
-                for (int k = 1; k < PB; k++)
-                    if (k > j && r >= k) v[k] -= f * col[k];
-                v[j] = r == j ? d * rs : v[j] * rs;
-            }
-            if (bad >= 0 && lane == 0 && P + bad < nb)
-                atomicCAS(&err[ERR_NOT_SPD], 0, (int32_t)(k0 + P + bad + 1));
-            if (lane < PB) {
-#pragma unroll
-                for (int c = 0; c < PB; c++) {
-                    if (c <= r) a_s[P + r][P + c] = v[c];
-                    lcol[c][r] = v[c];   // zero above the diagonal
-                }
-            }
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        for (int p = 0; p < NP; p++) {
+            if (p > 0) bar_sync_n(kBarNextReady, NT);
+            chol_inv16<TF>(a_s, x_s, lt[p & 1], colb16, lcol, p * PB, nb, k0, err);
             __syncwarp();
-            // column cc of L_pp^{-1}: t_k = (delta_kc - sum_{i<k} L_ki t_i) / L_kk
-            const int cc = lane & (PB - 1);
-            TF t[PB];
-#pragma unroll
-            for (int i = 0; i < PB; i++) t[i] = i == cc ? TF(1) : TF(0);
-#pragma unroll
-            for (int k = 0; k < PB; k++) {
-                t[k] *= rdv[k];
-                TF lc[PB];
-#pragma unroll
-                for (int i = 0; i < PB; i += 4) lds4<TF>(&lcol[k][i], lc + i);
-#pragma unroll
-                for (int i = 1; i < PB; i++)
-                    if (i > k) t[i] -= lc[i] * t[k];
-            }
-            if (lane < PB) {
-#pragma unroll
-                for (int i = 0; i < PB; i++) {
-                    x_s[P + i][P + cc] = i >= cc ? t[i] : TF(0);
-                    lt[cc][i] = t[i];
-                }
-            }
-        } else if (p > 0) {
-            // T_pJ[i][c] = sum_{k = c}^{P-1} L[P + i][k] (L^{-1})[k][c], by 16-wide k blocks
-            for (int e = tid - 32; e < PB * P; e += blockDim.x - 32) {
-                const int i = e / P, c = e - i * P;
-                TF acc = TF(0);
-                for (int kb = c & ~(PB - 1); kb < P; kb += PB) {
-#pragma unroll
-                    for (int k = 0; k < PB; k++)
-                        if (kb + k >= c) acc += a_s[P + i][kb + k] * x_s[kb + k][c];
-                }
-                tq[i][c] = acc;
-            }
+            bar_arrive_n(kBarPanelReady, NT);
         }
-        __syncthreads();
-        // ---------------- S2 (into registers) ----------------
-        const int m = NB - P - PB;   // panel rows below the diagonal block
-        TF pv[4] = {TF(0), TF(0), TF(0), TF(0)};
-        const int pr = P + PB + (tid >> 2), pc = (tid & 3) * 4;
-        const bool panel = tid < 4 * m;
-        if (panel) {
+    } else {
+        const int ut = tid - 32;
+        for (int p = 0; p < NP; p++) {
+            const int P = p * PB;
+            bar_sync_n(kBarPanelReady, NT);
+            const TF(*L16)[PB + 4] = lt[p & 1];
+            // (a) block p + 1: its rows of panel p, then its diagonal update
+            const int R0 = P + PB;
+            if (p + 1 < NP) {
+                TF xv = TF(0);
+                const int xr = R0 + (ut >> 4), xc = ut & 15;
+                if (ut < PB * PB) {
 #pragma unroll
-            for (int k = 0; k < PB; k++) {
-                const TF av = a_s[pr][P + k];
-                TF lv[4];
-                lds4<TF>(&lt[k][pc], lv);
-#pragma unroll
-                for (int q = 0; q < 4; q++) pv[q] += av * lv[q];
-            }
-        }
-        TF iv[3] = {TF(0), TF(0), TF(0)};
-        if (tid >= 256 && p > 0) {
-#pragma unroll
-            for (int s2 = 0; s2 < 3; s2++) {
-                const int e = (tid - 256) + 256 * s2;
-                if (s2 < p) {
-                    const int i = e / P, c = e - i * P;
+                    for (int k = 0; k < PB; k++) xv += a_s[xr][P + k] * L16[k][xc];
+                }
+                bar_sync_n(kBarUpdate, NU);
+                if (ut < PB * PB) {
+                    a_s[xr][P + xc] = xv;
+                    pant[xc][xr] = xv;
+                }
+                bar_sync_n(kBarUpdate, NU);
+                if (ut < PB * PB && xc + R0 <= xr) {
                     TF acc = TF(0);
 #pragma unroll
-                    for (int k = 0; k < PB; k++)
-                        if (k <= i) acc += x_s[P + i][P + k] * tq[k][c];
-                    iv[s2] = -acc;
+                    for (int k = 0; k < PB; k++) acc += pant[k][xr] * pant[k][R0 + xc];
+                    a_s[xr][R0 + xc] -= acc;
                 }
+                bar_arrive_n(kBarNextReady, NT);
             }
-        }
-        __syncthreads();
-        if (panel) {
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                a_s[pr][P + pc + q] = pv[q];
-                pant[pc + q][pr] = pv[q];
-            }
-        }
-        if (tid >= 256 && p > 0) {
-#pragma unroll
-            for (int s2 = 0; s2 < 3; s2++) {
-                const int e = (tid - 256) + 256 * s2;
-                if (s2 < p) {
-                    const int i = e / P, c = e - i * P;
-                    x_s[P + i][c] = iv[s2];
-                }
-            }
-        }
-        __syncthreads();
-        // ---------------- S3: trailing update ----------------
-        const int T0 = P + PB;
-        if (T0 < NB) {
-            const int tx = tid & 15, ty = tid >> 4;
-            const int i0 = ty * 2, j0 = tx * 4;
-            if (i0 >= T0 && j0 >= T0 && j0 <= i0 + 1) {
-                TF acc[2][4];
-#pragma unroll
-                for (int a2 = 0; a2 < 2; a2++)
-#pragma unroll
-                    for (int b2 = 0; b2 < 4; b2++) acc[a2][b2] = TF(0);
+            // (b1) rows below block p + 1 (four columns per thread) and T_pJ
+            const int R1 = R0 + PB, m2 = NB - R1;
+            const bool panel = m2 > 0 && ut < 4 * m2;
+            const int pr = R1 + (ut >> 2), pc = (ut & 3) * 4;
+            TF pv[4] = {TF(0), TF(0), TF(0), TF(0)};
+            if (panel) {
 #pragma unroll
                 for (int k = 0; k < PB; k++) {
-                    TF u[2], w[4];
-                    lds2<TF>(&pant[k][i0], u);
-                    lds4<TF>(&pant[k][j0], w);
+                    const TF av = a_s[pr][P + k];
+                    TF lv[4];
+                    lds4<TF>(&L16[k][pc], lv);
 #pragma unroll
-                    for (int a2 = 0; a2 < 2; a2++)
-#pragma unroll
-                        for (int b2 = 0; b2 < 4; b2++) acc[a2][b2] += u[a2] * w[b2];
+                    for (int q = 0; q < 4; q++) pv[q] += av * lv[q];
                 }
-#pragma unroll
-                for (int a2 = 0; a2 < 2; a2++)
-#pragma unroll
-                    for (int b2 = 0; b2 < 4; b2++)
-                        if (j0 + b2 <= i0 + a2) a_s[i0 + a2][j0 + b2] -= acc[a2][b2];
             }
-            __syncthreads();
+            if (p > 0) {
+                // T_pJ[i][c] = sum_{k = c}^{P-1} L[P + i][k] (L^{-1})[k][c], by 16-wide k blocks
+                for (int e = ut; e < PB * P; e += NU) {
+                    const int i = e / P, c = e - i * P;
+                    TF acc = TF(0);
+                    for (int kb = c & ~(PB - 1); kb < P; kb += PB) {
+#pragma unroll
+                        for (int k = 0; k < PB; k++)
+                            if (kb + k >= c) acc += a_s[P + i][kb + k] * x_s[kb + k][c];
+                    }
+                    tq[i][c] = acc;
+                }
+            }
+            bar_sync_n(kBarUpdate, NU);
+            // (b2) store the rows; (L^{-1})_pJ = -L_pp^{-1} T_pJ into registers
+            if (panel) {
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    a_s[pr][P + pc + q] = pv[q];
+                    pant[pc + q][pr] = pv[q];
+                }
+            }
+            TF iv[2] = {TF(0), TF(0)};
+            if (p > 0) {
+#pragma unroll
+                for (int s2 = 0; s2 < 2; s2++) {
+                    const int e = ut + NU * s2;
+                    if (e < PB * P) {
+                        const int i = e / P, c = e - i * P;
+                        TF acc = TF(0);
+#pragma unroll
+                        for (int k = 0; k < PB; k++)
+                            if (k <= i) acc += x_s[P + i][P + k] * tq[k][c];
+                        iv[s2] = -acc;
+                    }
+                }
+            }
+            bar_sync_n(kBarUpdate, NU);
+            // (b3) store the inverse's block row; trailing update of blocks (i, k),
+            // i >= k >= p + 1, except block (p + 1, p + 1) done in (a)
+            if (p > 0) {
+#pragma unroll
+                for (int s2 = 0; s2 < 2; s2++) {
+                    const int e = ut + NU * s2;
+                    if (e < PB * P) {
+                        const int i = e / P, c = e - i * P;
+                        x_s[P + i][c] = iv[s2];
+                    }
+                }
+            }
+            const int mt = NB - R0;
+            for (int e = ut; e < mt * mt; e += NU) {
+                const int i = R0 + e / mt, j = R0 + e % mt;
+                if (j > i || i < R1) continue;   // upper part, or inside block (p + 1, p + 1)
+                TF acc = TF(0);
+#pragma unroll
+                for (int k = 0; k < PB; k++) acc += pant[k][i] * pant[k][j];
+                a_s[i][j] -= acc;
+            }
         }
     }
+    __syncthreads();
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         const int i = e >> 6, c = e & 63;
         if (i < nb && c < nb) A[(k0 + i) * n + k0 + c] = c <= i ? a_s[i][c] : TF(0);
@@ -288,6 +323,7 @@ __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, TF 
         if (c > i) x_s[i][c] = TF(0);   // x_s = L^{-1} in full for callers that keep it
     }
 }
+
 
 // ---------------------------------------------------------------------------------
 // Tile-task Cholesky in one launch.  CTA 0 runs the diagonal chain: for each block
