@@ -335,7 +335,8 @@ static int tc_prepare(Mesh *m) {
         const int64_t rows = std::max<int64_t>(1, B.n_tmpl);
         for (int q = 0; q < 4; q++)
             FEM3_TRY(dev_alloc_t(m, &B.tc_op[q], rows * B.tc_Kp));
-        std::vector<int4> work;
+        std::vector<int4> &work = B.h_tc_work;
+        work.clear();
         for (int b = 0; b < B.n_bins; b++) {
             int D = B.h_dof_off[b + 1] - B.h_dof_off[b];
             int G = B.h_gp_off[b + 1] - B.h_gp_off[b];
@@ -348,7 +349,6 @@ static int tc_prepare(Mesh *m) {
         if (B.tc_n_work)
             FEM3_CUDA(cudaMemcpyAsync(B.tc_work, work.data(), sizeof(int4) * work.size(),
                                       cudaMemcpyHostToDevice, s));
-        FEM3_CUDA(cudaStreamSynchronize(s));   // `work` is a host temporary
     }
     FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kSmemBytes));

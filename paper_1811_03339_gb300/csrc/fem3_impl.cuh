@@ -80,6 +80,7 @@ struct AxisBins {
     float2 *ap_L = nullptr, *ap_R = nullptr;
     int tc_n_work = 0;
     std::vector<int32_t> h_gp_off, h_dof_off;
+    std::vector<int4> h_work, h_tc_work;   // host copies of the work lists
     std::vector<int64_t> h_tab_off;
     std::vector<int32_t> h_tab_ld;
 };

@@ -568,6 +568,10 @@ int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
 int bins_build(Mesh *m) {
     cudaStream_t s = m->stream;
     const int64_t n_gp = m->n_gp, n_dof = m->n_dof;
+    // pass 1, all axes: bin counts and offsets, then one read-back of every offset array
+    // (device-to-host copies into pageable memory complete before they return)
+    int32_t *gcount[3], *dcount[3], *gcur[3], *dcur[3], *gbin[3];
+    BinGeom Gs[3];
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
         B.c0 = axis == 0 ? 1 : 0;
@@ -578,35 +582,45 @@ int bins_build(Mesh *m) {
         B.nb0 = std::max(1, (int)ceil((m->hi[B.c0] - m->lo[B.c0]) / B.width));
         B.nb1 = std::max(1, (int)ceil((m->hi[B.c1] - m->lo[B.c1]) / B.width));
         B.n_bins = B.nb0 * B.nb1;
-        BinGeom G{B.c0, B.c1, B.nb0, B.nb1, B.org0, B.org1, B.width};
+        Gs[axis] = BinGeom{B.c0, B.c1, B.nb0, B.nb1, B.org0, B.org1, B.width};
+        const BinGeom G = Gs[axis];
         const int nb = B.n_bins;
-
-        int32_t *gcount, *dcount, *gcur, *dcur, *gbin;
-        FEM3_TRY(dev_alloc_t(m, &gcount, nb));
-        FEM3_TRY(dev_alloc_t(m, &dcount, nb));
-        FEM3_TRY(dev_alloc_t(m, &gcur, nb));
-        FEM3_TRY(dev_alloc_t(m, &dcur, nb));
-        FEM3_TRY(dev_alloc_t(m, &gbin, n_gp));
+        FEM3_TRY(dev_alloc_t(m, &gcount[axis], nb));
+        FEM3_TRY(dev_alloc_t(m, &dcount[axis], nb));
+        FEM3_TRY(dev_alloc_t(m, &gcur[axis], nb));
+        FEM3_TRY(dev_alloc_t(m, &dcur[axis], nb));
+        FEM3_TRY(dev_alloc_t(m, &gbin[axis], n_gp));
         FEM3_TRY(dev_alloc_t(m, &B.gp_off, nb + 1));
         FEM3_TRY(dev_alloc_t(m, &B.dof_off, nb + 1));
-        FEM3_CUDA(cudaMemsetAsync(gcount, 0, sizeof(int32_t) * nb, s));
-        FEM3_CUDA(cudaMemsetAsync(dcount, 0, sizeof(int32_t) * nb, s));
-        FEM3_CUDA(cudaMemsetAsync(gcur, 0, sizeof(int32_t) * nb, s));
-        FEM3_CUDA(cudaMemsetAsync(dcur, 0, sizeof(int32_t) * nb, s));
-        k_gp_bin_count<<<grid_for(n_gp), kThreads, 0, s>>>(m->gp, n_gp, G, gcount, gbin);
+        FEM3_CUDA(cudaMemsetAsync(gcount[axis], 0, sizeof(int32_t) * nb, s));
+        FEM3_CUDA(cudaMemsetAsync(dcount[axis], 0, sizeof(int32_t) * nb, s));
+        FEM3_CUDA(cudaMemsetAsync(gcur[axis], 0, sizeof(int32_t) * nb, s));
+        FEM3_CUDA(cudaMemsetAsync(dcur[axis], 0, sizeof(int32_t) * nb, s));
+        k_gp_bin_count<<<grid_for(n_gp), kThreads, 0, s>>>(m->gp, n_gp, G, gcount[axis], gbin[axis]);
         note_launch(m);
         k_dof_bin_count<<<grid_for(n_dof), kThreads, 0, s>>>(m->node_box, m->dof_node, n_dof, G,
-                                                             dcount);
+                                                             dcount[axis]);
         note_launch(m);
-        FEM3_TRY(scan_i32(gcount, B.gp_off, nb, s, m));
-        FEM3_TRY(scan_i32(dcount, B.dof_off, nb, s, m));
+        FEM3_TRY(scan_i32(gcount[axis], B.gp_off, nb, s, m));
+        FEM3_TRY(scan_i32(dcount[axis], B.dof_off, nb, s, m));
+    }
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        const int nb = B.n_bins;
         B.h_gp_off.resize(nb + 1);
         B.h_dof_off.resize(nb + 1);
         FEM3_CUDA(cudaMemcpyAsync(B.h_gp_off.data(), B.gp_off, sizeof(int32_t) * (nb + 1),
                                   cudaMemcpyDeviceToHost, s));
         FEM3_CUDA(cudaMemcpyAsync(B.h_dof_off.data(), B.dof_off, sizeof(int32_t) * (nb + 1),
                                   cudaMemcpyDeviceToHost, s));
-        FEM3_CUDA(cudaStreamSynchronize(s));
+    }
+    FEM3_CUDA(cudaStreamSynchronize(s));
+    // pass 2, all axes: fill, sort and lay out; host-to-device copies from pageable memory
+    // are staged before they return, so nothing waits for the device here
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        const int nb = B.n_bins;
+        const BinGeom G = Gs[axis];
         B.n_tmpl = B.h_dof_off[nb];
         B.max_dof = 0;
         B.max_gp = 0;
@@ -625,11 +639,11 @@ int bins_build(Mesh *m) {
         FEM3_TRY(dev_alloc_t(m, &B.slot_bin, n_gp));
         FEM3_TRY(dev_alloc_t(m, &B.dof_idx, B.n_tmpl));
         double lo = m->lo[axis], span = std::max(m->hi[axis] - m->lo[axis], 1e-300);
-        k_gp_bin_fill<<<grid_for(n_gp), kThreads, 0, s>>>(m->gp, n_gp, axis, lo, span, gbin,
-                                                          B.gp_off, gcur, gkeys);
+        k_gp_bin_fill<<<grid_for(n_gp), kThreads, 0, s>>>(m->gp, n_gp, axis, lo, span, gbin[axis],
+                                                          B.gp_off, gcur[axis], gkeys);
         note_launch(m);
         k_dof_bin_fill<<<grid_for(n_dof), kThreads, 0, s>>>(m->node_box, m->dof_node, n_dof, G,
-                                                            B.dof_off, dcur, dkeys);
+                                                            B.dof_off, dcur[axis], dkeys);
         note_launch(m);
         k_bin_sort<<<nb, 1024, 0, s>>>(B.gp_off, gkeys, B.gp_idx, B.slot_bin);
         note_launch(m);
@@ -651,7 +665,8 @@ int bins_build(Mesh *m) {
         B.h_tab_off.resize(nb);
         B.h_tab_ld.resize(nb);
         int64_t acc = 0;
-        std::vector<int4> work;
+        std::vector<int4> &work = B.h_work;
+        work.clear();
         for (int b = 0; b < nb; b++) {
             int D = B.h_dof_off[b + 1] - B.h_dof_off[b];
             int Gc = B.h_gp_off[b + 1] - B.h_gp_off[b];
@@ -678,8 +693,6 @@ int bins_build(Mesh *m) {
                                       cudaMemcpyHostToDevice, s));
         FEM3_TRY(dev_alloc_t(m, &m->tabL[axis], std::max<int64_t>(1, acc)));
         FEM3_TRY(dev_alloc_t(m, &m->tabR[axis], std::max<int64_t>(1, acc)));
-        // host vectors passed to async copies must outlive them
-        FEM3_CUDA(cudaStreamSynchronize(s));
     }
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
