@@ -125,16 +125,31 @@ __global__ void k_tet_geom(const double *__restrict__ verts, const int32_t *__re
 }
 
 // bounding box of the vertices (ordered-integer atomics) and total volume
+// bounding box of the nodes and total tet volume: reduced within each warp first, one
+// atomic per warp and quantity
 __global__ void k_extent(const double *__restrict__ verts, int64_t n_nodes,
                          const double *__restrict__ vol, int64_t n_tets,
                          unsigned long long *ext, double *vsum) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n_nodes)
-        for (int d = 0; d < 3; d++) {
-            atomicMin(&ext[d], ord_of(verts[3 * i + d]));
-            atomicMax(&ext[3 + d], ord_of(verts[3 * i + d]));
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        unsigned long long lo = ~0ull, hi = 0ull;
+        if (i < n_nodes) lo = hi = ord_of(verts[3 * i + d]);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o);
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, hi, o);
+            lo = a < lo ? a : lo;
+            hi = b > hi ? b : hi;
         }
-    if (i < n_tets) atomicAdd(vsum, vol[i]);
+        if (lane == 0 && lo != ~0ull) {
+            atomicMin(&ext[d], lo);
+            atomicMax(&ext[3 + d], hi);
+        }
+    }
+    double v = i < n_tets ? vol[i] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && v != 0.0) atomicAdd(vsum, v);
 }
 
 __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v) {
@@ -398,9 +413,11 @@ __global__ void k_dof_bin_fill(const double *__restrict__ box, const int32_t *__
 
 // One CTA per bin: bitonic sort of the bin's keys in shared memory, then write the
 // low 32 bits as the sorted ids (and the slot -> bin map for Gauss points).
+// one CTA per bin: bitonic sort of the bin's keys in shared memory (sized by the launch
+// for the largest bin, rounded up to a power of two)
 __global__ void k_bin_sort(const int32_t *__restrict__ off, unsigned long long *keys,
                            int32_t *ids, int32_t *slot_bin) {
-    __shared__ unsigned long long sh[kMaxBinItems];
+    extern __shared__ unsigned long long sh[];
     int b = blockIdx.x;
     int lo = off[b], n = off[b + 1] - lo;
     int p2 = 1;
@@ -645,10 +662,15 @@ int bins_build(Mesh *m) {
         k_dof_bin_fill<<<grid_for(n_dof), kThreads, 0, s>>>(m->node_box, m->dof_node, n_dof, G,
                                                             B.dof_off, dcur[axis], dkeys);
         note_launch(m);
-        k_bin_sort<<<nb, 1024, 0, s>>>(B.gp_off, gkeys, B.gp_idx, B.slot_bin);
-        note_launch(m);
-        k_bin_sort<<<nb, 1024, 0, s>>>(B.dof_off, dkeys, B.dof_idx, nullptr);
-        note_launch(m);
+        {
+            auto pow2 = [](int v) { int p = 1; while (p < v) p <<= 1; return p; };
+            const size_t shg = sizeof(unsigned long long) * pow2(std::max(1, B.max_gp));
+            const size_t shd = sizeof(unsigned long long) * pow2(std::max(1, B.max_dof));
+            k_bin_sort<<<nb, 256, shg, s>>>(B.gp_off, gkeys, B.gp_idx, B.slot_bin);
+            note_launch(m);
+            k_bin_sort<<<nb, 256, shd, s>>>(B.dof_off, dkeys, B.dof_idx, nullptr);
+            note_launch(m);
+        }
         FEM3_TRY(dev_alloc_t(m, &B.row_bin, std::max<int64_t>(1, B.n_tmpl)));
         if (B.n_tmpl > 0) {
             k_row_bin<<<nb, 256, 0, s>>>(B.dof_off, nb, B.row_bin);
