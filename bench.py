@@ -45,8 +45,8 @@ def _peaks():
 # DRAM bytes (read + write) of one k_walk_tables launch from the ncu capture summarised in
 # profiles/k_walk_tables_cube16_jitter.md, valid only for the kernel source it was taken
 # on (sha256 of csrc/walk.cu); otherwise the traffic is reported as unknown.
-WALK_TRAFFIC = {"walk_cu_sha256": "ddd5359012ad9668a52ce237a89efbe597d289c5957557e6f4484ee46e526ff8",
-                "bytes_per_launch": 201950720 + 107748096, "segments_per_launch": 16099980}
+WALK_TRAFFIC = {"walk_cu_sha256": "ac49b5f54c2396a1818e20aa53087dcf8b0358013716575252b590df22f20711",
+                "bytes_per_launch": 211476992 + 107675392, "segments_per_launch": 16099980}
 
 
 def _walk_traffic(segs_per_launch):

@@ -99,6 +99,7 @@ struct Mesh {
     int32_t *tets = nullptr;   // [n_tets][4]
     double *M = nullptr;       // [n_tets][16] rows (c_k, dlam_k/dx, dlam_k/dy, dlam_k/dz)
     double *inv = nullptr;     // [n_tets][3][4] 1/dlam_k/dx_axis, 0 if parallel
+    float4 *recf = nullptr;    // [n_tets][3][8] FP32 records of the walk's exit filter
     double *vol = nullptr;     // [n_tets]
     int32_t *nbr = nullptr;    // [n_tets][4]
     int32_t *dof = nullptr;    // [n_nodes]

@@ -35,9 +35,9 @@ __device__ __forceinline__ double double_of_ord(unsigned long long o) {
 __global__ void k_tet_geom(const double *__restrict__ verts, const int32_t *__restrict__ tets,
                            int64_t n_tets, int64_t n_nodes, double qa, double qb,
                            double *__restrict__ M, double *__restrict__ inv,
-                           double *__restrict__ vol, double *__restrict__ gp,
-                           double *__restrict__ gw, unsigned long long *__restrict__ node_box,
-                           int32_t *__restrict__ err) {
+                           float4 *__restrict__ recf, double *__restrict__ vol,
+                           double *__restrict__ gp, double *__restrict__ gw,
+                           unsigned long long *__restrict__ node_box, int32_t *__restrict__ err) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n_tets) return;
     double v[4][3];
@@ -93,11 +93,62 @@ __global__ void k_tet_geom(const double *__restrict__ verts, const int32_t *__re
         Mt[4 * k + 2] = g[k][1];
         Mt[4 * k + 3] = g[k][2];
     }
+    double iv[3][4];
     for (int a = 0; a < 3; a++) {
         double ds = 0;
         for (int k = 0; k < 4; k++) ds = fmax(ds, fabs(g[k][a]));
-        for (int k = 0; k < 4; k++)
-            inv[12 * t + 4 * a + k] = fabs(g[k][a]) > kEpsDRel * ds ? 1.0 / g[k][a] : 0.0;
+        for (int k = 0; k < 4; k++) {
+            iv[a][k] = fabs(g[k][a]) > kEpsDRel * ds ? 1.0 / g[k][a] : 0.0;
+            inv[12 * t + 4 * a + k] = iv[a][k];
+        }
+    }
+    // FP32 records of the walk's exit filter, one 128-byte record per (tet, axis), in
+    // tet-local form lambda_k(x) = A_k + grad lambda_k . (x - c_T) about an FP32 point c_T
+    // (the rounded centroid):
+    //   [0] A_k = lambda_k(c_T); [1], [2] hi + lo split of dlambda_k/dx_axis (the table
+    //   factor); [3] FP32 copy of the FP64 reciprocal (same sign, 0 where it is 0);
+    //   [4], [5] dlambda_k/dx_p1, dlambda_k/dx_p2 for p1 = axis + 1, p2 = axis + 2 (mod 3);
+    //   [6] (c_p1, c_p2, F0, Gmax): Gmax >= max_k sum_i |dlambda_k/dx_i| and
+    //   F0 >= 1 + Gmax |c_T|_inf, both rounded up; [7] unused.
+    // The filter that reads them decides only what its error bounds separate (the FP64
+    // step decides the rest).
+    float cT[3];
+    for (int d = 0; d < 3; d++)
+        cT[d] = __double2float_rn(0.25 * (((v[0][d] + v[1][d]) + v[2][d]) + v[3][d]));
+    float Ak[4];
+    double gs = 0.0, cn = 0.0;
+    for (int k = 0; k < 4; k++) {
+        Ak[k] = __double2float_rn(c[k] + g[k][0] * (double)cT[0] + g[k][1] * (double)cT[1] +
+                                  g[k][2] * (double)cT[2]);
+        gs = fmax(gs, fabs(g[k][0]) + fabs(g[k][1]) + fabs(g[k][2]));
+    }
+    for (int d = 0; d < 3; d++) cn = fmax(cn, fabs((double)cT[d]));
+    // values far outside FP32's normal range make the filter defer every step (F0 = inf)
+    bool in_range = gs * cn < 0x1p100;
+    for (int a = 0; a < 3; a++)
+        for (int k = 0; k < 4; k++) {
+            const double ga = fabs(g[k][a]), ia = fabs(iv[a][k]);
+            in_range &= (ga == 0.0 || (ga > 0x1p-100 && ga < 0x1p100)) &&
+                        (ia == 0.0 || (ia > 0x1p-100 && ia < 0x1p100));
+        }
+    const float gmax = __double2float_ru(gs * (1.0 + 1e-9));
+    const float f0 = in_range ? __double2float_ru((1.0 + gs * cn) * (1.0 + 1e-9)) : INFINITY;
+    for (int a = 0; a < 3; a++) {
+        const int p1 = a == 2 ? 0 : a + 1, p2 = a == 0 ? 2 : a - 1;
+        float gh[4], gl[4];
+        for (int k = 0; k < 4; k++) f64_split(g[k][a], gh[k], gl[k]);
+        float4 *R = recf + 8 * (3 * t + a);
+        R[0] = make_float4(Ak[0], Ak[1], Ak[2], Ak[3]);
+        R[1] = make_float4(gh[0], gh[1], gh[2], gh[3]);
+        R[2] = make_float4(gl[0], gl[1], gl[2], gl[3]);
+        R[3] = make_float4(__double2float_rn(iv[a][0]), __double2float_rn(iv[a][1]),
+                           __double2float_rn(iv[a][2]), __double2float_rn(iv[a][3]));
+        R[4] = make_float4(__double2float_rn(g[0][p1]), __double2float_rn(g[1][p1]),
+                           __double2float_rn(g[2][p1]), __double2float_rn(g[3][p1]));
+        R[5] = make_float4(__double2float_rn(g[0][p2]), __double2float_rn(g[1][p2]),
+                           __double2float_rn(g[2][p2]), __double2float_rn(g[3][p2]));
+        R[6] = make_float4(cT[p1], cT[p2], f0, gmax);
+        R[7] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // Gauss points: point q has barycentric qa at vertex q, qb elsewhere; summed in
     // vertex order without contraction (bit-identical to a plain IEEE evaluation)
@@ -483,6 +534,7 @@ int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
     const int64_t T = m->n_tets, N = m->n_nodes;
     FEM3_TRY(dev_alloc_t(m, &m->M, 16 * T));
     FEM3_TRY(dev_alloc_t(m, &m->inv, 12 * T));
+    FEM3_TRY(dev_alloc_t(m, &m->recf, 24 * T));
     FEM3_TRY(dev_alloc_t(m, &m->vol, T));
     FEM3_TRY(dev_alloc_t(m, &m->nbr, 4 * T));
     FEM3_TRY(dev_alloc_t(m, &m->dof, N));
@@ -500,7 +552,7 @@ int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
     k_box_init<<<grid_for(6 * N), kThreads, 0, s>>>(box, N);
     note_launch(m);
     k_tet_geom<<<grid_for(T), kThreads, 0, s>>>(verts_d, tets_d, T, N, qa, qb, m->M, m->inv,
-                                                 m->vol, m->gp, m->gw, box, m->err);
+                                                 m->recf, m->vol, m->gp, m->gw, box, m->err);
     note_launch(m);
     k_box_decode<<<grid_for(6 * N), kThreads, 0, s>>>(box, 6 * N);
     note_launch(m);

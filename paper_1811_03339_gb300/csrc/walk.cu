@@ -28,6 +28,7 @@ namespace {
 struct WalkGeom {
     const double *__restrict__ M;     // [T][16]
     const double *__restrict__ inv;   // [T][3][4]
+    const float4 *__restrict__ rec;   // [T][3][8] FP32 records of the exit filter
     const int32_t *__restrict__ tets; // [T][4]
     const int32_t *__restrict__ nbr;  // [T][4]
     const int32_t *__restrict__ dof;  // [N]
@@ -77,17 +78,126 @@ __device__ __forceinline__ double tet_rmax(const WalkGeom &W, int32_t t, int axi
     return key_double(kmin);
 }
 
-// next tet after leaving t at parameter rmax; -1 at the boundary, -2 on a bad pattern
-__device__ int32_t next_tet(const WalkGeom &W, int32_t t, int axis, int dir, double x0,
-                            double x1, double x2, const double b[4], double rmax) {
-    const double *Mt = W.M + 16 * (int64_t)t;
-    const double rs = dir > 0 ? rmax : -rmax;
-    int zmask = 0;
+// Per-line FP32 constants of the exit filter: the two coordinates across the axis,
+// p1 = axis + 1 and p2 = axis + 2 (mod 3), as hi + lo pairs, and an upper bound of |x|_inf.
+struct LineF {
+    float xh1, xl1, xh2, xl2, xn;
+};
+
+__device__ __forceinline__ LineF line_f(double x0, double x1, double x2, int axis) {
+    const double y1 = axis == 0 ? x1 : (axis == 1 ? x2 : x0);
+    const double y2 = axis == 0 ? x2 : (axis == 1 ? x0 : x1);
+    LineF X;
+    X.xh1 = __double2float_rn(y1);
+    X.xl1 = __double2float_rn(y1 - (double)X.xh1);
+    X.xh2 = __double2float_rn(y2);
+    X.xl2 = __double2float_rn(y2 - (double)X.xh2);
+    X.xn = __double2float_ru(fmax(fabs(x0), fmax(fabs(x1), fabs(x2))));
+    return X;
+}
+
+constexpr float kU32 = 5.9604644775390625e-08f;    // 2^-24, FP32 unit roundoff
+constexpr float kTwoM44 = 5.684341886080802e-14f;  // 2^-44
+
+// FP32 exit filter of one walk step (tet record R, ray direction dir along the axis).
+// In the tet-local form of the record the ray meets lambda_k = 0 at the axis offset
+// sigma_k = -beta_k / g_k from c_T, with beta_k = A_k + g_p1 dx_p1 + g_p2 dx_p2 and
+// dx = x - c_T across the axis; the exit candidate (g_k of sign -dir) with the smallest
+// dir * sigma_k is the exit, and lambda_k = beta_k + g_k sigma* at the exit gives the
+// zero pattern.  Each quantity carries a bound on its distance from the value the FP64
+// step computes: 16 u per magnitude for the FP32 rounding of the record, the split of x
+// and the arithmetic (about 6 u needed), and F = 2^-44 (F0 + Gmax |x|_inf) for the FP64
+// step's own rounding and the x split's second-order term (both below 2^-46 times that
+// sum).  A decision is taken only where its bound separates it, so it is the FP64
+// step's decision.  Returns false if some decision is within its bound (the caller then
+// takes the FP64 step); else kstar = the exit candidate and zmask = the zero pattern
+// without kstar's bit, which the caller tests in FP64.
+__device__ __forceinline__ bool exit_filter(const float4 *__restrict__ R, const LineF &X, int dir,
+                                            int &kstar, int &zmask) {
+    const float4 A4 = __ldg(R), G4 = __ldg(R + 1), I4 = __ldg(R + 3), P4 = __ldg(R + 4),
+                 Q4 = __ldg(R + 5), C4 = __ldg(R + 6);
+    const float A[4] = {A4.x, A4.y, A4.z, A4.w}, G[4] = {G4.x, G4.y, G4.z, G4.w},
+                I[4] = {I4.x, I4.y, I4.z, I4.w}, P[4] = {P4.x, P4.y, P4.z, P4.w},
+                Q[4] = {Q4.x, Q4.y, Q4.z, Q4.w};
+    const float d1 = (X.xh1 - C4.x) + X.xl1, d2 = (X.xh2 - C4.y) + X.xl2;
+    const float F = kTwoM44 * fmaf(C4.w, X.xn, C4.z);
+    float beta[4], eb[4], q[4], e[4];
+    bool cand[4];
+    float qs = INFINITY, es = 0.f;
+    int ks = -1;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        double lam = fma(rs, Mt[4 * k + 1 + axis], b[k]);
-        if (le_eps(lam)) zmask |= 1 << k;
+        beta[k] = fmaf(Q[k], d2, fmaf(P[k], d1, A[k]));
+        const float S = fabsf(A[k]) + fabsf(P[k] * d1) + fabsf(Q[k] * d2);
+        eb[k] = fmaf(16.f * kU32, S, F);
+        const float sg = -beta[k] * I[k];
+        q[k] = dir > 0 ? sg : -sg;
+        e[k] = fmaf(fabsf(I[k]), eb[k], 4.f * kU32 * fabsf(sg));
+        // the FP64 step's candidates: the sign bit of the reciprocal
+        const int ib = __float_as_int(I[k]);
+        cand[k] = dir > 0 ? ib < 0 : ib > 0;
+        if (cand[k] && q[k] < qs) {
+            qs = q[k];
+            es = e[k];
+            ks = k;
+        }
     }
+    if (ks < 0) return false;
+    const float sig = dir > 0 ? qs : -qs;
+    int zm = 0;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (k == ks) continue;
+        if (cand[k] && !(q[k] - qs > e[k] + es)) ok = false;
+        const float lam = fmaf(G[k], sig, beta[k]);
+        const float El =
+            eb[k] + F + fabsf(G[k]) * es + 4.f * kU32 * (fabsf(G[k] * sig) + fabsf(lam));
+        if (lam <= 1e-12f - El)
+            zm |= 1 << k;
+        else if (!(lam > 1e-12f + El))
+            ok = false;
+    }
+    kstar = ks;
+    zmask = zm;
+    return ok;
+}
+
+// One walk step in tet t: the go-out parameter r_max (the FP64 expression of tet_rmax)
+// and the zero pattern of the volume coordinates there (FP64 test lambda <= eps_lambda),
+// decided by the FP32 filter where its bounds allow and by the FP64 step otherwise, with
+// the same outcome either way.  r_max = +inf if the ray cannot leave t.
+__device__ __forceinline__ double exit_step(const WalkGeom &W, const LineF &X, int32_t t,
+                                            int axis, int dir, double x0, double x1, double x2,
+                                            int &zmask) {
+    int ks, zm;
+    if (exit_filter(W.rec + 8 * (3 * (int64_t)t + axis), X, dir, ks, zm)) {
+        const double2 *Mk = reinterpret_cast<const double2 *>(W.M + 16 * (int64_t)t) + 2 * ks;
+        const double2 a = Mk[0], c = Mk[1];
+        const double bk = fma(c.y, x2, fma(c.x, x1, fma(a.y, x0, a.x)));
+        const double iv = W.inv[12 * (int64_t)t + 4 * axis + ks];
+        const double rmax = dir > 0 ? -(bk * iv) : bk * iv;
+        const double gk = axis == 0 ? a.y : (axis == 1 ? c.x : c.y);
+        const double lam = fma(dir > 0 ? rmax : -rmax, gk, bk);
+        zmask = zm | (le_eps(lam) ? 1 << ks : 0);
+        return rmax;
+    }
+    double b[4];
+    const double rmax = tet_rmax(W, t, axis, dir, x0, x1, x2, b);
+    const double *Mt = W.M + 16 * (int64_t)t;
+    const double rs = dir > 0 ? rmax : -rmax;
+    int z = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (le_eps(fma(rs, Mt[4 * k + 1 + axis], b[k]))) z |= 1 << k;
+    zmask = z;
+    return rmax;
+}
+
+// next tet after leaving t at parameter rmax through the m-face of the zero pattern
+// zmask; -1 at the boundary, -2 on a bad pattern
+__device__ int32_t next_tet(const WalkGeom &W, int32_t t, int axis, int dir, double x0,
+                            double x1, double x2, int zmask, double rmax) {
     int nz = __popc(zmask);
     if (nz == 1) return W.nbr[4 * (int64_t)t + (__ffs(zmask) - 1)];
     if (nz < 2 || nz > 3) return -2;
@@ -123,15 +233,18 @@ __device__ int32_t next_tet(const WalkGeom &W, int32_t t, int axis, int dir, dou
     return next;
 }
 
+// position of dof j in the ascending list d[0 .. n), or -1: binary lifting for the number
+// of entries <= j, with a trip count set by n alone (lanes searching one list stay
+// converged) and every load inside the list
 __device__ __forceinline__ int bsearch_dof(const int32_t *__restrict__ d, int n, int32_t j) {
-    int lo = 0, hi = n - 1;
-    while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        int32_t v = __ldg(d + mid);
-        if (v == j) return mid;
-        if (v < j) lo = mid + 1; else hi = mid - 1;
+    if (n <= 0) return -1;
+    int base = 0;
+    for (int step = 1 << (31 - __clz(n)); step > 0; step >>= 1) {
+        const int c = base + step;
+        const int32_t v = __ldg(d + (c < n ? c : n) - 1);
+        if (c <= n && v <= j) base = c;
     }
-    return -1;
+    return (base > 0 && __ldg(d + base - 1) == j) ? base - 1 : -1;
 }
 
 struct TableArgs {
@@ -209,11 +322,23 @@ __global__ void k_pow_tables(double p0, double p1, double p2, float2 *cell, floa
     fill_pow_cell(p, j, cell + (size_t)a * 256 * 8, pexp + a * 128);
 }
 
+// (table entry) += (h + l)
+__device__ __forceinline__ void flush_entry(float2 *tab, int32_t col, int32_t ld, float h,
+                                            float l) {
+    float2 *te = tab + (int64_t)col * ld;
+    float2 v = *te;
+    df_add(h, l, v.x, v.y);
+    *te = v;
+}
+
 // One line (Gauss point in slot `slot` of an axis): both directions in one loop.  When
 // the left walk reaches the boundary the same iteration switches to the right walk, so a
 // lane's trip count is one whole chord (nearly equal for neighbouring Gauss points) and
-// the lanes of a warp stay converged.  Returns the number of segments; counts template
-// misses and failed walks.
+// the lanes of a warp stay converged.  The table entries of the current tet's vertices
+// are accumulated in registers (consecutive tets of a path share three vertices) and
+// added to the table when a vertex drops out of the current tet or the walk ends, so a
+// step costs about one table read-modify-write.  Returns the number of segments; counts
+// template misses and failed walks.
 __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
                                          const TableArgs &A1, int axis, int64_t slot,
                                          int &miss, int &bad) {
@@ -227,59 +352,109 @@ __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
     const int64_t toff = A0.tab_off[bin] + row;
     const double x0 = W.gp[3 * (int64_t)g], x1 = W.gp[3 * (int64_t)g + 1],
                  x2 = W.gp[3 * (int64_t)g + 2];
-    const double p_exp = A0.p_exp;   // same order on both sides of the line
-    int side = 0, dir = -1;
-    float2 *tab = A0.tab + toff;
-    float coef_h = A0.coef_h, coef_l = A0.coef_l;
+    const LineF X = line_f(x0, x1, x2, axis);
+    int side = 0;   // 0: left walk (dir -1, table L), 1: right walk (dir +1, table R)
     int32_t t = g >> 2;
     double r_prev = 0.0;
     float pp_h = 0.f, pp_l = 0.f;   // r_prev^p
-    int32_t cj[4] = {-1, -1, -1, -1}, cc[4] = {-1, -1, -1, -1};
+    // live vertices: dof (-2: none), table column (-1: none), accumulated entry (hi + lo)
+    int32_t sj[4] = {-2, -2, -2, -2}, sc[4] = {-1, -1, -1, -1};
+    float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
     int steps = 0;
-    for (int it = 0; it < 2 * W.max_steps; it++) {
-        double b[4];
-        const double rmax = tet_rmax(W, t, axis, dir, x0, x1, x2, b);
+    for (;;) {   // at most max_steps steps per side
+        const int dir = side ? 1 : -1;
+        float2 *const tab = (side ? A1.tab : A0.tab) + toff;
+        const int4 tv = __ldg(reinterpret_cast<const int4 *>(W.tets) + t);
+        int zmask;
+        const double rmax = exit_step(W, X, t, axis, dir, x0, x1, x2, zmask);
         int32_t nx = -2;
         if (rmax < INFINITY) {
+            nx = next_tet(W, t, axis, dir, x0, x1, x2, zmask, rmax);
             if (rmax - r_prev > W.eps_r) {
                 // table part in double-float FP32: c = coef (rmax^p - r_prev^p)
                 float ph, pl, ch, cl;
-                pow_df(rmax, p_exp, A0.pow_cell, A0.pow_exp, ph, pl);
+                pow_df(rmax, A0.p_exp, A0.pow_cell, A0.pow_exp, ph, pl);
                 df_add2(ph, pl, -pp_h, -pp_l, ch, cl);
-                df_mul(ch, cl, coef_h, coef_l, ch, cl);
-                const double *Mt = W.M + 16 * (int64_t)t;
-                int32_t nj[4], nc[4];
+                df_mul(ch, cl, side ? A1.coef_h : A0.coef_h, side ? A1.coef_l : A0.coef_l, ch,
+                       cl);
+                // dlambda_v/dx_axis as hi + lo pairs from the tet's record
+                const float4 *R = W.rec + 8 * (3 * (int64_t)t + axis);
+                const float4 gh4 = __ldg(R + 1), gl4 = __ldg(R + 2);
+                const float ghv[4] = {gh4.x, gh4.y, gh4.z, gh4.w},
+                            glv[4] = {gl4.x, gl4.y, gl4.z, gl4.w};
+                const int32_t j[4] = {W.dof[tv.x], W.dof[tv.y], W.dof[tv.z], W.dof[tv.w]};
+                // slots kept (their dof is a vertex of t) and vertices already in a slot
+                unsigned keep = 0, need = 0;
 #pragma unroll
                 for (int v = 0; v < 4; v++) {
-                    int32_t j = W.dof[W.tets[4 * (int64_t)t + v]];
-                    int32_t col = -1;
-                    if (j >= 0) {
+                    bool hit = false;
 #pragma unroll
-                        for (int q = 0; q < 4; q++)
-                            if (cj[q] == j) col = cc[q];
-                        if (col < 0) col = bsearch_dof(dofs, nd, j);
-                        if (col >= 0) {
-                            float gh, gl;
-                            f64_split(Mt[4 * v + 1 + axis], gh, gl);
-                            float2 *te = tab + (int64_t)col * ld;
-                            float2 tv = *te;
-                            df_fma(ch, cl, gh, gl, tv.x, tv.y);
-                            *te = tv;
-                        } else {
-                            miss++;
+                    for (int q = 0; q < 4; q++)
+                        if (sj[q] == j[v]) {
+                            hit = true;
+                            keep |= 1u << q;
                         }
-                    }
-                    nj[v] = j;
-                    nc[v] = col;
+                    if (!hit && j[v] >= 0) need |= 1u << v;
+                }
+                // slots whose vertex left: the entries go to the table (one write per pass
+                // for all lanes), then the slots are freed
+                unsigned flw = 0;
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (!(keep & (1u << q)) && sc[q] >= 0) flw |= 1u << q;
+                while (flw) {
+                    const int q = __ffs(flw) - 1;
+                    flw &= flw - 1;
+                    const int32_t c = q == 0 ? sc[0] : (q == 1 ? sc[1] : (q == 2 ? sc[2] : sc[3]));
+                    const float h = q == 0 ? sh[0] : (q == 1 ? sh[1] : (q == 2 ? sh[2] : sh[3]));
+                    const float l = q == 0 ? sl[0] : (q == 1 ? sl[1] : (q == 2 ? sl[2] : sl[3]));
+                    flush_entry(tab, c, ld, h, l);
                 }
 #pragma unroll
-                for (int v = 0; v < 4; v++) { cj[v] = nj[v]; cc[v] = nc[v]; }
+                for (int q = 0; q < 4; q++)
+                    if (!(keep & (1u << q))) {
+                        sj[q] = -2;
+                        sc[q] = -1;
+                        sh[q] = 0.f;
+                        sl[q] = 0.f;
+                    }
+                // new vertices take free slots; one template search per pass for all lanes
+                unsigned freem = ~keep & 0xFu;
+                while (need) {
+                    const int v = __ffs(need) - 1;
+                    need &= need - 1;
+                    const int q = __ffs(freem) - 1;
+                    freem &= freem - 1;
+                    const int32_t jv = v == 0 ? j[0] : (v == 1 ? j[1] : (v == 2 ? j[2] : j[3]));
+                    const int32_t c = bsearch_dof(dofs, nd, jv);
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (u == q) {
+                            sj[u] = jv;
+                            sc[u] = c;
+                        }
+                }
+                // add c * dlambda_v/dx_axis to the slot of each vertex v
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (sj[q] < 0) continue;
+                    float gh = ghv[0], gl = glv[0];
+#pragma unroll
+                    for (int v = 1; v < 4; v++)
+                        if (sj[q] == j[v]) {
+                            gh = ghv[v];
+                            gl = glv[v];
+                        }
+                    if (sc[q] >= 0)
+                        df_fma(ch, cl, gh, gl, sh[q], sl[q]);
+                    else
+                        miss++;
+                }
                 pp_h = ph;
                 pp_l = pl;
                 r_prev = rmax;
                 nseg++;
             }
-            nx = next_tet(W, t, axis, dir, x0, x1, x2, b, rmax);
         }
         steps++;
         if (nx >= 0 && steps < W.max_steps) {
@@ -287,20 +462,23 @@ __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
             continue;
         }
         bad += (nx != -1);   // no exit found, bad pattern or step cap
+        // end of this direction: the live entries go to the table
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (sc[q] >= 0) flush_entry(tab, sc[q], ld, sh[q], sl[q]);
+            sj[q] = -2;
+            sc[q] = -1;
+            sh[q] = 0.f;
+            sl[q] = 0.f;
+        }
         if (side == 1) break;
-        // switch to the right walk of the same line
+        // switch to the right walk of the same line (same order 1 - gamma on both sides)
         side = 1;
-        dir = 1;
-        tab = A1.tab + toff;
-        coef_h = A1.coef_h;
-        coef_l = A1.coef_l;
         t = g >> 2;
         r_prev = 0.0;
         pp_h = 0.f;
         pp_l = 0.f;
         steps = 0;
-#pragma unroll
-        for (int v = 0; v < 4; v++) { cj[v] = -1; cc[v] = -1; }
     }
     return nseg;
 }
@@ -318,7 +496,7 @@ struct AxisTables {
 
 // grid: x over the slots of an axis, y = axis; the three axes in one launch keep every SM
 // filled (one axis alone is about five CTAs per SM)
-__global__ void __launch_bounds__(128, 7) k_walk_tables(WalkGeom W, AxisTables T, int64_t n_gp,
+__global__ void __launch_bounds__(128, 6) k_walk_tables(WalkGeom W, AxisTables T, int64_t n_gp,
                                                         int32_t *err,
                                                         unsigned long long *seg_count) {
     const int axis = blockIdx.y;
@@ -344,7 +522,7 @@ struct WalkDesc {
     unsigned long long *seg;
 };
 
-__global__ void __launch_bounds__(128, 7) k_walk_batch(const WalkDesc *__restrict__ descs, int n_desc,
+__global__ void __launch_bounds__(128, 6) k_walk_batch(const WalkDesc *__restrict__ descs, int n_desc,
                                                     int64_t n_items) {
     const int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int nseg = 0, miss = 0, bad = 0, d = 0;
@@ -398,13 +576,14 @@ __global__ void k_walk_paths(WalkGeom W, int axis, int dir, const int64_t *__res
         return;
     }
     const double x0 = W.gp[3 * g], x1 = W.gp[3 * g + 1], x2 = W.gp[3 * g + 2];
+    const LineF X = line_f(x0, x1, x2, axis);
     int32_t t = (int32_t)(g >> 2);
     double r_prev = 0.0;
     int nseg = 0;
     bool ok = false;
     for (int step = 0; step < W.max_steps; step++) {
-        double b[4];
-        double rmax = tet_rmax(W, t, axis, dir, x0, x1, x2, b);
+        int zmask;
+        const double rmax = exit_step(W, X, t, axis, dir, x0, x1, x2, zmask);
         if (!(rmax < INFINITY)) break;
         if (rmax - r_prev > W.eps_r) {
             if (nseg >= cap) break;
@@ -414,7 +593,7 @@ __global__ void k_walk_paths(WalkGeom W, int axis, int dir, const int64_t *__res
             nseg++;
             r_prev = rmax;
         }
-        int32_t nx = next_tet(W, t, axis, dir, x0, x1, x2, b, rmax);
+        int32_t nx = next_tet(W, t, axis, dir, x0, x1, x2, zmask, rmax);
         if (nx == -1) { ok = true; break; }
         if (nx < 0) break;
         t = nx;
@@ -446,7 +625,7 @@ __global__ void k_table_rows(const float2 *__restrict__ tab, const int32_t *__re
 
 WalkGeom make_geom(Mesh *m) {
     WalkGeom W;
-    W.M = m->M; W.inv = m->inv; W.tets = m->tets; W.nbr = m->nbr; W.dof = m->dof;
+    W.M = m->M; W.inv = m->inv; W.rec = m->recf; W.tets = m->tets; W.nbr = m->nbr; W.dof = m->dof;
     W.vt_off = m->vt_off; W.vt_tet = m->vt_tet; W.gp = m->gp;
     W.eps_r = kEpsRRel * m->span;
     W.max_steps = m->max_steps;
