@@ -10,7 +10,7 @@ metric: Gauss-point paths per second - one path = one Gauss point and one axis, 
 directions walked and tabulated - through the whole step.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       [--precision tf32x3|fp32|fp64]
+       [--precision tf32x3|bf16x3|fp32|fp64]
 """
 from __future__ import annotations
 
@@ -266,6 +266,21 @@ def run_ours(args):
     m64.free()
     rel_mix_fp64 = float(torch.linalg.norm(u_mix - u64) / torch.linalg.norm(u64))
 
+    # --- the other tensor-core form (BF16 x 3 split products), same step ----------------
+    other = None
+    if args.precision in ("tf32x3", "bf16x3"):
+        oprec = "bf16x3" if args.precision == "tf32x3" else "tf32x3"
+        to = timed(oprec, k64, 1)
+        mo, uo = step(oprec, profile=True, keep=True)
+        mo.sync()
+        other = {"precision": oprec, "ms_per_step": sum(to) / k64,
+                 "vs_fp64_speedup": ms_fp64 / (sum(to) / k64),
+                 "refinement_sweeps": mo.iters, "final_rel_residual": mo.resid,
+                 "u_rel_diff_vs_fp64": float(torch.linalg.norm(uo - u64) / torch.linalg.norm(u64)),
+                 "stages_ms": dict(zip(["mesh", "bins", "walk_tables", "contract", "load",
+                                        "factor", "solve_refine"], mo.stage_ms()))}
+        mo.free()
+
     # walk+tables kernel: one launch per step covering the three axes, timed live by the
     # library's events on the launch stream.  Algorithmic FP64 flops per walked segment
     # (the quantities that decide the path; the table part runs in double-float FP32):
@@ -336,6 +351,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"tf32x3": "f64 walk/tables, tf32x3 contraction, f32 factor, f64 refinement",
+                      "bf16x3": "f64 walk/tables, bf16x3 contraction, f32 factor, f64 refinement",
                       "fp32": "f64 walk/tables, f32 contraction and factor, f64 refinement",
                       "fp64": "f64"}[args.precision],
             "data": "synthetic",
@@ -355,6 +371,7 @@ def run_ours(args):
             "fp64_form_ms_per_step": ms_fp64,
             "mixed_vs_fp64_speedup": ms_fp64 / ms_step,
             "u_rel_diff_mixed_vs_fp64": rel_mix_fp64,
+            "other_tensor_core_form": other,
             "stages_ms": dict(zip(["mesh", "bins", "walk_tables", "contract", "load", "factor",
                                    "solve_refine"], [round(x, 4) for x in stages])),
             "stages_ms_fp64": dict(zip(["mesh", "bins", "walk_tables", "contract", "load",
@@ -423,7 +440,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched workload")
     ap.add_argument("--tol", type=float, default=1e-10,

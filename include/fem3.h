@@ -62,6 +62,10 @@ extern "C" {
                            FP64 iterative refinement against the FP64 tables */
 #define FEM3_FP32 2     /* FP64 tables rounded to FP32, FP32 contraction (CUDA cores);
                            FP32 Cholesky; FP64 iterative refinement */
+#define FEM3_BF16X3 3   /* FP64 tables split into BF16 hi/lo, 3 tensor-core products
+                           (tcgen05 kind::f16 with BF16 A/B, FP32 accumulate; about
+                           3 * 2^-16 relative per product); FP32 Cholesky; FP64 iterative
+                           refinement against the FP64 tables (more sweeps than TF32X3) */
 
 typedef struct fem3_mesh_s *fem3_mesh;
 
@@ -116,7 +120,7 @@ int fem3_mesh_info(fem3_mesh m, int64_t *n_dof, int64_t *n_gp, int32_t *dof_of_n
  *
  *   alpha    host float64[3], each in (1, 2] (alpha = 2 gives the P1 Laplacian).
  *   K        host float64[3], each > 0.
- *   precision  FEM3_FP64, FEM3_TF32X3 or FEM3_FP32 (see above).
+ *   precision  FEM3_FP64, FEM3_TF32X3, FEM3_BF16X3 or FEM3_FP32 (see above).
  *   A_out    device float64 [n_dof][n_dof] or NULL; when given, the assembled matrix
  *            (converted to FP64 for the mixed precisions) is written there.
  * The matrix and its precision stay in the handle for fem3_solve / fem3_adjoint.
@@ -134,9 +138,9 @@ int fem3_load(fem3_mesh m, const double *f, int nrhs, double *b, void *stream);
 /*
  * fem3_solve - u = A^{-1} M f for the last assembled A.
  *   FP64: FP64 Cholesky and triangular solves.
- *   TF32X3 / FP32: FP32 Cholesky of the mixed-precision A, then iterative refinement
- *   with residuals r = M f - A u where A u is applied in FP64 from the FP64 tables,
- *   until ||r||_2 <= tol ||M f||_2 for every column or max_iter corrections.
+ *   TF32X3 / BF16X3 / FP32: FP32 Cholesky of the mixed-precision A, then iterative
+ *   refinement with residuals r = M f - A u where A u is applied in FP64 from the FP64
+ *   tables, until ||r||_2 <= tol ||M f||_2 for every column or max_iter corrections.
  *   f         host or device float64 column-major [n_nodes][nrhs].
  *   u         device float64 column-major [n_dof][nrhs].
  *   iters_out host int or NULL: refinement steps taken (0 for FP64).

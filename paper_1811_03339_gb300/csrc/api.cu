@@ -240,7 +240,8 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
                   double *A_out, void *stream) {
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m || !alpha || !K) return set_error(FEM3_E_ARG, "null argument");
-    if (precision != FEM3_FP64 && precision != FEM3_TF32X3 && precision != FEM3_FP32)
+    if (precision != FEM3_FP64 && precision != FEM3_TF32X3 && precision != FEM3_FP32 &&
+        precision != FEM3_BF16X3)
         return set_error(FEM3_E_ARG, "unknown precision");
     for (int a = 0; a < 3; a++) {
         if (!(alpha[a] > 1.0 && alpha[a] <= 2.0))
@@ -262,8 +263,8 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
     m->ap_ready = false;
     FEM3_TRY(walk_tables(m, alpha));
     stage_begin(m, 3);
-    if (precision == FEM3_TF32X3)
-        FEM3_TRY(contract_tc(m));
+    if (precision == FEM3_TF32X3 || precision == FEM3_BF16X3)
+        FEM3_TRY(contract_tc(m, precision == FEM3_BF16X3));
     else
         FEM3_TRY(contract(m, precision));
     stage_end(m, 3);
@@ -274,7 +275,8 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
         } else {
             FEM3_TRY(f32_to_f64(m->A32, A_out, n * n, m->stream));
             note_launch(m);
-            if (precision == FEM3_TF32X3) {   // the tensor-core path fills the lower triangle
+            if (precision == FEM3_TF32X3 || precision == FEM3_BF16X3) {
+                // the tensor-core paths fill the lower triangle
                 FEM3_TRY(sym_from_lower(A_out, n, m->stream));
                 note_launch(m);
             }

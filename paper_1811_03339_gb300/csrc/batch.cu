@@ -161,7 +161,8 @@ int fem3_batch_run(fem3_batch hb, const double *alpha, const double *K, int prec
     Batch *b = reinterpret_cast<Batch *>(hb);
     if (!b || !alpha || !K || !f || !u || nrhs < 1 || nrhs > 16)
         return set_error(FEM3_E_ARG, "bad argument (1 <= nrhs <= 16)");
-    if (precision != FEM3_FP64 && precision != FEM3_TF32X3 && precision != FEM3_FP32)
+    if (precision != FEM3_FP64 && precision != FEM3_TF32X3 && precision != FEM3_FP32 &&
+        precision != FEM3_BF16X3)
         return set_error(FEM3_E_ARG, "unknown precision");
     const int n = (int)b->ms.size();
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
@@ -203,7 +204,8 @@ int fem3_batch_run(fem3_batch hb, const double *alpha, const double *K, int prec
         m->stream = b->streams[i % b->streams.size()];
         const int64_t nn = std::max<int64_t>(1, m->n_dof * nrhs);
         if (m->n_dof == 0) continue;
-        if (precision == FEM3_TF32X3) st = contract_tc(m);
+        if (precision == FEM3_TF32X3 || precision == FEM3_BF16X3)
+            st = contract_tc(m, precision == FEM3_BF16X3);
         else st = contract(m, precision);
         if (st != FEM3_OK) break;
         cudaError_t e = cudaMallocAsync((void **)&bv[i], sizeof(double) * nn, m->stream);

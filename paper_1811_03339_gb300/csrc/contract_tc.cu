@@ -1,19 +1,24 @@
-// Tensor-core contraction X_b = L_b^T W R_b (TF32 x 3 split products, FP32 accumulate)
-// on sm_103a: TMA loads with 128-byte swizzle, tcgen05.mma issued by one thread, the
-// accumulator in tensor memory, tcgen05.ld epilogue adding s K (X + X^T) into the lower
-// triangle of the FP32 matrix.  Section 2.1 element sum restricted, bin by bin, to the Section 2.3 template.
+// Tensor-core contraction X_b = L_b^T W R_b (TF32 x 3 or BF16 x 3 split products, FP32
+// accumulate) on sm_103a: TMA loads with 128-byte swizzle, tcgen05.mma issued by one
+// thread, the accumulator in tensor memory, tcgen05.ld epilogue adding s K (X + X^T) into
+// the lower triangle of the FP32 matrix.  Section 2.1 element sum restricted, bin by bin,
+// to the Section 2.3 template.
 //
-// Operands.  The FP64 tables of one axis are split into TF32 pairs v = hi + lo (each
-// rounded to TF32, cvt.rna) with the Gauss weights folded into R; they are stored as
-// four row-major FP32 arrays [n_tmpl rows][Kp] where row dof_off[b] + c is local dof c
-// of bin b and column k its k-th Gauss point (zero for k >= G_b).  The product
+// Operands.  The tables of one axis (FP64 accuracy, hi + lo FP32 pairs) are split into
+// pairs v = hi + lo of TF32 (cvt.rna) or BF16 (round to nearest) values, with the Gauss
+// weights folded into R; they are stored as four row-major arrays [n_tmpl rows][Kp] where
+// row dof_off[b] + c is local dof c of bin b and column k its k-th Gauss point (zero for
+// k >= G_b).  The product
 //   X = Lhi Rhi^T + Lhi Rlo^T + Llo Rhi^T
-// drops only lo*lo (relative 2^-22).
+// drops lo*lo and the rounding of lo: about 3 * 2^-22 relative per product for TF32
+// (11-bit significands), 3 * 2^-16 for BF16 (8-bit significands).
 //
 // Tiles.  One CTA computes the 128 x N block (N <= 256) of X for rows
 // [128 mt, 128 mt + 128) and columns [256 nt, 256 nt + N) of one bin.  K steps of
-// 32 Gauss points (128 bytes: one swizzle row) go through a 2-stage TMA pipeline.
+// 128 bytes (one swizzle row: 32 TF32 or 64 BF16 Gauss points) go through a 2-stage TMA
+// pipeline; each K step is four MMAs of 32 bytes (K = 8 TF32 or 16 BF16) per product.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -25,9 +30,10 @@ namespace fem3 {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 256, kBK = 32, kStages = 2;
-constexpr uint32_t kTileA = kBM * kBK * 4;     // 16 KB
-constexpr uint32_t kTileB = kBN * kBK * 4;     // 32 KB
+constexpr int kBM = 128, kBN = 256, kStages = 2;
+constexpr int kRowBytes = 128;                 // one K step: one 128-byte swizzle row
+constexpr uint32_t kTileA = kBM * kRowBytes;   // 16 KB
+constexpr uint32_t kTileB = kBN * kRowBytes;   // 32 KB
 constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;   // 96 KB
 constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int kWaitLimit = 1 << 22;
@@ -78,18 +84,28 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
     d |= (uint64_t)2 << 61;                            // 128-byte swizzle
     return d;
 }
-// kind::tf32 instruction descriptor: FP32 accumulate, TF32 A/B, both K-major
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+// instruction descriptor: FP32 accumulate (bits 4-5), A and B types (bits 7-9, 10-12:
+// TF32 = 2 for kind::tf32, BF16 = 1 for kind::f16), both K-major, N / 8, M / 16
+__host__ __device__ constexpr uint32_t idesc_mma(int M, int N, uint32_t ab_type) {
+    return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
-__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+template <bool BF16>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+    if constexpr (BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    }
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -114,19 +130,34 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(r);
 }
 
+// hi + lo split of the value x + x2 (|x2| <= ulp(x)) into the operand type
+template <class OT> struct Split;
+template <> struct Split<float> {
+    __device__ static void run(float x, float x2, float &h, float &l) {
+        h = tf32_rna(x);
+        l = tf32_rna((x - h) + x2);
+    }
+};
+template <> struct Split<__nv_bfloat16> {
+    __device__ static void run(float x, float x2, __nv_bfloat16 &h, __nv_bfloat16 &l) {
+        h = __float2bfloat16_rn(x);
+        l = __float2bfloat16_rn((x - __bfloat162float(h)) + x2);   // x - h is exact
+    }
+};
+
 // ------------------------------- split kernel ------------------------------------
 // One warp per template row (bin b, local dof c), lanes over the row's Gauss points:
 // coalesced reads of the table row (hi + lo pairs).  Writes the operator-apply operands L
 // and W R as hi + lo FP32 pairs in the table layout and, when Lhi is given, the
-// tensor-core operands (the TF32 pairs of the same values, zero past the bin's Gauss
-// points).  No FP64 arithmetic: W R is formed in double-float FP32 operations.
+// tensor-core operands (the TF32 or BF16 pairs of the same values, zero past the bin's
+// Gauss points).  No FP64 arithmetic: W R is formed in double-float FP32 operations.
+template <class OT>
 __global__ void __launch_bounds__(256) k_split_ops(
     const float2 *__restrict__ tabL, const float2 *__restrict__ tabR,
     const int32_t *__restrict__ row_bin, const int32_t *__restrict__ dof_off,
     const int32_t *__restrict__ gp_off, const double *__restrict__ w_slot,
     const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
-    int64_t n_rows, int Kp, float *Lhi, float *Llo, float *Rhi, float *Rlo, float2 *apL,
-    float2 *apR) {
+    int64_t n_rows, int Kp, OT *Lhi, OT *Llo, OT *Rhi, OT *Rlo, float2 *apL, float2 *apR) {
     const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n_rows) return;
@@ -137,7 +168,7 @@ __global__ void __launch_bounds__(256) k_split_ops(
     const int64_t dst = row * (int64_t)Kp;
     const int kend = Lhi ? Kp : G;
     for (int k = lane; k < kend; k += 32) {
-        float lh = 0.f, ll = 0.f, rh = 0.f, rl = 0.f;
+        OT lh = OT(0.f), ll = OT(0.f), rh = OT(0.f), rl = OT(0.f);
         if (k < G) {
             const float2 lp = tabL[src + k], rp = tabR[src + k];
             const float a = lp.x, a2 = lp.y, r1 = rp.x, r2 = rp.y;
@@ -149,10 +180,8 @@ __global__ void __launch_bounds__(256) k_split_ops(
             apL[src + k] = make_float2(a, a2);
             apR[src + k] = make_float2(wr, wr2);
             if (Lhi) {
-                lh = tf32_rna(a);
-                ll = tf32_rna((a - lh) + a2);
-                rh = tf32_rna(wr);
-                rl = tf32_rna((wr - rh) + wr2);
+                Split<OT>::run(a, a2, lh, ll);
+                Split<OT>::run(wr, wr2, rh, rl);
             }
         }
         if (Lhi) {
@@ -169,6 +198,7 @@ struct TcWork {
     int bin, mt, nt, pad;
 };
 
+template <bool BF16>
 __global__ void __launch_bounds__(128, 1) k_contract_tc(
     const __grid_constant__ CUtensorMap mLhi, const __grid_constant__ CUtensorMap mLlo,
     const __grid_constant__ CUtensorMap mRhi, const __grid_constant__ CUtensorMap mRlo,
@@ -190,6 +220,7 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(
     const int G = gp_off[bin + 1] - gp_off[bin];
     const int nvalid = min(kBN, D - nt * kBN);          // columns of this tile
     const int N = (nvalid + 15) & ~15;                  // MMA N: multiple of 16, <= 256
+    constexpr int kBK = BF16 ? 64 : 32;                 // Gauss points per K step
     const int nk = (G + kBK - 1) / kBK;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -239,7 +270,7 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(
         }
     } else if (warp == 1 && lane == 0 && nk > 0) {
         // MMA issuer
-        const uint32_t idesc = idesc_tf32(kBM, N);
+        const uint32_t idesc = idesc_mma(kBM, N, BF16 ? 1u : 2u);
         for (int k = 0; k < nk; k++) {
             const int s = k % kStages;
             if (!mbar_wait(full0 + 8 * s, (k / kStages) & 1)) { s_fail = 1; break; }
@@ -247,12 +278,12 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(
             const uint32_t st = smem_u32(base + s * kStageBytes);
             const uint32_t aH = st, aL = st + kTileA, bH = st + 2 * kTileA, bL = st + 2 * kTileA + kTileB;
 #pragma unroll
-            for (int ks = 0; ks < kBK / 8; ks++) {      // 8 TF32 = 32 bytes per MMA K step
+            for (int ks = 0; ks < kRowBytes / 32; ks++) {   // 32 bytes per MMA K step
                 const uint32_t off = ks * 32;
                 const uint32_t acc = (k > 0 || ks > 0) ? 1u : 0u;
-                umma_tf32(tmem, umma_desc_sw128(aH + off), umma_desc_sw128(bH + off), idesc, acc);
-                umma_tf32(tmem, umma_desc_sw128(aH + off), umma_desc_sw128(bL + off), idesc, 1u);
-                umma_tf32(tmem, umma_desc_sw128(aL + off), umma_desc_sw128(bH + off), idesc, 1u);
+                umma<BF16>(tmem, umma_desc_sw128(aH + off), umma_desc_sw128(bH + off), idesc, acc);
+                umma<BF16>(tmem, umma_desc_sw128(aH + off), umma_desc_sw128(bL + off), idesc, 1u);
+                umma<BF16>(tmem, umma_desc_sw128(aL + off), umma_desc_sw128(bH + off), idesc, 1u);
             }
             umma_commit(empty0 + 8 * s);   // frees the stage when these MMAs finish
         }
@@ -307,14 +338,18 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-int make_map(CUtensorMap *map, float *base, int64_t rows, int Kp) {
+// [rows][Kp] operand of 4-byte (TF32) or 2-byte (BF16) elements; boxes of one 128-byte
+// swizzle row by 128 rows
+int make_map(CUtensorMap *map, void *base, int64_t rows, int Kp, bool bf16) {
     auto enc = get_encode();
     if (!enc) return set_error(FEM3_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+    const int esz = bf16 ? 2 : 4;
     cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)kBM};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+    CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                     2, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FEM3_E_CUDA, "cuTensorMapEncodeTiled failed");
@@ -331,10 +366,12 @@ static int tc_prepare(Mesh *m) {
         AxisBins &B = m->bins[axis];
         int maxG = 0;
         for (int b = 0; b < B.n_bins; b++) maxG = std::max(maxG, B.h_gp_off[b + 1] - B.h_gp_off[b]);
-        B.tc_Kp = std::max(kBK, (maxG + kBK - 1) / kBK * kBK);
+        B.tc_maxG = maxG;
+        // room for either operand type: Kp rounded to 64 Gauss points, 4 bytes each
         const int64_t rows = std::max<int64_t>(1, B.n_tmpl);
+        const int64_t kp_max = std::max(64, (maxG + 63) / 64 * 64);
         for (int q = 0; q < 4; q++)
-            FEM3_TRY(dev_alloc_t(m, &B.tc_op[q], rows * B.tc_Kp));
+            FEM3_TRY(dev_alloc(m, &B.tc_op[q], sizeof(float) * rows * kp_max));
         std::vector<int4> &work = B.h_tc_work;
         work.clear();
         for (int b = 0; b < B.n_bins; b++) {
@@ -350,13 +387,15 @@ static int tc_prepare(Mesh *m) {
             FEM3_CUDA(cudaMemcpyAsync(B.tc_work, work.data(), sizeof(int4) * work.size(),
                                       cudaMemcpyHostToDevice, s));
     }
-    FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kSmemBytes));
+    FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+    FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
     m->tc_ready = true;
     return FEM3_OK;
 }
 
-int contract_tc(Mesh *m) {
+int contract_tc(Mesh *m, bool bf16) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
     FEM3_TRY(tc_prepare(m));
@@ -371,16 +410,33 @@ int contract_tc(Mesh *m) {
         }
         if (!B.tc_n_work) continue;
         FEM3_TRY(ap_alloc(m, axis));
-        k_split_ops<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
-            m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot, B.tab_off,
-            B.tab_ld, B.n_tmpl, B.tc_Kp, B.tc_op[0], B.tc_op[1], B.tc_op[2], B.tc_op[3], B.ap_L,
-            B.ap_R);
+        const int kbk = bf16 ? 64 : 32;   // Gauss points per 128-byte swizzle row
+        const int Kp = std::max(kbk, (B.tc_maxG + kbk - 1) / kbk * kbk);
+        const unsigned grid = (unsigned)((B.n_tmpl + 7) / 8);
+        if (bf16) {
+            __nv_bfloat16 *op[4];
+            for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<__nv_bfloat16 *>(B.tc_op[q]);
+            k_split_ops<__nv_bfloat16><<<grid, 256, 0, s>>>(
+                m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
+                B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1], op[2], op[3], B.ap_L, B.ap_R);
+        } else {
+            float *op[4];
+            for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<float *>(B.tc_op[q]);
+            k_split_ops<float><<<grid, 256, 0, s>>>(
+                m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
+                B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1], op[2], op[3], B.ap_L, B.ap_R);
+        }
         note_launch(m);
         CUtensorMap maps[4];
-        for (int q = 0; q < 4; q++) FEM3_TRY(make_map(&maps[q], B.tc_op[q], B.n_tmpl, B.tc_Kp));
-        k_contract_tc<<<B.tc_n_work, 128, kSmemBytes, s>>>(
-            maps[0], maps[1], maps[2], maps[3], B.tc_work, B.dof_off, B.dof_idx, B.gp_off,
-            (float)m->sK[axis], m->A32, n, m->err);
+        for (int q = 0; q < 4; q++) FEM3_TRY(make_map(&maps[q], B.tc_op[q], B.n_tmpl, Kp, bf16));
+        if (bf16)
+            k_contract_tc<true><<<B.tc_n_work, 128, kSmemBytes, s>>>(
+                maps[0], maps[1], maps[2], maps[3], B.tc_work, B.dof_off, B.dof_idx, B.gp_off,
+                (float)m->sK[axis], m->A32, n, m->err);
+        else
+            k_contract_tc<false><<<B.tc_n_work, 128, kSmemBytes, s>>>(
+                maps[0], maps[1], maps[2], maps[3], B.tc_work, B.dof_off, B.dof_idx, B.gp_off,
+                (float)m->sK[axis], m->A32, n, m->err);
         note_launch(m);
     }
     m->contract_flops = flops;
@@ -406,7 +462,7 @@ int ap_prepare(Mesh *m) {
         AxisBins &B = m->bins[axis];
         if (B.n_tmpl == 0) continue;
         FEM3_TRY(ap_alloc(m, axis));
-        k_split_ops<<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
+        k_split_ops<float><<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
             m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot, B.tab_off,
             B.tab_ld, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_L, B.ap_R);
         note_launch(m);

@@ -71,10 +71,11 @@ struct AxisBins {
     int max_dof = 0, max_gp = 0;
     int4 *work = nullptr;        // contraction work items (bin, t1, t2, 0)
     int n_work = 0;
-    // tensor-core contraction operands: TF32 hi/lo of L and of W R, [n_tmpl][tc_Kp]
-    float *tc_op[4] = {nullptr, nullptr, nullptr, nullptr};
+    // tensor-core contraction operands: TF32 or BF16 hi/lo of L and of W R, [n_tmpl][Kp]
+    // (Kp = tc_maxG rounded to one 128-byte row of the operand type)
+    void *tc_op[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t *row_bin = nullptr;  // [n_tmpl] template row -> bin
-    int tc_Kp = 0;
+    int tc_maxG = 0;             // largest Gauss-point count of a bin
     int4 *tc_work = nullptr;     // (bin, m-tile, n-tile, 0)
     // operator-apply operands in the table layout: L and W R as hi + lo FP32 pairs
     float2 *ap_L = nullptr, *ap_R = nullptr;
@@ -201,7 +202,7 @@ int walk_paths(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, int ca
                int32_t *tet_out, double *r0, double *r1, int32_t *nseg);
 int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double *rows);
 int contract(Mesh *m, int precision);
-int contract_tc(Mesh *m);
+int contract_tc(Mesh *m, bool bf16);   // TF32 x 3 (bf16 = false) or BF16 x 3
 int load_vector(Mesh *m, const double *f_d, int nrhs, double *b_d);
 int load_vector_T(Mesh *m, const double *lam_d, double *out_d);
 int factor(Mesh *m);

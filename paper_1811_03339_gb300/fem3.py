@@ -20,7 +20,7 @@ FEM3_OK = 0
 FEM3_E_ARG, FEM3_E_MESH, FEM3_E_WALK, FEM3_E_NOT_SPD = -1, -2, -3, -4
 FEM3_E_NO_CONVERGE, FEM3_E_CUDA, FEM3_E_OOM, FEM3_E_STATE, FEM3_E_TEMPLATE = -5, -6, -7, -8, -9
 
-PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2}
+PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2, "bf16x3": 3}
 
 # every entry point declared in include/fem3.h
 SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_load", "fem3_solve",

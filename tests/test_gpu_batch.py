@@ -25,7 +25,7 @@ def _batch_case(seed=0):
     return meshes, alpha, K, fs
 
 
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "fp32", "bf16x3"])
 def test_batch_matches_single_mesh_and_oracle(precision):
     meshes, alpha, K, fs = _batch_case()
     b = fem3.Batch([(m.verts, m.tets) for m in meshes])
