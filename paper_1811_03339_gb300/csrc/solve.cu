@@ -1300,21 +1300,67 @@ int factor(Mesh *m) {
 
 // Fused operator apply, one CTA per transverse bin, in double-float arithmetic on the FP32
 // pipes.  With R~ = W R (split once per assembly, see k_split_ops), A u restricted to
-// the bin is L^T (R~ u) + R~^T (L u).  For each chunk of up to 128 Gauss points, phase 1
-// forms yR = R~ u_b and yL = L u_b (two threads per Gauss point: one vector split over the
-// template rows, or eight vectors split 4 + 4; u_b staged in shared memory as hi + lo
-// pairs), phase 2 adds s K (L^T yR + R~^T yL) to Au (warp per template row, lanes over the
-// chunk's Gauss points, then a butterfly over the lanes).  Phase 2 reads the chunk's
-// operands right after phase 1 did, so they come from cache.  Every product is exact up
-// to 2^-48 relative and sums carry their rounding errors (df_fma), so Au matches an FP64
-// evaluation to a few units in 2^-48.  NR = 1: u plain; NR = 8: u interleaved [dof][8].
+// the bin is L^T (R~ u) + R~^T (L u).  The bin's Gauss points go in chunks of 32; for each
+// chunk the L and R~ columns of up to RM template rows are staged in shared memory
+// (cp.async 16-byte copies, all in flight together, zero-filled past the bin's Gauss points;
+// rows of 34 pairs, 272 bytes) with u_b as hi + lo pairs.  Phase 1
+// forms yR = R~ u_b and yL = L u_b (warp w sums rows w, w + 8, ..., lane = Gauss point; the
+// eight partial sums are added in shared memory); phase 2 adds s K (L^T yR + R~^T yL) to Au,
+// one thread per template row, from the same staged rows (a bin with more than RM rows
+// stages its row chunks again for phase 2, from L2).  Every product is exact up to 2^-48
+// relative and sums carry their rounding errors (df_fma), so Au matches an FP64 evaluation to
+// a few units in 2^-48.  The kernel has no FP64 arithmetic: s K z is formed in double-float
+// FP32 operations and its two parts go to Au as exact FP64 values (bit assembly) through
+// FP64 atomics.  NR = 1: u plain; NR = 8: u interleaved [dof][8].
 constexpr int kApplyThreads = 256;
-constexpr int kApplyGC = 128;   // Gauss points per chunk (two threads each)
-constexpr int kApplyUC = 512;   // template rows of u staged per pass
+constexpr int kApplyGC = 32;                  // Gauss points per chunk
+constexpr int kApplyStride = kApplyGC + 2;    // staged row, float2 units: 272 B, 16-B aligned
+template <int NR> __host__ __device__ constexpr int apply_rows() { return NR == 1 ? 160 : 128; }
 
 template <int NR>
 constexpr size_t apply_bin_smem() {
-    return (size_t)(kApplyUC * NR + 2 * kApplyGC * NR + 2 * kApplyGC) * sizeof(float2);
+    return (size_t)(2 * apply_rows<NR>() * kApplyStride + apply_rows<NR>() * NR +
+                    2 * 8 * kApplyGC * NR + 2 * kApplyGC * NR) *
+           sizeof(float2);
+}
+
+// exact FP64 value of a normal FP32 number (zero and subnormals give 0), by bit assembly:
+// exponent rebiased by 1023 - 127, significand moved to the top of the 52-bit field
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double(e == 0u ? 0ll : (long long)d);
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+// stage rows [r0, r0 + rn) of the chunk's L and R~ columns [gc0, gc0 + 32): one 16-byte
+// copy per (row, pair of Gauss points), the part past the bin's G Gauss points zero-filled
+// (and not read: entries past G in a table row are padding).  The caller waits
+// (cp.async.wait_all) and synchronises.
+__device__ __forceinline__ void apply_stage_ops(const float2 *__restrict__ TL,
+                                                const float2 *__restrict__ TR, int ld, int G,
+                                                int gc0, int r0, int rn, float2 *Ls,
+                                                float2 *Rs) {
+    for (int e = threadIdx.x; e < rn * 16; e += kApplyThreads) {
+        const int r = e >> 4, q = e & 15, g = gc0 + 2 * q;
+        const int nb = g + 1 < G ? 16 : (g < G ? 8 : 0);
+        const int64_t o = (int64_t)(r0 + r) * ld + (nb ? g : 0);   // in the row when nb = 0
+        cp_async16(Ls + r * kApplyStride + 2 * q, TL + o, nb);
+        cp_async16(Rs + r * kApplyStride + 2 * q, TR + o, nb);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 template <int NR>
@@ -1322,113 +1368,110 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(
     const float2 *__restrict__ apL, const float2 *__restrict__ apR,
     const int32_t *__restrict__ gp_off, const int32_t *__restrict__ dof_off,
     const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
-    const int32_t *__restrict__ tab_ld, const double *__restrict__ u, int nv, double sK,
-    double *Au, int64_t ldA) {
-    constexpr int NH = NR == 1 ? 1 : NR / 2;   // vectors per thread in phase 1
+    const int32_t *__restrict__ tab_ld, const double *__restrict__ u, int nv, float sKh,
+    float sKl, double *Au, int64_t ldA) {
+    constexpr int RM = apply_rows<NR>();
     extern __shared__ __align__(16) float2 sm_apply[];
-    float2 *us = sm_apply;                  // [UC][NR]
-    float2 *yls = us + kApplyUC * NR;       // [GC][NR]  L u
-    float2 *yrs = yls + kApplyGC * NR;      // [GC][NR]  R~ u
-    float2 *half = yrs + kApplyGC * NR;     // [2][GC]: second half's partial sums (NR = 1)
+    float2 *Ls = sm_apply;                       // [RM][33]
+    float2 *Rs = Ls + RM * kApplyStride;         // [RM][33]
+    float2 *us = Rs + RM * kApplyStride;         // [RM][NR]
+    float2 *pL = us + RM * NR;                   // [8][32][NR] phase-1 partial sums, L u
+    float2 *pR = pL + 8 * kApplyGC * NR;         // [8][32][NR] R~ u
+    float2 *yL = pR + 8 * kApplyGC * NR;         // [32][NR]
+    float2 *yR = yL + kApplyGC * NR;             // [32][NR]
     const int b = blockIdx.x;
     const int d0 = dof_off[b], D = dof_off[b + 1] - d0;
-    const int g0 = gp_off[b], G = gp_off[b + 1] - g0, ld = tab_ld[b];
+    const int G = gp_off[b + 1] - gp_off[b], ld = tab_ld[b];
     if (D == 0 || G == 0) return;
     const float2 *TL = apL + tab_off[b], *TR = apR + tab_off[b];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int gi = tid & (kApplyGC - 1), h = tid >> 7;
     for (int gc0 = 0; gc0 < G; gc0 += kApplyGC) {
         const int gn = min(kApplyGC, G - gc0);
-        float lh[NH], ll[NH], rh[NH], rl[NH];
+        // ---- phase 1: lane = Gauss point gc0 + lane, warp = row slice ----
+        float lh[NR], ll[NR], rh[NR], rl[NR];
 #pragma unroll
-        for (int v = 0; v < NH; v++) { lh[v] = 0.f; ll[v] = 0.f; rh[v] = 0.f; rl[v] = 0.f; }
-        for (int cc0 = 0; cc0 < D; cc0 += kApplyUC) {
-            const int cn = min(kApplyUC, D - cc0);
-            __syncthreads();   // earlier readers of us and of the y buffers are done
-            for (int e = tid; e < cn * NR; e += kApplyThreads) {
-                const int c = e / NR, v = e - c * NR;
-                const int64_t dof = dof_idx[d0 + cc0 + c];
+        for (int v = 0; v < NR; v++) { lh[v] = 0.f; ll[v] = 0.f; rh[v] = 0.f; rl[v] = 0.f; }
+        int rc_last = 0;
+        for (int rc0 = 0; rc0 < D; rc0 += RM) {
+            const int rn = min(RM, D - rc0);
+            __syncthreads();   // earlier readers of the staged rows are done
+            apply_stage_ops(TL, TR, ld, G, gc0, rc0, rn, Ls, Rs);
+            for (int e = tid; e < rn * NR; e += kApplyThreads) {
+                const int r = e / NR, v = e - r * NR;
+                const int64_t dof = dof_idx[d0 + rc0 + r];
                 float a, a2;
                 f64_split(NR == 1 ? u[dof] : u[dof * 8 + v], a, a2);
                 us[e] = make_float2(a, a2);
             }
+            cp_async_wait_all();
             __syncthreads();
-            if (gi < gn) {
-                const float2 *Lc = TL + (int64_t)cc0 * ld + gc0 + gi;
-                const float2 *Rc = TR + (int64_t)cc0 * ld + gc0 + gi;
-                if constexpr (NR == 1) {
-#pragma unroll 4
-                    for (int c = h; c < cn; c += 2) {
-                        const float2 lv = Lc[(int64_t)c * ld], rv = Rc[(int64_t)c * ld];
-                        const float2 uv = us[c];
-                        df_fma(lv.x, lv.y, uv.x, uv.y, lh[0], ll[0]);
-                        df_fma(rv.x, rv.y, uv.x, uv.y, rh[0], rl[0]);
-                    }
-                } else {
-#pragma unroll 2
-                    for (int c = 0; c < cn; c++) {
-                        const float2 lv = Lc[(int64_t)c * ld], rv = Rc[(int64_t)c * ld];
-#pragma unroll
-                        for (int k = 0; k < NH; k++) {
-                            const float2 uv = us[c * NR + h * NH + k];
-                            df_fma(lv.x, lv.y, uv.x, uv.y, lh[k], ll[k]);
-                            df_fma(rv.x, rv.y, uv.x, uv.y, rh[k], rl[k]);
-                        }
-                    }
-                }
-            }
-        }
-        if constexpr (NR == 1) {
-            if (h == 1 && gi < gn) {
-                half[gi] = make_float2(lh[0], ll[0]);
-                half[kApplyGC + gi] = make_float2(rh[0], rl[0]);
-            }
-            __syncthreads();
-            if (h == 0 && gi < gn) {
-                const float2 ol = half[gi], orr = half[kApplyGC + gi];
-                df_add(ol.x, ol.y, lh[0], ll[0]);
-                df_add(orr.x, orr.y, rh[0], rl[0]);
-                yls[gi] = make_float2(lh[0], ll[0]);
-                yrs[gi] = make_float2(rh[0], rl[0]);
-            }
-        } else {
-            if (gi < gn) {
-#pragma unroll
-                for (int k = 0; k < NH; k++) {
-                    yls[gi * NR + h * NH + k] = make_float2(lh[k], ll[k]);
-                    yrs[gi * NR + h * NH + k] = make_float2(rh[k], rl[k]);
-                }
-            }
-        }
-        __syncthreads();
-        for (int c = warp; c < D; c += kApplyThreads / 32) {
-            const float2 *Lr = TL + (int64_t)c * ld + gc0, *Rr = TR + (int64_t)c * ld + gc0;
-            float zh[NR], zl[NR];
-#pragma unroll
-            for (int v = 0; v < NR; v++) { zh[v] = 0.f; zl[v] = 0.f; }
-            for (int r = lane; r < gn; r += 32) {
-                const float2 lv = Lr[r], rv = Rr[r];
+            for (int r = warp; r < rn; r += kApplyThreads / 32) {
+                const float2 lv = Ls[r * kApplyStride + lane], rv = Rs[r * kApplyStride + lane];
 #pragma unroll
                 for (int v = 0; v < NR; v++) {
-                    const float2 a = yrs[r * NR + v], q = yls[r * NR + v];
-                    df_fma(lv.x, lv.y, a.x, a.y, zh[v], zl[v]);
-                    df_fma(rv.x, rv.y, q.x, q.y, zh[v], zl[v]);
+                    const float2 uv = us[r * NR + v];
+                    df_fma(lv.x, lv.y, uv.x, uv.y, lh[v], ll[v]);
+                    df_fma(rv.x, rv.y, uv.x, uv.y, rh[v], rl[v]);
                 }
             }
-            // butterfly: every lane ends with all totals; lane v stores total v
+            rc_last = rc0;
+        }
 #pragma unroll
-            for (int v = 0; v < NR; v++)
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, zh[v], o);
-                    const float ol = __shfl_xor_sync(0xffffffffu, zl[v], o);
-                    df_add(oh, ol, zh[v], zl[v]);
+        for (int v = 0; v < NR; v++) {
+            pL[(warp * kApplyGC + lane) * NR + v] = make_float2(lh[v], ll[v]);
+            pR[(warp * kApplyGC + lane) * NR + v] = make_float2(rh[v], rl[v]);
+        }
+        __syncthreads();
+        for (int e = tid; e < kApplyGC * NR; e += kApplyThreads) {
+            float2 a = pL[e], c = pR[e];
+            float ah = a.x, al = a.y, ch = c.x, cl = c.y;
+#pragma unroll
+            for (int w = 1; w < 8; w++) {
+                const float2 x = pL[w * kApplyGC * NR + e], z = pR[w * kApplyGC * NR + e];
+                df_add(x.x, x.y, ah, al);
+                df_add(z.x, z.y, ch, cl);
+            }
+            yL[e] = make_float2(ah, al);
+            yR[e] = make_float2(ch, cl);
+        }
+        __syncthreads();
+        // ---- phase 2: thread per template row; the last staged row chunk first ----
+        for (int pass = 0; pass * RM < D; pass++) {
+            const int rc0 = pass == 0 ? rc_last : (pass - 1) * RM;   // rc_last: the last chunk
+            const int rn = min(RM, D - rc0);
+            if (pass > 0) {
+                __syncthreads();
+                apply_stage_ops(TL, TR, ld, G, gc0, rc0, rn, Ls, Rs);
+                cp_async_wait_all();
+                __syncthreads();
+            }
+            for (int r = tid; r < rn; r += kApplyThreads) {
+                float zh[NR], zl[NR];
+#pragma unroll
+                for (int v = 0; v < NR; v++) { zh[v] = 0.f; zl[v] = 0.f; }
+                const float4 *Lr = reinterpret_cast<const float4 *>(Ls + r * kApplyStride);
+                const float4 *Rr = reinterpret_cast<const float4 *>(Rs + r * kApplyStride);
+                for (int g2 = 0; 2 * g2 < gn; g2++) {   // two Gauss points per 16-byte read
+                    const float4 lv = Lr[g2], rv = Rr[g2];   // zero past G
+#pragma unroll
+                    for (int v = 0; v < NR; v++) {
+                        const float2 a0 = yR[2 * g2 * NR + v], q0 = yL[2 * g2 * NR + v];
+                        const float2 a1 = yR[(2 * g2 + 1) * NR + v], q1 = yL[(2 * g2 + 1) * NR + v];
+                        df_fma(lv.x, lv.y, a0.x, a0.y, zh[v], zl[v]);
+                        df_fma(rv.x, rv.y, q0.x, q0.y, zh[v], zl[v]);
+                        df_fma(lv.z, lv.w, a1.x, a1.y, zh[v], zl[v]);
+                        df_fma(rv.z, rv.w, q1.x, q1.y, zh[v], zl[v]);
+                    }
                 }
-            if (lane < NR && lane < nv) {
-                float th = zh[0], tl = zl[0];
+                const int64_t dof = dof_idx[d0 + rc0 + r];
 #pragma unroll
-                for (int v = 1; v < NR; v++)
-                    if (lane == v) { th = zh[v]; tl = zl[v]; }
-                atomicAdd(&Au[(int64_t)lane * ldA + dof_idx[d0 + c]], sK * ((double)th + (double)tl));
+                for (int v = 0; v < NR; v++) {
+                    if (v >= nv) break;
+                    float ph, pl;
+                    df_mul(zh[v], zl[v], sKh, sKl, ph, pl);
+                    atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(ph));
+                    atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(pl));
+                }
             }
         }
     }
@@ -1442,6 +1485,8 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
     FEM3_CUDA(cudaMemsetAsync(Au_d, 0, sizeof(double) * n * nv, s));
     static bool attr = false;
     if (!attr) {
+        FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)apply_bin_smem<1>()));
         FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)apply_bin_smem<8>()));
         attr = true;
@@ -1458,14 +1503,15 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
         for (int axis = 0; axis < 3; axis++) {
             AxisBins &B = m->bins[axis];
             if (B.n_tmpl == 0 || B.n_bins == 0) continue;
+            const float skh = (float)m->sK[axis], skl = (float)(m->sK[axis] - (double)skh);
             if (nv == 1) {
                 k_apply_bin<1><<<B.n_bins, kApplyThreads, apply_bin_smem<1>(), s>>>(
                     B.ap_L, B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, u_d, 1,
-                    m->sK[axis], Au_d, n);
+                    skh, skl, Au_d, n);
             } else {
                 k_apply_bin<8><<<B.n_bins, kApplyThreads, apply_bin_smem<8>(), s>>>(
                     B.ap_L, B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, u8, cnt,
-                    m->sK[axis], Au_d + v0 * n, n);
+                    skh, skl, Au_d + v0 * n, n);
             }
             note_launch(m);
         }

@@ -247,14 +247,15 @@ def test_full_size_cube16_fp64_matrix():
 
 
 def test_full_size_parallelepiped24_sampled():
-    """24^3 parallelepiped (82,944 tets, 12,167 dofs): sampled paths and table rows
-    against the oracle, chord ends in closed form, symmetry and residual at full size."""
+    """24^3 parallelepiped (82,944 tets, 12,167 dofs) in the form its configuration names
+    (BF16 split products, FP32 accumulation, FP64 refinement): sampled paths and table rows
+    against the oracle, symmetry and the refined residual at full size."""
     w = inputs.PARALLELEPIPED24
     mesh = inputs.workload_mesh("parallelepiped24")
     o = oracle.Oracle.from_mesh(mesh)
     m = fem3.Mesh(mesh.verts, mesh.tets)
     alpha, K = w["alpha"], w["K"]
-    A = m.assemble(alpha, K, "tf32x3", return_matrix=True)
+    A = m.assemble(alpha, K, "bf16x3", return_matrix=True)
     m.sync()
     rng = np.random.default_rng(7)
     gps = np.sort(rng.choice(o.n_gp, 200, replace=False))
