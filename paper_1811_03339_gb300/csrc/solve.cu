@@ -1363,14 +1363,32 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// one axis of the apply: its bins' operands and s K as an FP32 pair
+struct ApplyAxis {
+    const float2 *apL, *apR;
+    const int32_t *gp_off, *dof_off, *dof_idx, *tab_ld;
+    const int64_t *tab_off;
+    float sKh, sKl;
+    int n_bins;
+};
+struct ApplyAxes {
+    ApplyAxis a[3];
+};
+
+// grid: the bins of the three axes (block x -> axis, bin)
 template <int NR>
-__global__ void __launch_bounds__(kApplyThreads) k_apply_bin(
-    const float2 *__restrict__ apL, const float2 *__restrict__ apR,
-    const int32_t *__restrict__ gp_off, const int32_t *__restrict__ dof_off,
-    const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
-    const int32_t *__restrict__ tab_ld, const double *__restrict__ u, int nv, float sKh,
-    float sKl, double *Au, int64_t ldA) {
+__global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_constant__ ApplyAxes P,
+                                                             const double *__restrict__ u, int nv,
+                                                             double *Au, int64_t ldA) {
     constexpr int RM = apply_rows<NR>();
+    int b = blockIdx.x, axis = 0;
+    while (axis < 2 && b >= P.a[axis].n_bins) b -= P.a[axis++].n_bins;
+    const ApplyAxis &X = P.a[axis];
+    const float2 *__restrict__ apL = X.apL, *__restrict__ apR = X.apR;
+    const int32_t *__restrict__ gp_off = X.gp_off, *__restrict__ dof_off = X.dof_off,
+                  *__restrict__ dof_idx = X.dof_idx, *__restrict__ tab_ld = X.tab_ld;
+    const int64_t *__restrict__ tab_off = X.tab_off;
+    const float sKh = X.sKh, sKl = X.sKl;
     extern __shared__ __align__(16) float2 sm_apply[];
     float2 *Ls = sm_apply;                       // [RM][33]
     float2 *Rs = Ls + RM * kApplyStride;         // [RM][33]
@@ -1379,7 +1397,6 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(
     float2 *pR = pL + 8 * kApplyGC * NR;         // [8][32][NR] R~ u
     float2 *yL = pR + 8 * kApplyGC * NR;         // [32][NR]
     float2 *yR = yL + kApplyGC * NR;             // [32][NR]
-    const int b = blockIdx.x;
     const int d0 = dof_off[b], D = dof_off[b + 1] - d0;
     const int G = gp_off[b + 1] - gp_off[b], ld = tab_ld[b];
     if (D == 0 || G == 0) return;
@@ -1500,19 +1517,23 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
             k_interleave8<<<g256(8 * n), 256, 0, s>>>(u_d + v0 * n, n, cnt, u8);
             note_launch(m);
         }
+        ApplyAxes P;
+        int64_t nblk = 0;
         for (int axis = 0; axis < 3; axis++) {
             AxisBins &B = m->bins[axis];
-            if (B.n_tmpl == 0 || B.n_bins == 0) continue;
+            const bool on = B.n_tmpl > 0 && B.n_bins > 0;
             const float skh = (float)m->sK[axis], skl = (float)(m->sK[axis] - (double)skh);
-            if (nv == 1) {
-                k_apply_bin<1><<<B.n_bins, kApplyThreads, apply_bin_smem<1>(), s>>>(
-                    B.ap_L, B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, u_d, 1,
-                    skh, skl, Au_d, n);
-            } else {
-                k_apply_bin<8><<<B.n_bins, kApplyThreads, apply_bin_smem<8>(), s>>>(
-                    B.ap_L, B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_off, B.tab_ld, u8, cnt,
-                    skh, skl, Au_d + v0 * n, n);
-            }
+            P.a[axis] = ApplyAxis{B.ap_L, B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_ld,
+                                  B.tab_off, skh, skl, on ? B.n_bins : 0};
+            nblk += on ? B.n_bins : 0;
+        }
+        if (nblk > 0) {
+            if (nv == 1)
+                k_apply_bin<1><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<1>(), s>>>(
+                    P, u_d, 1, Au_d, n);
+            else
+                k_apply_bin<8><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<8>(), s>>>(
+                    P, u8, cnt, Au_d + v0 * n, n);
             note_launch(m);
         }
     }
