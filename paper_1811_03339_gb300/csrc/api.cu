@@ -4,7 +4,9 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "fem3_impl.cuh"
 
@@ -22,7 +24,12 @@ int cuda_error(cudaError_t e, const char *where) {
     return set_error(code, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-int dev_alloc(Mesh *m, void **p, size_t bytes) {
+// Device memory of a mesh lives until the mesh is freed.  Requests up to kArenaMax bytes
+// are carved (256-byte aligned) from 64 MB stream-ordered chunks, so a mesh makes a few
+// allocator calls instead of one per array; larger ones get their own allocation.
+constexpr size_t kArenaChunk = size_t(64) << 20, kArenaMax = size_t(16) << 20;
+
+static int raw_alloc(Mesh *m, void **p, size_t bytes) {
     *p = nullptr;
     cudaError_t e = cudaMallocAsync(p, bytes, m->stream);
     if (e != cudaSuccess) {
@@ -33,9 +40,49 @@ int dev_alloc(Mesh *m, void **p, size_t bytes) {
     return FEM3_OK;
 }
 
+int dev_alloc(Mesh *m, void **p, size_t bytes) {
+    bytes = (std::max<size_t>(bytes, 1) + 255) & ~size_t(255);
+    if (bytes > kArenaMax) return raw_alloc(m, p, bytes);
+    if (!m->arena || m->arena_used + bytes > m->arena_size) {
+        void *c;
+        FEM3_TRY(raw_alloc(m, &c, kArenaChunk));
+        m->arena = static_cast<char *>(c);
+        m->arena_size = kArenaChunk;
+        m->arena_used = 0;
+    }
+    *p = m->arena + m->arena_used;
+    m->arena_used += bytes;
+    return FEM3_OK;
+}
+
 void dev_free_all(Mesh *m) {
     for (void *p : m->allocs) cudaFreeAsync(p, m->stream);
     m->allocs.clear();
+    m->arena = nullptr;
+    m->arena_size = m->arena_used = 0;
+}
+
+// Pinned 1 KB host blocks for the small device-to-host reads of a mesh, kept for the
+// life of the process (pinned allocation and release are slow and release synchronises).
+static std::mutex g_pin_mu;
+static std::vector<double *> g_pin_free;
+static double *pinned_block() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        double *c = nullptr;
+        if (cudaMallocHost(&c, 64 * 128 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int i = 0; i < 64; i++) g_pin_free.push_back(c + 128 * i);
+    }
+    double *p = g_pin_free.back();
+    g_pin_free.pop_back();
+    return p;
+}
+static void pinned_release(double *p) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
 }
 
 bool is_device_ptr(const void *p) {
@@ -135,7 +182,7 @@ void fem3_mesh_free(fem3_mesh h) {
     if (!m) return;
     dev_free_all(m);
     cudaStreamSynchronize(m->stream);
-    if (m->h_norms) cudaFreeHost(m->h_norms);
+    if (m->h_norms) pinned_release(m->h_norms);
     if (m->ev_made)
         for (int k = 0; k < 16; k++) cudaEventDestroy(m->ev[k]);
     delete m;
@@ -179,10 +226,7 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
     stage_begin(m, 0);
     if ((st = dev_alloc_t(m, &m->err, ERR_COUNT)) != FEM3_OK) return fail(st);
     if ((st = dev_alloc_t(m, &m->norms, 128)) != FEM3_OK) return fail(st);
-    if (cudaMallocHost(&m->h_norms, 128 * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(set_error(FEM3_E_OOM, "cudaMallocHost"));
-    }
+    if (!(m->h_norms = pinned_block())) return fail(set_error(FEM3_E_OOM, "cudaMallocHost"));
     if (cudaMemsetAsync(m->err, 0, sizeof(int32_t) * ERR_COUNT, m->stream) != cudaSuccess)
         return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
     if ((st = dev_alloc_t(m, &m->verts, 3 * n_nodes)) != FEM3_OK) return fail(st);

@@ -152,7 +152,9 @@ struct Mesh {
     bool ev_made = false;
     float stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
-    std::vector<void *> allocs;
+    std::vector<void *> allocs;   // stream-ordered allocations, freed with the mesh
+    char *arena = nullptr;        // current sub-allocation chunk (one of allocs)
+    size_t arena_size = 0, arena_used = 0;
 };
 
 inline void note_launch(Mesh *m) { m->launches++; }
