@@ -31,11 +31,7 @@ static void batch_destroy(Batch *b) {
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     if (b->fork) cudaEventDestroy(b->fork);
     cudaFree(b->ws.d_desc);
-    cudaFree(b->ws.d_zptr);
-    cudaFree(b->ws.d_zlen);
     cudaFreeHost(b->ws.h_desc);
-    cudaFreeHost(b->ws.h_zptr);
-    cudaFreeHost(b->ws.h_zlen);
     cudaFree(b->d_tdesc);
     cudaFreeHost(b->h_tdesc);
     delete b;

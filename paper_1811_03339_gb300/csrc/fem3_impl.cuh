@@ -181,7 +181,6 @@ int scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, Mesh *m
 // scratch of the batched walk (descriptor arrays; freed by the batch)
 struct BatchWalkScratch {
     void *d_desc = nullptr, *h_desc = nullptr;
-    void *d_zptr = nullptr, *d_zlen = nullptr, *h_zptr = nullptr, *h_zlen = nullptr;
 };
 
 // one mesh of a batched triangular solve (device-resident descriptor)

@@ -295,31 +295,31 @@ __device__ __forceinline__ void pow_df(double r, double p, const float2 *__restr
     df_mul(qh, ql, s.x, s.y, ph, pl);
 }
 
-// cell j of the power for exponent p: Taylor terms C(p,k) m_c^(p-k) (k <= 4) and, for
-// j < 128, 2^((j - 64) p); FP64 values stored as hi + lo pairs
-__device__ __forceinline__ void fill_pow_cell(double p, int j, float2 *cell, float2 *pexp) {
-    const double mc = 1.0 + (2.0 * j + 1.0) / 512.0;
-    double binom = 1.0;
-    float2 *c = cell + 8 * j;
-    for (int k = 0; k < 8; k++) c[k] = make_float2(0.f, 0.f);
-    for (int k = 0; k <= 4; k++) {
-        float h, l;
+// entry k (0..7) of cell j of the power for exponent p: the Taylor term C(p,k) m_c^(p-k)
+// for k <= 4 (zero for k >= 5), and from k = 5, for j < 128, 2^((j - 64) p); FP64 values
+// stored as hi + lo pairs.  One thread per entry: the FP64 power is the slow part.
+__device__ __forceinline__ void fill_pow_entry(double p, int j, int k, float2 *cell,
+                                               float2 *pexp) {
+    float h = 0.f, l = 0.f;
+    if (k <= 4) {
+        const double mc = 1.0 + (2.0 * j + 1.0) / 512.0;
+        double binom = 1.0;
+        for (int i = 0; i < k; i++) binom = binom * (p - i) / (i + 1);
         f64_split(binom * pow(mc, p - k), h, l);
-        c[k] = make_float2(h, l);
-        binom = binom * (p - k) / (k + 1);
     }
-    if (j < 128) {
-        float h, l;
+    cell[8 * j + k] = make_float2(h, l);
+    if (k == 5 && j < 128) {
         f64_split(exp2((double)(j - 64) * p), h, l);
         pexp[j] = make_float2(h, l);
     }
 }
 
-// tables of the power for p = 1 - gamma_axis: cell[a][j][0..4], pexp[a][e + 64]
+// tables of the power for p = 1 - gamma_axis: cell[a][j][0..7], pexp[a][e + 64];
+// grid (8 entries, 3 axes) x 256 cells
 __global__ void k_pow_tables(double p0, double p1, double p2, float2 *cell, float2 *pexp) {
-    const int a = blockIdx.x, j = threadIdx.x;   // 3 blocks x 256 threads
+    const int k = blockIdx.x, a = blockIdx.y, j = threadIdx.x;
     const double p = a == 0 ? p0 : (a == 1 ? p1 : p2);
-    fill_pow_cell(p, j, cell + (size_t)a * 256 * 8, pexp + a * 128);
+    fill_pow_entry(p, j, k, cell + (size_t)a * 256 * 8, pexp + a * 128);
 }
 
 // (table entry) += (h + l)
@@ -353,6 +353,11 @@ __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
     const double x0 = W.gp[3 * (int64_t)g], x1 = W.gp[3 * (int64_t)g + 1],
                  x2 = W.gp[3 * (int64_t)g + 2];
     const LineF X = line_f(x0, x1, x2, axis);
+    // this line's rows of L and R (no other thread writes them): zero before accumulating
+    for (int c = 0; c < nd; c++) {
+        A0.tab[toff + (int64_t)c * ld] = make_float2(0.f, 0.f);
+        A1.tab[toff + (int64_t)c * ld] = make_float2(0.f, 0.f);
+    }
     int side = 0;   // 0: left walk (dir -1, table L), 1: right walk (dir +1, table R)
     int32_t t = g >> 2;
     double r_prev = 0.0;
@@ -545,23 +550,12 @@ __global__ void __launch_bounds__(128, 6) k_walk_batch(const WalkDesc *__restric
         atomicAdd(descs[d].seg, (unsigned long long)sum);
 }
 
-// tables of the table-driven power for each descriptor (block d, 256 threads)
+// tables of the table-driven power for each descriptor (grid: descriptor x 8 entries,
+// 256 cells)
 __global__ void k_pow_tables_batch(const WalkDesc *__restrict__ descs) {
     const WalkDesc &D = descs[blockIdx.x];
-    fill_pow_cell(D.A0.p_exp, threadIdx.x, const_cast<float2 *>(D.A0.pow_cell),
-                  const_cast<float2 *>(D.A0.pow_exp));
-}
-
-// zero n_buf device buffers given as (pointer, element count) pairs
-__global__ void k_zero_batch(double *const *__restrict__ ptr, const int64_t *__restrict__ len,
-                             int n_buf) {
-    for (int b = blockIdx.y; b < n_buf; b += gridDim.y) {
-        double *p = ptr[b];
-        const int64_t n = len[b];
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-             i += (int64_t)gridDim.x * blockDim.x)
-            p[i] = 0.0;
-    }
+    fill_pow_entry(D.A0.p_exp, threadIdx.x, blockIdx.y, const_cast<float2 *>(D.A0.pow_cell),
+                   const_cast<float2 *>(D.A0.pow_exp));
 }
 
 // Path export: same walk, segments written out for requested lines.
@@ -643,14 +637,9 @@ int walk_tables(Mesh *m, const double alpha[3]) {
         FEM3_TRY(dev_alloc_t(m, &m->pow_cell, 3 * 256 * 8));
         FEM3_TRY(dev_alloc_t(m, &m->pow_exp, 3 * 128));
     }
-    k_pow_tables<<<3, 256, 0, s>>>(1.0 - alpha[0] / 2.0, 1.0 - alpha[1] / 2.0, 1.0 - alpha[2] / 2.0,
-                                   m->pow_cell, m->pow_exp);
+    k_pow_tables<<<dim3(8, 3), 256, 0, s>>>(1.0 - alpha[0] / 2.0, 1.0 - alpha[1] / 2.0,
+                                            1.0 - alpha[2] / 2.0, m->pow_cell, m->pow_exp);
     note_launch(m);
-    for (int axis = 0; axis < 3; axis++) {
-        AxisBins &B = m->bins[axis];
-        FEM3_CUDA(cudaMemsetAsync(m->tabL[axis], 0, sizeof(float2) * B.tab_elems, s));
-        FEM3_CUDA(cudaMemsetAsync(m->tabR[axis], 0, sizeof(float2) * B.tab_elems, s));
-    }
     stage_begin(m, 2);
     AxisTables T;
     for (int axis = 0; axis < 3; axis++) {
@@ -700,24 +689,18 @@ int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double
     return FEM3_OK;
 }
 
-// Walk + tables for every mesh of a batch in three launches (zero, power tables, walk).
-// Scratch: device and pinned host arrays owned by the caller, sized for the batch.
+// Walk + tables for every mesh of a batch in two launches (power tables, walk; the walk
+// zeroes each line's table rows itself).  Scratch: a device and a pinned host descriptor
+// array owned by the caller, sized for the batch.
 int walk_tables_batch(Mesh *const *ms, int n, const double *alpha, cudaStream_t s,
                       BatchWalkScratch *bs) {
     const int n_desc = 3 * n;
     if (!bs->d_desc) {
         FEM3_CUDA(cudaMalloc(&bs->d_desc, sizeof(WalkDesc) * n_desc));
         FEM3_CUDA(cudaMallocHost(&bs->h_desc, sizeof(WalkDesc) * n_desc));
-        FEM3_CUDA(cudaMalloc(&bs->d_zptr, sizeof(double *) * 2 * n_desc));
-        FEM3_CUDA(cudaMalloc(&bs->d_zlen, sizeof(int64_t) * 2 * n_desc));
-        FEM3_CUDA(cudaMallocHost(&bs->h_zptr, sizeof(double *) * 2 * n_desc));
-        FEM3_CUDA(cudaMallocHost(&bs->h_zlen, sizeof(int64_t) * 2 * n_desc));
     }
     WalkDesc *hd = reinterpret_cast<WalkDesc *>(bs->h_desc);
-    double **zp = reinterpret_cast<double **>(bs->h_zptr);
-    int64_t *zl = reinterpret_cast<int64_t *>(bs->h_zlen);
     int64_t items = 0;
-    int64_t max_tab = 0;
     for (int i = 0; i < n; i++) {
         Mesh *m = ms[i];
         if (!m->pow_cell) {
@@ -745,26 +728,16 @@ int walk_tables_batch(Mesh *const *ms, int n, const double *alpha, cudaStream_t 
             D.err = m->err;
             D.seg = reinterpret_cast<unsigned long long *>(m->norms + kSegCounterSlot);
             items += m->n_gp;
-            zp[2 * (3 * i + axis)] = reinterpret_cast<double *>(m->tabL[axis]);
-            zl[2 * (3 * i + axis)] = B.tab_elems;
-            zp[2 * (3 * i + axis) + 1] = reinterpret_cast<double *>(m->tabR[axis]);
-            zl[2 * (3 * i + axis) + 1] = B.tab_elems;
-            max_tab = std::max<int64_t>(max_tab, B.tab_elems);
         }
         FEM3_CUDA(cudaMemsetAsync(m->norms + kSegCounterSlot, 0, sizeof(double), s));
     }
     FEM3_CUDA(cudaMemcpyAsync(bs->d_desc, hd, sizeof(WalkDesc) * n_desc, cudaMemcpyHostToDevice, s));
-    FEM3_CUDA(cudaMemcpyAsync(bs->d_zptr, zp, sizeof(double *) * 2 * n_desc, cudaMemcpyHostToDevice, s));
-    FEM3_CUDA(cudaMemcpyAsync(bs->d_zlen, zl, sizeof(int64_t) * 2 * n_desc, cudaMemcpyHostToDevice, s));
-    const unsigned gx = (unsigned)std::min<int64_t>(4096, std::max<int64_t>(1, (max_tab + 255) / 256));
-    k_zero_batch<<<dim3(gx, std::min(2 * n_desc, 65535)), 256, 0, s>>>(
-        reinterpret_cast<double *const *>(bs->d_zptr), reinterpret_cast<const int64_t *>(bs->d_zlen),
-        2 * n_desc);
-    k_pow_tables_batch<<<n_desc, 256, 0, s>>>(reinterpret_cast<const WalkDesc *>(bs->d_desc));
+    k_pow_tables_batch<<<dim3(n_desc, 8), 256, 0, s>>>(
+        reinterpret_cast<const WalkDesc *>(bs->d_desc));
     if (items > 0)
         k_walk_batch<<<(unsigned)((items + 127) / 128), 128, 0, s>>>(
             reinterpret_cast<const WalkDesc *>(bs->d_desc), n_desc, items);
-    for (int i = 0; i < n; i++) ms[i]->launches += 3;   // the batch's launches, counted per mesh
+    for (int i = 0; i < n; i++) ms[i]->launches += 2;   // the batch's launches, counted per mesh
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
