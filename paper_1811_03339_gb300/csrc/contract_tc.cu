@@ -147,8 +147,9 @@ template <> struct Split<__nv_bfloat16> {
 
 // ------------------------------- split kernel ------------------------------------
 // One warp per template row (bin b, local dof c), lanes over the row's Gauss points:
-// coalesced reads of the table row (hi + lo pairs).  Writes the operator-apply operands L
-// and W R as hi + lo FP32 pairs in the table layout and, when Lhi is given, the
+// coalesced reads of the table row (hi + lo pairs).  Writes the operator-apply operand W R
+// as hi + lo FP32 pairs in the table layout (the apply reads L from the table itself)
+// and, when Lhi is given, the
 // tensor-core operands (the TF32 or BF16 pairs of the same values, zero past the bin's
 // Gauss points).  No FP64 arithmetic: W R is formed in double-float FP32 operations.
 template <class OT>
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(256) k_split_ops(
     const int32_t *__restrict__ row_bin, const int32_t *__restrict__ dof_off,
     const int32_t *__restrict__ gp_off, const double *__restrict__ w_slot,
     const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
-    int64_t n_rows, int Kp, OT *Lhi, OT *Llo, OT *Rhi, OT *Rlo, float2 *apL, float2 *apR) {
+    int64_t n_rows, int Kp, OT *Lhi, OT *Llo, OT *Rhi, OT *Rlo, float2 *apR) {
     const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n_rows) return;
@@ -177,7 +178,6 @@ __global__ void __launch_bounds__(256) k_split_ops(
             float sh = 0.f, sl = 0.f;
             df_fma(r1, r2, wh, wl, sh, sl);
             const float wr = sh + sl, wr2 = sl - (wr - sh);
-            apL[src + k] = make_float2(a, a2);
             apR[src + k] = make_float2(wr, wr2);
             if (Lhi) {
                 Split<OT>::run(a, a2, lh, ll);
@@ -418,13 +418,13 @@ int contract_tc(Mesh *m, bool bf16) {
             for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<__nv_bfloat16 *>(B.tc_op[q]);
             k_split_ops<__nv_bfloat16><<<grid, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
-                B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1], op[2], op[3], B.ap_L, B.ap_R);
+                B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1], op[2], op[3], B.ap_R);
         } else {
             float *op[4];
             for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<float *>(B.tc_op[q]);
             k_split_ops<float><<<grid, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
-                B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1], op[2], op[3], B.ap_L, B.ap_R);
+                B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1], op[2], op[3], B.ap_R);
         }
         note_launch(m);
         CUtensorMap maps[4];
@@ -447,9 +447,8 @@ int contract_tc(Mesh *m, bool bf16) {
 
 int ap_alloc(Mesh *m, int axis) {
     AxisBins &B = m->bins[axis];
-    if (B.ap_L) return FEM3_OK;
+    if (B.ap_R) return FEM3_OK;
     const int64_t e = std::max<int64_t>(1, B.tab_elems);
-    FEM3_TRY(dev_alloc(m, (void **)&B.ap_L, sizeof(float2) * e));
     FEM3_TRY(dev_alloc(m, (void **)&B.ap_R, sizeof(float2) * e));
     return FEM3_OK;
 }
@@ -464,7 +463,7 @@ int ap_prepare(Mesh *m) {
         FEM3_TRY(ap_alloc(m, axis));
         k_split_ops<float><<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
             m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot, B.tab_off,
-            B.tab_ld, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_L, B.ap_R);
+            B.tab_ld, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_R);
         note_launch(m);
     }
     m->ap_ready = true;

@@ -77,8 +77,8 @@ struct AxisBins {
     int32_t *row_bin = nullptr;  // [n_tmpl] template row -> bin
     int tc_maxG = 0;             // largest Gauss-point count of a bin
     int4 *tc_work = nullptr;     // (bin, m-tile, n-tile, 0)
-    // operator-apply operands in the table layout: L and W R as hi + lo FP32 pairs
-    float2 *ap_L = nullptr, *ap_R = nullptr;
+    // operator-apply operand W R as hi + lo FP32 pairs in the table layout (L is the table)
+    float2 *ap_R = nullptr;
     int tc_n_work = 0;
     std::vector<int32_t> h_gp_off, h_dof_off;
     std::vector<int4> h_work, h_tc_work;   // host copies of the work lists
@@ -128,7 +128,7 @@ struct Mesh {
     float *A32 = nullptr;      // [n_dof][n_dof]
     bool factored = false;
     bool tc_ready = false;
-    bool ap_ready = false;     // ap_L / ap_R hold the current tables
+    bool ap_ready = false;     // ap_R holds W R of the current tables
 
     // workspaces
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

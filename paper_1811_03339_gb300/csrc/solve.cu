@@ -1300,10 +1300,11 @@ int factor(Mesh *m) {
 
 // Fused operator apply, one CTA per transverse bin, in double-float arithmetic on the FP32
 // pipes.  With R~ = W R (split once per assembly, see k_split_ops), A u restricted to
-// the bin is L^T (R~ u) + R~^T (L u).  The bin's Gauss points go in chunks of 32; for each
-// chunk the L and R~ columns of up to RM template rows are staged in shared memory
-// (cp.async 16-byte copies, all in flight together, zero-filled past the bin's Gauss points;
-// rows of 34 pairs, 272 bytes) with u_b as hi + lo pairs.  Phase 1
+// the bin is L^T (R~ u) + R~^T (L u) (L read from the table itself).  The bin's Gauss
+// points go in chunks of 32; for each chunk the L and R~ columns of up to RM template rows
+// are staged in shared memory (cp.async 16-byte copies, all in flight together, zero-filled
+// past the bin's Gauss points; rows of 34 pairs, 272 bytes) with u_b as hi + lo pairs.
+// Phase 1
 // forms yR = R~ u_b and yL = L u_b (warp w sums rows w, w + 8, ..., lane = Gauss point; the
 // eight partial sums are added in shared memory); phase 2 adds s K (L^T yR + R~^T yL) to Au,
 // one thread per template row, from the same staged rows (a bin with more than RM rows
@@ -1523,7 +1524,7 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
             AxisBins &B = m->bins[axis];
             const bool on = B.n_tmpl > 0 && B.n_bins > 0;
             const float skh = (float)m->sK[axis], skl = (float)(m->sK[axis] - (double)skh);
-            P.a[axis] = ApplyAxis{B.ap_L, B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_ld,
+            P.a[axis] = ApplyAxis{m->tabL[axis], B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_ld,
                                   B.tab_off, skh, skl, on ? B.n_bins : 0};
             nblk += on ? B.n_bins : 0;
         }
