@@ -405,72 +405,113 @@ __device__ __forceinline__ int bin_coord(double p, double org, double w, int nb)
     return i;
 }
 
-__global__ void k_gp_bin_count(const double *__restrict__ gp, int64_t n_gp, BinGeom G,
-                               int32_t *count, int32_t *gbin) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= n_gp) return;
-    int i0 = bin_coord(gp[3 * g + G.c0], G.org0, G.width, G.nb0);
-    int i1 = bin_coord(gp[3 * g + G.c1], G.org1, G.width, G.nb1);
-    int b = i0 + G.nb0 * i1;
-    gbin[g] = b;
-    atomicAdd(&count[b], 1);
+// ---------------------------------------------------------------------------------
+// Transverse bins of the three axes, built together: one launch per step with
+// blockIdx.y = axis.
+// ---------------------------------------------------------------------------------
+struct BinAxis {
+    BinGeom G;
+    int32_t *gcount, *dcount, *gcur, *dcur, *gbin, *gp_off, *dof_off;
+    unsigned long long *gkeys, *dkeys;
+    int32_t *gp_idx, *slot_bin, *dof_idx, *row_bin, *slot_of_gp;
+    double *w_slot;
+    double lo, span;   // extent along the axis (sort key of the Gauss points)
+    int n_bins;
+};
+struct BinAxes {
+    BinAxis a[3];
+};
+
+__global__ void k_bin_count3(const __grid_constant__ BinAxes P, const double *__restrict__ gp,
+                             int64_t n_gp, const double *__restrict__ box,
+                             const int32_t *__restrict__ dof_node, int64_t n_dof) {
+    const BinAxis &X = P.a[blockIdx.y];
+    const BinGeom G = X.G;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n_gp) {
+        const int i0 = bin_coord(gp[3 * i + G.c0], G.org0, G.width, G.nb0);
+        const int i1 = bin_coord(gp[3 * i + G.c1], G.org1, G.width, G.nb1);
+        const int b = i0 + G.nb0 * i1;
+        X.gbin[i] = b;
+        atomicAdd(&X.gcount[b], 1);
+    }
+    if (i < n_dof) {
+        const double *bx = box + 6 * (int64_t)dof_node[i];
+        const int a0 = bin_coord(bx[G.c0], G.org0, G.width, G.nb0);
+        const int a1 = bin_coord(bx[3 + G.c0], G.org0, G.width, G.nb0);
+        const int b0 = bin_coord(bx[G.c1], G.org1, G.width, G.nb1);
+        const int b1 = bin_coord(bx[3 + G.c1], G.org1, G.width, G.nb1);
+        for (int i1 = b0; i1 <= b1; i1++)
+            for (int i0 = a0; i0 <= a1; i0++) atomicAdd(&X.dcount[i0 + G.nb0 * i1], 1);
+    }
 }
 
-__global__ void k_dof_bin_count(const double *__restrict__ box, const int32_t *__restrict__ dof_node,
-                                int64_t n_dof, BinGeom G, int32_t *count) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n_dof) return;
-    const double *bx = box + 6 * (int64_t)dof_node[j];
-    int a0 = bin_coord(bx[G.c0], G.org0, G.width, G.nb0);
-    int a1 = bin_coord(bx[3 + G.c0], G.org0, G.width, G.nb0);
-    int b0 = bin_coord(bx[G.c1], G.org1, G.width, G.nb1);
-    int b1 = bin_coord(bx[3 + G.c1], G.org1, G.width, G.nb1);
-    for (int i1 = b0; i1 <= b1; i1++)
-        for (int i0 = a0; i0 <= a1; i0++) atomicAdd(&count[i0 + G.nb0 * i1], 1);
+// exclusive scans of the six count arrays (block q: axis q / 2, Gauss points or dofs),
+// total in out[n]; one CTA per array
+__global__ void k_bin_scan3(const __grid_constant__ BinAxes P) {
+    __shared__ int32_t sh[32];
+    const BinAxis &X = P.a[blockIdx.x >> 1];
+    const bool dofs = blockIdx.x & 1;
+    const int32_t *in = dofs ? X.dcount : X.gcount;
+    int32_t *out = dofs ? X.dof_off : X.gp_off;
+    const int n = X.n_bins;
+    int32_t carry = 0;
+    for (int base = 0; base < n; base += kScanBlock) {
+        const int i = base + threadIdx.x;
+        int32_t v = i < n ? in[i] : 0, tot;
+        const int32_t e = block_excl_scan(v, sh, &tot);
+        if (i < n) out[i] = e + carry;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
 }
 
-__global__ void k_gp_bin_fill(const double *__restrict__ gp, int64_t n_gp, int axis, double lo,
-                              double span, const int32_t *__restrict__ gbin,
-                              const int32_t *__restrict__ off, int32_t *cursor,
-                              unsigned long long *keys) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= n_gp) return;
-    int b = gbin[g];
-    int32_t pos = atomicAdd(&cursor[b], 1);
-    // sort key: position along the axis (30-bit quantised), then the Gauss point id
-    double u = (gp[3 * g + axis] - lo) / span;
-    u = u < 0 ? 0 : (u > 1 ? 1 : u);
-    unsigned long long q = (unsigned long long)(u * 1073741823.0);
-    keys[off[b] + pos] = (q << 32) | (unsigned long long)g;
+__global__ void k_bin_fill3(const __grid_constant__ BinAxes P, const double *__restrict__ gp,
+                            int64_t n_gp, const double *__restrict__ box,
+                            const int32_t *__restrict__ dof_node, int64_t n_dof) {
+    const int axis = blockIdx.y;
+    const BinAxis &X = P.a[axis];
+    const BinGeom G = X.G;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n_gp) {
+        const int b = X.gbin[i];
+        const int32_t pos = atomicAdd(&X.gcur[b], 1);
+        // sort key: position along the axis (30-bit quantised), then the Gauss point id
+        double u = (gp[3 * i + axis] - X.lo) / X.span;
+        u = u < 0 ? 0 : (u > 1 ? 1 : u);
+        const unsigned long long q = (unsigned long long)(u * 1073741823.0);
+        X.gkeys[X.gp_off[b] + pos] = (q << 32) | (unsigned long long)i;
+    }
+    if (i < n_dof) {
+        const double *bx = box + 6 * (int64_t)dof_node[i];
+        const int a0 = bin_coord(bx[G.c0], G.org0, G.width, G.nb0);
+        const int a1 = bin_coord(bx[3 + G.c0], G.org0, G.width, G.nb0);
+        const int b0 = bin_coord(bx[G.c1], G.org1, G.width, G.nb1);
+        const int b1 = bin_coord(bx[3 + G.c1], G.org1, G.width, G.nb1);
+        for (int i1 = b0; i1 <= b1; i1++)
+            for (int i0 = a0; i0 <= a1; i0++) {
+                const int b = i0 + G.nb0 * i1;
+                const int32_t pos = atomicAdd(&X.dcur[b], 1);
+                X.dkeys[X.dof_off[b] + pos] = (unsigned long long)i;
+            }
+    }
 }
 
-__global__ void k_dof_bin_fill(const double *__restrict__ box, const int32_t *__restrict__ dof_node,
-                               int64_t n_dof, BinGeom G, const int32_t *__restrict__ off,
-                               int32_t *cursor, unsigned long long *keys) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n_dof) return;
-    const double *bx = box + 6 * (int64_t)dof_node[j];
-    int a0 = bin_coord(bx[G.c0], G.org0, G.width, G.nb0);
-    int a1 = bin_coord(bx[3 + G.c0], G.org0, G.width, G.nb0);
-    int b0 = bin_coord(bx[G.c1], G.org1, G.width, G.nb1);
-    int b1 = bin_coord(bx[3 + G.c1], G.org1, G.width, G.nb1);
-    for (int i1 = b0; i1 <= b1; i1++)
-        for (int i0 = a0; i0 <= a1; i0++) {
-            int b = i0 + G.nb0 * i1;
-            int32_t pos = atomicAdd(&cursor[b], 1);
-            keys[off[b] + pos] = (unsigned long long)j;
-        }
-}
-
-// One CTA per bin: bitonic sort of the bin's keys in shared memory, then write the
-// low 32 bits as the sorted ids (and the slot -> bin map for Gauss points).
-// one CTA per bin: bitonic sort of the bin's keys in shared memory (sized by the launch
-// for the largest bin, rounded up to a power of two)
-__global__ void k_bin_sort(const int32_t *__restrict__ off, unsigned long long *keys,
-                           int32_t *ids, int32_t *slot_bin) {
+// one CTA per (bin, axis, kind): bitonic sort of the bin's keys in shared memory (sized by
+// the launch for the largest bin, rounded up to a power of two); kind 0 writes the
+// Gauss-point ids and the slot -> bin map, kind 1 the dof ids and the row -> bin map
+__global__ void k_bin_sort3(const __grid_constant__ BinAxes P) {
     extern __shared__ unsigned long long sh[];
-    int b = blockIdx.x;
-    int lo = off[b], n = off[b + 1] - lo;
+    const BinAxis &X = P.a[blockIdx.y];
+    const int b = blockIdx.x;
+    if (b >= X.n_bins) return;
+    const bool dofs = blockIdx.z == 1;
+    const int32_t *off = dofs ? X.dof_off : X.gp_off;
+    const unsigned long long *keys = dofs ? X.dkeys : X.gkeys;
+    int32_t *ids = dofs ? X.dof_idx : X.gp_idx;
+    int32_t *bin_of = dofs ? X.row_bin : X.slot_bin;
+    const int lo = off[b], n = off[b + 1] - lo;
     int p2 = 1;
     while (p2 < n) p2 <<= 1;
     for (int i = threadIdx.x; i < p2; i += blockDim.x) sh[i] = i < n ? keys[lo + i] : ~0ull;
@@ -478,10 +519,10 @@ __global__ void k_bin_sort(const int32_t *__restrict__ off, unsigned long long *
     for (int k = 2; k <= p2; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-                int l = i ^ j;
+                const int l = i ^ j;
                 if (l > i) {
-                    bool up = (i & k) == 0;
-                    unsigned long long a = sh[i], c = sh[l];
+                    const bool up = (i & k) == 0;
+                    const unsigned long long a = sh[i], c = sh[l];
                     if ((a > c) == up) { sh[i] = c; sh[l] = a; }
                 }
             }
@@ -489,26 +530,19 @@ __global__ void k_bin_sort(const int32_t *__restrict__ off, unsigned long long *
         }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         ids[lo + i] = (int32_t)(sh[i] & 0xffffffffull);
-        if (slot_bin) slot_bin[lo + i] = b;
+        bin_of[lo + i] = b;
     }
 }
 
-__global__ void k_row_bin(const int32_t *__restrict__ dof_off, int n_bins, int32_t *row_bin) {
-    int b = blockIdx.x;
-    if (b >= n_bins) return;
-    for (int r = dof_off[b] + threadIdx.x; r < dof_off[b + 1]; r += blockDim.x) row_bin[r] = b;
-}
-
-__global__ void k_slot_weights(const int32_t *__restrict__ gp_idx, const double *__restrict__ gw,
-                               int64_t n_gp, double *w_slot) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s < n_gp) w_slot[s] = gw[gp_idx[s]];
-}
-
-__global__ void k_invert_slots(const int32_t *__restrict__ gp_idx, int64_t n_gp,
-                               int32_t *slot_of_gp) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s < n_gp) slot_of_gp[gp_idx[s]] = (int32_t)s;
+// slot weights and the Gauss point -> slot map of each axis
+__global__ void k_bin_slots3(const __grid_constant__ BinAxes P, const double *__restrict__ gw,
+                             int64_t n_gp) {
+    const BinAxis &X = P.a[blockIdx.y];
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= n_gp) return;
+    const int32_t g = X.gp_idx[s];
+    X.w_slot[s] = gw[g];
+    X.slot_of_gp[g] = (int32_t)s;
 }
 
 }  // namespace
@@ -637,10 +671,10 @@ int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
 int bins_build(Mesh *m) {
     cudaStream_t s = m->stream;
     const int64_t n_gp = m->n_gp, n_dof = m->n_dof;
-    // pass 1, all axes: bin counts and offsets, then one read-back of every offset array
-    // (device-to-host copies into pageable memory complete before they return)
-    int32_t *gcount[3], *dcount[3], *gcur[3], *dcur[3], *gbin[3];
-    BinGeom Gs[3];
+    // geometry of the three axes' bins; counters and offsets in one allocation each
+    BinAxes P;
+    int64_t nb_tot = 0;
+    int nb_max = 1;
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
         B.c0 = axis == 0 ? 1 : 0;
@@ -651,90 +685,101 @@ int bins_build(Mesh *m) {
         B.nb0 = std::max(1, (int)ceil((m->hi[B.c0] - m->lo[B.c0]) / B.width));
         B.nb1 = std::max(1, (int)ceil((m->hi[B.c1] - m->lo[B.c1]) / B.width));
         B.n_bins = B.nb0 * B.nb1;
-        Gs[axis] = BinGeom{B.c0, B.c1, B.nb0, B.nb1, B.org0, B.org1, B.width};
-        const BinGeom G = Gs[axis];
-        const int nb = B.n_bins;
-        FEM3_TRY(dev_alloc_t(m, &gcount[axis], nb));
-        FEM3_TRY(dev_alloc_t(m, &dcount[axis], nb));
-        FEM3_TRY(dev_alloc_t(m, &gcur[axis], nb));
-        FEM3_TRY(dev_alloc_t(m, &dcur[axis], nb));
-        FEM3_TRY(dev_alloc_t(m, &gbin[axis], n_gp));
-        FEM3_TRY(dev_alloc_t(m, &B.gp_off, nb + 1));
-        FEM3_TRY(dev_alloc_t(m, &B.dof_off, nb + 1));
-        FEM3_CUDA(cudaMemsetAsync(gcount[axis], 0, sizeof(int32_t) * nb, s));
-        FEM3_CUDA(cudaMemsetAsync(dcount[axis], 0, sizeof(int32_t) * nb, s));
-        FEM3_CUDA(cudaMemsetAsync(gcur[axis], 0, sizeof(int32_t) * nb, s));
-        FEM3_CUDA(cudaMemsetAsync(dcur[axis], 0, sizeof(int32_t) * nb, s));
-        k_gp_bin_count<<<grid_for(n_gp), kThreads, 0, s>>>(m->gp, n_gp, G, gcount[axis], gbin[axis]);
-        note_launch(m);
-        k_dof_bin_count<<<grid_for(n_dof), kThreads, 0, s>>>(m->node_box, m->dof_node, n_dof, G,
-                                                             dcount[axis]);
-        note_launch(m);
-        FEM3_TRY(scan_i32(gcount[axis], B.gp_off, nb, s, m));
-        FEM3_TRY(scan_i32(dcount[axis], B.dof_off, nb, s, m));
+        nb_tot += B.n_bins;
+        nb_max = std::max(nb_max, B.n_bins);
+        BinAxis &X = P.a[axis];
+        X = BinAxis{};
+        X.G = BinGeom{B.c0, B.c1, B.nb0, B.nb1, B.org0, B.org1, B.width};
+        X.lo = m->lo[axis];
+        X.span = std::max(m->hi[axis] - m->lo[axis], 1e-300);
+        X.n_bins = B.n_bins;
     }
-    for (int axis = 0; axis < 3; axis++) {
-        AxisBins &B = m->bins[axis];
-        const int nb = B.n_bins;
-        B.h_gp_off.resize(nb + 1);
-        B.h_dof_off.resize(nb + 1);
-        FEM3_CUDA(cudaMemcpyAsync(B.h_gp_off.data(), B.gp_off, sizeof(int32_t) * (nb + 1),
-                                  cudaMemcpyDeviceToHost, s));
-        FEM3_CUDA(cudaMemcpyAsync(B.h_dof_off.data(), B.dof_off, sizeof(int32_t) * (nb + 1),
-                                  cudaMemcpyDeviceToHost, s));
+    int32_t *cnt, *offs;
+    FEM3_TRY(dev_alloc_t(m, &cnt, 4 * nb_tot));
+    FEM3_TRY(dev_alloc_t(m, &offs, 2 * (nb_tot + 3)));
+    FEM3_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 4 * nb_tot, s));
+    {
+        int64_t c = 0, o = 0;
+        for (int axis = 0; axis < 3; axis++) {
+            AxisBins &B = m->bins[axis];
+            BinAxis &X = P.a[axis];
+            const int nb = B.n_bins;
+            X.gcount = cnt + c;
+            X.dcount = cnt + c + nb;
+            X.gcur = cnt + c + 2 * nb;
+            X.dcur = cnt + c + 3 * nb;
+            c += 4 * nb;
+            B.gp_off = X.gp_off = offs + o;
+            B.dof_off = X.dof_off = offs + o + nb + 1;
+            o += 2 * (nb + 1);
+            FEM3_TRY(dev_alloc_t(m, &X.gbin, n_gp));
+        }
     }
+    // pass 1: counts and offsets of all axes, one read-back (device-to-host copies into
+    // pageable memory complete before they return)
+    const unsigned gx = grid_for(std::max(n_gp, n_dof));
+    k_bin_count3<<<dim3(gx, 3), kThreads, 0, s>>>(P, m->gp, n_gp, m->node_box, m->dof_node, n_dof);
+    note_launch(m);
+    k_bin_scan3<<<6, kScanBlock, 0, s>>>(P);
+    note_launch(m);
+    std::vector<int32_t> h_offs(2 * (nb_tot + 3));
+    FEM3_CUDA(cudaMemcpyAsync(h_offs.data(), offs, sizeof(int32_t) * h_offs.size(),
+                              cudaMemcpyDeviceToHost, s));
     FEM3_CUDA(cudaStreamSynchronize(s));
-    // pass 2, all axes: fill, sort and lay out; host-to-device copies from pageable memory
-    // are staged before they return, so nothing waits for the device here
+    // pass 2: sizes, allocations, then fill, sort and slot maps of all axes in one launch
+    // each; host-to-device copies from pageable memory are staged before they return
+    int max_gp = 1, max_dof = 1;
+    {
+        int64_t o = 0;
+        for (int axis = 0; axis < 3; axis++) {
+            AxisBins &B = m->bins[axis];
+            BinAxis &X = P.a[axis];
+            const int nb = B.n_bins;
+            B.h_gp_off.assign(h_offs.begin() + o, h_offs.begin() + o + nb + 1);
+            B.h_dof_off.assign(h_offs.begin() + o + nb + 1, h_offs.begin() + o + 2 * (nb + 1));
+            o += 2 * (nb + 1);
+            B.n_tmpl = B.h_dof_off[nb];
+            B.max_dof = 0;
+            B.max_gp = 0;
+            for (int b = 0; b < nb; b++) {
+                B.max_dof = std::max(B.max_dof, B.h_dof_off[b + 1] - B.h_dof_off[b]);
+                B.max_gp = std::max(B.max_gp, B.h_gp_off[b + 1] - B.h_gp_off[b]);
+            }
+            if (B.max_dof > kMaxBinItems || B.max_gp > kMaxBinItems)
+                return set_error(FEM3_E_ARG, "a transverse bin holds more than 4096 dofs or "
+                                             "Gauss points; lower fem3_options.bin_scale");
+            max_gp = std::max(max_gp, B.max_gp);
+            max_dof = std::max(max_dof, B.max_dof);
+            FEM3_TRY(dev_alloc_t(m, &X.gkeys, n_gp));
+            FEM3_TRY(dev_alloc_t(m, &X.dkeys, std::max<int64_t>(1, B.n_tmpl)));
+            FEM3_TRY(dev_alloc_t(m, &B.gp_idx, n_gp));
+            FEM3_TRY(dev_alloc_t(m, &B.slot_bin, n_gp));
+            FEM3_TRY(dev_alloc_t(m, &B.dof_idx, std::max<int64_t>(1, B.n_tmpl)));
+            FEM3_TRY(dev_alloc_t(m, &B.row_bin, std::max<int64_t>(1, B.n_tmpl)));
+            FEM3_TRY(dev_alloc_t(m, &B.w_slot, n_gp));
+            FEM3_TRY(dev_alloc_t(m, &B.slot_of_gp, n_gp));
+            X.gp_idx = B.gp_idx;
+            X.slot_bin = B.slot_bin;
+            X.dof_idx = B.dof_idx;
+            X.row_bin = B.row_bin;
+            X.w_slot = B.w_slot;
+            X.slot_of_gp = B.slot_of_gp;
+        }
+    }
+    k_bin_fill3<<<dim3(gx, 3), kThreads, 0, s>>>(P, m->gp, n_gp, m->node_box, m->dof_node, n_dof);
+    note_launch(m);
+    {
+        auto pow2 = [](int v) { int p = 1; while (p < v) p <<= 1; return p; };
+        const size_t sh = sizeof(unsigned long long) * pow2(std::max(max_gp, max_dof));
+        k_bin_sort3<<<dim3(nb_max, 3, 2), 256, sh, s>>>(P);
+        note_launch(m);
+    }
+    k_bin_slots3<<<dim3(grid_for(n_gp), 3), kThreads, 0, s>>>(P, m->gw, n_gp);
+    note_launch(m);
+
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
         const int nb = B.n_bins;
-        const BinGeom G = Gs[axis];
-        B.n_tmpl = B.h_dof_off[nb];
-        B.max_dof = 0;
-        B.max_gp = 0;
-        for (int b = 0; b < nb; b++) {
-            B.max_dof = std::max(B.max_dof, B.h_dof_off[b + 1] - B.h_dof_off[b]);
-            B.max_gp = std::max(B.max_gp, B.h_gp_off[b + 1] - B.h_gp_off[b]);
-        }
-        if (B.max_dof > kMaxBinItems || B.max_gp > kMaxBinItems)
-            return set_error(FEM3_E_ARG, "a transverse bin holds more than 4096 dofs or Gauss "
-                                         "points; lower fem3_options.bin_scale");
-
-        unsigned long long *gkeys, *dkeys;
-        FEM3_TRY(dev_alloc_t(m, &gkeys, n_gp));
-        FEM3_TRY(dev_alloc_t(m, &dkeys, B.n_tmpl));
-        FEM3_TRY(dev_alloc_t(m, &B.gp_idx, n_gp));
-        FEM3_TRY(dev_alloc_t(m, &B.slot_bin, n_gp));
-        FEM3_TRY(dev_alloc_t(m, &B.dof_idx, B.n_tmpl));
-        double lo = m->lo[axis], span = std::max(m->hi[axis] - m->lo[axis], 1e-300);
-        k_gp_bin_fill<<<grid_for(n_gp), kThreads, 0, s>>>(m->gp, n_gp, axis, lo, span, gbin[axis],
-                                                          B.gp_off, gcur[axis], gkeys);
-        note_launch(m);
-        k_dof_bin_fill<<<grid_for(n_dof), kThreads, 0, s>>>(m->node_box, m->dof_node, n_dof, G,
-                                                            B.dof_off, dcur[axis], dkeys);
-        note_launch(m);
-        {
-            auto pow2 = [](int v) { int p = 1; while (p < v) p <<= 1; return p; };
-            const size_t shg = sizeof(unsigned long long) * pow2(std::max(1, B.max_gp));
-            const size_t shd = sizeof(unsigned long long) * pow2(std::max(1, B.max_dof));
-            k_bin_sort<<<nb, 256, shg, s>>>(B.gp_off, gkeys, B.gp_idx, B.slot_bin);
-            note_launch(m);
-            k_bin_sort<<<nb, 256, shd, s>>>(B.dof_off, dkeys, B.dof_idx, nullptr);
-            note_launch(m);
-        }
-        FEM3_TRY(dev_alloc_t(m, &B.row_bin, std::max<int64_t>(1, B.n_tmpl)));
-        if (B.n_tmpl > 0) {
-            k_row_bin<<<nb, 256, 0, s>>>(B.dof_off, nb, B.row_bin);
-            note_launch(m);
-        }
-        FEM3_TRY(dev_alloc_t(m, &B.w_slot, n_gp));
-        k_slot_weights<<<grid_for(n_gp), kThreads, 0, s>>>(B.gp_idx, m->gw, n_gp, B.w_slot);
-        note_launch(m);
-        FEM3_TRY(dev_alloc_t(m, &B.slot_of_gp, n_gp));
-        k_invert_slots<<<grid_for(n_gp), kThreads, 0, s>>>(B.gp_idx, n_gp, B.slot_of_gp);
-        note_launch(m);
-
         // table layout: block of bin b is [D_b][ld_b], ld_b = Gauss points rounded up to 8
         B.h_tab_off.resize(nb);
         B.h_tab_ld.resize(nb);
