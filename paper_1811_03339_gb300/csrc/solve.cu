@@ -344,7 +344,7 @@ __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, TF 
 // all zero at launch.
 // ---------------------------------------------------------------------------------
 constexpr int kTileLd = NB + 4;
-constexpr int kCholTilesSmem = 3 * NB * kTileLd;   // elements of dynamic shared memory
+constexpr int kCholTilesSmem = 4 * NB * kTileLd;   // elements of dynamic shared memory
 
 __device__ __forceinline__ int tile_id(int i, int j) { return i * (i + 1) / 2 + j; }
 
@@ -362,23 +362,36 @@ __device__ __forceinline__ bool wait_tile(const int *f, int *abort_w, int32_t *e
     return true;
 }
 
-// dst[c][r] = src[r * ld + c] (r < rows, else 0), c < 64; 512 threads, 8 columns each.
-// L2 loads: the tile was written by another CTA of the same launch.
+// Tile loads, 512 threads: warp w reads rows 4w .. 4w + 3, lanes over the columns (each
+// load instruction covers 32 consecutive entries of one row), element e = 2k + h of a
+// thread is (row 4w + k, column lane + 32h).  L2 loads: the tile was written by another CTA
+// of the same launch.
+template <class TF>
+__device__ __forceinline__ void tile_regs(const TF *src, int64_t ld, int64_t rows, TF v[8]) {
+    const int lane = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 4;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+            v[2 * k + h] = r0 + k < rows ? __ldcg(src + (int64_t)(r0 + k) * ld + lane + 32 * h)
+                                         : TF(0);
+}
+// dst[c][r] = the loaded tile's entry (r, c)
+template <class TF>
+__device__ __forceinline__ void tile_store_T(const TF v[8], TF (*dst)[kTileLd]) {
+    const int lane = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * 4;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int h = 0; h < 2; h++) dst[lane + 32 * h][r0 + k] = v[2 * k + h];
+}
+// dst[c][r] = src[r * ld + c] (r < rows, else 0), c < 64
 template <class TF>
 __device__ __forceinline__ void load_tile_T(const TF *src, int64_t ld, int64_t rows,
                                             TF (*dst)[kTileLd]) {
-    const int r = threadIdx.x & 63, c0 = (threadIdx.x >> 6) * 8;
     TF v[8];
-    if (r < rows) {
-        const TF *p = src + (int64_t)r * ld + c0;
-#pragma unroll
-        for (int e = 0; e < 8; e++) v[e] = __ldcg(p + e);
-    } else {
-#pragma unroll
-        for (int e = 0; e < 8; e++) v[e] = TF(0);
-    }
-#pragma unroll
-    for (int e = 0; e < 8; e++) dst[c0 + e][r] = v[e];
+    tile_regs<TF>(src, ld, rows, v);
+    tile_store_T<TF>(v, dst);
 }
 
 // acc[p][q] += sgn * sum_c bi[c][ty*2+p] bj[c][tx*4+q] (operands in transposed layout).
@@ -522,7 +535,7 @@ __global__ void __launch_bounds__(512, 1) k_chol_tiles(TF *A, int64_t n, int nbl
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TF(*b0)[kTileLd] = reinterpret_cast<TF(*)[kTileLd]>(smem_raw);
     TF(*b1)[kTileLd] = b0 + NB;
-    __shared__ int s_task, s_ok;
+    __shared__ int s_task, s_ok, s_fa, s_fb, s_pa[2], s_pb[2];
     const int ntask = nblk * (nblk + 1) / 2;
     int *F = flags, *U = flags + ntask, *ticket = flags + 2 * ntask, *abort_w = ticket + 1;
     if (blockIdx.x == 0) {
@@ -543,18 +556,40 @@ __global__ void __launch_bounds__(512, 1) k_chol_tiles(TF *A, int64_t n, int nbl
         const int kmax = i == j ? max(j - 1, 0) : j;   // the chain applies k = j - 1 to (j, j)
         TF acc[2][4];
         load_acc<TF>(A, n, r0, c0, false, acc, tx, ty);
+        // Updates k = 0 .. kmax-1, pipelined: the tiles L_ik, L_jk of update k + 1 are
+        // loaded into registers while update k's product runs (when their flags are
+        // already set; otherwise after it, with a blocking wait), and stored into the other
+        // pair of shared tiles.  Threads 0 and 32 read the two flags at the same time.
+        TF va[8], vb[8];
+        bool have = false;   // va / vb hold the tiles of update k
         for (int k = 0; k < kmax; k++) {
-            if (tid == 0)
-                s_ok = wait_tile(&F[tile_id(i, k)], abort_w, err) &&
-                       wait_tile(&F[tile_id(j, k)], abort_w, err);
-            __syncthreads();
-            if (!s_ok) return;
-            load_tile_T<TF>(A + r0 * n + (int64_t)k * NB, n, rows_i, b0);
-            if (i != j) load_tile_T<TF>(A + c0 * n + (int64_t)k * NB, n, n - c0, b1);
-            __syncthreads();
-            tile_gemm_T<TF, true>(acc, b0, i == j ? b0 : b1, tx, ty);
-            __syncthreads();
+            TF(*ta)[kTileLd] = b0 + (k & 1) * 2 * NB;
+            TF(*tb)[kTileLd] = ta + NB;
+            if (!have) {
+                if (tid == 0) s_fa = wait_tile(&F[tile_id(i, k)], abort_w, err);
+                if (tid == 32) s_fb = wait_tile(&F[tile_id(j, k)], abort_w, err);
+                __syncthreads();
+                if (!(s_fa && s_fb)) return;
+                tile_regs<TF>(A + r0 * n + (int64_t)k * NB, n, rows_i, va);
+                if (i != j) tile_regs<TF>(A + c0 * n + (int64_t)k * NB, n, n - c0, vb);
+            }
+            tile_store_T<TF>(va, ta);
+            if (i != j) tile_store_T<TF>(vb, tb);
+            const int q = (k + 1) & 1;
+            if (k + 1 < kmax) {   // a look at update k + 1's flags, without waiting
+                if (tid == 0) s_pa[q] = ld_acquire_gpu(&F[tile_id(i, k + 1)]) != 0;
+                if (tid == 32) s_pb[q] = ld_acquire_gpu(&F[tile_id(j, k + 1)]) != 0;
+            }
+            __syncthreads();   // update k's tiles stored (the pair written two updates ago
+                               // is no longer read); update k + 1's flags seen
+            have = k + 1 < kmax && s_pa[q] && s_pb[q];
+            if (have) {
+                tile_regs<TF>(A + r0 * n + (int64_t)(k + 1) * NB, n, rows_i, va);
+                if (i != j) tile_regs<TF>(A + c0 * n + (int64_t)(k + 1) * NB, n, n - c0, vb);
+            }
+            tile_gemm_T<TF, true>(acc, ta, i == j ? ta : tb, tx, ty);
         }
+        __syncthreads();   // the last product is done before the shared tiles are reused
         if (i <= j + 1) {
             // diagonal or sub-diagonal tile: the chain finishes it
             store_acc<TF>(A, n, r0, c0, acc, tx, ty);
