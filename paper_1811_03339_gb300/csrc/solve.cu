@@ -189,13 +189,13 @@ __device__ __forceinline__ void chol_inv16(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1],
 // and update diagonal block p + 1, which releases warp 0 for block p + 1 at once, and
 // (b) meanwhile solve the rest of panel p, form the inverse's block row p
 // ((L^{-1})_pJ = -L_pp^{-1} sum_K L_pK (L^{-1})_KJ) and apply the rest of the trailing update.
-// a_s holds the block (rows and columns >= nb padded with the identity) and receives L;
-// x_s receives L^{-1} (zero above the diagonal on return).  L goes to A (rows/columns
-// k0 .. k0 + nb), L^{-1} to Linv (row-major 64 x 64); a non-positive pivot records 1 +
-// its global column.  Needs exactly 512 threads, all of the CTA.
+// a_s holds the block (rows and columns >= nb padded with the identity) and receives L
+// (lower triangle); x_s receives L^{-1} (zero above the diagonal on return); the caller
+// stores them.  A non-positive pivot records 1 + its global column (k0 + local).  Needs
+// exactly 512 threads, all of the CTA; ends with a barrier.
 template <class TF>
-__device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, TF *A, int64_t n,
-                               int64_t k0, TF *Linv, int32_t *err) {
+__device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, int64_t k0,
+                               int32_t *err) {
     constexpr int NT = 512, NU = NT - 32, NP = NB / PB;
     __shared__ __align__(16) TF lt[2][PB][PB + 4];     // lt[p & 1][k][c] = L_pp^{-1}[c][k]
     __shared__ __align__(16) TF pant[PB][NB + 4];      // pant[k][r] = L[r][P + k], r >= P + 16
@@ -318,10 +318,9 @@ __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, TF 
     __syncthreads();
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         const int i = e >> 6, c = e & 63;
-        if (i < nb && c < nb) A[(k0 + i) * n + k0 + c] = c <= i ? a_s[i][c] : TF(0);
-        Linv[e] = c <= i ? x_s[i][c] : TF(0);
-        if (c > i) x_s[i][c] = TF(0);   // x_s = L^{-1} in full for callers that keep it
+        if (c > i) x_s[i][c] = TF(0);   // x_s = L^{-1} in full
     }
+    __syncthreads();
 }
 
 
@@ -357,7 +356,7 @@ __device__ __forceinline__ bool wait_tile(const int *f, int *abort_w, int32_t *e
             atomicExch(abort_w, 1);
             return false;
         }
-        if (spins > 64) __nanosleep(32);
+        if (spins > 64) __nanosleep(128);   // 150 pollers on one L2 line slow its owner
     }
     return true;
 }
@@ -461,71 +460,89 @@ __device__ void chol_chain(TF *A, int64_t n, int nblk, TF *dinv, int *F, int *U,
                            int32_t *err, unsigned char *smem_raw) {
     TF(*b0)[kTileLd] = reinterpret_cast<TF(*)[kTileLd]>(smem_raw);
     TF(*b1)[kTileLd] = b0 + NB;
-    TF(*xt)[kTileLd] = b1 + NB;   // L_{j,j-1}^T of the previous step
+    TF(*xt)[kTileLd] = b1 + NB;   // L_{j+1,j}^T (from the sub-solve, for the next update)
+    TF(*at)[kTileLd] = xt + NB;   // A_{j+1,j}^T as the sub-solve reads it
     TF(*a_s)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(&b0[0][0]);
     TF(*x_s)[NB + 1] = reinterpret_cast<TF(*)[NB + 1]>(&b1[0][0]);
-    __shared__ int s_ok;
+    __shared__ int s_ok, s_pre;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    TF acc[2][4];   // the diagonal tile A~_jj of the coming step (loaded one step ahead)
+    if (tid == 0) s_ok = wait_tile(&U[tile_id(0, 0)], abort_w, err);
+    __syncthreads();
+    if (!s_ok) return;
+    load_acc<TF>(A, n, 0, 0, true, acc, tx, ty);
     for (int j = 0; j < nblk; j++) {
-        const int64_t c0 = (int64_t)j * NB;
-        if (tid == 0) s_ok = wait_tile(&U[tile_id(j, j)], abort_w, err);
-        __syncthreads();
-        if (!s_ok) return;
-        TF acc[2][4];
-        load_acc<TF>(A, n, c0, c0, true, acc, tx, ty);
-        if (j > 0) tile_gemm_T<TF, true>(acc, xt, xt, tx, ty);
+        const int64_t c0 = (int64_t)j * NB, r0 = c0 + NB;
+        const bool next = j + 1 < nblk;
+        if (j > 0) tile_gemm_T<TF, true>(acc, xt, xt, tx, ty);   // the update k = j - 1
 #pragma unroll
         for (int p = 0; p < 2; p++)
 #pragma unroll
             for (int q = 0; q < 4; q++) a_s[ty * 2 + p][tx * 4 + q] = acc[p][q];
         __syncthreads();
-        potrf_inv_smem<TF>(a_s, x_s, (int)min((int64_t)NB, n - c0), A, n, c0,
-                           dinv + (int64_t)j * NB * NB, err);
-        publish(&F[tile_id(j, j)]);
-        if (j + 1 >= nblk) break;
-        // L_{j+1,j} = A_{j+1,j} L_jj^{-T}, computed transposed: X^T = L_jj^{-1} A_{j+1,j}^T
-        const int64_t r0 = c0 + NB;
-        if (tid == 0) s_ok = wait_tile(&U[tile_id(j + 1, j)], abort_w, err);
-        __syncthreads();
-        if (!s_ok) return;
-        load_tile_T<TF>(A + r0 * n + c0, n, n - r0, b0);   // b0[k][r] = A_{j+1,j}[r][k]
-        __syncthreads();
-        TF o[2][4];
+        potrf_inv_smem<TF>(a_s, x_s, (int)min((int64_t)NB, n - c0), c0, err);
+        if (next) {
+            // L_{j+1,j} = A~_{j+1,j} L_jj^{-T}, computed transposed: xt = L_jj^{-1} A~_{j+1,j}^T
+            if (tid == 0) s_ok = wait_tile(&U[tile_id(j + 1, j)], abort_w, err);
+            __syncthreads();
+            if (!s_ok) return;
+            load_tile_T<TF>(A + r0 * n + c0, n, n - r0, at);   // at[k][r] = A_{j+1,j}[r][k]
+            __syncthreads();
+            TF o[2][4];
 #pragma unroll
-        for (int p = 0; p < 2; p++)
+            for (int p = 0; p < 2; p++)
 #pragma unroll
-            for (int q = 0; q < 4; q++) o[p][q] = TF(0);
+                for (int q = 0; q < 4; q++) o[p][q] = TF(0);
 #pragma unroll 8
-        for (int k = 0; k < NB; k++) {
-            TF v[4];
-            lds4<TF>(&b0[k][tx * 4], v);
-            const TF u0 = x_s[ty * 2][k], u1 = x_s[ty * 2 + 1][k];
+            for (int k = 0; k < NB; k++) {
+                TF v[4];
+                lds4<TF>(&at[k][tx * 4], v);
+                const TF u0 = x_s[ty * 2][k], u1 = x_s[ty * 2 + 1][k];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                o[0][q] = fma(u0, v[q], o[0][q]);
-                o[1][q] = fma(u1, v[q], o[1][q]);
+                for (int q = 0; q < 4; q++) {
+                    o[0][q] = fma(u0, v[q], o[0][q]);
+                    o[1][q] = fma(u1, v[q], o[1][q]);
+                }
             }
-        }
-        // o[p][q] = L_{j+1,j}[tx*4+q][ty*2+p]
+            // o[p][q] = L_{j+1,j}[tx*4+q][ty*2+p]; xt was last read by this step's update
 #pragma unroll
-        for (int p = 0; p < 2; p++) {
-            TF *dst = &xt[ty * 2 + p][tx * 4];
-            if constexpr (sizeof(TF) == 4) {
-                *reinterpret_cast<float4 *>(dst) = make_float4(o[p][0], o[p][1], o[p][2], o[p][3]);
-            } else {
-                *reinterpret_cast<double2 *>(dst) = make_double2(o[p][0], o[p][1]);
-                *reinterpret_cast<double2 *>(dst + 2) = make_double2(o[p][2], o[p][3]);
+            for (int p = 0; p < 2; p++) {
+                TF *dst = &xt[ty * 2 + p][tx * 4];
+                if constexpr (sizeof(TF) == 4) {
+                    *reinterpret_cast<float4 *>(dst) = make_float4(o[p][0], o[p][1], o[p][2], o[p][3]);
+                } else {
+                    *reinterpret_cast<double2 *>(dst) = make_double2(o[p][0], o[p][1]);
+                    *reinterpret_cast<double2 *>(dst + 2) = make_double2(o[p][2], o[p][3]);
+                }
             }
+            // the next diagonal tile goes into registers now if it is ready.  It is not
+            // waited for here: its task may be queued behind tasks of this column that
+            // wait for F(j, j), so the wait comes after the publication below.
+            if (tid == 0) s_pre = ld_acquire_gpu(&U[tile_id(j + 1, j + 1)]) != 0;
         }
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int64_t r = r0 + tx * 4 + q;
-            if (r < n) {
-                A[r * n + c0 + ty * 2] = o[0][q];
-                A[r * n + c0 + ty * 2 + 1] = o[1][q];
-            }
+        __syncthreads();   // xt complete; the next diagonal tile's flag seen
+        const bool pre = next && s_pre;
+        if (pre) load_acc<TF>(A, n, r0, r0, true, acc, tx, ty);
+        // L_jj into A, L_jj^{-1} into dinv, L_{j+1,j} into A: rows of 64, coalesced
+        const int nb = (int)min((int64_t)NB, n - c0);
+        TF *Lj = dinv + (int64_t)j * NB * NB;
+        for (int e = tid; e < NB * NB; e += blockDim.x) {
+            const int i = e >> 6, c = e & 63;
+            if (i < nb && c < nb) A[(c0 + i) * n + c0 + c] = c <= i ? a_s[i][c] : TF(0);
+            Lj[e] = x_s[i][c];
+            if (next && r0 + i < n) A[(r0 + i) * n + c0 + c] = xt[c][i];
         }
-        publish(&F[tile_id(j + 1, j)]);
+        __syncthreads();   // every store is issued before the (cumulative) releases
+        if (tid == 0) {
+            st_release_gpu(&F[tile_id(j, j)], 1);
+            if (next) st_release_gpu(&F[tile_id(j + 1, j)], 1);
+        }
+        if (next && !pre) {
+            if (tid == 0) s_ok = wait_tile(&U[tile_id(j + 1, j + 1)], abort_w, err);
+            __syncthreads();
+            if (!s_ok) return;
+            load_acc<TF>(A, n, r0, r0, true, acc, tx, ty);
+        }
     }
 }
 
