@@ -167,7 +167,9 @@ __global__ void __launch_bounds__(256) k_split_ops(
     const int g0 = gp_off[b], G = gp_off[b + 1] - g0;
     const int64_t src = tab_off[b] + (int64_t)c * tab_ld[b];
     const int64_t dst = row * (int64_t)Kp;
-    const int kend = Lhi ? Kp : G;
+    // the GEMM reads a bin's operands up to G rounded to one 128-byte row (kbk Gauss points)
+    const int kbk = 128 / (int)sizeof(OT);
+    const int kend = Lhi ? min(Kp, (G + kbk - 1) / kbk * kbk) : G;
     for (int k = lane; k < kend; k += 32) {
         OT lh = OT(0.f), ll = OT(0.f), rh = OT(0.f), rl = OT(0.f);
         if (k < G) {
