@@ -45,8 +45,8 @@ def _peaks():
 # DRAM bytes (read + write) of one k_walk_tables launch from the ncu capture summarised in
 # profiles/k_walk_tables_cube16_jitter.md, valid only for the kernel source it was taken
 # on (sha256 of csrc/walk.cu); otherwise the traffic is reported as unknown.
-WALK_TRAFFIC = {"walk_cu_sha256": "ac49b5f54c2396a1818e20aa53087dcf8b0358013716575252b590df22f20711",
-                "bytes_per_launch": 211476992 + 107675392, "segments_per_launch": 16099980}
+WALK_TRAFFIC = {"walk_cu_sha256": "8d4a3a9a9044db4188912077c2427c5934060a2d9df0bed704449ae17488e2ff",
+                "bytes_per_launch": 160922368 + 579908096, "segments_per_launch": 16099980}
 
 
 def _walk_traffic(segs_per_launch):
