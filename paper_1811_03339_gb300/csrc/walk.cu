@@ -48,6 +48,11 @@ __device__ __forceinline__ long long ord_key(double v) {
 __device__ __forceinline__ double key_double(long long k) {
     return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
 }
+// r < +inf (false for +inf and NaN), on the integer pipe
+__device__ __forceinline__ bool below_inf(double r) {
+    const long long b = __double_as_longlong(r);
+    return b != 0x7FF0000000000000LL && (b & 0x7FFFFFFFFFFFFFFFLL) <= 0x7FF0000000000000LL;
+}
 // lambda <= eps for every non-NaN lambda, on the integer pipe: IEEE bit patterns of
 // non-negative doubles are ordered like the values, negative ones are negative integers
 __device__ __forceinline__ bool le_eps(double lam) {
@@ -177,10 +182,15 @@ __device__ __forceinline__ double exit_step(const WalkGeom &W, const LineF &X, i
         const double bk = fma(c.y, x2, fma(c.x, x1, fma(a.y, x0, a.x)));
         const double iv = W.inv[12 * (int64_t)t + 4 * axis + ks];
         const double rmax = dir > 0 ? -(bk * iv) : bk * iv;
-        const double gk = axis == 0 ? a.y : (axis == 1 ? c.x : c.y);
-        const double lam = fma(dir > 0 ? rmax : -rmax, gk, bk);
-        zmask = zm | (le_eps(lam) ? 1 << ks : 0);
-        return rmax;
+        // lambda_k* at r_max is b - fl(b fl(1/g)) g with one fused rounding: at most 2^-52 |b|,
+        // below eps_lambda for |b| <= 4000 (an integer test); a larger |b| is tested in FP64
+        bool zk = (__double_as_longlong(bk) & 0x7fffffffffffffffLL) <= 0x40AF400000000000LL;
+        if (!zk) {
+            const double gk = axis == 0 ? a.y : (axis == 1 ? c.x : c.y);
+            zk = le_eps(fma(dir > 0 ? rmax : -rmax, gk, bk));
+        }
+        zmask = zm | (zk ? 1 << ks : 0);
+        return rmax;   // finite: b and 1/g are
     }
     double b[4];
     const double rmax = tet_rmax(W, t, axis, dir, x0, x1, x2, b);
@@ -373,7 +383,7 @@ __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
         int zmask;
         const double rmax = exit_step(W, X, t, axis, dir, x0, x1, x2, zmask);
         int32_t nx = -2;
-        if (rmax < INFINITY) {
+        if (below_inf(rmax)) {
             nx = next_tet(W, t, axis, dir, x0, x1, x2, zmask, rmax);
             if (rmax - r_prev > W.eps_r) {
                 // table part in double-float FP32: c = coef (rmax^p - r_prev^p)
@@ -578,7 +588,7 @@ __global__ void k_walk_paths(WalkGeom W, int axis, int dir, const int64_t *__res
     for (int step = 0; step < W.max_steps; step++) {
         int zmask;
         const double rmax = exit_step(W, X, t, axis, dir, x0, x1, x2, zmask);
-        if (!(rmax < INFINITY)) break;
+        if (!below_inf(rmax)) break;
         if (rmax - r_prev > W.eps_r) {
             if (nseg >= cap) break;
             tet_out[l * cap + nseg] = t;
