@@ -15,8 +15,8 @@
 //
 // Tiles.  One CTA computes the 128 x N block (N <= 256) of X for rows
 // [128 mt, 128 mt + 128) and columns [256 nt, 256 nt + N) of one bin.  K steps of
-// 128 bytes (one swizzle row: 32 TF32 or 64 BF16 Gauss points) go through a 2-stage TMA
-// pipeline; each K step is four MMAs of 32 bytes (K = 8 TF32 or 16 BF16) per product.
+// 128 bytes (one swizzle row: 32 TF32 or 64 BF16 Gauss points) are loaded by TMA into one
+// stage; each K step is four MMAs of 32 bytes (K = 8 TF32 or 16 BF16) per product.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -30,7 +30,11 @@ namespace fem3 {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 256, kStages = 2;
+// one pipeline stage: the bins' K loops are short (3 to 5 steps), and a 96 KB stage lets two
+// CTAs share an SM, each one's loads and epilogue overlapping the other's work
+constexpr int kBM = 128, kBN = 256, kStages = 1;
+constexpr int kBoxRows = 128;                  // rows of one TMA box
+constexpr uint32_t kBoxBytes = kBoxRows * 128; // 16 KB
 constexpr int kRowBytes = 128;                 // one K step: one 128-byte swizzle row
 constexpr uint32_t kTileA = kBM * kRowBytes;   // 16 KB
 constexpr uint32_t kTileB = kBN * kRowBytes;   // 32 KB
@@ -201,7 +205,7 @@ struct TcWork {
 };
 
 template <bool BF16>
-__global__ void __launch_bounds__(128, 1) k_contract_tc(
+__global__ void __launch_bounds__(128, 2) k_contract_tc(
     const __grid_constant__ CUtensorMap mLhi, const __grid_constant__ CUtensorMap mLlo,
     const __grid_constant__ CUtensorMap mRhi, const __grid_constant__ CUtensorMap mRlo,
     const int4 *__restrict__ work, const int32_t *__restrict__ dof_off,
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(256));
+                     "r"(kBN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -258,16 +262,17 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(
             }
             uint8_t *st = base + s * kStageBytes;
             const uint32_t bar = full0 + 8 * s;
-            const int nbox = N > kBN / 2 ? 2 : 1;          // 128-row boxes of each B operand
-            mbar_expect_tx(bar, 2 * kTileA + 2 * nbox * (kTileB / 2));
+            const int nbox = (N + kBoxRows - 1) / kBoxRows;   // 128-row boxes of each B operand
+            mbar_expect_tx(bar, 2 * kTileA + 2 * nbox * kBoxBytes);
             const int x = k * kBK;
             const int ya = row0 + mt * kBM, yb = row0 + nt * kBN;
             tma_load_2d(smem_u32(st), &mLhi, x, ya, bar);
             tma_load_2d(smem_u32(st + kTileA), &mLlo, x, ya, bar);
             for (int h = 0; h < nbox; h++) {
-                tma_load_2d(smem_u32(st + 2 * kTileA + h * (kTileB / 2)), &mRhi, x, yb + h * (kBN / 2), bar);
-                tma_load_2d(smem_u32(st + 2 * kTileA + kTileB + h * (kTileB / 2)), &mRlo, x,
-                            yb + h * (kBN / 2), bar);
+                tma_load_2d(smem_u32(st + 2 * kTileA + h * kBoxBytes), &mRhi, x, yb + h * kBoxRows,
+                            bar);
+                tma_load_2d(smem_u32(st + 2 * kTileA + kTileB + h * kBoxBytes), &mRlo, x,
+                            yb + h * kBoxRows, bar);
             }
         }
     } else if (warp == 1 && lane == 0 && nk > 0) {
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(128, 1) k_contract_tc(
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 2)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN));
 }
 
 // ------------------------------- host side ----------------------------------------
