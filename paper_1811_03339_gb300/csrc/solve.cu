@@ -989,9 +989,9 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve_chain(
         solve_chain<TF, NR>(n, nblk, Y, nrhs, backward != 0, Gop, Z, Yf, Pf, abort_w, err, smem_raw);
         return;
     }
-    TF *yb = reinterpret_cast<TF *>(smem_raw);   // [64][NR] dependency block, then b - S
-    TF *red = yb + NB * NR;                      // [8][64][NR + 1]
-    __shared__ int s_task, s_ok;
+    TF *yb = reinterpret_cast<TF *>(smem_raw);   // [2][64][NR] dependency blocks, then b - S
+    TF *red = yb + 2 * NB * NR;                  // [8][64][NR + 1]
+    __shared__ int s_task, s_ok, s_pre[2];
     const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
     const bool bw = backward != 0;
     for (;;) {
@@ -1003,26 +1003,48 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve_chain(
         TF part[NR];
 #pragma unroll
         for (int v = 0; v < NR; v++) part[v] = TF(0);
-        TF tc[8];
-        if (s - D - 1 >= 0) load_coef<TF>(L, n, j, solve_blk(0, nblk, bw), bw, r, g, tc);
-        for (int sd = 0; sd <= s - D - 1; sd++) {
-            if (tid == 0) s_ok = wait_flag(&Yf[sd], abort_w, err);
-            __syncthreads();
-            if (!s_ok) return;
+        // Dependencies sd = 0 .. last, pipelined: the solved block y_{sd+1} is loaded into
+        // registers while the product with y_sd runs (when its flag is already set;
+        // otherwise after it, with a blocking wait) and stored into the other shared buffer.
+        constexpr int PY = (NB * NR + kSolveThreads - 1) / kSolveThreads;   // y values / thread
+        const int last = s - D - 1;
+        auto load_y = [&](int sd, TF yv[PY]) {
             const int jd = solve_blk(sd, nblk, bw);
-            for (int e = tid; e < NB * NR; e += kSolveThreads) {
+#pragma unroll
+            for (int k = 0; k < PY; k++) {
+                const int e = tid + k * kSolveThreads;
                 const int c = e / NR, v = e % NR;
                 const int64_t rr = (int64_t)jd * NB + c;
-                yb[e] = (rr < n && v < nrhs) ? __ldcg(&Y[rr + (int64_t)v * n]) : TF(0);
+                yv[k] = (e < NB * NR && rr < n && v < nrhs) ? __ldcg(&Y[rr + (int64_t)v * n]) : TF(0);
             }
-            __syncthreads();
+        };
+        TF tc[8], yv[PY];
+        bool have = false;   // yv holds y_sd
+        if (last >= 0) load_coef<TF>(L, n, j, solve_blk(0, nblk, bw), bw, r, g, tc);
+        for (int sd = 0; sd <= last; sd++) {
+            TF *ybs = yb + (sd & 1) * NB * NR;
+            if (!have) {
+                if (tid == 0) s_ok = wait_flag(&Yf[sd], abort_w, err);
+                __syncthreads();
+                if (!s_ok) return;
+                load_y(sd, yv);
+            }
+#pragma unroll
+            for (int k = 0; k < PY; k++)
+                if (tid + k * kSolveThreads < NB * NR) ybs[tid + k * kSolveThreads] = yv[k];
+            const int q = (sd + 1) & 1;
+            if (tid == 0 && sd + 1 <= last) s_pre[q] = ld_acquire_gpu(&Yf[sd + 1]) != 0;
+            __syncthreads();   // y_sd stored (the buffer written two dependencies ago is no
+                               // longer read); y_{sd+1}'s flag seen
+            have = sd + 1 <= last && s_pre[q];
+            if (have) load_y(sd + 1, yv);
             TF tn[8];
-            if (sd + 1 <= s - D - 1) load_coef<TF>(L, n, j, solve_blk(sd + 1, nblk, bw), bw, r, g, tn);
-            chunk_gemv<TF, NR>(tc, yb, g, part);
+            if (sd + 1 <= last) load_coef<TF>(L, n, j, solve_blk(sd + 1, nblk, bw), bw, r, g, tn);
+            chunk_gemv<TF, NR>(tc, ybs, g, part);
 #pragma unroll
             for (int e = 0; e < 8; e++) tc[e] = tn[e];
-            __syncthreads();   // yb is refilled by the next dependency
         }
+        __syncthreads();   // the last product is done before yb is reused
         // t = b_s - S_s into yb, then z_s = Dm_j t
         store_partial<TF, NR>(red, r, g, part);
         __syncthreads();
