@@ -433,7 +433,9 @@ __global__ void k_bin_count3(const __grid_constant__ BinAxes P, const double *__
         const int i1 = bin_coord(gp[3 * i + G.c1], G.org1, G.width, G.nb1);
         const int b = i0 + G.nb0 * i1;
         X.gbin[i] = b;
-        atomicAdd(&X.gcount[b], 1);
+        // lanes of a warp (neighbouring Gauss points) mostly share a bin: one atomic per bin
+        const unsigned grp = __match_any_sync(__activemask(), b);
+        if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&X.gcount[b], __popc(grp));
     }
     if (i < n_dof) {
         const double *bx = box + 6 * (int64_t)dof_node[i];
@@ -476,7 +478,12 @@ __global__ void k_bin_fill3(const __grid_constant__ BinAxes P, const double *__r
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n_gp) {
         const int b = X.gbin[i];
-        const int32_t pos = atomicAdd(&X.gcur[b], 1);
+        // one atomic per bin and warp; lanes take consecutive places (the bin is sorted later)
+        const unsigned grp = __match_any_sync(__activemask(), b);
+        const int lead = __ffs(grp) - 1, lane = threadIdx.x & 31;
+        int32_t base = 0;
+        if (lane == lead) base = atomicAdd(&X.gcur[b], __popc(grp));
+        const int32_t pos = __shfl_sync(grp, base, lead) + __popc(grp & ((1u << lane) - 1u));
         // sort key: position along the axis (30-bit quantised), then the Gauss point id
         double u = (gp[3 * i + axis] - X.lo) / X.span;
         u = u < 0 ? 0 : (u > 1 ? 1 : u);
@@ -585,7 +592,8 @@ int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
     unsigned long long *box = reinterpret_cast<unsigned long long *>(m->node_box);
     k_box_init<<<grid_for(6 * N), kThreads, 0, s>>>(box, N);
     note_launch(m);
-    k_tet_geom<<<grid_for(T), kThreads, 0, s>>>(verts_d, tets_d, T, N, qa, qb, m->M, m->inv,
+    // 64-thread blocks: one long FP64 thread per tet, spread over every SM
+    k_tet_geom<<<grid_for(T, 64), 64, 0, s>>>(verts_d, tets_d, T, N, qa, qb, m->M, m->inv,
                                                  m->recf, m->vol, m->gp, m->gw, box, m->err);
     note_launch(m);
     k_box_decode<<<grid_for(6 * N), kThreads, 0, s>>>(box, 6 * N);
