@@ -259,6 +259,7 @@ def run_ours(args):
     stages = m.stage_ms()
     m.sync()
     cnt = m.counters()
+    tile_n, _ = m.tc_tile()   # tensor-core tile width chosen by the tuner (0: no TC form)
     ir_iters, ir_resid = m.iters, m.resid
     m.free()
     m64, u64 = step("fp64", profile=True, keep=True)
@@ -381,7 +382,8 @@ def run_ours(args):
             "refinement": {"iterations": ir_iters, "final_rel_residual": ir_resid, "tol": args.tol},
             "table_bytes": cnt["table_bytes"],
             "contraction": {"bin_dense_gflop": ctr_flops / 1e9,
-                            "gflops": ctr_flops / (stages[3] * 1e-3) / 1e9 if stages[3] > 0 else None},
+                            "gflops": ctr_flops / (stages[3] * 1e-3) / 1e9 if stages[3] > 0 else None,
+                            "tile_n": tile_n or None},
             "peaks_source": src,
             "batch": batch,
         }

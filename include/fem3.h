@@ -75,6 +75,9 @@ typedef struct fem3_options {
     int32_t max_steps; /* cap on tets crossed by one walk; <= 0 selects
                           8 * n_tets^(1/3) + 64 */
     int32_t profile;   /* nonzero: record CUDA events around each stage (fem3_stage_ms) */
+    int32_t tc_tile;   /* tile width (columns) of the tensor-core contraction: 128 or 256;
+                          0 selects the tuner: the first contraction of a problem size class
+                          in the process times both and later ones use the faster */
 } fem3_options;
 
 /*
@@ -197,6 +200,11 @@ int fem3_stage_ms(fem3_mesh m, int stage, float *ms);
  * launched since upload.  Any output pointer may be NULL. */
 int fem3_counters(fem3_mesh m, int64_t *segments, double *contract_flops,
                   int64_t *table_bytes, int64_t *launches);
+
+/* Tile width (128 or 256 columns) of the last tensor-core contraction of this handle, 0 if
+ * none, and whether that contraction ran the tuner (1) or used a forced or cached width
+ * (0).  Any output pointer may be NULL. */
+int fem3_tc_tile(fem3_mesh m, int32_t *tile_n, int32_t *tuned);
 
 /*
  * Batches of meshes (not in the paper, which assembles one mesh at a time).

@@ -205,6 +205,11 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
     m->max_steps = (opt && opt->max_steps > 0) ? opt->max_steps
                                                : (int)(8.0 * cbrt((double)n_tets)) + 64;
     m->profile = opt && opt->profile;
+    m->tc_tile_opt = opt ? opt->tc_tile : 0;
+    if (m->tc_tile_opt != 0 && m->tc_tile_opt != 128 && m->tc_tile_opt != 256) {
+        delete m;
+        return set_error(FEM3_E_ARG, "tc_tile must be 0, 128 or 256");
+    }
     auto fail = [&](int code) {
         fem3_mesh_free(reinterpret_cast<fem3_mesh>(m));
         return code;
@@ -459,6 +464,14 @@ int fem3_stage_ms(fem3_mesh h, int stage, float *ms) {
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m || !ms || stage < 0 || stage > 6) return set_error(FEM3_E_ARG, "bad argument");
     *ms = m->stage_ms[stage];
+    return FEM3_OK;
+}
+
+int fem3_tc_tile(fem3_mesh h, int32_t *tile_n, int32_t *tuned) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m) return set_error(FEM3_E_ARG, "null mesh");
+    if (tile_n) *tile_n = m->tc_tile_used;
+    if (tuned) *tuned = m->tc_tuned ? 1 : 0;
     return FEM3_OK;
 }
 

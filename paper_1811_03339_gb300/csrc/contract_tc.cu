@@ -13,8 +13,9 @@
 // drops lo*lo and the rounding of lo: about 3 * 2^-22 relative per product for TF32
 // (11-bit significands), 3 * 2^-16 for BF16 (8-bit significands).
 //
-// Tiles.  One CTA computes the 128 x N block (N <= 256) of X for rows
-// [128 mt, 128 mt + 128) and columns [256 nt, 256 nt + N) of one bin.  K steps of
+// Tiles.  One CTA computes the 128 x N block (N <= BN) of X for rows
+// [128 mt, 128 mt + 128) and columns [BN nt, BN nt + N) of one bin, BN = 128 or 256 (the
+// tile width is tuned per problem size class at run time, see contract_tc).  K steps of
 // 128 bytes (one swizzle row: 32 TF32 or 64 BF16 Gauss points) are loaded by TMA into one
 // stage; each K step is four MMAs of 32 bytes (K = 8 TF32 or 16 BF16) per product.
 #include <cuda.h>
@@ -22,6 +23,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "fem3_impl.cuh"
@@ -30,16 +33,20 @@ namespace fem3 {
 
 namespace {
 
-// one pipeline stage: the bins' K loops are short (3 to 5 steps), and a 96 KB stage lets two
-// CTAs share an SM, each one's loads and epilogue overlapping the other's work
-constexpr int kBM = 128, kBN = 256, kStages = 1;
+// one pipeline stage: the bins' K loops are short (3 to 5 steps), and a 64 or 96 KB stage
+// lets three or two CTAs share an SM, each one's loads and epilogue overlapping the others'
+constexpr int kBM = 128, kStages = 1;
 constexpr int kBoxRows = 128;                  // rows of one TMA box
 constexpr uint32_t kBoxBytes = kBoxRows * 128; // 16 KB
 constexpr int kRowBytes = 128;                 // one K step: one 128-byte swizzle row
 constexpr uint32_t kTileA = kBM * kRowBytes;   // 16 KB
-constexpr uint32_t kTileB = kBN * kRowBytes;   // 32 KB
-constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;   // 96 KB
-constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+template <int BN> struct TcCfg {
+    static constexpr uint32_t kTileB = BN * kRowBytes;                 // 16 or 32 KB
+    static constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;   // 64 or 96 KB
+    static constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256;
+    static constexpr int kMinBlocks = BN == 128 ? 3 : 2;
+};
+constexpr int kTileWidths[2] = {256, 128};   // candidates of the tuner, index = tile slot
 constexpr int kWaitLimit = 1 << 22;
 
 // ------------------------------- PTX helpers -------------------------------------
@@ -204,8 +211,8 @@ struct TcWork {
     int bin, mt, nt, pad;
 };
 
-template <bool BF16>
-__global__ void __launch_bounds__(128, 2) k_contract_tc(
+template <bool BF16, int BN>
+__global__ void __launch_bounds__(128, TcCfg<BN>::kMinBlocks) k_contract_tc(
     const __grid_constant__ CUtensorMap mLhi, const __grid_constant__ CUtensorMap mLlo,
     const __grid_constant__ CUtensorMap mRhi, const __grid_constant__ CUtensorMap mRlo,
     const int4 *__restrict__ work, const int32_t *__restrict__ dof_off,
@@ -215,6 +222,7 @@ __global__ void __launch_bounds__(128, 2) k_contract_tc(
     // 1024-byte aligned tile area (swizzle atoms), barriers after it
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr uint32_t kTileB = TcCfg<BN>::kTileB, kStageBytes = TcCfg<BN>::kStageBytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + kStages * kStageBytes);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 1);
     __shared__ int s_fail;
@@ -224,8 +232,8 @@ __global__ void __launch_bounds__(128, 2) k_contract_tc(
     const int row0 = dof_off[bin];
     const int D = dof_off[bin + 1] - row0;
     const int G = gp_off[bin + 1] - gp_off[bin];
-    const int nvalid = min(kBN, D - nt * kBN);          // columns of this tile
-    const int N = (nvalid + 15) & ~15;                  // MMA N: multiple of 16, <= 256
+    const int nvalid = min(BN, D - nt * BN);            // columns of this tile
+    const int N = (nvalid + 15) & ~15;                  // MMA N: multiple of 16, <= BN
     constexpr int kBK = BF16 ? 64 : 32;                 // Gauss points per K step
     const int nk = (G + kBK - 1) / kBK;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(128, 2) k_contract_tc(
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(kBN));
+                     "r"(BN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(128, 2) k_contract_tc(
             const int nbox = (N + kBoxRows - 1) / kBoxRows;   // 128-row boxes of each B operand
             mbar_expect_tx(bar, 2 * kTileA + 2 * nbox * kBoxBytes);
             const int x = k * kBK;
-            const int ya = row0 + mt * kBM, yb = row0 + nt * kBN;
+            const int ya = row0 + mt * kBM, yb = row0 + nt * BN;
             tma_load_2d(smem_u32(st), &mLhi, x, ya, bar);
             tma_load_2d(smem_u32(st + kTileA), &mLlo, x, ya, bar);
             for (int h = 0; h < nbox; h++) {
@@ -312,7 +320,7 @@ __global__ void __launch_bounds__(128, 2) k_contract_tc(
             if (!row_ok) continue;
 #pragma unroll
             for (int q = 0; q < 16; q++) {
-                const int c2 = nt * kBN + cb + q;
+                const int c2 = nt * BN + cb + q;
                 if (cb + q >= nvalid) break;
                 const int64_t j2 = dof_idx[row0 + c2];
                 // A = sK (X + X^T): X[c1][c2] and X[c2][c1] both land on the lower-triangle
@@ -326,7 +334,7 @@ __global__ void __launch_bounds__(128, 2) k_contract_tc(
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 2)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
 }
 
 // ------------------------------- host side ----------------------------------------
@@ -379,26 +387,87 @@ static int tc_prepare(Mesh *m) {
         const int64_t kp_max = std::max(64, (maxG + 63) / 64 * 64);
         for (int q = 0; q < 4; q++)
             FEM3_TRY(dev_alloc(m, &B.tc_op[q], sizeof(float) * rows * kp_max));
-        std::vector<int4> &work = B.h_tc_work;
-        work.clear();
-        for (int b = 0; b < B.n_bins; b++) {
-            int D = B.h_dof_off[b + 1] - B.h_dof_off[b];
-            int G = B.h_gp_off[b + 1] - B.h_gp_off[b];
-            if (D == 0 || G == 0) continue;
-            for (int mt = 0; mt * kBM < D; mt++)
-                for (int nt = 0; nt * kBN < D; nt++) work.push_back(make_int4(b, mt, nt, 0));
+        // work lists of both tile widths: (bin, m-tile, n-tile)
+        for (int w = 0; w < 2; w++) {
+            const int bn = kTileWidths[w];
+            std::vector<int4> &work = B.h_tc_work[w];
+            work.clear();
+            for (int b = 0; b < B.n_bins; b++) {
+                int D = B.h_dof_off[b + 1] - B.h_dof_off[b];
+                int G = B.h_gp_off[b + 1] - B.h_gp_off[b];
+                if (D == 0 || G == 0) continue;
+                for (int mt = 0; mt * kBM < D; mt++)
+                    for (int nt = 0; nt * bn < D; nt++) work.push_back(make_int4(b, mt, nt, 0));
+            }
+            B.tc_n_work[w] = (int)work.size();
+            FEM3_TRY(dev_alloc_t(m, &B.tc_work[w], std::max(1, B.tc_n_work[w])));
+            if (B.tc_n_work[w])
+                FEM3_CUDA(cudaMemcpyAsync(B.tc_work[w], work.data(), sizeof(int4) * work.size(),
+                                          cudaMemcpyHostToDevice, s));
         }
-        B.tc_n_work = (int)work.size();
-        FEM3_TRY(dev_alloc_t(m, &B.tc_work, std::max(1, B.tc_n_work)));
-        if (B.tc_n_work)
-            FEM3_CUDA(cudaMemcpyAsync(B.tc_work, work.data(), sizeof(int4) * work.size(),
-                                      cudaMemcpyHostToDevice, s));
     }
-    FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc<false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
-    FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc<true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+    static bool attr = false;
+    if (!attr) {
+        FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc<false, 256>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TcCfg<256>::kSmemBytes));
+        FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc<true, 256>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TcCfg<256>::kSmemBytes));
+        FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc<false, 128>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TcCfg<128>::kSmemBytes));
+        FEM3_CUDA(cudaFuncSetAttribute(k_contract_tc<true, 128>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TcCfg<128>::kSmemBytes));
+        attr = true;
+    }
     m->tc_ready = true;
+    return FEM3_OK;
+}
+
+// Tile-width tuner: the first tensor-core contraction of a problem size class (operand
+// type, template rows and largest bin, both bucketed) times the GEMMs of every axis with
+// each tile width (second of two runs, CUDA events) and keeps the faster; later meshes of
+// the class use it.  fem3_options.tc_tile forces a width.
+static std::mutex g_tile_mu;
+static std::map<uint64_t, int> g_tile_choice;   // class -> tile slot
+
+static uint64_t tile_class(const Mesh *m, bool bf16) {
+    int64_t rows = 0;
+    int maxg = 0;
+    for (int a = 0; a < 3; a++) {
+        rows += m->bins[a].n_tmpl;
+        maxg = std::max(maxg, m->bins[a].tc_maxG);
+    }
+    int lg = 0;
+    while ((int64_t(1) << lg) < rows) lg++;
+    return (uint64_t)bf16 | ((uint64_t)lg << 1) | ((uint64_t)((maxg + 31) / 32) << 8);
+}
+
+// the GEMMs of the three axes with tile slot w (A32 accumulates: the caller zeroes it)
+static int tc_gemms(Mesh *m, bool bf16, int w, const CUtensorMap (*maps)[4]) {
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n_dof;
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        const int nw = B.tc_n_work[w];
+        if (!nw) continue;
+        const CUtensorMap *mp = maps[axis];
+        const float sk = (float)m->sK[axis];
+#define FEM3_TC_LAUNCH(BF, BN)                                                                  \
+    k_contract_tc<BF, BN><<<nw, 128, TcCfg<BN>::kSmemBytes, s>>>(                              \
+        mp[0], mp[1], mp[2], mp[3], B.tc_work[w], B.dof_off, B.dof_idx, B.gp_off, sk, m->A32, n, \
+        m->err)
+        if (kTileWidths[w] == 256) {
+            if (bf16) FEM3_TC_LAUNCH(true, 256); else FEM3_TC_LAUNCH(false, 256);
+        } else {
+            if (bf16) FEM3_TC_LAUNCH(true, 128); else FEM3_TC_LAUNCH(false, 128);
+        }
+#undef FEM3_TC_LAUNCH
+        note_launch(m);
+    }
+    FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
 
@@ -406,8 +475,9 @@ int contract_tc(Mesh *m, bool bf16) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
     FEM3_TRY(tc_prepare(m));
-    FEM3_CUDA(cudaMemsetAsync(m->A32, 0, sizeof(float) * n * n, s));
     double flops = 0;
+    CUtensorMap maps[3][4];
+    // the split of every axis first (the GEMMs below may run more than once when tuning)
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
         for (int b = 0; b < B.n_bins; b++) {
@@ -415,7 +485,7 @@ int contract_tc(Mesh *m, bool bf16) {
             double G = B.h_gp_off[b + 1] - B.h_gp_off[b];
             flops += 2.0 * D * D * G;
         }
-        if (!B.tc_n_work) continue;
+        if (!B.tc_n_work[0]) continue;
         FEM3_TRY(ap_alloc(m, axis));
         const int kbk = bf16 ? 64 : 32;   // Gauss points per 128-byte swizzle row
         const int Kp = std::max(kbk, (B.tc_maxG + kbk - 1) / kbk * kbk);
@@ -434,18 +504,50 @@ int contract_tc(Mesh *m, bool bf16) {
                 B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1], op[2], op[3], B.ap_R);
         }
         note_launch(m);
-        CUtensorMap maps[4];
-        for (int q = 0; q < 4; q++) FEM3_TRY(make_map(&maps[q], B.tc_op[q], B.n_tmpl, Kp, bf16));
-        if (bf16)
-            k_contract_tc<true><<<B.tc_n_work, 128, kSmemBytes, s>>>(
-                maps[0], maps[1], maps[2], maps[3], B.tc_work, B.dof_off, B.dof_idx, B.gp_off,
-                (float)m->sK[axis], m->A32, n, m->err);
-        else
-            k_contract_tc<false><<<B.tc_n_work, 128, kSmemBytes, s>>>(
-                maps[0], maps[1], maps[2], maps[3], B.tc_work, B.dof_off, B.dof_idx, B.gp_off,
-                (float)m->sK[axis], m->A32, n, m->err);
-        note_launch(m);
+        for (int q = 0; q < 4; q++)
+            FEM3_TRY(make_map(&maps[axis][q], B.tc_op[q], B.n_tmpl, Kp, bf16));
     }
+    // tile width: forced, cached for the size class, or tuned now
+    int w = -1;
+    m->tc_tuned = false;
+    if (m->tc_tile_opt == 128 || m->tc_tile_opt == 256) {
+        w = m->tc_tile_opt == 256 ? 0 : 1;
+    } else {
+        const uint64_t key = tile_class(m, bf16);
+        {
+            std::lock_guard<std::mutex> lk(g_tile_mu);
+            auto it = g_tile_choice.find(key);
+            if (it != g_tile_choice.end()) w = it->second;
+        }
+        if (w < 0) {
+            cudaEvent_t e0, e1;
+            FEM3_CUDA(cudaEventCreate(&e0));
+            FEM3_CUDA(cudaEventCreate(&e1));
+            float best = 0.f;
+            for (int c = 0; c < 2; c++)
+                for (int rep = 0; rep < 2; rep++) {
+                    FEM3_CUDA(cudaMemsetAsync(m->A32, 0, sizeof(float) * n * n, s));
+                    FEM3_CUDA(cudaEventRecord(e0, s));
+                    FEM3_TRY(tc_gemms(m, bf16, c, maps));
+                    FEM3_CUDA(cudaEventRecord(e1, s));
+                    FEM3_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    FEM3_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (rep == 1 && (w < 0 || ms < best)) {
+                        best = ms;
+                        w = c;
+                    }
+                }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            std::lock_guard<std::mutex> lk(g_tile_mu);
+            g_tile_choice[key] = w;
+            m->tc_tuned = true;
+        }
+    }
+    m->tc_tile_used = kTileWidths[w];
+    FEM3_CUDA(cudaMemsetAsync(m->A32, 0, sizeof(float) * n * n, s));
+    FEM3_TRY(tc_gemms(m, bf16, w, maps));
     m->contract_flops = flops;
     m->ap_ready = true;
     FEM3_CUDA(cudaGetLastError());

@@ -76,12 +76,12 @@ struct AxisBins {
     void *tc_op[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t *row_bin = nullptr;  // [n_tmpl] template row -> bin
     int tc_maxG = 0;             // largest Gauss-point count of a bin
-    int4 *tc_work = nullptr;     // (bin, m-tile, n-tile, 0)
+    int4 *tc_work[2] = {nullptr, nullptr};   // (bin, m-tile, n-tile, 0) per tile width
     // operator-apply operand W R as hi + lo FP32 pairs in the table layout (L is the table)
     float2 *ap_R = nullptr;
-    int tc_n_work = 0;
+    int tc_n_work[2] = {0, 0};
     std::vector<int32_t> h_gp_off, h_dof_off;
-    std::vector<int4> h_work, h_tc_work;   // host copies of the work lists
+    std::vector<int4> h_work, h_tc_work[2];   // host copies of the work lists
     std::vector<int64_t> h_tab_off;
     std::vector<int32_t> h_tab_ld;
 };
@@ -128,6 +128,9 @@ struct Mesh {
     float *A32 = nullptr;      // [n_dof][n_dof]
     bool factored = false;
     bool tc_ready = false;
+    int tc_tile_opt = 0;       // tensor-core tile width asked for: 0 tuned, 128 or 256
+    int tc_tile_used = 0;      // width of the last tensor-core contraction
+    bool tc_tuned = false;     // the last contraction ran the tuner
     bool ap_ready = false;     // ap_R holds W R of the current tables
 
     // workspaces

@@ -25,7 +25,8 @@ PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2, "bf16x3": 3}
 # every entry point declared in include/fem3.h
 SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_load", "fem3_solve",
            "fem3_adjoint", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
-           "fem3_counters", "fem3_last_error", "fem3_mesh_free", "fem3_spd_solve_static",
+           "fem3_counters", "fem3_tc_tile", "fem3_last_error", "fem3_mesh_free",
+           "fem3_spd_solve_static",
            "fem3_batch_create", "fem3_batch_mesh", "fem3_batch_run", "fem3_batch_free")
 
 _lib = None
@@ -38,7 +39,8 @@ class Fem3Error(RuntimeError):
 
 
 class Options(C.Structure):
-    _fields_ = [("bin_scale", C.c_double), ("max_steps", C.c_int32), ("profile", C.c_int32)]
+    _fields_ = [("bin_scale", C.c_double), ("max_steps", C.c_int32), ("profile", C.c_int32),
+                ("tc_tile", C.c_int32)]
 
 
 def lib_path() -> str:
@@ -68,6 +70,7 @@ def load_library(build_if_missing: bool = True):
         "fem3_sync": [p, p],
         "fem3_stage_ms": [p, ci, C.POINTER(C.c_float)],
         "fem3_counters": [p, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)],
+        "fem3_tc_tile": [p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "fem3_last_error": [C.c_char_p, C.c_size_t],
         "fem3_mesh_free": [p],
         "fem3_spd_solve_static": [p, i64, p, p, p],
@@ -110,9 +113,9 @@ def _ptr(x):
 # functions with the C ABI's names
 # ---------------------------------------------------------------------------------
 def mesh_upload(verts, tets, bin_scale: float = 0.5, max_steps: int = 0, profile: bool = False,
-                stream=None):
+                stream=None, tc_tile: int = 0):
     lib = load_library()
-    opt = Options(bin_scale, max_steps, 1 if profile else 0)
+    opt = Options(bin_scale, max_steps, 1 if profile else 0, tc_tile)
     h = C.c_void_p()
     _check(lib.fem3_mesh_upload(_ptr(verts), int(verts.shape[0]), _ptr(tets), int(tets.shape[0]),
                                 C.byref(opt), _stream(stream), C.byref(h)))
@@ -181,6 +184,12 @@ def counters(h):
     return dict(segments=s.value, contract_flops=f.value, table_bytes=b.value, launches=n.value)
 
 
+def tc_tile(h):
+    t, u = C.c_int32(), C.c_int32()
+    _check(_lib.fem3_tc_tile(h, C.byref(t), C.byref(u)))
+    return t.value, bool(u.value)
+
+
 def spd_solve_static(A, b, x, stream=None):
     """Dense SPD solve with no device allocation (n <= 512); see include/fem3.h."""
     lib = load_library()
@@ -197,7 +206,7 @@ class Mesh:
     """A mesh uploaded to the current CUDA device (torch's current stream by default)."""
 
     def __init__(self, verts, tets, bin_scale: float = 0.5, max_steps: int = 0,
-                 profile: bool = False, stream=None):
+                 profile: bool = False, stream=None, tc_tile: int = 0):
         import torch
         self._torch = torch
         self.stream = stream
@@ -206,7 +215,7 @@ class Mesh:
             tets = np.ascontiguousarray(tets, dtype=np.int32)
         self.n_nodes = int(verts.shape[0])
         self.n_tets = int(tets.shape[0])
-        self.h = mesh_upload(verts, tets, bin_scale, max_steps, profile, stream)
+        self.h = mesh_upload(verts, tets, bin_scale, max_steps, profile, stream, tc_tile)
         self.n_dof, self.n_gp, self.dof_of_node = mesh_info(self.h, self.n_nodes)
         self.precision = None
 
@@ -276,6 +285,10 @@ class Mesh:
     def counters(self):
         return counters(self.h)
 
+    def tc_tile(self):
+        """(tile width of the last tensor-core contraction, whether it ran the tuner)"""
+        return tc_tile(self.h)
+
     def free(self):
         if getattr(self, "h", None):
             mesh_free(self.h)
@@ -307,7 +320,7 @@ class Batch:
         tp = (C.c_void_p * n)(*[t.ctypes.data for _, t in self._keep])
         nn = (C.c_int64 * n)(*[v.shape[0] for v, _ in self._keep])
         nt = (C.c_int64 * n)(*[t.shape[0] for _, t in self._keep])
-        opt = Options(bin_scale, max_steps, 0)
+        opt = Options(bin_scale, max_steps, 0, 0)
         h = C.c_void_p()
         _check(lib.fem3_batch_create(n, vp, nn, tp, nt, C.byref(opt), _stream(stream), C.byref(h)))
         self.h = h

@@ -38,3 +38,15 @@ def test_product_path_does_not_import_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "fem3_oracle" not in src, f
+
+
+def test_options_struct_matches_header():
+    """The binding's fem3_options mirror has the header's fields, in order and type."""
+    import ctypes as C
+    import re
+    from paper_1811_03339_gb300 import fem3
+    hdr = open(os.path.join(ROOT, "include", "fem3.h")).read()
+    body = hdr[hdr.index("typedef struct fem3_options {"):hdr.index("} fem3_options;")]
+    fields = re.findall(r"^\s*(double|int32_t)\s+(\w+);", body, re.M)
+    ctype = {"double": C.c_double, "int32_t": C.c_int32}
+    assert [(n, ctype[t]) for t, n in fields] == list(fem3.Options._fields_)

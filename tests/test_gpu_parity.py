@@ -170,6 +170,39 @@ def test_bf16_split_products_accuracy(name):
     m.free()
 
 
+def test_tensor_core_tile_widths_and_tuner():
+    """Both tile widths of the tensor-core contraction give the same matrix (to FP32
+    summation order) within the TF32x3 bound of the oracle; with no width forced, the first
+    contraction of a size class runs the tuner and later meshes of the class reuse its
+    choice."""
+    mesh, o, alpha, K = _case("cube7_jitter")
+    A_ref = o.assemble(alpha, K)
+    As = {}
+    for tile in (128, 256):
+        m = fem3.Mesh(mesh.verts, mesh.tets, tc_tile=tile)
+        As[tile] = m.assemble(alpha, K, "tf32x3", return_matrix=True).cpu().numpy()
+        m.sync()
+        assert m.tc_tile() == (tile, False)
+        assert _rel(As[tile], A_ref) <= 2e-6
+        m.free()
+    assert _rel(As[128], As[256]) <= 1e-6
+    chosen = []
+    for rep in range(2):
+        m = fem3.Mesh(mesh.verts, mesh.tets)
+        A = m.assemble(alpha, K, "bf16x3", return_matrix=True).cpu().numpy()
+        m.sync()
+        tile, tuned = m.tc_tile()
+        assert tile in (128, 256)
+        if rep == 1:
+            assert not tuned
+        chosen.append(tile)
+        assert _rel(A, A_ref) <= 1e-4
+        m.free()
+    assert chosen[0] == chosen[1]
+    with pytest.raises(fem3.Fem3Error):
+        fem3.Mesh(mesh.verts, mesh.tets, tc_tile=100)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "tf32x3", "bf16x3"])
 def test_adjoint_matches_oracle(precision):
     """dJ/dK and dJ/df of J = 0.5 ||u(K, f) - u_obs||^2 against the oracle's adjoint (which is
