@@ -349,33 +349,51 @@ __device__ __forceinline__ void flush_entry(float2 *tab, int32_t col, int32_t ld
 // added to the table when a vertex drops out of the current tet or the walk ends, so a
 // step costs about one table read-modify-write.  Returns the number of segments; counts
 // template misses and failed walks.
-__device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
-                                         const TableArgs &A1, int axis, int64_t slot,
-                                         int &miss, int &bad) {
+// Lines from `slot` on: after each line, next() gives the slot of another line or -1.  A
+// lane that finishes its line takes the next one in the same loop, so the lanes of a warp
+// stay busy until the lines run out instead of waiting for the warp's longest chord.
+template <class Next>
+__device__ __forceinline__ int walk_lines(const WalkGeom &W, const TableArgs &A0,
+                                          const TableArgs &A1, int axis, int64_t slot,
+                                          Next next, int &miss, int &bad) {
     int nseg = 0;
-    const int32_t g = A0.gp_idx[slot];
-    const int32_t bin = A0.slot_bin[slot];
-    const int32_t row = (int32_t)(slot - A0.gp_off[bin]);
-    const int32_t *dofs = A0.dof_idx + A0.dof_off[bin];
-    const int nd = A0.dof_off[bin + 1] - A0.dof_off[bin];
-    const int32_t ld = A0.tab_ld[bin];
-    const int64_t toff = A0.tab_off[bin] + row;
-    const double x0 = W.gp[3 * (int64_t)g], x1 = W.gp[3 * (int64_t)g + 1],
-                 x2 = W.gp[3 * (int64_t)g + 2];
-    const LineF X = line_f(x0, x1, x2, axis);
-    // this line's rows of L and R (no other thread writes them): zero before accumulating
-    for (int c = 0; c < nd; c++) {
-        A0.tab[toff + (int64_t)c * ld] = make_float2(0.f, 0.f);
-        A1.tab[toff + (int64_t)c * ld] = make_float2(0.f, 0.f);
-    }
-    int side = 0;   // 0: left walk (dir -1, table L), 1: right walk (dir +1, table R)
-    int32_t t = g >> 2;
-    double r_prev = 0.0;
-    float pp_h = 0.f, pp_l = 0.f;   // r_prev^p
+    int32_t g, nd, ld;
+    const int32_t *dofs;
+    int64_t toff;
+    double x0, x1, x2;
+    LineF X;
+    int side, steps;   // side 0: left walk (dir -1, table L), 1: right walk (dir +1, table R)
+    int32_t t;
+    double r_prev;
+    float pp_h, pp_l;   // r_prev^p
+    auto begin_line = [&](int64_t sl) {
+        g = A0.gp_idx[sl];
+        const int32_t bin = A0.slot_bin[sl];
+        const int32_t row = (int32_t)(sl - A0.gp_off[bin]);
+        dofs = A0.dof_idx + A0.dof_off[bin];
+        nd = A0.dof_off[bin + 1] - A0.dof_off[bin];
+        ld = A0.tab_ld[bin];
+        toff = A0.tab_off[bin] + row;
+        x0 = W.gp[3 * (int64_t)g];
+        x1 = W.gp[3 * (int64_t)g + 1];
+        x2 = W.gp[3 * (int64_t)g + 2];
+        X = line_f(x0, x1, x2, axis);
+        // this line's rows of L and R (no other thread writes them): zero before accumulating
+        for (int c = 0; c < nd; c++) {
+            A0.tab[toff + (int64_t)c * ld] = make_float2(0.f, 0.f);
+            A1.tab[toff + (int64_t)c * ld] = make_float2(0.f, 0.f);
+        }
+        side = 0;
+        steps = 0;
+        t = g >> 2;
+        r_prev = 0.0;
+        pp_h = 0.f;
+        pp_l = 0.f;
+    };
+    begin_line(slot);
     // live vertices: dof (-2: none), table column (-1: none), accumulated entry (hi + lo)
     int32_t sj[4] = {-2, -2, -2, -2}, sc[4] = {-1, -1, -1, -1};
     float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
-    int steps = 0;
     for (;;) {   // at most max_steps steps per side
         const int dir = side ? 1 : -1;
         float2 *const tab = (side ? A1.tab : A0.tab) + toff;
@@ -486,7 +504,12 @@ __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
             sh[q] = 0.f;
             sl[q] = 0.f;
         }
-        if (side == 1) break;
+        if (side == 1) {
+            const int64_t ns = next();
+            if (ns < 0) break;
+            begin_line(ns);
+            continue;
+        }
         // switch to the right walk of the same line (same order 1 - gamma on both sides)
         side = 1;
         t = g >> 2;
@@ -496,6 +519,12 @@ __device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
         steps = 0;
     }
     return nseg;
+}
+
+__device__ __forceinline__ int walk_line(const WalkGeom &W, const TableArgs &A0,
+                                         const TableArgs &A1, int axis, int64_t slot,
+                                         int &miss, int &bad) {
+    return walk_lines(W, A0, A1, axis, slot, []() -> int64_t { return -1; }, miss, bad);
 }
 
 __device__ __forceinline__ void count_segments(int nseg, unsigned long long *seg_count) {
@@ -509,15 +538,28 @@ struct AxisTables {
     TableArgs A0[3], A1[3];
 };
 
-// grid: x over the slots of an axis, y = axis; the three axes in one launch keep every SM
-// filled (one axis alone is about five CTAs per SM)
+// grid: x over blocks of `per_block` consecutive slots of an axis (bin order), y = axis; the
+// three axes in one launch keep every SM filled.  A block's lanes start on its first 128
+// lines and take the rest from a shared counter as they finish (per_block = 128 gives one
+// line per lane).
 __global__ void __launch_bounds__(128, 6) k_walk_tables(WalkGeom W, AxisTables T, int64_t n_gp,
-                                                        int32_t *err,
+                                                        int per_block, int32_t *err,
                                                         unsigned long long *seg_count) {
+    __shared__ int s_next;
     const int axis = blockIdx.y;
-    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t base = blockIdx.x * (int64_t)per_block;
+    const int64_t end = min(base + per_block, n_gp);
+    if (threadIdx.x == 0) s_next = blockDim.x;
+    __syncthreads();
+    const int64_t slot = base + threadIdx.x;
     int nseg = 0, miss = 0, bad = 0;
-    if (slot < n_gp) nseg = walk_line(W, T.A0[axis], T.A1[axis], axis, slot, miss, bad);
+    if (slot < end) {
+        auto next = [&]() -> int64_t {
+            const int64_t sl = base + atomicAdd(&s_next, 1);
+            return sl < end ? sl : -1;
+        };
+        nseg = walk_lines(W, T.A0[axis], T.A1[axis], axis, slot, next, miss, bad);
+    }
     if (bad) atomicAdd(&err[ERR_WALK], bad);
     if (miss) atomicAdd(&err[ERR_TEMPLATE], miss);
     count_segments(nseg, seg_count);   // every lane takes part
@@ -665,8 +707,21 @@ int walk_tables(Mesh *m, const double alpha[3]) {
         T.A1[axis].coef_h = -igh;
         T.A1[axis].coef_l = -igl;
     }
-    k_walk_tables<<<dim3((unsigned)((m->n_gp + 127) / 128), 3), 128, 0, s>>>(W, T, m->n_gp, m->err,
-                                                                            segc);
+    // one line per lane (128 slots a block) up to eight blocks per SM and axis; beyond that
+    // the blocks hold more slots and their lanes take further lines as they finish.  (At the
+    // 16^3 cube 2.5 lines per lane was 10 % slower than one: the lanes of a warp drift to
+    // different lines and diverge.)
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        FEM3_CUDA(cudaGetDevice(&dev));
+        FEM3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int64_t blocks = std::max<int64_t>(1, (int64_t)sms * 8);
+    const int per_block =
+        (int)std::max<int64_t>(128, (m->n_gp + blocks - 1) / blocks);
+    k_walk_tables<<<dim3((unsigned)((m->n_gp + per_block - 1) / per_block), 3), 128, 0, s>>>(
+        W, T, m->n_gp, per_block, m->err, segc);
     note_launch(m);
     stage_end(m, 2);
     FEM3_CUDA(cudaGetLastError());
