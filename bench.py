@@ -45,8 +45,8 @@ def _peaks():
 # DRAM bytes (read + write) of one k_walk_tables launch from the ncu capture summarised in
 # profiles/k_walk_tables_cube16_jitter.md, valid only for the kernel source it was taken
 # on (sha256 of csrc/walk.cu); otherwise the traffic is reported as unknown.
-WALK_TRAFFIC = {"walk_cu_sha256": "6f3a3bc47a047baf8fe034e9fc8e82dc5a78538c676bfed6b1aa719255498f40",
-                "bytes_per_launch": 161048320 + 579881216, "segments_per_launch": 16099980}
+WALK_TRAFFIC = {"walk_cu_sha256": "157a6103d050d38cdfc5119e78cb51ebdee01506e66cf0cd0c6a096271408cb3",
+                "bytes_per_launch": 164286976 + 584489216, "segments_per_launch": 16099980}
 
 
 def _walk_traffic(segs_per_launch):
