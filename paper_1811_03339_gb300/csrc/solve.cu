@@ -118,67 +118,49 @@ __device__ __forceinline__ void bar_arrive_n(int id, int count) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// warp 0: 16 x 16 Cholesky of block p of a_s (row per lane, pivot column through a
-// double-buffered shared vector) and the inverse by forward substitution (column per
-// lane); writes L_pp into a_s, L_pp^{-1} into x_s and lt[k][c] = L_pp^{-1}[c][k]
+// warp 0: 16 x 16 Cholesky of block p of a_s and its inverse in one pass.  Lanes 0..15 hold
+// row r of the block (lower part), lanes 16..31 column r of the identity; step j broadcasts
+// the pivot column (a_kj, k >= j, from lanes k) and every lane applies the same update,
+// x_k -= (x_j / a_jj) a_kj (k > j), x_j /= sqrt(a_jj): on the rows this is the right-looking
+// factorisation, on the identity's columns forward substitution with the new column of
+// L_pp, so the inverse needs no pass of its own.  Entries above the diagonal of the row
+// lanes are never read.  Writes L_pp into a_s, L_pp^{-1} into x_s and
+// lt[k][c] = L_pp^{-1}[c][k].
 template <class TF>
 __device__ __forceinline__ void chol_inv16(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], TF (*lt)[PB + 4],
-                                           TF (*colb16)[PB], TF (*lcol)[PB + 4], int P, int nb,
-                                           int64_t k0, int32_t *err) {
+                                           int P, int nb, int64_t k0, int32_t *err) {
     const int lane = threadIdx.x & 31;
     const int r = lane & (PB - 1);
-    TF v[PB], rdv[PB];
+    const bool inv = lane >= PB;
+    TF x[PB];
 #pragma unroll
-    for (int c = 0; c < PB; c++) v[c] = c <= r ? a_s[P + r][P + c] : TF(0);
+    for (int c = 0; c < PB; c++)
+        x[c] = inv ? (c == r ? TF(1) : TF(0)) : (c <= r ? a_s[P + r][P + c] : TF(0));
     int bad = -1;
 #pragma unroll
     for (int j = 0; j < PB; j++) {
-        TF *cb = colb16[j & 1];
-        if (lane < PB && r >= j) cb[r] = v[j];
-        __syncwarp();
         TF col[PB];
 #pragma unroll
-        for (int k = 0; k < PB; k += 4) lds4<TF>(cb + k, col + k);
+        for (int k = j; k < PB; k++) col[k] = __shfl_sync(0xffffffffu, x[j], k);
         const TF d = col[j];
         if (!(d > TF(0)) && bad < 0) bad = j;
         const TF rs = d > TF(0) ? rsqrt_t<TF>(d) : TF(1);
-        rdv[j] = rs;
-        const TF f = v[j] * rs * rs;   // a[r][j] / d
+        const TF f = x[j] * rs * rs;
 #pragma unroll
-        for (int k = 1; k < PB; k++)
-            if (k > j && r >= k) v[k] -= f * col[k];
-        v[j] = r == j ? d * rs : v[j] * rs;
+        for (int k = j + 1; k < PB; k++) x[k] -= f * col[k];
+        x[j] *= rs;
     }
     if (bad >= 0 && lane == 0 && P + bad < nb)
         atomicCAS(&err[ERR_NOT_SPD], 0, (int32_t)(k0 + P + bad + 1));
-    if (lane < PB) {
+    if (!inv) {
 #pragma unroll
-        for (int c = 0; c < PB; c++) {
-            if (c <= r) a_s[P + r][P + c] = v[c];
-            lcol[c][r] = v[c];   // zero above the diagonal
-        }
-    }
-    __syncwarp();
-    // column cc of L_pp^{-1}: t_k = (delta_kc - sum_{i<k} L_ki t_i) / L_kk
-    const int cc = lane & (PB - 1);
-    TF t[PB];
-#pragma unroll
-    for (int i = 0; i < PB; i++) t[i] = i == cc ? TF(1) : TF(0);
-#pragma unroll
-    for (int k = 0; k < PB; k++) {
-        t[k] *= rdv[k];
-        TF lc[PB];
-#pragma unroll
-        for (int i = 0; i < PB; i += 4) lds4<TF>(&lcol[k][i], lc + i);
-#pragma unroll
-        for (int i = 1; i < PB; i++)
-            if (i > k) t[i] -= lc[i] * t[k];
-    }
-    if (lane < PB) {
+        for (int c = 0; c < PB; c++)
+            if (c <= r) a_s[P + r][P + c] = x[c];
+    } else {
 #pragma unroll
         for (int i = 0; i < PB; i++) {
-            x_s[P + i][P + cc] = i >= cc ? t[i] : TF(0);
-            lt[cc][i] = t[i];
+            x_s[P + i][P + r] = i >= r ? x[i] : TF(0);
+            lt[r][i] = x[i];
         }
     }
 }
@@ -187,12 +169,15 @@ __device__ __forceinline__ void chol_inv16(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1],
 // 16 with look-ahead.  Warp 0 factors and inverts the 16 x 16 diagonal block p; the other
 // 15 warps then (a) solve the 16 rows of block p + 1 in panel p (L_{p+1,p} = A L_pp^{-T})
 // and update diagonal block p + 1, which releases warp 0 for block p + 1 at once, and
-// (b) meanwhile solve the rest of panel p, form the inverse's block row p
-// ((L^{-1})_pJ = -L_pp^{-1} sum_K L_pK (L^{-1})_KJ) and apply the rest of the trailing update.
-// a_s holds the block (rows and columns >= nb padded with the identity) and receives L
-// (lower triangle); x_s receives L^{-1} (zero above the diagonal on return); the caller
-// stores them.  A non-positive pivot records 1 + its global column (k0 + local).  Needs
-// exactly 512 threads, all of the CTA; ends with a barrier.
+// (b) meanwhile solve the rest of panel p, finish the inverse's block row p,
+// (L^{-1})_pJ = -L_pp^{-1} T_pJ, apply the rest of the trailing update (2 x 2 blocks per
+// thread) and form T_{p+1,J} = sum_K L_{p+1,K} (L^{-1})_KJ, which needs nothing of block
+// p + 1 and so overlaps its factorisation.  The blocks of L^{-1} above the diagonal are
+// zeroed first, while block 0 is factored.  a_s holds the block (rows and columns >= nb
+// padded with the identity) and receives L (lower triangle); x_s receives L^{-1} in full
+// (zero above the diagonal); the caller stores them.  A non-positive pivot records 1 + its
+// global column (k0 + local).  Needs exactly 512 threads, all of the CTA; ends with a
+// barrier.
 template <class TF>
 __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, int64_t k0,
                                int32_t *err) {
@@ -200,18 +185,20 @@ __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, int
     __shared__ __align__(16) TF lt[2][PB][PB + 4];     // lt[p & 1][k][c] = L_pp^{-1}[c][k]
     __shared__ __align__(16) TF pant[PB][NB + 4];      // pant[k][r] = L[r][P + k], r >= P + 16
     __shared__ __align__(16) TF tq[PB][NB - PB + 4];   // T_pJ, columns c < P
-    __shared__ __align__(16) TF colb16[2][PB];         // pivot column (16 x 16 factor)
-    __shared__ __align__(16) TF lcol[PB][PB + 4];      // lcol[k][i] = L_pp[i][k]
     const int tid = threadIdx.x;
     if (tid < 32) {
         for (int p = 0; p < NP; p++) {
             if (p > 0) bar_sync_n(kBarNextReady, NT);
-            chol_inv16<TF>(a_s, x_s, lt[p & 1], colb16, lcol, p * PB, nb, k0, err);
+            chol_inv16<TF>(a_s, x_s, lt[p & 1], p * PB, nb, k0, err);
             __syncwarp();
             bar_arrive_n(kBarPanelReady, NT);
         }
     } else {
         const int ut = tid - 32;
+        for (int e = ut; e < NB * NB; e += NU) {
+            const int i = e >> 6, c = e & 63;
+            if (c >= ((i >> 4) + 1) * PB) x_s[i][c] = TF(0);
+        }
         for (int p = 0; p < NP; p++) {
             const int P = p * PB;
             bar_sync_n(kBarPanelReady, NT);
@@ -239,7 +226,8 @@ __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, int
                 }
                 bar_arrive_n(kBarNextReady, NT);
             }
-            // (b1) rows below block p + 1 (four columns per thread) and T_pJ
+            // (b1) rows below block p + 1 (four columns per thread); the inverse's block
+            // row p from T_pJ (formed in the previous panel)
             const int R1 = R0 + PB, m2 = NB - R1;
             const bool panel = m2 > 0 && ut < 4 * m2;
             const int pr = R1 + (ut >> 2), pc = (ut & 3) * 4;
@@ -252,28 +240,6 @@ __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, int
                     lds4<TF>(&L16[k][pc], lv);
 #pragma unroll
                     for (int q = 0; q < 4; q++) pv[q] += av * lv[q];
-                }
-            }
-            if (p > 0) {
-                // T_pJ[i][c] = sum_{k = c}^{P-1} L[P + i][k] (L^{-1})[k][c], by 16-wide k blocks
-                for (int e = ut; e < PB * P; e += NU) {
-                    const int i = e / P, c = e - i * P;
-                    TF acc = TF(0);
-                    for (int kb = c & ~(PB - 1); kb < P; kb += PB) {
-#pragma unroll
-                        for (int k = 0; k < PB; k++)
-                            if (kb + k >= c) acc += a_s[P + i][kb + k] * x_s[kb + k][c];
-                    }
-                    tq[i][c] = acc;
-                }
-            }
-            bar_sync_n(kBarUpdate, NU);
-            // (b2) store the rows; (L^{-1})_pJ = -L_pp^{-1} T_pJ into registers
-            if (panel) {
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    a_s[pr][P + pc + q] = pv[q];
-                    pant[pc + q][pr] = pv[q];
                 }
             }
             TF iv[2] = {TF(0), TF(0)};
@@ -292,8 +258,14 @@ __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, int
                 }
             }
             bar_sync_n(kBarUpdate, NU);
-            // (b3) store the inverse's block row; trailing update of blocks (i, k),
-            // i >= k >= p + 1, except block (p + 1, p + 1) done in (a)
+            // (b2) store the rows and the inverse's block row
+            if (panel) {
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    a_s[pr][P + pc + q] = pv[q];
+                    pant[pc + q][pr] = pv[q];
+                }
+            }
             if (p > 0) {
 #pragma unroll
                 for (int s2 = 0; s2 < 2; s2++) {
@@ -304,21 +276,42 @@ __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, int
                     }
                 }
             }
-            const int mt = NB - R0;
-            for (int e = ut; e < mt * mt; e += NU) {
-                const int i = R0 + e / mt, j = R0 + e % mt;
-                if (j > i || i < R1) continue;   // upper part, or inside block (p + 1, p + 1)
+            if (p + 1 == NP) break;
+            bar_sync_n(kBarUpdate, NU);
+            // (b3) T_{p+1,J}[i][c] = sum_{k = c}^{R0 - 1} L[R0 + i][k] (L^{-1})[k][c], c < R0
+            for (int e = ut; e < PB * R0; e += NU) {
+                const int i = e / R0, c = e - i * R0;
                 TF acc = TF(0);
+                for (int kb = c & ~(PB - 1); kb < R0; kb += PB) {
 #pragma unroll
-                for (int k = 0; k < PB; k++) acc += pant[k][i] * pant[k][j];
-                a_s[i][j] -= acc;
+                    for (int k = 0; k < PB; k++)
+                        if (kb + k >= c) acc += a_s[R0 + i][kb + k] * x_s[kb + k][c];
+                }
+                tq[i][c] = acc;
+            }
+            // trailing update of blocks (i, k), i >= k >= p + 1, except block (p + 1, p + 1),
+            // in 2 x 2 blocks (rows i0, i0 + 1 >= R1; columns j0, j0 + 1 >= R0)
+            const int mr = (NB - R1) / 2, mc = (NB - R0) / 2;
+            for (int e = ut; e < mr * mc; e += NU) {
+                const int i0 = R1 + 2 * (e / mc), j0 = R0 + 2 * (e % mc);
+                if (j0 > i0) continue;
+                TF c00 = TF(0), c01 = TF(0), c10 = TF(0), c11 = TF(0);
+#pragma unroll
+                for (int k = 0; k < PB; k++) {
+                    TF pi[2], pj[2];
+                    lds2<TF>(&pant[k][i0], pi);
+                    lds2<TF>(&pant[k][j0], pj);
+                    c00 += pi[0] * pj[0];
+                    c01 += pi[0] * pj[1];
+                    c10 += pi[1] * pj[0];
+                    c11 += pi[1] * pj[1];
+                }
+                a_s[i0][j0] -= c00;
+                if (j0 + 1 <= i0) a_s[i0][j0 + 1] -= c01;
+                a_s[i0 + 1][j0] -= c10;
+                a_s[i0 + 1][j0 + 1] -= c11;
             }
         }
-    }
-    __syncthreads();
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int i = e >> 6, c = e & 63;
-        if (c > i) x_s[i][c] = TF(0);   // x_s = L^{-1} in full
     }
     __syncthreads();
 }
