@@ -3,8 +3,9 @@
 //  - b = M f with the P1 mass matrix (|T|/20 (1 + delta_ab) per tet), the weak
 //    right-hand side (f, v) of Section 3.
 //  - Right-looking blocked Cholesky A = L L^T (block 64): diagonal block in shared
-//    memory, panel triangular solve, trailing symmetric update; row-major storage,
-//    lower triangle.  TF is double (FP64 form) or float (mixed forms).
+//    memory, panel triangular solve, trailing symmetric update; row-major storage: the
+//    tiles below the diagonal in A's lower triangle, each diagonal tile as its inverse
+//    L_jj^{-1} (all the solves use).  TF is double (FP64 form) or float (mixed forms).
 //  - Blocked forward / backward substitution.
 //  - Refinement for the mixed forms: r = b - A u with A u applied in FP64 from the FP64
 //    derivative tables (A u = sum_i s_i K_i (L_i^T W (R_i u) + R_i^T W (L_i u))), the
@@ -476,7 +477,10 @@ __device__ void chol_chain(TF *A, int64_t n, int nblk, TF *dinv, int *F, int *U,
         potrf_inv_smem<TF>(a_s, x_s, (int)min((int64_t)NB, n - c0), c0, err);
         if (next) {
             // L_{j+1,j} = A~_{j+1,j} L_jj^{-T}, computed transposed: xt = L_jj^{-1} A~_{j+1,j}^T
+            // the next diagonal tile's flag is looked at now, beside this wait, and once more
+            // after the sub-solve if it was not set yet
             if (tid == 0) s_ok = wait_tile(&U[tile_id(j + 1, j)], abort_w, err);
+            if (tid == 32) s_pre = ld_acquire_gpu(&U[tile_id(j + 1, j + 1)]) != 0;
             __syncthreads();
             if (!s_ok) return;
             load_tile_T<TF>(A + r0 * n + c0, n, n - r0, at);   // at[k][r] = A_{j+1,j}[r][k]
@@ -511,17 +515,17 @@ __device__ void chol_chain(TF *A, int64_t n, int nblk, TF *dinv, int *F, int *U,
             // the next diagonal tile goes into registers now if it is ready.  It is not
             // waited for here: its task may be queued behind tasks of this column that
             // wait for F(j, j), so the wait comes after the publication below.
-            if (tid == 0) s_pre = ld_acquire_gpu(&U[tile_id(j + 1, j + 1)]) != 0;
+            if (tid == 0 && !s_pre) s_pre = ld_acquire_gpu(&U[tile_id(j + 1, j + 1)]) != 0;
         }
         __syncthreads();   // xt complete; the next diagonal tile's flag seen
         const bool pre = next && s_pre;
         if (pre) load_acc<TF>(A, n, r0, r0, true, acc, tx, ty);
-        // L_jj into A, L_jj^{-1} into dinv, L_{j+1,j} into A: rows of 64, coalesced
-        const int nb = (int)min((int64_t)NB, n - c0);
+        // L_jj^{-1} into dinv, L_{j+1,j} into A: rows of 64, coalesced.  L_jj itself is not
+        // stored: every solve with the factor applies L_jj^{-1}, so A's diagonal tiles keep
+        // their last update.
         TF *Lj = dinv + (int64_t)j * NB * NB;
         for (int e = tid; e < NB * NB; e += blockDim.x) {
             const int i = e >> 6, c = e & 63;
-            if (i < nb && c < nb) A[(c0 + i) * n + c0 + c] = c <= i ? a_s[i][c] : TF(0);
             Lj[e] = x_s[i][c];
             if (next && r0 + i < n) A[(r0 + i) * n + c0 + c] = xt[c][i];
         }
