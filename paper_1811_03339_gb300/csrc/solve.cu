@@ -167,8 +167,8 @@ __device__ __forceinline__ void chol_inv16(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1],
 }
 
 // Diagonal block: factor A_kk = L_kk L_kk^T and form L_kk^{-1} (512 threads), blocked by
-// 16 with look-ahead.  Warp 0 factors and inverts the 16 x 16 diagonal block p; the other
-// 15 warps then (a) solve the 16 rows of block p + 1 in panel p (L_{p+1,p} = A L_pp^{-T})
+// 16 with look-ahead.  Warp 0 factors and inverts the 16 x 16 diagonal block p; 12 other
+// warps then (a) solve the 16 rows of block p + 1 in panel p (L_{p+1,p} = A L_pp^{-T})
 // and update diagonal block p + 1, which releases warp 0 for block p + 1 at once, and
 // (b) meanwhile solve the rest of panel p, finish the inverse's block row p,
 // (L^{-1})_pJ = -L_pp^{-1} T_pJ, apply the rest of the trailing update (2 x 2 blocks per
@@ -182,7 +182,9 @@ __device__ __forceinline__ void chol_inv16(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1],
 template <class TF>
 __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, int64_t k0,
                                int32_t *err) {
-    constexpr int NT = 512, NU = NT - 32, NP = NB / PB;
+    // warps 4, 8 and 12 share warp 0's SM sub-partition and sit out: the 12 other warps
+    // do the update work, so warp 0's serial factor competes with no issuing neighbour
+    constexpr int NT = 416, NU = 384, NP = NB / PB;
     __shared__ __align__(16) TF lt[2][PB][PB + 4];     // lt[p & 1][k][c] = L_pp^{-1}[c][k]
     __shared__ __align__(16) TF pant[PB][NB + 4];      // pant[k][r] = L[r][P + k], r >= P + 16
     __shared__ __align__(16) TF tq[PB][NB - PB + 4];   // T_pJ, columns c < P
@@ -194,8 +196,8 @@ __device__ void potrf_inv_smem(TF (*a_s)[NB + 1], TF (*x_s)[NB + 1], int nb, int
             __syncwarp();
             bar_arrive_n(kBarPanelReady, NT);
         }
-    } else {
-        const int ut = tid - 32;
+    } else if (((tid >> 5) & 3) != 0) {
+        const int ut = ((tid >> 5) - 1 - (tid >> 7)) * 32 + (tid & 31);   // 0 .. NU - 1
         for (int e = ut; e < NB * NB; e += NU) {
             const int i = e >> 6, c = e & 63;
             if (c >= ((i >> 4) + 1) * PB) x_s[i][c] = TF(0);
