@@ -18,6 +18,12 @@
 // tile width is tuned per problem size class at run time, see contract_tc).  K steps of
 // 128 bytes (one swizzle row: 32 TF32 or 64 BF16 Gauss points) are loaded by TMA into one
 // stage; each K step is four MMAs of 32 bytes (K = 8 TF32 or 16 BF16) per product.
+//
+// Epilogue.  A bin of at most 128 dofs has all of X in one CTA: the accumulator goes
+// through shared memory (the free stage, rows XOR-swizzled by the row index so that rows
+// and columns read without bank conflicts) and each pair adds X[r][c] + X[c][r] once, the
+// lanes of a warp along one row of A.  Larger bins add each X element into the lower
+// triangle straight from the tcgen05.ld registers.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -305,11 +311,32 @@ __global__ void __launch_bounds__(128, TcCfg<BN>::kMinBlocks) k_contract_tc(
         umma_commit(done);
     }
     __syncthreads();
-    // epilogue: every warp waits for the accumulator
-    bool ok = (nk > 0) && mbar_wait(done, 0);
+    // epilogue: every warp waits for the accumulator; one verdict for the whole CTA
+    const bool ok = __syncthreads_and((nk > 0) && mbar_wait(done, 0) && !s_fail);
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!ok || s_fail) {
+    if (!ok) {
         if (threadIdx.x == 0 && nk > 0) atomicAdd(&err[ERR_TC], 1);
+    } else if (D <= kBM) {
+        // the stage is free (every load was consumed by an MMA that has completed):
+        // Xs[r][c] at r * 128 + (c ^ (r & 31)), 64 KB
+        float *Xs = reinterpret_cast<float *>(base);
+        const int r1 = warp * 32 + lane;
+        for (int cb = 0; cb < N; cb += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, v);
+#pragma unroll
+            for (int q = 0; q < 16; q++) Xs[r1 * kBM + ((cb + q) ^ lane)] = v[q];
+        }
+        __syncthreads();
+        // A = sK (X + X^T) on the lower triangle, once per pair (2 X[r][r] on the diagonal)
+        for (int r = warp; r < D; r += 4) {
+            const int64_t jr = dof_idx[row0 + r];
+            for (int c = lane; c <= r; c += 32) {
+                const float x = Xs[r * kBM + (c ^ (r & 31))] + Xs[c * kBM + (r ^ (c & 31))];
+                const int64_t jc = dof_idx[row0 + c];
+                atomicAdd(&A[(jr > jc ? jr : jc) * n_dof + (jr > jc ? jc : jr)], sK * x);
+            }
+        }
     } else {
         const int c1 = mt * kBM + warp * 32 + lane;     // local row (dof) of this thread
         const bool row_ok = c1 < D;
