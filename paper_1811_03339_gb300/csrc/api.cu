@@ -218,7 +218,7 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
         for (int k = 0; k < 16; k++) cudaEventCreate(&m->ev[k]);
         m->ev_made = true;
     }
-    // keep freed pool memory cached so that repeated uploads do not hit the driver
+    // keep freed pool memory cached so that repeated uploads make no CUDA driver allocation
     {
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, m->device) == cudaSuccess) {

@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(128, TcCfg<BN>::kMinBlocks) k_contract_tc(
         umma_commit(done);
     }
     __syncthreads();
-    // epilogue: every warp waits for the accumulator; one verdict for the whole CTA
+    // epilogue: every warp waits for the accumulator; one outcome for the whole CTA
     const bool ok = __syncthreads_and((nk > 0) && mbar_wait(done, 0) && !s_fail);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!ok) {
