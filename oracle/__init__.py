@@ -64,6 +64,8 @@ def _load():
         lib.or_table_row.argtypes = [p, i64, C.c_int, C.c_int, dbl, C.c_int, p]
         lib.or_assemble.restype = C.c_int
         lib.or_assemble.argtypes = [p, p, p, p]
+        lib.or_assemble_form.restype = C.c_int
+        lib.or_assemble_form.argtypes = [p, C.c_int, dbl, dbl, C.c_int, p, C.c_int, p]
         lib.or_load.restype = C.c_int
         lib.or_load.argtypes = [p, p, C.c_int, p]
         lib.or_load_T.restype = C.c_int
@@ -186,6 +188,27 @@ class Oracle:
         if e:
             raise OracleError(e, "assemble")
         return A
+
+    def assemble_form(self, axis: int, alpha: float, beta: float, trial_left: bool = True,
+                      c=None, all_nodes: bool = False) -> np.ndarray:
+        """One axis term of (c D^alpha u, D^^beta v) (Section 2.1, eq. "equ:varsss"):
+        K[k, l] = sum_g w_g c_g (D^alpha psi_l)(x_g) (D^^beta psi_k)(x_g), D^alpha the left
+        operator when trial_left (D^^beta the right one), orders in [0, 1]; c: values at the
+        Gauss points (``self.gp`` order) or None for 1."""
+        n = self.n_nodes if all_nodes else self.n_dof
+        K = np.empty((n, n))
+        cg = None
+        if c is not None:
+            cg = np.ascontiguousarray(c, dtype=np.float64)
+            if cg.shape != (self.n_gp,):
+                raise ValueError("c must hold one value per Gauss point")
+        e = self._lib.or_assemble_form(self._h, int(axis), float(alpha), float(beta),
+                                       int(bool(trial_left)),
+                                       None if cg is None else _ptr(cg), int(bool(all_nodes)),
+                                       _ptr(K))
+        if e:
+            raise OracleError(e, "assemble_form")
+        return K
 
     def load(self, f: np.ndarray) -> np.ndarray:
         """b = M f; f nodal [n_nodes] or [n_nodes, nrhs]; returns [n_dof] or [n_dof, nrhs]."""

@@ -463,6 +463,47 @@ int or_assemble(const or_mesh *m, const double alpha[3], const double K[3], doub
     return OR_OK;
 }
 
+/* One axis term of the general bilinear form of Section 2.1, (c D^alpha u, D^^beta v)
+ * (eq. "equ:varsss"), by the Gauss-quadrature element formula that follows it:
+ *   K[k][l] = sum_g w_g c(x_g) (D^alpha psi_l)(x_g) (D^^beta psi_k)(x_g),
+ * l the trial (column) and k the test (row) basis function.  D^alpha is the left
+ * operator and D^^beta the right one when trial_left = 1, the other way round when 0.
+ * Orders in [0, 1] (the tables of or_table_row: order 0 is the function itself, order 1
+ * its first derivative, with a minus sign for the right operator).  c: [n_gp] values of
+ * the coefficient at the Gauss points, or NULL for c = 1.  all_nodes = 1: rows and
+ * columns over every node (tables with their boundary terms); 0: interior dofs.  K:
+ * row-major [n][n].  The Riesz term of or_assemble is s K (form(L, R) + form(R, L)) at
+ * alpha = beta = alpha_i / 2 and c = 1. */
+int or_assemble_form(const or_mesh *m, int axis, double alpha, double beta, int trial_left,
+                     const double *c, int all_nodes, double *K)
+{
+    if (axis < 0 || axis > 2 || !(alpha >= 0.0 && alpha <= 1.0) || !(beta >= 0.0 && beta <= 1.0))
+        return OR_E_ARG;
+    int64_t n = all_nodes ? m->n_nodes : m->n_dof;
+    int64_t nn = n > 0 ? n : 1;
+    memset(K, 0, sizeof(double) * n * n);
+    double *P = calloc(nn, sizeof(double)), *Q = calloc(nn, sizeof(double));
+    int64_t *iP = malloc(sizeof(int64_t) * nn), *iQ = malloc(sizeof(int64_t) * nn);
+    if (!P || !Q || !iP || !iQ) { free(P); free(Q); free(iP); free(iQ); return OR_E_OOM; }
+    int dtrial = trial_left ? -1 : +1;   /* left operator: the path towards -e_axis */
+    for (int64_t g = 0; g < m->n_gp; g++) {
+        int e1 = or_table_row(m, g, axis, dtrial, alpha, all_nodes, P);
+        int e2 = or_table_row(m, g, axis, -dtrial, beta, all_nodes, Q);
+        if (e1 || e2) { free(P); free(Q); free(iP); free(iQ); return e1 ? e1 : e2; }
+        int64_t np = 0, nq = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (P[j] != 0.0) iP[np++] = j;
+            if (Q[j] != 0.0) iQ[nq++] = j;
+        }
+        double cw = m->gw[g] * (c ? c[g] : 1.0);
+        for (int64_t a = 0; a < nq; a++)
+            for (int64_t b = 0; b < np; b++)
+                K[iQ[a] * n + iP[b]] += cw * Q[iQ[a]] * P[iP[b]];
+    }
+    free(P); free(Q); free(iP); free(iQ);
+    return OR_OK;
+}
+
 /* Load vector b = M f with the P1 mass matrix M_jk = sum_g w_g phi_j(x_g) phi_k(x_g),
  * j over dofs, k over all nodes.  f: column-major [n_nodes][nrhs]; b: column-major
  * [n_dof][nrhs]. */

@@ -1,0 +1,200 @@
+"""Pins of the oracle's general bilinear form (c D^alpha u, D^^beta v) (Section 2.1,
+eq. "equ:varsss", with the Gauss-quadrature element formula that follows it).
+
+Nothing here goes through the oracle's walk or tables on the expected side:
+
+* order 1 with order 1 is minus the textbook P1 stiffness of the axis with coefficient c,
+  order 0 with order 0 the P1 mass matrix weighted by c, order 1 with order 0 the
+  convection matrix; all three are formed here from the barycentric gradients of every tet
+  (numpy inverse of [[1, 1, 1, 1], [v0 v1 v2 v3]]) and the 4-point rule written out;
+* for fractional orders alpha != beta the all-nodes form reproduces linear functions:
+  v^T K u equals the quadrature sum of the closed-form Riemann-Liouville derivatives of
+  the two linear functions on the chord [0, 1] of the unit cube (power rule);
+* at alpha = beta and c = 1 the two one-sided forms add up to the Riesz term of the
+  symmetric assembly (a consistency check between two oracle functions, not a pin).
+"""
+import math
+
+import numpy as np
+import pytest
+
+RULE_A = (5.0 + 3.0 * math.sqrt(5.0)) / 20.0
+RULE_B = (5.0 - math.sqrt(5.0)) / 20.0
+AFF = ((1.0, 0.3, 0.0), (0.0, 1.0, 0.2), (0.0, 0.0, 0.7))
+
+
+def coef(x):
+    """A positive, non-constant coefficient c(x) on the meshes used here."""
+    x = np.atleast_2d(x)
+    return 1.0 + 0.5 * x[:, 0] - 0.3 * x[:, 1] + 0.8 * x[:, 2] ** 2
+
+
+def p1_quadrature(mesh):
+    """Per tet: gradients [T,4,3], Gauss-point barycentrics [4,4], points [T,4,3], weights [T]."""
+    V = mesh.verts[mesh.tets]                          # [T, 4, 3]
+    T = len(mesh.tets)
+    P = np.ones((T, 4, 4))
+    P[:, 1:, :] = np.transpose(V, (0, 2, 1))           # columns [1; v_k]
+    Minv = np.linalg.inv(P)                            # row k: lambda_k = Minv[k] . [1; x]
+    grad = Minv[:, :, 1:]                              # [T, 4, 3]
+    W = np.full((4, 4), RULE_B)
+    np.fill_diagonal(W, RULE_A)                        # point q: lambda = W[q]
+    pts = np.einsum("qk,tkd->tqd", W, V)
+    vol = np.abs(np.linalg.det(V[:, 1:, :] - V[:, :1, :])) / 6.0
+    return grad, W, pts, vol / 4.0
+
+
+def textbook(mesh, axis, kind, c_fn):
+    """All-nodes matrices K[k, l] = sum_T sum_q w c(x_q) f_l(x_q) g_k(x_q) with
+    kind 'dd': f = d_i psi_l, g = d_i psi_k;  'mm': f = psi_l, g = psi_k;
+    'dm': f = d_i psi_l, g = psi_k."""
+    grad, W, pts, w = p1_quadrature(mesh)
+    n = mesh.n_nodes
+    K = np.zeros((n, n))
+    for t in range(len(mesh.tets)):
+        nodes = mesh.tets[t]
+        cw = w[t] * c_fn(pts[t])                       # [4]
+        gi = grad[t, :, axis]                          # [4]
+        for q in range(4):
+            lam = W[q]
+            if kind == "dd":
+                loc = cw[q] * np.outer(gi, gi)
+            elif kind == "mm":
+                loc = cw[q] * np.outer(lam, lam)
+            else:                                      # rows: test psi_k, columns: d_i psi_l
+                loc = cw[q] * np.outer(lam, gi)
+            K[np.ix_(nodes, nodes)] += loc
+    return K
+
+
+def restrict(K, dof):
+    idx = np.nonzero(dof >= 0)[0]
+    order = np.argsort(dof[idx])
+    idx = idx[order]
+    return K[np.ix_(idx, idx)]
+
+
+MESHES = [(3, 0.0, None), (3, 0.2, None), (3, 0.15, AFF)]
+
+
+@pytest.mark.parametrize("n,jit,aff", MESHES)
+def test_orders_one_one_are_minus_the_textbook_stiffness(oracle_for, n, jit, aff):
+    """D_L^1 = d/dx_i and D_R^1 = -d/dx_i, so (c D_L^1 u, D_R^1 v) = -(c d_i u, d_i v)."""
+    mesh, o = oracle_for(n, jit, 5, aff)
+    cg = coef(o.gp)
+    for axis in range(3):
+        want = textbook(mesh, axis, "dd", coef)
+        for all_nodes in (True, False):
+            got = o.assemble_form(axis, 1.0, 1.0, True, cg, all_nodes)
+            ref = -want if all_nodes else -restrict(want, o.dof)
+            assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), (axis, all_nodes)
+        # the other pairing gives the same matrix: (-d u)(d v) = (d u)(-d v)
+        got_r = o.assemble_form(axis, 1.0, 1.0, False, cg, True)
+        assert np.abs(got_r + want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n,jit,aff", MESHES)
+def test_orders_zero_zero_are_the_weighted_mass_matrix(oracle_for, n, jit, aff):
+    """Order 0 is the function itself on both sides: K = (c u, v), the P1 mass matrix."""
+    mesh, o = oracle_for(n, jit, 5, aff)
+    cg = coef(o.gp)
+    want = textbook(mesh, 0, "mm", coef)
+    for axis in range(3):
+        for trial_left in (True, False):
+            got = o.assemble_form(axis, 0.0, 0.0, trial_left, cg, True)
+            assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max(), (axis, trial_left)
+            got_d = o.assemble_form(axis, 0.0, 0.0, trial_left, cg, False)
+            ref = restrict(want, o.dof)
+            assert np.abs(got_d - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,jit,aff", MESHES)
+def test_orders_one_zero_are_the_convection_matrix(oracle_for, n, jit, aff):
+    """(c D_L^1 u, D_R^0 v) = (c d_i u, v) and (c D_R^1 u, D_L^0 v) = -(c d_i u, v)."""
+    mesh, o = oracle_for(n, jit, 5, aff)
+    cg = coef(o.gp)
+    for axis in range(3):
+        want = textbook(mesh, axis, "dm", coef)
+        got_l = o.assemble_form(axis, 1.0, 0.0, True, cg, True)
+        got_r = o.assemble_form(axis, 1.0, 0.0, False, cg, True)
+        scale = np.abs(want).max()
+        assert np.abs(got_l - want).max() <= 1e-12 * scale, axis
+        assert np.abs(got_r + want).max() <= 1e-12 * scale, axis
+
+
+def _rl_linear(x, c0, c1, gamma, side):
+    """Closed-form RL derivative of order gamma in [0, 1] of p(y) = c0 + c1 y at y = x on
+    the chord [0, 1] (power rule: D_L (y - a)^m = Gamma(m+1)/Gamma(m+1-gamma) (x - a)^(m-gamma))."""
+    if side == "L":
+        d, p_end, slope = x, c0, c1                     # p = p(0) + c1 (y - 0)
+    else:
+        d, p_end, slope = 1.0 - x, c0 + c1, -c1         # p = p(1) - c1 (1 - y)
+    val = slope * d ** (1.0 - gamma) / math.gamma(2.0 - gamma)
+    if gamma < 1.0:
+        val += p_end * d ** (-gamma) / math.gamma(1.0 - gamma)
+    return val
+
+
+@pytest.mark.parametrize("alpha,beta", [(0.7, 0.4), (0.3, 0.9), (0.55, 0.55), (1.0, 0.45)])
+@pytest.mark.parametrize("n,jit", [(3, 0.0), (4, 0.2)])
+def test_unequal_orders_reproduce_linear_functions(oracle_for, alpha, beta, n, jit):
+    """P1 reproduces linear functions, so with every node's basis function
+    v^T K u = sum_g w_g c(x_g) (D^alpha l_u)(x_g) (D^^beta l_v)(x_g) for linear l_u, l_v,
+    with the derivatives in closed form on the chord [0, 1] of the unit cube."""
+    mesh, o = oracle_for(n, jit, 7)
+    z = mesh.verts
+    cg = coef(o.gp)
+    lu = (2.0, np.array([-3.0, 0.5, 1.0]))              # l(x) = const + grad . x
+    lv = (1.0, np.array([1.0, 2.0, -1.0]))
+    u = lu[0] + z @ lu[1]
+    v = lv[0] + z @ lv[1]
+    for axis in range(3):
+        for trial_left in (True, False):
+            K = o.assemble_form(axis, alpha, beta, trial_left, cg, True)
+            got = float(v @ K @ u)
+            s_u, s_v = ("L", "R") if trial_left else ("R", "L")
+            want = 0.0
+            for g in range(o.n_gp):
+                x = o.gp[g]
+                rest_u = lu[0] + x @ lu[1] - lu[1][axis] * x[axis]
+                rest_v = lv[0] + x @ lv[1] - lv[1][axis] * x[axis]
+                du = _rl_linear(x[axis], rest_u, lu[1][axis], alpha, s_u)
+                dv = _rl_linear(x[axis], rest_v, lv[1][axis], beta, s_v)
+                want += o.gw[g] * cg[g] * du * dv
+            assert abs(got - want) <= 1e-10 * max(1.0, abs(want)), (axis, trial_left, got, want)
+
+
+def test_symmetric_split_adds_up_to_the_riesz_term(oracle_for):
+    """alpha = beta = alpha_i / 2, c = 1: s K (form(L, R) + form(R, L)) summed over the axes
+    is the symmetric assembly (consistency of two oracle functions)."""
+    from oracle import riesz_scale
+
+    mesh, o = oracle_for(3, 0.2, 5)
+    alpha = (1.3, 1.6, 1.9)
+    K = (1.0, 2.0, 0.5)
+    A = o.assemble(alpha, K)
+    B = np.zeros_like(A)
+    for axis in range(3):
+        g = alpha[axis] / 2.0
+        B += riesz_scale(alpha[axis]) * K[axis] * (
+            o.assemble_form(axis, g, g, True) + o.assemble_form(axis, g, g, False))
+    assert np.abs(A - B).max() <= 1e-13 * np.abs(A).max()
+
+
+def test_coefficient_enters_linearly(oracle_for):
+    mesh, o = oracle_for(3, 0.2, 5)
+    c1 = coef(o.gp)
+    c2 = np.cos(3.0 * o.gp[:, 0]) + 2.0
+    K1 = o.assemble_form(1, 0.6, 0.8, True, c1)
+    K2 = o.assemble_form(1, 0.6, 0.8, True, c2)
+    K12 = o.assemble_form(1, 0.6, 0.8, True, c1 + c2)
+    assert np.abs(K12 - K1 - K2).max() <= 1e-13 * np.abs(K12).max()
+
+
+def test_orders_outside_zero_one_are_refused(oracle_for):
+    from oracle import OracleError
+
+    mesh, o = oracle_for(3, 0.0, 5)
+    for a, b in ((1.2, 0.3), (-0.1, 0.5), (0.5, 1.01)):
+        with pytest.raises(OracleError):
+            o.assemble_form(0, a, b)
