@@ -66,6 +66,8 @@ def _load():
         lib.or_assemble.argtypes = [p, p, p, p]
         lib.or_assemble_form.restype = C.c_int
         lib.or_assemble_form.argtypes = [p, C.c_int, dbl, dbl, C.c_int, p, C.c_int, p]
+        lib.or_assemble_divergence.restype = C.c_int
+        lib.or_assemble_divergence.argtypes = [p, p, p, p, C.c_int, p]
         lib.or_load.restype = C.c_int
         lib.or_load.argtypes = [p, p, C.c_int, p]
         lib.or_load_T.restype = C.c_int
@@ -209,6 +211,23 @@ class Oracle:
         if e:
             raise OracleError(e, "assemble_form")
         return K
+
+    def assemble_divergence(self, beta, p, q, all_nodes: bool = False) -> np.ndarray:
+        """Section 3 (eq. "equ:sfde2"): A[k, l] = a(psi_l, psi_k) with
+        a(u, v) = -sum_i ((p_i D_L^{beta_i} u, D_i v) - (q_i D_R^{beta_i} u, D_i v));
+        p, q: [3, n_gp] coefficient values at the Gauss points (``self.gp`` order)."""
+        n = self.n_nodes if all_nodes else self.n_dof
+        b = np.ascontiguousarray(beta, dtype=np.float64)
+        pg = np.ascontiguousarray(p, dtype=np.float64)
+        qg = np.ascontiguousarray(q, dtype=np.float64)
+        if b.shape != (3,) or pg.shape != (3, self.n_gp) or qg.shape != (3, self.n_gp):
+            raise ValueError("beta [3], p and q [3, n_gp]")
+        A = np.empty((n, n))
+        e = self._lib.or_assemble_divergence(self._h, _ptr(b), _ptr(pg), _ptr(qg),
+                                             int(bool(all_nodes)), _ptr(A))
+        if e:
+            raise OracleError(e, "assemble_divergence")
+        return A
 
     def load(self, f: np.ndarray) -> np.ndarray:
         """b = M f; f nodal [n_nodes] or [n_nodes, nrhs]; returns [n_dof] or [n_dof, nrhs]."""

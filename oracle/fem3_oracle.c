@@ -23,6 +23,10 @@
  *   - Section 2.1: element-sum Galerkin matrix with Gauss quadrature,
  *        A_jk = sum_i s_i K_i sum_g w_g (D_R phi_j D_L phi_k + D_L phi_j D_R phi_k)(x_g)
  *     with the Riesz constant s_i = 1/(2 cos(pi alpha_i/2)) and order g_i = alpha_i/2.
+ *   - Section 2.1, eq. "equ:varsss": one axis term of the general form
+ *     (c D^alpha u, D^^beta v) with a coefficient and unequal orders in [0, 1], and
+ *     Section 3, eq. "equ:sfde2": the divergence-form operator with coefficients p_i, q_i
+ *     through its variational form (not symmetric).
  *   - The dense SPD solve (textbook Cholesky), the P1 load vector and the adjoint.
  *
  * Parity of each function is pinned by tests against closed forms, brute force and
@@ -501,6 +505,46 @@ int or_assemble_form(const or_mesh *m, int axis, double alpha, double beta, int 
                 K[iQ[a] * n + iP[b]] += cw * Q[iQ[a]] * P[iP[b]];
     }
     free(P); free(Q); free(iP); free(iQ);
+    return OR_OK;
+}
+
+/* The divergence-form operator with variable coefficients of Section 3 (eq. "equ:sfde2")
+ * through its variational form
+ *   a(u, v) = - sum_i ( (p_i D_L^{beta_i} u, D_i v) - (q_i D_R^{beta_i} u, D_i v) ),
+ * D_i the classical derivative, by the same Gauss quadrature:
+ *   A[k][l] = a(psi_l, psi_k)
+ *           = - sum_i sum_g w_g D_i psi_k(x_g) (p_i(x_g) D_L psi_l(x_g) - q_i(x_g) D_R psi_l(x_g)).
+ * D_i psi_k(x_g) is the order-1 left table row.  beta_i in [0, 1]; p, q: [3][n_gp]
+ * coefficient values at the Gauss points.  all_nodes as in or_assemble_form.  A:
+ * row-major [n][n]; it is not symmetric. */
+int or_assemble_divergence(const or_mesh *m, const double beta[3], const double *p,
+                           const double *q, int all_nodes, double *A)
+{
+    for (int i = 0; i < 3; i++)
+        if (!(beta[i] >= 0.0 && beta[i] <= 1.0)) return OR_E_ARG;
+    int64_t n = all_nodes ? m->n_nodes : m->n_dof;
+    int64_t nn = n > 0 ? n : 1;
+    memset(A, 0, sizeof(double) * n * n);
+    double *L = calloc(nn, sizeof(double)), *R = calloc(nn, sizeof(double));
+    double *D = calloc(nn, sizeof(double));
+    if (!L || !R || !D) { free(L); free(R); free(D); return OR_E_OOM; }
+    for (int axis = 0; axis < 3; axis++) {
+        for (int64_t g = 0; g < m->n_gp; g++) {
+            int e1 = or_table_row(m, g, axis, -1, beta[axis], all_nodes, L);
+            int e2 = or_table_row(m, g, axis, +1, beta[axis], all_nodes, R);
+            int e3 = or_table_row(m, g, axis, -1, 1.0, all_nodes, D);
+            if (e1 || e2 || e3) { free(L); free(R); free(D); return e1 ? e1 : (e2 ? e2 : e3); }
+            double pw = m->gw[g] * p[axis * m->n_gp + g], qw = m->gw[g] * q[axis * m->n_gp + g];
+            for (int64_t k = 0; k < n; k++) {
+                if (D[k] == 0.0) continue;
+                for (int64_t l = 0; l < n; l++) {
+                    double flux = pw * L[l] - qw * R[l];
+                    if (flux != 0.0) A[k * n + l] -= D[k] * flux;
+                }
+            }
+        }
+    }
+    free(L); free(R); free(D);
     return OR_OK;
 }
 

@@ -12,6 +12,11 @@ Nothing here goes through the oracle's walk or tables on the expected side:
   the two linear functions on the chord [0, 1] of the unit cube (power rule);
 * at alpha = beta and c = 1 the two one-sided forms add up to the Riesz term of the
   symmetric assembly (a consistency check between two oracle functions, not a pin).
+
+The divergence form of Section 3 (eq. "equ:sfde2") is pinned the same way: at beta = 1 it is
+minus the textbook stiffness with coefficient p_i + q_i, on linear functions it equals the
+quadrature sum of closed-form derivatives, and Section 3's problem with the paper's
+coefficients, moved to the unit cube, converges to its manufactured solution.
 """
 import math
 
@@ -198,3 +203,119 @@ def test_orders_outside_zero_one_are_refused(oracle_for):
     for a, b in ((1.2, 0.3), (-0.1, 0.5), (0.5, 1.01)):
         with pytest.raises(OracleError):
             o.assemble_form(0, a, b)
+
+
+# --- Section 3, eq. "equ:sfde2": divergence form with variable coefficients ---------------
+
+def _pq(x, i):
+    """Coefficients of one axis: p_i = cos(x_i), q_i = 1 - cos(x_i) (the paper's choice)."""
+    x = np.atleast_2d(x)
+    return np.cos(x[:, i]), 1.0 - np.cos(x[:, i])
+
+
+def _pq_gp(o):
+    p = np.stack([_pq(o.gp, i)[0] for i in range(3)])
+    q = np.stack([_pq(o.gp, i)[1] for i in range(3)])
+    return p, q
+
+
+def test_divergence_form_at_order_one_is_minus_the_laplacian(oracle_for):
+    """beta = 1: D_L^1 = D_i, D_R^1 = -D_i, so a(u, v) = -sum_i ((p_i + q_i) D_i u, D_i v);
+    with non-constant p_i + q_i the expected side is the textbook stiffness per axis."""
+    mesh, o = oracle_for(3, 0.2, 5)
+    p = np.stack([1.0 + 0.3 * o.gp[:, i] for i in range(3)])
+    q = np.stack([0.5 + o.gp[:, (i + 1) % 3] ** 2 for i in range(3)])
+    got = o.assemble_divergence((1.0, 1.0, 1.0), p, q, all_nodes=True)
+    want = np.zeros_like(got)
+    for i in range(3):
+        want -= textbook(mesh, i, "dd",
+                         lambda x, i=i: 1.5 + 0.3 * x[:, i] + x[:, (i + 1) % 3] ** 2)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("beta", [(0.8, 0.8, 0.8), (0.6, 0.7, 0.8)])
+def test_divergence_form_on_linear_functions(oracle_for, beta):
+    """v^T A u = -sum_g w_g sum_i D_i l_v (p_i D_L^b l_u - q_i D_R^b l_u)(x_g), the
+    derivatives of the linear function l_u in closed form on the chord [0, 1]."""
+    mesh, o = oracle_for(4, 0.2, 7)
+    z = mesh.verts
+    p, q = _pq_gp(o)
+    lu = (2.0, np.array([-3.0, 0.5, 1.0]))
+    lv = (1.0, np.array([1.0, 2.0, -1.0]))
+    u = lu[0] + z @ lu[1]
+    v = lv[0] + z @ lv[1]
+    got = float(v @ o.assemble_divergence(beta, p, q, all_nodes=True) @ u)
+    want = 0.0
+    for g in range(o.n_gp):
+        x = o.gp[g]
+        for i in range(3):
+            rest = lu[0] + x @ lu[1] - lu[1][i] * x[i]
+            dl = _rl_linear(x[i], rest, lu[1][i], beta[i], "L")
+            dr = _rl_linear(x[i], rest, lu[1][i], beta[i], "R")
+            want -= o.gw[g] * lv[1][i] * (p[i, g] * dl - q[i, g] * dr)
+    assert abs(got - want) <= 1e-10 * max(1.0, abs(want)), (got, want)
+
+
+def test_divergence_form_is_the_sum_of_one_axis_forms(oracle_for):
+    """(p D_L^b u, D_i v) = -form(i, b, 1, left, p), (q D_R^b u, D_i v) = form(i, b, 1, right, q)
+    (consistency of two oracle functions)."""
+    mesh, o = oracle_for(3, 0.2, 5)
+    p, q = _pq_gp(o)
+    beta = (0.6, 0.7, 0.8)
+    A = o.assemble_divergence(beta, p, q)
+    B = sum(o.assemble_form(i, beta[i], 1.0, True, p[i]) + o.assemble_form(i, beta[i], 1.0, False, q[i])
+            for i in range(3))
+    assert np.abs(A - B).max() <= 1e-13 * np.abs(A).max()
+
+
+_G = {2: 1.0, 3: -2.0, 4: 1.0}   # g(t) = t^2 (1 - t)^2
+
+
+def _dl_g(t, b, deriv=False):
+    """D_L^b g on [0, t] by the power rule, or its t-derivative."""
+    out = np.zeros_like(t)
+    for m, c in _G.items():
+        k = c * math.gamma(m + 1) / math.gamma(m + 1 - b)
+        out += k * (m - b) * t ** (m - b - 1) if deriv else k * t ** (m - b)
+    return out
+
+
+def _divergence_source(x, beta):
+    """f = sum_i D_i (p_i D_L^b u - q_i D_R^b u) for u = prod g(x_k) on the unit cube;
+    g is symmetric about 1/2, so D_R^b g at t is D_L^b g at 1 - t."""
+    x = np.clip(np.atleast_2d(x), 0.0, 1.0)
+    gx = [sum(c * x[:, k] ** m for m, c in _G.items()) for k in range(3)]
+    f = np.zeros(len(x))
+    for i in range(3):
+        t, b = x[:, i], beta[i]
+        h = gx[(i + 1) % 3] * gx[(i + 2) % 3]
+        f += h * (-np.sin(t) * _dl_g(t, b) + np.cos(t) * _dl_g(t, b, True)
+                  - np.sin(t) * _dl_g(1.0 - t, b) + (1.0 - np.cos(t)) * _dl_g(1.0 - t, b, True))
+    return f
+
+
+@pytest.mark.parametrize("beta", [(0.8, 0.8, 0.8), (0.6, 0.7, 0.8)])
+def test_divergence_form_manufactured_solution_converges(oracle_for, beta):
+    """Section 3's problem on the unit cube instead of the ball (its meshes are not
+    given): u = prod x_i^2 (1 - x_i)^2, p_i = cos x_i, q_i = 1 - cos x_i; the L2 error
+    falls with order close to 2 (the paper reports 1.6 - 1.95 on balls).  Between n = 6
+    and 12 the order is about 1.7 (n = 4 is still pre-asymptotic for this profile: the
+    same pipeline at beta = 1, the Laplacian, gives 1.5 from 4 to 8 and 1.8 from 8 to 12)."""
+    from paper_1811_03339_gb300 import inputs
+
+    errs = []
+    ns = (6, 12)
+    W = np.full((4, 4), RULE_B)
+    np.fill_diagonal(W, RULE_A)
+    for n in ns:
+        mesh, o = oracle_for(n, 0.0, 0)
+        p, q = _pq_gp(o)
+        A = o.assemble_divergence(beta, p, q)
+        b = o.load(_divergence_source(mesh.verts, beta))
+        u = np.linalg.solve(A, b)
+        full = np.zeros(mesh.n_nodes)
+        full[o.dof >= 0] = u[o.dof[o.dof >= 0]]
+        uh = (full[mesh.tets][:, None, :] * W[None]).sum(-1).ravel()
+        errs.append(math.sqrt(float((o.gw * (uh - inputs.manufactured_u(o.gp)) ** 2).sum())))
+    order = math.log(errs[0] / errs[1]) / math.log(ns[1] / ns[0])
+    assert order > 1.5, (errs, order)
