@@ -338,8 +338,8 @@ int fem3_load(fem3_mesh h, const double *f, int nrhs, double *b, void *stream) {
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m || !f || !b || nrhs < 1) return set_error(FEM3_E_ARG, "bad argument");
     m->stream = reinterpret_cast<cudaStream_t>(stream);
-    const void *fd;
-    void *owned;
+    const void *fd = nullptr;
+    void *owned = nullptr;
     FEM3_TRY(to_device(m, f, sizeof(double) * m->n_nodes * nrhs, &fd, &owned));
     int st = load_vector(m, (const double *)fd, nrhs, b);
     if (owned) cudaFreeAsync(owned, m->stream);
@@ -358,8 +358,8 @@ int fem3_solve(fem3_mesh h, const double *f, int nrhs, double tol, int max_iter,
         if (resid_out) *resid_out = 0;
         return check_errors(m);
     }
-    const void *fd;
-    void *owned;
+    const void *fd = nullptr;
+    void *owned = nullptr;
     FEM3_TRY(to_device(m, f, sizeof(double) * m->n_nodes * nrhs, &fd, &owned));
     double *b = nullptr;
     int st = FEM3_OK;
