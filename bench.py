@@ -68,6 +68,24 @@ def _dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of the ranks' values of x (x itself on one rank): the job takes as long as
+    its slowest rank.  A collective when world > 1: every rank calls it."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank_step: float, steps: int, total_ms: float) -> float:
+    """Units all ranks processed per second over the slowest rank's time (weak scaling: every
+    rank processes the same units each step)."""
+    return world * units_per_rank_step * steps / (total_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -241,13 +259,9 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         times = timed(args.precision, args.steps, args.warmup)
     barrier()
-    t_mix = sum(times)
-    if world > 1:
-        t = torch.tensor([t_mix], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_mix = float(t.item())
+    t_mix = max_over_ranks(sum(times), world, dev)
     ms_step = t_mix / args.steps
-    value = world * n_paths * args.steps / (t_mix / 1e3)
+    value = whole_job_rate(world, n_paths, args.steps, t_mix)
 
     # --- FP64 form (comparison) ----------------------------------------------------
     k64 = max(2, min(args.steps, 5))
@@ -329,7 +343,7 @@ def run_ours(args):
         mh.free()
         if it >= args.warmup:
             e2e_t.append(e0.elapsed_time(e1))
-    e2e_value = world * n_paths * len(e2e_t) / (sum(e2e_t) / 1e3)
+    e2e_value = whole_job_rate(world, n_paths, len(e2e_t), max_over_ranks(sum(e2e_t), world, dev))
     h2d = mesh.verts.nbytes + mesh.tets.nbytes + f_host.nbytes
     d2h = 8 * n_dof
 

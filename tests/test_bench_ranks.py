@@ -1,0 +1,67 @@
+"""Multi-rank logic of bench.py on CPU ranks (gloo, world size 2, launched like the GPU run:
+torch.distributed.run on 127.0.0.1): every rank gets the slowest rank's time, the value
+counts the units of all ranks, and the reference arm runs on rank 0 only."""
+import json
+import os
+import socket
+import subprocess
+import sys
+import textwrap
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_slowest_rank_sets_the_job_time(tmp_path):
+    pytest.importorskip("torch.distributed")
+    script = tmp_path / "ranks.py"
+    script.write_text(textwrap.dedent(f"""
+        import json, sys
+        sys.path.insert(0, {ROOT!r})
+        import torch.distributed as dist
+        import bench
+        dist.init_process_group("gloo")
+        rank, world, _ = bench._dist_env()
+        local_ms = [120.0, 200.0][rank]          # rank 1 is the slow one
+        t = bench.max_over_ranks(local_ms, world)
+        rate = bench.whole_job_rate(world, 1000, 4, t)
+        with open({str(tmp_path)!r} + f"/rank{{rank}}.json", "w") as fh:
+            json.dump({{"rank": rank, "world": world, "t": t, "rate": rate}}, fh)
+        dist.destroy_process_group()
+    """))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1", "--nproc-per-node",
+           "2", "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), str(script)]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    rows = [json.loads((tmp_path / f"rank{r}.json").read_text()) for r in range(2)]
+    assert sorted(r["rank"] for r in rows) == [0, 1]
+    for r in rows:
+        assert r["world"] == 2
+        assert r["t"] == 200.0
+        # 2 ranks x 1000 units x 4 steps in the slowest rank's 0.2 s
+        assert r["rate"] == pytest.approx(2 * 1000 * 4 / 0.2)
+
+
+def test_one_rank_is_the_plain_rate():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.max_over_ranks(12.5, 1) == 12.5
+    assert bench.whole_job_rate(1, 294912, 20, 80.0) == pytest.approx(294912 * 20 / 0.08)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """A non-zero rank of `bench.py --impl reference` exits 0 at once and prints nothing."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--gpus", "2"], capture_output=True, text=True, timeout=120, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.strip() == ""
