@@ -453,7 +453,8 @@ def run_batch(args, torch, fem3, inputs, stream):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    # 100 steps of about 4 ms keep the timed region long enough for several 200 ms clock samples
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "fp32", "fp64"])
