@@ -80,6 +80,25 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def contraction_rates(bin_dense_flops: float, stage_ms: float, precision: str, peaks: dict) -> dict:
+    """Tensor-core rate of the contraction stage: the split forms run three products
+    (hi hi, hi lo, lo hi) of the bins' dense flops 2 D_b^2 G_b on the MMA pipe; the rate is
+    taken over the whole stage (operand split, zeroing of A and the three launches), against
+    the measured sustained BF16 peak times the nominal dense TF32 : BF16 ratio 1.1 : 2.25 for
+    TF32.  Padding of the tiles to 128 rows and 16 columns is not counted.  Forms that do not
+    use the tensor cores get None."""
+    ratio = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0}.get(precision)
+    if ratio is None or not stage_ms or stage_ms <= 0:
+        return {"mma_tflops": None}
+    executed = 3.0 * bin_dense_flops
+    rate = executed / (stage_ms * 1e-3) / 1e12
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))) * ratio
+    return {"executed_mma_tflop": executed / 1e12, "mma_tflops": rate,
+            "mma_peak_tflops": peak, "mma_frac": rate / peak,
+            "mma_note": "three split products over the contraction stage time; peak = measured "
+                        "sustained bf16 x " + ("1.1/2.25 (tf32)" if precision == "tf32x3" else "1")}
+
+
 def whole_job_rate(world: int, units_per_rank_step: float, steps: int, total_ms: float) -> float:
     """Units all ranks processed per second over the slowest rank's time (weak scaling: every
     rank processes the same units each step)."""
@@ -397,7 +416,8 @@ def run_ours(args):
             "table_bytes": cnt["table_bytes"],
             "contraction": {"bin_dense_gflop": ctr_flops / 1e9,
                             "gflops": ctr_flops / (stages[3] * 1e-3) / 1e9 if stages[3] > 0 else None,
-                            "tile_n": tile_n or None},
+                            "tile_n": tile_n or None,
+                            **contraction_rates(ctr_flops, stages[3], args.precision, peaks)},
             "peaks_source": src,
             "batch": batch,
         }

@@ -65,3 +65,21 @@ def test_reference_arm_runs_on_rank_zero_only():
                           "--gpus", "2"], capture_output=True, text=True, timeout=120, env=env)
     assert out.returncode == 0, out.stderr[-2000:]
     assert out.stdout.strip() == ""
+
+
+def test_contraction_rates():
+    """Executed MMA flops of the split forms (three products) over the stage time, against
+    the measured BF16 peak scaled by the nominal TF32 : BF16 ratio."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    peaks = {"bf16_tflops": 1934.0, "bf16_tflops_sustained": 1746.0}
+    r = bench.contraction_rates(7.45e9, 0.559, "tf32x3", peaks)
+    assert r["executed_mma_tflop"] == pytest.approx(3 * 7.45e9 / 1e12)
+    assert r["mma_tflops"] == pytest.approx(3 * 7.45e9 / 0.559e-3 / 1e12)
+    assert r["mma_peak_tflops"] == pytest.approx(1746.0 * 1.1 / 2.25)
+    assert r["mma_frac"] == pytest.approx(r["mma_tflops"] / r["mma_peak_tflops"])
+    b = bench.contraction_rates(7.45e9, 0.489, "bf16x3", {"bf16_tflops": 1900.0})
+    assert b["mma_peak_tflops"] == pytest.approx(1900.0)
+    assert bench.contraction_rates(7.45e9, 20.0, "fp64", peaks) == {"mma_tflops": None}
+    assert bench.contraction_rates(7.45e9, 0.0, "tf32x3", peaks) == {"mma_tflops": None}
