@@ -99,6 +99,21 @@ def contraction_rates(bin_dense_flops: float, stage_ms: float, precision: str, p
                         "sustained bf16 x " + ("1.1/2.25 (tf32)" if precision == "tf32x3" else "1")}
 
 
+def walk_bandwidth(table_bytes: float, traffic_bytes, walk_ms: float, peaks: dict) -> dict:
+    """Bandwidth side of the walk + tables launch: the tables it writes (hi + lo pairs of
+    every bin block, zeroed and accumulated by the walking threads) and its measured DRAM
+    traffic per launch, each over the launch time, and the traffic's fraction of the
+    measured copy bandwidth."""
+    if not walk_ms or walk_ms <= 0:
+        return {"table_gbs": None}
+    out = {"table_bytes": table_bytes, "table_gbs": table_bytes / (walk_ms * 1e-3) / 1e9,
+           "hbm_peak_gbs": float(peaks["hbm_gbs"])}
+    if traffic_bytes:
+        out["traffic_gbs"] = traffic_bytes / (walk_ms * 1e-3) / 1e9
+        out["traffic_frac"] = out["traffic_gbs"] / out["hbm_peak_gbs"]
+    return out
+
+
 def whole_job_rate(world: int, units_per_rank_step: float, steps: int, total_ms: float) -> float:
     """Units all ranks processed per second over the slowest rank's time (weak scaling: every
     rank processes the same units each step)."""
@@ -414,6 +429,7 @@ def run_ours(args):
             "segments_per_step": cnt["segments"],
             "refinement": {"iterations": ir_iters, "final_rel_residual": ir_resid, "tol": args.tol},
             "table_bytes": cnt["table_bytes"],
+            "walk_bandwidth": walk_bandwidth(cnt["table_bytes"], traffic, stages[2], peaks),
             "contraction": {"bin_dense_gflop": ctr_flops / 1e9,
                             "gflops": ctr_flops / (stages[3] * 1e-3) / 1e9 if stages[3] > 0 else None,
                             "tile_n": tile_n or None,

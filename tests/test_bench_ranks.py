@@ -83,3 +83,15 @@ def test_contraction_rates():
     assert b["mma_peak_tflops"] == pytest.approx(1900.0)
     assert bench.contraction_rates(7.45e9, 20.0, "fp64", peaks) == {"mma_tflops": None}
     assert bench.contraction_rates(7.45e9, 0.0, "tf32x3", peaks) == {"mma_tflops": None}
+
+
+def test_walk_bandwidth():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    r = bench.walk_bandwidth(527e6, 749e6, 1.15, {"hbm_gbs": 6657.6})
+    assert r["table_gbs"] == pytest.approx(527e6 / 1.15e-3 / 1e9)
+    assert r["traffic_gbs"] == pytest.approx(749e6 / 1.15e-3 / 1e9)
+    assert r["traffic_frac"] == pytest.approx(r["traffic_gbs"] / 6657.6)
+    assert "traffic_gbs" not in bench.walk_bandwidth(527e6, None, 1.15, {"hbm_gbs": 6800.0})
+    assert bench.walk_bandwidth(527e6, 749e6, 0.0, {"hbm_gbs": 6800.0}) == {"table_gbs": None}
