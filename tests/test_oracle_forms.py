@@ -319,3 +319,51 @@ def test_divergence_form_manufactured_solution_converges(oracle_for, beta):
         errs.append(math.sqrt(float((o.gw * (uh - inputs.manufactured_u(o.gp)) ** 2).sum())))
     order = math.log(errs[0] / errs[1]) / math.log(ns[1] / ns[0])
     assert order > 1.5, (errs, order)
+
+
+def _rl_chord(a, b, x, c0, c1, gamma, side):
+    """RL derivative of order gamma in [0, 1] of p(y) = c0 + c1 y at y = x on the chord [a, b]."""
+    if side == "L":
+        d, p_end, slope = x - a, c0 + c1 * a, c1
+    else:
+        d, p_end, slope = b - x, c0 + c1 * b, -c1
+    val = slope * d ** (1.0 - gamma) / math.gamma(2.0 - gamma)
+    if gamma < 1.0:
+        val += p_end * d ** (-gamma) / math.gamma(1.0 - gamma)
+    return val
+
+
+def test_unequal_orders_on_the_parallelepiped(oracle_for):
+    """The linear-function identity on the parallelepiped {M y : y in [0, 1]^3}, whose chords
+    [a_i(x), b_i(x)] differ from point to point: their ends come from the plane intersections
+    in closed form, not from the walk."""
+    aff = np.asarray(AFF)
+    Minv = np.linalg.inv(aff)
+    mesh, o = oracle_for(3, 0.15, 2, AFF)
+    z = mesh.verts
+    cg = coef(o.gp)
+    lu = (2.0, np.array([-3.0, 0.5, 1.0]))
+    lv = (1.0, np.array([1.0, 2.0, -1.0]))
+    u = lu[0] + z @ lu[1]
+    v = lv[0] + z @ lv[1]
+    alpha, beta = 0.7, 0.35
+    for axis in range(3):
+        K = o.assemble_form(axis, alpha, beta, True, cg, True)
+        got = float(v @ K @ u)
+        want = 0.0
+        for g in range(o.n_gp):
+            x = o.gp[g]
+            y0, cdir = Minv @ x, Minv[:, axis]
+            lo, hi = -np.inf, np.inf
+            for k in range(3):
+                if abs(cdir[k]) < 1e-15:
+                    continue
+                t1, t2 = -y0[k] / cdir[k], (1.0 - y0[k]) / cdir[k]
+                lo, hi = max(lo, min(t1, t2)), min(hi, max(t1, t2))
+            a, b = x[axis] + lo, x[axis] + hi
+            rest_u = lu[0] + x @ lu[1] - lu[1][axis] * x[axis]
+            rest_v = lv[0] + x @ lv[1] - lv[1][axis] * x[axis]
+            du = _rl_chord(a, b, x[axis], rest_u, lu[1][axis], alpha, "L")
+            dv = _rl_chord(a, b, x[axis], rest_v, lv[1][axis], beta, "R")
+            want += o.gw[g] * cg[g] * du * dv
+        assert abs(got - want) <= 1e-10 * max(1.0, abs(want)), (axis, got, want)
