@@ -201,6 +201,12 @@ int fem3_stage_ms(fem3_mesh m, int stage, float *ms);
 int fem3_counters(fem3_mesh m, int64_t *segments, double *contract_flops,
                   int64_t *table_bytes, int64_t *launches);
 
+/* Transverse bins of one axis (Section 2.3 template, per axis): number of bins, template
+ * rows summed over the bins, and the largest template dof set and Gauss-point count of a
+ * bin.  axis in 0..2; any output pointer may be NULL. */
+int fem3_bin_stats(fem3_mesh m, int axis, int64_t *n_bins, int64_t *n_tmpl, int32_t *max_dof,
+                   int32_t *max_gp);
+
 /* Tile width (128 or 256 columns) of the last tensor-core contraction of this handle, 0 if
  * none, and whether that contraction ran the tuner (1) or used a forced or cached width
  * (0).  Any output pointer may be NULL. */
@@ -241,19 +247,22 @@ void fem3_batch_free(fem3_batch b);
 /*
  * fem3_spd_solve_static - solve A x = b for a dense symmetric positive definite matrix
  * without allocating any device memory.  The paper has no counterpart: this entry
- * point exists for callers that cannot call cudaMalloc where they need a solve (code
- * running while a stream is captured into a CUDA graph, latency-critical loops that
- * must not enter the allocator, host applications that own every device allocation).
+ * point exists for callers that cannot call cudaMalloc where they need a solve
+ * (latency-critical loops that must not enter the allocator, host applications or plugin
+ * hosts that own every device allocation and hand the library only the problem's
+ * buffers).
  *
  *   A       device float64 row-major [n][n], SPD; read only (the lower triangle is used).
  *   b       device float64 [n]; read only.
  *   x       device float64 [n]; receives the solution.
  *   n       1 <= n <= 512; larger systems are rejected with FEM3_E_ARG.
+ * A, b and x must be device (or managed) memory of the current device; any other pointer
+ * is rejected with FEM3_E_ARG before a kernel runs.
  * Working memory is one static device array of about 2.1 MB (a 512 x 512 FP64 factor,
  * one 64 x 64 block inverse and an error word) that every GPU which loads the library
  * holds until the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls share the array and it keeps the last call's
+ * device address (cudaGetSymbolAddress) with the device current.  All calls share the
+ * array and it keeps the last call's
  * contents: each call clears the error word and rewrites the factor, so calls that
  * overlap on the GPU (other streams, other host threads) race and must be serialised
  * by the caller.  Synchronises `stream`.  Errors: FEM3_E_ARG, FEM3_E_NOT_SPD,

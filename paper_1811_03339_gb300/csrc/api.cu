@@ -475,6 +475,18 @@ int fem3_tc_tile(fem3_mesh h, int32_t *tile_n, int32_t *tuned) {
     return FEM3_OK;
 }
 
+int fem3_bin_stats(fem3_mesh h, int axis, int64_t *n_bins, int64_t *n_tmpl, int32_t *max_dof,
+                   int32_t *max_gp) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || axis < 0 || axis > 2) return set_error(FEM3_E_ARG, "bad argument");
+    const AxisBins &B = m->bins[axis];
+    if (n_bins) *n_bins = B.n_bins;
+    if (n_tmpl) *n_tmpl = B.n_tmpl;
+    if (max_dof) *max_dof = B.max_dof;
+    if (max_gp) *max_gp = B.max_gp;
+    return FEM3_OK;
+}
+
 int fem3_counters(fem3_mesh h, int64_t *segments, double *contract_flops, int64_t *table_bytes,
                   int64_t *launches) {
     Mesh *m = reinterpret_cast<Mesh *>(h);

@@ -1,17 +1,19 @@
 // fem3_spd_solve_static: a dense SPD solve that allocates no device memory.
 //
 // Some callers cannot allocate device memory at the point where they need a solve:
-// code that runs while a CUDA stream is being captured into a graph (cudaMalloc is not
-// allowed there), latency-critical loops that must never enter the allocator, and host
-// applications or plugin hosts that own every device allocation themselves and hand
-// the library only the buffers of the problem.  This entry point serves them: its
-// working memory (the Cholesky factor, the inverse of the current 64 x 64 diagonal
-// block and an error word) is one file-scope static device array, so the caller passes
-// only the matrix, the right-hand side and the output.
+// latency-critical loops that must never enter the allocator, and host applications or
+// plugin hosts that own every device allocation themselves and hand the library only the
+// buffers of the problem.  This entry point serves them: its working memory (the
+// Cholesky factor, the inverse of the current 64 x 64 diagonal block and an error word)
+// is one file-scope static device array, so the caller passes only the matrix, the
+// right-hand side and the output.  Each call ends by reading the error word back and
+// synchronising its stream.
 //
-// It follows the same blocked right-looking Cholesky (64-wide blocks: diagonal factor
-// and inverse, panel product, trailing update) and blocked forward/backward
-// substitution as fem3_solve's FP64 form, in its own copies of those kernels.
+// The factorisation is its own multi-launch blocked right-looking Cholesky (64-wide
+// blocks: diagonal factor and inverse, panel product, trailing update of the lower
+// triangle, one launch each per block column) followed by blocked forward and backward
+// substitution.  It shares no kernel with fem3_solve, whose FP64 form serves only as the
+// reference in the test of this entry point.
 #include <math.h>
 
 #include <mutex>
@@ -202,6 +204,22 @@ int na_scratch(double **out) {
     return FEM3_OK;
 }
 
+// true if p is device (or managed) memory that the current device can use directly
+bool on_current_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 
 }  // namespace fem3
@@ -214,6 +232,11 @@ extern "C" int fem3_spd_solve_static(const double *A, int64_t n, const double *b
     if (n < 1 || n > kNaMaxN)
         return set_error(FEM3_E_ARG, "fem3_spd_solve_static accepts 1 <= n <= 512 (its static "
                                      "working memory holds one 512 x 512 factor)");
+    // the kernels read A and b and write x directly: all three must be device memory of
+    // the current device (a host or foreign-device pointer is rejected, never dereferenced)
+    if (!on_current_device(A) || !on_current_device(b) || !on_current_device(x))
+        return set_error(FEM3_E_ARG, "fem3_spd_solve_static: A, b and x must be device memory "
+                                     "of the current device");
     double *scratch = nullptr;
     FEM3_TRY(na_scratch(&scratch));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -25,7 +25,8 @@ PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2, "bf16x3": 3}
 # every entry point declared in include/fem3.h
 SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_load", "fem3_solve",
            "fem3_adjoint", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
-           "fem3_counters", "fem3_tc_tile", "fem3_last_error", "fem3_mesh_free",
+           "fem3_counters", "fem3_bin_stats", "fem3_tc_tile", "fem3_last_error",
+           "fem3_mesh_free",
            "fem3_spd_solve_static",
            "fem3_batch_create", "fem3_batch_mesh", "fem3_batch_run", "fem3_batch_free")
 
@@ -71,6 +72,7 @@ def load_library(build_if_missing: bool = True):
         "fem3_stage_ms": [p, ci, C.POINTER(C.c_float)],
         "fem3_counters": [p, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)],
         "fem3_tc_tile": [p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+        "fem3_bin_stats": [p, ci, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)],
         "fem3_last_error": [C.c_char_p, C.c_size_t],
         "fem3_mesh_free": [p],
         "fem3_spd_solve_static": [p, i64, p, p, p],
@@ -184,6 +186,12 @@ def counters(h):
     return dict(segments=s.value, contract_flops=f.value, table_bytes=b.value, launches=n.value)
 
 
+def bin_stats(h, axis):
+    nb, nt, md, mg = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int32()
+    _check(_lib.fem3_bin_stats(h, int(axis), C.byref(nb), C.byref(nt), C.byref(md), C.byref(mg)))
+    return dict(n_bins=nb.value, n_tmpl=nt.value, max_dof=md.value, max_gp=mg.value)
+
+
 def tc_tile(h):
     t, u = C.c_int32(), C.c_int32()
     _check(_lib.fem3_tc_tile(h, C.byref(t), C.byref(u)))
@@ -191,8 +199,18 @@ def tc_tile(h):
 
 
 def spd_solve_static(A, b, x, stream=None):
-    """Dense SPD solve with no device allocation (n <= 512); see include/fem3.h."""
+    """Dense SPD solve with no device allocation (n <= 512): A (n, n), b and x (n,), all
+    contiguous float64 CUDA tensors on the current device (see include/fem3.h)."""
+    import torch
     lib = load_library()
+    dev = torch.cuda.current_device()
+    for name, t in (("A", A), ("b", b), ("x", x)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous() and t.device.index == dev):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor on device {dev}")
+    n = A.shape[0] if A.dim() == 2 else -1
+    if A.dim() != 2 or A.shape[1] != n or b.shape != (n,) or x.shape != (n,):
+        raise ValueError("A must be (n, n), b and x (n,)")
     _check(lib.fem3_spd_solve_static(_ptr(A), int(A.shape[0]), _ptr(b), _ptr(x), _stream(stream)))
 
 
@@ -284,6 +302,10 @@ class Mesh:
 
     def counters(self):
         return counters(self.h)
+
+    def bin_stats(self, axis):
+        """bins of one axis: count, template rows, largest dof set and Gauss-point count"""
+        return bin_stats(self.h, axis)
 
     def tc_tile(self):
         """(tile width of the last tensor-core contraction, whether it ran the tuner)"""

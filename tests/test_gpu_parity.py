@@ -262,7 +262,11 @@ def test_load_vector():
 
 
 def test_full_size_cube16_fp64_matrix():
-    """16^3 jittered cube (24,576 tets, 3,375 dofs): whole matrix and solution."""
+    """16^3 jittered cube (24,576 tets, 3,375 dofs): whole FP64 matrix and solution, then
+    the whole tensor-core matrices element by element with each tile width forced: at this
+    size many bins hold more than 128 (and 256) dofs, so the multi-tile register epilogue
+    (m and n tiles > 0) is compared with the oracle, not only the one-tile shared-memory
+    epilogue of the small meshes."""
     mesh, o, alpha, K = _case("cube16_jitter")
     m = fem3.Mesh(mesh.verts, mesh.tets)
     A = m.assemble(alpha, K, "fp64", return_matrix=True).cpu().numpy()
@@ -272,41 +276,141 @@ def test_full_size_cube16_fp64_matrix():
     u = m.solve(f).cpu().numpy()
     u_ref = oracle.solve(A_ref, o.load(f))
     assert np.linalg.norm(u - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
+    assert max(m.bin_stats(a)["max_dof"] for a in range(3)) > 128
     # mixed form reaches the FP64 solution to 1e-8
     m.assemble(alpha, K, "tf32x3")
     u2 = m.solve(f, tol=1e-13).cpu().numpy()
     assert np.linalg.norm(u2 - u_ref) <= 1e-8 * np.linalg.norm(u_ref)
     m.free()
+    for tile in (128, 256):
+        mt = fem3.Mesh(mesh.verts, mesh.tets, tc_tile=tile)
+        for precision, bar in (("tf32x3", 2e-6), ("bf16x3", 1e-4)):
+            At = mt.assemble(alpha, K, precision, return_matrix=True).cpu().numpy()
+            mt.sync()
+            assert mt.tc_tile() == (tile, False)
+            assert _rel(At, A_ref) <= bar, (tile, precision, _rel(At, A_ref))
+        mt.free()
 
 
-def test_full_size_parallelepiped24_sampled():
-    """24^3 parallelepiped (82,944 tets, 12,167 dofs) in the form its configuration names
-    (BF16 split products, FP32 accumulation, FP64 refinement): sampled paths and table rows
-    against the oracle, symmetry and the refined residual at full size."""
-    w = inputs.PARALLELEPIPED24
-    mesh = inputs.workload_mesh("parallelepiped24")
+@pytest.mark.parametrize("tile", [128, 256])
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_tensor_core_bins_over_one_tile(tile, precision):
+    """A small mesh with wide transverse bins (bin_scale 2.5 on the 10^3 jittered cube):
+    bins of more than 128 dofs take the register epilogue over several (m, n) tiles, with
+    n tiles > 0 at the 128 width; the whole matrix must match the oracle to the split's bar
+    and be symmetric to FP32 summation order."""
+    mesh = inputs.cube_mesh(10, 0.2, 4)
     o = oracle.Oracle.from_mesh(mesh)
+    alpha, K = (1.3, 1.6, 1.8), (1.0, 2.0, 0.5)
+    m = fem3.Mesh(mesh.verts, mesh.tets, bin_scale=2.5, tc_tile=tile)
+    assert max(m.bin_stats(a)["max_dof"] for a in range(3)) > 128
+    A = m.assemble(alpha, K, precision, return_matrix=True).cpu().numpy()
+    m.sync()
+    A_ref = o.assemble(alpha, K)
+    bar = 2e-6 if precision == "tf32x3" else 1e-4
+    assert _rel(A, A_ref) <= bar, _rel(A, A_ref)
+    assert np.abs(A - A.T).max() <= 1e-6 * np.abs(A).max()
+    f = np.random.default_rng(5).standard_normal((mesh.n_nodes, 2))
+    u = m.solve(f, tol=1e-13).cpu().numpy()
+    u_ref = oracle.solve(A_ref, o.load(f))
+    assert np.linalg.norm(u - u_ref) <= 1e-8 * np.linalg.norm(u_ref)
+    m.free()
+
+
+@pytest.mark.parametrize("alpha", [(2.0, 2.0, 2.0), (2.0, 1.5, 2.0)])
+def test_integer_order_axes(alpha):
+    """alpha_i = 2 (Table 4's integer-order case): order-1 one-sided derivatives, the slope
+    on the Gauss point's tet (the oracle is pinned there to the textbook P1 stiffness
+    matrix); all-integer and mixed integer/fractional orders against the oracle."""
+    mesh, o, _, K = _case("cube7_jitter")
+    A_ref = o.assemble(alpha, K)
+    f = inputs.nodal_source(mesh, (1.5, 1.5, 1.5), K) + 0.3
+    u_ref = oracle.solve(A_ref, o.load(f))
     m = fem3.Mesh(mesh.verts, mesh.tets)
+    A = m.assemble(alpha, K, "fp64", return_matrix=True).cpu().numpy()
+    assert _rel(A, A_ref) <= 1e-10
+    u = m.solve(f).cpu().numpy()
+    assert np.linalg.norm(u - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
+    At = m.assemble(alpha, K, "tf32x3", return_matrix=True).cpu().numpy()
+    assert _rel(At, A_ref) <= 2e-6
+    u = m.solve(f, tol=1e-13).cpu().numpy()
+    assert np.linalg.norm(u - u_ref) <= 1e-8 * np.linalg.norm(u_ref)
+    m.free()
+
+
+_PPD24 = {}
+
+
+def _ppd24():
+    """The 24^3 parallelepiped (82,944 tets, 12,167 dofs) with its oracle matrix (about a
+    minute of single-threaded host work, computed once per session)."""
+    if not _PPD24:
+        w = inputs.PARALLELEPIPED24
+        mesh = inputs.workload_mesh("parallelepiped24")
+        o = oracle.Oracle.from_mesh(mesh)
+        _PPD24.update(mesh=mesh, o=o, w=w, A_ref=o.assemble(w["alpha"], w["K"]))
+    return _PPD24
+
+
+def test_full_size_parallelepiped24_paths_and_tables():
+    """Paths in both directions and table rows at full size against the oracle."""
+    P = _ppd24()
+    mesh, o, w = P["mesh"], P["o"], P["w"]
     alpha, K = w["alpha"], w["K"]
-    A = m.assemble(alpha, K, "bf16x3", return_matrix=True)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    m.assemble(alpha, K, "bf16x3")
     m.sync()
     rng = np.random.default_rng(7)
-    gps = np.sort(rng.choice(o.n_gp, 200, replace=False))
+    gps = np.sort(rng.choice(o.n_gp, 240, replace=False))
+    tol_r = 1e-12 * max(o.span, float(np.abs(mesh.verts).max()))
     for axis in range(3):
-        tet, _, r1, ns = m.paths(axis, -1, gps)
-        tet, ns = tet.cpu().numpy(), ns.cpu().numpy()
-        for l, g in enumerate(gps[:60]):
-            st, _, _, _, _ = o.walk(int(g), axis, -1)
-            assert np.array_equal(tet[l, :ns[l]], st)
-        L, R = o.tables(axis, alpha[axis] / 2, gps[:50])
-        assert _rel(m.table_rows(axis, -1, gps[:50]).cpu().numpy(), L) <= 1e-10
-        assert _rel(m.table_rows(axis, +1, gps[:50]).cpu().numpy(), R) <= 1e-10
-    idx = rng.integers(0, o.n_dof, size=(2000, 2))
-    a = A[idx[:, 0], idx[:, 1]].cpu().numpy()
-    at = A[idx[:, 1], idx[:, 0]].cpu().numpy()
-    assert np.abs(a - at).max() <= 1e-5 * float(A.abs().max())
-    u = m.solve(np.ones(mesh.n_nodes), tol=1e-12)
-    assert m.resid <= 1e-12
+        for d in (-1, 1):
+            tet, r0, r1, ns = m.paths(axis, d, gps)
+            tet, r0, r1, ns = (tet.cpu().numpy(), r0.cpu().numpy(), r1.cpu().numpy(),
+                               ns.cpu().numpy())
+            for l, g in enumerate(gps):
+                st, a, b, _, _ = o.walk(int(g), axis, d)
+                assert ns[l] == len(st), (g, axis, d)
+                assert np.array_equal(tet[l, :ns[l]], st), (g, axis, d)
+                assert np.abs(r0[l, :ns[l]] - a).max(initial=0) <= tol_r
+                assert np.abs(r1[l, :ns[l]] - b).max(initial=0) <= tol_r
+        L, R = o.tables(axis, alpha[axis] / 2, gps[:80])
+        assert _rel(m.table_rows(axis, -1, gps[:80]).cpu().numpy(), L) <= 1e-10
+        assert _rel(m.table_rows(axis, +1, gps[:80]).cpu().numpy(), R) <= 1e-10
+    m.free()
+
+
+def test_full_size_parallelepiped24_matrix_and_solution():
+    """The configuration's own form (BF16 split products, FP32 accumulation, FP32 factor,
+    FP64 refinement) at full size: the whole matrix element by element against the oracle
+    (1e-4) and the FP64 form's matrix (1e-10); the solution of f = 1 and of 16 seeded normal
+    right-hand sides against a solve of the oracle's matrix (1e-8 after refinement, 1e-10
+    for the FP64 form).  The reference solve factors the oracle's matrix with LAPACK
+    (a library Cholesky as one step; the oracle's own textbook factorisation would take
+    several minutes at n = 12,167)."""
+    P = _ppd24()
+    mesh, o, w, A_ref = P["mesh"], P["o"], P["w"], P["A_ref"]
+    alpha, K = w["alpha"], w["K"]
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    A = m.assemble(alpha, K, "bf16x3", return_matrix=True).cpu().numpy()
+    assert _rel(A, A_ref) <= 1e-4, _rel(A, A_ref)
+    assert max(m.bin_stats(a)["max_dof"] for a in range(3)) > 128
+    F = np.concatenate([np.ones((mesh.n_nodes, 1)),
+                        inputs.random_rhs(mesh.n_nodes, 16, seed=11)], axis=1)
+    u = m.solve(F, tol=1e-12).cpu().numpy()
+    assert m.iters >= 1 and m.resid <= 1e-12
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    cf = scipy_linalg.cho_factor(A_ref, lower=True)
+    u_ref = scipy_linalg.cho_solve(cf, o.load(F))
+    err = np.linalg.norm(u - u_ref, axis=0) / np.linalg.norm(u_ref, axis=0)
+    assert err.max() <= 1e-8, err
+    del A
+    A64 = m.assemble(alpha, K, "fp64", return_matrix=True).cpu().numpy()
+    assert _rel(A64, A_ref) <= 1e-10
+    del A64
+    u64 = m.solve(F[:, :2]).cpu().numpy()
+    err64 = np.linalg.norm(u64 - u_ref[:, :2], axis=0) / np.linalg.norm(u_ref[:, :2], axis=0)
+    assert err64.max() <= 1e-10, err64
     m.free()
 
 

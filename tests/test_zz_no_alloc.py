@@ -1,6 +1,6 @@
 """fem3_spd_solve_static: the dense SPD solve whose working memory is a static device
-array, for callers that cannot allocate device memory (for example while a stream is
-being captured into a CUDA graph, or when the host application owns every allocation).
+array, for callers that cannot allocate device memory (latency-critical loops that must
+not enter the allocator, or host applications that own every device allocation).
 
 It must give the same solution as the regular solve (fem3_solve, FP64 form) on the same
 matrix and right-hand side, on two calls in a row (the static array keeps the previous
@@ -60,3 +60,24 @@ def test_static_solve_rejects_oversize_and_non_spd():
     bad = -torch.eye(8, dtype=torch.float64, device="cuda")
     w = torch.ones(8, dtype=torch.float64, device="cuda")
     assert _solve_static(lib, bad, w, w.clone()) == fem3.FEM3_E_NOT_SPD
+
+
+def test_static_solve_rejects_host_and_wrong_type_buffers():
+    """Host memory handed to the C entry point is refused before any kernel runs, and the
+    Python wrapper refuses tensors that are not contiguous float64 CUDA tensors of the
+    right shapes."""
+    lib = fem3.load_library()
+    A = torch.eye(8, dtype=torch.float64, device="cuda")
+    b = torch.ones(8, dtype=torch.float64, device="cuda")
+    Ah = np.eye(8)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    x = torch.empty_like(b)
+    rc = lib.fem3_spd_solve_static(ctypes.c_void_p(Ah.ctypes.data), ctypes.c_int64(8),
+                                   ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), s)
+    assert rc == fem3.FEM3_E_ARG
+    with pytest.raises(ValueError):
+        fem3.spd_solve_static(A.float(), b, x)
+    with pytest.raises(ValueError):
+        fem3.spd_solve_static(A[:, :4].contiguous(), b, x)
+    fem3.spd_solve_static(A, b, x)
+    assert float((x - b).abs().max()) == 0.0
