@@ -1,22 +1,29 @@
 """Benchmark of the fractional FEM hot path on one GB300 (or N independent replicas).
 
-One step = the whole hot path on the 16^3 jittered cube (24,576 tets, 98,304 Gauss
-points, 3,375 dofs, alpha = (1.3, 1.6, 1.8), K = (1, 2, 0.5)): mesh records and
-transverse bins/template (mesh_upload), FP64 path walk + closed-form derivative
-tables + contraction (assemble), load vector + factorisation + refined solve (solve).
-Inputs (vertices, tets, nodal f) are resident in HBM when the timed region starts.
+Headline workload: the convex parallelepiped - the unit cube cut into 24^3 cells x 6 tets
+(82,944 tets, 331,776 Gauss points, 12,167 dofs), interior vertices jittered by +-0.15 h,
+mapped by [[1, .3, 0], [0, 1, .2], [0, 0, .7]] - with alpha = (1.2, 1.5, 1.9), K = (1, 1, 1),
+BF16 split-product contraction with FP32 accumulation, FP32 Cholesky and FP64 iterative
+refinement, right-hand sides f = 1 and 16 seeded N(0, 1) columns.  One step = the whole
+hot path: mesh records and transverse bins / template (mesh_upload), FP64 path walk +
+closed-form derivative tables + contraction (assemble), load vector + factorisation +
+refined solve of all 17 columns (solve).  Inputs (vertices, tets, nodal f) are resident
+in HBM when the timed region starts; every step uploads, assembles, solves and frees.
 
 metric: Gauss-point paths per second - one path = one Gauss point and one axis, both
 directions walked and tabulated - through the whole step.
 
+Sub-records: the 16^3 jittered cube (TF32 split products), the same step in the plain
+FP64 form, and a batch of 64 uneven cube meshes with 16 right-hand sides each.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       [--precision tf32x3|bf16x3|fp32|fp64]
+       [--workload parallelepiped24|cube16_jitter] [--precision bf16x3|tf32x3|fp32|fp64]
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -28,10 +35,22 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "cube16_jitter"
+HEADLINE = "parallelepiped24"
+DEFAULT_PRECISION = {"parallelepiped24": "bf16x3", "cube16_jitter": "tf32x3"}
 METRIC = "gauss_point_paths_per_s"
 UNIT = "paths/s"
 L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
+
+# Peaks derived from unit counts and clocks (152 SMs, 2,070 MHz maximum SM clock): FP32 lanes
+# 128 per SM (one FMA = 2 flops), FP64 rate 1/64 of FP32.  The measured HBM and BF16 peaks
+# come from MEASURED_PEAKS.json; TF32 tensor = measured BF16 x the nominal 1.1 : 2.25 ratio.
+SMS, SM_GHZ = 152, 2.070
+FP32_FMA_TFLOPS = SMS * 128 * 2 * SM_GHZ / 1e3          # 80.5
+FP32_ISSUE_TOPS = SMS * 128 * SM_GHZ / 1e3              # 40.3 T FP32 instructions/s
+FP64_TFLOPS = FP32_FMA_TFLOPS / 64                      # 1.26
+WALK_BYTES_PER_SEGMENT = 160      # one tet record read per walked segment
+WALK_FP64_FLOPS_PER_SEGMENT = 25
+DF_OPS_PER_PRODUCT = 13           # FP32 instructions of one double-float multiply-add
 
 
 def _peaks():
@@ -42,23 +61,27 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# DRAM bytes (read + write) of one k_walk_tables launch from the ncu capture summarised in
-# profiles/k_walk_tables_cube16_jitter.md, valid only for the kernel source it was taken
-# on (sha256 of csrc/walk.cu); otherwise the traffic is reported as unknown.
-WALK_TRAFFIC = {"walk_cu_sha256": "157a6103d050d38cdfc5119e78cb51ebdee01506e66cf0cd0c6a096271408cb3",
-                "bytes_per_launch": 164286976 + 584489216, "segments_per_launch": 16099980}
+# DRAM bytes (read + write) per launch from ncu captures of the kernels (summarised under
+# profiles/), valid only for the source file they were taken on (sha256) and for the units
+# of work of that capture; the bench scales them to its own launch by the units processed
+# and reports null when the source has changed since the capture.
+TRAFFIC = {}
 
 
-def _walk_traffic(segs_per_launch):
-    import hashlib
-    src = os.path.join(ROOT, "paper_1811_03339_gb300", "csrc", "walk.cu")
+def _source_sha(name):
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        with open(os.path.join(ROOT, "paper_1811_03339_gb300", "csrc", name), "rb") as fh:
+            return hashlib.sha256(fh.read()).hexdigest()
     except OSError:
         return None
-    if WALK_TRAFFIC["walk_cu_sha256"] != sha or not WALK_TRAFFIC["bytes_per_launch"]:
+
+
+def measured_traffic(kernel, units):
+    """ncu DRAM bytes of one launch of `kernel` scaled to `units` units of work, or None."""
+    rec = TRAFFIC.get(kernel)
+    if not rec or not units or _source_sha(rec["source"]) != rec["sha256"]:
         return None
-    return WALK_TRAFFIC["bytes_per_launch"]
+    return rec["bytes"] * units / rec["units"]
 
 
 def _dist_env():
@@ -80,44 +103,105 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def contraction_rates(bin_dense_flops: float, stage_ms: float, precision: str, peaks: dict) -> dict:
-    """Tensor-core rate of the contraction stage: the split forms run three products
-    (hi hi, hi lo, lo hi) of the bins' dense flops 2 D_b^2 G_b on the MMA pipe; the rate is
-    taken over the whole stage (operand split, zeroing of A and the three launches), against
-    the measured sustained BF16 peak times the nominal dense TF32 : BF16 ratio 1.1 : 2.25 for
-    TF32.  Padding of the tiles to 128 rows and 16 columns is not counted.  Forms that do not
-    use the tensor cores get None."""
-    ratio = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0}.get(precision)
-    if ratio is None or not stage_ms or stage_ms <= 0:
-        return {"mma_tflops": None}
-    executed = 3.0 * bin_dense_flops
-    rate = executed / (stage_ms * 1e-3) / 1e12
-    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))) * ratio
-    return {"executed_mma_tflop": executed / 1e12, "mma_tflops": rate,
-            "mma_peak_tflops": peak, "mma_frac": rate / peak,
-            "mma_note": "three split products over the contraction stage time; peak = measured "
-                        "sustained bf16 x " + ("1.1/2.25 (tf32)" if precision == "tf32x3" else "1")}
-
-
-def walk_bandwidth(table_bytes: float, traffic_bytes, walk_ms: float, peaks: dict) -> dict:
-    """Bandwidth side of the walk + tables launch: the tables it writes (hi + lo pairs of
-    every bin block, zeroed and accumulated by the walking threads) and its measured DRAM
-    traffic per launch, each over the launch time, and the traffic's fraction of the
-    measured copy bandwidth."""
-    if not walk_ms or walk_ms <= 0:
-        return {"table_gbs": None}
-    out = {"table_bytes": table_bytes, "table_gbs": table_bytes / (walk_ms * 1e-3) / 1e9,
-           "hbm_peak_gbs": float(peaks["hbm_gbs"])}
-    if traffic_bytes:
-        out["traffic_gbs"] = traffic_bytes / (walk_ms * 1e-3) / 1e9
-        out["traffic_frac"] = out["traffic_gbs"] / out["hbm_peak_gbs"]
-    return out
-
-
 def whole_job_rate(world: int, units_per_rank_step: float, steps: int, total_ms: float) -> float:
     """Units all ranks processed per second over the slowest rank's time (weak scaling: every
     rank processes the same units each step)."""
     return world * units_per_rank_step * steps / (total_ms / 1e3)
+
+
+def kernel_rooflines(kms: dict, cnt: dict, n_dof: int, precision: str, peaks: dict,
+                     workload: str) -> dict:
+    """Roofline of every timed kernel class of one profiled step: achieved = algorithmic
+    work of the class's launches / their summed CUDA-event time on the launch stream.
+
+    walk_tables  HBM: 160 B (one tet record) per walked segment; FP64 side: 25 flops per
+                 segment against the FP64 rate
+    split        HBM: per table element 16 B read (L and R pairs), 8 B written (W R pair)
+                 and the four operand halves (2 B each for BF16, 4 B for TF32)
+    contract     tensor: algorithmic flops sum_g 4 nnz(L[g]) nnz(R[g]) per axis (when
+                 counted) and the executed split-product MMA flops (3 x 2 D_b^2 G_b)
+    factor       FP32 pipe: n^3 / 3 flops
+    chain        HBM: one read of the factor's lower triangle (2 n^2 B for FP32) per launch
+    apply        FP32 issue: 4 double-float multiply-adds (13 FP32 instructions each) per
+                 table element and vector
+    """
+    out = {}
+    hbm = float(peaks["hbm_gbs"])
+    elems = cnt["table_bytes"] / 16.0          # table elements (hi + lo pairs) over the axes
+    w = kms.get("walk_tables", (0, 0))
+    if w[0] > 0:
+        segs = cnt["segments"]
+        gbs = WALK_BYTES_PER_SEGMENT * segs / (w[0] * 1e-3) / 1e9   # = per launch / launch time
+        fl = WALK_FP64_FLOPS_PER_SEGMENT * segs / (w[0] * 1e-3) / 1e12
+        out["walk_tables"] = {
+            "kernel": "k_walk_tables", "bound": "hbm", "unit": "GB/s", "achieved": gbs,
+            "peak": hbm, "frac": gbs / hbm, "launches": w[1], "launch_ms": w[0] / w[1],
+            "traffic": measured_traffic("k_walk_tables", segs / w[1]),
+            "algorithmic": f"{WALK_BYTES_PER_SEGMENT} B per walked segment x {segs} segments",
+            "fp64_tflops": fl, "fp64_peak_tflops": FP64_TFLOPS, "fp64_frac": fl / FP64_TFLOPS}
+    s = kms.get("split", (0, 0))
+    if s[0] > 0:
+        per = 16 + 8 + (8 if precision == "bf16x3" else 16 if precision == "tf32x3" else 0)
+        gbs = per * elems / (s[0] * 1e-3) / 1e9
+        out["split"] = {"kernel": "k_split_ops", "bound": "hbm", "unit": "GB/s", "achieved": gbs,
+                        "peak": hbm, "frac": gbs / hbm, "launches": s[1],
+                        "launch_ms": s[0] / s[1], "traffic": None,
+                        "algorithmic": f"{per} B per table element x {elems:.0f} elements"}
+    c = kms.get("contract", (0, 0))
+    if c[0] > 0:
+        ratio = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0}.get(precision)
+        executed = 3.0 * cnt["contract_flops"]
+        if ratio is not None:
+            peak = float(peaks.get("bf16_tflops", 1900.0)) * ratio
+            ach = executed / (c[0] * 1e-3) / 1e12
+            rec = {"kernel": "k_contract_tc", "bound": "tensor", "unit": "TFLOP/s",
+                   "achieved": ach, "peak": peak, "frac": ach / peak,
+                   "basis": "executed split-product MMA flops (3 x 2 D_b^2 G_b over the bins)"}
+        else:
+            peak = FP64_TFLOPS if precision == "fp64" else FP32_FMA_TFLOPS
+            ach = cnt["contract_flops"] / (c[0] * 1e-3) / 1e12
+            rec = {"kernel": "k_contract_simt", "bound": "alu", "unit": "TFLOP/s",
+                   "achieved": ach, "peak": peak, "frac": ach / peak,
+                   "basis": "dense bin flops 2 D_b^2 G_b"}
+        alg = cnt.get("algorithmic_flops")
+        if alg:
+            rec["algorithmic_tflops"] = alg / (c[0] * 1e-3) / 1e12
+            rec["executed_over_algorithmic"] = (executed if ratio is not None
+                                                else cnt["contract_flops"]) / alg
+        rec.update(launches=c[1], launch_ms=c[0] / c[1], traffic=None)
+        out["contract"] = rec
+    f = kms.get("factor", (0, 0))
+    if f[0] > 0:
+        fl = n_dof ** 3 / 3.0
+        peak = FP64_TFLOPS if precision == "fp64" else FP32_FMA_TFLOPS
+        ach = fl / (f[0] * 1e-3) / 1e12
+        out["factor"] = {"kernel": "k_chol_tiles", "bound": "alu", "unit": "TFLOP/s",
+                         "achieved": ach, "peak": peak, "frac": ach / peak, "launches": f[1],
+                         "launch_ms": f[0] / f[1], "traffic": None,
+                         "algorithmic": f"n^3/3 flops, n = {n_dof}",
+                         "peak_basis": "CUDA-core FMA rate from unit counts and clocks"}
+    ch = kms.get("chain", (0, 0))
+    if ch[0] > 0:
+        esz = 8 if precision == "fp64" else 4
+        byt = esz * n_dof * n_dof / 2.0
+        gbs = byt / (ch[0] / ch[1] * 1e-3) / 1e9
+        out["chain"] = {"kernel": "k_solve_chain", "bound": "hbm", "unit": "GB/s",
+                        "achieved": gbs, "peak": hbm, "frac": gbs / hbm, "launches": ch[1],
+                        "launch_ms": ch[0] / ch[1], "traffic": None,
+                        "algorithmic": "the factor's lower triangle once per launch"}
+    a = kms.get("apply", (0, 0))
+    if a[0] > 0 and cnt.get("apply_vectors"):
+        ops = 4 * DF_OPS_PER_PRODUCT * elems * cnt["apply_vectors"]
+        ach = ops / (a[0] * 1e-3) / 1e12
+        out["apply"] = {"kernel": "k_apply_bin", "bound": "alu", "unit": "T FP32 instr/s",
+                        "achieved": ach, "peak": FP32_ISSUE_TOPS, "frac": ach / FP32_ISSUE_TOPS,
+                        "launches": a[1], "launch_ms": a[0] / a[1], "traffic": None,
+                        "algorithmic": f"4 double-float multiply-adds ({DF_OPS_PER_PRODUCT} FP32 "
+                                       f"instructions each) per table element and vector, "
+                                       f"{elems:.0f} elements, {cnt['apply_vectors']} "
+                                       f"vector-applies",
+                        "bytes_gbs": 16 * elems * cnt["apply_passes"] / (a[0] * 1e-3) / 1e9}
+    return out
 
 
 class ClockSampler:
@@ -177,22 +261,55 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------------
-def oracle_step(mesh, w, f):
+def oracle_sample(workload, mesh, F, gp_stride, n_chol):
+    """The oracle, as it stands, on a bounded sample of one step of `workload`: the whole
+    mesh build, the element sum (walk, tables, sparse outer products) of every gp_stride-th
+    Gauss point, the load vector, and a Cholesky factorisation + solve of the right-hand
+    sides at size n_chol (an SPD stand-in: the textbook factorisation's arithmetic does not
+    depend on the values).  The step time is extrapolated: lines x n_gp / sampled, factor x
+    (n / n_chol)^3, solve x (n / n_chol)^2.  Single-threaded C."""
     import oracle
-    o = oracle.Oracle.from_mesh(mesh)
-    A = o.assemble(w["alpha"], w["K"])
-    u = oracle.solve(A, o.load(f))
-    return 3 * o.n_gp, u
-
-
-def cpu_baseline(mesh, w, f):
+    from paper_1811_03339_gb300 import inputs
+    w = inputs.WORKLOADS[workload]
     t0 = time.perf_counter()
-    n_paths, _ = oracle_step(mesh, w, f)
-    dt = time.perf_counter() - t0
-    return {"value": n_paths / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full step of {WORKLOAD} (mesh records, {n_paths} paths walked and "
-                      f"tabulated, sparse-row contraction, Cholesky solve) in {dt:.1f} s, "
-                      f"single-threaded C"}
+    o = oracle.Oracle.from_mesh(mesh)
+    t_mesh = time.perf_counter() - t0
+    gps = np.arange(0, o.n_gp, gp_stride, dtype=np.int64)
+    t0 = time.perf_counter()
+    o.assemble_gps(w["alpha"], w["K"], gps)
+    t_lines = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.load(F)
+    t_load = time.perf_counter() - t0
+    nrhs = 1 if F.ndim == 1 else F.shape[1]
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((n_chol, n_chol))
+    M = B @ B.T / n_chol + np.eye(n_chol)
+    t0 = time.perf_counter()
+    Lc = oracle.cholesky(M)
+    t_fac = time.perf_counter() - t0
+    rhs = rng.standard_normal((n_chol, nrhs))
+    t0 = time.perf_counter()
+    oracle.chol_solve(Lc, rhs)
+    t_sol = time.perf_counter() - t0
+    n = o.n_dof
+    est = (t_mesh + t_lines * o.n_gp / len(gps) + t_load + t_fac * (n / n_chol) ** 3
+           + t_sol * (n / n_chol) ** 2)
+    return {"paths": 3 * o.n_gp, "est_step_s": est,
+            "measured_s": t_mesh + t_lines + t_load + t_fac + t_sol,
+            "sample": (f"oracle (single-threaded C) on a bounded sample of one {workload} "
+                       f"step: mesh build (all {o.n_tets} tets), the element sum of every "
+                       f"{gp_stride}-th Gauss point ({len(gps)} of {o.n_gp}, three axes), the "
+                       f"load vector of {nrhs} columns, Cholesky + solve at n = {n_chol}; "
+                       f"extrapolated to the whole step (lines x {o.n_gp / len(gps):.0f}, "
+                       f"factor x (n/{n_chol})^3, solve x (n/{n_chol})^2, n = {n})")}
+
+
+def cpu_baseline(workload, mesh, F):
+    r = oracle_sample(workload, mesh, F, gp_stride=4, n_chol=2048)
+    return {"value": r["paths"] / r["est_step_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": r["sample"] + f"; {r['measured_s']:.1f} s of CPU work, estimated step "
+                                    f"{r['est_step_s']:.1f} s"}
 
 
 def run_reference(args):
@@ -200,34 +317,36 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_1811_03339_gb300 import inputs
-    w = inputs.WORKLOADS[WORKLOAD]
-    mesh = inputs.workload_mesh(WORKLOAD)
-    f = inputs.nodal_source(mesh, w["alpha"], w["K"])
-    times = []
+    workload = args.workload
+    mesh = inputs.workload_mesh(workload)
+    F = inputs.workload_rhs(workload, mesh)
+    est, measured = [], 0.0
     budget = 150.0
     t_start = time.perf_counter()
-    steps_run = 0
+    sample = ""
     for it in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        n_paths, _ = oracle_step(mesh, w, f)
-        dt = time.perf_counter() - t0
+        r = oracle_sample(workload, mesh, F, gp_stride=32, n_chol=1024)
+        sample = r["sample"]
         if it >= args.warmup:
-            times.append(dt)
-            steps_run += 1
-        if time.perf_counter() - t_start > budget and steps_run >= 1:
+            est.append(r["est_step_s"])
+            measured += r["measured_s"]
+        if time.perf_counter() - t_start > budget and est:
             break
-    value = n_paths * len(times) / sum(times)
+    paths = 3 * 4 * mesh.n_tets
+    value = paths * len(est) / sum(est)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-        "n_gpus": world, "steps": len(times), "steps_requested": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "n_gpus": world, "steps": len(est), "steps_requested": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(est) / len(est),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "tets": int(mesh.n_tets), "gauss_points": 4 * int(mesh.n_tets),
-                   "alpha": list(w["alpha"]), "K": list(w["K"])},
+        "config": {"workload": workload, "tets": int(mesh.n_tets),
+                   "gauss_points": 4 * int(mesh.n_tets), "paths_per_step": paths,
+                   "alpha": list(inputs.WORKLOADS[workload]["alpha"]),
+                   "K": list(inputs.WORKLOADS[workload]["K"])},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "full steps of the workload (oracle, single-threaded C); "
-                                   "stopped early after 150 s of work"},
+                         "sample": sample + f"; each step one such sample ({measured / len(est):.1f} s "
+                                            f"of CPU work), stopped early after {budget:.0f} s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -237,6 +356,139 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------
+def _stage_dict(st):
+    return dict(zip(["mesh", "bins", "walk_tables", "contract", "load", "factor",
+                     "solve_refine"], [round(x, 4) for x in st]))
+
+
+def measure_workload(args, torch, fem3, inputs, workload, precision, steps, warmup, dev, clk=None,
+                     with_fp64=True, with_e2e=False, world=1):
+    """Time one workload's step (CUDA events on torch's current stream, L2 flushed between
+    steps), then profile one step (stage and kernel-class events) and, optionally, time the
+    plain FP64 form and the end-to-end path through the C ABI with host buffers."""
+    w = inputs.WORKLOADS[workload]
+    mesh = inputs.workload_mesh(workload)
+    alpha, K = w["alpha"], w["K"]
+    F = inputs.workload_rhs(workload, mesh)
+    nrhs = 1 if F.ndim == 1 else F.shape[1]
+    verts_d = torch.from_numpy(mesh.verts).to(dev)
+    tets_d = torch.from_numpy(mesh.tets).to(dev)
+    F_d = torch.from_numpy(np.ascontiguousarray(F)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    n_paths = 3 * 4 * mesh.n_tets
+    stream = torch.cuda.current_stream()
+
+    def step(prec, profile=False, keep=False):
+        m = fem3.Mesh(verts_d, tets_d, bin_scale=args.bin_scale, profile=profile)
+        m.assemble(alpha, K, prec)
+        u = m.solve(F_d, tol=args.tol)
+        if keep:
+            return m, u
+        m.free()
+        return None, u
+
+    def timed(prec, k, warm):
+        for _ in range(warm):
+            step(prec)
+        times = []
+        for _ in range(k):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if clk is not None:
+        with clk:
+            times = timed(precision, steps, warmup)
+    else:
+        times = timed(precision, steps, warmup)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total = max_over_ranks(sum(times), world, dev)
+    out = {"workload": workload, "tets": int(mesh.n_tets), "gauss_points": 4 * int(mesh.n_tets),
+           "paths_per_step": n_paths, "rhs_columns": nrhs, "alpha": list(alpha), "K": list(K),
+           "precision": precision, "steps": steps, "ms_per_step": total / steps,
+           "value": whole_job_rate(world, n_paths, steps, total)}
+
+    # profiled step: stage and kernel-class events, counters
+    m, u_mix = step(precision, profile=True, keep=True)
+    m.sync()
+    kms = m.kernel_ms()
+    cnt = m.counters()
+    cnt["algorithmic_flops"] = m.contract_work()
+    out.update(dofs=int(m.n_dof), stages_ms=_stage_dict(m.stage_ms()),
+               kernel_ms={k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in kms.items()},
+               segments_per_step=cnt["segments"], table_bytes=cnt["table_bytes"],
+               gpu_launches_per_step=cnt["launches"],
+               refinement={"iterations": m.iters, "final_rel_residual": m.resid,
+                           "tol": args.tol},
+               bins=[m.bin_stats(a) for a in range(3)], tc_tile=m.tc_tile()[0] or None)
+    if precision != "fp64":
+        passes = 0
+        vecs = 0
+        for _ in range(m.iters):
+            vecs += nrhs
+            passes += (nrhs + 7) // 8
+        cnt["apply_vectors"], cnt["apply_passes"] = vecs, passes
+    n_dof = m.n_dof
+    m.free()
+    out["rooflines"] = kernel_rooflines(kms, cnt, n_dof, precision, _peaks()[0], workload)
+    if out["rooflines"]:
+        dom = max(out["rooflines"], key=lambda k: kms[k][0])
+        out["dominant_kernel"] = dom
+        out["dominant_share_of_kernel_time"] = kms[dom][0] / sum(v[0] for v in kms.values())
+
+    if with_fp64 and precision != "fp64":
+        t64 = timed("fp64", 2, 1)
+        m64, u64 = step("fp64", profile=True, keep=True)
+        m64.sync()
+        out["fp64_form"] = {"ms_per_step": sum(t64) / len(t64),
+                            "stages_ms": _stage_dict(m64.stage_ms())}
+        m64.free()
+        out["mixed_vs_fp64_speedup"] = out["fp64_form"]["ms_per_step"] / out["ms_per_step"]
+        du = (u_mix - u64).reshape(-1, nrhs) if nrhs > 1 else (u_mix - u64)
+        rel = torch.linalg.norm(du.reshape(-1, nrhs), dim=0) / torch.linalg.norm(
+            u64.reshape(-1, nrhs), dim=0)
+        out["u_rel_diff_mixed_vs_fp64_max"] = float(rel.max())
+
+    if with_e2e:
+        verts_h = torch.from_numpy(mesh.verts).pin_memory()
+        tets_h = torch.from_numpy(mesh.tets).pin_memory()
+        F_h = torch.from_numpy(np.ascontiguousarray(F)).pin_memory()
+        e2e_t = []
+        for it in range(warmup + steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mh = fem3.Mesh(verts_h.numpy(), tets_h.numpy(), bin_scale=args.bin_scale)
+            mh.assemble(alpha, K, precision)
+            u = mh.solve(F_h.numpy(), tol=args.tol)
+            u_host = u.cpu()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mh.free()
+            if it >= warmup:
+                e2e_t.append(e0.elapsed_time(e1))
+        out["e2e"] = {"value": whole_job_rate(world, n_paths, len(e2e_t),
+                                              max_over_ranks(sum(e2e_t), world, dev)),
+                      "unit": UNIT,
+                      "h2d_bytes_per_step": int(mesh.verts.nbytes + mesh.tets.nbytes + F.nbytes),
+                      "d2h_bytes_per_step": int(u_host.numel() * 8)}
+    out["_mesh"] = mesh
+    out["_F"] = F
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -248,193 +500,67 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = inputs.WORKLOADS[WORKLOAD]
-    mesh = inputs.workload_mesh(WORKLOAD)
-    alpha, K = w["alpha"], w["K"]
-    f_host = inputs.nodal_source(mesh, alpha, K)
-    verts_d = torch.from_numpy(mesh.verts).to(dev)
-    tets_d = torch.from_numpy(mesh.tets).to(dev)
-    f_d = torch.from_numpy(f_host).to(dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    n_paths = 3 * 4 * mesh.n_tets
-    stream = torch.cuda.current_stream()
+    workload = args.workload
+    precision = args.precision or DEFAULT_PRECISION[workload]
 
-    def step(precision, profile=False, keep=False):
-        m = fem3.Mesh(verts_d, tets_d, bin_scale=args.bin_scale, profile=profile)
-        m.assemble(alpha, K, precision)
-        u = m.solve(f_d, tol=args.tol)
-        if keep:
-            return m, u
-        m.free()
-        return None, u
-
-    def timed(precision, k, warm):
-        for _ in range(warm):
-            step(precision)
-        times = []
-        for _ in range(k):
-            flush.zero_()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step(precision)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-        return times
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    # --- main timed region: mixed-precision form ---------------------------------
-    barrier()
-    with ClockSampler(local) as clk:
-        times = timed(args.precision, args.steps, args.warmup)
-    barrier()
-    t_mix = max_over_ranks(sum(times), world, dev)
-    ms_step = t_mix / args.steps
-    value = whole_job_rate(world, n_paths, args.steps, t_mix)
-
-    # --- FP64 form (comparison) ----------------------------------------------------
-    k64 = max(2, min(args.steps, 5))
-    t64 = timed("fp64", k64, 1)
-    ms_fp64 = sum(t64) / k64
-
-    # --- stage breakdown and counters (profiled, untimed) ----------------------------
-    m, u_mix = step(args.precision, profile=True, keep=True)
-    stages = m.stage_ms()
-    m.sync()
-    cnt = m.counters()
-    tile_n, _ = m.tc_tile()   # tensor-core tile width chosen by the tuner (0: no TC form)
-    ir_iters, ir_resid = m.iters, m.resid
-    m.free()
-    m64, u64 = step("fp64", profile=True, keep=True)
-    stages64 = m64.stage_ms()
-    m64.free()
-    rel_mix_fp64 = float(torch.linalg.norm(u_mix - u64) / torch.linalg.norm(u64))
-
-    # --- the other tensor-core form (BF16 x 3 split products), same step ----------------
-    other = None
-    if args.precision in ("tf32x3", "bf16x3"):
-        oprec = "bf16x3" if args.precision == "tf32x3" else "tf32x3"
-        to = timed(oprec, k64, 1)
-        mo, uo = step(oprec, profile=True, keep=True)
-        mo.sync()
-        other = {"precision": oprec, "ms_per_step": sum(to) / k64,
-                 "vs_fp64_speedup": ms_fp64 / (sum(to) / k64),
-                 "refinement_sweeps": mo.iters, "final_rel_residual": mo.resid,
-                 "u_rel_diff_vs_fp64": float(torch.linalg.norm(uo - u64) / torch.linalg.norm(u64)),
-                 "stages_ms": dict(zip(["mesh", "bins", "walk_tables", "contract", "load",
-                                        "factor", "solve_refine"], mo.stage_ms()))}
-        mo.free()
-
-    # walk+tables kernel: one launch per step covering the three axes, timed live by the
-    # library's events on the launch stream.  Algorithmic FP64 flops per walked segment
-    # (the quantities that decide the path; the table part runs in double-float FP32):
-    # 24 (b~ = lambda_T(x_g), 12 FMA) + 2 (go-out ratios of ~2 exit candidates)
-    # + 8 (exit zero pattern, 4 FMA) + 1 (length test) = 35.
-    walk_ms = stages[2]
-    segs_per_launch = cnt["segments"]
-    fp64_flops_per_seg = 35.0
-    walk_flops = fp64_flops_per_seg * segs_per_launch
-    fp64_peak_gflops = 1250.0
-    traffic = _walk_traffic(segs_per_launch)
-    roofline = {
-        "kernel": "k_walk_tables",
-        "bound": "alu", "unit": "GFLOP/s (FP64)",
-        "achieved": walk_flops / (walk_ms * 1e-3) / 1e9,
-        "peak": fp64_peak_gflops,
-        "peak_source": "GB300 FP64 rate derived from unit counts and clocks: 152 SMs x 2 "
-                       "DFMA/clk x 2 flops x 2.07 GHz = 1.26 TFLOP/s (nominal 1.25; a DFMA "
-                       "loop measured 1,249.6 GFLOP/s on this pool)",
-        "frac": walk_flops / (walk_ms * 1e-3) / 1e9 / fp64_peak_gflops,
-        "traffic": traffic,
-        "launch_ms": walk_ms,
-        "algorithmic_unit": f"{fp64_flops_per_seg:.0f} FP64 flops per walked segment, "
-                            f"{segs_per_launch:.0f} segments per launch (three axes)",
-    }
-
-    # --- end to end through the C ABI with host buffers -----------------------------
-    verts_h = torch.from_numpy(mesh.verts).pin_memory()
-    tets_h = torch.from_numpy(mesh.tets).pin_memory()
-    f_h = torch.from_numpy(f_host).pin_memory()
-    e2e_t = []
-    n_dof = None
-    for it in range(args.warmup + args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        mh = fem3.Mesh(verts_h.numpy(), tets_h.numpy(), bin_scale=args.bin_scale)
-        mh.assemble(alpha, K, args.precision)
-        u = mh.solve(f_h.numpy(), tol=args.tol)
-        u_host = u.cpu()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        n_dof = mh.n_dof
-        mh.free()
-        if it >= args.warmup:
-            e2e_t.append(e0.elapsed_time(e1))
-    e2e_value = whole_job_rate(world, n_paths, len(e2e_t), max_over_ranks(sum(e2e_t), world, dev))
-    h2d = mesh.verts.nbytes + mesh.tets.nbytes + f_host.nbytes
-    d2h = 8 * n_dof
-
-    # --- kernel launches per step: counted by the library at every launch ------------
-    launches = cnt["launches"] * args.steps
-    launch_note = f"{cnt['launches']} libfem3 kernel launches per step (library counter)"
-
-    # --- batched workload: 64 uneven cube meshes, 16 right-hand sides each -----------
+    clk = ClockSampler(local)
+    head = measure_workload(args, torch, fem3, inputs, workload, precision, args.steps,
+                            args.warmup, dev, clk=clk, with_fp64=True, with_e2e=True,
+                            world=world)
+    sub = None
+    if not args.no_sub:
+        other = "cube16_jitter" if workload != "cube16_jitter" else HEADLINE
+        sub = measure_workload(args, torch, fem3, inputs, other, DEFAULT_PRECISION[other],
+                               max(5, min(args.steps, 20)), 3, dev, with_fp64=True,
+                               world=world)
+        for k in ("_mesh", "_F"):
+            sub.pop(k)
     batch = None
     if not args.no_batch:
-        batch = run_batch(args, torch, fem3, inputs, stream)
+        batch = run_batch(args, torch, fem3, inputs, torch.cuda.current_stream())
 
     line = None
     if rank == 0:
         peaks, src = _peaks()
-        base = cpu_baseline(mesh, w, f_host) if (world == 1 and not args.no_cpu_baseline) else None
-        ctr_flops = cnt["contract_flops"]
+        mesh, F = head.pop("_mesh"), head.pop("_F")
+        base = (cpu_baseline(workload, mesh, F)
+                if (world == 1 and not args.no_cpu_baseline) else None)
+        dom = head.get("dominant_kernel")
+        roof = dict(head["rooflines"][dom]) if dom else None
+        if roof is not None:
+            roof["share_of_kernel_time"] = head["dominant_share_of_kernel_time"]
+            roof["peak_source"] = ("measured (MEASURED_PEAKS.json)" if roof["unit"] in ("GB/s",)
+                                   or roof["bound"] == "tensor" else
+                                   "derived from unit counts and the 2,070 MHz clock")
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"tf32x3": "f64 walk/tables, tf32x3 contraction, f32 factor, f64 refinement",
                       "bf16x3": "f64 walk/tables, bf16x3 contraction, f32 factor, f64 refinement",
                       "fp32": "f64 walk/tables, f32 contraction and factor, f64 refinement",
-                      "fp64": "f64"}[args.precision],
+                      "fp64": "f64"}[precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "tets": int(mesh.n_tets),
-                       "gauss_points": 4 * int(mesh.n_tets), "dofs": int(n_dof),
-                       "paths_per_step": n_paths, "alpha": list(alpha), "K": list(K),
-                       "precision": args.precision, "parallelism": f"replicas{world}",
-                       "bin_scale": args.bin_scale,
+            "config": {"workload": workload, "tets": head["tets"],
+                       "gauss_points": head["gauss_points"], "dofs": head["dofs"],
+                       "paths_per_step": head["paths_per_step"],
+                       "rhs_columns": head["rhs_columns"], "alpha": head["alpha"],
+                       "K": head["K"], "precision": precision,
+                       "parallelism": f"replicas{world}", "bin_scale": args.bin_scale,
                        "l2": "flushed (256 MB write) between timed steps"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": launches,
-            "gpu_launches_note": launch_note,
-            "roofline": roofline,
+            "e2e": head["e2e"],
+            "gpu_launches": head["gpu_launches_per_step"] * args.steps,
+            "gpu_launches_note": f"{head['gpu_launches_per_step']} libfem3 kernel launches per "
+                                 f"step (library counter)",
+            "roofline": roof,
             "cpu_baseline": base,
             "clocks": clk.summary(),
-            "fp64_form_ms_per_step": ms_fp64,
-            "mixed_vs_fp64_speedup": ms_fp64 / ms_step,
-            "u_rel_diff_mixed_vs_fp64": rel_mix_fp64,
-            "other_tensor_core_form": other,
-            "stages_ms": dict(zip(["mesh", "bins", "walk_tables", "contract", "load", "factor",
-                                   "solve_refine"], [round(x, 4) for x in stages])),
-            "stages_ms_fp64": dict(zip(["mesh", "bins", "walk_tables", "contract", "load",
-                                        "factor", "solve_refine"],
-                                       [round(x, 4) for x in stages64])),
-            "segments_per_step": cnt["segments"],
-            "refinement": {"iterations": ir_iters, "final_rel_residual": ir_resid, "tol": args.tol},
-            "table_bytes": cnt["table_bytes"],
-            "walk_bandwidth": walk_bandwidth(cnt["table_bytes"], traffic, stages[2], peaks),
-            "contraction": {"bin_dense_gflop": ctr_flops / 1e9,
-                            "gflops": ctr_flops / (stages[3] * 1e-3) / 1e9 if stages[3] > 0 else None,
-                            "tile_n": tile_n or None,
-                            **contraction_rates(ctr_flops, stages[3], args.precision, peaks)},
+            "fp64_form_ms_per_step": head.get("fp64_form", {}).get("ms_per_step"),
+            "mixed_vs_fp64_speedup": head.get("mixed_vs_fp64_speedup"),
+            "u_rel_diff_mixed_vs_fp64_max": head.get("u_rel_diff_mixed_vs_fp64_max"),
+            "detail": {k: v for k, v in head.items() if k not in ("e2e",)},
             "peaks_source": src,
+            "sub_workload": sub,
             "batch": batch,
         }
         print(json.dumps(line), flush=True)
@@ -471,7 +597,7 @@ def run_batch(args, torch, fem3, inputs, stream):
             ts.append(e0.elapsed_time(e1))
         return sum(ts) / len(ts), us
 
-    ms_mix, u_mix = timed(args.precision, 3, 1)
+    ms_mix, u_mix = timed("tf32x3", 3, 1)
     iters = list(b.iters)
     ms_64, u_64 = timed("fp64", 1, 1)
     err = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(u_mix, u_64))
@@ -481,7 +607,7 @@ def run_batch(args, torch, fem3, inputs, stream):
            "ms_per_step": ms_mix, "paths_per_s": paths / (ms_mix / 1e3),
            "fp64_ms_per_step": ms_64, "mixed_vs_fp64_speedup": ms_64 / ms_mix,
            "u_rel_err_mixed_vs_fp64_max": err, "refinement_sweeps_max": max(iters),
-           "precision": args.precision}
+           "precision": "tf32x3"}
     b.free()
     return out
 
@@ -489,13 +615,17 @@ def run_batch(args, torch, fem3, inputs, stream):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    # 100 steps of about 4 ms keep the timed region long enough for several 200 ms clock samples
-    ap.add_argument("--steps", type=int, default=100)
+    # about 30 steps of 50-80 ms keep the timed region long enough for several 200 ms
+    # clock samples
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "fp32", "fp64"])
+    ap.add_argument("--workload", default=HEADLINE, choices=["parallelepiped24", "cube16_jitter"])
+    ap.add_argument("--precision", default=None, choices=["tf32x3", "bf16x3", "fp32", "fp64"],
+                    help="default: bf16x3 for the parallelepiped, tf32x3 for the cube")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched workload")
+    ap.add_argument("--no-sub", action="store_true", help="skip the second workload")
     ap.add_argument("--tol", type=float, default=1e-10,
                     help="relative residual at which refinement stops (the mixed form targets "
                          "1e-8 relative solution error; the FP64 form is direct)")

@@ -201,6 +201,20 @@ int fem3_stage_ms(fem3_mesh m, int stage, float *ms);
 int fem3_counters(fem3_mesh m, int64_t *segments, double *contract_flops,
                   int64_t *table_bytes, int64_t *launches);
 
+/* Algorithmic flops of the last assemble's contraction (Section 2.1 element sum as sparse
+ * outer products): sum over axes and Gauss points g of 2 * 2 * nnz(L_i[g]) * nnz(R_i[g]),
+ * counted from the tables' nonzeros (one read of the tables; synchronises `stream`).
+ * flops: host float64.  Errors: FEM3_E_ARG, FEM3_E_STATE (no assemble yet). */
+int fem3_contract_work(fem3_mesh m, double *flops, void *stream);
+
+/* Kernel classes timed launch by launch when the handle profiles (opt.profile != 0):
+ * CUDA events on the launch stream around every launch of the class, summed over the
+ * launches since the last fem3_assemble and collected by the next synchronising call
+ * (fem3_solve, fem3_sync).  Classes: 0 walk + derivative tables (one launch, three axes),
+ * 1 operand split of the tables, 2 contraction GEMMs, 3 Cholesky factorisation,
+ * 4 triangular-solve chains, 5 refinement operator apply.  Any output pointer may be NULL. */
+int fem3_kernel_ms(fem3_mesh m, int kclass, float *ms, int32_t *launches);
+
 /* Transverse bins of one axis (Section 2.3 template, per axis): number of bins, template
  * rows summed over the bins, and the largest template dof set and Gauss-point count of a
  * bin.  axis in 0..2; any output pointer may be NULL. */

@@ -64,6 +64,8 @@ def _load():
         lib.or_table_row.argtypes = [p, i64, C.c_int, C.c_int, dbl, C.c_int, p]
         lib.or_assemble.restype = C.c_int
         lib.or_assemble.argtypes = [p, p, p, p]
+        lib.or_assemble_gps.restype = C.c_int
+        lib.or_assemble_gps.argtypes = [p, p, p, p, i64, p]
         lib.or_assemble_form.restype = C.c_int
         lib.or_assemble_form.argtypes = [p, C.c_int, dbl, dbl, C.c_int, p, C.c_int, p]
         lib.or_assemble_divergence.restype = C.c_int
@@ -189,6 +191,20 @@ class Oracle:
         e = self._lib.or_assemble(self._h, _ptr(a), _ptr(k), _ptr(A))
         if e:
             raise OracleError(e, "assemble")
+        return A
+
+    def assemble_gps(self, alpha, K, gps, A: np.ndarray | None = None) -> np.ndarray:
+        """Add the element-sum terms of the listed Gauss points (all axes) to A (a new zero
+        matrix when None); a partition of the Gauss points sums to ``assemble``."""
+        a = np.ascontiguousarray(alpha, dtype=np.float64)
+        k = np.ascontiguousarray(K, dtype=np.float64)
+        g = np.ascontiguousarray(gps, dtype=np.int64)
+        if A is None:
+            A = np.zeros((self.n_dof, self.n_dof))
+        assert A.flags["C_CONTIGUOUS"] and A.shape == (self.n_dof, self.n_dof)
+        e = self._lib.or_assemble_gps(self._h, _ptr(a), _ptr(k), _ptr(g), len(g), _ptr(A))
+        if e:
+            raise OracleError(e, "assemble_gps")
         return A
 
     def assemble_form(self, axis: int, alpha: float, beta: float, trial_left: bool = True,

@@ -478,6 +478,46 @@ int or_assemble(const or_mesh *m, const double alpha[3], const double K[3], doub
  * columns over every node (tables with their boundary terms); 0: interior dofs.  K:
  * row-major [n][n].  The Riesz term of or_assemble is s K (form(L, R) + form(R, L)) at
  * alpha = beta = alpha_i / 2 and c = 1. */
+/* The Section 2.1 element sum restricted to the listed Gauss points: adds, for every axis,
+ * s_i K_i w_g (L[g] R[g]^T + R[g] L[g]^T) of each listed g to A (A is not cleared).  The
+ * sum over a partition of all Gauss points is or_assemble's matrix (up to the order of
+ * the floating-point additions).  Used to time the oracle on a bounded sample of lines. */
+int or_assemble_gps(const or_mesh *m, const double alpha[3], const double K[3],
+                    const int64_t *gps, int64_t n_g, double *A)
+{
+    int64_t n = m->n_dof;
+    double *L = calloc(n > 0 ? n : 1, sizeof(double)), *R = calloc(n > 0 ? n : 1, sizeof(double));
+    int64_t *iL = malloc(sizeof(int64_t) * (n > 0 ? n : 1)), *iR = malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    int st = OR_OK;
+    if (!L || !R || !iL || !iR) { free(L); free(R); free(iL); free(iR); return OR_E_OOM; }
+    for (int axis = 0; axis < 3 && st == OR_OK; axis++) {
+        if (!(alpha[axis] > 1.0 && alpha[axis] <= 2.0)) { st = OR_E_ARG; break; }
+        double gamma = alpha[axis] / 2.0;
+        double c = K[axis] / (2.0 * cos(M_PI * alpha[axis] / 2.0));
+        for (int64_t q = 0; q < n_g && st == OR_OK; q++) {
+            int64_t g = gps[q];
+            if (g < 0 || g >= m->n_gp) { st = OR_E_ARG; break; }
+            int e1 = or_table_row(m, g, axis, -1, gamma, 0, L);
+            int e2 = or_table_row(m, g, axis, +1, gamma, 0, R);
+            if (e1 || e2) { st = e1 ? e1 : e2; break; }
+            int64_t nl = 0, nr = 0;
+            for (int64_t j = 0; j < n; j++) {
+                if (L[j] != 0.0) iL[nl++] = j;
+                if (R[j] != 0.0) iR[nr++] = j;
+            }
+            double cw = c * m->gw[g];
+            for (int64_t a = 0; a < nl; a++)
+                for (int64_t b = 0; b < nr; b++)
+                    A[iL[a] * n + iR[b]] += cw * L[iL[a]] * R[iR[b]];
+            for (int64_t a = 0; a < nr; a++)
+                for (int64_t b = 0; b < nl; b++)
+                    A[iR[a] * n + iL[b]] += cw * R[iR[a]] * L[iL[b]];
+        }
+    }
+    free(L); free(R); free(iL); free(iR);
+    return st;
+}
+
 int or_assemble_form(const or_mesh *m, int axis, double alpha, double beta, int trial_left,
                      const double *c, int all_nodes, double *K)
 {

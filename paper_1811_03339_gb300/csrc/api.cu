@@ -110,6 +110,46 @@ void stage_collect(Mesh *m) {
         else
             cudaGetLastError();
     }
+    for (size_t i = 0; i < m->kc_used; i++) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, m->kc_ev[2 * i], m->kc_ev[2 * i + 1]) == cudaSuccess) {
+            m->kc_ms[m->kc_cls[i]] += ms;
+            m->kc_n[m->kc_cls[i]]++;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    m->kc_used = 0;
+}
+
+void kc_begin(Mesh *m, int cls) {
+    if (!m->profile) return;
+    while (m->kc_ev.size() < 2 * (m->kc_used + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        m->kc_ev.push_back(e);
+    }
+    if (m->kc_cls.size() < m->kc_used + 1) m->kc_cls.resize(m->kc_used + 1);
+    m->kc_cls[m->kc_used] = cls;
+    cudaEventRecord(m->kc_ev[2 * m->kc_used], m->stream);
+}
+
+void kc_end(Mesh *m, int cls) {
+    if (!m->profile || m->kc_ev.size() < 2 * (m->kc_used + 1) || m->kc_cls[m->kc_used] != cls)
+        return;
+    cudaEventRecord(m->kc_ev[2 * m->kc_used + 1], m->stream);
+    m->kc_used++;
+}
+
+void kc_reset(Mesh *m) {
+    m->kc_used = 0;
+    for (int k = 0; k < 8; k++) {
+        m->kc_ms[k] = 0.f;
+        m->kc_n[k] = 0;
+    }
 }
 
 int read_errors(Mesh *m, int32_t *h_err) {
@@ -185,6 +225,7 @@ void fem3_mesh_free(fem3_mesh h) {
     if (m->h_norms) pinned_release(m->h_norms);
     if (m->ev_made)
         for (int k = 0; k < 16; k++) cudaEventDestroy(m->ev[k]);
+    for (cudaEvent_t e : m->kc_ev) cudaEventDestroy(e);
     delete m;
 }
 
@@ -310,6 +351,7 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
     m->precision = precision;
     m->factored = false;
     m->ap_ready = false;
+    kc_reset(m);
     FEM3_TRY(walk_tables(m, alpha));
     stage_begin(m, 3);
     if (precision == FEM3_TF32X3 || precision == FEM3_BF16X3)
@@ -472,6 +514,22 @@ int fem3_tc_tile(fem3_mesh h, int32_t *tile_n, int32_t *tuned) {
     if (!m) return set_error(FEM3_E_ARG, "null mesh");
     if (tile_n) *tile_n = m->tc_tile_used;
     if (tuned) *tuned = m->tc_tuned ? 1 : 0;
+    return FEM3_OK;
+}
+
+int fem3_contract_work(fem3_mesh h, double *flops, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !flops) return set_error(FEM3_E_ARG, "bad argument");
+    if (m->precision < 0) return set_error(FEM3_E_STATE, "contraction work before assemble");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    return contract_work(m, flops);
+}
+
+int fem3_kernel_ms(fem3_mesh h, int kclass, float *ms, int32_t *launches) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || kclass < 0 || kclass >= KC_COUNT) return set_error(FEM3_E_ARG, "bad argument");
+    if (ms) *ms = m->kc_ms[kclass];
+    if (launches) *launches = m->kc_n[kclass];
     return FEM3_OK;
 }
 

@@ -102,7 +102,52 @@ __global__ void __launch_bounds__(256) k_contract_simt(
     }
 }
 
+// Algorithmic work of the contraction (the sparse outer products the element sum needs):
+// per bin (one CTA) and Gauss point column k, the nonzeros of L[.][k] and R[.][k] over the
+// bin's template rows; adds 2 * 2 nnz(L) nnz(R) (two products, one multiply-add each) per
+// Gauss point to *flops.
+__global__ void __launch_bounds__(128) k_contract_work(
+    const float2 *__restrict__ tabL, const float2 *__restrict__ tabR,
+    const int32_t *__restrict__ gp_off, const int32_t *__restrict__ dof_off,
+    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld, double *flops) {
+    const int b = blockIdx.x;
+    const int D = dof_off[b + 1] - dof_off[b];
+    const int G = gp_off[b + 1] - gp_off[b];
+    const int ld = tab_ld[b];
+    const float2 *L = tabL + tab_off[b], *R = tabR + tab_off[b];
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < G; k += blockDim.x) {
+        int nl = 0, nr = 0;
+        for (int c = 0; c < D; c++) {
+            const float2 a = L[(int64_t)c * ld + k], r = R[(int64_t)c * ld + k];
+            nl += (a.x != 0.f || a.y != 0.f);
+            nr += (r.x != 0.f || r.y != 0.f);
+        }
+        acc += 4.0 * (double)nl * (double)nr;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(flops, acc);
+}
+
 }  // namespace
+
+int contract_work(Mesh *m, double *flops_out) {
+    cudaStream_t s = m->stream;
+    double *d = m->norms + 121;
+    FEM3_CUDA(cudaMemsetAsync(d, 0, sizeof(double), s));
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        if (B.n_bins == 0 || B.n_tmpl == 0) continue;
+        k_contract_work<<<B.n_bins, 128, 0, s>>>(m->tabL[axis], m->tabR[axis], B.gp_off,
+                                                  B.dof_off, B.tab_off, B.tab_ld, d);
+        note_launch(m);
+    }
+    FEM3_CUDA(cudaGetLastError());
+    FEM3_CUDA(cudaMemcpyAsync(m->h_norms + 121, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FEM3_CUDA(cudaStreamSynchronize(s));
+    *flops_out = m->h_norms[121];
+    return FEM3_OK;
+}
 
 int contract(Mesh *m, int precision) {
     cudaStream_t s = m->stream;
@@ -121,6 +166,7 @@ int contract(Mesh *m, int precision) {
             flops += 2.0 * D * D * G;
         }
         if (!B.n_work) continue;
+        kc_begin(m, KC_CONTRACT);
         if (precision == FEM3_FP64)
             k_contract_simt<double><<<B.n_work, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.work, B.gp_off, B.gp_idx, B.dof_off, B.dof_idx,
@@ -129,6 +175,7 @@ int contract(Mesh *m, int precision) {
             k_contract_simt<float><<<B.n_work, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.work, B.gp_off, B.gp_idx, B.dof_off, B.dof_idx,
                 B.tab_off, B.tab_ld, m->gw, m->sK[axis], m->A32, n);
+        kc_end(m, KC_CONTRACT);
         note_launch(m);
     }
     m->contract_flops = flops;

@@ -517,6 +517,7 @@ int contract_tc(Mesh *m, bool bf16) {
         const int kbk = bf16 ? 64 : 32;   // Gauss points per 128-byte swizzle row
         const int Kp = std::max(kbk, (B.tc_maxG + kbk - 1) / kbk * kbk);
         const unsigned grid = (unsigned)((B.n_tmpl + 7) / 8);
+        kc_begin(m, KC_SPLIT);
         if (bf16) {
             __nv_bfloat16 *op[4];
             for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<__nv_bfloat16 *>(B.tc_op[q]);
@@ -530,6 +531,7 @@ int contract_tc(Mesh *m, bool bf16) {
                 m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
                 B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1], op[2], op[3], B.ap_R);
         }
+        kc_end(m, KC_SPLIT);
         note_launch(m);
         for (int q = 0; q < 4; q++)
             FEM3_TRY(make_map(&maps[axis][q], B.tc_op[q], B.n_tmpl, Kp, bf16));
@@ -574,7 +576,9 @@ int contract_tc(Mesh *m, bool bf16) {
     }
     m->tc_tile_used = kTileWidths[w];
     FEM3_CUDA(cudaMemsetAsync(m->A32, 0, sizeof(float) * n * n, s));
+    kc_begin(m, KC_CONTRACT);
     FEM3_TRY(tc_gemms(m, bf16, w, maps));
+    kc_end(m, KC_CONTRACT);
     m->contract_flops = flops;
     m->ap_ready = true;
     FEM3_CUDA(cudaGetLastError());
@@ -597,9 +601,11 @@ int ap_prepare(Mesh *m) {
         AxisBins &B = m->bins[axis];
         if (B.n_tmpl == 0) continue;
         FEM3_TRY(ap_alloc(m, axis));
+        kc_begin(m, KC_SPLIT);
         k_split_ops<float><<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
             m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot, B.tab_off,
             B.tab_ld, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_R);
+        kc_end(m, KC_SPLIT);
         note_launch(m);
     }
     m->ap_ready = true;

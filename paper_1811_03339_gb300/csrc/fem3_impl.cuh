@@ -50,6 +50,7 @@ constexpr double kEpsDRel = 1e-12;    // |gradient| below this fraction of the l
 
 constexpr int kMaxBinItems = 4096;    // max dofs or Gauss points in one transverse bin
 constexpr int kSegCounterSlot = 120;  // norms[120]: segment counter (norms[0..63] reductions)
+                                      // norms[121]: contraction work counter
 
 // Transverse bins of one axis: the plane of the two other coordinates is cut into an
 // nb0 x nb1 grid; a Gauss point belongs to the bin of its transverse position, a dof
@@ -154,6 +155,12 @@ struct Mesh {
     cudaEvent_t ev[16];
     bool ev_made = false;
     float stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // per kernel class (KernelClass): event pairs around each launch, summed when collected
+    std::vector<cudaEvent_t> kc_ev;
+    std::vector<int> kc_cls;
+    size_t kc_used = 0;
+    float kc_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int32_t kc_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
     std::vector<void *> allocs;   // stream-ordered allocations, freed with the mesh
     char *arena = nullptr;        // current sub-allocation chunk (one of allocs)
@@ -177,6 +184,21 @@ bool is_device_ptr(const void *p);
 void stage_begin(Mesh *m, int stage);
 void stage_end(Mesh *m, int stage);
 void stage_collect(Mesh *m);
+
+// Kernel classes timed one launch at a time when the mesh profiles (fem3_kernel_ms):
+// CUDA events on the launch stream around every launch of the class.
+enum KernelClass {
+    KC_WALK = 0,      // k_walk_tables: walk + derivative tables, three axes in one launch
+    KC_SPLIT = 1,     // k_split_ops: operand split of the tables
+    KC_CONTRACT = 2,  // contraction GEMMs (tensor-core or CUDA-core)
+    KC_FACTOR = 3,    // Cholesky factorisation
+    KC_CHAIN = 4,     // triangular-solve chains
+    KC_APPLY = 5,     // operator apply of the refinement residual
+    KC_COUNT = 6
+};
+void kc_begin(Mesh *m, int cls);
+void kc_end(Mesh *m, int cls);
+void kc_reset(Mesh *m);
 
 // exclusive scan of int32 counts into offsets [n+1]; returns total via device offsets[n]
 int scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, Mesh *m);
@@ -207,6 +229,7 @@ int walk_paths(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, int ca
 int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double *rows);
 int contract(Mesh *m, int precision);
 int contract_tc(Mesh *m, bool bf16);   // TF32 x 3 (bf16 = false) or BF16 x 3
+int contract_work(Mesh *m, double *flops);   // algorithmic flops of the element sum (synchronises)
 int load_vector(Mesh *m, const double *f_d, int nrhs, double *b_d);
 int load_vector_T(Mesh *m, const double *lam_d, double *out_d);
 int factor(Mesh *m);

@@ -732,8 +732,10 @@ int chol_tiles_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
     FEM3_CUDA(cudaMemsetAsync(m->chol_flags, 0, sizeof(int32_t) * (2 * ntask + 2), s));
     // one CTA per SM: the chain CTA gets an SM of its own
     const int grid = std::min(ntask + 1, std::max(sms, 2));
+    kc_begin(m, KC_FACTOR);
     k_chol_tiles<TF><<<grid, 512, kCholTilesSmem * sizeof(TF), s>>>(
         A, n, nblk, reinterpret_cast<TF *>(m->dinv), m->chol_flags, m->err);
+    kc_end(m, KC_FACTOR);
     note_launch(m);
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
@@ -1087,8 +1089,10 @@ static int launch_solve_chain(const TF *L, const TF *Dinv, int64_t n, int nblk, 
     }
     for (int backward = 0; backward < 2; backward++) {
         FEM3_CUDA(cudaMemsetAsync(m->flags, 0, sizeof(int32_t) * (2 * nblk + 2), s));
+        kc_begin(m, KC_CHAIN);
         k_solve_chain<TF, NR><<<1 + workers, kSolveThreads, solve_chain_smem<TF, NR>(), s>>>(
             L, Dinv, n, nblk, Y, nrhs, backward, Gop, Z, m->flags, m->err);
+        kc_end(m, KC_CHAIN);
         note_launch(m);
     }
     return FEM3_OK;
@@ -1230,13 +1234,14 @@ __global__ void k_residual_cols(const double *__restrict__ b, const double *__re
     }
 }
 
-// u8[i][v] = u[v * n + i] for v < nv, zero for nv <= v < 8
-__global__ void k_interleave8(const double *__restrict__ u, int64_t n, int nv, double *u8) {
+// ui[i][v] = u[v * n + i] for v < nv, zero for nv <= v < NR (NR = 4 or 8 vectors a pass)
+template <int NR>
+__global__ void k_interleave(const double *__restrict__ u, int64_t n, int nv, double *ui) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 8 * n) return;
-    const int64_t i = e >> 3;
-    const int v = (int)(e & 7);
-    u8[e] = v < nv ? u[(int64_t)v * n + i] : 0.0;
+    if (e >= NR * n) return;
+    const int64_t i = e / NR;
+    const int v = (int)(e - i * NR);
+    ui[e] = v < nv ? u[(int64_t)v * n + i] : 0.0;
 }
 
 __global__ void k_to_f32(const double *__restrict__ a, float *b, int64_t n) {
@@ -1491,7 +1496,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
                 const int r = e / NR, v = e - r * NR;
                 const int64_t dof = dof_idx[d0 + rc0 + r];
                 float a, a2;
-                f64_split(NR == 1 ? u[dof] : u[dof * 8 + v], a, a2);
+                f64_split(NR == 1 ? u[dof] : u[dof * NR + v], a, a2);
                 us[e] = make_float2(a, a2);
             }
             cp_async_wait_all();
@@ -1569,7 +1574,10 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
 }
 
 // Au = A u for nv vectors (column-major, leading dimension n_dof), applied from
-// the tables; vectors go through the tables in groups of up to eight per pass.
+// the tables; vectors go through the tables in groups of up to eight per pass, and a last
+// group of one or up to four vectors takes the narrower form of the kernel (the pass costs
+// about its vectors' arithmetic: an eight-wide pass for one leftover vector cost as much as
+// a full group).
 int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
@@ -1578,40 +1586,51 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
     if (!attr) {
         FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)apply_bin_smem<1>()));
+        FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)apply_bin_smem<4>()));
         FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)apply_bin_smem<8>()));
         attr = true;
     }
     FEM3_TRY(ap_prepare(m));
-    double *u8 = nullptr;
-    if (nv > 1) FEM3_CUDA(cudaMallocAsync((void **)&u8, sizeof(double) * 8 * std::max<int64_t>(1, n), s));
-    for (int v0 = 0; v0 < nv; v0 += 8) {
-        const int cnt = nv > 1 ? std::min(8, nv - v0) : 1;
-        if (nv > 1) {
-            k_interleave8<<<g256(8 * n), 256, 0, s>>>(u_d + v0 * n, n, cnt, u8);
-            note_launch(m);
-        }
-        ApplyAxes P;
-        int64_t nblk = 0;
-        for (int axis = 0; axis < 3; axis++) {
-            AxisBins &B = m->bins[axis];
-            const bool on = B.n_tmpl > 0 && B.n_bins > 0;
-            const float skh = (float)m->sK[axis], skl = (float)(m->sK[axis] - (double)skh);
-            P.a[axis] = ApplyAxis{m->tabL[axis], B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_ld,
-                                  B.tab_off, skh, skl, on ? B.n_bins : 0};
-            nblk += on ? B.n_bins : 0;
-        }
-        if (nblk > 0) {
-            if (nv == 1)
-                k_apply_bin<1><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<1>(), s>>>(
-                    P, u_d, 1, Au_d, n);
-            else
-                k_apply_bin<8><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<8>(), s>>>(
-                    P, u8, cnt, Au_d + v0 * n, n);
-            note_launch(m);
-        }
+    double *ui = nullptr;
+    if (nv > 1) FEM3_CUDA(cudaMallocAsync((void **)&ui, sizeof(double) * 8 * std::max<int64_t>(1, n), s));
+    ApplyAxes P;
+    int64_t nblk = 0;
+    for (int axis = 0; axis < 3; axis++) {
+        AxisBins &B = m->bins[axis];
+        const bool on = B.n_tmpl > 0 && B.n_bins > 0;
+        const float skh = (float)m->sK[axis], skl = (float)(m->sK[axis] - (double)skh);
+        P.a[axis] = ApplyAxis{m->tabL[axis], B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_ld,
+                              B.tab_off, skh, skl, on ? B.n_bins : 0};
+        nblk += on ? B.n_bins : 0;
     }
-    if (u8) FEM3_CUDA(cudaFreeAsync(u8, s));
+    for (int v0 = 0; v0 < nv && nblk > 0; v0 += 8) {
+        const int cnt = std::min(8, nv - v0);
+        double *out = Au_d + (int64_t)v0 * n;
+        if (cnt > 1) {
+            const int nri = cnt <= 4 ? 4 : 8;
+            if (nri == 4)
+                k_interleave<4><<<g256(4 * n), 256, 0, s>>>(u_d + (int64_t)v0 * n, n, cnt, ui);
+            else
+                k_interleave<8><<<g256(8 * n), 256, 0, s>>>(u_d + (int64_t)v0 * n, n, cnt, ui);
+            note_launch(m);
+        }
+        kc_begin(m, KC_APPLY);
+        if (cnt == 1) {
+            k_apply_bin<1><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<1>(), s>>>(
+                P, u_d + (int64_t)v0 * n, 1, out, n);
+        } else if (cnt <= 4) {
+            k_apply_bin<4><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<4>(), s>>>(
+                P, ui, cnt, out, n);
+        } else {
+            k_apply_bin<8><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<8>(), s>>>(
+                P, ui, cnt, out, n);
+        }
+        kc_end(m, KC_APPLY);
+        note_launch(m);
+    }
+    if (ui) FEM3_CUDA(cudaFreeAsync(ui, s));
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }

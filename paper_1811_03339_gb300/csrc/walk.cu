@@ -720,8 +720,10 @@ int walk_tables(Mesh *m, const double alpha[3]) {
     const int64_t blocks = std::max<int64_t>(1, (int64_t)sms * 8);
     const int per_block =
         (int)std::max<int64_t>(128, (m->n_gp + blocks - 1) / blocks);
+    kc_begin(m, KC_WALK);
     k_walk_tables<<<dim3((unsigned)((m->n_gp + per_block - 1) / per_block), 3), 128, 0, s>>>(
         W, T, m->n_gp, per_block, m->err, segc);
+    kc_end(m, KC_WALK);
     note_launch(m);
     stage_end(m, 2);
     FEM3_CUDA(cudaGetLastError());

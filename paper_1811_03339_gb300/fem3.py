@@ -25,7 +25,9 @@ PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2, "bf16x3": 3}
 # every entry point declared in include/fem3.h
 SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_load", "fem3_solve",
            "fem3_adjoint", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
-           "fem3_counters", "fem3_bin_stats", "fem3_tc_tile", "fem3_last_error",
+           "fem3_counters", "fem3_bin_stats", "fem3_kernel_ms", "fem3_contract_work",
+           "fem3_tc_tile",
+           "fem3_last_error",
            "fem3_mesh_free",
            "fem3_spd_solve_static",
            "fem3_batch_create", "fem3_batch_mesh", "fem3_batch_run", "fem3_batch_free")
@@ -73,6 +75,8 @@ def load_library(build_if_missing: bool = True):
         "fem3_counters": [p, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)],
         "fem3_tc_tile": [p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "fem3_bin_stats": [p, ci, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)],
+        "fem3_kernel_ms": [p, ci, C.POINTER(C.c_float), C.POINTER(i32)],
+        "fem3_contract_work": [p, C.POINTER(dbl), p],
         "fem3_last_error": [C.c_char_p, C.c_size_t],
         "fem3_mesh_free": [p],
         "fem3_spd_solve_static": [p, i64, p, p, p],
@@ -184,6 +188,25 @@ def counters(h):
     s, f, b, n = C.c_int64(), C.c_double(), C.c_int64(), C.c_int64()
     _check(_lib.fem3_counters(h, C.byref(s), C.byref(f), C.byref(b), C.byref(n)))
     return dict(segments=s.value, contract_flops=f.value, table_bytes=b.value, launches=n.value)
+
+
+def contract_work(h, stream=None):
+    f = C.c_double(0)
+    _check(_lib.fem3_contract_work(h, C.byref(f), _stream(stream)))
+    return f.value
+
+
+KERNEL_CLASSES = ("walk_tables", "split", "contract", "factor", "chain", "apply")
+
+
+def kernel_ms(h):
+    """{class: (summed ms, launches)} of the profiled launches since the last assemble"""
+    out = {}
+    for k, name in enumerate(KERNEL_CLASSES):
+        v, n = C.c_float(0), C.c_int32(0)
+        _check(_lib.fem3_kernel_ms(h, k, C.byref(v), C.byref(n)))
+        out[name] = (v.value, n.value)
+    return out
 
 
 def bin_stats(h, axis):
@@ -302,6 +325,14 @@ class Mesh:
 
     def counters(self):
         return counters(self.h)
+
+    def contract_work(self):
+        """algorithmic flops of the last contraction: sum_g 4 nnz(L[g]) nnz(R[g]) per axis"""
+        return contract_work(self.h, self.stream)
+
+    def kernel_ms(self):
+        """{kernel class: (ms, launches)} timed on the launch stream (profiling handles)"""
+        return kernel_ms(self.h)
 
     def bin_stats(self, axis):
         """bins of one axis: count, template rows, largest dof set and Gauss-point count"""

@@ -177,6 +177,19 @@ def nodal_source(mesh: Mesh, alpha, K) -> np.ndarray:
     return manufactured_f(mesh.verts, alpha, K)
 
 
+def workload_rhs(name: str, mesh: Mesh) -> np.ndarray:
+    """Nodal right-hand sides of a named workload, float64 [n_nodes] or [n_nodes, nrhs].
+
+    The cubes take the manufactured source of their alpha and K (one column).  The
+    parallelepiped (whose chords do not run from 0 to 1, so the manufactured profile does
+    not apply) takes f = 1 and 16 seeded N(0, 1) columns (seed 11): 17 columns."""
+    w = WORKLOADS[name]
+    if w["affine"] is None:
+        return nodal_source(mesh, w["alpha"], w["K"])
+    return np.concatenate([np.ones((mesh.n_nodes, 1)), random_rhs(mesh.n_nodes, 16, seed=11)],
+                          axis=1)
+
+
 def random_rhs(n_nodes: int, nrhs: int, seed: int) -> np.ndarray:
     """Seeded N(0,1) nodal right-hand sides, float64 column-major [n_nodes, nrhs] (as F-order)."""
     rng = np.random.default_rng(seed)

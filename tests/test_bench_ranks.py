@@ -67,31 +67,52 @@ def test_reference_arm_runs_on_rank_zero_only():
     assert out.stdout.strip() == ""
 
 
-def test_contraction_rates():
-    """Executed MMA flops of the split forms (three products) over the stage time, against
-    the measured BF16 peak scaled by the nominal TF32 : BF16 ratio."""
+def test_kernel_rooflines():
+    """Each kernel class's achieved rate is its algorithmic work over its summed event time:
+    160 B per walked segment for the walk, n^3/3 flops for the factor, the split-product MMA
+    flops for the tensor-core contraction (and the ratio to the counted algorithmic flops),
+    4 double-float multiply-adds per table element and vector for the apply."""
     sys.path.insert(0, ROOT)
     import bench
 
-    peaks = {"bf16_tflops": 1934.0, "bf16_tflops_sustained": 1746.0}
-    r = bench.contraction_rates(7.45e9, 0.559, "tf32x3", peaks)
-    assert r["executed_mma_tflop"] == pytest.approx(3 * 7.45e9 / 1e12)
-    assert r["mma_tflops"] == pytest.approx(3 * 7.45e9 / 0.559e-3 / 1e12)
-    assert r["mma_peak_tflops"] == pytest.approx(1746.0 * 1.1 / 2.25)
-    assert r["mma_frac"] == pytest.approx(r["mma_tflops"] / r["mma_peak_tflops"])
-    b = bench.contraction_rates(7.45e9, 0.489, "bf16x3", {"bf16_tflops": 1900.0})
-    assert b["mma_peak_tflops"] == pytest.approx(1900.0)
-    assert bench.contraction_rates(7.45e9, 20.0, "fp64", peaks) == {"mma_tflops": None}
-    assert bench.contraction_rates(7.45e9, 0.0, "tf32x3", peaks) == {"mma_tflops": None}
+    peaks = {"hbm_gbs": 6757.9, "bf16_tflops": 1894.9}
+    kms = {"walk_tables": (6.0, 1), "split": (1.0, 3), "contract": (1.2, 3), "factor": (26.8, 1),
+           "chain": (6.0, 12), "apply": (24.0, 9)}
+    cnt = {"segments": 82_230_391, "table_bytes": 16 * 134_000_000, "contract_flops": 64.9e9,
+           "algorithmic_flops": 9.0e9, "apply_vectors": 51, "apply_passes": 9}
+    r = bench.kernel_rooflines(kms, cnt, 12167, "bf16x3", peaks, "parallelepiped24")
+    w = r["walk_tables"]
+    assert w["achieved"] == pytest.approx(160 * 82_230_391 / 6.0e-3 / 1e9)
+    assert w["frac"] == pytest.approx(w["achieved"] / 6757.9)
+    assert w["fp64_tflops"] == pytest.approx(25 * 82_230_391 / 6.0e-3 / 1e12)
+    f = r["factor"]
+    assert f["achieved"] == pytest.approx(12167 ** 3 / 3 / 26.8e-3 / 1e12)
+    assert f["peak"] == pytest.approx(152 * 128 * 2 * 2.070 / 1e3)
+    c = r["contract"]
+    assert c["achieved"] == pytest.approx(3 * 64.9e9 / 1.2e-3 / 1e12)
+    assert c["peak"] == pytest.approx(1894.9)
+    assert c["executed_over_algorithmic"] == pytest.approx(3 * 64.9e9 / 9.0e9)
+    a = r["apply"]
+    assert a["achieved"] == pytest.approx(4 * 13 * 134e6 * 51 / 24.0e-3 / 1e12)
+    assert a["peak"] == pytest.approx(152 * 128 * 2.070 / 1e3)
+    assert r["chain"]["launch_ms"] == pytest.approx(0.5)
+    t = bench.kernel_rooflines(kms, cnt, 12167, "tf32x3", peaks, "parallelepiped24")
+    assert t["contract"]["peak"] == pytest.approx(1894.9 * 1.1 / 2.25)
+    s64 = bench.kernel_rooflines({"contract": (150.0, 3)}, cnt, 12167, "fp64", peaks, "x")
+    assert s64["contract"]["bound"] == "alu" and s64["contract"]["peak"] == pytest.approx(
+        152 * 128 * 2 * 2.070 / 1e3 / 64)
 
 
-def test_walk_bandwidth():
+def test_measured_traffic_scales_and_expires(monkeypatch):
+    """ncu traffic is scaled to the launch's units and dropped once the source changed."""
     sys.path.insert(0, ROOT)
     import bench
 
-    r = bench.walk_bandwidth(527e6, 749e6, 1.15, {"hbm_gbs": 6657.6})
-    assert r["table_gbs"] == pytest.approx(527e6 / 1.15e-3 / 1e9)
-    assert r["traffic_gbs"] == pytest.approx(749e6 / 1.15e-3 / 1e9)
-    assert r["traffic_frac"] == pytest.approx(r["traffic_gbs"] / 6657.6)
-    assert "traffic_gbs" not in bench.walk_bandwidth(527e6, None, 1.15, {"hbm_gbs": 6800.0})
-    assert bench.walk_bandwidth(527e6, 749e6, 0.0, {"hbm_gbs": 6800.0}) == {"table_gbs": None}
+    sha = bench._source_sha("walk.cu")
+    monkeypatch.setitem(bench.TRAFFIC, "k_walk_tables",
+                        {"source": "walk.cu", "sha256": sha, "bytes": 1.0e9, "units": 1.0e7})
+    assert bench.measured_traffic("k_walk_tables", 2.0e7) == pytest.approx(2.0e9)
+    monkeypatch.setitem(bench.TRAFFIC, "k_walk_tables",
+                        {"source": "walk.cu", "sha256": "0" * 64, "bytes": 1.0e9, "units": 1.0e7})
+    assert bench.measured_traffic("k_walk_tables", 2.0e7) is None
+    assert bench.measured_traffic("k_other", 1.0) is None

@@ -466,3 +466,38 @@ def test_device_inputs_match_host_inputs():
     assert _rel(Ad.cpu().numpy(), Ah.cpu().numpy()) <= 1e-14
     mh.free()
     md.free()
+
+
+def test_contraction_work_counts_the_oracle_nonzeros():
+    """fem3_contract_work = sum over axes and Gauss points of 4 nnz(L[g]) nnz(R[g]), the
+    nonzeros of the oracle's table rows (the supports agree exactly)."""
+    mesh, o, alpha, K = _case("cube7_jitter")
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    m.assemble(alpha, K, "tf32x3")
+    got = m.contract_work()
+    exp = 0
+    for axis in range(3):
+        L, R = o.tables(axis, alpha[axis] / 2)
+        exp += 4 * int(np.sum((L != 0).sum(1).astype(np.int64) * (R != 0).sum(1)))
+    assert got == exp
+    m.free()
+
+
+def test_kernel_class_timing():
+    """A profiling handle times every launch of each kernel class on the launch stream; the
+    walk class is the walk stage's one launch."""
+    mesh, o, alpha, K = _case("cube7_jitter")
+    m = fem3.Mesh(mesh.verts, mesh.tets, profile=True)
+    m.assemble(alpha, K, "tf32x3")
+    m.solve(np.ones((mesh.n_nodes, 3)), tol=1e-12)
+    k = m.kernel_ms()
+    for name in ("walk_tables", "split", "contract", "factor", "chain", "apply"):
+        assert k[name][1] >= 1 and k[name][0] > 0.0, name
+    assert k["walk_tables"][1] == 1
+    assert k["walk_tables"][0] <= m.stage_ms()[2] * 1.01 + 1e-3
+    # a new assemble starts the sums again
+    m.assemble(alpha, K, "fp64")
+    m.sync()
+    k2 = m.kernel_ms()
+    assert k2["walk_tables"][1] == 1 and k2["apply"][1] == 0
+    m.free()

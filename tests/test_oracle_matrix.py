@@ -192,3 +192,21 @@ def test_adjoint_matches_central_differences(oracle_for):
 def test_riesz_scale():
     assert riesz_scale(2.0) == pytest.approx(-0.5, abs=1e-15)
     assert riesz_scale(1.5) < 0
+
+
+def test_gauss_point_subsets_sum_to_the_assembly(oracle_for):
+    """The element sum over a partition of the Gauss points (three interleaved subsets and a
+    permuted order) adds up to the whole assembly: the bounded-sample timing of the oracle
+    runs the same arithmetic as the full assembly."""
+    mesh, o = oracle_for(4, 0.2, 3, None)
+    alpha, K = (1.3, 1.6, 1.8), (1.0, 2.0, 0.5)
+    A = o.assemble(alpha, K)
+    perm = np.random.default_rng(0).permutation(o.n_gp)
+    S = np.zeros_like(A)
+    for part in (perm[0::3], perm[1::3], perm[2::3]):
+        o.assemble_gps(alpha, K, part, S)
+    assert np.abs(S - A).max() <= 1e-13 * np.abs(A).max()
+    # one Gauss point alone is a rank-2 symmetric update of the matrix
+    one = o.assemble_gps(alpha, K, [5])
+    assert np.abs(one - one.T).max() <= 1e-15 * np.abs(one).max()
+    assert np.linalg.matrix_rank(one, tol=1e-10 * np.abs(one).max()) <= 6
