@@ -78,6 +78,9 @@ typedef struct fem3_options {
     int32_t tc_tile;   /* tile width (columns) of the tensor-core contraction: 128 or 256;
                           0 selects the tuner: the first contraction of a problem size class
                           in the process times both and later ones use the faster */
+    int32_t chol_tc;   /* FP32 factorisation of the mixed forms: 0 by size (blocked with
+                          tensor-core TF32 x 3 trailing updates from n_dof >= 4096, else the
+                          one-launch tile-task factorisation), 1 always blocked, -1 never */
 } fem3_options;
 
 /*

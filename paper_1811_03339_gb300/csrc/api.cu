@@ -247,6 +247,7 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
                                                : (int)(8.0 * cbrt((double)n_tets)) + 64;
     m->profile = opt && opt->profile;
     m->tc_tile_opt = opt ? opt->tc_tile : 0;
+    m->chol_tc_opt = opt ? opt->chol_tc : 0;
     if (m->tc_tile_opt != 0 && m->tc_tile_opt != 128 && m->tc_tile_opt != 256) {
         delete m;
         return set_error(FEM3_E_ARG, "tc_tile must be 0, 128 or 256");

@@ -1,0 +1,509 @@
+// Blocked right-looking Cholesky A = L L^T in FP32 with the trailing updates on the tensor
+// cores (tcgen05, TF32 x 3 split products, FP32 accumulation), for the mixed forms' large
+// matrices.  The factor is used as the preconditioner of the FP64 iterative refinement
+// (the mixed forms' solve), so it needs the accuracy of an FP32 factorisation, which the
+// split products keep (about 2^-21 relative per product against 2^-10 for one TF32
+// product).
+//
+// Per panel of P = 128 columns [j0, j0 + P):
+//   1. k_cholp_diag (one CTA): the 128 x 128 diagonal block as two 64 x 64 blocks -
+//      factor and invert D11, L21 = A21 L11^{-T}, factor and invert D22 - L21 L21^T - and
+//      the panel's inverse [[X11, 0], [-X22 L21 X11, X22]]; the 64 x 64 inverses go to dinv
+//      and L21 to A, the layout the triangular-solve chains read (the strictly lower
+//      64 x 64 tiles of A hold L; a diagonal tile is only ever used through its inverse);
+//   2. k_cholp_panel: L[i, panel] = A[i, panel] X^T for every row i below the panel, into
+//      A and, split into TF32 hi + lo pairs, into the K-major operand rows W_hi, W_lo;
+//   3. k_cholp_trail: A[I, J] -= W_I W_J^T over the 128 x 128 tiles I >= J of the trailing
+//      matrix, TMA loads (128-byte swizzle) into a two-stage ring, three MMAs per 32-column
+//      K step (hi hi, hi lo, lo hi) into a TMEM accumulator, and a read-modify-write
+//      epilogue of the tile (the lower triangle on diagonal tiles).
+// No kernel waits for another CTA; the mbarrier waits are bounded (ERR_CHOL on expiry).
+#include <math.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "fem3_impl.cuh"
+
+namespace fem3 {
+
+namespace {
+
+#include "chol_smem.cuh"
+
+constexpr int kWaitLimit = 1 << 22;
+#include "tc_ptx.cuh"
+
+constexpr int kP = 128;                        // panel width
+constexpr int kLd = NB + 1;                    // shared 64 x 64 block row stride
+constexpr int kDiagSmemFloats = 5 * NB * kLd;  // a_s, x_s, b_s (A21 -> L21), x11, t
+constexpr int kPanelRows = 64;                 // rows of a panel-solve CTA
+constexpr int kPLd = kP + 4;                   // shared row stride of the panel solve
+constexpr uint32_t kTile = 128 * 128;          // bytes of one 128-row x 128-byte TMA box
+constexpr uint32_t kStage = 4 * kTile;         // A hi, A lo, B hi, B lo: 64 KB
+constexpr int kStages = 2;
+constexpr int kCsLd = 129;                     // row stride of the staged C tile (floats)
+constexpr uint32_t kCsBytes = 128 * kCsLd * 4;  // 66 KB
+constexpr uint32_t kTrailSmem = kStages * kStage + kCsBytes + 1024 + 256;
+
+// ------------------------------- diagonal block ----------------------------------
+// c[i][j] (+)= sgn * sum_k a[i][k] b(k, j) over a 64 x 64 x 64 product in shared memory,
+// 512 threads, 8 outputs each; BT selects b(k, j) = b[j][k] (transposed) or b[k][j].
+template <bool BT>
+__device__ __forceinline__ void smem_gemm64(float (*c)[kLd], const float (*a)[kLd],
+                                            const float (*b)[kLd], float sgn, bool accumulate) {
+    const int tid = threadIdx.x, r = tid >> 3, c0 = (tid & 7) * 8;
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) acc[q] = 0.f;
+    for (int k = 0; k < NB; k++) {
+        const float av = a[r][k];
+#pragma unroll
+        for (int q = 0; q < 8; q++) acc[q] = fmaf(av, BT ? b[c0 + q][k] : b[k][c0 + q], acc[q]);
+    }
+    __syncthreads();   // c may alias an operand's storage in the caller's sequence
+#pragma unroll
+    for (int q = 0; q < 8; q++) c[r][c0 + q] = (accumulate ? c[r][c0 + q] : 0.f) + sgn * acc[q];
+    __syncthreads();
+}
+
+// one CTA of 512 threads: the diagonal block [j0, j0 + nbp) of A (nbp <= 128)
+__global__ void __launch_bounds__(512, 1) k_cholp_diag(float *A, int64_t n, int64_t j0, int nbp,
+                                                       float *dinv, float *Linv, int32_t *err) {
+    extern __shared__ __align__(16) float sm_diag[];
+    float(*a_s)[kLd] = reinterpret_cast<float(*)[kLd]>(sm_diag);
+    float(*x_s)[kLd] = a_s + NB;
+    float(*b_s)[kLd] = x_s + NB;
+    float(*x11)[kLd] = b_s + NB;
+    float(*t_s)[kLd] = x11 + NB;
+    const int tid = threadIdx.x;
+    const int nb1 = min(NB, nbp), nb2 = nbp - nb1;
+    // D11, identity past the block's end
+    for (int e = tid; e < NB * NB; e += 512) {
+        const int i = e >> 6, c = e & 63;
+        a_s[i][c] = (i < nb1 && c < nb1) ? A[(j0 + i) * n + j0 + c] : (i == c ? 1.f : 0.f);
+    }
+    __syncthreads();
+    potrf_inv_smem<float>(a_s, x_s, nb1, j0, err);
+    float *d1 = dinv + (j0 / NB) * (int64_t)NB * NB;
+    for (int e = tid; e < NB * NB; e += 512) {
+        const int i = e >> 6, c = e & 63;
+        d1[e] = x_s[i][c];
+        x11[i][c] = x_s[i][c];
+    }
+    if (nb2 > 0) {
+        // L21 = A21 X11^T (rows past the block's end are zero)
+        for (int e = tid; e < NB * NB; e += 512) {
+            const int i = e >> 6, c = e & 63;
+            b_s[i][c] = (i < nb2) ? A[(j0 + NB + i) * n + j0 + c] : 0.f;
+        }
+        __syncthreads();
+        smem_gemm64<true>(b_s, b_s, x11, 1.f, false);          // b_s = L21
+        for (int e = tid; e < NB * NB; e += 512) {
+            const int i = e >> 6, c = e & 63;
+            if (i < nb2) A[(j0 + NB + i) * n + j0 + c] = b_s[i][c];
+            a_s[i][c] = (i < nb2 && c < nb2) ? A[(j0 + NB + i) * n + j0 + NB + c]
+                                             : (i == c ? 1.f : 0.f);
+        }
+        __syncthreads();
+        // D22 - L21 L21^T (the identity padding stays: L21's padded rows are zero)
+        smem_gemm64<true>(t_s, b_s, b_s, 1.f, false);          // t = L21 L21^T
+        for (int e = tid; e < NB * NB; e += 512) {
+            const int i = e >> 6, c = e & 63;
+            a_s[i][c] -= t_s[i][c];
+        }
+        __syncthreads();
+        potrf_inv_smem<float>(a_s, x_s, nb2, j0 + NB, err);    // x_s = X22
+        float *d2 = d1 + (int64_t)NB * NB;
+        for (int e = tid; e < NB * NB; e += 512) d2[e] = x_s[e >> 6][e & 63];
+        // X21 = -X22 (L21 X11)
+        smem_gemm64<false>(t_s, b_s, x11, 1.f, false);         // t = L21 X11
+        smem_gemm64<false>(b_s, x_s, t_s, -1.f, false);        // b_s = X21
+    }
+    // the panel inverse [[X11, 0], [X21, X22]] (128 x 128, zero past nbp)
+    for (int e = tid; e < kP * kP; e += 512) {
+        const int i = e >> 7, c = e & 127;
+        float v = 0.f;
+        if (i < NB && c < NB) v = x11[i][c];
+        else if (i >= NB && nb2 > 0 && c < NB) v = b_s[i - NB][c];
+        else if (i >= NB && nb2 > 0 && c >= NB) v = x_s[i - NB][c - NB];
+        Linv[e] = v;
+    }
+}
+
+// ------------------------------- panel solve --------------------------------------
+// rows [r0, r0 + 64) below the panel: L[i][c] = sum_{k <= c} A[i][j0 + k] X[c][k]; written
+// to A and, as TF32 hi + lo, to W rows i - t0 (t0 = j0 + P, the first trailing row)
+__global__ void __launch_bounds__(256) k_cholp_panel(float *A, int64_t n, int64_t j0,
+                                                     const float *__restrict__ Linv, float *Whi,
+                                                     float *Wlo) {
+    extern __shared__ __align__(16) float sm_panel[];
+    float(*xt)[kPLd] = reinterpret_cast<float(*)[kPLd]>(sm_panel);   // xt[k][c] = X[c][k]
+    float(*as)[kPLd] = xt + kP;                                       // as[r][k]
+    const int tid = threadIdx.x;
+    const int64_t t0 = j0 + kP;
+    const int64_t r0 = t0 + (int64_t)blockIdx.x * kPanelRows;
+    for (int e = tid; e < kP * kP; e += 256) {
+        const int c = e >> 7, k = e & 127;
+        xt[k][c] = Linv[e];
+    }
+    for (int e = tid; e < kPanelRows * kP; e += 256) {
+        const int r = e >> 7, k = e & 127;
+        as[r][k] = r0 + r < n ? A[(r0 + r) * n + j0 + k] : 0.f;
+    }
+    __syncthreads();
+    const int ty = tid >> 4, tx = tid & 15;   // rows 4 ty .. 4 ty + 3, columns 8 tx .. 8 tx + 7
+    float acc[4][8];
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 8; q++) acc[p][q] = 0.f;
+    for (int k = 0; k < kP; k++) {
+        float a[4], b[8];
+#pragma unroll
+        for (int p = 0; p < 4; p++) a[p] = as[4 * ty + p][k];
+        const float4 b0 = *reinterpret_cast<const float4 *>(&xt[k][8 * tx]);
+        const float4 b1 = *reinterpret_cast<const float4 *>(&xt[k][8 * tx + 4]);
+        b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+        b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+        for (int p = 0; p < 4; p++)
+#pragma unroll
+            for (int q = 0; q < 8; q++) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+        const int64_t i = r0 + 4 * ty + p;
+        if (i >= n) continue;
+        float hi[8], lo[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            hi[q] = tf32_rna(acc[p][q]);
+            lo[q] = tf32_rna(acc[p][q] - hi[q]);
+        }
+        float *dst = A + i * n + j0 + 8 * tx;
+        float *wh = Whi + (i - t0) * kP + 8 * tx, *wl = Wlo + (i - t0) * kP + 8 * tx;
+#pragma unroll
+        for (int q = 0; q < 8; q++) dst[q] = acc[p][q];
+        *reinterpret_cast<float4 *>(wh) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4 *>(wh + 4) = make_float4(hi[4], hi[5], hi[6], hi[7]);
+        *reinterpret_cast<float4 *>(wl) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        *reinterpret_cast<float4 *>(wl + 4) = make_float4(lo[4], lo[5], lo[6], lo[7]);
+    }
+}
+
+// ------------------------------- trailing update ----------------------------------
+// tile index x -> (I, J), I >= J, x = I (I + 1) / 2 + J
+__device__ __forceinline__ void tri_decode(int x, int &I, int &J) {
+    int i = (int)((sqrtf(8.f * (float)x + 1.f) - 1.f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= x) i++;
+    while (i * (i + 1) / 2 > x) i--;
+    I = i;
+    J = x - i * (i + 1) / 2;
+}
+
+// mode 0: every tile I >= J; 1: the first block column (J = 0, the next panel's columns);
+// 2: every tile 1 <= J <= I (the rest)
+__global__ void __launch_bounds__(128, 1) k_cholp_trail(const __grid_constant__ CUtensorMap mHi,
+                                                        const __grid_constant__ CUtensorMap mLo,
+                                                        float *A, int64_t n, int64_t t0, int mode,
+                                                        int32_t *err) {
+    extern __shared__ __align__(1024) unsigned char sm_trail[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(sm_trail) + 1023) & ~(uintptr_t)1023);
+    float *Cs = reinterpret_cast<float *>(base + kStages * kStage);   // [128][129]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + kStages * kStage + kCsBytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 1);
+    __shared__ int s_fail;
+    int I, J;
+    if (mode == 1) {
+        I = blockIdx.x;
+        J = 0;
+    } else {
+        tri_decode(blockIdx.x, I, J);
+        if (mode == 2) {
+            I++;
+            J++;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int nk = kP / 32;   // K steps of 32 TF32 columns (one 128-byte swizzle row)
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]);
+    const uint32_t done = smem_u32(&bars[2 * kStages]);
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    // the C tile's rows are fetched now (4-byte cp.async: a row of A starts on any 4-byte
+    // boundary), all in flight at once, so that they arrive while the MMAs run
+    const int64_t gr0 = t0 + 128 * (int64_t)I, gc0 = t0 + 128 * (int64_t)J;
+    for (int e = threadIdx.x; e < 128 * 128; e += 128) {
+        const int r = e >> 7, c = e & 127;
+        const int64_t gr = gr0 + r, gc = gc0 + c;
+        if (gr < n && gc < n && (I != J || gc <= gr))
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(Cs + r * kCsLd + c)),
+                         "l"(A + gr * n + gc)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (warp == 0 && lane == 0) {
+        for (int k = 0; k < nk; k++) {
+            const int s = k % kStages;
+            if (k >= kStages && !mbar_wait(empty0 + 8 * s, ((k / kStages) - 1) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            uint8_t *st = base + s * kStage;
+            const uint32_t bar = full0 + 8 * s;
+            mbar_expect_tx(bar, kStage);
+            tma_load_2d(smem_u32(st), &mHi, 32 * k, 128 * I, bar);
+            tma_load_2d(smem_u32(st + kTile), &mLo, 32 * k, 128 * I, bar);
+            tma_load_2d(smem_u32(st + 2 * kTile), &mHi, 32 * k, 128 * J, bar);
+            tma_load_2d(smem_u32(st + 3 * kTile), &mLo, 32 * k, 128 * J, bar);
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_mma(128, 128, 2u);
+        for (int k = 0; k < nk; k++) {
+            const int s = k % kStages;
+            if (!mbar_wait(full0 + 8 * s, (k / kStages) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t st = smem_u32(base + s * kStage);
+            const uint32_t aH = st, aL = st + kTile, bH = st + 2 * kTile, bL = st + 3 * kTile;
+#pragma unroll
+            for (int ks = 0; ks < 4; ks++) {   // 32 bytes (8 TF32) per MMA
+                const uint32_t off = ks * 32;
+                umma<false>(tmem, umma_desc_sw128(aH + off), umma_desc_sw128(bH + off), idesc,
+                            (k > 0 || ks > 0) ? 1u : 0u);
+                umma<false>(tmem, umma_desc_sw128(aH + off), umma_desc_sw128(bL + off), idesc, 1u);
+                umma<false>(tmem, umma_desc_sw128(aL + off), umma_desc_sw128(bH + off), idesc, 1u);
+            }
+            umma_commit(empty0 + 8 * s);
+        }
+        umma_commit(done);
+    }
+    __syncthreads();
+    const bool ok = __syncthreads_and(mbar_wait(done, 0) && !s_fail);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) {
+        if (threadIdx.x == 0) atomicAdd(&err[ERR_CHOL], 1);
+    } else {
+        // thread = tile row (TMEM lane): C -= X in shared memory (row stride 129: lanes on
+        // consecutive rows hit distinct banks), then the tile goes back to A with the lanes
+        // of a warp along a row (each store instruction covers 128 consecutive bytes)
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        const int r = warp * 32 + lane;
+        for (int cb = 0; cb < 128; cb += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, v);
+#pragma unroll
+            for (int q = 0; q < 16; q++) Cs[r * kCsLd + cb + q] -= v[q];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 128 * 128; e += 128) {
+            const int rr = e >> 7, c = e & 127;
+            const int64_t gr = gr0 + rr, gc = gc0 + c;
+            if (gr < n && gc < n && (I != J || gc <= gr)) A[gr * n + gc] = Cs[rr * kCsLd + c];
+        }
+    }
+    if (!ok) asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+}
+
+// [rows][128] FP32 operand rows, boxes of 32 columns (one 128-byte swizzle row) x 128 rows
+int make_w_map(CUtensorMap *map, float *base, int64_t rows) {
+    auto enc = get_encode();
+    if (!enc) return set_error(FEM3_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)kP, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kP * sizeof(float)};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FEM3_E_CUDA, "cuTensorMapEncodeTiled failed (factor)");
+    return FEM3_OK;
+}
+
+// Side stream and events of the look-ahead, shared through a process-wide pool: a
+// factorisation takes a context for the time it enqueues its launches (every wait on an
+// event is enqueued before the event is recorded again), so concurrent callers never share
+// one.
+struct CholCtx {
+    int device = -1;
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> ev;
+};
+std::mutex g_ctx_mu;
+std::vector<CholCtx *> g_ctx_free;
+
+int ctx_acquire(CholCtx **out, int npan) {
+    int dev = 0;
+    FEM3_CUDA(cudaGetDevice(&dev));
+    CholCtx *c = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ctx_mu);
+        for (size_t i = 0; i < g_ctx_free.size(); i++)
+            if (g_ctx_free[i]->device == dev) {
+                c = g_ctx_free[i];
+                g_ctx_free.erase(g_ctx_free.begin() + i);
+                break;
+            }
+    }
+    if (!c) {
+        c = new CholCtx();
+        c->device = dev;
+        cudaError_t e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_error(e, "cudaStreamCreateWithFlags");
+        }
+    }
+    while ((int)c->ev.size() < 2 * npan) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (r != cudaSuccess) {
+            std::lock_guard<std::mutex> lk(g_ctx_mu);
+            g_ctx_free.push_back(c);
+            return cuda_error(r, "cudaEventCreateWithFlags");
+        }
+        c->ev.push_back(e);
+    }
+    *out = c;
+    return FEM3_OK;
+}
+
+void ctx_release(CholCtx *c) {
+    std::lock_guard<std::mutex> lk(g_ctx_mu);
+    g_ctx_free.push_back(c);
+}
+
+}  // namespace
+
+// FP32 factorisation of A (n x n, lower triangle) in place, inverses of the 64 x 64
+// diagonal blocks into m->dinv; the same output layout as the tile-task factorisation.
+//
+// Look-ahead over two streams.  Panel p: D(p) diagonal block, P(p) panel solve into the
+// operand buffer p % 2, Ta(p) the trailing update of panel p + 1's columns, Tb(p) the rest
+// of the trailing update.  The caller's stream runs D, P and Ta; the side stream runs Tb,
+// so Tb(p) overlaps D(p + 1) and P(p + 1).  Orderings: D(p) after Tb(p - 2) (which updated
+// panel p's columns and read the operand buffer P(p) rewrites), Ta(p) after Tb(p - 1) (both
+// update panel p + 1's columns), Tb(p) after P(p); the caller's stream waits for the last Tb.
+int chol_tc(Mesh *m, float *A, int64_t n) {
+    if (n <= 0) return FEM3_OK;
+    cudaStream_t s = m->stream;
+    const int64_t wrows = std::max<int64_t>(128, (n + 127) / 128 * 128);
+    if (!m->chol_w || m->chol_w_rows < wrows) {
+        FEM3_TRY(dev_alloc(m, (void **)&m->chol_w, sizeof(float) * (4 * wrows * kP + kP * kP)));
+        m->chol_w_rows = wrows;
+        // operand rows past the trailing matrix are read by the edge tiles' MMAs (their
+        // products are masked in the epilogue): keep them finite
+        FEM3_CUDA(cudaMemsetAsync(m->chol_w, 0, sizeof(float) * 4 * wrows * kP, s));
+    }
+    float *W[2][2] = {{m->chol_w, m->chol_w + wrows * kP},
+                      {m->chol_w + 2 * wrows * kP, m->chol_w + 3 * wrows * kP}};
+    float *Linv = m->chol_w + 4 * wrows * kP;
+    CUtensorMap maps[2][2];
+    for (int b = 0; b < 2; b++)
+        for (int h = 0; h < 2; h++) FEM3_TRY(make_w_map(&maps[b][h], W[b][h], wrows));
+    static bool attr = false;
+    if (!attr) {
+        FEM3_CUDA(cudaFuncSetAttribute(k_cholp_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float) * kDiagSmemFloats)));
+        FEM3_CUDA(cudaFuncSetAttribute(k_cholp_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float) * (kP + kPanelRows) * kPLd)));
+        FEM3_CUDA(cudaFuncSetAttribute(k_cholp_trail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kTrailSmem));
+        attr = true;
+    }
+    const int npan = (int)((n + kP - 1) / kP);
+    CholCtx *cx = nullptr;
+    FEM3_TRY(ctx_acquire(&cx, npan));
+    cudaStream_t s1 = cx->side;
+    cudaEvent_t *evP = cx->ev.data(), *evB = cx->ev.data() + npan;
+    float *dinv = reinterpret_cast<float *>(m->dinv);
+    int st = FEM3_OK;
+    int last_b = -1;
+    auto launch_ok = [&](const char *what) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess && st == FEM3_OK) st = cuda_error(e, what);
+        return st == FEM3_OK;
+    };
+    kc_begin(m, KC_FACTOR);
+    for (int p = 0; p < npan && st == FEM3_OK; p++) {
+        const int64_t j0 = (int64_t)p * kP;
+        const int nbp = (int)std::min<int64_t>(kP, n - j0);
+        if (p >= 2 && cudaStreamWaitEvent(s, evB[p - 2], 0) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "cudaStreamWaitEvent");
+            break;
+        }
+        k_cholp_diag<<<1, 512, sizeof(float) * kDiagSmemFloats, s>>>(A, n, j0, nbp, dinv, Linv,
+                                                                      m->err);
+        note_launch(m);
+        if (!launch_ok("k_cholp_diag")) break;
+        const int64_t t0 = j0 + nbp, mt = n - t0;
+        if (mt <= 0) break;
+        const int b = p & 1;
+        k_cholp_panel<<<(unsigned)((mt + kPanelRows - 1) / kPanelRows), 256,
+                        sizeof(float) * (kP + kPanelRows) * kPLd, s>>>(A, n, j0, Linv, W[b][0],
+                                                                       W[b][1]);
+        note_launch(m);
+        if (!launch_ok("k_cholp_panel")) break;
+        const int64_t T = (mt + 127) / 128;
+        if (cudaEventRecord(evP[p], s) != cudaSuccess ||
+            cudaStreamWaitEvent(s1, evP[p], 0) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "cudaEventRecord");
+            break;
+        }
+        const int64_t nb_rest = T * (T + 1) / 2 - T;
+        if (nb_rest > 0) {
+            k_cholp_trail<<<(unsigned)nb_rest, 128, kTrailSmem, s1>>>(maps[b][0], maps[b][1], A, n,
+                                                                     t0, 2, m->err);
+            note_launch(m);
+            if (!launch_ok("k_cholp_trail")) break;
+        }
+        if (cudaEventRecord(evB[p], s1) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "cudaEventRecord");
+            break;
+        }
+        last_b = p;
+        if (p >= 1 && cudaStreamWaitEvent(s, evB[p - 1], 0) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "cudaStreamWaitEvent");
+            break;
+        }
+        k_cholp_trail<<<(unsigned)T, 128, kTrailSmem, s>>>(maps[b][0], maps[b][1], A, n, t0, 1,
+                                                           m->err);
+        note_launch(m);
+        if (!launch_ok("k_cholp_trail")) break;
+    }
+    // join: the caller's stream continues after the side stream's last update
+    if (last_b >= 0 && cudaStreamWaitEvent(s, evB[last_b], 0) != cudaSuccess && st == FEM3_OK)
+        st = cuda_error(cudaGetLastError(), "cudaStreamWaitEvent");
+    kc_end(m, KC_FACTOR);
+    ctx_release(cx);
+    return st;
+}
+
+}  // namespace fem3

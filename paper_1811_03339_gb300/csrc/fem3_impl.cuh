@@ -142,6 +142,10 @@ struct Mesh {
     void *solve_G = nullptr;   // triangular-solve chain operators: nblk x 2 x 3 x 64 x 64 doubles
     int32_t *chol_flags = nullptr;  // tile-factorisation flags, then ticket and abort words
     void *dinv = nullptr;      // inverses of the 64 x 64 diagonal blocks of the factor
+    float *chol_w = nullptr;   // tensor-core factorisation: TF32 hi / lo operand rows, panel inverse
+    int64_t chol_w_rows = 0;
+    int chol_tc_opt = 0;       // 0: by size, 1: always, -1: never (tensor-core factorisation)
+    bool chol_tc_used = false; // the last factorisation ran on the tensor cores
     int flag_epoch = 0;        // value that marks "ready" in the current solve
     double *norms = nullptr;   // device scratch for reductions
     double *h_norms = nullptr; // pinned host mirror
@@ -233,6 +237,7 @@ int contract_work(Mesh *m, double *flops);   // algorithmic flops of the element
 int load_vector(Mesh *m, const double *f_d, int nrhs, double *b_d);
 int load_vector_T(Mesh *m, const double *lam_d, double *out_d);
 int factor(Mesh *m);
+int chol_tc(Mesh *m, float *A, int64_t n);   // blocked FP32 Cholesky, tcgen05 trailing updates
 int solve_direct(Mesh *m, const double *b_d, int nrhs, double *u_d);
 int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter, double *u_d,
                   int *iters, double *resid);

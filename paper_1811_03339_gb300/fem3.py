@@ -43,7 +43,7 @@ class Fem3Error(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("bin_scale", C.c_double), ("max_steps", C.c_int32), ("profile", C.c_int32),
-                ("tc_tile", C.c_int32)]
+                ("tc_tile", C.c_int32), ("chol_tc", C.c_int32)]
 
 
 def lib_path() -> str:
@@ -119,9 +119,9 @@ def _ptr(x):
 # functions with the C ABI's names
 # ---------------------------------------------------------------------------------
 def mesh_upload(verts, tets, bin_scale: float = 0.5, max_steps: int = 0, profile: bool = False,
-                stream=None, tc_tile: int = 0):
+                stream=None, tc_tile: int = 0, chol_tc: int = 0):
     lib = load_library()
-    opt = Options(bin_scale, max_steps, 1 if profile else 0, tc_tile)
+    opt = Options(bin_scale, max_steps, 1 if profile else 0, tc_tile, chol_tc)
     h = C.c_void_p()
     _check(lib.fem3_mesh_upload(_ptr(verts), int(verts.shape[0]), _ptr(tets), int(tets.shape[0]),
                                 C.byref(opt), _stream(stream), C.byref(h)))
@@ -247,7 +247,7 @@ class Mesh:
     """A mesh uploaded to the current CUDA device (torch's current stream by default)."""
 
     def __init__(self, verts, tets, bin_scale: float = 0.5, max_steps: int = 0,
-                 profile: bool = False, stream=None, tc_tile: int = 0):
+                 profile: bool = False, stream=None, tc_tile: int = 0, chol_tc: int = 0):
         import torch
         self._torch = torch
         self.stream = stream
@@ -256,7 +256,7 @@ class Mesh:
             tets = np.ascontiguousarray(tets, dtype=np.int32)
         self.n_nodes = int(verts.shape[0])
         self.n_tets = int(tets.shape[0])
-        self.h = mesh_upload(verts, tets, bin_scale, max_steps, profile, stream, tc_tile)
+        self.h = mesh_upload(verts, tets, bin_scale, max_steps, profile, stream, tc_tile, chol_tc)
         self.n_dof, self.n_gp, self.dof_of_node = mesh_info(self.h, self.n_nodes)
         self.precision = None
 
@@ -373,7 +373,7 @@ class Batch:
         tp = (C.c_void_p * n)(*[t.ctypes.data for _, t in self._keep])
         nn = (C.c_int64 * n)(*[v.shape[0] for v, _ in self._keep])
         nt = (C.c_int64 * n)(*[t.shape[0] for _, t in self._keep])
-        opt = Options(bin_scale, max_steps, 0, 0)
+        opt = Options(bin_scale, max_steps, 0, 0, 0)
         h = C.c_void_p()
         _check(lib.fem3_batch_create(n, vp, nn, tp, nt, C.byref(opt), _stream(stream), C.byref(h)))
         self.h = h
