@@ -135,6 +135,21 @@ int fem3_mesh_info(fem3_mesh m, int64_t *n_dof, int64_t *n_gp, int32_t *dof_of_n
 int fem3_assemble(fem3_mesh m, const double alpha[3], const double K[3], int precision,
                   double *A_out, void *stream);
 
+/*
+ * fem3_assemble_integer - the integer-order special case alpha_i = 2 on every axis
+ * (the right-hand columns of the paper's Table 4): -sum_i K_i d^2 u/dx_i^2, whose
+ * Galerkin matrix is the P1 stiffness matrix
+ *     A_jk = sum_i K_i sum_T |T| (d phi_j/dx_i)|_T (d phi_k/dx_i)|_T,
+ * assembled tet by tet from the volume-coordinate gradients (no path walk, no tables).
+ * fem3_assemble with alpha = (2, 2, 2) gives the same matrix through the walk.
+ *   K        host float64[3], each > 0.
+ *   A_out    device float64 [n_dof][n_dof] or NULL.
+ * The matrix is FP64 and stays in the handle: fem3_solve runs the FP64 form, fem3_adjoint /
+ * fem3_vjp take dA/dK_i from the same element formula; fem3_table_rows and
+ * fem3_contract_work report FEM3_E_STATE (no tables).
+ */
+int fem3_assemble_integer(fem3_mesh m, const double K[3], double *A_out, void *stream);
+
 /* Load vector b = M f, M the P1 mass matrix (rows: dofs, columns: all nodes), the
  * weak right-hand side (f, v) of Section 3.
  *   f    host or device float64 column-major [n_nodes][nrhs] (nodal values).
@@ -169,6 +184,21 @@ int fem3_solve(fem3_mesh m, const double *f, int nrhs, double tol, int max_iter,
  */
 int fem3_adjoint(fem3_mesh m, const double *u, const double *u_obs, double tol, int max_iter,
                  double *dJ_dK, double *dJ_df, void *stream);
+
+/*
+ * fem3_vjp - vector-Jacobian product of the solve u = A(K)^{-1} M f (the backward of an
+ * autograd function): for an upstream gradient g = dL/du,
+ *   lambda = A^{-1} g  (same factorisation and refinement as fem3_solve),
+ *   dL/dK_i = -lambda^T (dA/dK_i) u = -s_i sum_g w_g ((L_i lambda)_g (R_i u)_g
+ *                                                  + (R_i lambda)_g (L_i u)_g),
+ *   dL/df   = M^T lambda (nodal).
+ *   u, g    device float64 [n_dof] (one right-hand side; u the solution of the last
+ *           fem3_solve of this handle).
+ *   dK      host float64[3].   df  device float64 [n_nodes] or NULL.
+ * fem3_adjoint is the case g = u - u_obs.  Synchronises `stream`.  Not in the paper.
+ */
+int fem3_vjp(fem3_mesh m, const double *u, const double *g, double tol, int max_iter,
+             double *dK, double *df, void *stream);
 
 /*
  * fem3_paths - export walks for parity checks (Section 2.2).

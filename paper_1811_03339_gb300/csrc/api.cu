@@ -352,6 +352,7 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
     m->precision = precision;
     m->factored = false;
     m->ap_ready = false;
+    m->integer_order = false;
     kc_reset(m);
     FEM3_TRY(walk_tables(m, alpha));
     stage_begin(m, 3);
@@ -374,6 +375,33 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
             }
         }
     }
+    return FEM3_OK;
+}
+
+int fem3_assemble_integer(fem3_mesh h, const double K[3], double *A_out, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !K) return set_error(FEM3_E_ARG, "null argument");
+    for (int a = 0; a < 3; a++)
+        if (!(K[a] > 0.0)) return set_error(FEM3_E_ARG, "K must be positive");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = m->n_dof;
+    for (int a = 0; a < 3; a++) {
+        m->alpha[a] = 2.0;
+        m->K[a] = K[a];
+        m->s[a] = -0.5;
+        m->sK[a] = -0.5 * K[a];
+    }
+    m->precision = FEM3_FP64;
+    m->factored = false;
+    m->ap_ready = false;
+    m->integer_order = true;
+    kc_reset(m);
+    stage_begin(m, 3);
+    FEM3_TRY(assemble_integer(m, K));
+    stage_end(m, 3);
+    if (A_out)
+        FEM3_CUDA(cudaMemcpyAsync(A_out, m->A64, sizeof(double) * n * n, cudaMemcpyDeviceToDevice,
+                                  m->stream));
     return FEM3_OK;
 }
 
@@ -425,7 +453,8 @@ int fem3_solve(fem3_mesh h, const double *f, int nrhs, double tol, int max_iter,
             if (st == FEM3_OK && resid_out) {
                 double worst = 0;
                 for (int r = 0; r < nrhs && st == FEM3_OK; r++) {
-                    st = apply_A64(m, u + r * n, m->vec64[0]);
+                    st = m->integer_order ? apply_dense64(m, u + r * n, m->vec64[0])
+                                          : apply_A64(m, u + r * n, m->vec64[0]);
                     double rel = 0;
                     if (st == FEM3_OK) st = residual_norm(m, b + r * n, m->vec64[0], &rel);
                     worst = std::max(worst, rel);
@@ -445,26 +474,47 @@ int fem3_solve(fem3_mesh h, const double *f, int nrhs, double tol, int max_iter,
     return st != FEM3_OK ? st : st2;
 }
 
+// lambda = A^{-1} g, dK_i = -lambda^T (dA/dK_i) u, df = M^T lambda (g in m->vec64[2])
+static int vjp_from_seed(Mesh *m, const double *u, const double *g, double tol, int max_iter,
+                         double *dK, double *df) {
+    double *lam = m->vec64[3];
+    if (m->precision == FEM3_FP64) {
+        FEM3_TRY(solve_direct(m, g, 1, lam));
+    } else {
+        FEM3_TRY(solve_refined(m, g, 1, tol, max_iter > 0 ? max_iter : 50, lam, nullptr, nullptr));
+    }
+    double forms[3];
+    if (m->integer_order)
+        FEM3_TRY(axis_forms_integer(m, u, lam, forms));
+    else
+        FEM3_TRY(axis_forms(m, u, lam, forms));
+    for (int a = 0; a < 3; a++) dK[a] = -forms[a];
+    if (df) FEM3_TRY(load_vector_T(m, lam, df));
+    return check_errors(m);
+}
+
 int fem3_adjoint(fem3_mesh h, const double *u, const double *u_obs, double tol, int max_iter,
                  double *dJ_dK, double *dJ_df, void *stream) {
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m || !u || !u_obs || !dJ_dK) return set_error(FEM3_E_ARG, "bad argument");
     if (m->precision < 0 || !m->factored) return set_error(FEM3_E_STATE, "adjoint before solve");
     m->stream = reinterpret_cast<cudaStream_t>(stream);
-    const int64_t n = m->n_dof;
-    double *res = m->vec64[2], *lam = m->vec64[3];
-    FEM3_TRY(sub_vec(u, u_obs, res, n, m->stream));
+    double *res = m->vec64[2];
+    FEM3_TRY(sub_vec(u, u_obs, res, m->n_dof, m->stream));
     note_launch(m);
-    if (m->precision == FEM3_FP64) {
-        FEM3_TRY(solve_direct(m, res, 1, lam));
-    } else {
-        FEM3_TRY(solve_refined(m, res, 1, tol, max_iter > 0 ? max_iter : 50, lam, nullptr, nullptr));
-    }
-    double forms[3];
-    FEM3_TRY(axis_forms(m, u, lam, forms));
-    for (int a = 0; a < 3; a++) dJ_dK[a] = -forms[a];
-    if (dJ_df) FEM3_TRY(load_vector_T(m, lam, dJ_df));
-    return check_errors(m);
+    return vjp_from_seed(m, u, res, tol, max_iter, dJ_dK, dJ_df);
+}
+
+int fem3_vjp(fem3_mesh h, const double *u, const double *g, double tol, int max_iter,
+             double *dK, double *df, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !u || !g || !dK) return set_error(FEM3_E_ARG, "bad argument");
+    if (m->precision < 0 || !m->factored) return set_error(FEM3_E_STATE, "vjp before solve");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    double *seed = m->vec64[2];
+    FEM3_CUDA(cudaMemcpyAsync(seed, g, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice,
+                              m->stream));
+    return vjp_from_seed(m, u, seed, tol, max_iter, dK, df);
 }
 
 int fem3_paths(fem3_mesh h, int axis, int dir, const int64_t *gps, int64_t n_lines, int cap,
@@ -485,6 +535,8 @@ int fem3_table_rows(fem3_mesh h, int axis, int dir, const int64_t *gps, int64_t 
     if (!m || !gps || !rows || axis < 0 || axis > 2 || (dir != 1 && dir != -1) || n < 0)
         return set_error(FEM3_E_ARG, "bad argument");
     if (m->precision < 0) return set_error(FEM3_E_STATE, "tables before assemble");
+    if (m->integer_order)
+        return set_error(FEM3_E_STATE, "the integer-order assembly builds no derivative tables");
     m->stream = reinterpret_cast<cudaStream_t>(stream);
     return table_rows(m, axis, dir, gps, n, rows);
 }
@@ -521,7 +573,8 @@ int fem3_tc_tile(fem3_mesh h, int32_t *tile_n, int32_t *tuned) {
 int fem3_contract_work(fem3_mesh h, double *flops, void *stream) {
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m || !flops) return set_error(FEM3_E_ARG, "bad argument");
-    if (m->precision < 0) return set_error(FEM3_E_STATE, "contraction work before assemble");
+    if (m->precision < 0 || m->integer_order)
+        return set_error(FEM3_E_STATE, "contraction work needs the tables of a fractional assemble");
     m->stream = reinterpret_cast<cudaStream_t>(stream);
     return contract_work(m, flops);
 }

@@ -133,6 +133,7 @@ struct Mesh {
     int tc_tile_used = 0;      // width of the last tensor-core contraction
     bool tc_tuned = false;     // the last contraction ran the tuner
     bool ap_ready = false;     // ap_R holds W R of the current tables
+    bool integer_order = false;   // the matrix came from fem3_assemble_integer (no tables)
 
     // workspaces
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -237,7 +238,10 @@ int contract_work(Mesh *m, double *flops);   // algorithmic flops of the element
 int load_vector(Mesh *m, const double *f_d, int nrhs, double *b_d);
 int load_vector_T(Mesh *m, const double *lam_d, double *out_d);
 int factor(Mesh *m);
-int chol_tc(Mesh *m, float *A, int64_t n);   // blocked FP32 Cholesky, tcgen05 trailing updates
+int chol_tc(Mesh *m, float *A, int64_t n);
+int assemble_integer(Mesh *m, const double K[3]);       // P1 stiffness, alpha_i = 2
+int axis_forms_integer(Mesh *m, const double *u, const double *lam, double out[3]);
+int apply_dense64(Mesh *m, const double *x, double *y); // y = A64 x   // blocked FP32 Cholesky, tcgen05 trailing updates
 int solve_direct(Mesh *m, const double *b_d, int nrhs, double *u_d);
 int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter, double *u_d,
                   int *iters, double *resid);

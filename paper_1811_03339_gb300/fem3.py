@@ -23,8 +23,9 @@ FEM3_E_NO_CONVERGE, FEM3_E_CUDA, FEM3_E_OOM, FEM3_E_STATE, FEM3_E_TEMPLATE = -5,
 PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2, "bf16x3": 3}
 
 # every entry point declared in include/fem3.h
-SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_load", "fem3_solve",
-           "fem3_adjoint", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
+SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_assemble_integer",
+           "fem3_load", "fem3_solve",
+           "fem3_adjoint", "fem3_vjp", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
            "fem3_counters", "fem3_bin_stats", "fem3_kernel_ms", "fem3_contract_work",
            "fem3_tc_tile",
            "fem3_last_error",
@@ -65,9 +66,11 @@ def load_library(build_if_missing: bool = True):
         "fem3_mesh_upload": [p, i64, p, i64, C.POINTER(Options), p, C.POINTER(p)],
         "fem3_mesh_info": [p, C.POINTER(i64), C.POINTER(i64), p],
         "fem3_assemble": [p, p, p, ci, p, p],
+        "fem3_assemble_integer": [p, p, p, p],
         "fem3_load": [p, p, ci, p, p],
         "fem3_solve": [p, p, ci, dbl, ci, p, C.POINTER(ci), C.POINTER(dbl), p],
         "fem3_adjoint": [p, p, p, dbl, ci, p, p, p],
+        "fem3_vjp": [p, p, p, dbl, ci, p, p, p],
         "fem3_paths": [p, ci, ci, p, i64, ci, p, p, p, p, p],
         "fem3_table_rows": [p, ci, ci, p, i64, p, p],
         "fem3_sync": [p, p],
@@ -143,6 +146,12 @@ def assemble(h, alpha, K, precision="fp64", A_out=None, stream=None):
                               _ptr(A_out) if A_out is not None else None, _stream(stream)))
 
 
+def assemble_integer(h, K, A_out=None, stream=None):
+    k = np.ascontiguousarray(K, dtype=np.float64)
+    _check(_lib.fem3_assemble_integer(h, _ptr(k), _ptr(A_out) if A_out is not None else None,
+                                      _stream(stream)))
+
+
 def load(h, f, nrhs, b, stream=None):
     _check(_lib.fem3_load(h, _ptr(f), int(nrhs), _ptr(b), _stream(stream)))
 
@@ -158,6 +167,13 @@ def adjoint(h, u, u_obs, dJ_df=None, tol=1e-12, max_iter=50, stream=None):
     dK = np.zeros(3)
     _check(_lib.fem3_adjoint(h, _ptr(u), _ptr(u_obs), float(tol), int(max_iter), _ptr(dK),
                              _ptr(dJ_df) if dJ_df is not None else None, _stream(stream)))
+    return dK
+
+
+def vjp(h, u, g, df=None, tol=1e-12, max_iter=50, stream=None):
+    dK = np.zeros(3)
+    _check(_lib.fem3_vjp(h, _ptr(u), _ptr(g), float(tol), int(max_iter), _ptr(dK),
+                         _ptr(df) if df is not None else None, _stream(stream)))
     return dK
 
 
@@ -270,6 +286,13 @@ class Mesh:
         self.precision = precision
         return A
 
+    def assemble_integer(self, K, return_matrix=False):
+        """alpha_i = 2 on every axis: the P1 stiffness matrix, assembled tet by tet"""
+        A = self._dev((self.n_dof, self.n_dof)) if return_matrix else None
+        assemble_integer(self.h, K, A, self.stream)
+        self.precision = "fp64"
+        return A
+
     def load(self, f):
         f = self._as_nodal(f)
         nrhs = 1 if f.dim() == 1 else f.shape[0]
@@ -297,6 +320,13 @@ class Mesh:
         dJdf = self._dev((self.n_nodes,))
         dK = adjoint(self.h, u.contiguous(), u_obs.contiguous(), dJdf, tol, max_iter, self.stream)
         return dK, dJdf
+
+    def vjp(self, u, g, tol=1e-12, max_iter=50):
+        """(dL/dK [3] host, dL/df [n_nodes] device) for an upstream gradient g = dL/du of the
+        last solve's solution u (one right-hand side)."""
+        df = self._dev((self.n_nodes,))
+        dK = vjp(self.h, u.contiguous(), g.contiguous(), df, tol, max_iter, self.stream)
+        return dK, df
 
     def paths(self, axis, direction, gps, cap=None):
         t = self._torch
@@ -418,3 +448,47 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------------
+def _frac_solve_function():
+    import torch
+
+    class FracSolve(torch.autograd.Function):
+        """u = A(K)^{-1} M f on one mesh, differentiable in K (3 axis coefficients) and in
+        the nodal source f (one right-hand side).  Forward: fem3_assemble + fem3_solve;
+        backward: fem3_vjp (one adjoint solve with the same factorisation, the axis forms
+        of the tables and M^T lambda)."""
+
+        @staticmethod
+        def forward(ctx, K, f, mesh, alpha, precision, tol):
+            mesh.assemble(alpha, [float(x) for x in K.detach().cpu()], precision)
+            u = mesh.solve(f.detach(), tol=tol)
+            ctx.mesh, ctx.tol = mesh, tol
+            ctx.k_device, ctx.k_dtype = K.device, K.dtype
+            ctx.save_for_backward(u)
+            return u
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            (u,) = ctx.saved_tensors
+            dK, df = ctx.mesh.vjp(u, grad_u.to(u.dtype).contiguous(), tol=ctx.tol)
+            gK = torch.as_tensor(dK, dtype=ctx.k_dtype, device=ctx.k_device)
+            return gK, df, None, None, None, None
+
+    return FracSolve
+
+
+_FRAC_SOLVE = None
+
+
+def frac_solve(mesh, alpha, K, f, precision="fp64", tol=1e-12):
+    """Differentiable solve: K a float64 tensor [3] (any device), f a float64 CUDA tensor
+    [n_nodes]; returns u [n_dof] on the device.  Gradients flow to K and f through the
+    library's adjoint (fem3_vjp)."""
+    global _FRAC_SOLVE
+    if _FRAC_SOLVE is None:
+        _FRAC_SOLVE = _frac_solve_function()
+    return _FRAC_SOLVE.apply(K, f, mesh, tuple(float(a) for a in alpha), precision, tol)

@@ -528,3 +528,83 @@ def test_blocked_tensor_core_factorisation(name, n_cells, precision):
         sweeps[mode] = m.iters
         m.free()
     assert sweeps[1] <= sweeps[-1] + 1, sweeps
+
+
+def test_autograd_gradient_at_full_size():
+    """The adjoint configuration: the 16^3 jittered cube, J = 0.5 ||u(K, f) - u_obs||^2 with
+    u_obs = u(K_true) + 1% seeded noise, K_true = (1, 2, 0.5), f the manufactured source.
+    The gradient from torch.autograd through fem3.frac_solve (backward = fem3_vjp) against
+    central differences (h = 1e-6 in each K_i; a direction in f, where J is quadratic), each
+    J from the GPU's own FP64 solve, and against the oracle's adjoint gradient (itself pinned
+    to central differences); the TF32x3 form with refinement against the oracle too."""
+    mesh, o, alpha, K = _case("cube16_jitter")
+    f_np = inputs.nodal_source(mesh, alpha, K)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    m.assemble(alpha, K, "fp64")
+    u_true = m.solve(f_np).cpu().numpy()
+    u_obs = inputs.noisy_observation(u_true, 0.01, 3)
+    u_obs_t = torch.from_numpy(u_obs).cuda()
+
+    def grads(precision):
+        Kt = torch.tensor(K, dtype=torch.float64, requires_grad=True)
+        ft = torch.from_numpy(f_np).cuda().requires_grad_(True)
+        u = fem3.frac_solve(m, alpha, Kt, ft, precision, tol=1e-13)
+        J = 0.5 * ((u - u_obs_t) ** 2).sum()
+        J.backward()
+        return float(J), Kt.grad.numpy().copy(), ft.grad.cpu().numpy()
+
+    def J_of(Kv, fv):
+        m.assemble(alpha, Kv, "fp64")
+        uu = m.solve(fv)
+        return 0.5 * float(((uu - u_obs_t) ** 2).sum())
+
+    J0, gK, gf = grads("fp64")
+    assert J0 > 0 and np.all(np.isfinite(gK)) and np.all(np.isfinite(gf))
+    h = 1e-6
+    for i in range(3):
+        Kp, Km = list(K), list(K)
+        Kp[i] += h
+        Km[i] -= h
+        fd = (J_of(Kp, f_np) - J_of(Km, f_np)) / (2 * h)
+        assert abs(fd - gK[i]) <= 1e-6 * np.abs(gK).max(), (i, fd, gK[i])
+    v = np.random.default_rng(9).standard_normal(mesh.n_nodes)
+    hf = 1e-3 * np.abs(f_np).max()
+    fdv = (J_of(K, f_np + hf * v) - J_of(K, f_np - hf * v)) / (2 * hf)
+    assert abs(fdv - float(gf @ v)) <= 1e-7 * abs(float(gf @ v)) + 1e-12 * np.abs(gf).sum()
+    Jo, dK_ref, df_ref, _ = o.adjoint(alpha, K, f_np, u_obs)
+    assert abs(J0 - Jo) <= 1e-10 * Jo
+    assert np.abs(gK - dK_ref).max() <= 1e-8 * np.abs(dK_ref).max()
+    assert _rel(gf, df_ref) <= 1e-8
+    _, gK32, gf32 = grads("tf32x3")
+    assert np.abs(gK32 - dK_ref).max() <= 1e-8 * np.abs(dK_ref).max()
+    assert _rel(gf32, df_ref) <= 1e-8
+    m.free()
+
+
+def test_integer_order_fast_path():
+    """fem3_assemble_integer (alpha_i = 2, the element-by-element P1 stiffness, no walk)
+    equals the oracle's alpha = 2 matrix (pinned to the textbook P1 Laplacian) and the walk
+    path's alpha = 2 matrix; its solve and its gradient (element formula for dA/dK_i) match
+    the oracle's; it has no tables to export."""
+    mesh, o, _, K = _case("cube7_jitter")
+    a2 = (2.0, 2.0, 2.0)
+    A_ref = o.assemble(a2, K)
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    Aw = m.assemble(a2, K, "fp64", return_matrix=True).cpu().numpy()
+    A = m.assemble_integer(K, return_matrix=True).cpu().numpy()
+    assert _rel(A, A_ref) <= 1e-12
+    assert _rel(A, Aw) <= 1e-12
+    f = inputs.nodal_source(mesh, (1.5, 1.5, 1.5), K) + 0.3
+    u = m.solve(f)
+    u_ref = oracle.solve(A_ref, o.load(f))
+    assert np.linalg.norm(u.cpu().numpy() - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
+    assert m.resid <= 1e-12
+    u_obs = inputs.noisy_observation(u_ref, 0.01, 5)
+    dK, dJdf = m.adjoint(u, torch.from_numpy(u_obs).cuda())
+    _, dK_ref, df_ref, _ = o.adjoint(a2, K, f, u_obs)
+    assert np.abs(dK - dK_ref).max() <= 1e-8 * np.abs(dK_ref).max()
+    assert _rel(dJdf.cpu().numpy(), df_ref) <= 1e-8
+    with pytest.raises(fem3.Fem3Error) as e:
+        m.table_rows(0, -1, [0])
+    assert e.value.code == fem3.FEM3_E_STATE
+    m.free()
