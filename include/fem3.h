@@ -136,6 +136,29 @@ int fem3_assemble(fem3_mesh m, const double alpha[3], const double K[3], int pre
                   double *A_out, void *stream);
 
 /*
+ * fem3_assemble_form - one axis term of the general variational form of Section 2.1
+ * (eq. "equ:varsss" and the element quadrature formula after it) with a variable
+ * coefficient and unequal orders:
+ *     K[k][l] = sum_g w_g c(x_g) (D^alpha psi_l)(x_g) (D^^beta psi_k)(x_g)
+ * over the interior basis functions, D^alpha the left Riemann-Liouville operator along the
+ * axis and D^^beta the right one when trial_left (else the other way round), orders in
+ * [0, 1] (order 0: the function itself; order 1: the first derivative, with the one-sided
+ * sign: D_L^1 = d/dx, D_R^1 = -d/dx).  The tables of the axis are walked with the two
+ * orders (Section 2.2 paths, closed-form derivatives per segment), c multiplies the Gauss
+ * weights, and the product runs on the bins of the axis (CUDA cores for FP64 and FP32, the
+ * tensor cores for TF32X3 and BF16X3), without the symmetric fold of fem3_assemble.
+ *   axis      0, 1 or 2.
+ *   c         host or device float64 [n_gp] in Gauss-point order (4 t + q for the q-th
+ *             point of tet t), or NULL for c = 1.
+ *   K_out     device float64 [n_dof][n_dof] (row: test function k, column: trial l).
+ * The call rewrites the axis's tables: the handle then holds no operator for fem3_solve
+ * (FEM3_E_STATE until the next fem3_assemble).  Errors: FEM3_E_ARG, FEM3_E_OOM,
+ * FEM3_E_CUDA; walk errors at the next synchronising call.
+ */
+int fem3_assemble_form(fem3_mesh m, int axis, double alpha, double beta, int trial_left,
+                       const double *c, int precision, double *K_out, void *stream);
+
+/*
  * fem3_assemble_integer - the integer-order special case alpha_i = 2 on every axis
  * (the right-hand columns of the paper's Table 4): -sum_i K_i d^2 u/dx_i^2, whose
  * Galerkin matrix is the P1 stiffness matrix

@@ -405,6 +405,57 @@ int fem3_assemble_integer(fem3_mesh h, const double K[3], double *A_out, void *s
     return FEM3_OK;
 }
 
+int fem3_assemble_form(fem3_mesh h, int axis, double alpha, double beta, int trial_left,
+                       const double *c, int precision, double *K_out, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !K_out) return set_error(FEM3_E_ARG, "null argument");
+    if (axis < 0 || axis > 2) return set_error(FEM3_E_ARG, "axis must be 0, 1 or 2");
+    if (!(alpha >= 0.0 && alpha <= 1.0) || !(beta >= 0.0 && beta <= 1.0))
+        return set_error(FEM3_E_ARG, "the orders of the general form lie in [0, 1]");
+    if (precision != FEM3_FP64 && precision != FEM3_TF32X3 && precision != FEM3_FP32 &&
+        precision != FEM3_BF16X3)
+        return set_error(FEM3_E_ARG, "unknown precision");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = m->n_dof;
+    // the tables of this axis are rewritten: no assembled operator remains for fem3_solve
+    m->precision = -1;
+    m->factored = false;
+    m->ap_ready = false;
+    m->integer_order = false;
+    kc_reset(m);
+    if (precision == FEM3_FP64 && !m->A64) FEM3_TRY(dev_alloc_t(m, &m->A64, n * n));
+    if (precision != FEM3_FP64 && !m->A32) FEM3_TRY(dev_alloc_t(m, &m->A32, n * n));
+    if (!m->form_wc) FEM3_TRY(dev_alloc_t(m, &m->form_wc, 2 * m->n_gp));
+    const void *cd = nullptr;
+    void *owned = nullptr;
+    if (c) FEM3_TRY(to_device(m, c, sizeof(double) * m->n_gp, &cd, &owned));
+    // trial_left: D^a (trial) is the left operator and D^^b (test) the right one
+    const double order_left = trial_left ? alpha : beta, order_right = trial_left ? beta : alpha;
+    const bool test_right = trial_left != 0;
+    int st = walk_tables_form(m, axis, order_left, order_right);
+    if (st == FEM3_OK) st = weight_coef(m, (const double *)cd, m->form_wc);
+    stage_begin(m, 3);
+    if (st == FEM3_OK) {
+        if (precision == FEM3_TF32X3 || precision == FEM3_BF16X3)
+            st = contract_tc_form(m, axis, test_right, m->form_wc, precision == FEM3_BF16X3);
+        else
+            st = contract_form(m, axis, test_right, m->form_wc, precision);
+    }
+    stage_end(m, 3);
+    if (st == FEM3_OK) {
+        if (precision == FEM3_FP64) {
+            cudaError_t e = cudaMemcpyAsync(K_out, m->A64, sizeof(double) * n * n,
+                                            cudaMemcpyDeviceToDevice, m->stream);
+            if (e != cudaSuccess) st = cuda_error(e, "cudaMemcpyAsync");
+        } else {
+            st = f32_to_f64(m->A32, K_out, n * n, m->stream);
+            note_launch(m);
+        }
+    }
+    if (owned) cudaFreeAsync(owned, m->stream);
+    return st;
+}
+
 int fem3_load(fem3_mesh h, const double *f, int nrhs, double *b, void *stream) {
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m || !f || !b || nrhs < 1) return set_error(FEM3_E_ARG, "bad argument");
@@ -453,7 +504,7 @@ int fem3_solve(fem3_mesh h, const double *f, int nrhs, double tol, int max_iter,
             if (st == FEM3_OK && resid_out) {
                 double worst = 0;
                 for (int r = 0; r < nrhs && st == FEM3_OK; r++) {
-                    st = m->integer_order ? apply_dense64(m, u + r * n, m->vec64[0])
+                    st = m->integer_order ? apply_integer(m, u + r * n, m->vec64[0])
                                           : apply_A64(m, u + r * n, m->vec64[0]);
                     double rel = 0;
                     if (st == FEM3_OK) st = residual_norm(m, b + r * n, m->vec64[0], &rel);

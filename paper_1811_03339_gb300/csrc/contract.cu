@@ -7,6 +7,9 @@
 //   out(c1, c2) = sum_r w_r (L[c1][r] R[c2][r] + R[c1][r] L[c2][r])   (symmetric)
 // and adds s K out(c1, c2) to A[dof c1][dof c2] (and to the mirror element when t1 < t2).
 // TA is the arithmetic type (double for the FP64 form, float for the FP32 form).
+#include <algorithm>
+#include <vector>
+
 #include "fem3_impl.cuh"
 
 namespace fem3 {
@@ -129,7 +132,142 @@ __global__ void __launch_bounds__(128) k_contract_work(
     if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(flops, acc);
 }
 
+// One product of the general form (c D^a u, D^^b v), all 64 x 64 tile pairs of each bin:
+// out(c1, c2) = sum_r wc_r T[c1][r] S[c2][r] (T the test side's table, S the trial side's,
+// wc the Gauss weight times the coefficient) added to K[dof c1][dof c2].
+template <class TA>
+__global__ void __launch_bounds__(256) k_contract_form(
+    const float2 *__restrict__ tabT, const float2 *__restrict__ tabS,
+    const int4 *__restrict__ work, const int32_t *__restrict__ gp_off,
+    const int32_t *__restrict__ gp_idx, const int32_t *__restrict__ dof_off,
+    const int32_t *__restrict__ dof_idx, const int64_t *__restrict__ tab_off,
+    const int32_t *__restrict__ tab_ld, const double *__restrict__ wc, TA *K, int64_t n_dof) {
+    __shared__ TA sT[kKC][kTile], sS[kKC][kTile];
+    __shared__ TA sw[kKC];
+    const int4 wk = work[blockIdx.x];
+    const int bin = wk.x, t1 = wk.y, t2 = wk.z;
+    const int D = dof_off[bin + 1] - dof_off[bin];
+    const int G = gp_off[bin + 1] - gp_off[bin];
+    const int ld = tab_ld[bin];
+    const float2 *T = tabT + tab_off[bin], *S = tabS + tab_off[bin];
+    const int32_t *slots = gp_idx + gp_off[bin];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int a0 = t1 * kTile, b0 = t2 * kTile;
+    TA acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = TA(0);
+    for (int r0 = 0; r0 < G; r0 += kKC) {
+        if (threadIdx.x < kKC) {
+            const int r = r0 + threadIdx.x;
+            sw[threadIdx.x] = r < G ? TA(wc[slots[r]]) : TA(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int e = threadIdx.x + 256 * q;
+            const int c = e >> 4, k = e & 15, r = r0 + k;
+            const bool okr = r < G;
+            const int ca = a0 + c, cb = b0 + c;
+            sT[k][c] = (okr && ca < D) ? tab_value<TA>(T + (int64_t)ca * ld + r) : TA(0);
+            sS[k][c] = (okr && cb < D) ? tab_value<TA>(S + (int64_t)cb * ld + r) : TA(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kKC; k++) {
+            TA ta[4], sb[4];
+            const TA w = sw[k];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                ta[i] = sT[k][ty * 4 + i];
+                sb[i] = sS[k][tx * 4 + i] * w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(ta[i], sb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    const int32_t *dofs = dof_idx + dof_off[bin];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int c1 = a0 + ty * 4 + i;
+        if (c1 >= D) continue;
+        const int64_t j1 = dofs[c1];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int c2 = b0 + tx * 4 + j;
+            if (c2 >= D) continue;
+            atomicAdd(&K[j1 * n_dof + dofs[c2]], acc[i][j]);
+        }
+    }
+}
+
+// wc[g] = w[g] c[g] (c NULL: w)
+__global__ void k_weight_coef(const double *__restrict__ w, const double *__restrict__ c,
+                              int64_t n, double *wc) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g < n) wc[g] = c ? w[g] * c[g] : w[g];
+}
+
 }  // namespace
+
+int weight_coef(Mesh *m, const double *c_gp, double *wc_gp) {
+    k_weight_coef<<<(unsigned)((m->n_gp + 255) / 256), 256, 0, m->stream>>>(m->gw, c_gp, m->n_gp,
+                                                                             wc_gp);
+    note_launch(m);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+// K = T^T diag(wc) S over one axis's bins on CUDA cores (FP64 into A64 or FP32 into A32),
+// T the test side's table (R if test_right), S the trial side's
+int contract_form(Mesh *m, int axis, bool test_right, const double *wc_gp, int precision) {
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n_dof;
+    AxisBins &B = m->bins[axis];
+    if (!B.form_work) {
+        std::vector<int4> work;
+        for (int b = 0; b < B.n_bins; b++) {
+            const int D = B.h_dof_off[b + 1] - B.h_dof_off[b];
+            const int G = B.h_gp_off[b + 1] - B.h_gp_off[b];
+            if (D == 0 || G == 0) continue;
+            const int nt = (D + kTile - 1) / kTile;
+            for (int t1 = 0; t1 < nt; t1++)
+                for (int t2 = 0; t2 < nt; t2++) work.push_back(make_int4(b, t1, t2, 0));
+        }
+        B.n_form_work = (int)work.size();
+        FEM3_TRY(dev_alloc_t(m, &B.form_work, std::max(1, B.n_form_work)));
+        if (B.n_form_work)
+            FEM3_CUDA(cudaMemcpyAsync(B.form_work, work.data(), sizeof(int4) * work.size(),
+                                      cudaMemcpyHostToDevice, s));
+        // the pageable source must outlive the copy
+        FEM3_CUDA(cudaStreamSynchronize(s));
+    }
+    const float2 *T = test_right ? m->tabR[axis] : m->tabL[axis];
+    const float2 *S = test_right ? m->tabL[axis] : m->tabR[axis];
+    if (precision == FEM3_FP64) {
+        FEM3_CUDA(cudaMemsetAsync(m->A64, 0, sizeof(double) * n * n, s));
+    } else {
+        FEM3_CUDA(cudaMemsetAsync(m->A32, 0, sizeof(float) * n * n, s));
+    }
+    if (B.n_form_work) {
+        kc_begin(m, KC_CONTRACT);
+        if (precision == FEM3_FP64)
+            k_contract_form<double><<<B.n_form_work, 256, 0, s>>>(
+                T, S, B.form_work, B.gp_off, B.gp_idx, B.dof_off, B.dof_idx, B.tab_off, B.tab_ld,
+                wc_gp, m->A64, n);
+        else
+            k_contract_form<float><<<B.n_form_work, 256, 0, s>>>(
+                T, S, B.form_work, B.gp_off, B.gp_idx, B.dof_off, B.dof_idx, B.tab_off, B.tab_ld,
+                wc_gp, m->A32, n);
+        kc_end(m, KC_CONTRACT);
+        note_launch(m);
+    }
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
 
 int contract_work(Mesh *m, double *flops_out) {
     cudaStream_t s = m->stream;

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(128, TcCfg<BN>::kMinBlocks) k_contract_tc(
     const __grid_constant__ CUtensorMap mRhi, const __grid_constant__ CUtensorMap mRlo,
     const int4 *__restrict__ work, const int32_t *__restrict__ dof_off,
     const int32_t *__restrict__ dof_idx, const int32_t *__restrict__ gp_off, float sK, float *A,
-    int64_t n_dof, int32_t *err) {
+    int64_t n_dof, int full, int32_t *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned tile area (swizzle atoms), barriers after it
     uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -226,6 +226,22 @@ __global__ void __launch_bounds__(128, TcCfg<BN>::kMinBlocks) k_contract_tc(
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!ok) {
         if (threadIdx.x == 0 && nk > 0) atomicAdd(&err[ERR_TC], 1);
+    } else if (full) {
+        // general form: X itself (rows: the A operand's dofs, columns: the B operand's), no
+        // symmetric fold, straight from the tcgen05.ld registers
+        const int c1 = mt * kBM + warp * 32 + lane;
+        const bool row_ok = c1 < D;
+        const int64_t j1 = row_ok ? dof_idx[row0 + c1] : 0;
+        for (int cb = 0; cb < N; cb += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, v);
+            if (!row_ok) continue;
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                if (cb + q >= nvalid) break;
+                atomicAdd(&A[j1 * n_dof + dof_idx[row0 + nt * BN + cb + q]], sK * v[q]);
+            }
+        }
     } else if (D <= kBM) {
         // the stage is free (every load was consumed by an MMA that has completed):
         // Xs[r][c] at r * 128 + (c ^ (r & 31)), 64 KB
@@ -368,19 +384,21 @@ static uint64_t tile_class(const Mesh *m, bool bf16) {
 }
 
 // the GEMMs of the three axes with tile slot w (A32 accumulates: the caller zeroes it)
-static int tc_gemms(Mesh *m, bool bf16, int w, const CUtensorMap (*maps)[4]) {
+static int tc_gemms(Mesh *m, bool bf16, int w, const CUtensorMap (*maps)[4], int only_axis = -1,
+                    int full = 0) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
     for (int axis = 0; axis < 3; axis++) {
+        if (only_axis >= 0 && axis != only_axis) continue;
         AxisBins &B = m->bins[axis];
         const int nw = B.tc_n_work[w];
         if (!nw) continue;
         const CUtensorMap *mp = maps[axis];
-        const float sk = (float)m->sK[axis];
+        const float sk = full ? 1.0f : (float)m->sK[axis];
 #define FEM3_TC_LAUNCH(BF, BN)                                                                  \
     k_contract_tc<BF, BN><<<nw, 128, TcCfg<BN>::kSmemBytes, s>>>(                              \
         mp[0], mp[1], mp[2], mp[3], B.tc_work[w], B.dof_off, B.dof_idx, B.gp_off, sk, m->A32, n, \
-        m->err)
+        full, m->err)
         if (kTileWidths[w] == 256) {
             if (bf16) FEM3_TC_LAUNCH(true, 256); else FEM3_TC_LAUNCH(false, 256);
         } else {
@@ -476,6 +494,63 @@ int contract_tc(Mesh *m, bool bf16) {
     kc_end(m, KC_CONTRACT);
     m->contract_flops = flops;
     m->ap_ready = true;
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+namespace {
+// ws[slot] = wc[gp_idx[slot]]: the form's weights in one axis's slot order
+__global__ void k_gather_slots(const double *__restrict__ wc, const int32_t *__restrict__ gp_idx,
+                               int64_t n, double *ws) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) ws[i] = wc[gp_idx[i]];
+}
+}  // namespace
+
+// General form (c D^a u, D^^b v) of one axis on the tensor cores: K = T^T diag(wc) S (T the
+// test side's table, S the trial side's) with the split products of the precision, into
+// A32 (cleared first); every tile of every bin, no symmetric fold.  wc_gp holds 2 n_gp
+// values: the weights per Gauss point, then room for them in slot order.
+int contract_tc_form(Mesh *m, int axis, bool test_right, double *wc_gp, bool bf16) {
+    cudaStream_t s = m->stream;
+    const int64_t n = m->n_dof;
+    FEM3_TRY(tc_prepare(m));
+    AxisBins &B = m->bins[axis];
+    FEM3_CUDA(cudaMemsetAsync(m->A32, 0, sizeof(float) * n * n, s));
+    if (!B.tc_n_work[0]) return FEM3_OK;
+    FEM3_TRY(ap_alloc(m, axis));
+    double *ws = wc_gp + m->n_gp;
+    k_gather_slots<<<(unsigned)((m->n_gp + 255) / 256), 256, 0, s>>>(wc_gp, B.gp_idx, m->n_gp, ws);
+    note_launch(m);
+    const int kbk = bf16 ? 64 : 32;
+    const int Kp = std::max(kbk, (B.tc_maxG + kbk - 1) / kbk * kbk);
+    const unsigned grid = (unsigned)((B.n_tmpl + 7) / 8);
+    const float2 *T = test_right ? m->tabR[axis] : m->tabL[axis];
+    const float2 *S = test_right ? m->tabL[axis] : m->tabR[axis];
+    kc_begin(m, KC_SPLIT);
+    if (bf16) {
+        __nv_bfloat16 *op[4];
+        for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<__nv_bfloat16 *>(B.tc_op[q]);
+        k_split_ops<__nv_bfloat16><<<grid, 256, 0, s>>>(T, S, B.row_bin, B.dof_off, B.gp_off, ws,
+                                                         B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0],
+                                                         op[1], op[2], op[3], B.ap_R);
+    } else {
+        float *op[4];
+        for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<float *>(B.tc_op[q]);
+        k_split_ops<float><<<grid, 256, 0, s>>>(T, S, B.row_bin, B.dof_off, B.gp_off, ws,
+                                                B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1],
+                                                op[2], op[3], B.ap_R);
+    }
+    kc_end(m, KC_SPLIT);
+    note_launch(m);
+    CUtensorMap maps[3][4];
+    for (int q = 0; q < 4; q++) FEM3_TRY(make_map(&maps[axis][q], B.tc_op[q], B.n_tmpl, Kp, bf16));
+    const int w = m->tc_tile_opt == 256 ? 0 : 1;   // 128 columns unless 256 is forced
+    m->tc_tile_used = kTileWidths[w];
+    kc_begin(m, KC_CONTRACT);
+    FEM3_TRY(tc_gemms(m, bf16, w, maps, axis, 1));
+    kc_end(m, KC_CONTRACT);
+    m->ap_ready = false;   // ap_R now holds the form's operand
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }

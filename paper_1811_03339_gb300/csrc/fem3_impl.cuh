@@ -72,6 +72,8 @@ struct AxisBins {
     int max_dof = 0, max_gp = 0;
     int4 *work = nullptr;        // contraction work items (bin, t1, t2, 0)
     int n_work = 0;
+    int4 *form_work = nullptr;   // general-form work items: every tile pair (bin, t1, t2, 0)
+    int n_form_work = 0;
     // tensor-core contraction operands: TF32 or BF16 hi/lo of L and of W R, [n_tmpl][Kp]
     // (Kp = tc_maxG rounded to one 128-byte row of the operand type)
     void *tc_op[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -134,6 +136,7 @@ struct Mesh {
     bool tc_tuned = false;     // the last contraction ran the tuner
     bool ap_ready = false;     // ap_R holds W R of the current tables
     bool integer_order = false;   // the matrix came from fem3_assemble_integer (no tables)
+    double *form_wc = nullptr;    // general form: w c per Gauss point, and per slot of one axis
 
     // workspaces
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -235,13 +238,18 @@ int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double
 int contract(Mesh *m, int precision);
 int contract_tc(Mesh *m, bool bf16);   // TF32 x 3 (bf16 = false) or BF16 x 3
 int contract_work(Mesh *m, double *flops);   // algorithmic flops of the element sum (synchronises)
+// general form (c D^a u, D^^b v) of one axis
+int walk_tables_form(Mesh *m, int axis, double order_left, double order_right);
+int weight_coef(Mesh *m, const double *c_gp, double *wc_gp);   // wc = w c per Gauss point
+int contract_form(Mesh *m, int axis, bool test_right, const double *wc_gp, int precision);
+int contract_tc_form(Mesh *m, int axis, bool test_right, double *wc_gp, bool bf16);
 int load_vector(Mesh *m, const double *f_d, int nrhs, double *b_d);
 int load_vector_T(Mesh *m, const double *lam_d, double *out_d);
 int factor(Mesh *m);
 int chol_tc(Mesh *m, float *A, int64_t n);
 int assemble_integer(Mesh *m, const double K[3]);       // P1 stiffness, alpha_i = 2
 int axis_forms_integer(Mesh *m, const double *u, const double *lam, double out[3]);
-int apply_dense64(Mesh *m, const double *x, double *y); // y = A64 x   // blocked FP32 Cholesky, tcgen05 trailing updates
+int apply_integer(Mesh *m, const double *x, double *y); // y = A x, element by element   // blocked FP32 Cholesky, tcgen05 trailing updates
 int solve_direct(Mesh *m, const double *b_d, int nrhs, double *u_d);
 int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter, double *u_d,
                   int *iters, double *resid);

@@ -67,16 +67,29 @@ __global__ void k_p1_axis_forms(const double *__restrict__ M, const double *__re
     }
 }
 
-// y = A x for the dense FP64 matrix (one warp per row)
-__global__ void k_gemv64(const double *__restrict__ A, const double *__restrict__ x, int64_t n,
-                         double *y) {
-    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row >= n) return;
-    double acc = 0.0;
-    for (int64_t c = lane; c < n; c += 32) acc = fma(A[row * n + c], x[c], acc);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) y[row] = acc;
+// y += A x tet by tet (the element matrices of k_p1_stiffness applied to x; the assembled
+// matrix itself is overwritten by its factorisation)
+__global__ void k_p1_apply(const double *__restrict__ M, const double *__restrict__ vol,
+                           const int32_t *__restrict__ tets, const int32_t *__restrict__ dof,
+                           int64_t n_tets, double K0, double K1, double K2,
+                           const double *__restrict__ x, double *y) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_tets) return;
+    const double *Mt = M + 16 * t;
+    int32_t j[4];
+    double dx[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; a++) {
+        j[a] = dof[tets[4 * t + a]];
+        if (j[a] < 0) continue;
+        for (int i = 0; i < 3; i++) dx[i] += Mt[4 * a + 1 + i] * x[j[a]];
+    }
+    const double v = vol[t];
+    for (int a = 0; a < 4; a++) {
+        if (j[a] < 0) continue;
+        const double e = v * (K0 * Mt[4 * a + 1] * dx[0] + K1 * Mt[4 * a + 2] * dx[1] +
+                              K2 * Mt[4 * a + 3] * dx[2]);
+        atomicAdd(&y[j[a]], e);
+    }
 }
 
 inline unsigned grid_tets(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -99,10 +112,11 @@ int assemble_integer(Mesh *m, const double K[3]) {
     return FEM3_OK;
 }
 
-int apply_dense64(Mesh *m, const double *x, double *y) {
-    const int64_t n = m->n_dof;
-    if (n > 0) {
-        k_gemv64<<<(unsigned)((n + 7) / 8), 256, 0, m->stream>>>(m->A64, x, n, y);
+int apply_integer(Mesh *m, const double *x, double *y) {
+    FEM3_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * m->n_dof, m->stream));
+    if (m->n_dof > 0 && m->n_tets > 0) {
+        k_p1_apply<<<grid_tets(m->n_tets), 256, 0, m->stream>>>(
+            m->M, m->vol, m->tets, m->dof, m->n_tets, m->K[0], m->K[1], m->K[2], x, y);
         note_launch(m);
     }
     FEM3_CUDA(cudaGetLastError());

@@ -406,7 +406,9 @@ __device__ __forceinline__ int walk_lines(const WalkGeom &W, const TableArgs &A0
             if (rmax - r_prev > W.eps_r) {
                 // table part in double-float FP32: c = coef (rmax^p - r_prev^p)
                 float ph, pl, ch, cl;
-                pow_df(rmax, A0.p_exp, A0.pow_cell, A0.pow_exp, ph, pl);
+                // each side has its own order (unequal orders of the general form)
+                pow_df(rmax, side ? A1.p_exp : A0.p_exp, side ? A1.pow_cell : A0.pow_cell,
+                       side ? A1.pow_exp : A0.pow_exp, ph, pl);
                 df_add2(ph, pl, -pp_h, -pp_l, ch, cl);
                 df_mul(ch, cl, side ? A1.coef_h : A0.coef_h, side ? A1.coef_l : A0.coef_l, ch,
                        cl);
@@ -543,10 +545,10 @@ struct AxisTables {
 // lines and take the rest from a shared counter as they finish (per_block = 128 gives one
 // line per lane).
 __global__ void __launch_bounds__(128, 6) k_walk_tables(WalkGeom W, AxisTables T, int64_t n_gp,
-                                                        int per_block, int32_t *err,
+                                                        int per_block, int axis0, int32_t *err,
                                                         unsigned long long *seg_count) {
     __shared__ int s_next;
-    const int axis = blockIdx.y;
+    const int axis = axis0 + blockIdx.y;
     const int64_t base = blockIdx.x * (int64_t)per_block;
     const int64_t end = min(base + per_block, n_gp);
     if (threadIdx.x == 0) s_next = blockDim.x;
@@ -722,10 +724,55 @@ int walk_tables(Mesh *m, const double alpha[3]) {
         (int)std::max<int64_t>(128, (m->n_gp + blocks - 1) / blocks);
     kc_begin(m, KC_WALK);
     k_walk_tables<<<dim3((unsigned)((m->n_gp + per_block - 1) / per_block), 3), 128, 0, s>>>(
-        W, T, m->n_gp, per_block, m->err, segc);
+        W, T, m->n_gp, per_block, 0, m->err, segc);
     kc_end(m, KC_WALK);
     note_launch(m);
     stage_end(m, 2);
+    FEM3_CUDA(cudaGetLastError());
+    return FEM3_OK;
+}
+
+// Tables of one axis for the general form (c D^a u, D^^b v) (Section 2.1, eq. "equ:varsss"):
+// the left table L with order order_left and the right table R with order order_right, each
+// in [0, 1] (order 0: the basis function itself; order 1: the slope on the Gauss point's
+// tet), both with the one-sided coefficient +-1/Gamma(2 - order).  The power tables of
+// slots 0 and 1 take the two exponents.
+int walk_tables_form(Mesh *m, int axis, double order_left, double order_right) {
+    cudaStream_t s = m->stream;
+    WalkGeom W = make_geom(m);
+    unsigned long long *segc = reinterpret_cast<unsigned long long *>(m->norms + kSegCounterSlot);
+    FEM3_CUDA(cudaMemsetAsync(segc, 0, sizeof(unsigned long long), s));
+    if (!m->pow_cell) {
+        FEM3_TRY(dev_alloc_t(m, &m->pow_cell, 3 * 256 * 8));
+        FEM3_TRY(dev_alloc_t(m, &m->pow_exp, 3 * 128));
+    }
+    k_pow_tables<<<dim3(8, 3), 256, 0, s>>>(1.0 - order_left, 1.0 - order_right,
+                                            1.0 - order_right, m->pow_cell, m->pow_exp);
+    note_launch(m);
+    AxisBins &B = m->bins[axis];
+    AxisTables T;
+    const double il = 1.0 / tgamma(2.0 - order_left), ir = 1.0 / tgamma(2.0 - order_right);
+    const float ilh = (float)il, ill = (float)(il - (double)ilh);
+    const float irh = (float)ir, irl = (float)(ir - (double)irh);
+    T.A0[axis] = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
+                           B.tab_ld, m->tabL[axis], 1.0 - order_left, ilh, ill,
+                           m->pow_cell, m->pow_exp};
+    T.A1[axis] = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
+                           B.tab_ld, m->tabR[axis], 1.0 - order_right, -irh, -irl,
+                           m->pow_cell + 256 * 8, m->pow_exp + 128};
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        FEM3_CUDA(cudaGetDevice(&dev));
+        FEM3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int64_t blocks = std::max<int64_t>(1, (int64_t)sms * 8);
+    const int per_block = (int)std::max<int64_t>(128, (m->n_gp + blocks - 1) / blocks);
+    kc_begin(m, KC_WALK);
+    k_walk_tables<<<dim3((unsigned)((m->n_gp + per_block - 1) / per_block), 1), 128, 0, s>>>(
+        W, T, m->n_gp, per_block, axis, m->err, segc);
+    kc_end(m, KC_WALK);
+    note_launch(m);
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }

@@ -24,6 +24,7 @@ PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2, "bf16x3": 3}
 
 # every entry point declared in include/fem3.h
 SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_assemble_integer",
+           "fem3_assemble_form",
            "fem3_load", "fem3_solve",
            "fem3_adjoint", "fem3_vjp", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
            "fem3_counters", "fem3_bin_stats", "fem3_kernel_ms", "fem3_contract_work",
@@ -67,6 +68,7 @@ def load_library(build_if_missing: bool = True):
         "fem3_mesh_info": [p, C.POINTER(i64), C.POINTER(i64), p],
         "fem3_assemble": [p, p, p, ci, p, p],
         "fem3_assemble_integer": [p, p, p, p],
+        "fem3_assemble_form": [p, ci, dbl, dbl, ci, p, ci, p, p],
         "fem3_load": [p, p, ci, p, p],
         "fem3_solve": [p, p, ci, dbl, ci, p, C.POINTER(ci), C.POINTER(dbl), p],
         "fem3_adjoint": [p, p, p, dbl, ci, p, p, p],
@@ -150,6 +152,12 @@ def assemble_integer(h, K, A_out=None, stream=None):
     k = np.ascontiguousarray(K, dtype=np.float64)
     _check(_lib.fem3_assemble_integer(h, _ptr(k), _ptr(A_out) if A_out is not None else None,
                                       _stream(stream)))
+
+
+def assemble_form(h, axis, alpha, beta, trial_left, c, precision, K_out, stream=None):
+    _check(_lib.fem3_assemble_form(h, int(axis), float(alpha), float(beta), int(bool(trial_left)),
+                                   _ptr(c) if c is not None else None, PRECISIONS[precision],
+                                   _ptr(K_out), _stream(stream)))
 
 
 def load(h, f, nrhs, b, stream=None):
@@ -292,6 +300,16 @@ class Mesh:
         assemble_integer(self.h, K, A, self.stream)
         self.precision = "fp64"
         return A
+
+    def assemble_form(self, axis, alpha, beta, trial_left=True, c=None, precision="fp64"):
+        """One axis term K[k, l] = sum_g w_g c_g (D^alpha psi_l)(x_g) (D^^beta psi_k)(x_g)
+        (left trial operator when trial_left); c: values at the Gauss points or None."""
+        if c is not None and isinstance(c, np.ndarray):
+            c = np.ascontiguousarray(c, dtype=np.float64)
+        K = self._dev((self.n_dof, self.n_dof))
+        assemble_form(self.h, axis, alpha, beta, trial_left, c, precision, K, self.stream)
+        self.precision = None
+        return K
 
     def load(self, f):
         f = self._as_nodal(f)
