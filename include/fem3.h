@@ -159,6 +159,26 @@ int fem3_assemble_form(fem3_mesh m, int axis, double alpha, double beta, int tri
                        const double *c, int precision, double *K_out, void *stream);
 
 /*
+ * fem3_assemble_divergence - Section 3's divergence-form operator (eq. "equ:sfde2"):
+ *     a(u, v) = -sum_i ((p_i D_L^{beta_i} u, D_i v) - (q_i D_R^{beta_i} u, D_i v)),
+ *     A[k][l] = a(psi_l, psi_k)   (not symmetric),
+ * as the sum over the axes of two terms of the general form (fem3_assemble_form with order
+ * 1 on the test side: D_L^1 = d/dx_i, D_R^1 = -d/dx_i), accumulated in FP64.
+ *   beta     host float64[3], each in [0, 1].
+ *   p, q     host or device float64 [3][n_gp]: the coefficients of each axis at the Gauss
+ *            points (Gauss-point order as in fem3_assemble_form), positive for the solve.
+ *   precision  the products of the terms (FEM3_FP64, FEM3_TF32X3, FEM3_BF16X3, FEM3_FP32);
+ *            the operator fem3_solve uses is this matrix itself.
+ *   A_out    device float64 [n_dof][n_dof] or NULL.
+ * The matrix stays in the handle: fem3_solve then runs restarted GMRES (30 vectors, FP64)
+ * right-preconditioned by the FP64 Cholesky factor of -(A + A^T)/2 (SPD for positive p, q;
+ * FEM3_E_NOT_SPD otherwise), per column, until ||b - A u|| <= tol ||b|| (max_iter Arnoldi
+ * steps, 300 when <= 0); iters_out reports the steps of the slowest column.  No adjoint.
+ */
+int fem3_assemble_divergence(fem3_mesh m, const double beta[3], const double *p,
+                             const double *q, int precision, double *A_out, void *stream);
+
+/*
  * fem3_assemble_integer - the integer-order special case alpha_i = 2 on every axis
  * (the right-hand columns of the paper's Table 4): -sum_i K_i d^2 u/dx_i^2, whose
  * Galerkin matrix is the P1 stiffness matrix

@@ -353,6 +353,7 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
     m->factored = false;
     m->ap_ready = false;
     m->integer_order = false;
+    m->nonsym = false;
     kc_reset(m);
     FEM3_TRY(walk_tables(m, alpha));
     stage_begin(m, 3);
@@ -395,6 +396,7 @@ int fem3_assemble_integer(fem3_mesh h, const double K[3], double *A_out, void *s
     m->factored = false;
     m->ap_ready = false;
     m->integer_order = true;
+    m->nonsym = false;
     kc_reset(m);
     stage_begin(m, 3);
     FEM3_TRY(assemble_integer(m, K));
@@ -422,6 +424,7 @@ int fem3_assemble_form(fem3_mesh h, int axis, double alpha, double beta, int tri
     m->factored = false;
     m->ap_ready = false;
     m->integer_order = false;
+    m->nonsym = false;
     kc_reset(m);
     if (precision == FEM3_FP64 && !m->A64) FEM3_TRY(dev_alloc_t(m, &m->A64, n * n));
     if (precision != FEM3_FP64 && !m->A32) FEM3_TRY(dev_alloc_t(m, &m->A32, n * n));
@@ -453,6 +456,46 @@ int fem3_assemble_form(fem3_mesh h, int axis, double alpha, double beta, int tri
         }
     }
     if (owned) cudaFreeAsync(owned, m->stream);
+    return st;
+}
+
+int fem3_assemble_divergence(fem3_mesh h, const double beta[3], const double *p,
+                             const double *q, int precision, double *A_out, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !beta || !p || !q) return set_error(FEM3_E_ARG, "null argument");
+    for (int a = 0; a < 3; a++)
+        if (!(beta[a] >= 0.0 && beta[a] <= 1.0))
+            return set_error(FEM3_E_ARG, "beta must lie in [0, 1]");
+    if (precision != FEM3_FP64 && precision != FEM3_TF32X3 && precision != FEM3_FP32 &&
+        precision != FEM3_BF16X3)
+        return set_error(FEM3_E_ARG, "unknown precision");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = m->n_dof;
+    m->precision = -1;
+    m->factored = false;
+    m->ap_ready = false;
+    m->integer_order = false;
+    m->nonsym = false;
+    kc_reset(m);
+    const void *pd = nullptr, *qd = nullptr;
+    void *po = nullptr, *qo = nullptr;
+    FEM3_TRY(to_device(m, p, sizeof(double) * 3 * m->n_gp, &pd, &po));
+    int st = to_device(m, q, sizeof(double) * 3 * m->n_gp, &qd, &qo);
+    stage_begin(m, 3);
+    if (st == FEM3_OK)
+        st = assemble_divergence(m, beta, (const double *)pd, (const double *)qd, precision);
+    stage_end(m, 3);
+    if (st == FEM3_OK && A_out) {
+        cudaError_t e = cudaMemcpyAsync(A_out, m->A_ns, sizeof(double) * n * n,
+                                        cudaMemcpyDeviceToDevice, m->stream);
+        if (e != cudaSuccess) st = cuda_error(e, "cudaMemcpyAsync");
+    }
+    if (po) cudaFreeAsync(po, m->stream);
+    if (qo) cudaFreeAsync(qo, m->stream);
+    if (st == FEM3_OK) {
+        m->precision = precision;
+        m->nonsym = true;
+    }
     return st;
 }
 
@@ -490,6 +533,34 @@ int fem3_solve(fem3_mesh h, const double *f, int nrhs, double tol, int max_iter,
     stage_begin(m, 4);
     if (st == FEM3_OK) st = load_vector(m, (const double *)fd, nrhs, b);
     stage_end(m, 4);
+    if (m->nonsym) {
+        // divergence form: GMRES per column, preconditioned by the SPD part's factor
+        if (st == FEM3_OK && !m->factored) {
+            stage_begin(m, 5);
+            st = factor_nonsym(m);
+            stage_end(m, 5);
+            if (st == FEM3_OK) st = check_errors(m);
+            if (st == FEM3_OK) m->factored = true;
+        }
+        stage_begin(m, 6);
+        int it_max = 0;
+        double worst = 0;
+        for (int r = 0; r < nrhs && st == FEM3_OK; r++) {
+            int it = 0;
+            double rel = 0;
+            st = gmres_solve(m, b + r * n, u + r * n, tol, max_iter > 0 ? max_iter : 300, &it, &rel);
+            it_max = std::max(it_max, it);
+            worst = std::max(worst, rel);
+        }
+        stage_end(m, 6);
+        if (iters_out) *iters_out = it_max;
+        if (resid_out) *resid_out = worst;
+        if (b) cudaFreeAsync(b, m->stream);
+        if (owned) cudaFreeAsync(owned, m->stream);
+        int st2 = check_errors(m);
+        stage_collect(m);
+        return st != FEM3_OK ? st : st2;
+    }
     if (st == FEM3_OK && !m->factored) {
         stage_begin(m, 5);
         st = factor(m);
@@ -549,6 +620,7 @@ int fem3_adjoint(fem3_mesh h, const double *u, const double *u_obs, double tol, 
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m || !u || !u_obs || !dJ_dK) return set_error(FEM3_E_ARG, "bad argument");
     if (m->precision < 0 || !m->factored) return set_error(FEM3_E_STATE, "adjoint before solve");
+    if (m->nonsym) return set_error(FEM3_E_STATE, "no adjoint for the divergence form");
     m->stream = reinterpret_cast<cudaStream_t>(stream);
     double *res = m->vec64[2];
     FEM3_TRY(sub_vec(u, u_obs, res, m->n_dof, m->stream));
@@ -561,6 +633,7 @@ int fem3_vjp(fem3_mesh h, const double *u, const double *g, double tol, int max_
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m || !u || !g || !dK) return set_error(FEM3_E_ARG, "bad argument");
     if (m->precision < 0 || !m->factored) return set_error(FEM3_E_STATE, "vjp before solve");
+    if (m->nonsym) return set_error(FEM3_E_STATE, "no adjoint for the divergence form");
     m->stream = reinterpret_cast<cudaStream_t>(stream);
     double *seed = m->vec64[2];
     FEM3_CUDA(cudaMemcpyAsync(seed, g, sizeof(double) * m->n_dof, cudaMemcpyDeviceToDevice,

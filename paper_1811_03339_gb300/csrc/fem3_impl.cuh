@@ -137,6 +137,8 @@ struct Mesh {
     bool ap_ready = false;     // ap_R holds W R of the current tables
     bool integer_order = false;   // the matrix came from fem3_assemble_integer (no tables)
     double *form_wc = nullptr;    // general form: w c per Gauss point, and per slot of one axis
+    double *A_ns = nullptr;       // divergence-form (non-symmetric) matrix, FP64 [n_dof][n_dof]
+    bool nonsym = false;          // the current operator is A_ns (GMRES solve)
 
     // workspaces
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -249,7 +251,12 @@ int factor(Mesh *m);
 int chol_tc(Mesh *m, float *A, int64_t n);
 int assemble_integer(Mesh *m, const double K[3]);       // P1 stiffness, alpha_i = 2
 int axis_forms_integer(Mesh *m, const double *u, const double *lam, double out[3]);
-int apply_integer(Mesh *m, const double *x, double *y); // y = A x, element by element   // blocked FP32 Cholesky, tcgen05 trailing updates
+int apply_integer(Mesh *m, const double *x, double *y); // y = A x, element by element
+int assemble_divergence(Mesh *m, const double beta[3], const double *p_d, const double *q_d,
+                        int precision);
+int factor_nonsym(Mesh *m);   // FP64 Cholesky of -(A + A^T)/2: the GMRES preconditioner
+int gmres_solve(Mesh *m, const double *b, double *x, double tol, int max_iter, int *iters,
+                double *resid);   // blocked FP32 Cholesky, tcgen05 trailing updates
 int solve_direct(Mesh *m, const double *b_d, int nrhs, double *u_d);
 int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter, double *u_d,
                   int *iters, double *resid);

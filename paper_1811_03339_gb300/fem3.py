@@ -24,7 +24,7 @@ PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2, "bf16x3": 3}
 
 # every entry point declared in include/fem3.h
 SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_assemble_integer",
-           "fem3_assemble_form",
+           "fem3_assemble_form", "fem3_assemble_divergence",
            "fem3_load", "fem3_solve",
            "fem3_adjoint", "fem3_vjp", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
            "fem3_counters", "fem3_bin_stats", "fem3_kernel_ms", "fem3_contract_work",
@@ -69,6 +69,7 @@ def load_library(build_if_missing: bool = True):
         "fem3_assemble": [p, p, p, ci, p, p],
         "fem3_assemble_integer": [p, p, p, p],
         "fem3_assemble_form": [p, ci, dbl, dbl, ci, p, ci, p, p],
+        "fem3_assemble_divergence": [p, p, p, p, ci, p, p],
         "fem3_load": [p, p, ci, p, p],
         "fem3_solve": [p, p, ci, dbl, ci, p, C.POINTER(ci), C.POINTER(dbl), p],
         "fem3_adjoint": [p, p, p, dbl, ci, p, p, p],
@@ -158,6 +159,13 @@ def assemble_form(h, axis, alpha, beta, trial_left, c, precision, K_out, stream=
     _check(_lib.fem3_assemble_form(h, int(axis), float(alpha), float(beta), int(bool(trial_left)),
                                    _ptr(c) if c is not None else None, PRECISIONS[precision],
                                    _ptr(K_out), _stream(stream)))
+
+
+def assemble_divergence(h, beta, p, q, precision, A_out=None, stream=None):
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    _check(_lib.fem3_assemble_divergence(h, _ptr(b), _ptr(p), _ptr(q), PRECISIONS[precision],
+                                         _ptr(A_out) if A_out is not None else None,
+                                         _stream(stream)))
 
 
 def load(h, f, nrhs, b, stream=None):
@@ -310,6 +318,17 @@ class Mesh:
         assemble_form(self.h, axis, alpha, beta, trial_left, c, precision, K, self.stream)
         self.precision = None
         return K
+
+    def assemble_divergence(self, beta, p, q, precision="fp64", return_matrix=False):
+        """Section 3's divergence form; p, q [3, n_gp] at the Gauss points.  fem3_solve then
+        runs preconditioned GMRES on it."""
+        if isinstance(p, np.ndarray):
+            p = np.ascontiguousarray(p, dtype=np.float64)
+            q = np.ascontiguousarray(q, dtype=np.float64)
+        A = self._dev((self.n_dof, self.n_dof)) if return_matrix else None
+        assemble_divergence(self.h, beta, p, q, precision, A, self.stream)
+        self.precision = precision
+        return A
 
     def load(self, f):
         f = self._as_nodal(f)

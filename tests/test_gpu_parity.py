@@ -658,3 +658,36 @@ def test_general_form_over_many_tiles():
     A = m.assemble(alpha, K3, "tf32x3", return_matrix=True).cpu().numpy()
     assert _rel(A, o.assemble(alpha, K3)) <= 2e-6
     m.free()
+
+
+@pytest.mark.parametrize("name", ["cube7_jitter", "ppd5"])
+def test_divergence_form_and_gmres(name):
+    """Section 3's divergence form with the paper's coefficients (p_i = cos x_i,
+    q_i = 1 - cos x_i) and beta = (0.6, 0.7, 0.8): the matrix against
+    Oracle.assemble_divergence (1e-10 FP64, 2e-6 TF32 x 3), and the GMRES solve
+    (preconditioned by the SPD part's factor) against a LAPACK solve of the oracle's
+    matrix and load vector (1e-10 FP64; the TF32 x 3 operator within its own perturbation)."""
+    mesh, o, _, _ = _case(name)
+    beta = (0.6, 0.7, 0.8)
+    x = o.gp
+    p = np.stack([np.cos(x[:, i]) for i in range(3)])
+    q = 1.0 - p
+    A_ref = o.assemble_divergence(beta, p, q)
+    f = np.random.default_rng(12).standard_normal((mesh.n_nodes, 2))
+    u_ref = np.linalg.solve(A_ref, o.load(f))
+    m = fem3.Mesh(mesh.verts, mesh.tets)
+    A = m.assemble_divergence(beta, p, q, "fp64", return_matrix=True).cpu().numpy()
+    assert _rel(A, A_ref) <= 1e-10
+    assert np.abs(A - A.T).max() > 1e-3 * np.abs(A).max()   # really not symmetric
+    u = m.solve(f, tol=1e-13).cpu().numpy()
+    err = np.linalg.norm(u - u_ref, axis=0) / np.linalg.norm(u_ref, axis=0)
+    assert err.max() <= 1e-10, err
+    assert 1 <= m.iters <= 60 and m.resid <= 1e-13
+    At = m.assemble_divergence(beta, p, q, "tf32x3", return_matrix=True).cpu().numpy()
+    assert _rel(At, A_ref) <= 2e-6
+    ut = m.solve(f, tol=1e-12).cpu().numpy()
+    errt = np.linalg.norm(ut - u_ref, axis=0) / np.linalg.norm(u_ref, axis=0)
+    assert errt.max() <= 1e-4, errt
+    with pytest.raises(fem3.Fem3Error):
+        m.adjoint(torch.from_numpy(u[:, 0].copy()).cuda(), torch.zeros(m.n_dof, dtype=torch.float64, device="cuda"))
+    m.free()
