@@ -136,6 +136,22 @@ int fem3_assemble(fem3_mesh m, const double alpha[3], const double K[3], int pre
                   double *A_out, void *stream);
 
 /*
+ * fem3_assemble_part - one part of the matrix of fem3_assemble, for assembling one mesh
+ * over several devices (each device one part, then a sum all-reduce of the parts).
+ * The element sum of Section 2.1 is a sum over Gauss points, so the Gauss points of every
+ * axis are split by transverse bins: part p of P walks and contracts the bins
+ * [nb p / P, nb (p + 1) / P) of each axis (nb the axis's bin count), and the P parts sum to
+ * the whole matrix (up to the order of floating-point additions).
+ *   alpha, K, precision  as fem3_assemble.
+ *   part, nparts         0 <= part < nparts.
+ *   A_out    device float64 [n_dof][n_dof]: the part (symmetric, both triangles).
+ * The handle then holds no operator for fem3_solve (FEM3_E_STATE until the next
+ * fem3_assemble).  Not in the paper.
+ */
+int fem3_assemble_part(fem3_mesh m, const double alpha[3], const double K[3], int precision,
+                       int part, int nparts, double *A_out, void *stream);
+
+/*
  * fem3_assemble_form - one axis term of the general variational form of Section 2.1
  * (eq. "equ:varsss" and the element quadrature formula after it) with a variable
  * coefficient and unequal orders:

@@ -379,6 +379,24 @@ int fem3_assemble(fem3_mesh h, const double alpha[3], const double K[3], int pre
     return FEM3_OK;
 }
 
+int fem3_assemble_part(fem3_mesh h, const double alpha[3], const double K[3], int precision,
+                       int part, int nparts, double *A_out, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !A_out) return set_error(FEM3_E_ARG, "null argument");
+    if (nparts < 1 || part < 0 || part >= nparts)
+        return set_error(FEM3_E_ARG, "0 <= part < nparts required");
+    m->part = part;
+    m->nparts = nparts;
+    const int st = fem3_assemble(h, alpha, K, precision, A_out, stream);
+    m->part = 0;
+    m->nparts = 1;
+    // a part of the matrix (and of the tables) is no operator to solve with
+    m->precision = -1;
+    m->factored = false;
+    m->ap_ready = false;
+    return st;
+}
+
 int fem3_assemble_integer(fem3_mesh h, const double K[3], double *A_out, void *stream) {
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m || !K) return set_error(FEM3_E_ARG, "null argument");

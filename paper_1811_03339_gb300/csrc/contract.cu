@@ -304,15 +304,25 @@ int contract(Mesh *m, int precision) {
             flops += 2.0 * D * D * G;
         }
         if (!B.n_work) continue;
+        // the work items of this part's bins (the list is in bin order)
+        int b0, b1;
+        part_bins(m, axis, b0, b1);
+        const auto lb = [&](int b) {
+            return (int)(std::lower_bound(B.h_work.begin(), B.h_work.end(), b,
+                                          [](const int4 &x, int v) { return x.x < v; }) -
+                         B.h_work.begin());
+        };
+        const int w0 = lb(b0), nw = lb(b1) - w0;
+        if (nw <= 0) continue;
         kc_begin(m, KC_CONTRACT);
         if (precision == FEM3_FP64)
-            k_contract_simt<double><<<B.n_work, 256, 0, s>>>(
-                m->tabL[axis], m->tabR[axis], B.work, B.gp_off, B.gp_idx, B.dof_off, B.dof_idx,
-                B.tab_off, B.tab_ld, m->gw, m->sK[axis], m->A64, n);
+            k_contract_simt<double><<<nw, 256, 0, s>>>(
+                m->tabL[axis], m->tabR[axis], B.work + w0, B.gp_off, B.gp_idx, B.dof_off,
+                B.dof_idx, B.tab_off, B.tab_ld, m->gw, m->sK[axis], m->A64, n);
         else
-            k_contract_simt<float><<<B.n_work, 256, 0, s>>>(
-                m->tabL[axis], m->tabR[axis], B.work, B.gp_off, B.gp_idx, B.dof_off, B.dof_idx,
-                B.tab_off, B.tab_ld, m->gw, m->sK[axis], m->A32, n);
+            k_contract_simt<float><<<nw, 256, 0, s>>>(
+                m->tabL[axis], m->tabR[axis], B.work + w0, B.gp_off, B.gp_idx, B.dof_off,
+                B.dof_idx, B.tab_off, B.tab_ld, m->gw, m->sK[axis], m->A32, n);
         kc_end(m, KC_CONTRACT);
         note_launch(m);
     }

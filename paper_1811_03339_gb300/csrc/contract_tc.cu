@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(256) k_split_ops(
     const int32_t *__restrict__ row_bin, const int32_t *__restrict__ dof_off,
     const int32_t *__restrict__ gp_off, const double *__restrict__ w_slot,
     const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
-    int64_t n_rows, int Kp, OT *Lhi, OT *Llo, OT *Rhi, OT *Rlo, float2 *apR) {
-    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    int64_t row_lo, int64_t n_rows, int Kp, OT *Lhi, OT *Llo, OT *Rhi, OT *Rlo, float2 *apR) {
+    const int64_t row = row_lo + blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n_rows) return;
     const int b = row_bin[row];
@@ -391,13 +391,23 @@ static int tc_gemms(Mesh *m, bool bf16, int w, const CUtensorMap (*maps)[4], int
     for (int axis = 0; axis < 3; axis++) {
         if (only_axis >= 0 && axis != only_axis) continue;
         AxisBins &B = m->bins[axis];
-        const int nw = B.tc_n_work[w];
-        if (!nw) continue;
+        // the work items of this part's bins: the list is in bin order
+        int b0, b1;
+        part_bins(m, axis, b0, b1);
+        const std::vector<int4> &hw = B.h_tc_work[w];
+        const auto lb = [&](int b) {
+            return (int)(std::lower_bound(hw.begin(), hw.end(), b,
+                                          [](const int4 &x, int v) { return x.x < v; }) -
+                         hw.begin());
+        };
+        const int w0 = lb(b0), nw = lb(b1) - w0;
+        if (nw <= 0) continue;
+        const int4 *wk = B.tc_work[w] + w0;
         const CUtensorMap *mp = maps[axis];
         const float sk = full ? 1.0f : (float)m->sK[axis];
 #define FEM3_TC_LAUNCH(BF, BN)                                                                  \
     k_contract_tc<BF, BN><<<nw, 128, TcCfg<BN>::kSmemBytes, s>>>(                              \
-        mp[0], mp[1], mp[2], mp[3], B.tc_work[w], B.dof_off, B.dof_idx, B.gp_off, sk, m->A32, n, \
+        mp[0], mp[1], mp[2], mp[3], wk, B.dof_off, B.dof_idx, B.gp_off, sk, m->A32, n, \
         full, m->err)
         if (kTileWidths[w] == 256) {
             if (bf16) FEM3_TC_LAUNCH(true, 256); else FEM3_TC_LAUNCH(false, 256);
@@ -429,20 +439,24 @@ int contract_tc(Mesh *m, bool bf16) {
         FEM3_TRY(ap_alloc(m, axis));
         const int kbk = bf16 ? 64 : 32;   // Gauss points per 128-byte swizzle row
         const int Kp = std::max(kbk, (B.tc_maxG + kbk - 1) / kbk * kbk);
-        const unsigned grid = (unsigned)((B.n_tmpl + 7) / 8);
+        // template rows of this part's bins (all rows unless assembled in parts)
+        int b0, b1;
+        part_bins(m, axis, b0, b1);
+        const int64_t row_lo = B.h_dof_off[b0], row_hi = B.h_dof_off[b1];
+        const unsigned grid = (unsigned)std::max<int64_t>(1, (row_hi - row_lo + 7) / 8);
         kc_begin(m, KC_SPLIT);
         if (bf16) {
             __nv_bfloat16 *op[4];
             for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<__nv_bfloat16 *>(B.tc_op[q]);
             k_split_ops<__nv_bfloat16><<<grid, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
-                B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1], op[2], op[3], B.ap_R);
+                B.tab_off, B.tab_ld, row_lo, row_hi, Kp, op[0], op[1], op[2], op[3], B.ap_R);
         } else {
             float *op[4];
             for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<float *>(B.tc_op[q]);
             k_split_ops<float><<<grid, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
-                B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1], op[2], op[3], B.ap_R);
+                B.tab_off, B.tab_ld, row_lo, row_hi, Kp, op[0], op[1], op[2], op[3], B.ap_R);
         }
         kc_end(m, KC_SPLIT);
         note_launch(m);
@@ -454,6 +468,8 @@ int contract_tc(Mesh *m, bool bf16) {
     m->tc_tuned = false;
     if (m->tc_tile_opt == 128 || m->tc_tile_opt == 256) {
         w = m->tc_tile_opt == 256 ? 0 : 1;
+    } else if (m->nparts > 1) {
+        w = 1;   // a part's GEMMs are not representative of the size class: no tuning
     } else {
         const uint64_t key = tile_class(m, bf16);
         {
@@ -532,14 +548,14 @@ int contract_tc_form(Mesh *m, int axis, bool test_right, double *wc_gp, bool bf1
         __nv_bfloat16 *op[4];
         for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<__nv_bfloat16 *>(B.tc_op[q]);
         k_split_ops<__nv_bfloat16><<<grid, 256, 0, s>>>(T, S, B.row_bin, B.dof_off, B.gp_off, ws,
-                                                         B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0],
-                                                         op[1], op[2], op[3], B.ap_R);
+                                                         B.tab_off, B.tab_ld, 0, B.n_tmpl, Kp,
+                                                         op[0], op[1], op[2], op[3], B.ap_R);
     } else {
         float *op[4];
         for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<float *>(B.tc_op[q]);
         k_split_ops<float><<<grid, 256, 0, s>>>(T, S, B.row_bin, B.dof_off, B.gp_off, ws,
-                                                B.tab_off, B.tab_ld, B.n_tmpl, Kp, op[0], op[1],
-                                                op[2], op[3], B.ap_R);
+                                                B.tab_off, B.tab_ld, 0, B.n_tmpl, Kp, op[0],
+                                                op[1], op[2], op[3], B.ap_R);
     }
     kc_end(m, KC_SPLIT);
     note_launch(m);
@@ -574,7 +590,7 @@ int ap_prepare(Mesh *m) {
         kc_begin(m, KC_SPLIT);
         k_split_ops<float><<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
             m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot, B.tab_off,
-            B.tab_ld, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_R);
+            B.tab_ld, 0, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_R);
         kc_end(m, KC_SPLIT);
         note_launch(m);
     }

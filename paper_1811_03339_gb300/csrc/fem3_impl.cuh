@@ -139,6 +139,7 @@ struct Mesh {
     double *form_wc = nullptr;    // general form: w c per Gauss point, and per slot of one axis
     double *A_ns = nullptr;       // divergence-form (non-symmetric) matrix, FP64 [n_dof][n_dof]
     bool nonsym = false;          // the current operator is A_ns (GMRES solve)
+    int part = 0, nparts = 1;     // assembly restricted to part `part` of every axis's bins
 
     // workspaces
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -178,6 +179,13 @@ struct Mesh {
 };
 
 inline void note_launch(Mesh *m) { m->launches++; }
+
+// bins [b0, b1) of the current part of an axis: contiguous ranges of equal bin count
+inline void part_bins(const Mesh *m, int axis, int &b0, int &b1) {
+    const int64_t nb = m->bins[axis].n_bins;
+    b0 = (int)(nb * m->part / m->nparts);
+    b1 = (int)(nb * (m->part + 1) / m->nparts);
+}
 
 // device memory owned by a mesh (stream-ordered pool allocations)
 int dev_alloc(Mesh *m, void **p, size_t bytes);

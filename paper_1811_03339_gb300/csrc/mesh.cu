@@ -178,9 +178,13 @@ __global__ void k_tet_geom(const double *__restrict__ verts, const int32_t *__re
 // bounding box of the vertices (ordered-integer atomics) and total volume
 // bounding box of the nodes and total tet volume: reduced within each warp first, one
 // atomic per warp and quantity
+// The volume goes into one partial sum per warp (no atomics) and k_sum_ordered adds the
+// partials in a fixed order: the total, and the bin width derived from it, are the same
+// bits on every run (with atomics the order of the additions varied, the last bit of the
+// width with it, and at a width that divides the extent the bin count flipped).
 __global__ void k_extent(const double *__restrict__ verts, int64_t n_nodes,
                          const double *__restrict__ vol, int64_t n_tets,
-                         unsigned long long *ext, double *vsum) {
+                         unsigned long long *ext, double *vpart) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -200,7 +204,21 @@ __global__ void k_extent(const double *__restrict__ verts, int64_t n_nodes,
     }
     double v = i < n_tets ? vol[i] : 0.0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0 && v != 0.0) atomicAdd(vsum, v);
+    if (lane == 0) vpart[i >> 5] = v;
+}
+
+// out = sum of in[0 .. n) in a fixed order (one block of 256 threads)
+__global__ void k_sum_ordered(const double *__restrict__ in, int64_t n, double *out) {
+    __shared__ double sh[256];
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 256) a += in[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
 }
 
 __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v) {
@@ -638,13 +656,17 @@ int mesh_build(Mesh *m, const double *verts_d, const int32_t *tets_d) {
     note_launch(m);
 
     unsigned long long *ext = nullptr;
-    double *vsum = nullptr;
+    double *vsum = nullptr, *vpart = nullptr;
+    const unsigned ge = grid_for(std::max(N, T));
+    const int64_t nwarp = (int64_t)ge * (kThreads / 32);
     FEM3_TRY(dev_alloc_t(m, &ext, 6));
     FEM3_TRY(dev_alloc_t(m, &vsum, 1));
+    FEM3_TRY(dev_alloc_t(m, &vpart, nwarp));
     k_box_init<<<1, 32, 0, s>>>(ext, 1);
     note_launch(m);
-    FEM3_CUDA(cudaMemsetAsync(vsum, 0, sizeof(double), s));
-    k_extent<<<grid_for(std::max(N, T)), kThreads, 0, s>>>(verts_d, N, m->vol, T, ext, vsum);
+    k_extent<<<ge, kThreads, 0, s>>>(verts_d, N, m->vol, T, ext, vpart);
+    note_launch(m);
+    k_sum_ordered<<<1, 256, 0, s>>>(vpart, nwarp, vsum);
     note_launch(m);
 
     int32_t n_dof = 0;
@@ -690,8 +712,10 @@ int bins_build(Mesh *m) {
         B.width = m->bin_scale * m->h_est;
         B.org0 = m->lo[B.c0];
         B.org1 = m->lo[B.c1];
-        B.nb0 = std::max(1, (int)ceil((m->hi[B.c0] - m->lo[B.c0]) / B.width));
-        B.nb1 = std::max(1, (int)ceil((m->hi[B.c1] - m->lo[B.c1]) / B.width));
+        // an extent that is a whole number of widths up to rounding gets that many bins, not
+        // one more nearly empty row (points on the far edge clamp into the last bin)
+        B.nb0 = std::max(1, (int)ceil((m->hi[B.c0] - m->lo[B.c0]) / B.width * (1.0 - 1e-9)));
+        B.nb1 = std::max(1, (int)ceil((m->hi[B.c1] - m->lo[B.c1]) / B.width * (1.0 - 1e-9)));
         B.n_bins = B.nb0 * B.nb1;
         nb_tot += B.n_bins;
         nb_max = std::max(nb_max, B.n_bins);

@@ -538,6 +538,7 @@ __device__ __forceinline__ void count_segments(int nseg, unsigned long long *seg
 // the three axes' table arguments (kernel parameters)
 struct AxisTables {
     TableArgs A0[3], A1[3];
+    int64_t lo[3], hi[3];   // the slots of each axis to walk, [lo, hi) (a bin range's slots)
 };
 
 // grid: x over blocks of `per_block` consecutive slots of an axis (bin order), y = axis; the
@@ -549,8 +550,8 @@ __global__ void __launch_bounds__(128, 6) k_walk_tables(WalkGeom W, AxisTables T
                                                         unsigned long long *seg_count) {
     __shared__ int s_next;
     const int axis = axis0 + blockIdx.y;
-    const int64_t base = blockIdx.x * (int64_t)per_block;
-    const int64_t end = min(base + per_block, n_gp);
+    const int64_t base = T.lo[axis] + blockIdx.x * (int64_t)per_block;
+    const int64_t end = min(base + per_block, T.hi[axis]);
     if (threadIdx.x == 0) s_next = blockDim.x;
     __syncthreads();
     const int64_t slot = base + threadIdx.x;
@@ -713,6 +714,15 @@ int walk_tables(Mesh *m, const double alpha[3]) {
     // the blocks hold more slots and their lanes take further lines as they finish.  (At the
     // 16^3 cube 2.5 lines per lane was 10 % slower than one: the lanes of a warp drift to
     // different lines and diverge.)
+    // the slots of this part's bins (all slots unless the mesh is assembled in parts)
+    int64_t span = 0;
+    for (int axis = 0; axis < 3; axis++) {
+        int b0, b1;
+        part_bins(m, axis, b0, b1);
+        T.lo[axis] = m->bins[axis].h_gp_off[b0];
+        T.hi[axis] = m->bins[axis].h_gp_off[b1];
+        span = std::max(span, T.hi[axis] - T.lo[axis]);
+    }
     static int sms = 0;
     if (sms == 0) {
         int dev = 0;
@@ -720,11 +730,10 @@ int walk_tables(Mesh *m, const double alpha[3]) {
         FEM3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     }
     const int64_t blocks = std::max<int64_t>(1, (int64_t)sms * 8);
-    const int per_block =
-        (int)std::max<int64_t>(128, (m->n_gp + blocks - 1) / blocks);
+    const int per_block = (int)std::max<int64_t>(128, (span + blocks - 1) / blocks);
     kc_begin(m, KC_WALK);
-    k_walk_tables<<<dim3((unsigned)((m->n_gp + per_block - 1) / per_block), 3), 128, 0, s>>>(
-        W, T, m->n_gp, per_block, 0, m->err, segc);
+    k_walk_tables<<<dim3((unsigned)std::max<int64_t>(1, (span + per_block - 1) / per_block), 3),
+                    128, 0, s>>>(W, T, m->n_gp, per_block, 0, m->err, segc);
     kc_end(m, KC_WALK);
     note_launch(m);
     stage_end(m, 2);
@@ -768,6 +777,8 @@ int walk_tables_form(Mesh *m, int axis, double order_left, double order_right) {
     }
     const int64_t blocks = std::max<int64_t>(1, (int64_t)sms * 8);
     const int per_block = (int)std::max<int64_t>(128, (m->n_gp + blocks - 1) / blocks);
+    T.lo[axis] = 0;
+    T.hi[axis] = m->n_gp;
     kc_begin(m, KC_WALK);
     k_walk_tables<<<dim3((unsigned)((m->n_gp + per_block - 1) / per_block), 1), 128, 0, s>>>(
         W, T, m->n_gp, per_block, axis, m->err, segc);

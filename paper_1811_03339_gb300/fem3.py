@@ -24,7 +24,7 @@ PRECISIONS = {"fp64": 0, "tf32x3": 1, "fp32": 2, "bf16x3": 3}
 
 # every entry point declared in include/fem3.h
 SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_assemble_integer",
-           "fem3_assemble_form", "fem3_assemble_divergence",
+           "fem3_assemble_form", "fem3_assemble_divergence", "fem3_assemble_part",
            "fem3_load", "fem3_solve",
            "fem3_adjoint", "fem3_vjp", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
            "fem3_counters", "fem3_bin_stats", "fem3_kernel_ms", "fem3_contract_work",
@@ -69,6 +69,7 @@ def load_library(build_if_missing: bool = True):
         "fem3_assemble": [p, p, p, ci, p, p],
         "fem3_assemble_integer": [p, p, p, p],
         "fem3_assemble_form": [p, ci, dbl, dbl, ci, p, ci, p, p],
+        "fem3_assemble_part": [p, p, p, ci, ci, ci, p, p],
         "fem3_assemble_divergence": [p, p, p, p, ci, p, p],
         "fem3_load": [p, p, ci, p, p],
         "fem3_solve": [p, p, ci, dbl, ci, p, C.POINTER(ci), C.POINTER(dbl), p],
@@ -147,6 +148,13 @@ def assemble(h, alpha, K, precision="fp64", A_out=None, stream=None):
     k = np.ascontiguousarray(K, dtype=np.float64)
     _check(_lib.fem3_assemble(h, _ptr(a), _ptr(k), PRECISIONS[precision],
                               _ptr(A_out) if A_out is not None else None, _stream(stream)))
+
+
+def assemble_part(h, alpha, K, precision, part, nparts, A_out, stream=None):
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    k = np.ascontiguousarray(K, dtype=np.float64)
+    _check(_lib.fem3_assemble_part(h, _ptr(a), _ptr(k), PRECISIONS[precision], int(part),
+                                   int(nparts), _ptr(A_out), _stream(stream)))
 
 
 def assemble_integer(h, K, A_out=None, stream=None):
@@ -300,6 +308,14 @@ class Mesh:
         A = self._dev((self.n_dof, self.n_dof)) if return_matrix else None
         assemble(self.h, alpha, K, precision, A, self.stream)
         self.precision = precision
+        return A
+
+    def assemble_part(self, alpha, K, precision, part, nparts):
+        """Part `part` of `nparts` of the matrix (the bins [nb part/nparts, nb (part+1)/nparts)
+        of every axis); the parts sum to the whole matrix."""
+        A = self._dev((self.n_dof, self.n_dof))
+        assemble_part(self.h, alpha, K, precision, part, nparts, A, self.stream)
+        self.precision = None
         return A
 
     def assemble_integer(self, K, return_matrix=False):
