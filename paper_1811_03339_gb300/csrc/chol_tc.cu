@@ -46,6 +46,9 @@ constexpr int kStages = 2;
 constexpr int kCsLd = 129;                     // row stride of the staged C tile (floats)
 constexpr uint32_t kCsBytes = 128 * kCsLd * 4;  // 66 KB
 constexpr uint32_t kTrailSmem = kStages * kStage + kCsBytes + 1024 + 256;
+constexpr int kTrailThreads = 320;              // TMA warp, MMA warp, eight epilogue warps
+constexpr int kEpiThreads = 256;
+constexpr int kReservedSms = 20;                // left to the critical chain by the bulk update
 
 // ------------------------------- diagonal block ----------------------------------
 // c[i][j] (+)= sgn * sum_k a[i][k] b(k, j) over a 64 x 64 x 64 product in shared memory,
@@ -203,133 +206,192 @@ __device__ __forceinline__ void tri_decode(int x, int &I, int &J) {
     J = x - i * (i + 1) / 2;
 }
 
-// mode 0: every tile I >= J; 1: the first block column (J = 0, the next panel's columns);
-// 2: every tile 1 <= J <= I (the rest)
-__global__ void __launch_bounds__(128, 1) k_cholp_trail(const __grid_constant__ CUtensorMap mHi,
-                                                        const __grid_constant__ CUtensorMap mLo,
-                                                        float *A, int64_t n, int64_t t0, int mode,
-                                                        int32_t *err) {
+// tile x of a launch -> (I, J).  mode 0: every tile I >= J; 1: the first block column (J = 0,
+// the next panel's columns); 2: every tile 1 <= J <= I (the rest)
+__device__ __forceinline__ void tile_of(int x, int mode, int &I, int &J) {
+    if (mode == 1) {
+        I = x;
+        J = 0;
+        return;
+    }
+    tri_decode(x, I, J);
+    if (mode == 2) {
+        I++;
+        J++;
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// named barrier of the eight epilogue warps (id 1; 0 is __syncthreads)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Persistent trailing update: CTA c takes tiles c, c + gridDim.x, ...  Warp 0 streams the
+// operands of its tiles through the two-stage TMA ring, warp 1 issues the MMAs of tile i
+// into TMEM accumulator i % 2 (256 columns: two 128 x 128 FP32 accumulators), warps 2-9
+// (two per TMEM lane quadrant, each half of the columns) run the epilogue of tile i while the
+// MMAs of tile i + 1 proceed: fetch C(i) by 4-byte cp.async, wait for the accumulator,
+// C -= X in shared memory, free the accumulator, write C back.  The fetch and the write-back
+// go row by row (a warp per row, its lanes along the row: one row pointer per row, each
+// instruction 128 consecutive bytes).  Every mbarrier wait is
+// bounded; a role that gives up records ERR_CHOL and the others give up on their next wait.
+__global__ void __launch_bounds__(kTrailThreads, 1) k_cholp_trail(
+    const __grid_constant__ CUtensorMap mHi, const __grid_constant__ CUtensorMap mLo, float *A,
+    int64_t n, int64_t t0, int mode, int ntiles, int32_t *err) {
     extern __shared__ __align__(1024) unsigned char sm_trail[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(sm_trail) + 1023) & ~(uintptr_t)1023);
     float *Cs = reinterpret_cast<float *>(base + kStages * kStage);   // [128][129]
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + kStages * kStage + kCsBytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 1);
-    __shared__ int s_fail;
-    int I, J;
-    if (mode == 1) {
-        I = blockIdx.x;
-        J = 0;
-    } else {
-        tri_decode(blockIdx.x, I, J);
-        if (mode == 2) {
-            I++;
-            J++;
-        }
-    }
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
+    __shared__ int s_fail;    // producer / MMA gave up (read only as an early exit)
+    __shared__ int s_efail;   // an epilogue wait gave up: written by the epilogue warps before
+                              // a named barrier and read after it, so all four exit together
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int nk = kP / 32;   // K steps of 32 TF32 columns (one 128-byte swizzle row)
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]);
-    const uint32_t done = smem_u32(&bars[2 * kStages]);
+    const uint32_t accf0 = smem_u32(&bars[2 * kStages]), acce0 = smem_u32(&bars[2 * kStages + 2]);
     if (threadIdx.x == 0) {
         s_fail = 0;
-        for (int s = 0; s < kStages; s++) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+        s_efail = 0;
+        for (int st = 0; st < kStages; st++) {
+            mbar_init(full0 + 8 * st, 1);
+            mbar_init(empty0 + 8 * st, 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, kEpiThreads);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 2) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(128));
+                     "r"(2 * 128));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-    // the C tile's rows are fetched now (4-byte cp.async: a row of A starts on any 4-byte
-    // boundary), all in flight at once, so that they arrive while the MMAs run
-    const int64_t gr0 = t0 + 128 * (int64_t)I, gc0 = t0 + 128 * (int64_t)J;
-    for (int e = threadIdx.x; e < 128 * 128; e += 128) {
-        const int r = e >> 7, c = e & 127;
-        const int64_t gr = gr0 + r, gc = gc0 + c;
-        if (gr < n && gc < n && (I != J || gc <= gr))
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(Cs + r * kCsLd + c)),
-                         "l"(A + gr * n + gc)
-                         : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int ntl = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (warp == 0 && lane == 0) {
-        for (int k = 0; k < nk; k++) {
-            const int s = k % kStages;
-            if (k >= kStages && !mbar_wait(empty0 + 8 * s, ((k / kStages) - 1) & 1)) {
-                s_fail = 1;
-                break;
+        for (int i = 0; i < ntl && !s_fail; i++) {
+            int I, J;
+            tile_of((int)blockIdx.x + i * (int)gridDim.x, mode, I, J);
+            for (int k = 0; k < nk; k++) {
+                const int q = i * nk + k, st = q & 1;
+                if (q >= 2 && !mbar_wait(empty0 + 8 * st, ((q >> 1) - 1) & 1)) {
+                    s_fail = 1;
+                    break;
+                }
+                uint8_t *sp = base + st * kStage;
+                const uint32_t bar = full0 + 8 * st;
+                mbar_expect_tx(bar, kStage);
+                tma_load_2d(smem_u32(sp), &mHi, 32 * k, 128 * I, bar);
+                tma_load_2d(smem_u32(sp + kTile), &mLo, 32 * k, 128 * I, bar);
+                tma_load_2d(smem_u32(sp + 2 * kTile), &mHi, 32 * k, 128 * J, bar);
+                tma_load_2d(smem_u32(sp + 3 * kTile), &mLo, 32 * k, 128 * J, bar);
             }
-            uint8_t *st = base + s * kStage;
-            const uint32_t bar = full0 + 8 * s;
-            mbar_expect_tx(bar, kStage);
-            tma_load_2d(smem_u32(st), &mHi, 32 * k, 128 * I, bar);
-            tma_load_2d(smem_u32(st + kTile), &mLo, 32 * k, 128 * I, bar);
-            tma_load_2d(smem_u32(st + 2 * kTile), &mHi, 32 * k, 128 * J, bar);
-            tma_load_2d(smem_u32(st + 3 * kTile), &mLo, 32 * k, 128 * J, bar);
         }
     } else if (warp == 1 && lane == 0) {
         const uint32_t idesc = idesc_mma(128, 128, 2u);
-        for (int k = 0; k < nk; k++) {
-            const int s = k % kStages;
-            if (!mbar_wait(full0 + 8 * s, (k / kStages) & 1)) {
+        for (int i = 0; i < ntl && !s_fail; i++) {
+            const int b = i & 1;
+            if (i >= 2 && !mbar_wait(acce0 + 8 * b, ((i >> 1) - 1) & 1)) {
                 s_fail = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t st = smem_u32(base + s * kStage);
-            const uint32_t aH = st, aL = st + kTile, bH = st + 2 * kTile, bL = st + 3 * kTile;
+            const uint32_t d = tmem + (uint32_t)(b * 128);
+            for (int k = 0; k < nk; k++) {
+                const int q = i * nk + k, st = q & 1;
+                if (!mbar_wait(full0 + 8 * st, (q >> 1) & 1)) {
+                    s_fail = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sp = smem_u32(base + st * kStage);
+                const uint32_t aH = sp, aL = sp + kTile, bH = sp + 2 * kTile, bL = sp + 3 * kTile;
 #pragma unroll
-            for (int ks = 0; ks < 4; ks++) {   // 32 bytes (8 TF32) per MMA
-                const uint32_t off = ks * 32;
-                umma<false>(tmem, umma_desc_sw128(aH + off), umma_desc_sw128(bH + off), idesc,
-                            (k > 0 || ks > 0) ? 1u : 0u);
-                umma<false>(tmem, umma_desc_sw128(aH + off), umma_desc_sw128(bL + off), idesc, 1u);
-                umma<false>(tmem, umma_desc_sw128(aL + off), umma_desc_sw128(bH + off), idesc, 1u);
+                for (int ks = 0; ks < 4; ks++) {   // 32 bytes (8 TF32) per MMA
+                    const uint32_t off = ks * 32;
+                    umma<false>(d, umma_desc_sw128(aH + off), umma_desc_sw128(bH + off), idesc,
+                                (k > 0 || ks > 0) ? 1u : 0u);
+                    umma<false>(d, umma_desc_sw128(aH + off), umma_desc_sw128(bL + off), idesc, 1u);
+                    umma<false>(d, umma_desc_sw128(aL + off), umma_desc_sw128(bH + off), idesc, 1u);
+                }
+                umma_commit(empty0 + 8 * st);
             }
-            umma_commit(empty0 + 8 * s);
+            umma_commit(accf0 + 8 * b);
         }
-        umma_commit(done);
+    } else if (warp >= 2) {
+        const int ew = warp - 2;                     // epilogue warp 0 .. 7
+        const int quad = warp & 3;                   // TMEM lane quadrant of this warp
+        const int half = ew >> 2;                    // columns [64 half, 64 half + 64)
+        const int row = quad * 32 + lane;            // tile row = TMEM lane
+        for (int i = 0; i < ntl; i++) {
+            int I, J;
+            tile_of((int)blockIdx.x + i * (int)gridDim.x, mode, I, J);
+            const int64_t gr0 = t0 + 128 * (int64_t)I, gc0 = t0 + 128 * (int64_t)J;
+            // C(i): every row in flight at once (a row of A starts on any 4-byte boundary)
+            for (int r = ew; r < 128; r += 8) {
+                const int64_t gr = gr0 + r;
+                if (gr >= n) break;
+                const int64_t cend = (I == J ? gr + 1 : n) - gc0;   // valid columns [0, cend)
+                const float *src = A + gr * n + gc0;
+                const uint32_t dst = smem_u32(Cs + r * kCsLd);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int c = lane + 32 * q;
+                    if (c < cend && gc0 + c < n)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4 * c),
+                                     "l"(src + c)
+                                     : "memory");
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            const int b = i & 1;
+            const bool got = mbar_wait(accf0 + 8 * b, (i >> 1) & 1);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            if (!got) s_efail = 1;
+            epi_sync();
+            if (s_efail) break;   // the same value for all epilogue threads (see s_efail)
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int cb = 0; cb < 64; cb += 16) {
+                const int c0 = 64 * half + cb;
+                float v[16];
+                tmem_ld16(tmem + (uint32_t)(b * 128) + ((uint32_t)(quad * 32) << 16) + c0, v);
+#pragma unroll
+                for (int q = 0; q < 16; q++) Cs[row * kCsLd + c0 + q] -= v[q];
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(acce0 + 8 * b);   // the accumulator is free for tile i + 2
+            epi_sync();
+            for (int r = ew; r < 128; r += 8) {
+                const int64_t gr = gr0 + r;
+                if (gr >= n) break;
+                const int64_t cend = (I == J ? gr + 1 : n) - gc0;
+                float *dstg = A + gr * n + gc0;
+                const float *srcs = Cs + r * kCsLd;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int c = lane + 32 * q;
+                    if (c < cend && gc0 + c < n) dstg[c] = srcs[c];
+                }
+            }
+            epi_sync();   // Cs is read out before the next tile's rows arrive
+        }
     }
     __syncthreads();
-    const bool ok = __syncthreads_and(mbar_wait(done, 0) && !s_fail);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!ok) {
-        if (threadIdx.x == 0) atomicAdd(&err[ERR_CHOL], 1);
-    } else {
-        // thread = tile row (TMEM lane): C -= X in shared memory (row stride 129: lanes on
-        // consecutive rows hit distinct banks), then the tile goes back to A with the lanes
-        // of a warp along a row (each store instruction covers 128 consecutive bytes)
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
-        const int r = warp * 32 + lane;
-        for (int cb = 0; cb < 128; cb += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cb, v);
-#pragma unroll
-            for (int q = 0; q < 16; q++) Cs[r * kCsLd + cb + q] -= v[q];
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < 128 * 128; e += 128) {
-            const int rr = e >> 7, c = e & 127;
-            const int64_t gr = gr0 + rr, gc = gc0 + c;
-            if (gr < n && gc < n && (I != J || gc <= gr)) A[gr * n + gc] = Cs[rr * kCsLd + c];
-        }
-    }
-    if (!ok) asm volatile("cp.async.wait_all;" ::: "memory");
+    if (threadIdx.x == 0 && (s_fail || s_efail)) atomicAdd(&err[ERR_CHOL], 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 2)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(2 * 128));
 }
 
 // [rows][128] FP32 operand rows, boxes of 32 columns (one 128-byte swizzle row) x 128 rows
@@ -438,6 +500,12 @@ int chol_tc(Mesh *m, float *A, int64_t n) {
                                        (int)kTrailSmem));
         attr = true;
     }
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        FEM3_CUDA(cudaGetDevice(&dev));
+        FEM3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
     const int npan = (int)((n + kP - 1) / kP);
     CholCtx *cx = nullptr;
     FEM3_TRY(ctx_acquire(&cx, npan));
@@ -479,8 +547,9 @@ int chol_tc(Mesh *m, float *A, int64_t n) {
         }
         const int64_t nb_rest = T * (T + 1) / 2 - T;
         if (nb_rest > 0) {
-            k_cholp_trail<<<(unsigned)nb_rest, 128, kTrailSmem, s1>>>(maps[b][0], maps[b][1], A, n,
-                                                                     t0, 2, m->err);
+            const int g = (int)std::min<int64_t>(nb_rest, std::max(1, sms - kReservedSms));
+            k_cholp_trail<<<g, kTrailThreads, kTrailSmem, s1>>>(maps[b][0], maps[b][1], A, n, t0, 2,
+                                                               (int)nb_rest, m->err);
             note_launch(m);
             if (!launch_ok("k_cholp_trail")) break;
         }
@@ -493,8 +562,8 @@ int chol_tc(Mesh *m, float *A, int64_t n) {
             st = cuda_error(cudaGetLastError(), "cudaStreamWaitEvent");
             break;
         }
-        k_cholp_trail<<<(unsigned)T, 128, kTrailSmem, s>>>(maps[b][0], maps[b][1], A, n, t0, 1,
-                                                           m->err);
+        k_cholp_trail<<<(unsigned)std::min<int64_t>(T, kReservedSms), kTrailThreads, kTrailSmem,
+                        s>>>(maps[b][0], maps[b][1], A, n, t0, 1, (int)T, m->err);
         note_launch(m);
         if (!launch_ok("k_cholp_trail")) break;
     }

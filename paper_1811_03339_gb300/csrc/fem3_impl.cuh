@@ -273,7 +273,7 @@ int axis_forms(Mesh *m, const double *u_d, const double *lam_d, double out[3]);
 int read_errors(Mesh *m, int32_t *h_err);
 int trsm_batch(const BatchTrsmDesc *d_desc, int n_mesh, int max_nblk, int nrhs, bool fp64,
                cudaStream_t s);
-int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d);
+int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d, bool df = true);
 int f32_to_f64(const float *a, double *b, int64_t n, cudaStream_t s);
 int sym_from_lower(double *A, int64_t n, cudaStream_t s);
 int sub_vec(const double *a, const double *b, double *c, int64_t n, cudaStream_t s);

@@ -973,6 +973,34 @@ __global__ void k_residual_cols(const double *__restrict__ b, const double *__re
     }
 }
 
+// r -= Ad (the late sweeps' residual update) with the norms of r and b per column
+__global__ void k_residual_update_cols(const double *__restrict__ b, const double *__restrict__ Ad,
+                                       int64_t n, double *r, double *norms) {
+    const int c = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double rr = 0, bb = 0;
+    if (i < n) {
+        const int64_t k = (int64_t)c * n + i;
+        const double v = r[k] - Ad[k];
+        r[k] = v;
+        rr = v * v;
+        bb = b[k] * b[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_down_sync(0xffffffffu, rr, o);
+        bb += __shfl_down_sync(0xffffffffu, bb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&norms[2 * c], rr);
+        atomicAdd(&norms[2 * c + 1], bb);
+    }
+}
+
+__global__ void k_f32_to_f64_n(const float *__restrict__ a, double *b, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
 // ui[i][v] = u[v * n + i] for v < nv, zero for nv <= v < NR (NR = 4 or 8 vectors a pass)
 template <int NR>
 __global__ void k_interleave(const double *__restrict__ u, int64_t n, int nv, double *ui) {
@@ -1206,7 +1234,10 @@ struct ApplyAxes {
 };
 
 // grid: the bins of the three axes (block x -> axis, bin)
-template <int NR>
+// DF = false: the same operator in plain FP32 arithmetic (hi parts of the table pairs and of
+// u, FMA accumulation), about 1e-6 relative: the refinement's late sweeps, whose residual
+// update r -= A d has a tiny correction d (see solve_refined)
+template <int NR, bool DF = true>
 __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_constant__ ApplyAxes P,
                                                              const double *__restrict__ u, int nv,
                                                              double *Au, int64_t ldA) {
@@ -1257,8 +1288,13 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
 #pragma unroll
                 for (int v = 0; v < NR; v++) {
                     const float2 uv = us[r * NR + v];
-                    df_fma(lv.x, lv.y, uv.x, uv.y, lh[v], ll[v]);
-                    df_fma(rv.x, rv.y, uv.x, uv.y, rh[v], rl[v]);
+                    if constexpr (DF) {
+                        df_fma(lv.x, lv.y, uv.x, uv.y, lh[v], ll[v]);
+                        df_fma(rv.x, rv.y, uv.x, uv.y, rh[v], rl[v]);
+                    } else {
+                        lh[v] = fmaf(lv.x, uv.x, lh[v]);
+                        rh[v] = fmaf(rv.x, uv.x, rh[v]);
+                    }
                 }
             }
             rc_last = rc0;
@@ -1275,8 +1311,13 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
 #pragma unroll
             for (int w = 1; w < 8; w++) {
                 const float2 x = pL[w * kApplyGC * NR + e], z = pR[w * kApplyGC * NR + e];
-                df_add(x.x, x.y, ah, al);
-                df_add(z.x, z.y, ch, cl);
+                if constexpr (DF) {
+                    df_add(x.x, x.y, ah, al);
+                    df_add(z.x, z.y, ch, cl);
+                } else {
+                    ah += x.x;
+                    ch += z.x;
+                }
             }
             yL[e] = make_float2(ah, al);
             yR[e] = make_float2(ch, cl);
@@ -1304,20 +1345,31 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
                     for (int v = 0; v < NR; v++) {
                         const float2 a0 = yR[2 * g2 * NR + v], q0 = yL[2 * g2 * NR + v];
                         const float2 a1 = yR[(2 * g2 + 1) * NR + v], q1 = yL[(2 * g2 + 1) * NR + v];
-                        df_fma(lv.x, lv.y, a0.x, a0.y, zh[v], zl[v]);
-                        df_fma(rv.x, rv.y, q0.x, q0.y, zh[v], zl[v]);
-                        df_fma(lv.z, lv.w, a1.x, a1.y, zh[v], zl[v]);
-                        df_fma(rv.z, rv.w, q1.x, q1.y, zh[v], zl[v]);
+                        if constexpr (DF) {
+                            df_fma(lv.x, lv.y, a0.x, a0.y, zh[v], zl[v]);
+                            df_fma(rv.x, rv.y, q0.x, q0.y, zh[v], zl[v]);
+                            df_fma(lv.z, lv.w, a1.x, a1.y, zh[v], zl[v]);
+                            df_fma(rv.z, rv.w, q1.x, q1.y, zh[v], zl[v]);
+                        } else {
+                            zh[v] = fmaf(lv.x, a0.x, zh[v]);
+                            zh[v] = fmaf(rv.x, q0.x, zh[v]);
+                            zh[v] = fmaf(lv.z, a1.x, zh[v]);
+                            zh[v] = fmaf(rv.z, q1.x, zh[v]);
+                        }
                     }
                 }
                 const int64_t dof = dof_idx[d0 + rc0 + r];
 #pragma unroll
                 for (int v = 0; v < NR; v++) {
                     if (v >= nv) break;
-                    float ph, pl;
-                    df_mul(zh[v], zl[v], sKh, sKl, ph, pl);
-                    atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(ph));
-                    atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(pl));
+                    if constexpr (DF) {
+                        float ph, pl;
+                        df_mul(zh[v], zl[v], sKh, sKl, ph, pl);
+                        atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(ph));
+                        atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(pl));
+                    } else {
+                        atomicAdd(&Au[(int64_t)v * ldA + dof], (double)(zh[v] * sKh));
+                    }
                 }
             }
         }
@@ -1329,7 +1381,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
 // group of one or up to four vectors takes the narrower form of the kernel (the pass costs
 // about its vectors' arithmetic: an eight-wide pass for one leftover vector cost as much as
 // a full group).
-int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
+int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d, bool df) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
     FEM3_CUDA(cudaMemsetAsync(Au_d, 0, sizeof(double) * n * nv, s));
@@ -1340,6 +1392,15 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
         FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)apply_bin_smem<4>()));
         FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)apply_bin_smem<8>()));
+        FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<1, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)apply_bin_smem<1>()));
+        FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<4, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)apply_bin_smem<4>()));
+        FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<8, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)apply_bin_smem<8>()));
         attr = true;
     }
@@ -1368,16 +1429,20 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
             note_launch(m);
         }
         kc_begin(m, KC_APPLY);
+#define FEM3_APPLY(NR_, DF_, U_, CNT_)                                                          \
+    k_apply_bin<NR_, DF_><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<NR_>(), s>>>(P, U_, CNT_, \
+                                                                                   out, n)
         if (cnt == 1) {
-            k_apply_bin<1><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<1>(), s>>>(
-                P, u_d + (int64_t)v0 * n, 1, out, n);
+            if (df) FEM3_APPLY(1, true, u_d + (int64_t)v0 * n, 1);
+            else FEM3_APPLY(1, false, u_d + (int64_t)v0 * n, 1);
         } else if (cnt <= 4) {
-            k_apply_bin<4><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<4>(), s>>>(
-                P, ui, cnt, out, n);
+            if (df) FEM3_APPLY(4, true, ui, cnt);
+            else FEM3_APPLY(4, false, ui, cnt);
         } else {
-            k_apply_bin<8><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<8>(), s>>>(
-                P, ui, cnt, out, n);
+            if (df) FEM3_APPLY(8, true, ui, cnt);
+            else FEM3_APPLY(8, false, ui, cnt);
         }
+#undef FEM3_APPLY
         kc_end(m, KC_APPLY);
         note_launch(m);
     }
@@ -1386,7 +1451,7 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d) {
     return FEM3_OK;
 }
 
-int apply_A64(Mesh *m, const double *u_d, double *Au_d) { return apply_multi(m, u_d, 1, Au_d); }
+int apply_A64(Mesh *m, const double *u_d, double *Au_d) { return apply_multi(m, u_d, 1, Au_d, true); }
 
 int axis_forms(Mesh *m, const double *u_d, const double *lam_d, double out[3]) {
     cudaStream_t s = m->stream;
@@ -1418,23 +1483,31 @@ int solve_direct(Mesh *m, const double *b_d, int nrhs, double *u_d) {
 
 // Refinement for all right-hand sides together: u = 0, r = b; repeat
 //   d = A32^{-1} r (FP32 factor, all columns in one wavefront sweep pair), u += d,
-//   r = b - A u (FP64 operator from the tables), until every column has
-//   ||r|| <= tol ||b|| or max_iter sweeps.
+//   r = b - A u (FP64 operator from the tables, double-float arithmetic),
+// until every column has ||r|| <= tol ||b|| or max_iter sweeps.  Once the residual is below
+// kLateFactor * tol, a sweep's residual is updated from its correction alone,
+// r = r - A d, with A d applied in plain FP32 (about 1e-6 relative): d is as small as r, so
+// the update's error is about 1e-6 ||r|| <= 1e-6 kLateFactor tol ||b|| = tol ||b|| / 100,
+// while the double-float apply of A u costs six times the instructions.
+constexpr double kLateFactor = 1e4;
+
 int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter, double *u_d,
                   int *iters, double *resid) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
     const int64_t nn = n * nrhs;
     if (nrhs > 32) return set_error(FEM3_E_ARG, "at most 32 right-hand sides per solve");
-    double *Au = nullptr, *r = nullptr;
+    double *Au = nullptr, *r = nullptr, *d64 = nullptr;
     float *r32 = nullptr;
     FEM3_CUDA(cudaMallocAsync((void **)&Au, sizeof(double) * nn, s));
     FEM3_CUDA(cudaMallocAsync((void **)&r, sizeof(double) * nn, s));
+    FEM3_CUDA(cudaMallocAsync((void **)&d64, sizeof(double) * nn, s));
     FEM3_CUDA(cudaMallocAsync((void **)&r32, sizeof(float) * nn, s));
     FEM3_CUDA(cudaMemsetAsync(u_d, 0, sizeof(double) * nn, s));
     FEM3_CUDA(cudaMemcpyAsync(r, b_d, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
     int it = 0;
     double worst = 1.0;
+    bool late = false;
     int st = FEM3_OK;
     for (;;) {
         k_to_f32<<<g256(nn), 256, 0, s>>>(r, r32, nn);
@@ -1444,9 +1517,16 @@ int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter
         if (st != FEM3_OK) break;
         k_axpy_f32<<<g256(nn), 256, 0, s>>>(r32, u_d, nn);
         note_launch(m);
-        if ((st = apply_multi(m, u_d, nrhs, Au)) != FEM3_OK) break;
         FEM3_CUDA(cudaMemsetAsync(m->norms, 0, sizeof(double) * 2 * nrhs, s));
-        k_residual_cols<<<dim3(g256(n), nrhs), 256, 0, s>>>(b_d, Au, n, r, m->norms);
+        if (late) {
+            k_f32_to_f64_n<<<g256(nn), 256, 0, s>>>(r32, d64, nn);
+            note_launch(m);
+            if ((st = apply_multi(m, d64, nrhs, Au, false)) != FEM3_OK) break;
+            k_residual_update_cols<<<dim3(g256(n), nrhs), 256, 0, s>>>(b_d, Au, n, r, m->norms);
+        } else {
+            if ((st = apply_multi(m, u_d, nrhs, Au, true)) != FEM3_OK) break;
+            k_residual_cols<<<dim3(g256(n), nrhs), 256, 0, s>>>(b_d, Au, n, r, m->norms);
+        }
         note_launch(m);
         FEM3_CUDA(cudaMemcpyAsync(m->h_norms, m->norms, sizeof(double) * 2 * nrhs,
                                   cudaMemcpyDeviceToHost, s));
@@ -1458,7 +1538,9 @@ int solve_refined(Mesh *m, const double *b_d, int nrhs, double tol, int max_iter
         }
         it++;
         if (worst <= tol || it >= max_iter || !(worst < INFINITY)) break;
+        late = worst <= kLateFactor * tol;
     }
+    cudaFreeAsync(d64, s);
     cudaFreeAsync(Au, s);
     cudaFreeAsync(r, s);
     cudaFreeAsync(r32, s);
