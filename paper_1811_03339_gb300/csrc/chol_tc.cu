@@ -6,17 +6,20 @@
 // product).
 //
 // Per panel of P = 128 columns [j0, j0 + P):
-//   1. k_cholp_diag (one CTA): the 128 x 128 diagonal block as two 64 x 64 blocks -
-//      factor and invert D11, L21 = A21 L11^{-T}, factor and invert D22 - L21 L21^T - and
-//      the panel's inverse [[X11, 0], [-X22 L21 X11, X22]]; the 64 x 64 inverses go to dinv
-//      and L21 to A, the layout the triangular-solve chains read (the strictly lower
-//      64 x 64 tiles of A hold L; a diagonal tile is only ever used through its inverse);
-//   2. k_cholp_panel: L[i, panel] = A[i, panel] X^T for every row i below the panel, into
-//      A and, split into TF32 hi + lo pairs, into the K-major operand rows W_hi, W_lo;
-//   3. k_cholp_trail: A[I, J] -= W_I W_J^T over the 128 x 128 tiles I >= J of the trailing
-//      matrix, TMA loads (128-byte swizzle) into a two-stage ring, three MMAs per 32-column
-//      K step (hi hi, hi lo, lo hi) into a TMEM accumulator, and a read-modify-write
-//      epilogue of the tile (the lower triangle on diagonal tiles).
+//   1. k_cholp_diag (one CTA): the 128 x 128 diagonal block as two 64 x 64 blocks - factor
+//      and invert D11 (X11 = L11^{-1}), L21 = A21 X11^T, factor and invert D22 - L21 L21^T;
+//      X11 and X22 go to dinv and L21 to A, the layout the triangular-solve chains read (the
+//      strictly lower 64 x 64 tiles of A hold L; a diagonal tile is only used through its
+//      inverse), and [X11 | X22 | L21] to the panel solve;
+//   2. k_cholp_panel: for every row below the panel, L[:, 0:64] = A[:, 0:64] X11^T and
+//      L[:, 64:128] = (A[:, 64:128] - L[:, 0:64] L21^T) X22^T, into A and, split into TF32
+//      hi + lo pairs, into the K-major operand rows W_hi, W_lo;
+//   3. k_cholp_trail (persistent): A[I, J] -= W_I W_J^T over the 128 x 128 tiles I >= J of
+//      the trailing matrix - TMA loads (128-byte swizzle) into a two-stage ring, three MMAs
+//      per 32-column K step (hi hi, hi lo, lo hi) into one of two TMEM accumulators, and an
+//      epilogue (eight warps) that overlaps the next tile's MMAs.
+// Look-ahead: the next panel's block column is updated on the caller's stream and the rest of
+// the trailing matrix on a side stream, so the next diagonal block and panel overlap it.
 // No kernel waits for another CTA; the mbarrier waits are bounded (ERR_CHOL on expiry).
 #include <math.h>
 
@@ -37,9 +40,8 @@ constexpr int kWaitLimit = 1 << 22;
 
 constexpr int kP = 128;                        // panel width
 constexpr int kLd = NB + 1;                    // shared 64 x 64 block row stride
-constexpr int kDiagSmemFloats = 5 * NB * kLd;  // a_s, x_s, b_s (A21 -> L21), x11, t
+constexpr int kDiagSmemFloats = 6 * NB * kLd;  // a_s, x_s, b_s (A21 -> L21), x11, t, A22
 constexpr int kPanelRows = 64;                 // rows of a panel-solve CTA
-constexpr int kPLd = kP + 4;                   // shared row stride of the panel solve
 constexpr uint32_t kTile = 128 * 128;          // bytes of one 128-row x 128-byte TMA box
 constexpr uint32_t kStage = 4 * kTile;         // A hi, A lo, B hi, B lo: 64 KB
 constexpr int kStages = 2;
@@ -71,21 +73,27 @@ __device__ __forceinline__ void smem_gemm64(float (*c)[kLd], const float (*a)[kL
     __syncthreads();
 }
 
-// one CTA of 512 threads: the diagonal block [j0, j0 + nbp) of A (nbp <= 128)
+// one CTA of 512 threads: the diagonal block [j0, j0 + nbp) of A (nbp <= 128).  Every global
+// load of the block is issued first; then D11 = L11 L11^T with X11 = L11^{-1}, L21 = A21 X11^T,
+// D22 - L21 L21^T = L22 L22^T with X22 = L22^{-1}.  Out: X11, X22 into dinv (the
+// triangular-solve chains' diagonal inverses), L21 into A, and [X11 | X22 | L21] (three
+// 64 x 64 blocks, row-major) into Pinv for the panel solve.
 __global__ void __launch_bounds__(512, 1) k_cholp_diag(float *A, int64_t n, int64_t j0, int nbp,
-                                                       float *dinv, float *Linv, int32_t *err) {
+                                                       float *dinv, float *Pinv, int32_t *err) {
     extern __shared__ __align__(16) float sm_diag[];
     float(*a_s)[kLd] = reinterpret_cast<float(*)[kLd]>(sm_diag);
     float(*x_s)[kLd] = a_s + NB;
-    float(*b_s)[kLd] = x_s + NB;
+    float(*b_s)[kLd] = x_s + NB;   // A21, then L21
     float(*x11)[kLd] = b_s + NB;
-    float(*t_s)[kLd] = x11 + NB;
+    float(*t_s)[kLd] = x11 + NB;   // L21 L21^T
+    float(*d22)[kLd] = t_s + NB;   // A22 as loaded
     const int tid = threadIdx.x;
     const int nb1 = min(NB, nbp), nb2 = nbp - nb1;
-    // D11, identity past the block's end
     for (int e = tid; e < NB * NB; e += 512) {
         const int i = e >> 6, c = e & 63;
         a_s[i][c] = (i < nb1 && c < nb1) ? A[(j0 + i) * n + j0 + c] : (i == c ? 1.f : 0.f);
+        b_s[i][c] = (i < nb2) ? A[(j0 + NB + i) * n + j0 + c] : 0.f;
+        d22[i][c] = (i < nb2 && c < nb2) ? A[(j0 + NB + i) * n + j0 + NB + c] : (i == c ? 1.f : 0.f);
     }
     __syncthreads();
     potrf_inv_smem<float>(a_s, x_s, nb1, j0, err);
@@ -94,105 +102,124 @@ __global__ void __launch_bounds__(512, 1) k_cholp_diag(float *A, int64_t n, int6
         const int i = e >> 6, c = e & 63;
         d1[e] = x_s[i][c];
         x11[i][c] = x_s[i][c];
+        Pinv[e] = x_s[i][c];
     }
     if (nb2 > 0) {
-        // L21 = A21 X11^T (rows past the block's end are zero)
-        for (int e = tid; e < NB * NB; e += 512) {
-            const int i = e >> 6, c = e & 63;
-            b_s[i][c] = (i < nb2) ? A[(j0 + NB + i) * n + j0 + c] : 0.f;
-        }
         __syncthreads();
-        smem_gemm64<true>(b_s, b_s, x11, 1.f, false);          // b_s = L21
-        for (int e = tid; e < NB * NB; e += 512) {
-            const int i = e >> 6, c = e & 63;
-            if (i < nb2) A[(j0 + NB + i) * n + j0 + c] = b_s[i][c];
-            a_s[i][c] = (i < nb2 && c < nb2) ? A[(j0 + NB + i) * n + j0 + NB + c]
-                                             : (i == c ? 1.f : 0.f);
-        }
-        __syncthreads();
-        // D22 - L21 L21^T (the identity padding stays: L21's padded rows are zero)
+        smem_gemm64<true>(b_s, b_s, x11, 1.f, false);          // b_s = L21 = A21 X11^T
         smem_gemm64<true>(t_s, b_s, b_s, 1.f, false);          // t = L21 L21^T
         for (int e = tid; e < NB * NB; e += 512) {
             const int i = e >> 6, c = e & 63;
-            a_s[i][c] -= t_s[i][c];
+            if (i < nb2) A[(j0 + NB + i) * n + j0 + c] = b_s[i][c];
+            Pinv[2 * NB * NB + e] = b_s[i][c];
+            // the identity padding stays: L21's padded rows are zero
+            a_s[i][c] = d22[i][c] - t_s[i][c];
         }
         __syncthreads();
         potrf_inv_smem<float>(a_s, x_s, nb2, j0 + NB, err);    // x_s = X22
         float *d2 = d1 + (int64_t)NB * NB;
-        for (int e = tid; e < NB * NB; e += 512) d2[e] = x_s[e >> 6][e & 63];
-        // X21 = -X22 (L21 X11)
-        smem_gemm64<false>(t_s, b_s, x11, 1.f, false);         // t = L21 X11
-        smem_gemm64<false>(b_s, x_s, t_s, -1.f, false);        // b_s = X21
-    }
-    // the panel inverse [[X11, 0], [X21, X22]] (128 x 128, zero past nbp)
-    for (int e = tid; e < kP * kP; e += 512) {
-        const int i = e >> 7, c = e & 127;
-        float v = 0.f;
-        if (i < NB && c < NB) v = x11[i][c];
-        else if (i >= NB && nb2 > 0 && c < NB) v = b_s[i - NB][c];
-        else if (i >= NB && nb2 > 0 && c >= NB) v = x_s[i - NB][c - NB];
-        Linv[e] = v;
+        for (int e = tid; e < NB * NB; e += 512) {
+            d2[e] = x_s[e >> 6][e & 63];
+            Pinv[NB * NB + e] = x_s[e >> 6][e & 63];
+        }
     }
 }
 
 // ------------------------------- panel solve --------------------------------------
-// rows [r0, r0 + 64) below the panel: L[i][c] = sum_{k <= c} A[i][j0 + k] X[c][k]; written
-// to A and, as TF32 hi + lo, to W rows i - t0 (t0 = j0 + P, the first trailing row)
+// rows [r0, r0 + 64) below the panel (r0 >= t0 = j0 + P), in two 64-column steps:
+//   L[:, 0:64]   = A[:, 0:64] X11^T
+//   L[:, 64:128] = (A[:, 64:128] - L[:, 0:64] L21^T) X22^T
+// written to A and, as TF32 hi + lo, to the operand rows W[i - t0] of the trailing update.
+// 256 threads, each 4 rows x 4 columns of every 64 x 64 product.
+constexpr int kQ = 68;   // shared row stride (floats) of the 64-wide blocks: 16-byte rows
+__device__ __forceinline__ void panel_gemm64(const float (*a)[kQ], const float (*bt)[kQ],
+                                             float acc[4][4], int ty, int tx) {
+    // acc[p][q] += sum_k a[4 ty + p][k] bt[k][4 tx + q]
+#pragma unroll 4
+    for (int k = 0; k < 64; k++) {
+        const float4 b4 = *reinterpret_cast<const float4 *>(&bt[k][4 * tx]);
+        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            const float av = a[4 * ty + p][k];
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[p][q] = fmaf(av, bv[q], acc[p][q]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_cholp_panel(float *A, int64_t n, int64_t j0,
-                                                     const float *__restrict__ Linv, float *Whi,
+                                                     const float *__restrict__ Pinv, float *Whi,
                                                      float *Wlo) {
     extern __shared__ __align__(16) float sm_panel[];
-    float(*xt)[kPLd] = reinterpret_cast<float(*)[kPLd]>(sm_panel);   // xt[k][c] = X[c][k]
-    float(*as)[kPLd] = xt + kP;                                       // as[r][k]
+    float(*x11t)[kQ] = reinterpret_cast<float(*)[kQ]>(sm_panel);   // x11t[k][c] = X11[c][k]
+    float(*x22t)[kQ] = x11t + 64;                                    // x22t[k][c] = X22[c][k]
+    float(*l21t)[kQ] = x22t + 64;                                    // l21t[k][c] = L21[c][k]
+    float(*a1)[kQ] = l21t + 64;   // A[:, 0:64], then L[:, 0:64]
+    float(*a2)[kQ] = a1 + 64;     // A[:, 64:128], then T, then L[:, 64:128]
     const int tid = threadIdx.x;
     const int64_t t0 = j0 + kP;
     const int64_t r0 = t0 + (int64_t)blockIdx.x * kPanelRows;
-    for (int e = tid; e < kP * kP; e += 256) {
-        const int c = e >> 7, k = e & 127;
-        xt[k][c] = Linv[e];
+    for (int e = tid; e < 64 * 64; e += 256) {
+        const int c = e >> 6, k = e & 63;
+        x11t[k][c] = Pinv[e];
+        x22t[k][c] = Pinv[64 * 64 + e];
+        l21t[k][c] = Pinv[2 * 64 * 64 + e];
     }
     for (int e = tid; e < kPanelRows * kP; e += 256) {
         const int r = e >> 7, k = e & 127;
-        as[r][k] = r0 + r < n ? A[(r0 + r) * n + j0 + k] : 0.f;
+        const float v = r0 + r < n ? A[(r0 + r) * n + j0 + k] : 0.f;
+        if (k < 64) a1[r][k] = v; else a2[r][k - 64] = v;
     }
     __syncthreads();
-    const int ty = tid >> 4, tx = tid & 15;   // rows 4 ty .. 4 ty + 3, columns 8 tx .. 8 tx + 7
-    float acc[4][8];
+    const int ty = tid >> 4, tx = tid & 15;
+    float acc[4][4];
+    // L1 = A1 X11^T
 #pragma unroll
     for (int p = 0; p < 4; p++)
 #pragma unroll
-        for (int q = 0; q < 8; q++) acc[p][q] = 0.f;
-    for (int k = 0; k < kP; k++) {
-        float a[4], b[8];
+        for (int q = 0; q < 4; q++) acc[p][q] = 0.f;
+    panel_gemm64(a1, x11t, acc, ty, tx);
+    __syncthreads();
 #pragma unroll
-        for (int p = 0; p < 4; p++) a[p] = as[4 * ty + p][k];
-        const float4 b0 = *reinterpret_cast<const float4 *>(&xt[k][8 * tx]);
-        const float4 b1 = *reinterpret_cast<const float4 *>(&xt[k][8 * tx + 4]);
-        b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
-        b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+    for (int p = 0; p < 4; p++)
 #pragma unroll
-        for (int p = 0; p < 4; p++)
+        for (int q = 0; q < 4; q++) a1[4 * ty + p][4 * tx + q] = acc[p][q];
+    __syncthreads();
+    // T = A2 - L1 L21^T
 #pragma unroll
-            for (int q = 0; q < 8; q++) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
-    }
+    for (int p = 0; p < 4; p++)
 #pragma unroll
-    for (int p = 0; p < 4; p++) {
-        const int64_t i = r0 + 4 * ty + p;
+        for (int q = 0; q < 4; q++) acc[p][q] = 0.f;
+    panel_gemm64(a1, l21t, acc, ty, tx);
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) a2[4 * ty + p][4 * tx + q] -= acc[p][q];
+    __syncthreads();
+    // L2 = T X22^T
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[p][q] = 0.f;
+    panel_gemm64(a2, x22t, acc, ty, tx);
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) a2[4 * ty + p][4 * tx + q] = acc[p][q];
+    __syncthreads();
+    // stores: A rows (lanes along the row) and the TF32 hi / lo operand rows
+    for (int e = tid; e < kPanelRows * kP; e += 256) {
+        const int r = e >> 7, k = e & 127;
+        const int64_t i = r0 + r;
         if (i >= n) continue;
-        float hi[8], lo[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            hi[q] = tf32_rna(acc[p][q]);
-            lo[q] = tf32_rna(acc[p][q] - hi[q]);
-        }
-        float *dst = A + i * n + j0 + 8 * tx;
-        float *wh = Whi + (i - t0) * kP + 8 * tx, *wl = Wlo + (i - t0) * kP + 8 * tx;
-#pragma unroll
-        for (int q = 0; q < 8; q++) dst[q] = acc[p][q];
-        *reinterpret_cast<float4 *>(wh) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<float4 *>(wh + 4) = make_float4(hi[4], hi[5], hi[6], hi[7]);
-        *reinterpret_cast<float4 *>(wl) = make_float4(lo[0], lo[1], lo[2], lo[3]);
-        *reinterpret_cast<float4 *>(wl + 4) = make_float4(lo[4], lo[5], lo[6], lo[7]);
+        const float v = k < 64 ? a1[r][k] : a2[r][k - 64];
+        A[i * n + j0 + k] = v;
+        const float hi = tf32_rna(v);
+        Whi[(i - t0) * kP + k] = hi;
+        Wlo[(i - t0) * kP + k] = tf32_rna(v - hi);
     }
 }
 
@@ -478,7 +505,7 @@ int chol_tc(Mesh *m, float *A, int64_t n) {
     cudaStream_t s = m->stream;
     const int64_t wrows = std::max<int64_t>(128, (n + 127) / 128 * 128);
     if (!m->chol_w || m->chol_w_rows < wrows) {
-        FEM3_TRY(dev_alloc(m, (void **)&m->chol_w, sizeof(float) * (4 * wrows * kP + kP * kP)));
+        FEM3_TRY(dev_alloc(m, (void **)&m->chol_w, sizeof(float) * (4 * wrows * kP + 3 * 64 * 64)));
         m->chol_w_rows = wrows;
         // operand rows past the trailing matrix are read by the edge tiles' MMAs (their
         // products are masked in the epilogue): keep them finite
@@ -486,7 +513,7 @@ int chol_tc(Mesh *m, float *A, int64_t n) {
     }
     float *W[2][2] = {{m->chol_w, m->chol_w + wrows * kP},
                       {m->chol_w + 2 * wrows * kP, m->chol_w + 3 * wrows * kP}};
-    float *Linv = m->chol_w + 4 * wrows * kP;
+    float *Linv = m->chol_w + 4 * wrows * kP;   // [X11 | X22 | L21] of the current panel
     CUtensorMap maps[2][2];
     for (int b = 0; b < 2; b++)
         for (int h = 0; h < 2; h++) FEM3_TRY(make_w_map(&maps[b][h], W[b][h], wrows));
@@ -495,7 +522,7 @@ int chol_tc(Mesh *m, float *A, int64_t n) {
         FEM3_CUDA(cudaFuncSetAttribute(k_cholp_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(float) * kDiagSmemFloats)));
         FEM3_CUDA(cudaFuncSetAttribute(k_cholp_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(float) * (kP + kPanelRows) * kPLd)));
+                                       (int)(sizeof(float) * 5 * 64 * kQ)));
         FEM3_CUDA(cudaFuncSetAttribute(k_cholp_trail, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kTrailSmem));
         attr = true;
@@ -535,8 +562,7 @@ int chol_tc(Mesh *m, float *A, int64_t n) {
         if (mt <= 0) break;
         const int b = p & 1;
         k_cholp_panel<<<(unsigned)((mt + kPanelRows - 1) / kPanelRows), 256,
-                        sizeof(float) * (kP + kPanelRows) * kPLd, s>>>(A, n, j0, Linv, W[b][0],
-                                                                       W[b][1]);
+                        sizeof(float) * 5 * 64 * kQ, s>>>(A, n, j0, Linv, W[b][0], W[b][1]);
         note_launch(m);
         if (!launch_ok("k_cholp_panel")) break;
         const int64_t T = (mt + 127) / 128;
