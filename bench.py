@@ -51,6 +51,7 @@ FP64_TFLOPS = FP32_FMA_TFLOPS / 64                      # 1.26
 WALK_BYTES_PER_SEGMENT = 160      # one tet record read per walked segment
 WALK_FP64_FLOPS_PER_SEGMENT = 25
 DF_OPS_PER_PRODUCT = 13           # FP32 instructions of one double-float multiply-add
+CHOL_TC_MIN_N = 4096              # the library's blocked tensor-core factorisation from this order
 
 
 def _peaks():
@@ -65,7 +66,12 @@ def _peaks():
 # profiles/), valid only for the source file they were taken on (sha256) and for the units
 # of work of that capture; the bench scales them to its own launch by the units processed
 # and reports null when the source has changed since the capture.
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu capture of one launch on the 16^3 jittered cube (16,099,980 segments)
+    "k_walk_tables": {"source": "walk.cu",
+                      "sha256": "4e2c8962c5f01a637b7099c0894a65296071a091c7cc0344e7934c3e88eb9bed",
+                      "bytes": 164346112 + 583106304, "units": 16099980},
+}
 
 
 def _source_sha(name):
@@ -173,13 +179,26 @@ def kernel_rooflines(kms: dict, cnt: dict, n_dof: int, precision: str, peaks: di
     f = kms.get("factor", (0, 0))
     if f[0] > 0:
         fl = n_dof ** 3 / 3.0
-        peak = FP64_TFLOPS if precision == "fp64" else FP32_FMA_TFLOPS
-        ach = fl / (f[0] * 1e-3) / 1e12
-        out["factor"] = {"kernel": "k_chol_tiles", "bound": "alu", "unit": "TFLOP/s",
-                         "achieved": ach, "peak": peak, "frac": ach / peak, "launches": f[1],
-                         "launch_ms": f[0] / f[1], "traffic": None,
-                         "algorithmic": f"n^3/3 flops, n = {n_dof}",
-                         "peak_basis": "CUDA-core FMA rate from unit counts and clocks"}
+        if precision != "fp64" and n_dof >= CHOL_TC_MIN_N:
+            # blocked factorisation: the trailing updates (nearly all of n^3/3) run as three
+            # TF32 split products on the tensor cores; the time is the factorisation's wall
+            # time on the launch stream (diagonal chain and side-stream update together)
+            peak = float(peaks.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
+            ach = 3.0 * fl / (f[0] * 1e-3) / 1e12
+            out["factor"] = {"kernel": "k_cholp_trail (+ k_cholp_diag, k_cholp_panel)",
+                             "bound": "tensor", "unit": "TFLOP/s", "achieved": ach, "peak": peak,
+                             "frac": ach / peak, "launches": f[1], "launch_ms": f[0] / f[1],
+                             "traffic": None,
+                             "algorithmic": f"3 x n^3/3 split-product flops, n = {n_dof}; "
+                                            f"{fl / (f[0] * 1e-3) / 1e12:.1f} TFLOP/s of n^3/3"}
+        else:
+            peak = FP64_TFLOPS if precision == "fp64" else FP32_FMA_TFLOPS
+            ach = fl / (f[0] * 1e-3) / 1e12
+            out["factor"] = {"kernel": "k_chol_tiles", "bound": "alu", "unit": "TFLOP/s",
+                             "achieved": ach, "peak": peak, "frac": ach / peak, "launches": f[1],
+                             "launch_ms": f[0] / f[1], "traffic": None,
+                             "algorithmic": f"n^3/3 flops, n = {n_dof}",
+                             "peak_basis": "CUDA-core FMA rate from unit counts and clocks"}
     ch = kms.get("chain", (0, 0))
     if ch[0] > 0:
         esz = 8 if precision == "fp64" else 4
