@@ -326,7 +326,8 @@ int fem3_tc_tile(fem3_mesh m, int32_t *tile_n, int32_t *tuned);
  *   Synchronises `stream`.
  * fem3_batch_mesh - the handle of mesh i (owned by the batch: do not free it); use it
  *   for fem3_mesh_info, fem3_paths or fem3_table_rows.
- * fem3_batch_run - assemble and solve every mesh of the batch.
+ * fem3_batch_run - assemble and solve every mesh of the batch (see also the graph note
+ *   after the declarations).
  *   One launch walks every Gauss-point line of every mesh (Section 2.2, 2.1 tables);
  *   contraction, load vector and factorisation of each mesh run on internal streams;
  *   each refinement sweep solves all meshes in one batched triangular solve.
@@ -348,6 +349,13 @@ int fem3_batch_mesh(fem3_batch b, int i, fem3_mesh *out);
 int fem3_batch_run(fem3_batch b, const double *alpha, const double *K, int precision,
                    const double *const *f, int nrhs, double tol, int max_iter, double *const *u,
                    int *iters, double *resid, void *stream);
+/* The assembly and factorisation of a run (walk, contractions, load vectors, factorisations:
+ * everything before the first refinement sweep) is captured as one CUDA graph by the second
+ * run with the same alpha, K, precision, nrhs and f pointers and replayed as one graph launch
+ * by later runs with them (the first run goes eagerly; a change of any of them captures
+ * again).  The refinement sweeps are host-driven.  fem3_batch_graph_launches reports the
+ * graph launches so far, the capturing run's own launch included (host int64). */
+int fem3_batch_graph_launches(fem3_batch b, int64_t *n);
 void fem3_batch_free(fem3_batch b);
 
 /*

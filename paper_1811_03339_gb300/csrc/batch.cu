@@ -3,6 +3,14 @@
 // contraction, load vector and factorisation of each mesh run on internal streams so
 // that small meshes overlap; each refinement sweep solves all meshes in one batched
 // block-step triangular solve and checks all residuals with a single host wait.
+//
+// The assembly and factorisation of the whole batch (walk, contractions, load vectors,
+// factorisations: everything before the first refinement sweep) is captured as one CUDA
+// graph the second time a run has the same orders, coefficients, precision, column count and
+// right-hand-side arrays, and replayed as one graph launch from then on (the first run goes
+// eagerly: it makes the allocations, the tile tuner's timings and the factorisation's side
+// streams that a capture must not make).  The refinement sweeps stay host-driven: each one
+// checks the residuals before the next.
 #include <math.h>
 
 #include <algorithm>
@@ -21,15 +29,47 @@ struct Batch {
     BatchWalkScratch ws;
     BatchTrsmDesc *d_tdesc = nullptr, *h_tdesc = nullptr;
     int max_nblk = 0;
+    // per-mesh run buffers, kept across runs (a captured graph refers to their addresses):
+    // load vector b, residual r, A u (column-major, n_dof x nrhs) and the FP32 correction
+    std::vector<double *> bv, rv, auv;
+    std::vector<float *> r32;
+    int nrhs_cap = 0;
+    // the captured assembly + factorisation and what it was captured for
+    cudaGraphExec_t exec = nullptr;
+    // the capture runs on a private stream (the caller's may be the legacy stream, which
+    // cannot be captured); it starts after the work enqueued so far on the caller's stream
+    cudaStream_t cap = nullptr;
+    cudaEvent_t cap_in = nullptr;
+    std::vector<double> key_ak;          // alpha, K
+    std::vector<const double *> key_f;   // right-hand-side arrays
+    int key_prec = -1, key_nrhs = 0;
+    int runs = 0;                        // eager runs so far
+    int graph_launches = 0;              // replays so far
 };
+
+static void free_run_buffers(Batch *b) {
+    for (double *p : b->bv) cudaFree(p);
+    for (double *p : b->rv) cudaFree(p);
+    for (double *p : b->auv) cudaFree(p);
+    for (float *p : b->r32) cudaFree(p);
+    b->bv.clear();
+    b->rv.clear();
+    b->auv.clear();
+    b->r32.clear();
+    b->nrhs_cap = 0;
+}
 
 static void batch_destroy(Batch *b) {
     if (!b) return;
     for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    free_run_buffers(b);
     for (Mesh *m : b->ms) fem3_mesh_free(reinterpret_cast<fem3_mesh>(m));
     for (cudaEvent_t e : b->done) cudaEventDestroy(e);
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->cap_in) cudaEventDestroy(b->cap_in);
     cudaFree(b->ws.d_desc);
     cudaFreeHost(b->ws.h_desc);
     cudaFree(b->d_tdesc);
@@ -134,6 +174,8 @@ int fem3_batch_create(int n_meshes, const double *const *verts, const int64_t *n
         b->done.push_back(e);
     }
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->cap_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&b->d_tdesc, sizeof(BatchTrsmDesc) * n_meshes) != cudaSuccess ||
         cudaMallocHost(&b->h_tdesc, sizeof(BatchTrsmDesc) * n_meshes) != cudaSuccess) {
         batch_destroy(b);
@@ -171,7 +213,7 @@ int fem3_batch_run(fem3_batch hb, const double *alpha, const double *K, int prec
     if (max_iter <= 0) max_iter = 50;
     const bool fp64 = precision == FEM3_FP64;
 
-    // 1. every line of every mesh: one batched walk on the caller's stream
+    // host-side state of every mesh for this run (the refinement reads it)
     for (int i = 0; i < n; i++) {
         Mesh *m = b->ms[i];
         m->stream = cs;
@@ -186,33 +228,106 @@ int fem3_batch_run(fem3_batch hb, const double *alpha, const double *K, int prec
         }
         m->precision = precision;
         m->factored = false;
+        m->ap_ready = false;
     }
-    for (int i = 0; i < n; i++) b->ms[i]->ap_ready = false;
-    FEM3_TRY(walk_tables_batch(b->ms.data(), n, alpha, cs, &b->ws));
-    FEM3_TRY(fork_to(b, cs));
+    // run buffers for nrhs columns (kept across runs)
+    if (b->nrhs_cap < nrhs) {
+        for (cudaStream_t t : b->streams) FEM3_CUDA(cudaStreamSynchronize(t));
+        FEM3_CUDA(cudaStreamSynchronize(cs));
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        free_run_buffers(b);
+        b->bv.assign(n, nullptr);
+        b->rv.assign(n, nullptr);
+        b->auv.assign(n, nullptr);
+        b->r32.assign(n, nullptr);
+        for (int i = 0; i < n; i++) {
+            const size_t nn = (size_t)std::max<int64_t>(1, b->ms[i]->n_dof * nrhs);
+            if (cudaMalloc((void **)&b->bv[i], sizeof(double) * nn) != cudaSuccess ||
+                cudaMalloc((void **)&b->rv[i], sizeof(double) * nn) != cudaSuccess ||
+                cudaMalloc((void **)&b->auv[i], sizeof(double) * nn) != cudaSuccess ||
+                cudaMalloc((void **)&b->r32[i], sizeof(float) * nn) != cudaSuccess)
+                return cuda_error(cudaGetLastError(), "cudaMalloc (batch run buffers)");
+        }
+        b->nrhs_cap = nrhs;
+    }
+    std::vector<double *> &bv = b->bv, &rv = b->rv, &auv = b->auv;
+    std::vector<float *> &r32 = b->r32;
 
-    // 2. per mesh on the internal streams: contraction, load vector, factorisation
-    std::vector<double *> bv(n, nullptr), rv(n, nullptr), auv(n, nullptr);
-    std::vector<float *> r32(n, nullptr);
+    // 1 + 2: walk of every line of every mesh (one launch on the caller's stream), then per
+    // mesh on the internal streams contraction, load vector and factorisation; replayed
+    // from the captured graph when the run matches the one it was captured for
+    std::vector<double> ak(alpha, alpha + 3 * n);
+    ak.insert(ak.end(), K, K + 3 * n);
+    std::vector<const double *> fk(f, f + n);
+    const bool same = b->exec && b->key_prec == precision && b->key_nrhs == nrhs &&
+                      b->key_ak == ak && b->key_f == fk;
+    auto enqueue_assembly = [&](cudaStream_t os) -> int {
+        FEM3_TRY(walk_tables_batch(b->ms.data(), n, alpha, os, &b->ws));
+        FEM3_TRY(fork_to(b, os));
+        for (int i = 0; i < n; i++) {
+            Mesh *m = b->ms[i];
+            m->stream = b->streams[i % b->streams.size()];
+            if (m->n_dof == 0) continue;
+            if (precision == FEM3_TF32X3 || precision == FEM3_BF16X3)
+                FEM3_TRY(contract_tc(m, precision == FEM3_BF16X3));
+            else
+                FEM3_TRY(contract(m, precision));
+            FEM3_TRY(load_vector(m, f[i], nrhs, bv[i]));
+            FEM3_TRY(factor(m));
+        }
+        FEM3_TRY(join_to(b, os));
+        return FEM3_OK;
+    };
     int st = FEM3_OK;
+    if (same) {
+        FEM3_CUDA(cudaGraphLaunch(b->exec, cs));
+        b->graph_launches++;
+    } else if (b->runs >= 1) {
+        // capture the assembly + factorisation; on any failure discard it and run eagerly
+        if (b->exec) {
+            FEM3_CUDA(cudaStreamSynchronize(cs));
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        bool captured = false;
+        FEM3_CUDA(cudaEventRecord(b->cap_in, cs));
+        FEM3_CUDA(cudaStreamWaitEvent(b->cap, b->cap_in, 0));
+        if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const int cst = enqueue_assembly(b->cap);
+            const cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+            if (cst == FEM3_OK && ce == cudaSuccess && g &&
+                cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
+                captured = true;
+                b->key_prec = precision;
+                b->key_nrhs = nrhs;
+                b->key_ak = ak;
+                b->key_f = fk;
+            }
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+        if (captured) {
+            FEM3_CUDA(cudaGraphLaunch(b->exec, cs));
+            b->graph_launches++;
+        } else {
+            b->exec = nullptr;
+            st = enqueue_assembly(cs);
+        }
+    } else {
+        st = enqueue_assembly(cs);
+        b->runs++;
+    }
+    // the first correction starts from u = 0: the residual is b
+    if (st == FEM3_OK) st = fork_to(b, cs);
     for (int i = 0; i < n && st == FEM3_OK; i++) {
         Mesh *m = b->ms[i];
         m->stream = b->streams[i % b->streams.size()];
-        const int64_t nn = std::max<int64_t>(1, m->n_dof * nrhs);
         if (m->n_dof == 0) continue;
-        if (precision == FEM3_TF32X3 || precision == FEM3_BF16X3)
-            st = contract_tc(m, precision == FEM3_BF16X3);
-        else st = contract(m, precision);
-        if (st != FEM3_OK) break;
-        cudaError_t e = cudaMallocAsync((void **)&bv[i], sizeof(double) * nn, m->stream);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&rv[i], sizeof(double) * nn, m->stream);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&auv[i], sizeof(double) * nn, m->stream);
-        if (e == cudaSuccess && !fp64) e = cudaMallocAsync((void **)&r32[i], sizeof(float) * nn, m->stream);
-        if (e != cudaSuccess) { st = cuda_error(e, "cudaMallocAsync"); break; }
-        if ((st = load_vector(m, f[i], nrhs, bv[i])) != FEM3_OK) break;
-        if ((st = factor(m)) != FEM3_OK) break;
         m->factored = true;
-        // first correction: from u = 0 the residual is b
         FEM3_CUDA(cudaMemcpyAsync(rv[i], bv[i], sizeof(double) * m->n_dof * nrhs,
                                   cudaMemcpyDeviceToDevice, m->stream));
         FEM3_CUDA(cudaMemsetAsync(u[i], 0, sizeof(double) * m->n_dof * nrhs, m->stream));
@@ -280,14 +395,7 @@ int fem3_batch_run(fem3_batch hb, const double *alpha, const double *K, int prec
         }
     }
 
-    // 4. release per-run buffers, join into the caller's stream, report
-    for (int i = 0; i < n; i++) {
-        Mesh *m = b->ms[i];
-        if (bv[i]) cudaFreeAsync(bv[i], m->stream);
-        if (rv[i]) cudaFreeAsync(rv[i], m->stream);
-        if (auv[i]) cudaFreeAsync(auv[i], m->stream);
-        if (r32[i]) cudaFreeAsync(r32[i], m->stream);
-    }
+    // 4. join into the caller's stream, report
     FEM3_TRY(join_to(b, cs));
     if (st != FEM3_OK) return st;
     int bad = FEM3_OK;
@@ -303,6 +411,13 @@ int fem3_batch_run(fem3_batch hb, const double *alpha, const double *K, int prec
                                                     ": iterative refinement did not converge");
     }
     return bad;
+}
+
+int fem3_batch_graph_launches(fem3_batch hb, int64_t *n) {
+    Batch *b = reinterpret_cast<Batch *>(hb);
+    if (!b || !n) return set_error(FEM3_E_ARG, "bad argument");
+    *n = b->graph_launches;
+    return FEM3_OK;
 }
 
 void fem3_batch_free(fem3_batch hb) { batch_destroy(reinterpret_cast<Batch *>(hb)); }

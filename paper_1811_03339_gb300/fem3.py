@@ -32,7 +32,8 @@ SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_assemble
            "fem3_last_error",
            "fem3_mesh_free",
            "fem3_spd_solve_static",
-           "fem3_batch_create", "fem3_batch_mesh", "fem3_batch_run", "fem3_batch_free")
+           "fem3_batch_create", "fem3_batch_mesh", "fem3_batch_run", "fem3_batch_graph_launches",
+           "fem3_batch_free")
 
 _lib = None
 
@@ -90,6 +91,7 @@ def load_library(build_if_missing: bool = True):
         "fem3_batch_create": [ci, p, p, p, p, C.POINTER(Options), p, C.POINTER(p)],
         "fem3_batch_mesh": [p, ci, C.POINTER(p)],
         "fem3_batch_run": [p, p, p, ci, p, ci, dbl, ci, p, p, p, p],
+        "fem3_batch_graph_launches": [p, C.POINTER(i64)],
         "fem3_batch_free": [p],
     }
     for name, args in sig.items():
@@ -490,6 +492,13 @@ class Batch:
                                    float(tol), int(max_iter), up, it, rs, _stream(self.stream)))
         self.iters, self.resid = list(it), list(rs)
         return [x.T for x in u_dev]
+
+    def graph_launches(self):
+        """launches of the captured assembly + factorisation graph so far (the capturing run's
+        own launch included)"""
+        v = C.c_int64(0)
+        _check(_lib.fem3_batch_graph_launches(self.h, C.byref(v)))
+        return v.value
 
     def free(self):
         if getattr(self, "h", None) and _lib is not None:
