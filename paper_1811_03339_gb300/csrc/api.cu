@@ -290,7 +290,7 @@ int fem3_mesh_upload(const double *verts, int64_t n_nodes, const int32_t *tets, 
     stage_end(m, 1);
     const int64_t n = std::max<int64_t>(1, m->n_dof);
     if ((st = dev_alloc_t(m, &m->flags, 2 * ((n + 63) / 64) + 2)) != FEM3_OK) return fail(st);
-    if ((st = dev_alloc(m, &m->solve_ws, sizeof(double) * 64 * 16 * ((n + 63) / 64))) != FEM3_OK)
+    if ((st = dev_alloc(m, &m->solve_ws, sizeof(double) * 64 * 24 * ((n + 63) / 64))) != FEM3_OK)
         return fail(st);
     if ((st = dev_alloc(m, &m->solve_G, sizeof(double) * 2 * 3 * 64 * 64 * ((n + 63) / 64))) != FEM3_OK)
         return fail(st);

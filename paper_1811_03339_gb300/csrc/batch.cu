@@ -285,6 +285,9 @@ int fem3_batch_run(fem3_batch hb, const double *alpha, const double *K, int prec
     if (same) {
         FEM3_CUDA(cudaGraphLaunch(b->exec, cs));
         b->graph_launches++;
+        // the replayed contraction wrote the apply operands, as the captured one did
+        const bool tc = precision == FEM3_TF32X3 || precision == FEM3_BF16X3;
+        for (Mesh *m : b->ms) m->ap_ready = tc && m->n_dof > 0;
     } else if (b->runs >= 1) {
         // capture the assembly + factorisation; on any failure discard it and run eagerly
         if (b->exec) {

@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(256) k_split_ops(
     const int32_t *__restrict__ row_bin, const int32_t *__restrict__ dof_off,
     const int32_t *__restrict__ gp_off, const double *__restrict__ w_slot,
     const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
-    int64_t row_lo, int64_t n_rows, int Kp, OT *Lhi, OT *Llo, OT *Rhi, OT *Rlo, float2 *apR) {
+    int64_t row_lo, int64_t n_rows, int Kp, OT *Lhi, OT *Llo, OT *Rhi, OT *Rlo, float2 *apR,
+    int4 *rng) {
     const int64_t row = row_lo + blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n_rows) return;
@@ -97,6 +98,8 @@ __global__ void __launch_bounds__(256) k_split_ops(
     // the GEMM reads a bin's operands up to G rounded to one 128-byte row (kbk Gauss points)
     const int kbk = 128 / (int)sizeof(OT);
     const int kend = Lhi ? min(Kp, (G + kbk - 1) / kbk * kbk) : G;
+    // Gauss-point range [first, end) of the row's nonzeros in L and in W R
+    int lf = G, le = 0, rf = G, re = 0;
     for (int k = lane; k < kend; k += 32) {
         OT lh = OT(0.f), ll = OT(0.f), rh = OT(0.f), rl = OT(0.f);
         if (k < G) {
@@ -108,6 +111,14 @@ __global__ void __launch_bounds__(256) k_split_ops(
             df_fma(r1, r2, wh, wl, sh, sl);
             const float wr = sh + sl, wr2 = sl - (wr - sh);
             apR[src + k] = make_float2(wr, wr2);
+            if (a != 0.f || a2 != 0.f) {
+                lf = min(lf, k);
+                le = k + 1;
+            }
+            if (wr != 0.f || wr2 != 0.f) {
+                rf = min(rf, k);
+                re = k + 1;
+            }
             if (Lhi) {
                 Split<OT>::run(a, a2, lh, ll);
                 Split<OT>::run(wr, wr2, rh, rl);
@@ -120,6 +131,11 @@ __global__ void __launch_bounds__(256) k_split_ops(
             Rlo[dst + k] = rl;
         }
     }
+    lf = __reduce_min_sync(0xffffffffu, lf);
+    le = __reduce_max_sync(0xffffffffu, le);
+    rf = __reduce_min_sync(0xffffffffu, rf);
+    re = __reduce_max_sync(0xffffffffu, re);
+    if (lane == 0) rng[row] = make_int4(le > 0 ? lf : 0, le, re > 0 ? rf : 0, re);
 }
 
 // ------------------------------- GEMM kernel --------------------------------------
@@ -450,13 +466,13 @@ int contract_tc(Mesh *m, bool bf16) {
             for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<__nv_bfloat16 *>(B.tc_op[q]);
             k_split_ops<__nv_bfloat16><<<grid, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
-                B.tab_off, B.tab_ld, row_lo, row_hi, Kp, op[0], op[1], op[2], op[3], B.ap_R);
+                B.tab_off, B.tab_ld, row_lo, row_hi, Kp, op[0], op[1], op[2], op[3], B.ap_R, B.ap_rng);
         } else {
             float *op[4];
             for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<float *>(B.tc_op[q]);
             k_split_ops<float><<<grid, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
-                B.tab_off, B.tab_ld, row_lo, row_hi, Kp, op[0], op[1], op[2], op[3], B.ap_R);
+                B.tab_off, B.tab_ld, row_lo, row_hi, Kp, op[0], op[1], op[2], op[3], B.ap_R, B.ap_rng);
         }
         kc_end(m, KC_SPLIT);
         note_launch(m);
@@ -509,7 +525,7 @@ int contract_tc(Mesh *m, bool bf16) {
     FEM3_TRY(tc_gemms(m, bf16, w, maps));
     kc_end(m, KC_CONTRACT);
     m->contract_flops = flops;
-    m->ap_ready = true;
+    m->ap_ready = m->nparts <= 1;   // a part's split covers only its own bins' rows
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
@@ -549,13 +565,13 @@ int contract_tc_form(Mesh *m, int axis, bool test_right, double *wc_gp, bool bf1
         for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<__nv_bfloat16 *>(B.tc_op[q]);
         k_split_ops<__nv_bfloat16><<<grid, 256, 0, s>>>(T, S, B.row_bin, B.dof_off, B.gp_off, ws,
                                                          B.tab_off, B.tab_ld, 0, B.n_tmpl, Kp,
-                                                         op[0], op[1], op[2], op[3], B.ap_R);
+                                                         op[0], op[1], op[2], op[3], B.ap_R, B.ap_rng);
     } else {
         float *op[4];
         for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<float *>(B.tc_op[q]);
         k_split_ops<float><<<grid, 256, 0, s>>>(T, S, B.row_bin, B.dof_off, B.gp_off, ws,
                                                 B.tab_off, B.tab_ld, 0, B.n_tmpl, Kp, op[0],
-                                                op[1], op[2], op[3], B.ap_R);
+                                                op[1], op[2], op[3], B.ap_R, B.ap_rng);
     }
     kc_end(m, KC_SPLIT);
     note_launch(m);
@@ -576,6 +592,7 @@ int ap_alloc(Mesh *m, int axis) {
     if (B.ap_R) return FEM3_OK;
     const int64_t e = std::max<int64_t>(1, B.tab_elems);
     FEM3_TRY(dev_alloc(m, (void **)&B.ap_R, sizeof(float2) * e));
+    FEM3_TRY(dev_alloc(m, (void **)&B.ap_rng, sizeof(int4) * std::max<int64_t>(1, B.n_tmpl)));
     return FEM3_OK;
 }
 
@@ -590,7 +607,7 @@ int ap_prepare(Mesh *m) {
         kc_begin(m, KC_SPLIT);
         k_split_ops<float><<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
             m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot, B.tab_off,
-            B.tab_ld, 0, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_R);
+            B.tab_ld, 0, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_R, B.ap_rng);
         kc_end(m, KC_SPLIT);
         note_launch(m);
     }

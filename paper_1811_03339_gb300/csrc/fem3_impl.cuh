@@ -65,7 +65,14 @@ struct AxisBins {
     int32_t *slot_of_gp = nullptr; // [n_gp]     Gauss point -> slot
     double *w_slot = nullptr;    // [n_gp]       Gauss weight of each slot
     int32_t *dof_off = nullptr;  // [n_bins+1]
-    int32_t *dof_idx = nullptr;  // [n_tmpl]     sorted dof ids per bin
+    int32_t *dof_idx = nullptr;  // [n_tmpl]     dof ids per bin, sorted by dof_key
+    // [n_tmpl] row keys: (lower end of the dof's element patch along the axis, quantised to
+    // 30 bits) << 32 | dof id, ascending within a bin; [n_dof] that quantised position
+    unsigned long long *dof_key = nullptr;
+    uint32_t *dof_q = nullptr;
+    // [n_tmpl] Gauss-point ranges [first, end) of the nonzeros of each row of L and of R
+    // (x, y: L; z, w: R), written with the apply operands
+    int4 *ap_rng = nullptr;
     int64_t *tab_off = nullptr;  // [n_bins]     element offset of the bin's table block
     int32_t *tab_ld = nullptr;   // [n_bins]     leading dimension (padded Gauss-point count)
     int64_t n_tmpl = 0, tab_elems = 0;
@@ -145,7 +152,7 @@ struct Mesh {
     double *vec64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     float *vec32[2] = {nullptr, nullptr};
     int32_t *flags = nullptr;  // triangular-solve flags: [2 nblk + 2]
-    void *solve_ws = nullptr;  // triangular-solve z blocks: nblk x 64 x 16 doubles
+    void *solve_ws = nullptr;  // triangular-solve z blocks: nblk x 64 x 24 doubles
     void *solve_G = nullptr;   // triangular-solve chain operators: nblk x 2 x 3 x 64 x 64 doubles
     int32_t *chol_flags = nullptr;  // tile-factorisation flags, then ticket and abort words
     void *dinv = nullptr;      // inverses of the 64 x 64 diagonal blocks of the factor

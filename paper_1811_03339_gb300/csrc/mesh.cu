@@ -432,6 +432,7 @@ struct BinAxis {
     int32_t *gcount, *dcount, *gcur, *dcur, *gbin, *gp_off, *dof_off;
     unsigned long long *gkeys, *dkeys;
     int32_t *gp_idx, *slot_bin, *dof_idx, *row_bin, *slot_of_gp;
+    uint32_t *dq;   // [n_dof] quantised position of each dof's element patch along the axis
     double *w_slot;
     double lo, span;   // extent along the axis (sort key of the Gauss points)
     int n_bins;
@@ -514,11 +515,21 @@ __global__ void k_bin_fill3(const __grid_constant__ BinAxes P, const double *__r
         const int a1 = bin_coord(bx[3 + G.c0], G.org0, G.width, G.nb0);
         const int b0 = bin_coord(bx[G.c1], G.org1, G.width, G.nb1);
         const int b1 = bin_coord(bx[3 + G.c1], G.org1, G.width, G.nb1);
+        // sort key of a template row: the lower end of the dof's element patch along the
+        // axis (30-bit quantised), then the dof id.  With the Gauss points of a bin sorted
+        // along the axis as well, a row's nonzeros in the left table (paths running from the
+        // Gauss point towards -x) start at a Gauss point that grows with the key, and those
+        // in the right table end at one: the apply skips the rest of each row.
+        double u = (bx[axis] - X.lo) / X.span;
+        u = u < 0 ? 0 : (u > 1 ? 1 : u);
+        const uint32_t q = (uint32_t)(u * 1073741823.0);
+        X.dq[i] = q;
+        const unsigned long long key = ((unsigned long long)q << 32) | (unsigned long long)i;
         for (int i1 = b0; i1 <= b1; i1++)
             for (int i0 = a0; i0 <= a1; i0++) {
                 const int b = i0 + G.nb0 * i1;
                 const int32_t pos = atomicAdd(&X.dcur[b], 1);
-                X.dkeys[X.dof_off[b] + pos] = (unsigned long long)i;
+                X.dkeys[X.dof_off[b] + pos] = key;
             }
     }
 }
@@ -556,6 +567,7 @@ __global__ void k_bin_sort3(const __grid_constant__ BinAxes P) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         ids[lo + i] = (int32_t)(sh[i] & 0xffffffffull);
         bin_of[lo + i] = b;
+        if (dofs) X.dkeys[lo + i] = sh[i];   // the walk searches a row by its key
     }
 }
 
@@ -784,6 +796,9 @@ int bins_build(Mesh *m) {
             max_dof = std::max(max_dof, B.max_dof);
             FEM3_TRY(dev_alloc_t(m, &X.gkeys, n_gp));
             FEM3_TRY(dev_alloc_t(m, &X.dkeys, std::max<int64_t>(1, B.n_tmpl)));
+            FEM3_TRY(dev_alloc_t(m, &X.dq, std::max<int64_t>(1, n_dof)));
+            B.dof_key = X.dkeys;
+            B.dof_q = X.dq;
             FEM3_TRY(dev_alloc_t(m, &B.gp_idx, n_gp));
             FEM3_TRY(dev_alloc_t(m, &B.slot_bin, n_gp));
             FEM3_TRY(dev_alloc_t(m, &B.dof_idx, std::max<int64_t>(1, B.n_tmpl)));

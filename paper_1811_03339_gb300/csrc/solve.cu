@@ -384,13 +384,13 @@ __global__ void __launch_bounds__(512, 1) k_chol_tiles(TF *A, int64_t n, int nbl
 }
 
 // at most this many right-hand sides per triangular-solve launch
-constexpr int kMaxRhs = 16;
+constexpr int kMaxRhs = 24;
 
 // ---------------------------------------------------------------------------------
 // Batched block-step triangular solves across meshes (no waiting between CTAs, so the
 // meshes of a batch share launches).  Step s: mesh m solves its block k = s (forward)
 // or nblk_m - 1 - s (backward) with the diagonal inverse, then updates the blocks that
-// depend on it.  All right-hand sides of a mesh (<= 16, column-major, ld = n) together.
+// depend on it.  All right-hand sides of a mesh (<= 24, column-major, ld = n) together.
 // ---------------------------------------------------------------------------------
 template <class TF>
 __global__ void __launch_bounds__(256) k_btrsm_diag(const BatchTrsmDesc *__restrict__ d, int s,
@@ -481,7 +481,7 @@ int chol_tiles_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
 }
 
 // ---------------------------------------------------------------------------------
-// Chain triangular solves (one launch per direction, 1..16 right-hand sides).
+// Chain triangular solves (one launch per direction, 1..24 right-hand sides).
 // Forward: y_j = Dinv_j (b_j - sum_{k<j} L_jk y_k); backward: x_j = Dinv_j^T (y_j -
 // sum_{k>j} L_kj^T x_k).  Step s solves block j(s) (j = s forward, nblk-1-s backward);
 // M(s, s') is the coefficient tile between the blocks of steps s and s' < s.
@@ -493,7 +493,7 @@ int chol_tiles_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
 // chain only waits for tickets that precede the ones any worker can be blocked on, so the
 // launch needs no co-residency; waits are bounded (ERR_SOLVE, abort word).
 // Y is column-major (n x nrhs, leading dimension n), solved in place.  flags: Yf [nblk],
-// Pf [nblk], ticket, abort word, all zero at launch; S: nblk x 64 x 16 workspace.
+// Pf [nblk], ticket, abort word, all zero at launch; Z: nblk x 64 x 24 workspace.
 // ---------------------------------------------------------------------------------
 constexpr int kSolveThreads = 512;            // thread (r, g): row r = t & 63, column chunk g = t >> 6
 
@@ -855,12 +855,12 @@ int solve_prep_t(const TF *L, int64_t n, cudaStream_t s, Mesh *m) {
     return FEM3_OK;
 }
 
-// L y = b (forward) then L^T x = y (backward), in place in Y (n x nrhs, nrhs <= 16);
+// L y = b (forward) then L^T x = y (backward), in place in Y (n x nrhs, nrhs <= 24);
 // uses the operators of solve_prep_t for the same factor.
 template <class TF>
 int solve_chain_t(const TF *L, int64_t n, TF *Y, int nrhs, cudaStream_t s, Mesh *m) {
     if (n <= 0) return FEM3_OK;
-    if (nrhs < 1 || nrhs > kMaxRhs) return set_error(FEM3_E_ARG, "1..16 right-hand sides per block solve");
+    if (nrhs < 1 || nrhs > kMaxRhs) return set_error(FEM3_E_ARG, "1..24 right-hand sides per block solve");
     const int nblk = (int)((n + NB - 1) / NB);
     static int sms = 0;
     if (sms == 0) {
@@ -875,7 +875,8 @@ int solve_chain_t(const TF *L, int64_t n, TF *Y, int nrhs, cudaStream_t s, Mesh 
     if (nrhs == 1) FEM3_TRY((launch_solve_chain<TF, 1>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
     else if (nrhs <= 4) FEM3_TRY((launch_solve_chain<TF, 4>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
     else if (nrhs <= 8) FEM3_TRY((launch_solve_chain<TF, 8>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
-    else FEM3_TRY((launch_solve_chain<TF, 16>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
+    else if (nrhs <= 16) FEM3_TRY((launch_solve_chain<TF, 16>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
+    else FEM3_TRY((launch_solve_chain<TF, 24>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
 }
@@ -1072,7 +1073,7 @@ int residual_norm(Mesh *m, const double *b, const double *Au, double *rel) {
     return FEM3_OK;
 }
 
-// L Y = B then L^T X = Y for nrhs <= 16 columns (column-major, leading dimension n)
+// L Y = B then L^T X = Y for nrhs <= 24 columns (column-major, leading dimension n)
 template <class TF>
 int trsm_t(const TF *L, int64_t n, TF *Y, int nrhs, cudaStream_t s, Mesh *m) {
     return solve_chain_t<TF>(L, n, Y, nrhs, s, m);
@@ -1158,28 +1159,39 @@ int factor(Mesh *m) {
 // Fused operator apply, one CTA per transverse bin, in double-float arithmetic on the FP32
 // pipes.  With R~ = W R (split once per assembly, see k_split_ops), A u restricted to
 // the bin is L^T (R~ u) + R~^T (L u) (L read from the table itself).  The bin's Gauss
-// points go in chunks of 32; for each chunk the L and R~ columns of up to RM template rows
-// are staged in shared memory (cp.async 16-byte copies, all in flight together, zero-filled
-// past the bin's Gauss points; rows of 34 pairs, 272 bytes) with u_b as hi + lo pairs.
-// Phase 1
-// forms yR = R~ u_b and yL = L u_b (warp w sums rows w, w + 8, ..., lane = Gauss point; the
-// eight partial sums are added in shared memory); phase 2 adds s K (L^T yR + R~^T yL) to Au,
-// one thread per template row, from the same staged rows (a bin with more than RM rows
-// stages its row chunks again for phase 2, from L2).  Every product is exact up to 2^-48
-// relative and sums carry their rounding errors (df_fma), so Au matches an FP64 evaluation to
-// a few units in 2^-48.  The kernel has no FP64 arithmetic: s K z is formed in double-float
-// FP32 operations and its two parts go to Au as exact FP64 values (bit assembly) through
-// FP64 atomics.  NR = 1: u plain; NR = 8: u interleaved [dof][8].
+// points go in chunks of 32, and the chunks are independent: for a chunk, yR = R~ u_b and
+// yL = L u_b over its Gauss points (phase 1), then Au += s K (L^T yR + R~^T yL) over the
+// chunk's columns (phase 2).  The template rows go in pieces of kApplyRM: a piece's L and
+// R~ columns of the chunk are staged in shared memory (cp.async 16-byte copies, zero-filled
+// past the bin's Gauss points; rows of 34 pairs, 272 bytes) with u_b as hi + lo pairs and
+// the rows' nonzero ranges; phase 2 takes the piece staged last first and stages the others
+// again (from L2).
+// Rows and Gauss points of a bin are both ordered along the axis, so a row's nonzeros in L
+// (paths towards -x) start at a Gauss point that grows with the row and its nonzeros in R~
+// end at one: each row carries its exact ranges (k_split_ops) and both phases skip the
+// entries outside them, which are exact zeros.
+// Phase 1: warp w sums rows w, w + 8, ... (lane = Gauss point, all NR vectors); the eight
+// partial sums are added in shared memory.  Phase 2: thread = (row, group of NV vectors) for
+// NR = 4 and 8, each over the pairs of Gauss points that hold nonzeros of some row of its
+// warp (a warp-uniform range: the yL / yR reads are broadcasts); for NR = 1 thread = (row,
+// slice of the pairs), the slices added by shuffles.
+// Every product is exact up to 2^-48 relative and sums carry their rounding errors
+// (df_fma), so Au matches an FP64 evaluation to a few units in 2^-48.  The kernel has no
+// FP64 arithmetic: s K z is formed in double-float FP32 operations and its two parts go to
+// Au as exact FP64 values (bit assembly) through FP64 atomics.  NR = 1: u plain; NR = 4, 8:
+// u interleaved [dof][NR].
 constexpr int kApplyThreads = 256;
 constexpr int kApplyGC = 32;                  // Gauss points per chunk
 constexpr int kApplyStride = kApplyGC + 2;    // staged row, float2 units: 272 B, 16-B aligned
-template <int NR> __host__ __device__ constexpr int apply_rows() { return NR == 1 ? 160 : 128; }
+constexpr int kApplyRM = 64;                  // rows per staged piece
 
+// 76,800 bytes at NR = 8: three CTAs per SM (233,472 bytes less 1,024 reserved per CTA)
 template <int NR>
 constexpr size_t apply_bin_smem() {
-    return (size_t)(2 * apply_rows<NR>() * kApplyStride + apply_rows<NR>() * NR +
-                    2 * 8 * kApplyGC * NR + 2 * kApplyGC * NR) *
-           sizeof(float2);
+    return (size_t)(2 * kApplyRM * kApplyStride + kApplyRM * NR + 2 * 8 * kApplyGC * NR +
+                    2 * kApplyGC * NR) *
+               sizeof(float2) +
+           kApplyRM * sizeof(int4);
 }
 
 // exact FP64 value of a normal FP32 number (zero and subnormals give 0), by bit assembly:
@@ -1202,12 +1214,13 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_b
 
 // stage rows [r0, r0 + rn) of the chunk's L and R~ columns [gc0, gc0 + 32): one 16-byte
 // copy per (row, pair of Gauss points), the part past the bin's G Gauss points zero-filled
-// (and not read: entries past G in a table row are padding).  The caller waits
-// (cp.async.wait_all) and synchronises.
+// (and not read: entries past G in a table row are padding); and the rows' nonzero ranges.
+// The caller waits (cp.async.wait_all) and synchronises.
 __device__ __forceinline__ void apply_stage_ops(const float2 *__restrict__ TL,
-                                                const float2 *__restrict__ TR, int ld, int G,
+                                                const float2 *__restrict__ TR,
+                                                const int4 *__restrict__ rng, int ld, int G,
                                                 int gc0, int r0, int rn, float2 *Ls,
-                                                float2 *Rs) {
+                                                float2 *Rs, int4 *Qs) {
     for (int e = threadIdx.x; e < rn * 16; e += kApplyThreads) {
         const int r = e >> 4, q = e & 15, g = gc0 + 2 * q;
         const int nb = g + 1 < G ? 16 : (g < G ? 8 : 0);
@@ -1216,14 +1229,116 @@ __device__ __forceinline__ void apply_stage_ops(const float2 *__restrict__ TL,
         cp_async16(Rs + r * kApplyStride + 2 * q, TR + o, nb);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int r = threadIdx.x; r < rn; r += kApplyThreads) Qs[r] = __ldg(rng + r0 + r);
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// pairs [p0, p1) of the chunk's Gauss points that hold a row's nonzeros in [first, end)
+__device__ __forceinline__ void pair_range(int first, int end, int gc0, int gn, int &p0,
+                                           int &p1) {
+    p0 = max(first - gc0, 0) >> 1;
+    p1 = (min(end - gc0, gn) + 1) >> 1;
+}
+
+// phase 2 of one staged piece: thread = (row, group of NV vectors, slice of S of the 16
+// pairs of Gauss points); adds s K (L^T yR + R~^T yL) of the chunk to Au
+template <int NR, int NV, int S, bool DF>
+__device__ __forceinline__ void apply_phase2(const float2 *Ls, const float2 *Rs, const int4 *Qs,
+                                             const float2 *yL, const float2 *yR, int rn,
+                                             int gc0, int gn, const int32_t *__restrict__ dofs,
+                                             float sKh, float sKl, int nv, double *Au,
+                                             int64_t ldA) {
+    constexpr int VS = NR / NV;   // vector groups per row
+    const int t = threadIdx.x;
+    const int r = t / (VS * S), vg = (t / S) % VS, s = t % S;   // compile-time divisors
+    const bool act = r < rn;
+    const int rr = act ? r : 0;
+    const int4 q = Qs[rr];
+    int l0, l1, q0, q1;
+    pair_range(q.x, q.y, gc0, gn, l0, l1);
+    pair_range(q.z, q.w, gc0, gn, q0, q1);
+    if (!act) { l0 = q0 = kApplyGC; l1 = q1 = 0; }
+    if constexpr (S == 1) {
+        // the union over the warp's rows (entries outside a row's own range are zeros)
+        l0 = __reduce_min_sync(0xffffffffu, l0);
+        l1 = __reduce_max_sync(0xffffffffu, l1);
+        q0 = __reduce_min_sync(0xffffffffu, q0);
+        q1 = __reduce_max_sync(0xffffffffu, q1);
+    } else {
+        constexpr int PS = (kApplyGC / 2) / S;   // pairs per slice
+        l0 = max(l0, s * PS);
+        l1 = min(l1, (s + 1) * PS);
+        q0 = max(q0, s * PS);
+        q1 = min(q1, (s + 1) * PS);
+    }
+    const float4 *Lr = reinterpret_cast<const float4 *>(Ls + rr * kApplyStride);
+    const float4 *Rr = reinterpret_cast<const float4 *>(Rs + rr * kApplyStride);
+    const float2 *yRv = yR + vg * NV, *yLv = yL + vg * NV;
+    float zh[NV], zl[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) { zh[k] = 0.f; zl[k] = 0.f; }
+    for (int g2 = l0; g2 < l1; g2++) {   // two Gauss points per 16-byte read
+        const float4 lv = Lr[g2];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            const float2 a0 = yRv[2 * g2 * NR + k], a1 = yRv[(2 * g2 + 1) * NR + k];
+            if constexpr (DF) {
+                df_fma(lv.x, lv.y, a0.x, a0.y, zh[k], zl[k]);
+                df_fma(lv.z, lv.w, a1.x, a1.y, zh[k], zl[k]);
+            } else {
+                zh[k] = fmaf(lv.x, a0.x, zh[k]);
+                zh[k] = fmaf(lv.z, a1.x, zh[k]);
+            }
+        }
+    }
+    for (int g2 = q0; g2 < q1; g2++) {
+        const float4 rv = Rr[g2];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            const float2 a0 = yLv[2 * g2 * NR + k], a1 = yLv[(2 * g2 + 1) * NR + k];
+            if constexpr (DF) {
+                df_fma(rv.x, rv.y, a0.x, a0.y, zh[k], zl[k]);
+                df_fma(rv.z, rv.w, a1.x, a1.y, zh[k], zl[k]);
+            } else {
+                zh[k] = fmaf(rv.x, a0.x, zh[k]);
+                zh[k] = fmaf(rv.z, a1.x, zh[k]);
+            }
+        }
+    }
+    if constexpr (S > 1) {   // the row's S slices sit in neighbouring lanes
+#pragma unroll
+        for (int o = 1; o < S; o <<= 1)
+#pragma unroll
+            for (int k = 0; k < NV; k++) {
+                const float xh = __shfl_xor_sync(0xffffffffu, zh[k], o);
+                const float xl = __shfl_xor_sync(0xffffffffu, zl[k], o);
+                if constexpr (DF) df_add(xh, xl, zh[k], zl[k]);
+                else zh[k] += xh;
+            }
+    }
+    if (!act || s != 0) return;
+    const int64_t dof = dofs[r];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        const int v = vg * NV + k;
+        if (v >= nv) break;
+        if constexpr (DF) {
+            float ph, pl;
+            df_mul(zh[k], zl[k], sKh, sKl, ph, pl);
+            atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(ph));
+            atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(pl));
+        } else {
+            atomicAdd(&Au[(int64_t)v * ldA + dof], (double)(zh[k] * sKh));
+        }
+    }
+}
+
 // one axis of the apply: its bins' operands and s K as an FP32 pair
 struct ApplyAxis {
     const float2 *apL, *apR;
+    const int4 *rng;   // per template row: Gauss-point ranges of the nonzeros of L and W R
     const int32_t *gp_off, *dof_off, *dof_idx, *tab_ld;
     const int64_t *tab_off;
     float sKh, sKl;
@@ -1241,7 +1356,8 @@ template <int NR, bool DF = true>
 __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_constant__ ApplyAxes P,
                                                              const double *__restrict__ u, int nv,
                                                              double *Au, int64_t ldA) {
-    constexpr int RM = apply_rows<NR>();
+    static_assert(NR == 1 || NR == 4 || NR == 8, "vectors per pass");
+    constexpr int RM = kApplyRM;
     int b = blockIdx.x, axis = 0;
     while (axis < 2 && b >= P.a[axis].n_bins) b -= P.a[axis++].n_bins;
     const ApplyAxis &X = P.a[axis];
@@ -1251,29 +1367,31 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
     const int64_t *__restrict__ tab_off = X.tab_off;
     const float sKh = X.sKh, sKl = X.sKl;
     extern __shared__ __align__(16) float2 sm_apply[];
-    float2 *Ls = sm_apply;                       // [RM][33]
-    float2 *Rs = Ls + RM * kApplyStride;         // [RM][33]
+    float2 *Ls = sm_apply;                       // [RM][34]
+    float2 *Rs = Ls + RM * kApplyStride;         // [RM][34]
     float2 *us = Rs + RM * kApplyStride;         // [RM][NR]
     float2 *pL = us + RM * NR;                   // [8][32][NR] phase-1 partial sums, L u
     float2 *pR = pL + 8 * kApplyGC * NR;         // [8][32][NR] R~ u
     float2 *yL = pR + 8 * kApplyGC * NR;         // [32][NR]
     float2 *yR = yL + kApplyGC * NR;             // [32][NR]
+    int4 *Qs = reinterpret_cast<int4 *>(yR + kApplyGC * NR);   // [RM] row ranges
     const int d0 = dof_off[b], D = dof_off[b + 1] - d0;
     const int G = gp_off[b + 1] - gp_off[b], ld = tab_ld[b];
     if (D == 0 || G == 0) return;
     const float2 *TL = apL + tab_off[b], *TR = apR + tab_off[b];
+    const int4 *rng = X.rng + d0;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int np = (D + RM - 1) / RM;
     for (int gc0 = 0; gc0 < G; gc0 += kApplyGC) {
         const int gn = min(kApplyGC, G - gc0);
         // ---- phase 1: lane = Gauss point gc0 + lane, warp = row slice ----
         float lh[NR], ll[NR], rh[NR], rl[NR];
 #pragma unroll
         for (int v = 0; v < NR; v++) { lh[v] = 0.f; ll[v] = 0.f; rh[v] = 0.f; rl[v] = 0.f; }
-        int rc_last = 0;
-        for (int rc0 = 0; rc0 < D; rc0 += RM) {
-            const int rn = min(RM, D - rc0);
+        for (int p = 0; p < np; p++) {
+            const int rc0 = p * RM, rn = min(RM, D - rc0);
             __syncthreads();   // earlier readers of the staged rows are done
-            apply_stage_ops(TL, TR, ld, G, gc0, rc0, rn, Ls, Rs);
+            apply_stage_ops(TL, TR, rng, ld, G, gc0, rc0, rn, Ls, Rs, Qs);
             for (int e = tid; e < rn * NR; e += kApplyThreads) {
                 const int r = e / NR, v = e - r * NR;
                 const int64_t dof = dof_idx[d0 + rc0 + r];
@@ -1284,20 +1402,27 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
             cp_async_wait_all();
             __syncthreads();
             for (int r = warp; r < rn; r += kApplyThreads / 32) {
-                const float2 lv = Ls[r * kApplyStride + lane], rv = Rs[r * kApplyStride + lane];
+                // does the row's nonzero range meet this chunk in L, in R~?  (usually one)
+                const int4 q = Qs[r];
+                if (q.x < gc0 + kApplyGC && q.y > gc0) {
+                    const float2 lv = Ls[r * kApplyStride + lane];
 #pragma unroll
-                for (int v = 0; v < NR; v++) {
-                    const float2 uv = us[r * NR + v];
-                    if constexpr (DF) {
-                        df_fma(lv.x, lv.y, uv.x, uv.y, lh[v], ll[v]);
-                        df_fma(rv.x, rv.y, uv.x, uv.y, rh[v], rl[v]);
-                    } else {
-                        lh[v] = fmaf(lv.x, uv.x, lh[v]);
-                        rh[v] = fmaf(rv.x, uv.x, rh[v]);
+                    for (int v = 0; v < NR; v++) {
+                        const float2 uv = us[r * NR + v];
+                        if constexpr (DF) df_fma(lv.x, lv.y, uv.x, uv.y, lh[v], ll[v]);
+                        else lh[v] = fmaf(lv.x, uv.x, lh[v]);
+                    }
+                }
+                if (q.z < gc0 + kApplyGC && q.w > gc0) {
+                    const float2 rv = Rs[r * kApplyStride + lane];
+#pragma unroll
+                    for (int v = 0; v < NR; v++) {
+                        const float2 uv = us[r * NR + v];
+                        if constexpr (DF) df_fma(rv.x, rv.y, uv.x, uv.y, rh[v], rl[v]);
+                        else rh[v] = fmaf(rv.x, uv.x, rh[v]);
                     }
                 }
             }
-            rc_last = rc0;
         }
 #pragma unroll
         for (int v = 0; v < NR; v++) {
@@ -1323,54 +1448,38 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
             yR[e] = make_float2(ch, cl);
         }
         __syncthreads();
-        // ---- phase 2: thread per template row; the last staged row chunk first ----
-        for (int pass = 0; pass * RM < D; pass++) {
-            const int rc0 = pass == 0 ? rc_last : (pass - 1) * RM;   // rc_last: the last chunk
-            const int rn = min(RM, D - rc0);
+        // ---- phase 2: the piece staged last first ----
+        for (int pass = 0; pass < np; pass++) {
+            const int p = pass == 0 ? np - 1 : pass - 1;
+            const int rc0 = p * RM, rn = min(RM, D - rc0);
             if (pass > 0) {
                 __syncthreads();
-                apply_stage_ops(TL, TR, ld, G, gc0, rc0, rn, Ls, Rs);
+                apply_stage_ops(TL, TR, rng, ld, G, gc0, rc0, rn, Ls, Rs, Qs);
                 cp_async_wait_all();
                 __syncthreads();
             }
-            for (int r = tid; r < rn; r += kApplyThreads) {
-                float zh[NR], zl[NR];
-#pragma unroll
-                for (int v = 0; v < NR; v++) { zh[v] = 0.f; zl[v] = 0.f; }
-                const float4 *Lr = reinterpret_cast<const float4 *>(Ls + r * kApplyStride);
-                const float4 *Rr = reinterpret_cast<const float4 *>(Rs + r * kApplyStride);
-                for (int g2 = 0; 2 * g2 < gn; g2++) {   // two Gauss points per 16-byte read
-                    const float4 lv = Lr[g2], rv = Rr[g2];   // zero past G
-#pragma unroll
-                    for (int v = 0; v < NR; v++) {
-                        const float2 a0 = yR[2 * g2 * NR + v], q0 = yL[2 * g2 * NR + v];
-                        const float2 a1 = yR[(2 * g2 + 1) * NR + v], q1 = yL[(2 * g2 + 1) * NR + v];
-                        if constexpr (DF) {
-                            df_fma(lv.x, lv.y, a0.x, a0.y, zh[v], zl[v]);
-                            df_fma(rv.x, rv.y, q0.x, q0.y, zh[v], zl[v]);
-                            df_fma(lv.z, lv.w, a1.x, a1.y, zh[v], zl[v]);
-                            df_fma(rv.z, rv.w, q1.x, q1.y, zh[v], zl[v]);
-                        } else {
-                            zh[v] = fmaf(lv.x, a0.x, zh[v]);
-                            zh[v] = fmaf(rv.x, q0.x, zh[v]);
-                            zh[v] = fmaf(lv.z, a1.x, zh[v]);
-                            zh[v] = fmaf(rv.z, q1.x, zh[v]);
-                        }
-                    }
-                }
-                const int64_t dof = dof_idx[d0 + rc0 + r];
-#pragma unroll
-                for (int v = 0; v < NR; v++) {
-                    if (v >= nv) break;
-                    if constexpr (DF) {
-                        float ph, pl;
-                        df_mul(zh[v], zl[v], sKh, sKl, ph, pl);
-                        atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(ph));
-                        atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(pl));
-                    } else {
-                        atomicAdd(&Au[(int64_t)v * ldA + dof], (double)(zh[v] * sKh));
-                    }
-                }
+            const int32_t *dofs = dof_idx + d0 + rc0;
+            if constexpr (NR == 8) {
+                if (rn <= 32)
+                    apply_phase2<8, 1, 1, DF>(Ls, Rs, Qs, yL, yR, rn, gc0, gn, dofs, sKh, sKl, nv,
+                                              Au, ldA);
+                else
+                    apply_phase2<8, 2, 1, DF>(Ls, Rs, Qs, yL, yR, rn, gc0, gn, dofs, sKh, sKl, nv,
+                                              Au, ldA);
+            } else if constexpr (NR == 4) {
+                if (rn <= 32)
+                    apply_phase2<4, 1, 2, DF>(Ls, Rs, Qs, yL, yR, rn, gc0, gn, dofs, sKh, sKl, nv,
+                                              Au, ldA);
+                else
+                    apply_phase2<4, 1, 1, DF>(Ls, Rs, Qs, yL, yR, rn, gc0, gn, dofs, sKh, sKl, nv,
+                                              Au, ldA);
+            } else {
+                if (rn <= 32)
+                    apply_phase2<1, 1, 8, DF>(Ls, Rs, Qs, yL, yR, rn, gc0, gn, dofs, sKh, sKl, nv,
+                                              Au, ldA);
+                else
+                    apply_phase2<1, 1, 4, DF>(Ls, Rs, Qs, yL, yR, rn, gc0, gn, dofs, sKh, sKl, nv,
+                                              Au, ldA);
             }
         }
     }
@@ -1413,8 +1522,8 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d, bool df) {
         AxisBins &B = m->bins[axis];
         const bool on = B.n_tmpl > 0 && B.n_bins > 0;
         const float skh = (float)m->sK[axis], skl = (float)(m->sK[axis] - (double)skh);
-        P.a[axis] = ApplyAxis{m->tabL[axis], B.ap_R, B.gp_off, B.dof_off, B.dof_idx, B.tab_ld,
-                              B.tab_off, skh, skl, on ? B.n_bins : 0};
+        P.a[axis] = ApplyAxis{m->tabL[axis], B.ap_R, B.ap_rng, B.gp_off, B.dof_off, B.dof_idx,
+                              B.tab_ld, B.tab_off, skh, skl, on ? B.n_bins : 0};
         nblk += on ? B.n_bins : 0;
     }
     for (int v0 = 0; v0 < nv && nblk > 0; v0 += 8) {

@@ -243,15 +243,16 @@ __device__ int32_t next_tet(const WalkGeom &W, int32_t t, int axis, int dir, dou
     return next;
 }
 
-// position of dof j in the ascending list d[0 .. n), or -1: binary lifting for the number
+// position of key j in the ascending list d[0 .. n), or -1: binary lifting for the number
 // of entries <= j, with a trip count set by n alone (lanes searching one list stay
 // converged) and every load inside the list
-__device__ __forceinline__ int bsearch_dof(const int32_t *__restrict__ d, int n, int32_t j) {
+__device__ __forceinline__ int bsearch_key(const unsigned long long *__restrict__ d, int n,
+                                           unsigned long long j) {
     if (n <= 0) return -1;
     int base = 0;
     for (int step = 1 << (31 - __clz(n)); step > 0; step >>= 1) {
         const int c = base + step;
-        const int32_t v = __ldg(d + (c < n ? c : n) - 1);
+        const unsigned long long v = __ldg(d + (c < n ? c : n) - 1);
         if (c <= n && v <= j) base = c;
     }
     return (base > 0 && __ldg(d + base - 1) == j) ? base - 1 : -1;
@@ -262,7 +263,8 @@ struct TableArgs {
     const int32_t *__restrict__ slot_bin; // [n_gp]
     const int32_t *__restrict__ gp_off;   // [n_bins+1]
     const int32_t *__restrict__ dof_off;  // [n_bins+1]
-    const int32_t *__restrict__ dof_idx;
+    const unsigned long long *__restrict__ dof_key;   // template rows' keys (sorted per bin)
+    const uint32_t *__restrict__ dof_q;               // [n_dof] position part of a dof's key
     const int64_t *__restrict__ tab_off;
     const int32_t *__restrict__ tab_ld;
     float2 *tab;                          // L (side 0) or R (side 1) of this axis, hi + lo pairs
@@ -358,7 +360,7 @@ __device__ __forceinline__ int walk_lines(const WalkGeom &W, const TableArgs &A0
                                           Next next, int &miss, int &bad) {
     int nseg = 0;
     int32_t g, nd, ld;
-    const int32_t *dofs;
+    const unsigned long long *dofs;
     int64_t toff;
     double x0, x1, x2;
     LineF X;
@@ -370,7 +372,7 @@ __device__ __forceinline__ int walk_lines(const WalkGeom &W, const TableArgs &A0
         g = A0.gp_idx[sl];
         const int32_t bin = A0.slot_bin[sl];
         const int32_t row = (int32_t)(sl - A0.gp_off[bin]);
-        dofs = A0.dof_idx + A0.dof_off[bin];
+        dofs = A0.dof_key + A0.dof_off[bin];
         nd = A0.dof_off[bin + 1] - A0.dof_off[bin];
         ld = A0.tab_ld[bin];
         toff = A0.tab_off[bin] + row;
@@ -461,7 +463,9 @@ __device__ __forceinline__ int walk_lines(const WalkGeom &W, const TableArgs &A0
                     const int q = __ffs(freem) - 1;
                     freem &= freem - 1;
                     const int32_t jv = v == 0 ? j[0] : (v == 1 ? j[1] : (v == 2 ? j[2] : j[3]));
-                    const int32_t c = bsearch_dof(dofs, nd, jv);
+                    const unsigned long long key =
+                        ((unsigned long long)__ldg(A0.dof_q + jv) << 32) | (unsigned long long)jv;
+                    const int32_t c = bsearch_key(dofs, nd, key);
 #pragma unroll
                     for (int u = 0; u < 4; u++)
                         if (u == q) {
@@ -702,8 +706,8 @@ int walk_tables(Mesh *m, const double alpha[3]) {
         double gamma = alpha[axis] / 2.0;
         double ig = 1.0 / tgamma(2.0 - gamma);
         const float igh = (float)ig, igl = (float)(ig - (double)igh);
-        T.A0[axis] = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
-                               B.tab_ld, m->tabL[axis], 1.0 - gamma, igh, igl,
+        T.A0[axis] = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_key, B.dof_q,
+                               B.tab_off, B.tab_ld, m->tabL[axis], 1.0 - gamma, igh, igl,
                                m->pow_cell + (size_t)axis * 256 * 8, m->pow_exp + axis * 128};
         T.A1[axis] = T.A0[axis];
         T.A1[axis].tab = m->tabR[axis];
@@ -763,11 +767,11 @@ int walk_tables_form(Mesh *m, int axis, double order_left, double order_right) {
     const double il = 1.0 / tgamma(2.0 - order_left), ir = 1.0 / tgamma(2.0 - order_right);
     const float ilh = (float)il, ill = (float)(il - (double)ilh);
     const float irh = (float)ir, irl = (float)(ir - (double)irh);
-    T.A0[axis] = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
-                           B.tab_ld, m->tabL[axis], 1.0 - order_left, ilh, ill,
+    T.A0[axis] = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_key, B.dof_q,
+                           B.tab_off, B.tab_ld, m->tabL[axis], 1.0 - order_left, ilh, ill,
                            m->pow_cell, m->pow_exp};
-    T.A1[axis] = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
-                           B.tab_ld, m->tabR[axis], 1.0 - order_right, -irh, -irl,
+    T.A1[axis] = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_key, B.dof_q,
+                           B.tab_off, B.tab_ld, m->tabR[axis], 1.0 - order_right, -irh, -irl,
                            m->pow_cell + 256 * 8, m->pow_exp + 128};
     static int sms = 0;
     if (sms == 0) {
@@ -840,8 +844,8 @@ int walk_tables_batch(Mesh *const *ms, int n, const double *alpha, cudaStream_t 
             const float igh = (float)ig, igl = (float)(ig - (double)igh);
             WalkDesc &D = hd[3 * i + axis];
             D.W = W;
-            D.A0 = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_idx, B.tab_off,
-                             B.tab_ld, m->tabL[axis], 1.0 - gamma, igh, igl,
+            D.A0 = TableArgs{B.gp_idx, B.slot_bin, B.gp_off, B.dof_off, B.dof_key, B.dof_q,
+                             B.tab_off, B.tab_ld, m->tabL[axis], 1.0 - gamma, igh, igl,
                              m->pow_cell + (size_t)axis * 256 * 8, m->pow_exp + axis * 128};
             D.A1 = D.A0;
             D.A1.tab = m->tabR[axis];
