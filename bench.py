@@ -128,8 +128,9 @@ def kernel_rooflines(kms: dict, cnt: dict, n_dof: int, precision: str, peaks: di
                  counted) and the executed split-product MMA flops (3 x 2 D_b^2 G_b)
     factor       FP32 pipe: n^3 / 3 flops
     chain        HBM: one read of the factor's lower triangle (2 n^2 B for FP32) per launch
-    apply        FP32 issue: 4 double-float multiply-adds (13 FP32 instructions each) per
-                 table element and vector
+    apply        FP32 issue: 2 double-float multiply-adds (13 FP32 instructions each) per
+                 nonzero table entry (of L and of R) and vector, when the nonzeros are counted
+                 (else 4 per dense bin-table element pair)
     """
     out = {}
     hbm = float(peaks["hbm_gbs"])
@@ -210,16 +211,25 @@ def kernel_rooflines(kms: dict, cnt: dict, n_dof: int, precision: str, peaks: di
                         "algorithmic": "the factor's lower triangle once per launch"}
     a = kms.get("apply", (0, 0))
     if a[0] > 0 and cnt.get("apply_vectors"):
-        ops = 4 * DF_OPS_PER_PRODUCT * elems * cnt["apply_vectors"]
+        nnz = cnt.get("table_nnz")
+        if nnz:
+            ops = 2 * DF_OPS_PER_PRODUCT * nnz * cnt["apply_vectors"]
+            alg = (f"2 double-float multiply-adds ({DF_OPS_PER_PRODUCT} FP32 instructions each) "
+                   f"per nonzero table entry and vector, {nnz} nonzeros of L and R, "
+                   f"{cnt['apply_vectors']} vector-applies")
+        else:
+            ops = 4 * DF_OPS_PER_PRODUCT * elems * cnt["apply_vectors"]
+            alg = (f"4 double-float multiply-adds ({DF_OPS_PER_PRODUCT} FP32 instructions each) "
+                   f"per table element and vector, {elems:.0f} elements, "
+                   f"{cnt['apply_vectors']} vector-applies")
         ach = ops / (a[0] * 1e-3) / 1e12
         out["apply"] = {"kernel": "k_apply_bin", "bound": "alu", "unit": "T FP32 instr/s",
                         "achieved": ach, "peak": FP32_ISSUE_TOPS, "frac": ach / FP32_ISSUE_TOPS,
                         "launches": a[1], "launch_ms": a[0] / a[1], "traffic": None,
-                        "algorithmic": f"4 double-float multiply-adds ({DF_OPS_PER_PRODUCT} FP32 "
-                                       f"instructions each) per table element and vector, "
-                                       f"{elems:.0f} elements, {cnt['apply_vectors']} "
-                                       f"vector-applies",
+                        "algorithmic": alg,
                         "bytes_gbs": 16 * elems * cnt["apply_passes"] / (a[0] * 1e-3) / 1e9}
+        if nnz:
+            out["apply"]["nonzero_fraction_of_bin_tables"] = nnz / (2.0 * elems)
     return out
 
 
@@ -444,6 +454,7 @@ def measure_workload(args, torch, fem3, inputs, workload, precision, steps, warm
     kms = m.kernel_ms()
     cnt = m.counters()
     cnt["algorithmic_flops"] = m.contract_work()
+    cnt["table_nnz"] = m.table_nnz()
     out.update(dofs=int(m.n_dof), stages_ms=_stage_dict(m.stage_ms()),
                kernel_ms={k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in kms.items()},
                segments_per_step=cnt["segments"], table_bytes=cnt["table_bytes"],

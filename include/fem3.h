@@ -299,6 +299,13 @@ int fem3_counters(fem3_mesh m, int64_t *segments, double *contract_flops,
  * flops: host float64.  Errors: FEM3_E_ARG, FEM3_E_STATE (no assemble yet). */
 int fem3_contract_work(fem3_mesh m, double *flops, void *stream);
 
+/* Nonzeros of the last assemble's derivative tables (Section 2.1 tables, Section 2.3
+ * layout), L and R of every axis together: sum over axes and Gauss points g of
+ * nnz(L_i[g]) + nnz(R_i[g]); the operator apply A u from the tables takes two
+ * multiply-adds per nonzero and vector.  One read of the tables; synchronises `stream`.
+ * nnz: host int64.  Errors: FEM3_E_ARG, FEM3_E_STATE (no fractional assemble yet). */
+int fem3_table_nnz(fem3_mesh m, int64_t *nnz, void *stream);
+
 /* Kernel classes timed launch by launch when the handle profiles (opt.profile != 0):
  * CUDA events on the launch stream around every launch of the class, summed over the
  * launches since the last fem3_assemble and collected by the next synchronising call

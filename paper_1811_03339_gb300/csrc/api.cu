@@ -718,7 +718,16 @@ int fem3_contract_work(fem3_mesh h, double *flops, void *stream) {
     if (m->precision < 0 || m->integer_order)
         return set_error(FEM3_E_STATE, "contraction work needs the tables of a fractional assemble");
     m->stream = reinterpret_cast<cudaStream_t>(stream);
-    return contract_work(m, flops);
+    return contract_work(m, flops, nullptr);
+}
+
+int fem3_table_nnz(fem3_mesh h, int64_t *nnz, void *stream) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !nnz) return set_error(FEM3_E_ARG, "bad argument");
+    if (m->precision < 0 || m->integer_order)
+        return set_error(FEM3_E_STATE, "table nonzeros need the tables of a fractional assemble");
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    return contract_work(m, nullptr, nnz);
 }
 
 int fem3_kernel_ms(fem3_mesh h, int kclass, float *ms, int32_t *launches) {

@@ -234,10 +234,11 @@ __device__ __forceinline__ void tri_decode(int x, int &I, int &J) {
 }
 
 // tile x of a launch -> (I, J).  mode 0: every tile I >= J; 1: the first block column (J = 0,
-// the next panel's columns); 2: every tile 1 <= J <= I (the rest)
+// the next panel's columns); 2: every tile 1 <= J <= I (the rest); 3: the first block column
+// below its diagonal tile (I >= 1, J = 0)
 __device__ __forceinline__ void tile_of(int x, int mode, int &I, int &J) {
-    if (mode == 1) {
-        I = x;
+    if (mode == 1 || mode == 3) {
+        I = mode == 3 ? x + 1 : x;
         J = 0;
         return;
     }
@@ -442,7 +443,8 @@ int make_w_map(CUtensorMap *map, float *base, int64_t rows) {
 // one.
 struct CholCtx {
     int device = -1;
-    cudaStream_t side = nullptr;
+    cudaStream_t side = nullptr;   // bulk trailing updates
+    cudaStream_t col = nullptr;    // the next panel's columns below its diagonal tile
     std::vector<cudaEvent_t> ev;
 };
 std::mutex g_ctx_mu;
@@ -465,12 +467,14 @@ int ctx_acquire(CholCtx **out, int npan) {
         c = new CholCtx();
         c->device = dev;
         cudaError_t e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->col, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
+            if (c->side) cudaStreamDestroy(c->side);
             delete c;
             return cuda_error(e, "cudaStreamCreateWithFlags");
         }
     }
-    while ((int)c->ev.size() < 2 * npan) {
+    while ((int)c->ev.size() < 4 * npan) {
         cudaEvent_t e;
         cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
         if (r != cudaSuccess) {
@@ -494,12 +498,16 @@ void ctx_release(CholCtx *c) {
 // FP32 factorisation of A (n x n, lower triangle) in place, inverses of the 64 x 64
 // diagonal blocks into m->dinv; the same output layout as the tile-task factorisation.
 //
-// Look-ahead over two streams.  Panel p: D(p) diagonal block, P(p) panel solve into the
-// operand buffer p % 2, Ta(p) the trailing update of panel p + 1's columns, Tb(p) the rest
-// of the trailing update.  The caller's stream runs D, P and Ta; the side stream runs Tb,
-// so Tb(p) overlaps D(p + 1) and P(p + 1).  Orderings: D(p) after Tb(p - 2) (which updated
-// panel p's columns and read the operand buffer P(p) rewrites), Ta(p) after Tb(p - 1) (both
-// update panel p + 1's columns), Tb(p) after P(p); the caller's stream waits for the last Tb.
+// Look-ahead over three streams.  Panel p: D(p) diagonal block, P(p) panel solve into the
+// operand buffer p % 2, Ta(p) the trailing update of panel p + 1's diagonal tile, Tc(p) that
+// of the rest of panel p + 1's columns, Tb(p) the rest of the trailing update.  The caller's
+// stream runs D, P and Ta (the critical chain), the column stream Tc and the side stream Tb,
+// so Tc(p) overlaps D(p + 1) and Tb(p) overlaps D(p + 1) and P(p + 1).  Orderings: D(p) after
+// Tb(p - 2) (which updated panel p's columns and read the operand buffer P(p) rewrites) and
+// Ta(p - 1); P(p) after Tc(p - 1) (panel p's columns below the diagonal tile; Tc(p - 2),
+// earlier on its stream, read the operand buffer P(p) rewrites); Ta(p) and Tc(p) after P(p)
+// and Tb(p - 1) (which updated the same columns); Tb(p) after P(p); the caller's stream waits
+// for the last Tb and Tc.
 int chol_tc(Mesh *m, float *A, int64_t n) {
     if (n <= 0) return FEM3_OK;
     cudaStream_t s = m->stream;
@@ -536,11 +544,11 @@ int chol_tc(Mesh *m, float *A, int64_t n) {
     const int npan = (int)((n + kP - 1) / kP);
     CholCtx *cx = nullptr;
     FEM3_TRY(ctx_acquire(&cx, npan));
-    cudaStream_t s1 = cx->side;
-    cudaEvent_t *evP = cx->ev.data(), *evB = cx->ev.data() + npan;
+    cudaStream_t s1 = cx->side, s2 = cx->col;
+    cudaEvent_t *evP = cx->ev.data(), *evB = evP + npan, *evQ = evB + npan, *evR = evQ + npan;
     float *dinv = reinterpret_cast<float *>(m->dinv);
     int st = FEM3_OK;
-    int last_b = -1;
+    int last_b = -1, last_r = -1;
     auto launch_ok = [&](const char *what) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess && st == FEM3_OK) st = cuda_error(e, what);
@@ -561,6 +569,10 @@ int chol_tc(Mesh *m, float *A, int64_t n) {
         const int64_t t0 = j0 + nbp, mt = n - t0;
         if (mt <= 0) break;
         const int b = p & 1;
+        if (p >= 1 && cudaStreamWaitEvent(s, evR[p - 1], 0) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "cudaStreamWaitEvent");
+            break;
+        }
         k_cholp_panel<<<(unsigned)((mt + kPanelRows - 1) / kPanelRows), 256,
                         sizeof(float) * 5 * 64 * kQ, s>>>(A, n, j0, Linv, W[b][0], W[b][1]);
         note_launch(m);
@@ -588,13 +600,34 @@ int chol_tc(Mesh *m, float *A, int64_t n) {
             st = cuda_error(cudaGetLastError(), "cudaStreamWaitEvent");
             break;
         }
-        k_cholp_trail<<<(unsigned)std::min<int64_t>(T, kReservedSms), kTrailThreads, kTrailSmem,
-                        s>>>(maps[b][0], maps[b][1], A, n, t0, 1, (int)T, m->err);
+        // Tc(p) on the column stream, after P(p) and Tb(p - 1) (both behind this point of the
+        // caller's stream); then Ta(p), the one tile D(p + 1) waits for
+        if (cudaEventRecord(evQ[p], s) != cudaSuccess ||
+            cudaStreamWaitEvent(s2, evQ[p], 0) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "cudaEventRecord");
+            break;
+        }
+        if (T > 1) {
+            k_cholp_trail<<<(unsigned)std::min<int64_t>(T - 1, kReservedSms), kTrailThreads,
+                            kTrailSmem, s2>>>(maps[b][0], maps[b][1], A, n, t0, 3, (int)(T - 1),
+                                              m->err);
+            note_launch(m);
+            if (!launch_ok("k_cholp_trail")) break;
+        }
+        if (cudaEventRecord(evR[p], s2) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "cudaEventRecord");
+            break;
+        }
+        last_r = p;
+        k_cholp_trail<<<1, kTrailThreads, kTrailSmem, s>>>(maps[b][0], maps[b][1], A, n, t0, 1, 1,
+                                                             m->err);
         note_launch(m);
         if (!launch_ok("k_cholp_trail")) break;
     }
-    // join: the caller's stream continues after the side stream's last update
+    // join: the caller's stream continues after the side streams' last updates
     if (last_b >= 0 && cudaStreamWaitEvent(s, evB[last_b], 0) != cudaSuccess && st == FEM3_OK)
+        st = cuda_error(cudaGetLastError(), "cudaStreamWaitEvent");
+    if (last_r >= 0 && cudaStreamWaitEvent(s, evR[last_r], 0) != cudaSuccess && st == FEM3_OK)
         st = cuda_error(cudaGetLastError(), "cudaStreamWaitEvent");
     kc_end(m, KC_FACTOR);
     ctx_release(cx);

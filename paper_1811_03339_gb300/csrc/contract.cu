@@ -8,6 +8,7 @@
 // and adds s K out(c1, c2) to A[dof c1][dof c2] (and to the mirror element when t1 < t2).
 // TA is the arithmetic type (double for the FP64 form, float for the FP32 form).
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "fem3_impl.cuh"
@@ -112,13 +113,15 @@ __global__ void __launch_bounds__(256) k_contract_simt(
 __global__ void __launch_bounds__(128) k_contract_work(
     const float2 *__restrict__ tabL, const float2 *__restrict__ tabR,
     const int32_t *__restrict__ gp_off, const int32_t *__restrict__ dof_off,
-    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld, double *flops) {
+    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld, double *flops,
+    unsigned long long *nnz) {
     const int b = blockIdx.x;
     const int D = dof_off[b + 1] - dof_off[b];
     const int G = gp_off[b + 1] - gp_off[b];
     const int ld = tab_ld[b];
     const float2 *L = tabL + tab_off[b], *R = tabR + tab_off[b];
     double acc = 0.0;
+    unsigned long long cnt = 0;
     for (int k = threadIdx.x; k < G; k += blockDim.x) {
         int nl = 0, nr = 0;
         for (int c = 0; c < D; c++) {
@@ -127,9 +130,14 @@ __global__ void __launch_bounds__(128) k_contract_work(
             nr += (r.x != 0.f || r.y != 0.f);
         }
         acc += 4.0 * (double)nl * (double)nr;
+        cnt += (unsigned long long)(nl + nr);
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xffffffffu, acc, o);
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    }
     if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(flops, acc);
+    if ((threadIdx.x & 31) == 0 && cnt != 0) atomicAdd(nnz, cnt);
 }
 
 // One product of the general form (c D^a u, D^^b v), all 64 x 64 tile pairs of each bin:
@@ -269,21 +277,27 @@ int contract_form(Mesh *m, int axis, bool test_right, const double *wc_gp, int p
     return FEM3_OK;
 }
 
-int contract_work(Mesh *m, double *flops_out) {
+int contract_work(Mesh *m, double *flops_out, int64_t *nnz_out) {
     cudaStream_t s = m->stream;
     double *d = m->norms + 121;
-    FEM3_CUDA(cudaMemsetAsync(d, 0, sizeof(double), s));
+    unsigned long long *c = reinterpret_cast<unsigned long long *>(m->norms + 122);
+    FEM3_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(double), s));
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
         if (B.n_bins == 0 || B.n_tmpl == 0) continue;
         k_contract_work<<<B.n_bins, 128, 0, s>>>(m->tabL[axis], m->tabR[axis], B.gp_off,
-                                                  B.dof_off, B.tab_off, B.tab_ld, d);
+                                                  B.dof_off, B.tab_off, B.tab_ld, d, c);
         note_launch(m);
     }
     FEM3_CUDA(cudaGetLastError());
-    FEM3_CUDA(cudaMemcpyAsync(m->h_norms + 121, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FEM3_CUDA(cudaMemcpyAsync(m->h_norms + 121, d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     FEM3_CUDA(cudaStreamSynchronize(s));
-    *flops_out = m->h_norms[121];
+    if (flops_out) *flops_out = m->h_norms[121];
+    if (nnz_out) {
+        unsigned long long v;
+        memcpy(&v, m->h_norms + 122, sizeof(v));
+        *nnz_out = (int64_t)v;
+    }
     return FEM3_OK;
 }
 

@@ -254,7 +254,8 @@ int walk_paths(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, int ca
 int table_rows(Mesh *m, int axis, int dir, const int64_t *gps, int64_t n, double *rows);
 int contract(Mesh *m, int precision);
 int contract_tc(Mesh *m, bool bf16);   // TF32 x 3 (bf16 = false) or BF16 x 3
-int contract_work(Mesh *m, double *flops);   // algorithmic flops of the element sum (synchronises)
+// algorithmic flops of the element sum and nonzeros of the tables (synchronises)
+int contract_work(Mesh *m, double *flops, int64_t *nnz);
 // general form (c D^a u, D^^b v) of one axis
 int walk_tables_form(Mesh *m, int axis, double order_left, double order_right);
 int weight_coef(Mesh *m, const double *c_gp, double *wc_gp);   // wc = w c per Gauss point

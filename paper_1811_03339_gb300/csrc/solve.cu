@@ -1185,11 +1185,15 @@ constexpr int kApplyGC = 32;                  // Gauss points per chunk
 constexpr int kApplyStride = kApplyGC + 2;    // staged row, float2 units: 272 B, 16-B aligned
 constexpr int kApplyRM = 64;                  // rows per staged piece
 
-// 76,800 bytes at NR = 8: three CTAs per SM (233,472 bytes less 1,024 reserved per CTA)
+// phase-1 partial-sum buffers: one per warp, or four for NR > 8 (warps 4-7 first add into
+// those of warps 0-3)
+template <int NR> __host__ __device__ constexpr int apply_pw() { return NR > 8 ? 4 : 8; }
+// 76,800 bytes at NR = 8: three CTAs per SM (233,472 bytes less 1,024 reserved per CTA);
+// 88,064 bytes at NR = 17: two
 template <int NR>
 constexpr size_t apply_bin_smem() {
-    return (size_t)(2 * kApplyRM * kApplyStride + kApplyRM * NR + 2 * 8 * kApplyGC * NR +
-                    2 * kApplyGC * NR) *
+    return (size_t)(2 * kApplyRM * kApplyStride + kApplyRM * NR +
+                    2 * apply_pw<NR>() * kApplyGC * NR + 2 * kApplyGC * NR) *
                sizeof(float2) +
            kApplyRM * sizeof(int4);
 }
@@ -1318,12 +1322,15 @@ __device__ __forceinline__ void apply_phase2(const float2 *Ls, const float2 *Rs,
                 else zh[k] += xh;
             }
     }
-    if (!act || s != 0) return;
+    // after the butterfly every slice lane holds the row's sums: lane s writes the vectors
+    // k = s (mod S)
+    if (!act) return;
     const int64_t dof = dofs[r];
 #pragma unroll
     for (int k = 0; k < NV; k++) {
         const int v = vg * NV + k;
         if (v >= nv) break;
+        if (k % S != s) continue;
         if constexpr (DF) {
             float ph, pl;
             df_mul(zh[k], zl[k], sKh, sKl, ph, pl);
@@ -1353,11 +1360,11 @@ struct ApplyAxes {
 // u, FMA accumulation), about 1e-6 relative: the refinement's late sweeps, whose residual
 // update r -= A d has a tiny correction d (see solve_refined)
 template <int NR, bool DF = true>
-__global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_constant__ ApplyAxes P,
-                                                             const double *__restrict__ u, int nv,
-                                                             double *Au, int64_t ldA) {
-    static_assert(NR == 1 || NR == 4 || NR == 8, "vectors per pass");
-    constexpr int RM = kApplyRM;
+__global__ void __launch_bounds__(kApplyThreads, NR > 8 ? 2 : 3)
+    k_apply_bin(const __grid_constant__ ApplyAxes P, const double *__restrict__ u, int nv,
+                double *Au, int64_t ldA) {
+    static_assert(NR == 1 || NR == 4 || NR == 8 || NR == 17, "vectors per pass");
+    constexpr int RM = kApplyRM, PW = apply_pw<NR>();
     int b = blockIdx.x, axis = 0;
     while (axis < 2 && b >= P.a[axis].n_bins) b -= P.a[axis++].n_bins;
     const ApplyAxis &X = P.a[axis];
@@ -1370,9 +1377,9 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
     float2 *Ls = sm_apply;                       // [RM][34]
     float2 *Rs = Ls + RM * kApplyStride;         // [RM][34]
     float2 *us = Rs + RM * kApplyStride;         // [RM][NR]
-    float2 *pL = us + RM * NR;                   // [8][32][NR] phase-1 partial sums, L u
-    float2 *pR = pL + 8 * kApplyGC * NR;         // [8][32][NR] R~ u
-    float2 *yL = pR + 8 * kApplyGC * NR;         // [32][NR]
+    float2 *pL = us + RM * NR;                   // [PW][32][NR] phase-1 partial sums, L u
+    float2 *pR = pL + PW * kApplyGC * NR;        // [PW][32][NR] R~ u
+    float2 *yL = pR + PW * kApplyGC * NR;        // [32][NR]
     float2 *yR = yL + kApplyGC * NR;             // [32][NR]
     int4 *Qs = reinterpret_cast<int4 *>(yR + kApplyGC * NR);   // [RM] row ranges
     const int d0 = dof_off[b], D = dof_off[b + 1] - d0;
@@ -1424,17 +1431,46 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
                 }
             }
         }
+        if constexpr (PW == 8) {
 #pragma unroll
-        for (int v = 0; v < NR; v++) {
-            pL[(warp * kApplyGC + lane) * NR + v] = make_float2(lh[v], ll[v]);
-            pR[(warp * kApplyGC + lane) * NR + v] = make_float2(rh[v], rl[v]);
+            for (int v = 0; v < NR; v++) {
+                pL[(warp * kApplyGC + lane) * NR + v] = make_float2(lh[v], ll[v]);
+                pR[(warp * kApplyGC + lane) * NR + v] = make_float2(rh[v], rl[v]);
+            }
+        } else {
+            // warps 4-7 store, warps 0-3 add their own sums to them
+            const int w4 = warp & 3;
+            if (warp >= 4) {
+#pragma unroll
+                for (int v = 0; v < NR; v++) {
+                    pL[(w4 * kApplyGC + lane) * NR + v] = make_float2(lh[v], ll[v]);
+                    pR[(w4 * kApplyGC + lane) * NR + v] = make_float2(rh[v], rl[v]);
+                }
+            }
+            __syncthreads();
+            if (warp < 4) {
+#pragma unroll
+                for (int v = 0; v < NR; v++) {
+                    const int e = (w4 * kApplyGC + lane) * NR + v;
+                    const float2 x = pL[e], z = pR[e];
+                    if constexpr (DF) {
+                        df_add(x.x, x.y, lh[v], ll[v]);
+                        df_add(z.x, z.y, rh[v], rl[v]);
+                    } else {
+                        lh[v] += x.x;
+                        rh[v] += z.x;
+                    }
+                    pL[e] = make_float2(lh[v], ll[v]);
+                    pR[e] = make_float2(rh[v], rl[v]);
+                }
+            }
         }
         __syncthreads();
         for (int e = tid; e < kApplyGC * NR; e += kApplyThreads) {
             float2 a = pL[e], c = pR[e];
             float ah = a.x, al = a.y, ch = c.x, cl = c.y;
 #pragma unroll
-            for (int w = 1; w < 8; w++) {
+            for (int w = 1; w < PW; w++) {
                 const float2 x = pL[w * kApplyGC * NR + e], z = pR[w * kApplyGC * NR + e];
                 if constexpr (DF) {
                     df_add(x.x, x.y, ah, al);
@@ -1473,6 +1509,13 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
                 else
                     apply_phase2<4, 1, 1, DF>(Ls, Rs, Qs, yL, yR, rn, gc0, gn, dofs, sKh, sKl, nv,
                                               Au, ldA);
+            } else if constexpr (NR == 17) {
+                if (rn <= 32)
+                    apply_phase2<17, 17, 8, DF>(Ls, Rs, Qs, yL, yR, rn, gc0, gn, dofs, sKh, sKl,
+                                                nv, Au, ldA);
+                else
+                    apply_phase2<17, 17, 4, DF>(Ls, Rs, Qs, yL, yR, rn, gc0, gn, dofs, sKh, sKl,
+                                                nv, Au, ldA);
             } else {
                 if (rn <= 32)
                     apply_phase2<1, 1, 8, DF>(Ls, Rs, Qs, yL, yR, rn, gc0, gn, dofs, sKh, sKl, nv,
@@ -1486,10 +1529,11 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply_bin(const __grid_consta
 }
 
 // Au = A u for nv vectors (column-major, leading dimension n_dof), applied from
-// the tables; vectors go through the tables in groups of up to eight per pass, and a last
-// group of one or up to four vectors takes the narrower form of the kernel (the pass costs
-// about its vectors' arithmetic: an eight-wide pass for one leftover vector cost as much as
-// a full group).
+// the tables; vectors go through the tables in groups: up to 17 per pass while at least 13
+// are left, then up to eight, and a last group of one or up to four vectors takes the
+// narrower form of the kernel (a pass costs a fixed part, staging and the phases' overhead,
+// plus about its vectors' arithmetic: an eight-wide pass for one leftover vector cost as much
+// as a full group).
 int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d, bool df) {
     cudaStream_t s = m->stream;
     const int64_t n = m->n_dof;
@@ -1511,11 +1555,17 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d, bool df) {
         FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<8, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)apply_bin_smem<8>()));
+        FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<17>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)apply_bin_smem<17>()));
+        FEM3_CUDA(cudaFuncSetAttribute(k_apply_bin<17, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)apply_bin_smem<17>()));
         attr = true;
     }
     FEM3_TRY(ap_prepare(m));
     double *ui = nullptr;
-    if (nv > 1) FEM3_CUDA(cudaMallocAsync((void **)&ui, sizeof(double) * 8 * std::max<int64_t>(1, n), s));
+    if (nv > 1)
+        FEM3_CUDA(cudaMallocAsync((void **)&ui, sizeof(double) * 17 * std::max<int64_t>(1, n), s));
     ApplyAxes P;
     int64_t nblk = 0;
     for (int axis = 0; axis < 3; axis++) {
@@ -1526,30 +1576,34 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d, bool df) {
                               B.tab_ld, B.tab_off, skh, skl, on ? B.n_bins : 0};
         nblk += on ? B.n_bins : 0;
     }
-    for (int v0 = 0; v0 < nv && nblk > 0; v0 += 8) {
-        const int cnt = std::min(8, nv - v0);
+    for (int v0 = 0, cnt = 0; v0 < nv && nblk > 0; v0 += cnt) {
+        const int left = nv - v0;
+        const int nri = left >= 13 ? 17 : (left >= 5 ? 8 : (left >= 2 ? 4 : 1));
+        cnt = std::min(nri, left);
         double *out = Au_d + (int64_t)v0 * n;
-        if (cnt > 1) {
-            const int nri = cnt <= 4 ? 4 : 8;
-            if (nri == 4)
-                k_interleave<4><<<g256(4 * n), 256, 0, s>>>(u_d + (int64_t)v0 * n, n, cnt, ui);
-            else
-                k_interleave<8><<<g256(8 * n), 256, 0, s>>>(u_d + (int64_t)v0 * n, n, cnt, ui);
-            note_launch(m);
-        }
+        if (nri == 4)
+            k_interleave<4><<<g256(4 * n), 256, 0, s>>>(u_d + (int64_t)v0 * n, n, cnt, ui);
+        else if (nri == 8)
+            k_interleave<8><<<g256(8 * n), 256, 0, s>>>(u_d + (int64_t)v0 * n, n, cnt, ui);
+        else if (nri == 17)
+            k_interleave<17><<<g256(17 * n), 256, 0, s>>>(u_d + (int64_t)v0 * n, n, cnt, ui);
+        if (nri > 1) note_launch(m);
         kc_begin(m, KC_APPLY);
 #define FEM3_APPLY(NR_, DF_, U_, CNT_)                                                          \
     k_apply_bin<NR_, DF_><<<(unsigned)nblk, kApplyThreads, apply_bin_smem<NR_>(), s>>>(P, U_, CNT_, \
                                                                                    out, n)
-        if (cnt == 1) {
+        if (nri == 1) {
             if (df) FEM3_APPLY(1, true, u_d + (int64_t)v0 * n, 1);
             else FEM3_APPLY(1, false, u_d + (int64_t)v0 * n, 1);
-        } else if (cnt <= 4) {
+        } else if (nri == 4) {
             if (df) FEM3_APPLY(4, true, ui, cnt);
             else FEM3_APPLY(4, false, ui, cnt);
-        } else {
+        } else if (nri == 8) {
             if (df) FEM3_APPLY(8, true, ui, cnt);
             else FEM3_APPLY(8, false, ui, cnt);
+        } else {
+            if (df) FEM3_APPLY(17, true, ui, cnt);
+            else FEM3_APPLY(17, false, ui, cnt);
         }
 #undef FEM3_APPLY
         kc_end(m, KC_APPLY);

@@ -28,6 +28,7 @@ SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_assemble
            "fem3_load", "fem3_solve",
            "fem3_adjoint", "fem3_vjp", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
            "fem3_counters", "fem3_bin_stats", "fem3_kernel_ms", "fem3_contract_work",
+           "fem3_table_nnz",
            "fem3_tc_tile",
            "fem3_last_error",
            "fem3_mesh_free",
@@ -85,6 +86,7 @@ def load_library(build_if_missing: bool = True):
         "fem3_bin_stats": [p, ci, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)],
         "fem3_kernel_ms": [p, ci, C.POINTER(C.c_float), C.POINTER(i32)],
         "fem3_contract_work": [p, C.POINTER(dbl), p],
+        "fem3_table_nnz": [p, C.POINTER(i64), p],
         "fem3_last_error": [C.c_char_p, C.c_size_t],
         "fem3_mesh_free": [p],
         "fem3_spd_solve_static": [p, i64, p, p, p],
@@ -236,6 +238,12 @@ def contract_work(h, stream=None):
     f = C.c_double(0)
     _check(_lib.fem3_contract_work(h, C.byref(f), _stream(stream)))
     return f.value
+
+
+def table_nnz(h, stream=None):
+    v = C.c_int64(0)
+    _check(_lib.fem3_table_nnz(h, C.byref(v), _stream(stream)))
+    return v.value
 
 
 KERNEL_CLASSES = ("walk_tables", "split", "contract", "factor", "chain", "apply")
@@ -414,6 +422,10 @@ class Mesh:
     def contract_work(self):
         """algorithmic flops of the last contraction: sum_g 4 nnz(L[g]) nnz(R[g]) per axis"""
         return contract_work(self.h, self.stream)
+
+    def table_nnz(self):
+        """nonzeros of the last assemble's tables: sum over axes and g of nnz(L[g]) + nnz(R[g])"""
+        return table_nnz(self.h, self.stream)
 
     def kernel_ms(self):
         """{kernel class: (ms, launches)} timed on the launch stream (profiling handles)"""

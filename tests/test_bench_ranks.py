@@ -100,6 +100,11 @@ def test_kernel_rooflines():
     a = r["apply"]
     assert a["achieved"] == pytest.approx(4 * 13 * 134e6 * 51 / 24.0e-3 / 1e12)
     assert a["peak"] == pytest.approx(152 * 128 * 2.070 / 1e3)
+    # with the tables' nonzeros counted: 2 multiply-adds per nonzero of L or R and vector
+    nz = bench.kernel_rooflines(kms, dict(cnt, table_nnz=150_000_000), 12167, "bf16x3", peaks,
+                                "parallelepiped24")["apply"]
+    assert nz["achieved"] == pytest.approx(2 * 13 * 150e6 * 51 / 24.0e-3 / 1e12)
+    assert nz["nonzero_fraction_of_bin_tables"] == pytest.approx(150e6 / (2 * 134e6))
     assert r["chain"]["launch_ms"] == pytest.approx(0.5)
     t = bench.kernel_rooflines(kms, cnt, 12167, "tf32x3", peaks, "parallelepiped24")
     assert t["contract"]["peak"] == pytest.approx(1894.9 * 1.1 / 2.25)

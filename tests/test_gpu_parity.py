@@ -237,10 +237,12 @@ def test_reassemble_same_mesh(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
-@pytest.mark.parametrize("nrhs", [16, 21])
+@pytest.mark.parametrize("nrhs", [16, 17, 21, 30])
 def test_many_right_hand_sides(precision, nrhs):
-    """Columns go through the wavefront solve 16 at a time and through the table operator
-    8 at a time; every column must match the oracle."""
+    """Columns go through the wavefront solve up to 24 at a time and through the table
+    operator in groups of up to 17 (while 13 or more are left), 8, 4 or 1 (16: one group of
+    17 slots; 21: 17 + 4; 30: 17 + 13 and 24 + 6 in the solve); every column must match the
+    oracle."""
     mesh, o, alpha, K = _case("cube7_jitter")
     f = np.random.default_rng(nrhs).standard_normal((mesh.n_nodes, nrhs))
     m = fem3.Mesh(mesh.verts, mesh.tets)
@@ -488,6 +490,9 @@ def test_contraction_work_counts_the_oracle_nonzeros():
         L, R = o.tables(axis, alpha[axis] / 2)
         exp += 4 * int(np.sum((L != 0).sum(1).astype(np.int64) * (R != 0).sum(1)))
     assert got == exp
+    nnz = sum(int((L != 0).sum() + (R != 0).sum())
+              for L, R in (o.tables(a, alpha[a] / 2) for a in range(3)))
+    assert m.table_nnz() == nnz
     m.free()
 
 
