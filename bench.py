@@ -36,7 +36,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HEADLINE = "parallelepiped24"
-DEFAULT_PRECISION = {"parallelepiped24": "bf16x3", "cube16_jitter": "tf32x3"}
+DEFAULT_PRECISION = {"parallelepiped24": "bf16x3", "cube16_jitter": "tf32x3",
+                     "parallelepiped16": "bf16x3"}
 METRIC = "gauss_point_paths_per_s"
 UNIT = "paths/s"
 L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
@@ -650,7 +651,8 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=HEADLINE, choices=["parallelepiped24", "cube16_jitter"])
+    ap.add_argument("--workload", default=HEADLINE,
+                    choices=["parallelepiped24", "cube16_jitter", "parallelepiped16"])
     ap.add_argument("--precision", default=None, choices=["tf32x3", "bf16x3", "fp32", "fp64"],
                     help="default: bf16x3 for the parallelepiped, tf32x3 for the cube")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -33,11 +33,15 @@ CUBE16_JITTER = dict(n=16, jitter=0.2, seed=1, affine=None,
 PARALLELEPIPED24 = dict(n=24, jitter=0.15, seed=2,
                         affine=((1.0, 0.3, 0.0), (0.0, 1.0, 0.2), (0.0, 0.0, 0.7)),
                         alpha=(1.2, 1.5, 1.9), K=(1.0, 1.0, 1.0))
+# the same parallelepiped recipe at 16^3 cells (3,375 dofs, the same 17 right-hand sides):
+# kernel profiles that need a few GB on the device at most
+PARALLELEPIPED16 = dict(PARALLELEPIPED24, n=16)
 
 WORKLOADS = {
     "cube4": CUBE4,
     "cube16_jitter": CUBE16_JITTER,
     "parallelepiped24": PARALLELEPIPED24,
+    "parallelepiped16": PARALLELEPIPED16,
 }
 
 
