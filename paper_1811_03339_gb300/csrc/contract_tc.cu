@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) k_split_ops(
     const int32_t *__restrict__ gp_off, const double *__restrict__ w_slot,
     const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
     int64_t row_lo, int64_t n_rows, int Kp, OT *Lhi, OT *Llo, OT *Rhi, OT *Rlo, float2 *apR,
-    int4 *rng) {
+    int4 *rng, RowLists rl) {
     const int64_t row = row_lo + blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n_rows) return;
@@ -98,10 +98,15 @@ __global__ void __launch_bounds__(256) k_split_ops(
     // the GEMM reads a bin's operands up to G rounded to one 128-byte row (kbk Gauss points)
     const int kbk = 128 / (int)sizeof(OT);
     const int kend = Lhi ? min(Kp, (G + kbk - 1) / kbk * kbk) : G;
-    // Gauss-point range [first, end) of the row's nonzeros in L and in W R
-    int lf = G, le = 0, rf = G, re = 0;
-    for (int k = lane; k < kend; k += 32) {
-        OT lh = OT(0.f), ll = OT(0.f), rh = OT(0.f), rl = OT(0.f);
+    // Gauss-point range [first, end) of the row's nonzeros in L and in W R; the nonzeros
+    // themselves compacted in Gauss-point order (lanes in step: one ballot per 32 points)
+    int lf = G, le = 0, rf = G, re = 0, nl = 0, nr = 0;
+    const unsigned below = (1u << lane) - 1u;
+    for (int k0 = 0; k0 < kend; k0 += 32) {
+        const int k = k0 + lane;
+        OT lh = OT(0.f), ll = OT(0.f), rh = OT(0.f), rl2 = OT(0.f);
+        float2 lv = make_float2(0.f, 0.f), rv = make_float2(0.f, 0.f);
+        bool nzl = false, nzr = false;
         if (k < G) {
             const float2 lp = tabL[src + k], rp = tabR[src + k];
             const float a = lp.x, a2 = lp.y, r1 = rp.x, r2 = rp.y;
@@ -110,32 +115,120 @@ __global__ void __launch_bounds__(256) k_split_ops(
             float sh = 0.f, sl = 0.f;
             df_fma(r1, r2, wh, wl, sh, sl);
             const float wr = sh + sl, wr2 = sl - (wr - sh);
-            apR[src + k] = make_float2(wr, wr2);
-            if (a != 0.f || a2 != 0.f) {
+            if (apR) apR[src + k] = make_float2(wr, wr2);
+            lv = lp;
+            rv = make_float2(wr, wr2);
+            nzl = a != 0.f || a2 != 0.f;
+            nzr = wr != 0.f || wr2 != 0.f;
+            if (nzl) {
                 lf = min(lf, k);
                 le = k + 1;
             }
-            if (wr != 0.f || wr2 != 0.f) {
+            if (nzr) {
                 rf = min(rf, k);
                 re = k + 1;
             }
             if (Lhi) {
                 Split<OT>::run(a, a2, lh, ll);
-                Split<OT>::run(wr, wr2, rh, rl);
+                Split<OT>::run(wr, wr2, rh, rl2);
             }
         }
-        if (Lhi) {
+        if (Lhi && k < kend) {
             Lhi[dst + k] = lh;
             Llo[dst + k] = ll;
             Rhi[dst + k] = rh;
-            Rlo[dst + k] = rl;
+            Rlo[dst + k] = rl2;
+        }
+        if (rl.g0) {
+            const unsigned bl = __ballot_sync(0xffffffffu, nzl), br = __ballot_sync(0xffffffffu, nzr);
+            if (nzl) {
+                const int64_t o = src + nl + __popc(bl & below);
+                rl.g0[o] = (uint16_t)k;
+                rl.v0[o] = lv;
+            }
+            if (nzr) {
+                const int64_t o = src + nr + __popc(br & below);
+                rl.g1[o] = (uint16_t)k;
+                rl.v1[o] = rv;
+            }
+            nl += __popc(bl);
+            nr += __popc(br);
         }
     }
     lf = __reduce_min_sync(0xffffffffu, lf);
     le = __reduce_max_sync(0xffffffffu, le);
     rf = __reduce_min_sync(0xffffffffu, rf);
     re = __reduce_max_sync(0xffffffffu, re);
-    if (lane == 0) rng[row] = make_int4(le > 0 ? lf : 0, le, re > 0 ? rf : 0, re);
+    if (lane == 0) {
+        rng[row] = make_int4(le > 0 ? lf : 0, le, re > 0 ? rf : 0, re);
+        if (rl.g0) {
+            rl.n0[row] = nl;
+            rl.n1[row] = nr;
+        }
+    }
+}
+
+// Gauss-point-major lists of the nonzeros of L and W R, one CTA per bin: warp w takes the
+// chunks of 32 Gauss points w, w + 8, ... (lane = point), walks the rows in order (loads
+// along the Gauss points, eight rows in flight) and appends (the row's index in the bin,
+// value) to the point's list.  Entry k of point g = 32 c + l (chunk c of width w_c <= 32) sits
+// at tab_off[b] + 32 c D_b + k w_c + l: the lanes of a chunk at the same entry are adjacent
+// (coalesced stores here and loads in the apply), and the chunks fill the bin's D_b x ld_b
+// block (w_c summed over the chunks is G_b <= ld_b).
+constexpr int kGpRows = 8;
+__global__ void __launch_bounds__(256) k_gp_lists(
+    const float2 *__restrict__ tabL, const float2 *__restrict__ tabR,
+    const double *__restrict__ w_slot, const int32_t *__restrict__ gp_off,
+    const int32_t *__restrict__ dof_off,
+    const int64_t *__restrict__ tab_off, const int32_t *__restrict__ tab_ld,
+    uint16_t *__restrict__ rL, float2 *__restrict__ vL, int32_t *__restrict__ nL,
+    uint16_t *__restrict__ rR, float2 *__restrict__ vR, int32_t *__restrict__ nR) {
+    const int b = blockIdx.x;
+    const int D = dof_off[b + 1] - dof_off[b];
+    const int g0 = gp_off[b], G = gp_off[b + 1] - g0, ld = tab_ld[b];
+    const int64_t t0 = tab_off[b];
+    const float2 *L = tabL + t0, *R = tabR + t0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int gc = 32 * warp; gc < G; gc += 256) {
+        const int g = gc + lane, wc = min(32, G - gc);
+        if (g >= G) continue;
+        const int64_t base = t0 + (int64_t)gc * D + lane;
+        float wh, wl;   // the point's weight; W R formed as in k_split_ops (the same values)
+        f64_split(w_slot[g0 + g], wh, wl);
+        int nl = 0, nr = 0;
+        for (int c0 = 0; c0 < D; c0 += kGpRows) {
+            float2 a[kGpRows], w[kGpRows];
+#pragma unroll
+            for (int j = 0; j < kGpRows; j++) {
+                const int c = min(c0 + j, D - 1);   // rows past D repeat the last (not used)
+                a[j] = __ldg(L + (int64_t)c * ld + g);
+                w[j] = __ldg(R + (int64_t)c * ld + g);
+            }
+#pragma unroll
+            for (int j = 0; j < kGpRows; j++) {
+                float sh = 0.f, sl = 0.f;
+                df_fma(w[j].x, w[j].y, wh, wl, sh, sl);
+                const float wr = sh + sl;
+                w[j] = make_float2(wr, sl - (wr - sh));
+            }
+#pragma unroll
+            for (int j = 0; j < kGpRows; j++) {
+                if (c0 + j >= D) break;
+                if (a[j].x != 0.f || a[j].y != 0.f) {
+                    rL[base + (int64_t)nl * wc] = (uint16_t)(c0 + j);
+                    vL[base + (int64_t)nl * wc] = a[j];
+                    nl++;
+                }
+                if (w[j].x != 0.f || w[j].y != 0.f) {
+                    rR[base + (int64_t)nr * wc] = (uint16_t)(c0 + j);
+                    vR[base + (int64_t)nr * wc] = w[j];
+                    nr++;
+                }
+            }
+        }
+        nL[g0 + g] = nl;
+        nR[g0 + g] = nr;
+    }
 }
 
 // ------------------------------- GEMM kernel --------------------------------------
@@ -453,6 +546,7 @@ int contract_tc(Mesh *m, bool bf16) {
         }
         if (!B.tc_n_work[0]) continue;
         FEM3_TRY(ap_alloc(m, axis));
+        const bool whole = m->nparts <= 1;   // a part's apply operands are not kept
         const int kbk = bf16 ? 64 : 32;   // Gauss points per 128-byte swizzle row
         const int Kp = std::max(kbk, (B.tc_maxG + kbk - 1) / kbk * kbk);
         // template rows of this part's bins (all rows unless assembled in parts)
@@ -466,14 +560,17 @@ int contract_tc(Mesh *m, bool bf16) {
             for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<__nv_bfloat16 *>(B.tc_op[q]);
             k_split_ops<__nv_bfloat16><<<grid, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
-                B.tab_off, B.tab_ld, row_lo, row_hi, Kp, op[0], op[1], op[2], op[3], B.ap_R, B.ap_rng);
+                B.tab_off, B.tab_ld, row_lo, row_hi, Kp, op[0], op[1], op[2], op[3], B.ap_R, B.ap_rng,
+                whole ? row_lists(B) : RowLists{});
         } else {
             float *op[4];
             for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<float *>(B.tc_op[q]);
             k_split_ops<float><<<grid, 256, 0, s>>>(
                 m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot,
-                B.tab_off, B.tab_ld, row_lo, row_hi, Kp, op[0], op[1], op[2], op[3], B.ap_R, B.ap_rng);
+                B.tab_off, B.tab_ld, row_lo, row_hi, Kp, op[0], op[1], op[2], op[3], B.ap_R, B.ap_rng,
+                whole ? row_lists(B) : RowLists{});
         }
+        if (whole) launch_gp_lists(m, axis);
         kc_end(m, KC_SPLIT);
         note_launch(m);
         for (int q = 0; q < 4; q++)
@@ -565,13 +662,14 @@ int contract_tc_form(Mesh *m, int axis, bool test_right, double *wc_gp, bool bf1
         for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<__nv_bfloat16 *>(B.tc_op[q]);
         k_split_ops<__nv_bfloat16><<<grid, 256, 0, s>>>(T, S, B.row_bin, B.dof_off, B.gp_off, ws,
                                                          B.tab_off, B.tab_ld, 0, B.n_tmpl, Kp,
-                                                         op[0], op[1], op[2], op[3], B.ap_R, B.ap_rng);
+                                                         op[0], op[1], op[2], op[3], B.ap_R, B.ap_rng,
+                                                         RowLists{});
     } else {
         float *op[4];
         for (int q = 0; q < 4; q++) op[q] = reinterpret_cast<float *>(B.tc_op[q]);
         k_split_ops<float><<<grid, 256, 0, s>>>(T, S, B.row_bin, B.dof_off, B.gp_off, ws,
                                                 B.tab_off, B.tab_ld, 0, B.n_tmpl, Kp, op[0],
-                                                op[1], op[2], op[3], B.ap_R, B.ap_rng);
+                                                op[1], op[2], op[3], B.ap_R, B.ap_rng, RowLists{});
     }
     kc_end(m, KC_SPLIT);
     note_launch(m);
@@ -589,11 +687,37 @@ int contract_tc_form(Mesh *m, int axis, bool test_right, double *wc_gp, bool bf1
 
 int ap_alloc(Mesh *m, int axis) {
     AxisBins &B = m->bins[axis];
-    if (B.ap_R) return FEM3_OK;
-    const int64_t e = std::max<int64_t>(1, B.tab_elems);
-    FEM3_TRY(dev_alloc(m, (void **)&B.ap_R, sizeof(float2) * e));
-    FEM3_TRY(dev_alloc(m, (void **)&B.ap_rng, sizeof(int4) * std::max<int64_t>(1, B.n_tmpl)));
+    if (B.ap_rng) return FEM3_OK;
+    const int64_t e = std::max<int64_t>(1, B.tab_elems), nt = std::max<int64_t>(1, B.n_tmpl);
+    const int64_t ng = std::max<int64_t>(1, m->n_gp);
+    FEM3_TRY(dev_alloc(m, (void **)&B.ap_rng, sizeof(int4) * nt));
+    if (!apply_lists_fit(m)) {   // the dense apply's W R operand instead of the lists
+        FEM3_TRY(dev_alloc(m, (void **)&B.ap_R, sizeof(float2) * e));
+        return FEM3_OK;
+    }
+    for (int t = 0; t < 2; t++) {
+        FEM3_TRY(dev_alloc(m, (void **)&B.rl_g[t], sizeof(uint16_t) * e));
+        FEM3_TRY(dev_alloc(m, (void **)&B.rl_v[t], sizeof(float2) * e));
+        FEM3_TRY(dev_alloc(m, (void **)&B.rl_n[t], sizeof(int32_t) * nt));
+        FEM3_TRY(dev_alloc(m, (void **)&B.gl_r[t], sizeof(uint16_t) * e));
+        FEM3_TRY(dev_alloc(m, (void **)&B.gl_v[t], sizeof(float2) * e));
+        FEM3_TRY(dev_alloc(m, (void **)&B.gl_n[t], sizeof(int32_t) * ng));
+    }
     return FEM3_OK;
+}
+
+RowLists row_lists(AxisBins &B) {
+    return RowLists{B.rl_g[0], B.rl_g[1], B.rl_v[0], B.rl_v[1], B.rl_n[0], B.rl_n[1]};
+}
+
+void launch_gp_lists(Mesh *m, int axis) {
+    AxisBins &B = m->bins[axis];
+    if (B.n_bins == 0 || !B.gl_r[0]) return;
+    k_gp_lists<<<B.n_bins, 256, 0, m->stream>>>(m->tabL[axis], m->tabR[axis], B.w_slot,
+                                                 B.gp_off, B.dof_off, B.tab_off, B.tab_ld,
+                                                 B.gl_r[0], B.gl_v[0], B.gl_n[0], B.gl_r[1],
+                                                 B.gl_v[1], B.gl_n[1]);
+    note_launch(m);
 }
 
 // Operator-apply operands of the current tables, without the tensor-core operands.
@@ -607,7 +731,9 @@ int ap_prepare(Mesh *m) {
         kc_begin(m, KC_SPLIT);
         k_split_ops<float><<<(unsigned)((B.n_tmpl + 7) / 8), 256, 0, s>>>(
             m->tabL[axis], m->tabR[axis], B.row_bin, B.dof_off, B.gp_off, B.w_slot, B.tab_off,
-            B.tab_ld, 0, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_R, B.ap_rng);
+            B.tab_ld, 0, B.n_tmpl, 0, nullptr, nullptr, nullptr, nullptr, B.ap_R, B.ap_rng,
+            row_lists(B));
+        launch_gp_lists(m, axis);
         kc_end(m, KC_SPLIT);
         note_launch(m);
     }

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include <string>
@@ -73,6 +75,17 @@ struct AxisBins {
     // [n_tmpl] Gauss-point ranges [first, end) of the nonzeros of each row of L and of R
     // (x, y: L; z, w: R), written with the apply operands
     int4 *ap_rng = nullptr;
+    // the nonzeros of L and W R (t = 0: L, 1: W R) as lists, written with the apply operands:
+    // row-major, a template row's list in the place of its dense table row (Gauss-point index
+    // in the bin, value), and Gauss-point major in chunks of 32 points within the bin's block
+    // (row index in the bin, value; layout at k_gp_lists); list lengths per template row and
+    // per Gauss-point slot
+    uint16_t *rl_g[2] = {nullptr, nullptr};
+    float2 *rl_v[2] = {nullptr, nullptr};
+    int32_t *rl_n[2] = {nullptr, nullptr};
+    uint16_t *gl_r[2] = {nullptr, nullptr};
+    float2 *gl_v[2] = {nullptr, nullptr};
+    int32_t *gl_n[2] = {nullptr, nullptr};
     int64_t *tab_off = nullptr;  // [n_bins]     element offset of the bin's table block
     int32_t *tab_ld = nullptr;   // [n_bins]     leading dimension (padded Gauss-point count)
     int64_t n_tmpl = 0, tab_elems = 0;
@@ -229,6 +242,13 @@ void kc_reset(Mesh *m);
 int scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s, Mesh *m);
 
 // scratch of the batched walk (descriptor arrays; freed by the batch)
+// row-major lists of a table pair (L, W R) as k_split_ops writes them (null: not written)
+struct RowLists {
+    uint16_t *g0, *g1;   // Gauss-point index in the bin
+    float2 *v0, *v1;     // L, W R values (hi + lo)
+    int32_t *n0, *n1;    // [n_tmpl] lengths
+};
+
 struct BatchWalkScratch {
     void *d_desc = nullptr, *h_desc = nullptr;
 };
@@ -290,6 +310,23 @@ int residual_norm(Mesh *m, const double *b, const double *Au, double *rel);
 
 int ap_alloc(Mesh *m, int axis);   // operator-apply operand buffers of one axis
 int ap_prepare(Mesh *m);           // split the current tables into the apply operands
+// The operator apply runs from the lists of the tables' nonzeros when a bin's u rows and its
+// Gauss points' sums of 17 vectors fit the list kernel's shared memory; otherwise from the
+// dense table blocks (with the W R operand in the table layout)
+constexpr size_t kListSmemMax = 112 * 1024;   // two CTAs per SM
+inline size_t apply_lists_smem(int nr, int max_dof, int max_gp) {
+    return 8 * (size_t)nr * ((size_t)max_dof + 2 * (size_t)max_gp);
+}
+inline bool apply_lists_fit(const Mesh *m) {
+    int md = 0, mg = 0;
+    for (int a = 0; a < 3; a++) {
+        md = std::max(md, m->bins[a].max_dof);
+        mg = std::max(mg, m->bins[a].max_gp);
+    }
+    return apply_lists_smem(17, md, mg) <= kListSmemMax;
+}
+RowLists row_lists(AxisBins &B);   // the axis's row-major list arrays
+void launch_gp_lists(Mesh *m, int axis);   // Gauss-point-major lists of L and W R
 
 // ---------------------------------------------------------------------------------
 // FP64 values in FP32 arithmetic.  GB300 runs FP64 arithmetic and f64 <-> f32

@@ -1528,6 +1528,173 @@ __global__ void __launch_bounds__(kApplyThreads, NR > 8 ? 2 : 3)
     }
 }
 
+// The same operator from the lists of the tables' nonzeros (the Gauss-point-major and
+// row-major lists that k_gp_lists and k_split_ops write with the apply operands): the work is
+// the nonzeros, about a fifth of the dense bin blocks (a Gauss point's line crosses the
+// element patches of a few of its bin's template dofs).  One CTA per bin:
+//   phase 0: u of the bin's template rows into shared memory (hi + lo pairs, [D][NR]);
+//   phase 1, warp = chunk of 32 Gauss points, lane = point: yL[g] = sum over g's L list of
+//     L[r][g] u[r] and yR[g] over its W R list, all NR vectors, into shared memory (the chunk
+//     layout puts the lanes' entries k side by side);
+//   phase 2, thread = (template row r, group of NV vectors): z = sum over r's L list of
+//     L[r][g] yR[g] + over its W R list of (W R)[r][g] yL[g]; Au[dof(r)] += s K z (FP64
+//     atomics of the double-float parts, as in k_apply_bin).
+// With rows and Gauss points ordered along the axis, a point's L list grows along the bin as
+// its W R list shrinks (and likewise for a row), so the lanes of a warp do similar work.
+// u comes split into hi + lo FP32 pairs, [dof][NR] (k_split_vec).  The bin's rows, Gauss
+// points and their NR sums must fit the launch's shared memory (apply_multi checks).
+template <int NR>
+__global__ void k_split_vec(const double *__restrict__ u, int64_t n, int nv, float2 *uf) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= NR * n) return;
+    const int64_t i = e / NR;
+    const int v = (int)(e - i * NR);
+    float h = 0.f, l = 0.f;
+    if (v < nv) f64_split(u[(int64_t)v * n + i], h, l);
+    uf[e] = make_float2(h, l);
+}
+
+struct ListAxis {
+    const uint16_t *rg[2];          // row-major lists: Gauss-point index, value (t = 0 L, 1 W R)
+    const float2 *rv[2];
+    const int32_t *rn[2];
+    const uint16_t *gr[2];          // Gauss-point-major lists (chunk layout): row index, value
+    const float2 *gv[2];
+    const int32_t *gn[2];
+    const int32_t *gp_off, *dof_off, *dof_idx, *tab_ld;
+    const int64_t *tab_off;
+    float sKh, sKl;
+    int n_bins;
+};
+struct ListAxes {
+    ListAxis a[3];
+};
+
+constexpr int kListThreads = 256;
+constexpr int kListBatch = 2;   // list entries whose loads are in flight together
+
+template <int NR, int VS, bool DF>
+__global__ void __launch_bounds__(kListThreads) k_apply_lists(const __grid_constant__ ListAxes P,
+                                                              const float2 *__restrict__ uf,
+                                                              int nv, double *Au, int64_t ldA,
+                                                              int max_dof) {
+    constexpr int NV = (NR + VS - 1) / VS;   // phase-2 vectors per thread (the last group short)
+    int b = blockIdx.x, axis = 0;
+    while (axis < 2 && b >= P.a[axis].n_bins) b -= P.a[axis++].n_bins;
+    const ListAxis &X = P.a[axis];
+    const int d0 = X.dof_off[b], D = X.dof_off[b + 1] - d0;
+    const int g0 = X.gp_off[b], G = X.gp_off[b + 1] - g0;
+    if (D == 0 || G == 0) return;
+    const int ld = X.tab_ld[b];
+    const int64_t t0 = X.tab_off[b];
+    extern __shared__ __align__(16) float2 sm_lists[];
+    float2 *us = sm_lists;                         // [max_dof][NR]
+    float2 *yL = us + (int64_t)max_dof * NR;       // [G][NR]
+    float2 *yR = yL + (int64_t)G * NR;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // ---- phase 0 ----
+    for (int e = tid; e < D * NR; e += kListThreads) {
+        const int c = e / NR, v = e - c * NR;
+        us[e] = __ldg(uf + (int64_t)__ldg(X.dof_idx + d0 + c) * NR + v);
+    }
+    __syncthreads();
+    // ---- phase 1: warp = (chunk of 32 Gauss points, table), lane = point ----
+    const int nchunk = (G + 31) >> 5;
+    for (int wi = warp; wi < 2 * nchunk; wi += kListThreads / 32) {
+        const int gc = 32 * (wi >> 1), t = wi & 1;
+        const int g = gc + lane, wc = min(32, G - gc);
+        const bool in = g < G;
+        const int64_t base = t0 + (int64_t)gc * D + lane;
+        {
+            float h[NR], l[NR];
+#pragma unroll
+            for (int k = 0; k < NR; k++) { h[k] = 0.f; l[k] = 0.f; }
+            const int cnt = in ? X.gn[t][g0 + g] : 0;
+            const int cmax = __reduce_max_sync(0xffffffffu, cnt);
+            const uint16_t *__restrict__ rl = X.gr[t] + base;
+            const float2 *__restrict__ vl = X.gv[t] + base;
+            for (int q0 = 0; q0 < cmax; q0 += kListBatch) {
+                float2 a[kListBatch];
+                int r[kListBatch];
+#pragma unroll
+                for (int j = 0; j < kListBatch; j++) {
+                    // only the lane's own entries are read (cnt = 0 past the bin's points)
+                    const bool ok = q0 + j < cnt;
+                    const int64_t o = (int64_t)(q0 + j) * wc;
+                    a[j] = ok ? __ldg(vl + o) : make_float2(0.f, 0.f);
+                    r[j] = ok ? (int)__ldg(rl + o) : 0;
+                }
+#pragma unroll
+                for (int j = 0; j < kListBatch; j++) {
+                    const float2 *ur = us + r[j] * NR;
+#pragma unroll
+                    for (int k = 0; k < NR; k++) {
+                        const float2 uu = ur[k];
+                        if constexpr (DF) df_fma(a[j].x, a[j].y, uu.x, uu.y, h[k], l[k]);
+                        else h[k] = fmaf(a[j].x, uu.x, h[k]);
+                    }
+                }
+            }
+            if (in) {
+                float2 *y = (t == 0 ? yL : yR) + (int64_t)g * NR;
+#pragma unroll
+                for (int k = 0; k < NR; k++) y[k] = make_float2(h[k], l[k]);
+            }
+        }
+    }
+    __syncthreads();
+    // ---- phase 2: per template row, its two lists against yR, yL ----
+    for (int it = tid; it < D * VS; it += kListThreads) {
+        const int c = it / VS, vg = it - c * VS, v0 = vg * NV;
+        const int64_t base = t0 + (int64_t)c * ld;
+        float zh[NV], zl[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) { zh[k] = 0.f; zl[k] = 0.f; }
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            const float2 *y = t == 0 ? yR : yL;   // L pairs with R~ u, R~ with L u
+            const int cnt = X.rn[t][d0 + c];
+            const uint16_t *__restrict__ gl = X.rg[t] + base;
+            const float2 *__restrict__ vl = X.rv[t] + base;
+            for (int q0 = 0; q0 < cnt; q0 += kListBatch) {
+                float2 a[kListBatch];
+                int gi[kListBatch];
+#pragma unroll
+                for (int j = 0; j < kListBatch; j++) {
+                    const bool ok = q0 + j < cnt;
+                    a[j] = ok ? __ldg(vl + q0 + j) : make_float2(0.f, 0.f);
+                    gi[j] = (int)__ldg(gl + (ok ? q0 + j : 0));
+                }
+#pragma unroll
+                for (int j = 0; j < kListBatch; j++) {
+                    const float2 *yr = y + gi[j] * NR + v0;
+#pragma unroll
+                    for (int k = 0; k < NV; k++) {
+                        if (v0 + k >= NR) break;
+                        const float2 yy = yr[k];
+                        if constexpr (DF) df_fma(a[j].x, a[j].y, yy.x, yy.y, zh[k], zl[k]);
+                        else zh[k] = fmaf(a[j].x, yy.x, zh[k]);
+                    }
+                }
+            }
+        }
+        const int64_t dof = X.dof_idx[d0 + c];
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            const int v = v0 + k;
+            if (v >= NR || v >= nv) break;
+            if constexpr (DF) {
+                float ph, pl;
+                df_mul(zh[k], zl[k], X.sKh, X.sKl, ph, pl);
+                atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(ph));
+                atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(pl));
+            } else {
+                atomicAdd(&Au[(int64_t)v * ldA + dof], (double)(zh[k] * X.sKh));
+            }
+        }
+    }
+}
+
 // Au = A u for nv vectors (column-major, leading dimension n_dof), applied from
 // the tables; vectors go through the tables in groups: up to 17 per pass while at least 13
 // are left, then up to eight, and a last group of one or up to four vectors takes the
@@ -1563,24 +1730,78 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d, bool df) {
         attr = true;
     }
     FEM3_TRY(ap_prepare(m));
-    double *ui = nullptr;
-    if (nv > 1)
-        FEM3_CUDA(cudaMallocAsync((void **)&ui, sizeof(double) * 17 * std::max<int64_t>(1, n), s));
     ApplyAxes P;
+    ListAxes PL;
     int64_t nblk = 0;
+    int max_gp = 0, max_dof = 0;
     for (int axis = 0; axis < 3; axis++) {
         AxisBins &B = m->bins[axis];
         const bool on = B.n_tmpl > 0 && B.n_bins > 0;
         const float skh = (float)m->sK[axis], skl = (float)(m->sK[axis] - (double)skh);
         P.a[axis] = ApplyAxis{m->tabL[axis], B.ap_R, B.ap_rng, B.gp_off, B.dof_off, B.dof_idx,
                               B.tab_ld, B.tab_off, skh, skl, on ? B.n_bins : 0};
+        PL.a[axis] = ListAxis{{B.rl_g[0], B.rl_g[1]}, {B.rl_v[0], B.rl_v[1]},
+                              {B.rl_n[0], B.rl_n[1]}, {B.gl_r[0], B.gl_r[1]},
+                              {B.gl_v[0], B.gl_v[1]}, {B.gl_n[0], B.gl_n[1]},
+                              B.gp_off, B.dof_off, B.dof_idx, B.tab_ld, B.tab_off, skh, skl,
+                              on ? B.n_bins : 0};
         nblk += on ? B.n_bins : 0;
+        if (on) {
+            max_gp = std::max(max_gp, B.max_gp);
+            max_dof = std::max(max_dof, B.max_dof);
+        }
     }
+    // the lists' kernel when the largest bin's Gauss points and their 17 sums fit
+    const bool lists = apply_lists_fit(m);
+    if (lists) {
+        static bool lattr = false;
+        if (!lattr) {
+#define FEM3_LATTR(NR_, VS_)                                                                     \
+    FEM3_CUDA(cudaFuncSetAttribute(k_apply_lists<NR_, VS_, true>,                                \
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kListSmemMax)); \
+    FEM3_CUDA(cudaFuncSetAttribute(k_apply_lists<NR_, VS_, false>,                               \
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kListSmemMax))
+            FEM3_LATTR(17, 3);
+            FEM3_LATTR(8, 2);
+            FEM3_LATTR(4, 2);
+            FEM3_LATTR(1, 1);
+#undef FEM3_LATTR
+            lattr = true;
+        }
+    }
+    double *ui = nullptr;
+    if (nv > 1 || lists)
+        FEM3_CUDA(cudaMallocAsync((void **)&ui, sizeof(double) * 17 * std::max<int64_t>(1, n), s));
+    float2 *uf = reinterpret_cast<float2 *>(ui);
     for (int v0 = 0, cnt = 0; v0 < nv && nblk > 0; v0 += cnt) {
         const int left = nv - v0;
         const int nri = left >= 13 ? 17 : (left >= 5 ? 8 : (left >= 2 ? 4 : 1));
         cnt = std::min(nri, left);
         double *out = Au_d + (int64_t)v0 * n;
+        if (lists) {
+            const double *us = u_d + (int64_t)v0 * n;
+            const size_t sh = apply_lists_smem(nri, max_dof, max_gp);
+#define FEM3_LISTS(NR_, VS_)                                                                     \
+    do {                                                                                         \
+        k_split_vec<NR_><<<g256((int64_t)NR_ * n), 256, 0, s>>>(us, n, cnt, uf);                 \
+        note_launch(m);                                                                          \
+        kc_begin(m, KC_APPLY);                                                                   \
+        if (df)                                                                                  \
+            k_apply_lists<NR_, VS_, true><<<(unsigned)nblk, kListThreads, sh, s>>>(PL, uf, cnt,  \
+                                                                                 out, n, max_dof); \
+        else                                                                                     \
+            k_apply_lists<NR_, VS_, false><<<(unsigned)nblk, kListThreads, sh, s>>>(PL, uf, cnt, \
+                                                                                  out, n, max_dof); \
+        kc_end(m, KC_APPLY);                                                                     \
+        note_launch(m);                                                                          \
+    } while (0)
+            if (nri == 17) FEM3_LISTS(17, 3);
+            else if (nri == 8) FEM3_LISTS(8, 2);
+            else if (nri == 4) FEM3_LISTS(4, 2);
+            else FEM3_LISTS(1, 1);
+#undef FEM3_LISTS
+            continue;
+        }
         if (nri == 4)
             k_interleave<4><<<g256(4 * n), 256, 0, s>>>(u_d + (int64_t)v0 * n, n, cnt, ui);
         else if (nri == 8)

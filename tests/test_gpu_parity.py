@@ -254,6 +254,25 @@ def test_many_right_hand_sides(precision, nrhs):
     m.free()
 
 
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_dense_apply_for_wide_bins(precision):
+    """Bins too wide for the list apply's shared memory (17 x 8 B x (D + 2 G) above 112 KB)
+    take the dense-block apply: the refined solution still matches the oracle, 17 columns."""
+    mesh, o, alpha, K = _case("cube7_jitter")
+    m = fem3.Mesh(mesh.verts, mesh.tets, bin_scale=3.0)
+    st = [m.bin_stats(a) for a in range(3)]
+    md, mg = max(x["max_dof"] for x in st), max(x["max_gp"] for x in st)
+    assert 17 * 8 * (md + 2 * mg) > 112 * 1024, (md, mg)
+    m.assemble(alpha, K, precision)
+    f = np.random.default_rng(17).standard_normal((mesh.n_nodes, 17))
+    u = m.solve(f, tol=1e-13).cpu().numpy()
+    u_ref = oracle.solve(o.assemble(alpha, K), o.load(f))
+    err = np.linalg.norm(u - u_ref, axis=0) / np.linalg.norm(u_ref, axis=0)
+    assert err.max() <= 1e-8, err
+    assert m.resid <= 1e-13
+    m.free()
+
+
 def test_load_vector():
     mesh, o, alpha, K = _case("cube3_jitter")
     m = fem3.Mesh(mesh.verts, mesh.tets)
