@@ -68,10 +68,10 @@ def _peaks():
 # of work of that capture; the bench scales them to its own launch by the units processed
 # and reports null when the source has changed since the capture.
 TRAFFIC = {
-    # ncu capture of one launch on the 16^3 jittered cube (16,099,980 segments)
+    # ncu capture of one launch on the 16^3 parallelepiped (16,301,215 segments)
     "k_walk_tables": {"source": "walk.cu",
-                      "sha256": "4e2c8962c5f01a637b7099c0894a65296071a091c7cc0344e7934c3e88eb9bed",
-                      "bytes": 164346112 + 583106304, "units": 16099980},
+                      "sha256": "f5c92935fc52fb0c9b1330c1e5b8263bad3af43b89dae583d9a101bc5830f08f",
+                      "bytes": 189565952 + 598637568, "units": 16301215},
 }
 
 
@@ -117,7 +117,7 @@ def whole_job_rate(world: int, units_per_rank_step: float, steps: int, total_ms:
 
 
 def kernel_rooflines(kms: dict, cnt: dict, n_dof: int, precision: str, peaks: dict,
-                     workload: str) -> dict:
+                     workload: str, tc_factor=None) -> dict:
     """Roofline of every timed kernel class of one profiled step: achieved = algorithmic
     work of the class's launches / their summed CUDA-event time on the launch stream.
 
@@ -181,7 +181,9 @@ def kernel_rooflines(kms: dict, cnt: dict, n_dof: int, precision: str, peaks: di
     f = kms.get("factor", (0, 0))
     if f[0] > 0:
         fl = n_dof ** 3 / 3.0
-        if precision != "fp64" and n_dof >= CHOL_TC_MIN_N:
+        if tc_factor is None:
+            tc_factor = n_dof >= CHOL_TC_MIN_N
+        if precision != "fp64" and tc_factor:
             # blocked factorisation: the trailing updates (nearly all of n^3/3) run as three
             # TF32 split products on the tensor cores; the time is the factorisation's wall
             # time on the launch stream (diagonal chain and side-stream update together)
@@ -409,7 +411,8 @@ def measure_workload(args, torch, fem3, inputs, workload, precision, steps, warm
     stream = torch.cuda.current_stream()
 
     def step(prec, profile=False, keep=False):
-        m = fem3.Mesh(verts_d, tets_d, bin_scale=args.bin_scale, profile=profile)
+        m = fem3.Mesh(verts_d, tets_d, bin_scale=args.bin_scale, profile=profile,
+                      chol_tc=args.chol_tc)
         m.assemble(alpha, K, prec)
         u = m.solve(F_d, tol=args.tol)
         if keep:
@@ -472,7 +475,9 @@ def measure_workload(args, torch, fem3, inputs, workload, precision, steps, warm
         cnt["apply_vectors"], cnt["apply_passes"] = vecs, passes
     n_dof = m.n_dof
     m.free()
-    out["rooflines"] = kernel_rooflines(kms, cnt, n_dof, precision, _peaks()[0], workload)
+    tc_factor = args.chol_tc == 1 or (args.chol_tc == 0 and n_dof >= CHOL_TC_MIN_N)
+    out["rooflines"] = kernel_rooflines(kms, cnt, n_dof, precision, _peaks()[0], workload,
+                                        tc_factor)
     if out["rooflines"]:
         dom = max(out["rooflines"], key=lambda k: kms[k][0])
         out["dominant_kernel"] = dom
@@ -501,7 +506,8 @@ def measure_workload(args, torch, fem3, inputs, workload, precision, steps, warm
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            mh = fem3.Mesh(verts_h.numpy(), tets_h.numpy(), bin_scale=args.bin_scale)
+            mh = fem3.Mesh(verts_h.numpy(), tets_h.numpy(), bin_scale=args.bin_scale,
+                           chol_tc=args.chol_tc)
             mh.assemble(alpha, K, precision)
             u = mh.solve(F_h.numpy(), tol=args.tol)
             u_host = u.cpu()
@@ -661,6 +667,9 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10,
                     help="relative residual at which refinement stops (the mixed form targets "
                          "1e-8 relative solution error; the FP64 form is direct)")
+    ap.add_argument("--chol-tc", type=int, default=0, choices=[-1, 0, 1],
+                    help="FP32 factorisation: 1 the blocked tensor-core one, -1 the tile-task "
+                         "one, 0 by size (tensor cores from 4,096 dofs)")
     ap.add_argument("--bin-scale", type=float, default=0.5,
                     help="transverse bin width in mean cell sizes (template granularity)")
     args = ap.parse_args()
