@@ -72,7 +72,19 @@ TRAFFIC = {
     "k_walk_tables": {"source": "walk.cu",
                       "sha256": "f5c92935fc52fb0c9b1330c1e5b8263bad3af43b89dae583d9a101bc5830f08f",
                       "bytes": 189565952 + 598637568, "units": 16301215},
+    # ncu capture of one 17-vector double-float launch on the 16^3 parallelepiped (units:
+    # 14,392,119 nonzeros of the tables, read once per launch from their two list layouts)
+    "k_apply_lists": {"source": "solve.cu",
+                      "sha256": "910862fcb819f0a3c91d9c144a0ee41bc54ae03679b1160273d7f83f5f2dd089",
+                      "bytes": 433922304 + 3908864, "units": 14392119},
 }
+
+# the operator apply runs from the nonzero lists when a bin's rows and its Gauss points' sums
+# of 17 vectors fit 112 KB of shared memory (8 B x 17 x (max_dof + 2 max_gp)), as in the library
+def apply_uses_lists(bins):
+    md = max(b["max_dof"] for b in bins)
+    mg = max(b["max_gp"] for b in bins)
+    return 8 * 17 * (md + 2 * mg) <= 112 * 1024
 
 
 def _source_sha(name):
@@ -226,9 +238,12 @@ def kernel_rooflines(kms: dict, cnt: dict, n_dof: int, precision: str, peaks: di
                    f"per table element and vector, {elems:.0f} elements, "
                    f"{cnt['apply_vectors']} vector-applies")
         ach = ops / (a[0] * 1e-3) / 1e12
-        out["apply"] = {"kernel": "k_apply_bin", "bound": "alu", "unit": "T FP32 instr/s",
+        lists = bool(nnz) and cnt.get("apply_lists", True)
+        out["apply"] = {"kernel": "k_apply_lists" if lists else "k_apply_bin", "bound": "alu",
+                        "unit": "T FP32 instr/s",
                         "achieved": ach, "peak": FP32_ISSUE_TOPS, "frac": ach / FP32_ISSUE_TOPS,
-                        "launches": a[1], "launch_ms": a[0] / a[1], "traffic": None,
+                        "launches": a[1], "launch_ms": a[0] / a[1],
+                        "traffic": measured_traffic("k_apply_lists", nnz) if lists else None,
                         "algorithmic": alg,
                         "bytes_gbs": 16 * elems * cnt["apply_passes"] / (a[0] * 1e-3) / 1e9}
         if nnz:
@@ -459,6 +474,7 @@ def measure_workload(args, torch, fem3, inputs, workload, precision, steps, warm
     cnt = m.counters()
     cnt["algorithmic_flops"] = m.contract_work()
     cnt["table_nnz"] = m.table_nnz()
+    cnt["apply_lists"] = apply_uses_lists([m.bin_stats(a) for a in range(3)])
     out.update(dofs=int(m.n_dof), stages_ms=_stage_dict(m.stage_ms()),
                kernel_ms={k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in kms.items()},
                segments_per_step=cnt["segments"], table_bytes=cnt["table_bytes"],
