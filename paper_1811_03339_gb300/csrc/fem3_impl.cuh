@@ -311,11 +311,13 @@ int residual_norm(Mesh *m, const double *b, const double *Au, double *rel);
 int ap_alloc(Mesh *m, int axis);   // operator-apply operand buffers of one axis
 int ap_prepare(Mesh *m);           // split the current tables into the apply operands
 // The operator apply runs from the lists of the tables' nonzeros when a bin's u rows and its
-// Gauss points' sums of 17 vectors fit the list kernel's shared memory; otherwise from the
-// dense table blocks (with the W R operand in the table layout)
-constexpr size_t kListSmemMax = 112 * 1024;   // two CTAs per SM
+// Gauss points' sums of 17 vectors fit the list kernel's shared memory and its rows its
+// threads' items (kListItems per thread, two vector groups); otherwise from the dense table
+// blocks (with the W R operand in the table layout)
+constexpr size_t kListSmemMax = 112 * 1024;   // two CTAs per SM at least
+constexpr int kListItems = 2;                  // phase-2 items (row, vector group) per thread
 inline size_t apply_lists_smem(int nr, int max_dof, int max_gp) {
-    return 8 * (size_t)nr * ((size_t)max_dof + 2 * (size_t)max_gp);
+    return 8 * (size_t)nr * ((size_t)max_dof + (size_t)max_gp);
 }
 inline bool apply_lists_fit(const Mesh *m) {
     int md = 0, mg = 0;
@@ -323,7 +325,7 @@ inline bool apply_lists_fit(const Mesh *m) {
         md = std::max(md, m->bins[a].max_dof);
         mg = std::max(mg, m->bins[a].max_gp);
     }
-    return apply_lists_smem(17, md, mg) <= kListSmemMax;
+    return apply_lists_smem(17, md, mg) <= kListSmemMax && 2 * md <= 256 * kListItems;
 }
 RowLists row_lists(AxisBins &B);   // the axis's row-major list arrays
 void launch_gp_lists(Mesh *m, int axis);   // Gauss-point-major lists of L and W R

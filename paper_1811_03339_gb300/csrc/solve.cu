@@ -1574,11 +1574,12 @@ constexpr int kListThreads = 256;
 constexpr int kListBatch = 2;   // list entries whose loads are in flight together
 
 template <int NR, int VS, bool DF>
-__global__ void __launch_bounds__(kListThreads) k_apply_lists(const __grid_constant__ ListAxes P,
+__global__ void __launch_bounds__(kListThreads, 3) k_apply_lists(const __grid_constant__ ListAxes P,
                                                               const float2 *__restrict__ uf,
                                                               int nv, double *Au, int64_t ldA,
                                                               int max_dof) {
-    constexpr int NV = (NR + VS - 1) / VS;   // phase-2 vectors per thread (the last group short)
+    constexpr int NV = (NR + VS - 1) / VS;   // phase-2 vectors per item (the last group short)
+    constexpr int NH = (NR + 1) / 2;         // phase-1 vectors per warp item (two halves)
     int b = blockIdx.x, axis = 0;
     while (axis < 2 && b >= P.a[axis].n_bins) b -= P.a[axis++].n_bins;
     const ListAxis &X = P.a[axis];
@@ -1589,30 +1590,39 @@ __global__ void __launch_bounds__(kListThreads) k_apply_lists(const __grid_const
     const int64_t t0 = X.tab_off[b];
     extern __shared__ __align__(16) float2 sm_lists[];
     float2 *us = sm_lists;                         // [max_dof][NR]
-    float2 *yL = us + (int64_t)max_dof * NR;       // [G][NR]
-    float2 *yR = yL + (int64_t)G * NR;
+    float2 *y = us + (int64_t)max_dof * NR;        // [G][NR]: R~ u, then L u
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // phase-2 items (row, vector group) of this thread, fixed for both rounds
+    float zh[kListItems][NV], zl[kListItems][NV];
+#pragma unroll
+    for (int i = 0; i < kListItems; i++)
+#pragma unroll
+        for (int k = 0; k < NV; k++) { zh[i][k] = 0.f; zl[i][k] = 0.f; }
     // ---- phase 0 ----
     for (int e = tid; e < D * NR; e += kListThreads) {
         const int c = e / NR, v = e - c * NR;
         us[e] = __ldg(uf + (int64_t)__ldg(X.dof_idx + d0 + c) * NR + v);
     }
-    __syncthreads();
-    // ---- phase 1: warp = (chunk of 32 Gauss points, table), lane = point ----
-    const int nchunk = (G + 31) >> 5;
-    for (int wi = warp; wi < 2 * nchunk; wi += kListThreads / 32) {
-        const int gc = 32 * (wi >> 1), t = wi & 1;
-        const int g = gc + lane, wc = min(32, G - gc);
-        const bool in = g < G;
-        const int64_t base = t0 + (int64_t)gc * D + lane;
-        {
-            float h[NR], l[NR];
+    // Round 0: y = R~ u from the points' W R lists, then the rows' L lists against it;
+    // round 1: y = L u from the points' L lists, then the rows' W R lists.
 #pragma unroll
-            for (int k = 0; k < NR; k++) { h[k] = 0.f; l[k] = 0.f; }
-            const int cnt = in ? X.gn[t][g0 + g] : 0;
+    for (int round = 0; round < 2; round++) {
+        const int tg = 1 - round, tr = round;   // point-list table, row-list table
+        __syncthreads();   // u staged / the rows are done with the previous round's y
+        // ---- phase 1: warp = (chunk of 32 Gauss points, half of the vectors), lane = point
+        const int nchunk = (G + 31) >> 5;
+        for (int wi = warp; wi < 2 * nchunk; wi += kListThreads / 32) {
+            const int gc = 32 * (wi >> 1), v0 = NH * (wi & 1);
+            const int g = gc + lane, wc = min(32, G - gc);
+            const bool in = g < G;
+            const int64_t base = t0 + (int64_t)gc * D + lane;
+            float h[NH], l[NH];
+#pragma unroll
+            for (int k = 0; k < NH; k++) { h[k] = 0.f; l[k] = 0.f; }
+            const int cnt = in ? X.gn[tg][g0 + g] : 0;
             const int cmax = __reduce_max_sync(0xffffffffu, cnt);
-            const uint16_t *__restrict__ rl = X.gr[t] + base;
-            const float2 *__restrict__ vl = X.gv[t] + base;
+            const uint16_t *__restrict__ rl = X.gr[tg] + base;
+            const float2 *__restrict__ vl = X.gv[tg] + base;
             for (int q0 = 0; q0 < cmax; q0 += kListBatch) {
                 float2 a[kListBatch];
                 int r[kListBatch];
@@ -1626,9 +1636,10 @@ __global__ void __launch_bounds__(kListThreads) k_apply_lists(const __grid_const
                 }
 #pragma unroll
                 for (int j = 0; j < kListBatch; j++) {
-                    const float2 *ur = us + r[j] * NR;
+                    const float2 *ur = us + r[j] * NR + v0;
 #pragma unroll
-                    for (int k = 0; k < NR; k++) {
+                    for (int k = 0; k < NH; k++) {
+                        if (v0 + k >= NR) break;
                         const float2 uu = ur[k];
                         if constexpr (DF) df_fma(a[j].x, a[j].y, uu.x, uu.y, h[k], l[k]);
                         else h[k] = fmaf(a[j].x, uu.x, h[k]);
@@ -1636,26 +1647,23 @@ __global__ void __launch_bounds__(kListThreads) k_apply_lists(const __grid_const
                 }
             }
             if (in) {
-                float2 *y = (t == 0 ? yL : yR) + (int64_t)g * NR;
+                float2 *yg = y + (int64_t)g * NR + v0;
 #pragma unroll
-                for (int k = 0; k < NR; k++) y[k] = make_float2(h[k], l[k]);
+                for (int k = 0; k < NH; k++)
+                    if (v0 + k < NR) yg[k] = make_float2(h[k], l[k]);
             }
         }
-    }
-    __syncthreads();
-    // ---- phase 2: per template row, its two lists against yR, yL ----
-    for (int it = tid; it < D * VS; it += kListThreads) {
-        const int c = it / VS, vg = it - c * VS, v0 = vg * NV;
-        const int64_t base = t0 + (int64_t)c * ld;
-        float zh[NV], zl[NV];
+        __syncthreads();
+        // ---- phase 2: the thread's rows, their table-tr lists against y ----
 #pragma unroll
-        for (int k = 0; k < NV; k++) { zh[k] = 0.f; zl[k] = 0.f; }
-#pragma unroll
-        for (int t = 0; t < 2; t++) {
-            const float2 *y = t == 0 ? yR : yL;   // L pairs with R~ u, R~ with L u
-            const int cnt = X.rn[t][d0 + c];
-            const uint16_t *__restrict__ gl = X.rg[t] + base;
-            const float2 *__restrict__ vl = X.rv[t] + base;
+        for (int i = 0; i < kListItems; i++) {
+            const int it = tid + i * kListThreads;
+            if (it >= D * VS) break;
+            const int c = it / VS, v0 = (it - c * VS) * NV;
+            const int64_t base = t0 + (int64_t)c * ld;
+            const int cnt = X.rn[tr][d0 + c];
+            const uint16_t *__restrict__ gl = X.rg[tr] + base;
+            const float2 *__restrict__ vl = X.rv[tr] + base;
             for (int q0 = 0; q0 < cnt; q0 += kListBatch) {
                 float2 a[kListBatch];
                 int gi[kListBatch];
@@ -1672,12 +1680,19 @@ __global__ void __launch_bounds__(kListThreads) k_apply_lists(const __grid_const
                     for (int k = 0; k < NV; k++) {
                         if (v0 + k >= NR) break;
                         const float2 yy = yr[k];
-                        if constexpr (DF) df_fma(a[j].x, a[j].y, yy.x, yy.y, zh[k], zl[k]);
-                        else zh[k] = fmaf(a[j].x, yy.x, zh[k]);
+                        if constexpr (DF) df_fma(a[j].x, a[j].y, yy.x, yy.y, zh[i][k], zl[i][k]);
+                        else zh[i][k] = fmaf(a[j].x, yy.x, zh[i][k]);
                     }
                 }
             }
         }
+    }
+    // ---- the thread's rows into Au ----
+#pragma unroll
+    for (int i = 0; i < kListItems; i++) {
+        const int it = tid + i * kListThreads;
+        if (it >= D * VS) break;
+        const int c = it / VS, v0 = (it - c * VS) * NV;
         const int64_t dof = X.dof_idx[d0 + c];
 #pragma unroll
         for (int k = 0; k < NV; k++) {
@@ -1685,11 +1700,11 @@ __global__ void __launch_bounds__(kListThreads) k_apply_lists(const __grid_const
             if (v >= NR || v >= nv) break;
             if constexpr (DF) {
                 float ph, pl;
-                df_mul(zh[k], zl[k], X.sKh, X.sKl, ph, pl);
+                df_mul(zh[i][k], zl[i][k], X.sKh, X.sKl, ph, pl);
                 atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(ph));
                 atomicAdd(&Au[(int64_t)v * ldA + dof], f32_to_f64_exact(pl));
             } else {
-                atomicAdd(&Au[(int64_t)v * ldA + dof], (double)(zh[k] * X.sKh));
+                atomicAdd(&Au[(int64_t)v * ldA + dof], (double)(zh[i][k] * X.sKh));
             }
         }
     }
@@ -1761,7 +1776,7 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d, bool df) {
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kListSmemMax)); \
     FEM3_CUDA(cudaFuncSetAttribute(k_apply_lists<NR_, VS_, false>,                               \
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kListSmemMax))
-            FEM3_LATTR(17, 3);
+            FEM3_LATTR(17, 2);
             FEM3_LATTR(8, 2);
             FEM3_LATTR(4, 2);
             FEM3_LATTR(1, 1);
@@ -1795,7 +1810,7 @@ int apply_multi(Mesh *m, const double *u_d, int nv, double *Au_d, bool df) {
         kc_end(m, KC_APPLY);                                                                     \
         note_launch(m);                                                                          \
     } while (0)
-            if (nri == 17) FEM3_LISTS(17, 3);
+            if (nri == 17) FEM3_LISTS(17, 2);
             else if (nri == 8) FEM3_LISTS(8, 2);
             else if (nri == 4) FEM3_LISTS(4, 2);
             else FEM3_LISTS(1, 1);
