@@ -876,6 +876,7 @@ int solve_chain_t(const TF *L, int64_t n, TF *Y, int nrhs, cudaStream_t s, Mesh 
     else if (nrhs <= 4) FEM3_TRY((launch_solve_chain<TF, 4>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
     else if (nrhs <= 8) FEM3_TRY((launch_solve_chain<TF, 8>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
     else if (nrhs <= 16) FEM3_TRY((launch_solve_chain<TF, 16>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
+    else if (nrhs <= 20) FEM3_TRY((launch_solve_chain<TF, 20>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
     else FEM3_TRY((launch_solve_chain<TF, 24>(L, Dinv, n, nblk, Y, nrhs, Gop, Z, workers, s, m)));
     FEM3_CUDA(cudaGetLastError());
     return FEM3_OK;
