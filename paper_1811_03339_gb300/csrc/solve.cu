@@ -1555,6 +1555,27 @@ __global__ void k_split_vec(const double *__restrict__ u, int64_t n, int nv, flo
     uf[e] = make_float2(h, l);
 }
 
+// loads that do not happen when `pred` is false (a predicated PTX load: no access is made, the
+// address need not be valid, and the result keeps its zero)
+__device__ __forceinline__ float2 ldg_if(const float2 *p, bool pred) {
+    float x = 0.f, y = 0.f;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+        "@q ld.global.nc.v2.f32 {%0, %1}, [%3];\n\t}"
+        : "+f"(x), "+f"(y)
+        : "r"((int)pred), "l"(p));
+    return make_float2(x, y);
+}
+__device__ __forceinline__ int ldg_if(const uint16_t *p, bool pred) {
+    uint32_t v = 0;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t"
+        "@q ld.global.nc.u16 %0, [%2];\n\t}"
+        : "+r"(v)
+        : "r"((int)pred), "l"(p));
+    return (int)v;
+}
+
 struct ListAxis {
     const uint16_t *rg[2];          // row-major lists: Gauss-point index, value (t = 0 L, 1 W R)
     const float2 *rv[2];
@@ -1632,8 +1653,8 @@ __global__ void __launch_bounds__(kListThreads, 3) k_apply_lists(const __grid_co
                     // only the lane's own entries are read (cnt = 0 past the bin's points)
                     const bool ok = q0 + j < cnt;
                     const int64_t o = (int64_t)(q0 + j) * wc;
-                    a[j] = ok ? __ldg(vl + o) : make_float2(0.f, 0.f);
-                    r[j] = ok ? (int)__ldg(rl + o) : 0;
+                    a[j] = ldg_if(vl + o, ok);
+                    r[j] = ldg_if(rl + o, ok);
                 }
 #pragma unroll
                 for (int j = 0; j < kListBatch; j++) {
@@ -1670,9 +1691,10 @@ __global__ void __launch_bounds__(kListThreads, 3) k_apply_lists(const __grid_co
                 int gi[kListBatch];
 #pragma unroll
                 for (int j = 0; j < kListBatch; j++) {
+                    // the row's own entries only
                     const bool ok = q0 + j < cnt;
-                    a[j] = ok ? __ldg(vl + q0 + j) : make_float2(0.f, 0.f);
-                    gi[j] = (int)__ldg(gl + (ok ? q0 + j : 0));
+                    a[j] = ldg_if(vl + q0 + j, ok);
+                    gi[j] = ldg_if(gl + q0 + j, ok);
                 }
 #pragma unroll
                 for (int j = 0; j < kListBatch; j++) {
