@@ -498,7 +498,9 @@ int chol_tiles_t(TF *A, int64_t n, cudaStream_t s, Mesh *m) {
 constexpr int kSolveThreads = 512;            // thread (r, g): row r = t & 63, column chunk g = t >> 6
 
 template <class TF> struct SolveCfg {
-    static constexpr int D = sizeof(TF) == 4 ? 3 : 2;   // dependency tiles the chain applies itself
+    // dependency tiles the chain applies itself: one more lengthens every chain step, one
+    // fewer puts the workers' hand-over on the critical path (2 timed fastest, both types)
+    static constexpr int D = 2;
 };
 
 // shared memory: ring of D + 1 solved blocks [64][NR] (chain) or one dependency block and
