@@ -17,7 +17,7 @@
 //   3. k_cholp_trail (persistent): A[I, J] -= W_I W_J^T over the 128 x 128 tiles I >= J of
 //      the trailing matrix - TMA loads (128-byte swizzle) into a two-stage ring, three MMAs
 //      per 32-column K step (hi hi, hi lo, lo hi) into one of two TMEM accumulators, and an
-//      epilogue (eight warps) that overlaps the next tile's MMAs.
+//      epilogue (sixteen warps) that overlaps the next tile's MMAs.
 // Look-ahead: the next panel's block column is updated on the caller's stream and the rest of
 // the trailing matrix on a side stream, so the next diagonal block and panel overlap it.
 // No kernel waits for another CTA; the mbarrier waits are bounded (ERR_CHOL on expiry).
@@ -48,8 +48,8 @@ constexpr int kStages = 2;
 constexpr int kCsLd = 129;                     // row stride of the staged C tile (floats)
 constexpr uint32_t kCsBytes = 128 * kCsLd * 4;  // 66 KB
 constexpr uint32_t kTrailSmem = kStages * kStage + kCsBytes + 1024 + 256;
-constexpr int kTrailThreads = 320;              // TMA warp, MMA warp, eight epilogue warps
-constexpr int kEpiThreads = 256;
+constexpr int kTrailThreads = 576;              // TMA warp, MMA warp, sixteen epilogue warps
+constexpr int kEpiThreads = 512;
 constexpr int kReservedSms = 20;                // left to the critical chain by the bulk update
 
 // ------------------------------- diagonal block ----------------------------------
@@ -252,13 +252,13 @@ __device__ __forceinline__ void tile_of(int x, int mode, int &I, int &J) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-// named barrier of the eight epilogue warps (id 1; 0 is __syncthreads)
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// named barrier of the sixteen epilogue warps (id 1; 0 is __syncthreads)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 
 // Persistent trailing update: CTA c takes tiles c, c + gridDim.x, ...  Warp 0 streams the
 // operands of its tiles through the two-stage TMA ring, warp 1 issues the MMAs of tile i
-// into TMEM accumulator i % 2 (256 columns: two 128 x 128 FP32 accumulators), warps 2-9
-// (two per TMEM lane quadrant, each half of the columns) run the epilogue of tile i while the
+// into TMEM accumulator i % 2 (256 columns: two 128 x 128 FP32 accumulators), warps 2-17
+// (four per TMEM lane quadrant, each a quarter of the columns) run the epilogue of tile i while the
 // MMAs of tile i + 1 proceed: fetch C(i) by 4-byte cp.async, wait for the accumulator,
 // C -= X in shared memory, free the accumulator, write C back.  The fetch and the write-back
 // go row by row (a warp per row, its lanes along the row: one row pointer per row, each
@@ -355,16 +355,16 @@ __global__ void __launch_bounds__(kTrailThreads, 1) k_cholp_trail(
             umma_commit(accf0 + 8 * b);
         }
     } else if (warp >= 2) {
-        const int ew = warp - 2;                     // epilogue warp 0 .. 7
+        const int ew = warp - 2;                     // epilogue warp 0 .. 15
         const int quad = warp & 3;                   // TMEM lane quadrant of this warp
-        const int half = ew >> 2;                    // columns [64 half, 64 half + 64)
+        const int qcol = ew >> 2;                    // columns [32 qcol, 32 qcol + 32)
         const int row = quad * 32 + lane;            // tile row = TMEM lane
         for (int i = 0; i < ntl; i++) {
             int I, J;
             tile_of((int)blockIdx.x + i * (int)gridDim.x, mode, I, J);
             const int64_t gr0 = t0 + 128 * (int64_t)I, gc0 = t0 + 128 * (int64_t)J;
             // C(i): every row in flight at once (a row of A starts on any 4-byte boundary)
-            for (int r = ew; r < 128; r += 8) {
+            for (int r = ew; r < 128; r += 16) {
                 const int64_t gr = gr0 + r;
                 if (gr >= n) break;
                 const int64_t cend = (I == J ? gr + 1 : n) - gc0;   // valid columns [0, cend)
@@ -388,8 +388,8 @@ __global__ void __launch_bounds__(kTrailThreads, 1) k_cholp_trail(
             if (s_efail) break;   // the same value for all epilogue threads (see s_efail)
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-            for (int cb = 0; cb < 64; cb += 16) {
-                const int c0 = 64 * half + cb;
+            for (int cb = 0; cb < 32; cb += 16) {
+                const int c0 = 32 * qcol + cb;
                 float v[16];
                 tmem_ld16(tmem + (uint32_t)(b * 128) + ((uint32_t)(quad * 32) << 16) + c0, v);
 #pragma unroll
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kTrailThreads, 1) k_cholp_trail(
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(acce0 + 8 * b);   // the accumulator is free for tile i + 2
             epi_sync();
-            for (int r = ew; r < 128; r += 8) {
+            for (int r = ew; r < 128; r += 16) {
                 const int64_t gr = gr0 + r;
                 if (gr >= n) break;
                 const int64_t cend = (I == J ? gr + 1 : n) - gc0;
