@@ -325,6 +325,13 @@ int fem3_bin_stats(fem3_mesh m, int axis, int64_t *n_bins, int64_t *n_tmpl, int3
  * (0).  Any output pointer may be NULL. */
 int fem3_tc_tile(fem3_mesh m, int32_t *tile_n, int32_t *tuned);
 
+/* Which form the refinement's operator apply A u (Section 2.3 tables) takes for this mesh:
+ * *lists = 1 from the nonzero lists of the tables (the bins' template rows and Gauss-point
+ * sums of 17 vectors fit the list kernel's 112 KB of shared memory and its threads' items),
+ * 0 from the dense table blocks of the bins.  Decided by the bins alone, so known once the
+ * mesh is uploaded.  lists: host int32.  Errors: FEM3_E_ARG. */
+int fem3_apply_lists(fem3_mesh m, int32_t *lists);
+
 /*
  * Batches of meshes (not in the paper, which assembles one mesh at a time).
  *

@@ -712,6 +712,13 @@ int fem3_tc_tile(fem3_mesh h, int32_t *tile_n, int32_t *tuned) {
     return FEM3_OK;
 }
 
+int fem3_apply_lists(fem3_mesh h, int32_t *lists) {
+    Mesh *m = reinterpret_cast<Mesh *>(h);
+    if (!m || !lists) return set_error(FEM3_E_ARG, "bad argument");
+    *lists = apply_lists_fit(m) ? 1 : 0;
+    return FEM3_OK;
+}
+
 int fem3_contract_work(fem3_mesh h, double *flops, void *stream) {
     Mesh *m = reinterpret_cast<Mesh *>(h);
     if (!m || !flops) return set_error(FEM3_E_ARG, "bad argument");

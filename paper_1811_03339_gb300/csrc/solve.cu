@@ -1534,14 +1534,16 @@ __global__ void __launch_bounds__(kApplyThreads, NR > 8 ? 2 : 3)
 // The same operator from the lists of the tables' nonzeros (the Gauss-point-major and
 // row-major lists that k_gp_lists and k_split_ops write with the apply operands): the work is
 // the nonzeros, about a fifth of the dense bin blocks (a Gauss point's line crosses the
-// element patches of a few of its bin's template dofs).  One CTA per bin:
+// element patches of a few of its bin's template dofs).  One CTA per bin, one y buffer:
 //   phase 0: u of the bin's template rows into shared memory (hi + lo pairs, [D][NR]);
-//   phase 1, warp = chunk of 32 Gauss points, lane = point: yL[g] = sum over g's L list of
-//     L[r][g] u[r] and yR[g] over its W R list, all NR vectors, into shared memory (the chunk
-//     layout puts the lanes' entries k side by side);
-//   phase 2, thread = (template row r, group of NV vectors): z = sum over r's L list of
-//     L[r][g] yR[g] + over its W R list of (W R)[r][g] yL[g]; Au[dof(r)] += s K z (FP64
-//     atomics of the double-float parts, as in k_apply_bin).
+//   then two rounds, (point table, row table) = (W R, L) and then (L, W R):
+//   phase 1, warp = (chunk of 32 Gauss points, half of the vectors), lane = point: y[g] =
+//     sum over g's list in the point table of T[r][g] u[r], into shared memory ([G][NR]; the
+//     chunk layout puts the lanes' entries k side by side);
+//   phase 2, thread = up to two items (template row r, group of NV vectors): z += sum over
+//     r's list in the row table of T'[r][g] y[g], z kept in registers across the rounds;
+//   at the end Au[dof(r)] += s K z (FP64 atomics of the double-float parts, as in
+//   k_apply_bin).
 // With rows and Gauss points ordered along the axis, a point's L list grows along the bin as
 // its W R list shrinks (and likewise for a row), so the lanes of a warp do similar work.
 // u comes split into hi + lo FP32 pairs, [dof][NR] (k_split_vec).  The bin's rows, Gauss

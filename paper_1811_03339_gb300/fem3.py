@@ -29,7 +29,7 @@ SYMBOLS = ("fem3_mesh_upload", "fem3_mesh_info", "fem3_assemble", "fem3_assemble
            "fem3_adjoint", "fem3_vjp", "fem3_paths", "fem3_table_rows", "fem3_sync", "fem3_stage_ms",
            "fem3_counters", "fem3_bin_stats", "fem3_kernel_ms", "fem3_contract_work",
            "fem3_table_nnz",
-           "fem3_tc_tile",
+           "fem3_tc_tile", "fem3_apply_lists",
            "fem3_last_error",
            "fem3_mesh_free",
            "fem3_spd_solve_static",
@@ -83,6 +83,7 @@ def load_library(build_if_missing: bool = True):
         "fem3_stage_ms": [p, ci, C.POINTER(C.c_float)],
         "fem3_counters": [p, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)],
         "fem3_tc_tile": [p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+        "fem3_apply_lists": [p, C.POINTER(C.c_int32)],
         "fem3_bin_stats": [p, ci, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)],
         "fem3_kernel_ms": [p, ci, C.POINTER(C.c_float), C.POINTER(i32)],
         "fem3_contract_work": [p, C.POINTER(dbl), p],
@@ -271,6 +272,12 @@ def tc_tile(h):
     return t.value, bool(u.value)
 
 
+def apply_lists(h):
+    v = C.c_int32()
+    _check(_lib.fem3_apply_lists(h, C.byref(v)))
+    return bool(v.value)
+
+
 def spd_solve_static(A, b, x, stream=None):
     """Dense SPD solve with no device allocation (n <= 512): A (n, n), b and x (n,), all
     contiguous float64 CUDA tensors on the current device (see include/fem3.h)."""
@@ -438,6 +445,11 @@ class Mesh:
     def tc_tile(self):
         """(tile width of the last tensor-core contraction, whether it ran the tuner)"""
         return tc_tile(self.h)
+
+    def apply_lists(self):
+        """whether the refinement's operator apply runs from the tables' nonzero lists (else
+        from the dense table blocks of the bins)"""
+        return apply_lists(self.h)
 
     def free(self):
         if getattr(self, "h", None):

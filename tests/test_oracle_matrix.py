@@ -210,3 +210,21 @@ def test_gauss_point_subsets_sum_to_the_assembly(oracle_for):
     one = o.assemble_gps(alpha, K, [5])
     assert np.abs(one - one.T).max() <= 1e-15 * np.abs(one).max()
     assert np.linalg.matrix_rank(one, tol=1e-10 * np.abs(one).max()) <= 6
+
+
+def test_gauss_point_slices_on_threads_sum_to_the_assembly(oracle_for):
+    """Slices of the Gauss points assembled at once on four threads, one oracle call per
+    thread into its own matrix (as the bench's all-core CPU leg runs it), add up to the
+    whole assembly: the oracle's calls share no mutable state."""
+    from concurrent.futures import ThreadPoolExecutor
+    mesh, o = oracle_for(4, 0.2, 3, None)
+    alpha, K = (1.3, 1.6, 1.8), (1.0, 2.0, 0.5)
+    A = o.assemble(alpha, K)
+    parts = np.array_split(np.arange(o.n_gp, dtype=np.int64), 4)
+    with ThreadPoolExecutor(4) as ex:
+        mats = list(ex.map(lambda p: o.assemble_gps(alpha, K, p), parts))
+    S = sum(mats)
+    assert np.abs(S - A).max() <= 1e-13 * np.abs(A).max()
+    # each slice alone is what the same call makes on this thread
+    for p, Mp in zip(parts, mats):
+        assert np.array_equal(Mp, o.assemble_gps(alpha, K, p))
