@@ -254,15 +254,28 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 }
 // named barrier of the sixteen epilogue warps (id 1; 0 is __syncthreads)
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+// a global load that is not made when `pred` is false (predicated PTX: no access at all), 0
+// then; the L1-cached path, not the read-only one (the kernel writes A)
+__device__ __forceinline__ float ld_if(const float *p, bool pred) {
+    float x = 0.f;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t@q ld.global.f32 %0, [%2];\n\t}"
+        : "+f"(x)
+        : "r"((int)pred), "l"(p));
+    return x;
+}
 
 // Persistent trailing update: CTA c takes tiles c, c + gridDim.x, ...  Warp 0 streams the
 // operands of its tiles through the two-stage TMA ring, warp 1 issues the MMAs of tile i
 // into TMEM accumulator i % 2 (256 columns: two 128 x 128 FP32 accumulators), warps 2-17
 // (four per TMEM lane quadrant, each a quarter of the columns) run the epilogue of tile i while the
-// MMAs of tile i + 1 proceed: fetch C(i) by 4-byte cp.async, wait for the accumulator,
-// C -= X in shared memory, free the accumulator, write C back.  The fetch and the write-back
-// go row by row (a warp per row, its lanes along the row: one row pointer per row, each
-// instruction 128 consecutive bytes).  Every mbarrier wait is
+// MMAs of tile i + 1 proceed: C(i), fetched into registers during tile i - 1, goes to shared
+// memory, the fetch of C(i + 1) is issued, then wait for the accumulator, C -= X in shared
+// memory, free the accumulator, write C back: each fetch has a whole tile's epilogue to
+// arrive.  The fetch and the write-back go row by row (a warp per row, its lanes along the
+// row: one row pointer per row, each instruction 128 consecutive bytes; A's rows start on
+// any 4-byte boundary).  A CTA reads only its own tiles, each before it writes it.  Every
+// mbarrier wait is
 // bounded; a role that gives up records ERR_CHOL and the others give up on their next wait.
 __global__ void __launch_bounds__(kTrailThreads, 1) k_cholp_trail(
     const __grid_constant__ CUtensorMap mHi, const __grid_constant__ CUtensorMap mLo, float *A,
@@ -359,30 +372,39 @@ __global__ void __launch_bounds__(kTrailThreads, 1) k_cholp_trail(
         const int quad = warp & 3;                   // TMEM lane quadrant of this warp
         const int qcol = ew >> 2;                    // columns [32 qcol, 32 qcol + 32)
         const int row = quad * 32 + lane;            // tile row = TMEM lane
+        // the next tile's C in registers: rows ew + 16 k, columns lane + 32 q (only its valid
+        // elements are read: rows below n, columns below n and, on a diagonal tile, up to the
+        // diagonal)
+        float cn[8][4];
+        auto fetch = [&](int i) {
+            int I, J;
+            tile_of((int)blockIdx.x + i * (int)gridDim.x, mode, I, J);
+            const int64_t gr0 = t0 + 128 * (int64_t)I, gc0 = t0 + 128 * (int64_t)J;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int64_t gr = gr0 + ew + 16 * k;
+                const int64_t cend = gr < n ? (I == J ? gr + 1 : n) - gc0 : 0;
+                const float *src = A + gr * n + gc0;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int c = lane + 32 * q;
+                    cn[k][q] = ld_if(src + c, c < cend && gc0 + c < n);
+                }
+            }
+        };
+        if (ntl > 0) fetch(0);
         for (int i = 0; i < ntl; i++) {
             int I, J;
             tile_of((int)blockIdx.x + i * (int)gridDim.x, mode, I, J);
             const int64_t gr0 = t0 + 128 * (int64_t)I, gc0 = t0 + 128 * (int64_t)J;
-            // C(i): every row in flight at once (a row of A starts on any 4-byte boundary)
-            for (int r = ew; r < 128; r += 16) {
-                const int64_t gr = gr0 + r;
-                if (gr >= n) break;
-                const int64_t cend = (I == J ? gr + 1 : n) - gc0;   // valid columns [0, cend)
-                const float *src = A + gr * n + gc0;
-                const uint32_t dst = smem_u32(Cs + r * kCsLd);
+            // C(i) into shared memory (Cs is free: the previous tile was written back)
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const int c = lane + 32 * q;
-                    if (c < cend && gc0 + c < n)
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + 4 * c),
-                                     "l"(src + c)
-                                     : "memory");
-                }
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
+            for (int k = 0; k < 8; k++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) Cs[(ew + 16 * k) * kCsLd + lane + 32 * q] = cn[k][q];
+            if (i + 1 < ntl) fetch(i + 1);
             const int b = i & 1;
             const bool got = mbar_wait(accf0 + 8 * b, (i >> 1) & 1);
-            asm volatile("cp.async.wait_all;" ::: "memory");
             if (!got) s_efail = 1;
             epi_sync();
             if (s_efail) break;   // the same value for all epilogue threads (see s_efail)
