@@ -126,3 +126,30 @@ def test_measured_traffic_scales_and_expires(monkeypatch):
                         {"source": "walk.cu", "sha256": "0" * 64, "bytes": 1.0e9, "units": 1.0e7})
     assert bench.measured_traffic("k_walk_tables", 2.0e7) is None
     assert bench.measured_traffic("k_other", 1.0) is None
+
+
+def test_cpu_baseline_all_core_leg(monkeypatch):
+    """The all-core leg times the same sample's element sum on threads and keeps every other
+    term of the one-core estimate (mesh build, load, factor, solve), on a 4^3 cube."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1811_03339_gb300 import inputs
+
+    mesh = inputs.cube_mesh(4, 0.2, 3)
+    F = inputs.random_rhs(mesh.n_nodes, 2, 5)
+    r = bench.oracle_sample("cube16_jitter", mesh, F, gp_stride=2, n_chol=64, threads=2)
+    n_gp = 4 * mesh.n_tets
+    scale = n_gp / len(range(0, n_gp, 2))
+    assert r["paths"] == 3 * n_gp
+    assert r["lines_s"] > 0 and r["lines_all_s"] > 0
+    assert (r["est_step_all_s"] - r["lines_all_s"] * scale
+            == pytest.approx(r["est_step_s"] - r["lines_s"] * scale))
+    real = bench.oracle_sample
+    monkeypatch.setattr(bench, "oracle_sample",
+                        lambda w, m, f, gp_stride, n_chol, threads=0: real(w, m, f, 2, 64, threads))
+    monkeypatch.setattr(bench, "_oracle_threads", lambda: 2)
+    out = bench.cpu_baseline("cube16_jitter", mesh, F)
+    assert out["cores"] == 1 and out["kind"] == "oracle" and out["value"] > 0
+    assert out["all_cores"]["cores"] == 2 and out["all_cores"]["value"] > 0
+    monkeypatch.setattr(bench, "_oracle_threads", lambda: 1)
+    assert "all_cores" not in bench.cpu_baseline("cube16_jitter", mesh, F)
