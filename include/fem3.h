@@ -219,8 +219,11 @@ int fem3_load(fem3_mesh m, const double *f, int nrhs, double *b, void *stream);
  * fem3_solve - u = A^{-1} M f for the last assembled A.
  *   FP64: FP64 Cholesky and triangular solves.
  *   TF32X3 / BF16X3 / FP32: FP32 Cholesky of the mixed-precision A, then iterative
- *   refinement with residuals r = M f - A u where A u is applied in FP64 from the FP64
- *   tables, until ||r||_2 <= tol ||M f||_2 for every column or max_iter corrections.
+ *   refinement: d = A32^{-1} r, u += d, r = M f - A u with A u applied from the tables
+ *   in double-float FP32 arithmetic (FP64-accurate), until ||r||_2 <= tol ||M f||_2 for
+ *   every column or max_iter corrections.  Once every column's residual is below
+ *   1e4 tol, a sweep updates r -= A d instead, with A d in plain FP32 (about 1e-6
+ *   relative; d is as small as r, so the update's error stays near tol / 100).
  *   f         host or device float64 column-major [n_nodes][nrhs].
  *   u         device float64 column-major [n_dof][nrhs].
  *   iters_out host int or NULL: refinement steps taken (0 for FP64).
