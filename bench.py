@@ -75,8 +75,8 @@ TRAFFIC = {
     # ncu capture of one 17-vector double-float launch on the 16^3 parallelepiped (units:
     # 14,392,119 nonzeros of the tables, read once per launch from their two list layouts)
     "k_apply_lists": {"source": "solve.cu",
-                      "sha256": "96372b4c78b7e0a6e282bca723b8ea3f8d4aa9b844f46a26f162a958d565fe8f",
-                      "bytes": 433890048 + 4170496, "units": 14392119},
+                      "sha256": "338f5e8603fcac2521983a70e9b21d81327abaefc04680a6d409ed64289638c0",
+                      "bytes": 433901312 + 5169152, "units": 14392119},
 }
 
 def _source_sha(name):

@@ -1597,7 +1597,7 @@ struct ListAxes {
 };
 
 constexpr int kListThreads = 256;
-constexpr int kListBatch = 2;   // list entries whose loads are in flight together
+constexpr int kListBatch = 3;   // list entries whose loads are in flight together (timed: 3 of 2, 3, 4)
 
 template <int NR, int VS, bool DF>
 __global__ void __launch_bounds__(kListThreads, 3) k_apply_lists(const __grid_constant__ ListAxes P,
