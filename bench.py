@@ -127,8 +127,11 @@ def kernel_rooflines(kms: dict, cnt: dict, n_dof: int, precision: str, peaks: di
 
     walk_tables  HBM: 160 B (one tet record) per walked segment; FP64 side: 25 flops per
                  segment against the FP64 rate
-    split        HBM: per table element 16 B read (L and R pairs), 8 B written (W R pair)
-                 and the four operand halves (2 B each for BF16, 4 B for TF32)
+    split        HBM: per table element 16 B read (L and R pairs) and the four operand halves
+                 written (2 B each for BF16, 4 B for TF32); then, where the apply runs from
+                 the nonzero lists, their entries (10 B per nonzero of L or W R in each of the
+                 row-major and Gauss-point-major layouts), else the dense W R pair (8 B per
+                 element)
     contract     tensor: algorithmic flops sum_g 4 nnz(L[g]) nnz(R[g]) per axis (when
                  counted) and the executed split-product MMA flops (3 x 2 D_b^2 G_b)
     factor       FP32 pipe: n^3 / 3 flops
@@ -153,12 +156,19 @@ def kernel_rooflines(kms: dict, cnt: dict, n_dof: int, precision: str, peaks: di
             "fp64_tflops": fl, "fp64_peak_tflops": FP64_TFLOPS, "fp64_frac": fl / FP64_TFLOPS}
     s = kms.get("split", (0, 0))
     if s[0] > 0:
-        per = 16 + 8 + (8 if precision == "bf16x3" else 16 if precision == "tf32x3" else 0)
-        gbs = per * elems / (s[0] * 1e-3) / 1e9
-        out["split"] = {"kernel": "k_split_ops", "bound": "hbm", "unit": "GB/s", "achieved": gbs,
+        per = 16 + (8 if precision == "bf16x3" else 16 if precision == "tf32x3" else 0)
+        snz = cnt.get("table_nnz") or 0
+        slists = bool(snz) and cnt.get("apply_lists", True)
+        nbytes = per * elems + (2 * 10 * snz if slists else 8 * elems)
+        gbs = nbytes / (s[0] * 1e-3) / 1e9
+        tail = (f"the nonzero lists, 2 x 10 B per nonzero x {snz} nonzeros" if slists else
+                "the dense W R pair, 8 B per element")
+        out["split"] = {"kernel": "k_split_ops (+ k_gp_lists)" if slists else "k_split_ops",
+                        "bound": "hbm", "unit": "GB/s", "achieved": gbs,
                         "peak": hbm, "frac": gbs / hbm, "launches": s[1],
                         "launch_ms": s[0] / s[1], "traffic": None,
-                        "algorithmic": f"{per} B per table element x {elems:.0f} elements"}
+                        "algorithmic": f"{per} B per table element x {elems:.0f} elements, plus "
+                                       + tail}
     c = kms.get("contract", (0, 0))
     if c[0] > 0:
         ratio = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0}.get(precision)

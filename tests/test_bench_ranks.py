@@ -105,6 +105,15 @@ def test_kernel_rooflines():
                                 "parallelepiped24")["apply"]
     assert nz["achieved"] == pytest.approx(2 * 13 * 150e6 * 51 / 24.0e-3 / 1e12)
     assert nz["nonzero_fraction_of_bin_tables"] == pytest.approx(150e6 / (2 * 134e6))
+    # split: 16 B read + BF16 operands (8 B) per element, then the dense W R pair (8 B) or the
+    # two list layouts (2 x 10 B per nonzero)
+    assert r["split"]["achieved"] == pytest.approx((16 + 8 + 8) * 134e6 / 1.0e-3 / 1e9)
+    sl = bench.kernel_rooflines(kms, dict(cnt, table_nnz=150_000_000, apply_lists=True), 12167,
+                                "bf16x3", peaks, "parallelepiped24")["split"]
+    assert sl["achieved"] == pytest.approx(((16 + 8) * 134e6 + 20 * 150e6) / 1.0e-3 / 1e9)
+    sd = bench.kernel_rooflines(kms, dict(cnt, table_nnz=150_000_000, apply_lists=False), 12167,
+                                "tf32x3", peaks, "parallelepiped24")["split"]
+    assert sd["achieved"] == pytest.approx((16 + 16 + 8) * 134e6 / 1.0e-3 / 1e9)
     assert r["chain"]["launch_ms"] == pytest.approx(0.5)
     t = bench.kernel_rooflines(kms, cnt, 12167, "tf32x3", peaks, "parallelepiped24")
     assert t["contract"]["peak"] == pytest.approx(1894.9 * 1.1 / 2.25)
