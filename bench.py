@@ -712,7 +712,7 @@ def run_batch(args, torch, fem3, inputs, stream):
     return out
 
 
-def main():
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     # about 30 steps of 50-80 ms keep the timed region long enough for several 200 ms
@@ -735,7 +735,11 @@ def main():
                          "one, 0 by size (tensor cores from 4,096 dofs)")
     ap.add_argument("--bin-scale", type=float, default=0.5,
                     help="transverse bin width in mean cell sizes (template granularity)")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -162,3 +162,25 @@ def test_cpu_baseline_all_core_leg(monkeypatch):
     assert out["all_cores"]["cores"] == 2 and out["all_cores"]["value"] > 0
     monkeypatch.setattr(bench, "_oracle_threads", lambda: 1)
     assert "all_cores" not in bench.cpu_baseline("cube16_jitter", mesh, F)
+
+
+def test_profile_commands_parse():
+    """Every bench command that a summary under profiles/ gives (the plain run and the one under
+    ncu) is accepted by bench.py's own argument parser: the summaries name runnable commands."""
+    import glob
+    import re
+    import shlex
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    found = 0
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read().replace("\\\n", " ")
+        for m in re.finditer(r"python bench\.py([^\n`]*)", text):
+            args = shlex.split(m.group(1))
+            if args and args[0].startswith("`"):
+                continue
+            bench.build_parser().parse_args(args)
+            found += 1
+    assert found >= 8, found
